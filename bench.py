@@ -1,0 +1,382 @@
+"""Benchmark of the DG-MHD hot path: DoF-updates/s per RK stage.
+
+Default workload: 3D 256^3 periodic box, degree 2 (10 Legendre modes, 27 Gauss
+points per cell), GLM cleaning (9 variables, 90 DoF per cell), FP32 form with
+FP64 cell means; seeded decaying-turbulence start (solenoidal v, E(k) ~ k^-2 on
+2 <= |k| <= 8, rms Mach 2, B0 = (0.5, 0, 0), rho = p = 1). A step is one
+SSP-RK3 step (3 RK stages, each a full application of the DG operator plus the
+SSP combination; the timestep reduction once per step). value = DoF x stages
+/ device time. The plain FP64 path on the same workload is timed as well.
+
+Launch: python bench.py [--gpus N --steps K --warmup W] (torchrun for N > 1:
+every rank runs an independent replica: weak scaling, no collective on the
+data path). --impl reference times the CPU oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIGS = {
+    "turb256": dict(workload="3D 256^3 periodic, degree 2, GLM, decaying turbulence (Mach 2)", D=3, n=256, d=2,
+                    divb="glm"),
+    "turb128": dict(workload="3D 128^3 periodic, degree 2, GLM, decaying turbulence (Mach 2)", D=3, n=128, d=2,
+                    divb="glm"),
+    "fourier64": dict(workload="3D 64^3 periodic, degree 3, GLM, seeded smooth Fourier state", D=3, n=64, d=3,
+                      divb="glm"),
+}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_turbulence(sol, cfg, device):
+    """Project the turbulence start onto the basis with the library's own
+    projection kernel; point values are built on the GPU slab by slab."""
+    import torch
+    from paper_1806_02343_gb300 import workloads as W
+    n, d = cfg["n"], cfg["d"]
+    npts = d + 1
+    gx1, _ = __import__("numpy").polynomial.legendre.leggauss(npts)
+    T = W.Turbulence3D(nvar=9)
+    coords = ((torch.arange(n, device=device, dtype=torch.float64)[:, None] + 0.5
+               + 0.5 * torch.as_tensor(gx1, device=device)[None, :]) / n).reshape(-1)  # [n*npts]
+    Q = npts ** 3
+    nodal = torch.empty((9, Q, sol.stride), dtype=torch.float64, device=device)
+    zs = max(1, 2 ** 22 // (n * n))  # cells per z-slab
+    for z0 in range(0, n, zs):
+        z1 = min(n, z0 + zs)
+        gz = coords[z0 * npts:z1 * npts]
+        v = T.grid_velocity(coords, coords, gz)          # [x, y, z, 3]
+        U = T.state_from_velocity(v)                      # [x, y, z, 9]
+        nz = z1 - z0
+        U = U.reshape(n, npts, n, npts, nz, npts, 9)      # ix qx iy qy iz qz var
+        U = U.permute(6, 1, 3, 5, 4, 2, 0).reshape(9, Q, nz * n * n)
+        nodal[:, :, z0 * n * n:z1 * n * n] = U
+        del v, U
+    return nodal, npts
+
+
+def build_fourier(sol, cfg, device):
+    import numpy as np
+    import torch
+    from paper_1806_02343_gb300 import workloads as W
+    n, d = cfg["n"], cfg["d"]
+    npts = d + 1
+    g1, _ = np.polynomial.legendre.leggauss(npts)
+    F = W.SmoothFourier3D(nvar=9)
+    Q = npts ** 3
+    nodal = torch.empty((9, Q, sol.stride), dtype=torch.float64, device=device)
+    c1 = ((torch.arange(n, device=device, dtype=torch.float64)[:, None] + 0.5
+           + 0.5 * torch.as_tensor(g1, device=device)[None, :]) / n).reshape(-1)
+    X, Y, Z = torch.meshgrid(c1, c1, c1, indexing="ij")
+    U = F(torch.stack([X, Y, Z], -1))
+    U = U.reshape(n, npts, n, npts, n, npts, 9).permute(6, 1, 3, 5, 4, 2, 0).reshape(9, Q, n ** 3)
+    nodal[:, :, : n ** 3] = U
+    return nodal, npts
+
+
+def run_ours(args, cfg, rank, world, device):
+    import torch
+    from paper_1806_02343_gb300 import binding as Bd
+    from paper_1806_02343_gb300.binding import Solver
+
+    D, n, d, divb = cfg["D"], cfg["n"], cfg["d"], cfg["divb"]
+    ncell = n ** D
+    res = {}
+
+    def make(prec):
+        sol = Solver(D, (n,) * D, d, divb, precision=prec)
+        w, wm = sol.alloc_state(device)
+        builder = build_turbulence if "turb" in cfg["name"] else build_fourier
+        nodal, npts = builder(sol, cfg, device)
+        sol.project(nodal, npts, w, wm)
+        del nodal
+        torch.cuda.synchronize()
+        return sol, w, wm
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ------------------------------------------------------------ FP32 form (value)
+    sol, w, wm = make(Bd.DG_PREC_FP32MIX)
+    dof = ncell * sol.nrows
+    for _ in range(args.warmup):
+        sol.step(w, wm)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(device.index if device.index is not None else 0)
+    barrier()
+    torch.cuda.synchronize()
+    sol.profile(True)
+    clk.start()
+    ev0.record(st)
+    for _ in range(args.steps):
+        sol.step(w, wm)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = sol.launch_count()
+    kern = {}
+    for k, name in ((Bd.KIND_FACE, "face_flux"), (Bd.KIND_CELL, "cell_update"), (Bd.KIND_DT, "timestep")):
+        t, nl = sol.profile_read(k)
+        kern[name] = {"ms_total": t, "launches": nl, "ms_per_launch": t / max(nl, 1)}
+    sol.profile(False)
+    status = sol.status()
+    finite = bool(torch.isfinite(wm[:, :ncell]).all().item())
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    stages = 3 * args.steps
+    value = dof * stages * world / (ms * 1e-3)
+    res.update(dict(ms=ms, value=value, dof=dof, launches=launches, kern=kern, clocks=clocks, status=status,
+                    finite=finite))
+
+    # roofline of the dominant kernel: algorithmic bytes of a stage attributed to the
+    # cell-update kernel (it reads the stage input and u^n and writes the stage output)
+    hbm, src = _peaks()
+    nf32 = sol.nrows - sol.nmean
+    bytes_cell = nf32 * 4 * (1 + 2.0 / 3.0 + 1) + sol.nmean * 8 * (1 + 2.0 / 3.0 + 1)
+    dom = max(("face_flux", "cell_update"), key=lambda k: kern[k]["ms_total"])
+    per_launch_ms = kern["cell_update"]["ms_per_launch"]
+    achieved = bytes_cell * ncell / (per_launch_ms * 1e-3) / 1e9
+    res["roofline"] = {"bound": "hbm", "kernel": "k_cell (stage algorithmic bytes)", "dominant_kernel": dom,
+                       "achieved": achieved, "peak": hbm, "peak_source": src, "unit": "GB/s",
+                       "frac": achieved / hbm, "traffic": None,
+                       "bytes_per_cell_stage": bytes_cell,
+                       "stage_frac": bytes_cell * ncell * stages / (ms * 1e-3) / 1e9 / hbm}
+
+    # ------------------------------------------------------------ end to end through the C ABI
+    # host (pinned) state in, one step, state out
+    hw = torch.empty(w.shape, dtype=w.dtype, pin_memory=True)
+    hm = torch.empty(wm.shape, dtype=wm.dtype, pin_memory=True)
+    hw.copy_(w)
+    hm.copy_(wm)
+    torch.cuda.synchronize()
+    ke = max(1, min(args.steps, 2))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(st)
+    for _ in range(ke):
+        w.copy_(hw, non_blocking=True)
+        wm.copy_(hm, non_blocking=True)
+        sol.step(w, wm)
+        hw.copy_(w, non_blocking=True)
+        hm.copy_(wm, non_blocking=True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ems = e0.elapsed_time(e1)
+    bi = w.numel() * w.element_size() + wm.numel() * wm.element_size()
+    res["e2e"] = {"value": dof * 3 * ke * world / (ems * 1e-3), "unit": "DoF-updates/s",
+                  "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi, "steps": ke}
+    del sol, w, wm, hw, hm
+    torch.cuda.empty_cache()
+
+    # ------------------------------------------------------------ plain FP64 path, same workload
+    if not args.skip_fp64:
+        sol, w, _ = make(Bd.DG_PREC_FP64)
+        sol.step(w)
+        torch.cuda.synchronize()
+        k64 = max(1, args.fp64_steps)
+        e0.record(st)
+        for _ in range(k64):
+            sol.step(w)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        res["fp64_plain"] = {"value": dof * 3 * k64 / (ms64 * 1e-3), "unit": "DoF-updates/s",
+                             "ms_per_step": ms64 / k64, "steps": k64, "status": sol.status()}
+        del sol, w
+        torch.cuda.empty_cache()
+    return res
+
+
+def _oracle_sample(cfg, nsample):
+    """Oracle scheme and projected start on a periodic nsample^3 box (the same
+    scheme and initial condition as the GPU workload, fewer cells)."""
+    import numpy as np
+    from oracle.dg import Scheme
+    from paper_1806_02343_gb300 import workloads as W
+    S = Scheme(cfg["D"], cfg["d"], cfg["divb"], 5.0 / 3.0, nsample)
+    npts = cfg["d"] + 1
+    if "turb" in cfg["name"]:
+        T = W.Turbulence3D(nvar=9)
+        g1, _ = np.polynomial.legendre.leggauss(npts)
+        c1 = ((np.arange(nsample)[:, None] + 0.5 + 0.5 * g1[None, :]) / nsample).reshape(-1)
+        v = T.grid_velocity(c1, c1, c1)                       # [x, y, z, 3] on the Gauss grid
+        U = T.state_from_velocity(v).reshape(nsample, npts, nsample, npts, nsample, npts, 9)
+        # -> [cell (x fastest), q (axis 0 slowest), var]
+        U = U.transpose(4, 2, 0, 1, 3, 5, 6).reshape(nsample ** 3, npts ** 3, 9)
+        cache = {}
+
+        def fn(x):
+            return U
+
+        w = S.project(fn, npts=npts)
+    else:
+        w = S.project(W.SmoothFourier3D(nvar=9), npts=npts)
+    return S, w
+
+
+def cpu_baseline(cfg, nsample=24, steps=1, warmup=0, sample=None):
+    """The CPU oracle as it stands: SSP-RK3 steps on a bounded sample (a
+    periodic nsample^3 box of the same scheme and initial condition)."""
+    S, w = sample if sample is not None else _oracle_sample(cfg, nsample)
+    for _ in range(warmup):
+        S.step(w)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        w, dt = S.step(w)
+    el = time.perf_counter() - t0
+    dof = S.C * S.N
+    return {"value": dof * 3 * steps / el, "unit": "DoF-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"SSP-RK3 steps of the same scheme and start on a {nsample}^3 periodic box "
+                      f"({S.C} cells x {S.N} DoF), numpy FP64, single thread", "seconds": el}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="turb256", choices=sorted(CONFIGS))
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=24)
+    args = ap.parse_args()
+    cfg = dict(CONFIGS[args.config])
+    cfg["name"] = args.config
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    config = {"workload": cfg["workload"], "cells": cfg["n"] ** cfg["D"], "degree": cfg["d"],
+              "divb": cfg["divb"], "limiter": "off", "rk": "SSP-RK3",
+              "l2_flush": "inputs larger than L2 (state >= 6 GB)", "replicas_per_gpu": 1}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        sample = _oracle_sample(cfg, args.cpu_sample)
+        cb = cpu_baseline(cfg, args.cpu_sample, steps=args.steps, warmup=args.warmup, sample=sample)
+        v = cb["value"]
+        line = {"impl": "reference", "metric": "DG-MHD DoF-updates/s per RK stage", "value": v,
+                "unit": "DoF-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": cb["seconds"] * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": {"kind": cb["kind"], "cores": cb["cores"], "sample": cb["sample"], "value": v,
+                                 "unit": "DoF-updates/s"},
+                "e2e": {"value": v, "unit": "DoF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_1806_02343_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    res = run_ours(args, cfg, rank, world, device)
+    if rank != 0:
+        return
+    cb = cpu_baseline(cfg, args.cpu_sample)
+    line = {
+        "metric": "DG-MHD DoF-updates/s per RK stage", "value": res["value"], "unit": "DoF-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 cell means)",
+        "data": "synthetic", "config": config, "e2e": res["e2e"], "roofline": res["roofline"],
+        "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "clocks": res["clocks"], "gpu_launches": res["launches"], "kernels": res["kern"],
+        "fp64_plain": res.get("fp64_plain"), "status": res["status"], "finite": res["finite"],
+        "dof": res["dof"],
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * dg_mhd.h -- C ABI of the GB300 DG-MHD hot path.
+ *
+ * The operator is the modal discontinuous Galerkin scheme for ideal MHD of
+ * Guillet, Pakmor, Springel, Chandrashekar & Klingenberg (2018):
+ *   du/dt + sum_a d f_a(u)/dx_a = s                      (Sec. 2, eq. cns-eq)
+ *   M_l dw_l/dt = (2/dx)[ int f_a . d_a phi_l - oint F*.n phi_l ] + int s.phi_l
+ *                                                        (Sec. 3.5, eq. wdot)
+ * with HLLD face fluxes (Sec. 4.1.2), Powell source terms on a locally
+ * divergence-free (LDF) B basis (Sec. 4.1.3) or GLM cleaning (Sec. 4.1.5),
+ * TVB-characteristic and positivity limiters (Sec. 4.2, 4.3), the CFL
+ * timestep (Sec. 3.6, eq. cfl; Powell: eq. powell_dt) and SSP Runge-Kutta.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Pointers named w, wmean, rhs, rhs_mean, dt_dev are DEVICE pointers owned by
+ * the caller. Pointers inside dg_mesh_desc and `nodal` of dg_mhd_project are
+ * HOST or DEVICE as stated. `stream` is a cudaStream_t passed as void*
+ * (NULL = legacy default stream). Every call is asynchronous on `stream`
+ * unless stated; nothing synchronises the host except dg_mhd_status(ctx, 1)
+ * and dg_mhd_init / dg_mhd_destroy.
+ *
+ * State layout (SoA, coalesced along cells): w[row][cell], row-major with the
+ * cell index fastest, n_cells cells padded to `cell_stride` (a multiple of 4).
+ * Rows: for the GLM scheme 9 Legendre variables x n(d) modes
+ * (rho, m_x, m_y, m_z, E, B_x, B_y, B_z, psi; row = var*n + mode). For the
+ * Powell scheme 5 Legendre hydro variables x n(d), then N_div LDF rows for B,
+ * then (2D only) n(d) Legendre rows for B_z. Modes are ordered by total degree,
+ * then k1 descending, then k2 descending; Legendre polynomials have l_k(1) = 1,
+ * so mode 0 is the cell mean. LDF rows follow App. A.2 (curls of Legendre
+ * potentials, stable-sorted by degree, unnormalised Gram-Schmidt).
+ *
+ * Precision: DG_PREC_FP64 -> w/rhs are double; wmean/rhs_mean unused (NULL).
+ * DG_PREC_FP32MIX -> w/rhs are float and the degree-0 rows are ALSO held in
+ * double in wmean[mean_row][cell] (mean rows = Legendre mode 0 of each
+ * variable, then the degree-0 LDF rows, in row order); the double copy is
+ * authoritative and the float mode-0 entries mirror it.
+ *
+ * Errors: every int-returning call returns a dg_status. Nothing throws or
+ * aborts. Errors found on the device (non-finite state, positivity floor
+ * used, c_h below the signal speed, timed-out wait) are latched in a device
+ * status word and reported by dg_mhd_status.
+ */
+#ifndef DG_MHD_H
+#define DG_MHD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_mhd_ctx dg_mhd_ctx;
+
+typedef enum {
+  DG_OK = 0,
+  DG_E_ARG = -1,         /* bad argument (NULL, size, enum out of range)      */
+  DG_E_MESH = -2,        /* invalid mesh description                           */
+  DG_E_CUDA = -3,        /* a CUDA runtime call failed                         */
+  DG_E_NONFINITE = -4,   /* NaN/Inf found in the state or the timestep        */
+  DG_E_CH = -5,          /* GLM: c_h below the largest signal speed (Sec 4.1.5)*/
+  DG_E_TIMEOUT = -6,     /* a bounded device wait gave up                      */
+  DG_E_UNSUPPORTED = -7, /* combination not built (e.g. degree > 3)            */
+  DG_W_FLOOR = 1         /* warning: positivity floor injected mass/energy     */
+} dg_status;
+
+enum { DG_DIVB_POWELL = 0, DG_DIVB_GLM = 1 };
+enum { DG_PREC_FP64 = 0, DG_PREC_FP32MIX = 1 };
+enum { DG_LIMIT_OFF = 0, DG_LIMIT_TVB = 1, DG_LIMIT_MLP = 2 };
+
+/* Mesh: a uniform periodic box of n[0] x n[1] (x n[2]) cubic cells, cells
+ * numbered x-fastest (Sec. 3.1: non-overlapping cubes; the octree of
+ * Sec. 4.4 with every leaf on one level). Host memory, copied at init. */
+typedef struct {
+  int dim;            /* 2 or 3                                             */
+  int32_t n[3];       /* cells per axis (n[2] ignored for dim 2)            */
+  double box_len;     /* physical side length of a cell row along x: n[0]*dx */
+  int periodic;       /* must be 1                                           */
+} dg_mesh_desc;
+
+/* Parameters of Sec. 3.6, 4.1, 4.2, 4.3, 5.1 (defaults in brackets). */
+typedef struct {
+  double cfl;         /* C of eq. cfl                                [0.3]  */
+  double cfl_glm;     /* C' of Sec. 4.1.5, C < C' < 1                 [0.9]  */
+  double c_r;         /* c_p^2 / c_h                                 [0.18] */
+  double c_h_fixed;   /* > 0: use this global c_h (AMR practice)      [0]    */
+  double eta_powell;  /* eq. powell_dt threshold                      [0.2]  */
+  double eps_hlld;    /* relative degeneracy test of the HLLD * states [1e-8]*/
+  double Mtilde;      /* TVB threshold M~ (Sec. 4.2.1, 5.1)          [5]    */
+  double beta;        /* minmod factor                               [2]    */
+  double tvb_eps;     /* trigger threshold epsilon                   [1e-8] */
+  double eps_rho;     /* positivity floors (Sec. 4.3, 5.1)           [1e-12]*/
+  double eps_p;       /*                                             [1e-12]*/
+  int precision;      /* DG_PREC_*                                   [FP64] */
+  int limiter;        /* DG_LIMIT_*                                  [OFF]  */
+  int positivity;     /* 1: positivity limiter on                    [0]    */
+} dg_mhd_params;
+
+/* Fills *p with the defaults listed above. */
+void dg_mhd_default_params(dg_mhd_params* p);
+
+/* Builds the basis and quadrature tables (Sec. 3.2, 3.3, 3.5; App. A), the
+ * face lists, and the device scratch for one mesh. degree d in 0..3;
+ * divB_scheme DG_DIVB_*; gamma > 1. p NULL = defaults. On success *out owns
+ * all device memory it allocated; release it with dg_mhd_destroy.
+ * Uses the current CUDA device. Synchronous. */
+int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double gamma,
+                const dg_mhd_params* p, dg_mhd_ctx** out);
+
+/* Layout of the caller's buffers: rows per cell, degree-0 ("mean") rows per
+ * cell, cells, and the cell stride (elements between consecutive rows). */
+int dg_mhd_state_layout(const dg_mhd_ctx* ctx, int64_t* n_rows, int64_t* n_mean_rows,
+                        int64_t* n_cells, int64_t* cell_stride);
+
+/* L2 projection of point values onto the basis (eq. u-exp inverted with the
+ * diagonal mass matrix, Sec. 3.1): nodal[var][q][cell] (DEVICE, double,
+ * cell index fastest with stride cell_stride) holds the conserved variables at
+ * the npts^dim tensor Gauss-Legendre points of each cell (last axis fastest);
+ * npts in 1..8. Writes w (and wmean in FP32MIX). */
+int dg_mhd_project(dg_mhd_ctx* ctx, const double* nodal, int npts, void* w, double* wmean,
+                   void* stream);
+
+/* Sets the GLM wave speed c_h and damping rate c_h^2/c_p^2 used by
+ * dg_mhd_rhs (Sec. 4.1.5). dg_mhd_dt and dg_mhd_step set them on the device
+ * themselves; this call is for evaluating the operator at chosen values. */
+int dg_mhd_set_glm(dg_mhd_ctx* ctx, double c_h, double damping_rate, void* stream);
+
+/* One application of the spatial operator, eq. wdot: rhs = dw/dt for every
+ * cell (projection, volume integral, HLLD face fluxes, Powell or GLM terms).
+ * w is not modified. rhs has the layout of w. */
+int dg_mhd_rhs(dg_mhd_ctx* ctx, const void* w, const double* wmean, void* rhs, double* rhs_mean,
+               void* stream);
+
+/* Limiters of Sec. 4.2-4.3 in place on w: TVB-characteristic slope limiter
+ * (with the LDF slope fix of Sec. 4.2.4 for Powell) if enabled, then the
+ * positivity limiter if enabled. troubled (DEVICE, nullable) receives 1 for
+ * cells whose slopes the TVB limiter modified, else 0. */
+int dg_mhd_limit(dg_mhd_ctx* ctx, void* w, double* wmean, uint8_t* troubled, void* stream);
+
+/* Global timestep: eq. cfl from cell means, and eq. powell_dt for Powell
+ * (|div B| from the face jumps of App. C eq. divb-cell). Writes dt to the
+ * DEVICE scalar *dt_dev and, for GLM, sets c_h and the damping rate. */
+int dg_mhd_dt(dg_mhd_ctx* ctx, const void* w, const double* wmean, double* dt_dev, void* stream);
+
+/* One SSP-RK3 step (Shu-Osher form, Sec. 3.6) in place on w (and wmean).
+ * dt_dev: DEVICE scalar with the step, or NULL to compute it first with
+ * dg_mhd_dt (then read it back with dg_mhd_last_dt). Limiters, if enabled,
+ * are applied to every stage input before it is evaluated (Sec. 4.3). */
+int dg_mhd_step(dg_mhd_ctx* ctx, void* w, double* wmean, const double* dt_dev, void* stream);
+
+/* Device address of the timestep computed by the last dg_mhd_dt/step call. */
+const double* dg_mhd_last_dt(const dg_mhd_ctx* ctx);
+
+/* Reads the device status word. sync = 1: synchronise the stream first and
+ * clear the word after reading. Returns DG_OK, a latched error or DG_W_FLOOR. */
+int dg_mhd_status(dg_mhd_ctx* ctx, int sync);
+
+/* Measurement support (no counterpart in the paper). Kernel kinds:
+ * 0 face flux, 1 cell update, 2 timestep, 3 limiter, 4 projection.
+ * dg_mhd_profile(ctx, 1) resets the counters and, from then on, records a
+ * CUDA event pair on the launch stream around every kernel launch;
+ * dg_mhd_profile(ctx, 0) stops recording (launches are still counted).
+ * dg_mhd_profile_read synchronises the device and returns, for one kind, the
+ * summed event-timed device milliseconds and the number of launches since the
+ * last reset. dg_mhd_launch_count returns all launches since the last reset. */
+int dg_mhd_profile(dg_mhd_ctx* ctx, int enable);
+int dg_mhd_profile_read(dg_mhd_ctx* ctx, int kind, double* total_ms, int64_t* launches);
+int64_t dg_mhd_launch_count(const dg_mhd_ctx* ctx);
+
+/* Releases every device allocation of ctx. ctx may be NULL. */
+void dg_mhd_destroy(dg_mhd_ctx* ctx);
+
+/* Static string for a dg_status value. */
+const char* dg_mhd_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_MHD_H */

@@ -56,9 +56,8 @@ class Scheme:
         self.D, self.d, self.divb, self.gamma = D, d, divb, gamma
         self.P = params or Params()
         self.ncell = tuple([ncell] * D) if np.isscalar(ncell) else tuple(ncell)
-        self.L = L
+        self.L = L                      # side of the box along x; cells are cubes
         self.dx = L / self.ncell[0]
-        assert all(abs(L / n - self.dx) < 1e-15 for n in self.ncell)
         self.C = int(np.prod(self.ncell))
         self.V = 9 if divb == "glm" else 8
         self.modes = B.mode_list(D, d)
@@ -283,7 +282,7 @@ class Scheme:
         u = self.eval_points(w, self.synth(qp))
         x = self.centers[:, None, :] + 0.5 * self.dx * qp[None, :, :]
         ur = fn_ref(x)
-        vol = self.L ** self.D
+        vol = float(np.prod(self.ncell)) * self.dx ** self.D
         cell = (0.5 * self.dx) ** self.D / vol
         err = np.einsum("cqv,q->v", np.abs(u - ur), qw) * cell
         ref = np.einsum("cqv,q->v", np.abs(ur), qw) * cell

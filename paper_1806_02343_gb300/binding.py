@@ -1,0 +1,194 @@
+"""ctypes binding of the C ABI in include/dg_mhd.h (argument marshalling only).
+
+Every numerical step runs in the CUDA library; this module only loads it,
+passes device pointers from torch tensors and the current CUDA stream, and
+turns status codes into exceptions. There is no CPU fallback: if the library
+is missing, `lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libdgmhd.so")
+
+DG_OK, DG_W_FLOOR = 0, 1
+DG_DIVB_POWELL, DG_DIVB_GLM = 0, 1
+DG_PREC_FP64, DG_PREC_FP32MIX = 0, 1
+DG_LIMIT_OFF, DG_LIMIT_TVB, DG_LIMIT_MLP = 0, 1, 2
+
+# every entry point declared in include/dg_mhd.h
+EXPORTS = [
+    "dg_mhd_default_params", "dg_mhd_init", "dg_mhd_state_layout", "dg_mhd_project", "dg_mhd_set_glm",
+    "dg_mhd_rhs", "dg_mhd_limit", "dg_mhd_dt", "dg_mhd_step", "dg_mhd_last_dt", "dg_mhd_status",
+    "dg_mhd_profile", "dg_mhd_profile_read", "dg_mhd_launch_count", "dg_mhd_destroy", "dg_mhd_strerror",
+]
+KIND_FACE, KIND_CELL, KIND_DT, KIND_LIMIT, KIND_PROJECT = range(5)
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int32 * 3), ("box_len", ctypes.c_double),
+                ("periodic", ctypes.c_int)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("cfl", "cfl_glm", "c_r", "c_h_fixed", "eta_powell", "eps_hlld",
+                                               "Mtilde", "beta", "tvb_eps", "eps_rho", "eps_p")] + \
+               [(k, ctypes.c_int) for k in ("precision", "limiter", "positivity")]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library {LIB_PATH} is not built (run __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64p, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p
+    L.dg_mhd_default_params.argtypes = [ctypes.POINTER(Params)]
+    L.dg_mhd_default_params.restype = None
+    L.dg_mhd_init.argtypes = [ctypes.POINTER(MeshDesc), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                              ctypes.POINTER(Params), ctypes.POINTER(vp)]
+    L.dg_mhd_state_layout.argtypes = [vp, i64p, i64p, i64p, i64p]
+    L.dg_mhd_project.argtypes = [vp, dp, ctypes.c_int, vp, dp, vp]
+    L.dg_mhd_set_glm.argtypes = [vp, ctypes.c_double, ctypes.c_double, vp]
+    L.dg_mhd_rhs.argtypes = [vp, vp, dp, vp, dp, vp]
+    L.dg_mhd_limit.argtypes = [vp, vp, dp, vp, vp]
+    L.dg_mhd_dt.argtypes = [vp, vp, dp, dp, vp]
+    L.dg_mhd_step.argtypes = [vp, vp, dp, dp, vp]
+    L.dg_mhd_last_dt.argtypes = [vp]
+    L.dg_mhd_last_dt.restype = ctypes.c_void_p
+    L.dg_mhd_status.argtypes = [vp, ctypes.c_int]
+    L.dg_mhd_profile.argtypes = [vp, ctypes.c_int]
+    L.dg_mhd_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), i64p]
+    L.dg_mhd_launch_count.argtypes = [vp]
+    L.dg_mhd_launch_count.restype = ctypes.c_int64
+    L.dg_mhd_destroy.argtypes = [vp]
+    L.dg_mhd_destroy.restype = None
+    L.dg_mhd_strerror.argtypes = [ctypes.c_int]
+    L.dg_mhd_strerror.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if not hasattr(L, name):
+            raise RuntimeError(f"{LIB_PATH} does not export {name}")
+    _lib = L
+    return L
+
+
+class DGError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {lib().dg_mhd_strerror(code).decode()} ({code})")
+        self.code = code
+
+
+def _check(code, what):
+    if code < 0:
+        raise DGError(code, what)
+    return code
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().dg_mhd_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Solver:
+    """Owns one dg_mhd_ctx. State tensors are allocated by the caller (torch) with
+    the layout reported by dg_mhd_state_layout: w[row][cell_stride]."""
+
+    def __init__(self, dim, n, degree, divb, gamma=5.0 / 3.0, box_len=1.0, **params):
+        import torch
+        L = lib()
+        m = MeshDesc()
+        m.dim = dim
+        nn = list(n) + [1] * (3 - len(n))
+        for a in range(3):
+            m.n[a] = nn[a]
+        m.box_len = box_len
+        m.periodic = 1
+        self.params = default_params(**params)
+        self.divb = divb
+        h = ctypes.c_void_p()
+        _check(L.dg_mhd_init(ctypes.byref(m), degree, DG_DIVB_GLM if divb == "glm" else DG_DIVB_POWELL, gamma,
+                             ctypes.byref(self.params), ctypes.byref(h)), "dg_mhd_init")
+        self.h = h
+        a, b, c, d = (ctypes.c_int64() for _ in range(4))
+        _check(L.dg_mhd_state_layout(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
+               "dg_mhd_state_layout")
+        self.nrows, self.nmean, self.ncell, self.stride = a.value, b.value, c.value, d.value
+        self.fp32 = self.params.precision == DG_PREC_FP32MIX
+        self.dtype = torch.float32 if self.fp32 else torch.float64
+        self.dim, self.degree = dim, degree
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().dg_mhd_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------- buffers
+    def alloc_state(self, device="cuda"):
+        import torch
+        w = torch.zeros((self.nrows, self.stride), dtype=self.dtype, device=device)
+        wm = torch.zeros((self.nmean, self.stride), dtype=torch.float64, device=device) if self.fp32 else None
+        return w, wm
+
+    # ------------------------------------------------------------- entry points
+    def project(self, nodal, npts, w, wmean=None):
+        _check(lib().dg_mhd_project(self.h, _ptr(nodal), npts, _ptr(w), _ptr(wmean), _stream()), "dg_mhd_project")
+
+    def set_glm(self, ch, kappa):
+        _check(lib().dg_mhd_set_glm(self.h, ch, kappa, _stream()), "dg_mhd_set_glm")
+
+    def rhs(self, w, wmean, out, outmean=None):
+        _check(lib().dg_mhd_rhs(self.h, _ptr(w), _ptr(wmean), _ptr(out), _ptr(outmean), _stream()), "dg_mhd_rhs")
+
+    def limit(self, w, wmean=None, troubled=None):
+        return _check(lib().dg_mhd_limit(self.h, _ptr(w), _ptr(wmean), _ptr(troubled), _stream()),
+                      "dg_mhd_limit")
+
+    def dt(self, w, wmean=None, out=None):
+        import torch
+        if out is None:
+            out = torch.zeros(1, dtype=torch.float64, device=w.device)
+        _check(lib().dg_mhd_dt(self.h, _ptr(w), _ptr(wmean), _ptr(out), _stream()), "dg_mhd_dt")
+        return out
+
+    def step(self, w, wmean=None, dt=None):
+        _check(lib().dg_mhd_step(self.h, _ptr(w), _ptr(wmean), _ptr(dt), _stream()), "dg_mhd_step")
+
+    def last_dt_ptr(self):
+        return lib().dg_mhd_last_dt(self.h)
+
+    def profile(self, enable):
+        _check(lib().dg_mhd_profile(self.h, 1 if enable else 0), "dg_mhd_profile")
+
+    def profile_read(self, kind):
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        _check(lib().dg_mhd_profile_read(self.h, kind, ctypes.byref(ms), ctypes.byref(n)), "dg_mhd_profile_read")
+        return ms.value, n.value
+
+    def launch_count(self):
+        return lib().dg_mhd_launch_count(self.h)
+
+    def status(self, sync=True):
+        return lib().dg_mhd_status(self.h, 1 if sync else 0)

@@ -1,0 +1,567 @@
+// C ABI of the DG-MHD library (see include/dg_mhd.h for the contract).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/dg_mhd.h"
+#include "dg_basis.h"
+#include "dg_ctx.h"
+#include "dg_kernels.cuh"
+#include "dg_limit.cuh"
+
+using namespace dgmhd;
+
+namespace {
+
+#define CK(x)                                   \
+  do {                                          \
+    if ((x) != cudaSuccess) return DG_E_CUDA;   \
+  } while (0)
+
+template <typename T>
+int upload(T** dst, const std::vector<double>& src) {
+  std::vector<T> tmp(src.begin(), src.end());
+  if (tmp.empty()) tmp.push_back(T(0));
+  CK(cudaMalloc(dst, tmp.size() * sizeof(T)));
+  CK(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return DG_OK;
+}
+
+struct HostTables {
+  std::vector<double> Pv, dPv, Pf, Lv, dLv, Lf, L0, wv, wf, minv;
+};
+
+// reference coordinates of volume point q (tensor rule, last axis fastest)
+void vol_point(int D, const std::vector<double>& x1, int q, double* xi) {
+  const int m = (int)x1.size();
+  for (int a = D - 1; a >= 0; --a) {
+    xi[a] = x1[q % m];
+    q /= m;
+  }
+  for (int a = D; a < 3; ++a) xi[a] = 0.0;
+}
+
+// point p of face f = 2*axis + side: tangential axes in increasing order, last fastest
+void face_point(int D, const std::vector<double>& x1, int f, int p, double* xi) {
+  const int a = f >> 1;
+  const int m = (int)x1.size();
+  int others[2], no = 0;
+  for (int b = 0; b < D; ++b)
+    if (b != a) others[no++] = b;
+  for (int j = no - 1; j >= 0; --j) {
+    xi[others[j]] = x1[p % m];
+    p /= m;
+  }
+  xi[a] = (f & 1) ? 1.0 : -1.0;
+  for (int b = D; b < 3; ++b) xi[b] = 0.0;
+}
+
+void build_host_tables(const Basis& B, const Geom& g, HostTables& h) {
+  std::vector<double> x1, w1;
+  gauss_legendre(g.nq1, x1, w1);
+  const int D = g.D, n = g.n, nd = g.ndiv, DB = g.DB, Qv = g.Qv, Qf = g.Qf;
+  h.wv.assign(Qv, 1.0);
+  for (int q = 0; q < Qv; ++q) {
+    int qq = q;
+    for (int a = 0; a < D; ++a) {
+      h.wv[q] *= w1[qq % g.nq1];
+      qq /= g.nq1;
+    }
+  }
+  h.wf.assign(Qf, 1.0);
+  for (int p = 0; p < Qf; ++p) {
+    int pp = p;
+    for (int a = 0; a < D - 1; ++a) {
+      h.wf[p] *= w1[pp % g.nq1];
+      pp /= g.nq1;
+    }
+  }
+  double xi[3];
+  h.Pv.assign((size_t)n * Qv, 0.0);
+  h.dPv.assign((size_t)D * n * Qv, 0.0);
+  for (int l = 0; l < n; ++l)
+    for (int q = 0; q < Qv; ++q) {
+      vol_point(D, x1, q, xi);
+      h.Pv[(size_t)l * Qv + q] = B.eval(B.leg[l], xi);
+      for (int a = 0; a < D; ++a) h.dPv[((size_t)a * n + l) * Qv + q] = B.eval_deriv(B.leg[l], a, xi);
+    }
+  h.Pf.assign((size_t)2 * D * n * Qf, 0.0);
+  for (int f = 0; f < 2 * D; ++f)
+    for (int l = 0; l < n; ++l)
+      for (int p = 0; p < Qf; ++p) {
+        face_point(D, x1, f, p, xi);
+        h.Pf[((size_t)f * n + l) * Qf + p] = B.eval(B.leg[l], xi);
+      }
+  h.Lv.assign((size_t)std::max(1, nd * DB * Qv), 0.0);
+  h.dLv.assign((size_t)std::max(1, D * nd * DB * Qv), 0.0);
+  h.Lf.assign((size_t)std::max(1, 2 * D * nd * DB * Qf), 0.0);
+  h.L0.assign((size_t)std::max(1, nd * DB), 0.0);
+  for (int j = 0; j < nd; ++j)
+    for (int c = 0; c < DB; ++c) {
+      for (int q = 0; q < Qv; ++q) {
+        vol_point(D, x1, q, xi);
+        h.Lv[((size_t)j * DB + c) * Qv + q] = B.eval(B.ldf[j][c], xi);
+        for (int a = 0; a < D; ++a)
+          h.dLv[(((size_t)a * nd + j) * DB + c) * Qv + q] = B.eval_deriv(B.ldf[j][c], a, xi);
+      }
+      for (int f = 0; f < 2 * D; ++f)
+        for (int p = 0; p < Qf; ++p) {
+          face_point(D, x1, f, p, xi);
+          h.Lf[(((size_t)f * nd + j) * DB + c) * Qf + p] = B.eval(B.ldf[j][c], xi);
+        }
+      if (B.ldf_deg[j] == 0) {
+        double z[3] = {0.0, 0.0, 0.0};
+        h.L0[(size_t)j * DB + c] = B.eval(B.ldf[j][c], z);
+      }
+    }
+  h.minv.assign(g.nrows, 0.0);
+  for (int r = 0; r < g.nrows; ++r) {
+    double m;
+    if (g.ldf0 >= 0 && r >= g.ldf0 && r < g.ldf0 + nd) m = B.ldf_mass[r - g.ldf0];
+    else if (g.bz2d >= 0 && r >= g.bz2d) m = B.leg_mass[r - g.bz2d];
+    else m = B.leg_mass[r % n];
+    h.minv[r] = 1.0 / m;
+  }
+}
+
+template <typename T>
+int upload_tables(const HostTables& h, Tables<T>& t) {
+  int e;
+  if ((e = upload(&t.Pv, h.Pv))) return e;
+  if ((e = upload(&t.dPv, h.dPv))) return e;
+  if ((e = upload(&t.Pf, h.Pf))) return e;
+  if ((e = upload(&t.Lv, h.Lv))) return e;
+  if ((e = upload(&t.dLv, h.dLv))) return e;
+  if ((e = upload(&t.Lf, h.Lf))) return e;
+  if ((e = upload(&t.L0, h.L0))) return e;
+  if ((e = upload(&t.wv, h.wv))) return e;
+  if ((e = upload(&t.wf, h.wf))) return e;
+  if ((e = upload(&t.minv, h.minv))) return e;
+  return DG_OK;
+}
+
+template <typename T>
+void free_tables(Tables<T>& t) {
+  T* ptrs[] = {t.Pv, t.dPv, t.Pf, t.Lv, t.dLv, t.Lf, t.L0, t.wv, t.wf, t.minv};
+  for (T* p : ptrs)
+    if (p) cudaFree(p);
+  t = Tables<T>();
+}
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline bool fp32(const Ctx& c) { return c.p.precision == DG_PREC_FP32MIX; }
+
+}  // namespace
+
+namespace dgmhd {
+
+void Prof::begin(int k, cudaStream_t st) {
+  launches[k] += 1;
+  if (!on) return;
+  while (pool.size() < used + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    pool.push_back(e);
+  }
+  cudaEventRecord(pool[used], st);
+  kind.push_back(k);
+}
+
+void Prof::end(int k, cudaStream_t st) {
+  (void)k;
+  if (!on || pool.size() < used + 2 || kind.size() * 2 != used + 2) return;
+  cudaEventRecord(pool[used + 1], st);
+  used += 2;
+}
+
+int Prof::collect() {
+  if (cudaDeviceSynchronize() != cudaSuccess) return DG_E_CUDA;
+  for (size_t i = 0; i + 1 < used; i += 2) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, pool[i], pool[i + 1]) == cudaSuccess) ms[kind[i / 2]] += t;
+  }
+  used = 0;
+  kind.clear();
+  return DG_OK;
+}
+
+void Prof::reset() {
+  for (int k = 0; k < KINDS; ++k) {
+    launches[k] = 0;
+    ms[k] = 0.0;
+  }
+  used = 0;
+  kind.clear();
+}
+
+void Prof::release() {
+  for (auto e : pool) cudaEventDestroy(e);
+  pool.clear();
+  reset();
+}
+
+}  // namespace dgmhd
+
+extern "C" {
+
+int dg_mhd_profile(dg_mhd_ctx* ctx, int enable) {
+  if (!ctx) return DG_E_ARG;
+  ctx->c.prof.reset();
+  ctx->c.prof.on = enable != 0;
+  return DG_OK;
+}
+
+int dg_mhd_profile_read(dg_mhd_ctx* ctx, int kind, double* total_ms, int64_t* launches) {
+  if (!ctx || kind < 0 || kind >= Prof::KINDS) return DG_E_ARG;
+  int e = ctx->c.prof.collect();
+  if (e) return e;
+  if (total_ms) *total_ms = ctx->c.prof.ms[kind];
+  if (launches) *launches = ctx->c.prof.launches[kind];
+  return DG_OK;
+}
+
+int64_t dg_mhd_launch_count(const dg_mhd_ctx* ctx) {
+  if (!ctx) return 0;
+  int64_t s = 0;
+  for (int k = 0; k < Prof::KINDS; ++k) s += ctx->c.prof.launches[k];
+  return s;
+}
+
+void dg_mhd_default_params(dg_mhd_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->cfl = 0.3;
+  p->cfl_glm = 0.9;
+  p->c_r = 0.18;
+  p->c_h_fixed = 0.0;
+  p->eta_powell = 0.2;
+  p->eps_hlld = 1e-8;
+  p->Mtilde = 5.0;
+  p->beta = 2.0;
+  p->tvb_eps = 1e-8;
+  p->eps_rho = 1e-12;
+  p->eps_p = 1e-12;
+  p->precision = DG_PREC_FP64;
+  p->limiter = DG_LIMIT_OFF;
+  p->positivity = 0;
+}
+
+const char* dg_mhd_strerror(int s) {
+  switch (s) {
+    case DG_OK: return "ok";
+    case DG_E_ARG: return "invalid argument";
+    case DG_E_MESH: return "invalid mesh";
+    case DG_E_CUDA: return "CUDA runtime error";
+    case DG_E_NONFINITE: return "non-finite state or timestep";
+    case DG_E_CH: return "GLM c_h below the signal speed";
+    case DG_E_TIMEOUT: return "bounded device wait timed out";
+    case DG_E_UNSUPPORTED: return "unsupported configuration";
+    case DG_W_FLOOR: return "positivity floor injected mass or energy";
+    default: return "unknown status";
+  }
+}
+
+void dg_mhd_destroy(dg_mhd_ctx* ctx) {
+  if (!ctx) return;
+  Ctx& c = ctx->c;
+  c.prof.release();
+  free_tables(c.t64);
+  free_tables(c.t32);
+  void* ptrs[] = {c.sc, c.face_buf, c.face_buf32, c.stage_buf[0], c.stage_buf[1], c.stage_buf[2],
+                  c.stage_mean[0], c.stage_mean[1], c.stage_mean[2], c.cellscratch, c.proj_tab, c.proj_w,
+                  c.troubled};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete c.hb;
+  delete ctx;
+}
+
+int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double gamma, const dg_mhd_params* p,
+                dg_mhd_ctx** out) {
+  if (!mesh || !out) return DG_E_ARG;
+  *out = nullptr;
+  if (mesh->dim != 2 && mesh->dim != 3) return DG_E_MESH;
+  if (!mesh->periodic) return DG_E_UNSUPPORTED;
+  if (degree < 0 || degree > MAXD) return DG_E_UNSUPPORTED;
+  if (divB_scheme != DG_DIVB_POWELL && divB_scheme != DG_DIVB_GLM) return DG_E_ARG;
+  if (!(gamma > 1.0)) return DG_E_ARG;
+  for (int a = 0; a < mesh->dim; ++a)
+    if (mesh->n[a] < 1) return DG_E_MESH;
+  if (!(mesh->box_len > 0.0)) return DG_E_MESH;
+  dg_mhd_params prm;
+  if (p) prm = *p;
+  else dg_mhd_default_params(&prm);
+  if (prm.precision != DG_PREC_FP64 && prm.precision != DG_PREC_FP32MIX) return DG_E_ARG;
+  if (!(prm.cfl > 0.0) || !(prm.cfl_glm > 0.0)) return DG_E_ARG;
+
+  dg_mhd_ctx* ctx = new (std::nothrow) dg_mhd_ctx();
+  if (!ctx) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  c.p = prm;
+  Geom& g = c.g;
+  g.D = mesh->dim;
+  g.d = degree;
+  g.glm = divB_scheme == DG_DIVB_GLM;
+  c.hb = new Basis();
+  if (!c.hb->build(g.D, degree, !g.glm)) {
+    dg_mhd_destroy(ctx);
+    return DG_E_UNSUPPORTED;
+  }
+  g.n = c.hb->n;
+  g.ndiv = c.hb->ndiv;
+  g.DB = g.D;
+  g.nq1 = degree + 1;
+  g.Qv = 1;
+  for (int a = 0; a < g.D; ++a) g.Qv *= g.nq1;
+  g.Qf = g.Qv / g.nq1;
+  g.V = g.glm ? 9 : 8;
+  if (g.glm) {
+    g.nrows = 9 * g.n;
+    g.ldf0 = -1;
+    g.bz2d = -1;
+  } else {
+    g.ldf0 = 5 * g.n;
+    g.nrows = 5 * g.n + g.ndiv;
+    g.bz2d = -1;
+    if (g.D == 2) {
+      g.bz2d = g.nrows;
+      g.nrows += g.n;
+    }
+  }
+  g.nx = mesh->n[0];
+  g.ny = mesh->n[1];
+  g.nz = g.D == 3 ? mesh->n[2] : 1;
+  g.ncell = (int64_t)g.nx * g.ny * g.nz;
+  g.stride = (g.ncell + 31) / 32 * 32;
+  g.dx = mesh->box_len / g.nx;
+  g.gamma = gamma;
+
+  HostTables h;
+  build_host_tables(*c.hb, g, h);
+  int e;
+  if ((e = upload_tables(h, c.t64)) || (e = upload_tables(h, c.t32))) {
+    dg_mhd_destroy(ctx);
+    return e;
+  }
+  const size_t esz = fp32(c) ? sizeof(float) : sizeof(double);
+  const size_t state_bytes = (size_t)g.nrows * g.stride * esz;
+  const size_t face_elems = (size_t)g.D * g.ncell * g.Qf * 9;
+  bool ok = cudaMalloc(&c.sc, sizeof(DevScalars)) == cudaSuccess &&
+            cudaMemset(c.sc, 0, sizeof(DevScalars)) == cudaSuccess &&
+            cudaMalloc(&c.stage_buf[0], state_bytes) == cudaSuccess &&
+            cudaMalloc(&c.stage_buf[1], state_bytes) == cudaSuccess &&
+            cudaMalloc(&c.troubled, (size_t)g.stride) == cudaSuccess;
+  if (ok) {
+    if (fp32(c)) {
+      ok = cudaMalloc(&c.face_buf32, face_elems * sizeof(float)) == cudaSuccess &&
+           cudaMalloc(&c.stage_mean[0], (size_t)9 * g.stride * sizeof(double)) == cudaSuccess &&
+           cudaMalloc(&c.stage_mean[1], (size_t)9 * g.stride * sizeof(double)) == cudaSuccess;
+    } else {
+      ok = cudaMalloc(&c.face_buf, face_elems * sizeof(double)) == cudaSuccess;
+    }
+  }
+  if (!ok) {
+    dg_mhd_destroy(ctx);
+    return DG_E_CUDA;
+  }
+  // initial GLM speeds: fixed c_h if given (damping from c_r), else set by dt
+  if (g.glm && prm.c_h_fixed > 0.0) {
+    launch_set_glm(c.sc, prm.c_h_fixed, prm.c_h_fixed / prm.c_r, nullptr);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    dg_mhd_destroy(ctx);
+    return DG_E_CUDA;
+  }
+  *out = ctx;
+  return DG_OK;
+}
+
+int dg_mhd_state_layout(const dg_mhd_ctx* ctx, int64_t* n_rows, int64_t* n_mean_rows, int64_t* n_cells,
+                        int64_t* cell_stride) {
+  if (!ctx) return DG_E_ARG;
+  const Geom& g = ctx->c.g;
+  if (n_rows) *n_rows = g.nrows;
+  if (n_mean_rows) *n_mean_rows = g.glm ? 9 : 8;
+  if (n_cells) *n_cells = g.ncell;
+  if (cell_stride) *cell_stride = g.stride;
+  return DG_OK;
+}
+
+int dg_mhd_project(dg_mhd_ctx* ctx, const double* nodal, int npts, void* w, double* wmean, void* stream) {
+  if (!ctx || !nodal || !w || npts < 1 || npts > 8) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  const Geom& g = c.g;
+  if (fp32(c) && !wmean) return DG_E_ARG;
+  if (npts != c.proj_npts) {
+    // table[(r*Qp + q)*3 + k] = k-th active component of row r at point q
+    std::vector<double> x1, w1;
+    gauss_legendre(npts, x1, w1);
+    int Qp = 1;
+    for (int a = 0; a < g.D; ++a) Qp *= npts;
+    std::vector<double> tab((size_t)g.nrows * Qp * 3, 0.0), wq(Qp, 1.0);
+    double xi[3];
+    for (int q = 0; q < Qp; ++q) {
+      int qq = q;
+      for (int a = 0; a < g.D; ++a) {
+        wq[q] *= w1[qq % npts];
+        qq /= npts;
+      }
+      vol_point(g.D, x1, q, xi);
+      for (int r = 0; r < g.nrows; ++r) {
+        double* t = &tab[((size_t)r * Qp + q) * 3];
+        if (g.ldf0 >= 0 && r >= g.ldf0 && r < g.ldf0 + g.ndiv) {
+          for (int k = 0; k < g.DB; ++k) t[k] = c.hb->eval(c.hb->ldf[r - g.ldf0][k], xi);
+        } else {
+          const int l = (g.bz2d >= 0 && r >= g.bz2d) ? r - g.bz2d : r % g.n;
+          t[0] = c.hb->eval(c.hb->leg[l], xi);
+        }
+      }
+    }
+    if (c.proj_tab) cudaFree(c.proj_tab);
+    if (c.proj_w) cudaFree(c.proj_w);
+    c.proj_tab = nullptr;
+    c.proj_w = nullptr;
+    if (upload(&c.proj_tab, tab) || upload(&c.proj_w, wq)) return DG_E_CUDA;
+    c.proj_npts = npts;
+  }
+  c.prof.launches[4] += 1;
+  if (fp32(c))
+    launch_project<float>(g, npts, c.proj_tab, c.proj_w, nodal, c.t32.minv, (float*)w, wmean, S(stream));
+  else
+    launch_project<double>(g, npts, c.proj_tab, c.proj_w, nodal, c.t64.minv, (double*)w, nullptr, S(stream));
+  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
+}
+
+int dg_mhd_set_glm(dg_mhd_ctx* ctx, double c_h, double damping_rate, void* stream) {
+  if (!ctx || !(c_h > 0.0) || !(damping_rate >= 0.0)) return DG_E_ARG;
+  launch_set_glm(ctx->c.sc, c_h, damping_rate, S(stream));
+  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
+}
+
+namespace {
+
+// rhs (combine = 0) or SSP stage out = ca*w0 + cb*(w + dt*L(w)) (combine = 1)
+int operator_pass(Ctx& c, const void* w, const double* wmean, void* out, double* outmean, const void* w0,
+                  const double* w0mean, double ca, double cb, int combine, cudaStream_t st) {
+  const Geom& g = c.g;
+  if (fp32(c)) {
+    c.prof.begin(0, st);
+    launch_face<float>(g, c.t32, (const float*)w, c.face_buf32, c.sc, c.p.eps_hlld, st);
+    c.prof.end(0, st);
+    c.prof.begin(1, st);
+    launch_cell<float>(g, c.t32, (const float*)w, c.face_buf32, (float*)out, (const float*)w0, ca, cb, combine,
+                       c.sc, wmean, w0mean, outmean, st);
+    c.prof.end(1, st);
+  } else {
+    c.prof.begin(0, st);
+    launch_face<double>(g, c.t64, (const double*)w, c.face_buf, c.sc, c.p.eps_hlld, st);
+    c.prof.end(0, st);
+    c.prof.begin(1, st);
+    launch_cell<double>(g, c.t64, (const double*)w, c.face_buf, (double*)out, (const double*)w0, ca, cb,
+                        combine, c.sc, nullptr, nullptr, nullptr, st);
+    c.prof.end(1, st);
+  }
+  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
+}
+
+int dt_pass(Ctx& c, const void* w, const double* wmean, double* dt_out, cudaStream_t st) {
+  const Geom& g = c.g;
+  c.prof.begin(2, st);
+  if (fp32(c)) {
+    if (!g.glm) launch_divb_face<float>(g, c.t32, (const float*)w, c.face_buf32, st);
+    launch_dt<float>(g, c.t32, (const float*)w, wmean, c.face_buf32, c.p, c.sc, dt_out, st);
+  } else {
+    if (!g.glm) launch_divb_face<double>(g, c.t64, (const double*)w, c.face_buf, st);
+    launch_dt<double>(g, c.t64, (const double*)w, nullptr, c.face_buf, c.p, c.sc, dt_out, st);
+  }
+  c.prof.end(2, st);
+  // k_dt_init + k_dt + k_dt_finalize (+ k_divb_face): count the extra launches
+  c.prof.launches[2] += g.glm ? 2 : 3;
+  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
+}
+
+int limit_pass(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t st) {
+  if (c.p.limiter == DG_LIMIT_OFF && !c.p.positivity) return DG_OK;
+  return run_limiter(c, w, wmean, troubled, st);
+}
+
+}  // namespace
+
+int dg_mhd_rhs(dg_mhd_ctx* ctx, const void* w, const double* wmean, void* rhs, double* rhs_mean, void* stream) {
+  if (!ctx || !w || !rhs) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  if (fp32(c) && (!wmean || !rhs_mean)) return DG_E_ARG;
+  return operator_pass(c, w, wmean, rhs, rhs_mean, nullptr, nullptr, 0.0, 1.0, 0, S(stream));
+}
+
+int dg_mhd_limit(dg_mhd_ctx* ctx, void* w, double* wmean, uint8_t* troubled, void* stream) {
+  if (!ctx || !w) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  if (fp32(c) && !wmean) return DG_E_ARG;
+  return limit_pass(c, w, wmean, troubled, S(stream));
+}
+
+int dg_mhd_dt(dg_mhd_ctx* ctx, const void* w, const double* wmean, double* dt_dev, void* stream) {
+  if (!ctx || !w) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  if (fp32(c) && !wmean) return DG_E_ARG;
+  return dt_pass(c, w, wmean, dt_dev, S(stream));
+}
+
+const double* dg_mhd_last_dt(const dg_mhd_ctx* ctx) {
+  if (!ctx) return nullptr;
+  return &ctx->c.sc->dt;
+}
+
+int dg_mhd_step(dg_mhd_ctx* ctx, void* w, double* wmean, const double* dt_dev, void* stream) {
+  if (!ctx || !w) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  if (fp32(c) && !wmean) return DG_E_ARG;
+  cudaStream_t st = S(stream);
+  int e;
+  if ((e = limit_pass(c, w, wmean, nullptr, st))) return e;
+  if (dt_dev) {
+    c.prof.launches[2] += 1;
+    launch_dt_from_value(c.g, c.p, dt_dev, c.sc, st);
+  }
+  else if ((e = dt_pass(c, w, wmean, nullptr, st))) return e;
+  void* s1 = c.stage_buf[0];
+  void* s2 = c.stage_buf[1];
+  double* m1 = c.stage_mean[0];
+  double* m2 = c.stage_mean[1];
+  // u1 = u + dt L(u)
+  if ((e = operator_pass(c, w, wmean, s1, m1, w, wmean, 0.0, 1.0, 1, st))) return e;
+  if ((e = limit_pass(c, s1, m1, nullptr, st))) return e;
+  // u2 = 3/4 u + 1/4 (u1 + dt L(u1))
+  if ((e = operator_pass(c, s1, m1, s2, m2, w, wmean, 0.75, 0.25, 1, st))) return e;
+  if ((e = limit_pass(c, s2, m2, nullptr, st))) return e;
+  // u^{n+1} = 1/3 u + 2/3 (u2 + dt L(u2))
+  if ((e = operator_pass(c, s2, m2, w, wmean, w, wmean, 1.0 / 3.0, 2.0 / 3.0, 1, st))) return e;
+  return DG_OK;
+}
+
+int dg_mhd_status(dg_mhd_ctx* ctx, int sync) {
+  if (!ctx) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  if (sync && cudaDeviceSynchronize() != cudaSuccess) return DG_E_CUDA;
+  int st = 0, fl = 0;
+  if (cudaMemcpy(&st, &c.sc->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DG_E_CUDA;
+  if (cudaMemcpy(&fl, &c.sc->floor_used, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DG_E_CUDA;
+  if (sync) {
+    int z = 0;
+    cudaMemcpy(&c.sc->status, &z, sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(&c.sc->floor_used, &z, sizeof(int), cudaMemcpyHostToDevice);
+  }
+  if (st & 1) return DG_E_NONFINITE;
+  if (st & 4) return DG_E_CH;
+  if (st & 8) return DG_E_TIMEOUT;
+  if (fl) return DG_W_FLOOR;
+  return DG_OK;
+}
+
+}  // extern "C"

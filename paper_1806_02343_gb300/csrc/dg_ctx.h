@@ -1,0 +1,101 @@
+// Internal context of the DG-MHD library: mesh, device tables, scratch.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/dg_mhd.h"
+#include "dg_basis.h"
+
+namespace dgmhd {
+
+constexpr int MAXV = 9;       // conserved variables incl. psi
+constexpr int MAXD = 3;       // supported polynomial degree
+constexpr int MAXQV = 64;     // (MAXD+1)^3 volume points
+constexpr int MAXQF = 16;     // (MAXD+1)^2 points per face
+constexpr int MAXROWS = 180;  // 9 * n(3)
+
+// Device-resident basis tables for one (D, d, scheme). T = double or float.
+// Layouts (q: volume point, p: face point, f = 2*axis + side, side 1 = +face):
+//   Pv[l*Qv+q]            Legendre values at volume points
+//   dPv[(a*n+l)*Qv+q]     d/dxi_a of Legendre
+//   Pf[(f*n+l)*Qf+p]      Legendre values at face points
+//   Lv[(j*DB+c)*Qv+q]     LDF component c at volume points
+//   dLv[((a*nd+j)*DB+c)*Qv+q]
+//   Lf[((f*nd+j)*DB+c)*Qf+p]
+//   wv[q], wf[p], minv[r] = 1/M_r, L0[j*DB+c] = cell mean of LDF component
+template <typename T>
+struct Tables {
+  T *Pv = nullptr, *dPv = nullptr, *Pf = nullptr;
+  T *Lv = nullptr, *dLv = nullptr, *Lf = nullptr, *L0 = nullptr;
+  T *wv = nullptr, *wf = nullptr, *minv = nullptr;
+};
+
+// Kernel-facing description of the discretisation (passed by value).
+struct Geom {
+  int D, d, n, ndiv, DB;  // DB: LDF components (= D)
+  int Qv, Qf, nq1;        // volume pts, face pts, pts per dim
+  int V;                  // variables (8 Powell, 9 GLM)
+  int nrows;              // DoF rows per cell
+  int ldf0;               // first LDF row (5n) or -1
+  int bz2d;               // first B_z Legendre row in 2D Powell, or -1
+  int glm;                // 1: GLM, 0: Powell
+  int nx, ny, nz;         // cells per axis (nz = 1 in 2D)
+  int64_t ncell, stride;  // cells and row stride
+  double dx, gamma;
+};
+
+// Scalars kept on the device so that a step never waits for the host.
+struct DevScalars {
+  double dt;       // current timestep
+  double ch;       // GLM c_h
+  double kappa;    // GLM damping rate c_h^2 / c_p^2
+  double dtmin_raw;
+  unsigned long long dt_bits;  // atomicMin target (positive doubles order as uint64)
+  unsigned long long smax_bits;
+  int status;      // latched dg_status bits
+  int floor_used;
+};
+
+// Launch accounting: counts every kernel launch; with `on`, records a CUDA
+// event pair on the launch stream around each launch of a given kind.
+struct Prof {
+  static constexpr int KINDS = 5;
+  bool on = false;
+  int64_t launches[KINDS] = {0, 0, 0, 0, 0};
+  double ms[KINDS] = {0, 0, 0, 0, 0};
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> kind;   // kind of each recorded pair
+  size_t used = 0;         // events in use (2 per pair)
+  void begin(int k, cudaStream_t st);
+  void end(int k, cudaStream_t st);
+  int collect();
+  void reset();
+  void release();
+};
+
+struct Ctx {
+  Prof prof;
+  Geom g;
+  dg_mhd_params p;
+  Basis* hb = nullptr;  // host basis (kept for projection tables)
+  Tables<double> t64;
+  Tables<float> t32;
+  DevScalars* sc = nullptr;        // device
+  double* face_buf = nullptr;      // FP64 face fluxes
+  float* face_buf32 = nullptr;     // FP32 face fluxes
+  void* stage_buf[3] = {nullptr, nullptr, nullptr};  // rhs / stage states
+  double* stage_mean[3] = {nullptr, nullptr, nullptr};
+  double* cellscratch = nullptr;   // per-cell dt contributions
+  int proj_npts = 0;
+  double* proj_tab = nullptr;      // projection table [r][q][comp]
+  double* proj_w = nullptr;
+  uint8_t* troubled = nullptr;     // per-cell limiter flags (scratch)
+};
+
+}  // namespace dgmhd
+
+struct dg_mhd_ctx {
+  dgmhd::Ctx c;
+};

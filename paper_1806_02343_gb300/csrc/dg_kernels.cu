@@ -1,0 +1,530 @@
+// CUDA-core kernels of the DG-MHD operator (Sec. 3.5 eq. wdot, Sec. 4.1).
+//
+// k_face   one thread per (axis, cell, face point): traces of both cells at the
+//          face point (modal -> nodal, Sec. 3.1), B^n_F (eq. bxface-average-alfven),
+//          HLLD (Sec. 4.1.2) and, for GLM, the upwinded psi*, B_n* (Sec. 4.1.5).
+//          Writes F* and B^n_F per face point to a face buffer.
+// k_cell   one warp per cell: volume fluxes at the Gauss points and the volume
+//          integral int f_a . d_a phi_l, the surface integral of F*.n phi_l over
+//          the cell's 2D faces, the Powell face term of eq. powell-src-face with
+//          q(<u>_K) (eq. powellq-average), the GLM damping source, the mass
+//          matrix and the 2/dx metric factor; optionally the SSP-RK combination.
+// k_dt     eq. cfl per cell from the cell mean, eq. powell_dt from the face
+//          jumps of eq. divb-cell; min-reduced with an atomicMin on the bits.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstdint>
+
+#include "dg_kernels.cuh"
+#include "dg_phys.cuh"
+
+namespace dgmhd {
+
+namespace {
+
+constexpr int WARPS_PER_BLOCK = 4;
+
+__device__ __forceinline__ void cell_coords(const Geom& g, int64_t c, int& ix, int& iy, int& iz) {
+  ix = (int)(c % g.nx);
+  int64_t r = c / g.nx;
+  iy = (int)(r % g.ny);
+  iz = (int)(r / g.ny);
+}
+
+__device__ __forceinline__ int64_t cell_index(const Geom& g, int ix, int iy, int iz) {
+  return ((int64_t)iz * g.ny + iy) * g.nx + ix;
+}
+
+__device__ __forceinline__ int64_t neighbour(const Geom& g, int64_t c, int a, int dir) {
+  int ix, iy, iz;
+  cell_coords(g, c, ix, iy, iz);
+  if (a == 0) ix = (ix + dir + g.nx) % g.nx;
+  else if (a == 1) iy = (iy + dir + g.ny) % g.ny;
+  else iz = (iz + dir + g.nz) % g.nz;
+  return cell_index(g, ix, iy, iz);
+}
+
+// state variable of a Legendre row (Powell: rows < ldf0 are hydro, rows >= bz2d are B_z)
+__device__ __forceinline__ int legendre_var(const Geom& g, int r) {
+  if (g.bz2d >= 0 && r >= g.bz2d) return 7;
+  return r / g.n;
+}
+
+__device__ __forceinline__ bool is_ldf_row(const Geom& g, int r) {
+  return g.ldf0 >= 0 && r >= g.ldf0 && r < g.ldf0 + g.ndiv;
+}
+
+// mean row m -> DoF row
+__device__ __forceinline__ int mean_row(const Geom& g, int m) {
+  if (g.glm) return m * g.n;
+  if (m < 5) return m * g.n;
+  if (g.D == 3) return g.ldf0 + (m - 5);
+  return m < 7 ? g.ldf0 + (m - 5) : g.bz2d;
+}
+
+__device__ __forceinline__ int n_mean_rows(const Geom& g) { return g.glm ? 9 : 8; }
+
+// DoF row -> mean row index, or -1
+__device__ __forceinline__ int mean_index(const Geom& g, int r) {
+  for (int m = 0; m < n_mean_rows(g); ++m)
+    if (mean_row(g, m) == r) return m;
+  return -1;
+}
+
+// Evaluate the state at point index `pt` of a point set given by tables
+// P (Legendre, [l][npt]) and L (LDF, [j][c][npt]); coefficients read through `coef`.
+template <typename T, typename F>
+__device__ __forceinline__ void eval_state(const Geom& g, const T* __restrict__ P, const T* __restrict__ L,
+                                           int npt, int pt, F coef, T* u) {
+  for (int v = 0; v < g.V; ++v) u[v] = T(0);
+  const int nleg = g.glm ? 9 : 5;
+  for (int v = 0; v < nleg; ++v) {
+    T s = T(0);
+    for (int l = 0; l < g.n; ++l) s += coef(v * g.n + l) * P[l * npt + pt];
+    u[v] = s;
+  }
+  if (!g.glm) {
+    T b[3] = {T(0), T(0), T(0)};
+    for (int j = 0; j < g.ndiv; ++j) {
+      const T wj = coef(g.ldf0 + j);
+      for (int c = 0; c < g.DB; ++c) b[c] += wj * L[(j * g.DB + c) * npt + pt];
+    }
+    for (int c = 0; c < g.DB; ++c) u[5 + c] = b[c];
+    if (g.bz2d >= 0) {
+      T s = T(0);
+      for (int l = 0; l < g.n; ++l) s += coef(g.bz2d + l) * P[l * npt + pt];
+      u[7] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- face fluxes
+template <typename T>
+__global__ void k_face(Geom g, Tables<T> tb, const T* __restrict__ w, T* __restrict__ fbuf,
+                       const DevScalars* __restrict__ sc, T eps) {
+  const int64_t total = (int64_t)g.D * g.ncell * g.Qf;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= total) return;
+  const int p = (int)(tid % g.Qf);
+  const int64_t fc = tid / g.Qf;
+  const int64_t c = fc % g.ncell;
+  const int a = (int)(fc / g.ncell);
+  const int64_t cl = neighbour(g, c, a, -1);
+  const int64_t S = g.stride;
+  T uL[MAXV], uR[MAXV];
+  const int fL = 2 * a + 1, fR = 2 * a;
+  eval_state(g, tb.Pf + (size_t)fL * g.n * g.Qf, tb.Lf + (size_t)fL * g.ndiv * g.DB * g.Qf, g.Qf, p,
+             [&](int r) { return w[r * S + cl]; }, uL);
+  eval_state(g, tb.Pf + (size_t)fR * g.n * g.Qf, tb.Lf + (size_t)fR * g.ndiv * g.DB * g.Qf, g.Qf, p,
+             [&](int r) { return w[r * S + c]; }, uR);
+  T F[MAXV];
+  const T ch = g.glm ? (T)sc->ch : T(0);
+  const T bnF = face_flux(uL, uR, a, (T)g.gamma, g.glm != 0, ch, eps, F);
+  T* o = fbuf + tid * 9;
+  for (int k = 0; k < g.V; ++k) o[k] = F[k];
+  if (!g.glm) o[8] = bnF;
+}
+
+// ---------------------------------------------------------------- cell update
+template <typename T>
+__global__ void k_cell(Geom g, Tables<T> tb, const T* __restrict__ w, const T* __restrict__ fbuf, T* out,
+                       const T* w0, double ca, double cb, int combine, const DevScalars* __restrict__ sc,
+                       const double* __restrict__ wmean, const double* w0mean, double* outmean) {
+  // out may alias w0 (in-place final stage): each element is read and then
+  // written by the same thread.
+  extern __shared__ unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c = (int64_t)blockIdx.x * WARPS_PER_BLOCK + warp;
+  const int per_warp = g.nrows + g.D * g.V * g.Qv + 2 * g.D * g.Qf * g.V + 2 * g.D * g.Qf;
+  T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)warp * per_warp;
+  T* wc = sm;
+  T* G = wc + g.nrows;
+  T* FS = G + g.D * g.V * g.Qv;
+  T* PJ = FS + 2 * g.D * g.Qf * g.V;
+  if (c >= g.ncell) return;
+  const int64_t S = g.stride;
+  const bool mix = (wmean != nullptr);
+  for (int r = lane; r < g.nrows; r += 32) wc[r] = w[r * S + c];
+  __syncwarp();
+  if (mix && lane < n_mean_rows(g)) wc[mean_row(g, lane)] = (T)wmean[lane * S + c];
+  __syncwarp();
+  const T gamma = (T)g.gamma;
+  const T ch = g.glm ? (T)sc->ch : T(0);
+  const T ch2 = ch * ch;
+  // volume: fluxes at the Gauss points, weighted
+  for (int q = lane; q < g.Qv; q += 32) {
+    T u[MAXV];
+    eval_state(g, tb.Pv, tb.Lv, g.Qv, q, [&](int r) { return wc[r]; }, u);
+    const T wq = tb.wv[q];
+    for (int a = 0; a < g.D; ++a) {
+      T f[MAXV];
+      flux_dir(u, a, gamma, g.glm != 0, ch2, f);
+      for (int v = 0; v < g.V; ++v) G[(a * g.V + v) * g.Qv + q] = wq * f[v];
+    }
+  }
+  // faces: outward-normal flux times weights, Powell jump terms
+  for (int idx = lane; idx < 2 * g.D * g.Qf; idx += 32) {
+    const int f = idx / g.Qf, p = idx % g.Qf;
+    const int a = f >> 1, side = f & 1;
+    const int64_t fc = side ? neighbour(g, c, a, +1) : c;
+    const T* F = fbuf + (((int64_t)a * g.ncell + fc) * g.Qf + p) * 9;
+    const T sgn = side ? T(1) : T(-1);
+    const T wp = tb.wf[p];
+    for (int v = 0; v < g.V; ++v) FS[(f * g.Qf + p) * g.V + v] = sgn * wp * F[v];
+    if (!g.glm) {
+      // own normal field B_a at this face point (LDF rows)
+      T ba = T(0);
+      for (int j = 0; j < g.ndiv; ++j)
+        ba += wc[g.ldf0 + j] * tb.Lf[(((size_t)f * g.ndiv + j) * g.DB + a) * g.Qf + p];
+      PJ[f * g.Qf + p] = wp * sgn * (F[8] - ba);
+    }
+  }
+  __syncwarp();
+  // Powell q(<u>_K) = (0, B, v.B, v) from the cell mean
+  T qv[MAXV];
+  if (!g.glm) {
+    const T rho = wc[0];
+    const T vx = wc[g.n] / rho, vy = wc[2 * g.n] / rho, vz = wc[3 * g.n] / rho;
+    T b[3] = {T(0), T(0), T(0)};
+    for (int j = 0; j < g.DB; ++j)  // degree-0 LDF rows come first
+      for (int cc = 0; cc < g.DB; ++cc) b[cc] += wc[g.ldf0 + j] * tb.L0[j * g.DB + cc];
+    if (g.bz2d >= 0) b[2] = wc[g.bz2d];
+    qv[0] = T(0); qv[1] = b[0]; qv[2] = b[1]; qv[3] = b[2];
+    qv[4] = vx * b[0] + vy * b[1] + vz * b[2];
+    qv[5] = vx; qv[6] = vy; qv[7] = vz; qv[8] = T(0);
+  }
+  const double dt = sc->dt;
+  const double kappa = g.glm ? sc->kappa : 0.0;
+  const double metric = 2.0 / g.dx;
+  for (int r = lane; r < g.nrows; r += 32) {
+    double acc = 0.0;  // double accumulation: exact conservation of the mean rows
+    if (!is_ldf_row(g, r)) {
+      const int v = legendre_var(g, r);
+      const int l = (g.bz2d >= 0 && r >= g.bz2d) ? r - g.bz2d : r % g.n;
+      T s = T(0);
+      if (l != 0) {
+        for (int a = 0; a < g.D; ++a) {
+          const T* Gp = G + (a * g.V + v) * g.Qv;
+          const T* Dp = tb.dPv + ((size_t)a * g.n + l) * g.Qv;
+          for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
+        }
+      }
+      acc += (double)s;
+      for (int f = 0; f < 2 * g.D; ++f) {
+        const T* Pp = tb.Pf + ((size_t)f * g.n + l) * g.Qf;
+        T sf = T(0);
+        for (int p = 0; p < g.Qf; ++p) {
+          T term = FS[(f * g.Qf + p) * g.V + v];
+          if (!g.glm) term += PJ[f * g.Qf + p] * qv[v];
+          sf += term * Pp[p];
+        }
+        acc -= (double)sf;
+      }
+    } else {
+      const int j = r - g.ldf0;
+      T s = T(0);
+      for (int a = 0; a < g.D; ++a)
+        for (int cc = 0; cc < g.DB; ++cc) {
+          const T* Gp = G + (a * g.V + 5 + cc) * g.Qv;
+          const T* Dp = tb.dLv + (((size_t)a * g.ndiv + j) * g.DB + cc) * g.Qv;
+          for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
+        }
+      acc += (double)s;
+      for (int f = 0; f < 2 * g.D; ++f) {
+        T sf = T(0);
+        for (int cc = 0; cc < g.DB; ++cc) {
+          const T* Lp = tb.Lf + (((size_t)f * g.ndiv + j) * g.DB + cc) * g.Qf;
+          for (int p = 0; p < g.Qf; ++p)
+            sf += (FS[(f * g.Qf + p) * g.V + 5 + cc] + PJ[f * g.Qf + p] * qv[5 + cc]) * Lp[p];
+        }
+        acc -= (double)sf;
+      }
+    }
+    double rhs = metric * (double)tb.minv[r] * acc;
+    if (g.glm && r >= 8 * g.n) rhs -= kappa * (double)wc[r];
+    const int m = mix ? mean_index(g, r) : -1;
+    if (!combine) {
+      out[r * S + c] = (T)rhs;
+      if (m >= 0) outmean[m * S + c] = rhs;
+    } else if (m >= 0) {
+      // FP64 update of a degree-0 row; the float entry mirrors it
+      const double o = ca * w0mean[m * S + c] + cb * (wmean[m * S + c] + dt * rhs);
+      outmean[m * S + c] = o;
+      out[r * S + c] = (T)o;
+    } else {
+      const double ws = (double)wc[r];
+      const double wz = (double)w0[r * S + c];
+      out[r * S + c] = (T)(ca * wz + cb * (ws + dt * rhs));
+    }
+  }
+}
+
+// ---------------------------------------------------------------- projection
+template <typename T>
+__global__ void k_project(Geom g, int Qp, const double* __restrict__ tab, const double* __restrict__ wq,
+                          const double* __restrict__ nodal, const T* __restrict__ minv, T* __restrict__ w,
+                          double* __restrict__ wmean) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c = (int64_t)blockIdx.x * WARPS_PER_BLOCK + warp;
+  if (c >= g.ncell) return;
+  const int64_t S = g.stride;
+  // tab[(r*Qp + q)*3 + k]: value of row r's k-th active component at point q;
+  // the variable of component k is given by the row kind
+  for (int r = lane; r < g.nrows; r += 32) {
+    double acc = 0.0;
+    if (!is_ldf_row(g, r)) {
+      const int v = legendre_var(g, r);
+      for (int q = 0; q < Qp; ++q) acc += wq[q] * nodal[((int64_t)v * Qp + q) * S + c] * tab[((size_t)r * Qp + q) * 3];
+    } else {
+      for (int q = 0; q < Qp; ++q)
+        for (int k = 0; k < g.DB; ++k)
+          acc += wq[q] * nodal[((int64_t)(5 + k) * Qp + q) * S + c] * tab[((size_t)r * Qp + q) * 3 + k];
+    }
+    acc *= (double)minv[r];
+    w[r * S + c] = (T)acc;
+  }
+  if (wmean != nullptr) {
+    __syncwarp();
+    for (int m = lane; m < n_mean_rows(g); m += 32) {
+      const int r = mean_row(g, m);
+      double acc = 0.0;
+      if (!is_ldf_row(g, r)) {
+        const int v = legendre_var(g, r);
+        for (int q = 0; q < Qp; ++q)
+          acc += wq[q] * nodal[((int64_t)v * Qp + q) * S + c] * tab[((size_t)r * Qp + q) * 3];
+      } else {
+        for (int q = 0; q < Qp; ++q)
+          for (int k = 0; k < g.DB; ++k)
+            acc += wq[q] * nodal[((int64_t)(5 + k) * Qp + q) * S + c] * tab[((size_t)r * Qp + q) * 3 + k];
+      }
+      wmean[m * S + c] = acc * (double)minv[r];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Powell |div B| face jumps
+template <typename T>
+__global__ void k_divb_face(Geom g, Tables<T> tb, const T* __restrict__ w, T* __restrict__ jbuf) {
+  const int64_t total = (int64_t)g.D * g.ncell * g.Qf;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= total) return;
+  const int p = (int)(tid % g.Qf);
+  const int64_t fc = tid / g.Qf;
+  const int64_t c = fc % g.ncell;
+  const int a = (int)(fc / g.ncell);
+  const int64_t cl = neighbour(g, c, a, -1);
+  const int64_t S = g.stride;
+  const int fL = 2 * a + 1, fR = 2 * a;
+  T rL = T(0), rR = T(0), bL = T(0), bR = T(0);
+  for (int l = 0; l < g.n; ++l) {
+    rL += w[l * S + cl] * tb.Pf[((size_t)fL * g.n + l) * g.Qf + p];
+    rR += w[l * S + c] * tb.Pf[((size_t)fR * g.n + l) * g.Qf + p];
+  }
+  for (int j = 0; j < g.ndiv; ++j) {
+    bL += w[(g.ldf0 + j) * S + cl] * tb.Lf[(((size_t)fL * g.ndiv + j) * g.DB + a) * g.Qf + p];
+    bR += w[(g.ldf0 + j) * S + c] * tb.Lf[(((size_t)fR * g.ndiv + j) * g.DB + a) * g.Qf + p];
+  }
+  const T bF = bn_face(rL, rR, bL, bR);
+  const T wp = tb.wf[p];
+  T* o = jbuf + tid * 2;
+  o[0] = wp * (bF > bL ? bF - bL : bL - bF);  // contribution to the L cell
+  o[1] = wp * (bF > bR ? bF - bR : bR - bF);  // contribution to the R cell
+}
+
+// ---------------------------------------------------------------- dt
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+template <typename T>
+__global__ void k_dt(Geom g, Tables<T> tb, const T* __restrict__ w, const double* __restrict__ wmean,
+                     const T* __restrict__ jbuf, dg_mhd_params p, DevScalars* __restrict__ sc) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double dtc = DBL_MAX, smax = 0.0;
+  if (c < g.ncell) {
+    const int64_t S = g.stride;
+    auto mean = [&](int m) {
+      return wmean ? wmean[m * S + c] : (double)w[(int64_t)mean_row(g, m) * S + c];
+    };
+    const double rho = mean(0);
+    const double vx = mean(1) / rho, vy = mean(2) / rho, vz = mean(3) / rho;
+    const double E = mean(4);
+    double b[3];
+    if (g.glm) {
+      b[0] = mean(5); b[1] = mean(6); b[2] = mean(7);
+    } else {
+      b[0] = b[1] = b[2] = 0.0;
+      for (int j = 0; j < g.DB; ++j)
+        for (int cc = 0; cc < g.DB; ++cc) b[cc] += mean(5 + j) * (double)tb.L0[j * g.DB + cc];
+      if (g.bz2d >= 0) b[2] = mean(7);
+    }
+    const double b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    const double pr = (g.gamma - 1.0) * (E - 0.5 * rho * (vx * vx + vy * vy + vz * vz) - 0.5 * b2);
+    const double cs = sqrt(g.gamma * pr / rho + b2 / rho);
+    const double av[3] = {fabs(vx), fabs(vy), fabs(vz)};
+    double s = 0.0;
+    for (int a = 0; a < g.D; ++a) s += (av[a] + cs) / g.dx;
+    dtc = p.cfl / (2.0 * g.d + 1.0) / s;
+    smax = s * g.dx / g.D;
+    if (!g.glm) {
+      // (1/V_K) oint |B^n_F - B^n_K| dS: sum this cell's 2D faces in fixed order
+      double acc = 0.0;
+      for (int a = 0; a < g.D; ++a) {
+        const int64_t cp = neighbour(g, c, a, +1);
+        for (int q = 0; q < g.Qf; ++q) {
+          acc += (double)jbuf[(((int64_t)a * g.ncell + c) * g.Qf + q) * 2 + 1];   // minus face: R side
+          acc += (double)jbuf[(((int64_t)a * g.ncell + cp) * g.Qf + q) * 2 + 0];  // plus face: L side
+        }
+      }
+      double meas = 1.0;
+      for (int a = 0; a < g.D - 1; ++a) meas *= 0.5 * g.dx;
+      double divb = acc * meas;
+      for (int a = 0; a < g.D; ++a) divb /= g.dx;
+      const double rate = divb * fabs(vx * b[0] + vy * b[1] + vz * b[2]) / E;
+      if (rate > 0.0) dtc = fmin(dtc, p.eta_powell / rate);
+    }
+    if (!(dtc > 0.0) || !isfinite(dtc)) {
+      atomicOr(&sc->status, 1);
+      dtc = DBL_MAX;
+    }
+  }
+  // block reduction then one atomic per block
+  __shared__ double red[256];
+  __shared__ double reds[256];
+  red[threadIdx.x] = dtc;
+  reds[threadIdx.x] = smax;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + o]);
+      reds[threadIdx.x] = fmax(reds[threadIdx.x], reds[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicMin(&sc->dt_bits, dbits(red[0]));
+    atomicMax(&sc->smax_bits, dbits(reds[0]));
+  }
+}
+
+__global__ void k_dt_init(DevScalars* sc) {
+  sc->dt_bits = dbits(DBL_MAX);
+  sc->smax_bits = 0ull;
+}
+
+__global__ void k_dt_finalize(Geom g, dg_mhd_params p, DevScalars* sc, const double* dt_in, double* dt_out) {
+  double dt = dt_in ? *dt_in : __longlong_as_double((long long)sc->dt_bits);
+  if (!(dt > 0.0) || !isfinite(dt) || dt >= DBL_MAX) {
+    atomicOr(&sc->status, 1);
+  }
+  sc->dt = dt;
+  if (dt_out) *dt_out = dt;
+  if (g.glm) {
+    double ch = p.c_h_fixed > 0.0 ? p.c_h_fixed : p.cfl_glm / (2.0 * g.d + 1.0) * g.dx / (g.D * dt);
+    sc->ch = ch;
+    const double tau = fmax(p.c_r / ch, 3.0 * dt);
+    sc->kappa = 1.0 / tau;
+    if (p.c_h_fixed > 0.0 && !dt_in) {
+      const double smax = __longlong_as_double((long long)sc->smax_bits);
+      if (ch < smax) atomicOr(&sc->status, 4);
+    }
+  }
+}
+
+__global__ void k_set_glm(DevScalars* sc, double ch, double kappa) {
+  sc->ch = ch;
+  sc->kappa = kappa;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+static inline unsigned nblocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <typename T>
+void launch_face(const Geom& g, const Tables<T>& tb, const T* w, T* fbuf, const DevScalars* sc, double eps,
+                 cudaStream_t st) {
+  const int64_t total = (int64_t)g.D * g.ncell * g.Qf;
+  k_face<T><<<nblocks(total, 128), 128, 0, st>>>(g, tb, w, fbuf, sc, (T)eps);
+}
+
+template <typename T>
+static size_t cell_smem(const Geom& g) {
+  const int per_warp = g.nrows + g.D * g.V * g.Qv + 2 * g.D * g.Qf * g.V + 2 * g.D * g.Qf;
+  return (size_t)per_warp * WARPS_PER_BLOCK * sizeof(T);
+}
+
+template <typename T>
+void launch_cell(const Geom& g, const Tables<T>& tb, const T* w, const T* fbuf, T* out, const T* w0,
+                 double ca, double cb, int combine, const DevScalars* sc, const double* wmean,
+                 const double* w0mean, double* outmean, cudaStream_t st) {
+  const size_t sm = cell_smem<T>(g);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_cell<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_cell<T><<<nblocks(g.ncell, WARPS_PER_BLOCK), 32 * WARPS_PER_BLOCK, sm, st>>>(
+      g, tb, w, fbuf, out, w0, ca, cb, combine, sc, wmean, w0mean, outmean);
+}
+
+template <typename T>
+void launch_project(const Geom& g, int npts, const double* tab, const double* wq, const double* nodal,
+                    const T* minv, T* w, double* wmean, cudaStream_t st) {
+  int Qp = 1;
+  for (int a = 0; a < g.D; ++a) Qp *= npts;
+  k_project<T><<<nblocks(g.ncell, WARPS_PER_BLOCK), 32 * WARPS_PER_BLOCK, 0, st>>>(g, Qp, tab, wq, nodal, minv,
+                                                                                   w, wmean);
+}
+
+template <typename T>
+void launch_divb_face(const Geom& g, const Tables<T>& tb, const T* w, T* jbuf, cudaStream_t st) {
+  const int64_t total = (int64_t)g.D * g.ncell * g.Qf;
+  k_divb_face<T><<<nblocks(total, 128), 128, 0, st>>>(g, tb, w, jbuf);
+}
+
+template <typename T>
+void launch_dt(const Geom& g, const Tables<T>& tb, const T* w, const double* wmean, const T* jbuf,
+               const dg_mhd_params& p, DevScalars* sc, double* dt_out, cudaStream_t st) {
+  k_dt_init<<<1, 1, 0, st>>>(sc);
+  k_dt<T><<<nblocks(g.ncell, 256), 256, 0, st>>>(g, tb, w, wmean, jbuf, p, sc);
+  k_dt_finalize<<<1, 1, 0, st>>>(g, p, sc, nullptr, dt_out);
+}
+
+void launch_dt_from_value(const Geom& g, const dg_mhd_params& p, const double* dt_in, DevScalars* sc,
+                          cudaStream_t st) {
+  k_dt_finalize<<<1, 1, 0, st>>>(g, p, sc, dt_in, nullptr);
+}
+
+void launch_set_glm(DevScalars* sc, double ch, double kappa, cudaStream_t st) {
+  k_set_glm<<<1, 1, 0, st>>>(sc, ch, kappa);
+}
+
+template <typename T>
+__global__ void k_mirror_means(Geom g, const double* __restrict__ wmean, T* __restrict__ w) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const int nm = g.glm ? 9 : 8;
+  for (int m = 0; m < nm; ++m) w[(int64_t)mean_row(g, m) * g.stride + c] = (T)wmean[(int64_t)m * g.stride + c];
+}
+
+template <typename T>
+void launch_mirror_means(const Geom& g, const double* wmean, T* w, cudaStream_t st) {
+  k_mirror_means<T><<<nblocks(g.ncell, 256), 256, 0, st>>>(g, wmean, w);
+}
+
+#define INST(T)                                                                                              \
+  template void launch_face<T>(const Geom&, const Tables<T>&, const T*, T*, const DevScalars*, double,      \
+                               cudaStream_t);                                                                \
+  template void launch_cell<T>(const Geom&, const Tables<T>&, const T*, const T*, T*, const T*, double,     \
+                               double, int, const DevScalars*, const double*, const double*, double*,      \
+                               cudaStream_t);                                                                \
+  template void launch_project<T>(const Geom&, int, const double*, const double*, const double*, const T*, \
+                                  T*, double*, cudaStream_t);                                               \
+  template void launch_divb_face<T>(const Geom&, const Tables<T>&, const T*, T*, cudaStream_t);            \
+  template void launch_dt<T>(const Geom&, const Tables<T>&, const T*, const double*, const T*,             \
+                             const dg_mhd_params&, DevScalars*, double*, cudaStream_t);                    \
+  template void launch_mirror_means<T>(const Geom&, const double*, T*, cudaStream_t);
+INST(double)
+INST(float)
+
+}  // namespace dgmhd

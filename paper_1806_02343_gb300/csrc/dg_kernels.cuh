@@ -1,0 +1,29 @@
+// Kernels of the CUDA-core DG-MHD path (FP64 plain form and the FP32 form).
+#pragma once
+#include "dg_ctx.h"
+
+namespace dgmhd {
+
+// launches (all asynchronous on `st`)
+template <typename T>
+void launch_face(const Geom& g, const Tables<T>& tb, const T* w, T* fbuf, const DevScalars* sc, double eps,
+                 cudaStream_t st);
+template <typename T>
+void launch_cell(const Geom& g, const Tables<T>& tb, const T* w, const T* fbuf, T* out, const T* w0,
+                 double ca, double cb, int combine, const DevScalars* sc, const double* wmean,
+                 const double* w0mean, double* outmean, cudaStream_t st);
+template <typename T>
+void launch_project(const Geom& g, int npts, const double* tab, const double* wq, const double* nodal,
+                    const T* minv, T* w, double* wmean, cudaStream_t st);
+template <typename T>
+void launch_divb_face(const Geom& g, const Tables<T>& tb, const T* w, T* jbuf, cudaStream_t st);
+template <typename T>
+void launch_dt(const Geom& g, const Tables<T>& tb, const T* w, const double* wmean, const T* jbuf,
+               const dg_mhd_params& p, DevScalars* sc, double* dt_out, cudaStream_t st);
+void launch_dt_from_value(const Geom& g, const dg_mhd_params& p, const double* dt_in, DevScalars* sc,
+                          cudaStream_t st);
+void launch_set_glm(DevScalars* sc, double ch, double kappa, cudaStream_t st);
+template <typename T>
+void launch_mirror_means(const Geom& g, const double* wmean, T* w, cudaStream_t st);
+
+}  // namespace dgmhd

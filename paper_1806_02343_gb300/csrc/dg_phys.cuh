@@ -1,0 +1,235 @@
+// Pointwise ideal-MHD physics on the device (one thread = one point).
+//
+// Conserved variables u = (rho, m_x, m_y, m_z, E, B_x, B_y, B_z[, psi]) (Sec. 2).
+// * flux_dir: analytic flux of eq. mhd-flux along axis a; GLM adds psi to the
+//   B_a row and c_h^2 B_a as the psi flux (Sec. 4.1.5);
+// * bn_face: eq. bxface-average-alfven;
+// * glm_face: upwinded (B_n*, psi*) of the linear GLM subsystem (Sec. 4.1.5);
+// * hlld: Miyoshi & Kusano (2005) five-wave flux, the solver of Sec. 4.1.2,
+//   with the normal field of both states set to B^n_F first (Sec. 4.1.3), the
+//   thermal pressure of each state kept.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace dgmhd {
+
+template <typename T>
+__device__ __forceinline__ T dsqrt(T x) { return sqrt(x); }
+template <>
+__device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+
+template <typename T>
+__device__ __forceinline__ void flux_dir(const T* u, int a, T gamma, bool glm, T ch2, T* f) {
+  const T rho = u[0];
+  const T ir = T(1) / rho;
+  const T vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
+  const T bx = u[5], by = u[6], bz = u[7];
+  const T b2 = bx * bx + by * by + bz * bz;
+  const T p = (gamma - T(1)) * (u[4] - T(0.5) * rho * (vx * vx + vy * vy + vz * vz) - T(0.5) * b2);
+  const T pT = p + T(0.5) * b2;
+  const T va = a == 0 ? vx : (a == 1 ? vy : vz);
+  const T ba = a == 0 ? bx : (a == 1 ? by : bz);
+  const T vb = vx * bx + vy * by + vz * bz;
+  f[0] = u[1 + a];
+  f[1] = u[1] * va - bx * ba;
+  f[2] = u[2] * va - by * ba;
+  f[3] = u[3] * va - bz * ba;
+  f[1 + a] += pT;
+  f[4] = (u[4] + pT) * va - vb * ba;
+  f[5] = bx * va - vx * ba;
+  f[6] = by * va - vy * ba;
+  f[7] = bz * va - vz * ba;
+  if (glm) {
+    f[5 + a] += u[8];
+    f[8] = ch2 * ba;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T bn_face(T rL, T rR, T bL, T bR) {
+  const T sL = T(1) / dsqrt(rL), sR = T(1) / dsqrt(rR);
+  return (bL * sL + bR * sR) / (sL + sR);
+}
+
+// Rotated-frame state: rho, u (normal), v, w (tangential), p, By, Bz (tangential)
+template <typename T>
+struct Prim {
+  T r, u, v, w, p, by, bz;
+};
+
+// HLLD flux in the rotated frame; out[0..7] = (rho, m_n, m_t1, m_t2, E, B_n, B_t1, B_t2).
+template <typename T>
+__device__ __forceinline__ void hlld(const Prim<T>& L, const Prim<T>& R, T bn, T gamma, T eps, T* out) {
+  const T gm1i = T(1) / (gamma - T(1));
+  const T bn2 = bn * bn;
+  const T b2L = bn2 + L.by * L.by + L.bz * L.bz;
+  const T b2R = bn2 + R.by * R.by + R.bz * R.bz;
+  const T EL = L.p * gm1i + T(0.5) * L.r * (L.u * L.u + L.v * L.v + L.w * L.w) + T(0.5) * b2L;
+  const T ER = R.p * gm1i + T(0.5) * R.r * (R.u * R.u + R.v * R.v + R.w * R.w) + T(0.5) * b2R;
+  const T pTL = L.p + T(0.5) * b2L, pTR = R.p + T(0.5) * b2R;
+  // fast speeds
+  T cfL, cfR;
+  {
+    T a2 = gamma * L.p / L.r, bb = b2L / L.r, bn2r = bn2 / L.r;
+    T disc = (a2 + bb) * (a2 + bb) - T(4) * a2 * bn2r;
+    disc = disc > T(0) ? disc : T(0);
+    cfL = dsqrt(T(0.5) * (a2 + bb + dsqrt(disc)));
+    a2 = gamma * R.p / R.r;
+    bb = b2R / R.r;
+    bn2r = bn2 / R.r;
+    disc = (a2 + bb) * (a2 + bb) - T(4) * a2 * bn2r;
+    disc = disc > T(0) ? disc : T(0);
+    cfR = dsqrt(T(0.5) * (a2 + bb + dsqrt(disc)));
+  }
+  const T cmax = cfL > cfR ? cfL : cfR;
+  const T SL = (L.u < R.u ? L.u : R.u) - cmax;
+  const T SR = (L.u > R.u ? L.u : R.u) + cmax;
+
+  auto phys = [&](const Prim<T>& s, T E, T pT, T* F, T* U) {
+    const T vb = s.u * bn + s.v * s.by + s.w * s.bz;
+    U[0] = s.r; U[1] = s.r * s.u; U[2] = s.r * s.v; U[3] = s.r * s.w;
+    U[4] = E; U[5] = bn; U[6] = s.by; U[7] = s.bz;
+    F[0] = s.r * s.u;
+    F[1] = s.r * s.u * s.u + pT - bn2;
+    F[2] = s.r * s.v * s.u - bn * s.by;
+    F[3] = s.r * s.w * s.u - bn * s.bz;
+    F[4] = (E + pT) * s.u - bn * vb;
+    F[5] = T(0);
+    F[6] = s.by * s.u - bn * s.v;
+    F[7] = s.bz * s.u - bn * s.w;
+  };
+
+  T FL[8], UL[8];
+  if (SL > T(0)) {
+    phys(L, EL, pTL, FL, UL);
+    for (int k = 0; k < 8; ++k) out[k] = FL[k];
+    return;
+  }
+  T FR[8], UR[8];
+  phys(L, EL, pTL, FL, UL);
+  phys(R, ER, pTR, FR, UR);
+  const T dL = SL - L.u, dR = SR - R.u;
+  const T den = dR * R.r - dL * L.r;
+  const T SM = (dR * R.r * R.u - dL * L.r * L.u - pTR + pTL) / den;
+  const T pTs = (dR * R.r * pTL - dL * L.r * pTR + L.r * R.r * dR * dL * (R.u - L.u)) / den;
+
+  // single-starred states
+  T rs[2], vs[2], ws[2], bys[2], bzs[2], Es[2];
+  for (int side = 0; side < 2; ++side) {
+    const Prim<T>& s = side ? R : L;
+    const T S = side ? SR : SL;
+    const T d = side ? dR : dL;
+    const T E = side ? ER : EL;
+    const T pT = side ? pTR : pTL;
+    rs[side] = s.r * d / (S - SM);
+    const T q = s.r * d * (S - SM);
+    const T dd = q - bn2;
+    const T aq = q < T(0) ? -q : q;
+    const T add = dd < T(0) ? -dd : dd;
+    if (add < eps * (aq + bn2)) {
+      vs[side] = s.v; ws[side] = s.w; bys[side] = s.by; bzs[side] = s.bz;
+    } else {
+      const T fv = bn * (SM - s.u) / dd;
+      const T fb = (s.r * d * d - bn2) / dd;
+      vs[side] = s.v - s.by * fv;
+      ws[side] = s.w - s.bz * fv;
+      bys[side] = s.by * fb;
+      bzs[side] = s.bz * fb;
+    }
+    const T vb = s.u * bn + s.v * s.by + s.w * s.bz;
+    const T vbs = SM * bn + vs[side] * bys[side] + ws[side] * bzs[side];
+    Es[side] = (d * E - pT * s.u + pTs * SM + bn * (vb - vbs)) / (S - SM);
+  }
+  const T sqL = dsqrt(rs[0]), sqR = dsqrt(rs[1]);
+  const T sgn = bn >= T(0) ? T(1) : T(-1);
+  const T abn = bn < T(0) ? -bn : bn;
+  const T SsL = SM - abn / sqL, SsR = SM + abn / sqR;
+
+  auto starU = [&](int side, T v, T w, T by, T bz, T E, T* U) {
+    U[0] = rs[side]; U[1] = rs[side] * SM; U[2] = rs[side] * v; U[3] = rs[side] * w;
+    U[4] = E; U[5] = bn; U[6] = by; U[7] = bz;
+  };
+
+  if (SsL >= T(0) || (SM < T(0) && SsR < T(0))) {
+    // single-starred region on the left (SL <= 0 <= SsL) or right (SsR <= 0 <= SR) or outside
+    if (SsL >= T(0)) {
+      T Us[8];
+      starU(0, vs[0], ws[0], bys[0], bzs[0], Es[0], Us);
+      for (int k = 0; k < 8; ++k) out[k] = FL[k] + SL * (Us[k] - UL[k]);
+      return;
+    }
+    if (SR >= T(0)) {
+      T Us[8];
+      starU(1, vs[1], ws[1], bys[1], bzs[1], Es[1], Us);
+      for (int k = 0; k < 8; ++k) out[k] = FR[k] + SR * (Us[k] - UR[k]);
+      return;
+    }
+    for (int k = 0; k < 8; ++k) out[k] = FR[k];
+    return;
+  }
+  // double-starred states (SsL < 0 and (SM >= 0 or SsR >= 0))
+  const T inv = T(1) / (sqL + sqR);
+  const T vss = (sqL * vs[0] + sqR * vs[1] + (bys[1] - bys[0]) * sgn) * inv;
+  const T wss = (sqL * ws[0] + sqR * ws[1] + (bzs[1] - bzs[0]) * sgn) * inv;
+  const T byss = (sqL * bys[1] + sqR * bys[0] + sqL * sqR * (vs[1] - vs[0]) * sgn) * inv;
+  const T bzss = (sqL * bzs[1] + sqR * bzs[0] + sqL * sqR * (ws[1] - ws[0]) * sgn) * inv;
+  const T vbss = SM * bn + vss * byss + wss * bzss;
+  const int side = SM >= T(0) ? 0 : 1;
+  const T S = side ? SR : SL;
+  const T Ss = side ? SsR : SsL;
+  const T sq = side ? sqR : sqL;
+  const T vbs = SM * bn + vs[side] * bys[side] + ws[side] * bzs[side];
+  const T Ess = side ? Es[1] + sq * (vbs - vbss) * sgn : Es[0] - sq * (vbs - vbss) * sgn;
+  T Us[8], Uss[8];
+  starU(side, vs[side], ws[side], bys[side], bzs[side], Es[side], Us);
+  starU(side, vss, wss, byss, bzss, Ess, Uss);
+  const T* F0 = side ? FR : FL;
+  const T* U0 = side ? UR : UL;
+  for (int k = 0; k < 8; ++k) out[k] = F0[k] + S * (Us[k] - U0[k]) + Ss * (Uss[k] - Us[k]);
+}
+
+// Face flux for a face normal to `a` from conserved traces uL, uR (xyz frame).
+// Writes F[0..V-1] in the xyz frame and returns B^n_F.
+template <typename T>
+__device__ __forceinline__ T face_flux(const T* uL, const T* uR, int a, T gamma, bool glm, T ch, T eps,
+                                       T* F) {
+  const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+  Prim<T> L, R;
+  {
+    const T ir = T(1) / uL[0];
+    const T v0 = uL[1] * ir, v1 = uL[2] * ir, v2 = uL[3] * ir;
+    const T b2 = uL[5] * uL[5] + uL[6] * uL[6] + uL[7] * uL[7];
+    L.r = uL[0];
+    L.p = (gamma - T(1)) * (uL[4] - T(0.5) * uL[0] * (v0 * v0 + v1 * v1 + v2 * v2) - T(0.5) * b2);
+    const T vv[3] = {v0, v1, v2};
+    L.u = vv[a]; L.v = vv[t1]; L.w = vv[t2];
+    L.by = uL[5 + t1]; L.bz = uL[5 + t2];
+  }
+  {
+    const T ir = T(1) / uR[0];
+    const T v0 = uR[1] * ir, v1 = uR[2] * ir, v2 = uR[3] * ir;
+    const T b2 = uR[5] * uR[5] + uR[6] * uR[6] + uR[7] * uR[7];
+    R.r = uR[0];
+    R.p = (gamma - T(1)) * (uR[4] - T(0.5) * uR[0] * (v0 * v0 + v1 * v1 + v2 * v2) - T(0.5) * b2);
+    const T vv[3] = {v0, v1, v2};
+    R.u = vv[a]; R.v = vv[t1]; R.w = vv[t2];
+    R.by = uR[5 + t1]; R.bz = uR[5 + t2];
+  }
+  const T bnL = uL[5 + a], bnR = uR[5 + a];
+  const T bnF = bn_face(L.r, R.r, bnL, bnR);
+  T Fr[8];
+  hlld(L, R, bnF, gamma, eps, Fr);
+  F[0] = Fr[0];
+  F[1 + a] = Fr[1]; F[1 + t1] = Fr[2]; F[1 + t2] = Fr[3];
+  F[4] = Fr[4];
+  F[5 + a] = Fr[5]; F[5 + t1] = Fr[6]; F[5 + t2] = Fr[7];
+  if (glm) {
+    const T bstar = T(0.5) * (bnL + bnR) - (uR[8] - uL[8]) / (T(2) * ch);
+    const T pstar = T(0.5) * (uL[8] + uR[8]) - T(0.5) * ch * (bnR - bnL);
+    F[5 + a] = pstar;
+    F[8] = ch * ch * bstar;
+  }
+  return bnF;
+}
+
+}  // namespace dgmhd
