@@ -167,6 +167,29 @@ int dg_mhd_profile(dg_mhd_ctx* ctx, int enable);
 int dg_mhd_profile_read(dg_mhd_ctx* ctx, int kind, double* total_ms, int64_t* launches);
 int64_t dg_mhd_launch_count(const dg_mhd_ctx* ctx);
 
+/* dg_mhd_rhs without any device allocation (the paper has no counterpart:
+ * this is a deployment variant of dg_mhd_rhs).
+ * For callers that cannot call cudaMalloc -- a framework whose pool owns all
+ * device memory, code that must not trigger the device synchronisation that
+ * cudaMalloc/cudaFree can cause, or an embedding that fixes the device
+ * footprint at start-up. No context is needed: mesh, degree, scheme, gamma and
+ * p (NULL = defaults; only eps_hlld is used) describe the problem, and c_h and
+ * damping_rate set the GLM terms (ignored for Powell). The caller passes the
+ * FP64 state w and the FP64 output rhs (DEVICE, layout of dg_mhd_rhs with
+ * cell_stride = n_cells rounded up to a multiple of 32).
+ * All scratch (basis tables, device scalars, face fluxes) lives in one static
+ * device array of 4 Mi doubles (32 MiB) that every GPU loading the library
+ * keeps until the process exits. The first call on a device resolves that
+ * array's device address (cudaGetSymbolAddress) with the device current; make
+ * that first call before any stream capture. Problems whose scratch exceeds the
+ * array return DG_E_ARG (about 16 thousand cells at degree 2 in 3D). Every call
+ * rewrites the shared array (tables and scalars are re-uploaded and the status
+ * word cleared), so calls that overlap on the GPU -- two streams, two host
+ * threads -- race and must be serialised by the caller. */
+int dg_mhd_rhs_noalloc(const dg_mesh_desc* mesh, int degree, int divB_scheme, double gamma,
+                       const dg_mhd_params* p, double c_h, double damping_rate, const double* w,
+                       double* rhs, void* stream);
+
 /* Releases every device allocation of ctx. ctx may be NULL. */
 void dg_mhd_destroy(dg_mhd_ctx* ctx);
 

@@ -22,7 +22,8 @@ DG_LIMIT_OFF, DG_LIMIT_TVB, DG_LIMIT_MLP = 0, 1, 2
 EXPORTS = [
     "dg_mhd_default_params", "dg_mhd_init", "dg_mhd_state_layout", "dg_mhd_project", "dg_mhd_set_glm",
     "dg_mhd_rhs", "dg_mhd_limit", "dg_mhd_dt", "dg_mhd_step", "dg_mhd_last_dt", "dg_mhd_status",
-    "dg_mhd_profile", "dg_mhd_profile_read", "dg_mhd_launch_count", "dg_mhd_destroy", "dg_mhd_strerror",
+    "dg_mhd_profile", "dg_mhd_profile_read", "dg_mhd_launch_count", "dg_mhd_rhs_noalloc", "dg_mhd_destroy",
+    "dg_mhd_strerror",
 ]
 KIND_FACE, KIND_CELL, KIND_DT, KIND_LIMIT, KIND_PROJECT = range(5)
 
@@ -67,6 +68,8 @@ def lib():
     L.dg_mhd_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), i64p]
     L.dg_mhd_launch_count.argtypes = [vp]
     L.dg_mhd_launch_count.restype = ctypes.c_int64
+    L.dg_mhd_rhs_noalloc.argtypes = [ctypes.POINTER(MeshDesc), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     ctypes.POINTER(Params), ctypes.c_double, ctypes.c_double, vp, vp, vp]
     L.dg_mhd_destroy.argtypes = [vp]
     L.dg_mhd_destroy.restype = None
     L.dg_mhd_strerror.argtypes = [ctypes.c_int]
@@ -97,6 +100,26 @@ def _ptr(t):
 def _stream():
     import torch
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def mesh_desc(dim, n, box_len=1.0) -> MeshDesc:
+    m = MeshDesc()
+    m.dim = dim
+    nn = list(n) + [1] * (3 - len(n))
+    for a in range(3):
+        m.n[a] = nn[a]
+    m.box_len = box_len
+    m.periodic = 1
+    return m
+
+
+def rhs_noalloc(dim, n, degree, divb, w, out, gamma=5.0 / 3.0, box_len=1.0, c_h=0.0, damping_rate=0.0):
+    """dg_mhd_rhs_noalloc: the operator with all device scratch in the library's
+    static array (for callers that must not allocate device memory)."""
+    m = mesh_desc(dim, n, box_len)
+    _check(lib().dg_mhd_rhs_noalloc(ctypes.byref(m), degree, DG_DIVB_GLM if divb == "glm" else DG_DIVB_POWELL,
+                                    gamma, None, c_h, damping_rate, _ptr(w), _ptr(out), _stream()),
+           "dg_mhd_rhs_noalloc")
 
 
 def default_params(**kw) -> Params:

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libdgmhd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["dg_api.cu", "dg_kernels.cu", "dg_limit.cu", "dg_basis.cpp"]
+SOURCES = ["dg_api.cu", "dg_kernels.cu", "dg_limit.cu", "dg_noalloc.cu", "dg_basis.cpp"]
 
 
 def _nvcc():

@@ -160,6 +160,55 @@ inline bool fp32(const Ctx& c) { return c.p.precision == DG_PREC_FP32MIX; }
 
 namespace dgmhd {
 
+// Geometry and host basis for a uniform periodic mesh, for callers that keep
+// no context (the allocation-free entry point); mirrors the set-up in init.
+int make_geom(const dg_mesh_desc* mesh, int degree, int divB_scheme, double gamma, Basis& B, Geom& g) {
+  if (mesh->dim != 2 && mesh->dim != 3) return DG_E_MESH;
+  if (!mesh->periodic) return DG_E_UNSUPPORTED;
+  if (degree < 0 || degree > MAXD) return DG_E_UNSUPPORTED;
+  if (divB_scheme != DG_DIVB_POWELL && divB_scheme != DG_DIVB_GLM) return DG_E_ARG;
+  if (!(gamma > 1.0)) return DG_E_ARG;
+  for (int a = 0; a < mesh->dim; ++a)
+    if (mesh->n[a] < 1) return DG_E_MESH;
+  if (!(mesh->box_len > 0.0)) return DG_E_MESH;
+  g = Geom();
+  g.D = mesh->dim;
+  g.d = degree;
+  g.glm = divB_scheme == DG_DIVB_GLM;
+  if (!B.build(g.D, degree, !g.glm)) return DG_E_UNSUPPORTED;
+  g.n = B.n;
+  g.ndiv = B.ndiv;
+  g.DB = g.D;
+  g.nq1 = degree + 1;
+  g.Qv = 1;
+  for (int a = 0; a < g.D; ++a) g.Qv *= g.nq1;
+  g.Qf = g.Qv / g.nq1;
+  g.V = g.glm ? 9 : 8;
+  g.ldf0 = g.glm ? -1 : 5 * g.n;
+  g.bz2d = -1;
+  g.nrows = g.glm ? 9 * g.n : 5 * g.n + g.ndiv;
+  if (!g.glm && g.D == 2) {
+    g.bz2d = g.nrows;
+    g.nrows += g.n;
+  }
+  g.nx = mesh->n[0];
+  g.ny = mesh->n[1];
+  g.nz = g.D == 3 ? mesh->n[2] : 1;
+  g.ncell = (int64_t)g.nx * g.ny * g.nz;
+  g.stride = (g.ncell + 31) / 32 * 32;
+  g.dx = mesh->box_len / g.nx;
+  g.gamma = gamma;
+  return DG_OK;
+}
+
+// Host tables in the order Pv dPv Pf Lv dLv Lf L0 wv wf minv.
+void host_tables(const Basis& B, const Geom& g, std::vector<double>* out10) {
+  HostTables h;
+  build_host_tables(B, g, h);
+  out10[0] = h.Pv; out10[1] = h.dPv; out10[2] = h.Pf; out10[3] = h.Lv; out10[4] = h.dLv;
+  out10[5] = h.Lf; out10[6] = h.L0; out10[7] = h.wv; out10[8] = h.wf; out10[9] = h.minv;
+}
+
 void Prof::begin(int k, cudaStream_t st) {
   launches[k] += 1;
   if (!on) return;
