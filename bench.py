@@ -374,6 +374,7 @@ def main():
         "clocks": res["clocks"], "gpu_launches": res["launches"], "kernels": res["kern"],
         "fp64_plain": res.get("fp64_plain"), "status": res["status"], "finite": res["finite"],
         "dof": res["dof"],
+        "kernel_path": "specialised GLM 3D kernels (k_face_glm, k_cell_glm)",
     }
     print(json.dumps(line))
 

@@ -94,6 +94,8 @@ typedef struct {
   int precision;      /* DG_PREC_*                                   [FP64] */
   int limiter;        /* DG_LIMIT_*                                  [OFF]  */
   int positivity;     /* 1: positivity limiter on                    [0]    */
+  int generic_kernels;/* 1: force the generic kernels even where a    [0]
+                         specialised kernel exists (testing)                 */
 } dg_mhd_params;
 
 /* Fills *p with the defaults listed above. */

@@ -12,7 +12,10 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libdgmhd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["dg_api.cu", "dg_kernels.cu", "dg_limit.cu", "dg_noalloc.cu", "dg_basis.cpp"]
+# FP32 kernels of the specialised path use the hardware's approximate division,
+# reciprocal square root and square root (FP64 code is unaffected)
+FAST_MATH = {"dg_fast.cu"}
+SOURCES = ["dg_api.cu", "dg_kernels.cu", "dg_fast.cu", "dg_limit.cu", "dg_noalloc.cu", "dg_basis.cpp"]
 
 
 def _nvcc():
@@ -32,6 +35,8 @@ def _compile(src, verbose_ptxas=False):
     cmd = [_nvcc(), "-c", os.path.join(CSRC, src), "-o", obj] + _flags()
     if src.endswith(".cpp"):
         cmd += ["-x", "cu"]
+    if src in FAST_MATH:
+        cmd += ["--use_fast_math"]
     if verbose_ptxas:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

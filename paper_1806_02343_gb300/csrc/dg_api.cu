@@ -10,6 +10,7 @@
 #include "../../include/dg_mhd.h"
 #include "dg_basis.h"
 #include "dg_ctx.h"
+#include "dg_fast.cuh"
 #include "dg_kernels.cuh"
 #include "dg_limit.cuh"
 
@@ -153,6 +154,51 @@ void free_tables(Tables<T>& t) {
 }
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+template <typename T, int DEG>
+void* make_fast_tabs(const HostTables& h, const Geom& g) {
+  using Dm = FastDims<DEG>;
+  auto* ft = new FastAll<T, DEG>();
+  const int n = g.n, Qv = g.Qv, Qf = g.Qf;
+  for (int a = 0; a < 3; ++a)
+    for (int l = 0; l < n; ++l)
+      for (int p = 0; p < Qf; ++p) {
+        ft->face[a].PL[l][p] = (T)h.Pf[((size_t)(2 * a + 1) * n + l) * Qf + p];
+        ft->face[a].PR[l][p] = (T)h.Pf[((size_t)(2 * a) * n + l) * Qf + p];
+      }
+  for (int l = 0; l < n; ++l) {
+    for (int q = 0; q < Qv; ++q) {
+      ft->cell.P[l][q] = (T)h.Pv[(size_t)l * Qv + q];
+      for (int a = 0; a < 3; ++a) ft->cell.dPw[a][l][q] = (T)(h.dPv[((size_t)a * n + l) * Qv + q] * h.wv[q]);
+    }
+    for (int f = 0; f < 6; ++f)
+      for (int p = 0; p < Qf; ++p) ft->cell.Pfw[f][l][p] = (T)(h.Pf[((size_t)f * n + l) * Qf + p] * h.wf[p]);
+    ft->cell.minv[l] = (T)h.minv[l];
+  }
+  static_assert(Dm::N > 0, "");
+  return ft;
+}
+
+void free_fast_tabs(Ctx& c) {
+  if (!c.fast_tabs) return;
+  switch (c.fast) {
+    case 11: delete (FastAll<float, 1>*)c.fast_tabs; break;
+    case 12: delete (FastAll<float, 2>*)c.fast_tabs; break;
+    case 13: delete (FastAll<float, 3>*)c.fast_tabs; break;
+    case 21: delete (FastAll<double, 1>*)c.fast_tabs; break;
+    case 22: delete (FastAll<double, 2>*)c.fast_tabs; break;
+  }
+  c.fast_tabs = nullptr;
+  c.fast = 0;
+}
+
+FastGeom fast_geom(const Geom& g) {
+  FastGeom f;
+  f.nx = g.nx; f.ny = g.ny; f.nz = g.nz;
+  f.ncell = g.ncell; f.stride = g.stride;
+  f.dx = g.dx; f.gamma = g.gamma;
+  return f;
+}
 
 inline bool fp32(const Ctx& c) { return c.p.precision == DG_PREC_FP32MIX; }
 
@@ -319,6 +365,7 @@ void dg_mhd_destroy(dg_mhd_ctx* ctx) {
   if (!ctx) return;
   Ctx& c = ctx->c;
   c.prof.release();
+  free_fast_tabs(c);
   free_tables(c.t64);
   free_tables(c.t32);
   void* ptrs[] = {c.sc, c.face_buf, c.face_buf32, c.stage_buf[0], c.stage_buf[1], c.stage_buf[2],
@@ -399,7 +446,7 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
   }
   const size_t esz = fp32(c) ? sizeof(float) : sizeof(double);
   const size_t state_bytes = (size_t)g.nrows * g.stride * esz;
-  const size_t face_elems = (size_t)g.D * g.ncell * g.Qf * 9;
+  const size_t face_elems = (size_t)g.D * g.stride * g.Qf * 9;
   bool ok = cudaMalloc(&c.sc, sizeof(DevScalars)) == cudaSuccess &&
             cudaMemset(c.sc, 0, sizeof(DevScalars)) == cudaSuccess &&
             cudaMalloc(&c.stage_buf[0], state_bytes) == cudaSuccess &&
@@ -417,6 +464,19 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
   if (!ok) {
     dg_mhd_destroy(ctx);
     return DG_E_CUDA;
+  }
+  // specialised GLM kernels for uniform 3D meshes
+  if (g.glm && g.D == 3 && !prm.generic_kernels) {
+    if (fp32(c)) {
+      if (degree == 1) c.fast_tabs = make_fast_tabs<float, 1>(h, g);
+      if (degree == 2) c.fast_tabs = make_fast_tabs<float, 2>(h, g);
+      if (degree == 3) c.fast_tabs = make_fast_tabs<float, 3>(h, g);
+      if (c.fast_tabs) c.fast = 10 + degree;
+    } else {
+      if (degree == 1) c.fast_tabs = make_fast_tabs<double, 1>(h, g);
+      if (degree == 2) c.fast_tabs = make_fast_tabs<double, 2>(h, g);
+      if (c.fast_tabs) c.fast = 20 + degree;
+    }
   }
   // initial GLM speeds: fixed c_h if given (damping from c_r), else set by dt
   if (g.glm && prm.c_h_fixed > 0.0) {
@@ -498,6 +558,31 @@ namespace {
 int operator_pass(Ctx& c, const void* w, const double* wmean, void* out, double* outmean, const void* w0,
                   const double* w0mean, double ca, double cb, int combine, cudaStream_t st) {
   const Geom& g = c.g;
+  if (c.fast) {
+    const FastGeom fg = fast_geom(g);
+#define FASTCASE(code, T, DEG, FB)                                                                          \
+  case code: {                                                                                              \
+    const auto& ft = *(const FastAll<T, DEG>*)c.fast_tabs;                                                \
+    c.prof.begin(0, st);                                                                                    \
+    launch_face_glm<T, DEG>(ft, fg, (const T*)w, FB, c.sc, c.p.eps_hlld, st);                               \
+    c.prof.end(0, st);                                                                                      \
+    c.prof.launches[0] += 2;                                                                                \
+    c.prof.begin(1, st);                                                                                    \
+    launch_cell_glm<T, DEG>(ft, fg, (const T*)w, FB, (T*)out, (const T*)w0, ca, cb, combine, c.sc, wmean,   \
+                            w0mean, outmean, st);                                                           \
+    c.prof.end(1, st);                                                                                      \
+    break;                                                                                                  \
+  }
+    switch (c.fast) {
+      FASTCASE(11, float, 1, c.face_buf32)
+      FASTCASE(12, float, 2, c.face_buf32)
+      FASTCASE(13, float, 3, c.face_buf32)
+      FASTCASE(21, double, 1, c.face_buf)
+      FASTCASE(22, double, 2, c.face_buf)
+    }
+#undef FASTCASE
+    return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
+  }
   if (fp32(c)) {
     c.prof.begin(0, st);
     launch_face<float>(g, c.t32, (const float*)w, c.face_buf32, c.sc, c.p.eps_hlld, st);

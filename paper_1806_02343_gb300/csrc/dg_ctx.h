@@ -92,6 +92,8 @@ struct Ctx {
   double* proj_tab = nullptr;      // projection table [r][q][comp]
   double* proj_w = nullptr;
   uint8_t* troubled = nullptr;     // per-cell limiter flags (scratch)
+  int fast = 0;                    // specialised GLM path: 10*prec + degree, 0 = none
+  void* fast_tabs = nullptr;       // host FastAll<T, DEG> (kernel parameters)
 };
 
 }  // namespace dgmhd

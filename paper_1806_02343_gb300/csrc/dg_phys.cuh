@@ -113,79 +113,71 @@ __device__ __forceinline__ void hlld(const Prim<T>& L, const Prim<T>& R, T bn, T
   const T SM = (dR * R.r * R.u - dL * L.r * L.u - pTR + pTL) / den;
   const T pTs = (dR * R.r * pTL - dL * L.r * pTR + L.r * R.r * dR * dL * (R.u - L.u)) / den;
 
-  // single-starred states
-  T rs[2], vs[2], ws[2], bys[2], bzs[2], Es[2];
-  for (int side = 0; side < 2; ++side) {
-    const Prim<T>& s = side ? R : L;
-    const T S = side ? SR : SL;
-    const T d = side ? dR : dL;
-    const T E = side ? ER : EL;
-    const T pT = side ? pTR : pTL;
-    rs[side] = s.r * d / (S - SM);
-    const T q = s.r * d * (S - SM);
-    const T dd = q - bn2;
-    const T aq = q < T(0) ? -q : q;
-    const T add = dd < T(0) ? -dd : dd;
+  // single-starred states (Miyoshi & Kusano 2005), side by side without
+  // run-time indexing so that everything stays in registers
+  const T rsL = L.r * dL / (SL - SM), rsR = R.r * dR / (SR - SM);
+  T vsL, wsL, bysL, bzsL, vsR, wsR, bysR, bzsR;
+  {
+    const T q = L.r * dL * (SL - SM), dd = q - bn2;
+    const T aq = q < T(0) ? -q : q, add = dd < T(0) ? -dd : dd;
     if (add < eps * (aq + bn2)) {
-      vs[side] = s.v; ws[side] = s.w; bys[side] = s.by; bzs[side] = s.bz;
+      vsL = L.v; wsL = L.w; bysL = L.by; bzsL = L.bz;
     } else {
-      const T fv = bn * (SM - s.u) / dd;
-      const T fb = (s.r * d * d - bn2) / dd;
-      vs[side] = s.v - s.by * fv;
-      ws[side] = s.w - s.bz * fv;
-      bys[side] = s.by * fb;
-      bzs[side] = s.bz * fb;
+      const T fv = bn * (SM - L.u) / dd, fb = (L.r * dL * dL - bn2) / dd;
+      vsL = L.v - L.by * fv; wsL = L.w - L.bz * fv; bysL = L.by * fb; bzsL = L.bz * fb;
     }
-    const T vb = s.u * bn + s.v * s.by + s.w * s.bz;
-    const T vbs = SM * bn + vs[side] * bys[side] + ws[side] * bzs[side];
-    Es[side] = (d * E - pT * s.u + pTs * SM + bn * (vb - vbs)) / (S - SM);
   }
-  const T sqL = dsqrt(rs[0]), sqR = dsqrt(rs[1]);
+  {
+    const T q = R.r * dR * (SR - SM), dd = q - bn2;
+    const T aq = q < T(0) ? -q : q, add = dd < T(0) ? -dd : dd;
+    if (add < eps * (aq + bn2)) {
+      vsR = R.v; wsR = R.w; bysR = R.by; bzsR = R.bz;
+    } else {
+      const T fv = bn * (SM - R.u) / dd, fb = (R.r * dR * dR - bn2) / dd;
+      vsR = R.v - R.by * fv; wsR = R.w - R.bz * fv; bysR = R.by * fb; bzsR = R.bz * fb;
+    }
+  }
+  const T vbL = L.u * bn + L.v * L.by + L.w * L.bz, vbR = R.u * bn + R.v * R.by + R.w * R.bz;
+  const T vbsL = SM * bn + vsL * bysL + wsL * bzsL, vbsR = SM * bn + vsR * bysR + wsR * bzsR;
+  const T EsL = (dL * EL - pTL * L.u + pTs * SM + bn * (vbL - vbsL)) / (SL - SM);
+  const T EsR = (dR * ER - pTR * R.u + pTs * SM + bn * (vbR - vbsR)) / (SR - SM);
+  const T sqL = dsqrt(rsL), sqR = dsqrt(rsR);
   const T sgn = bn >= T(0) ? T(1) : T(-1);
   const T abn = bn < T(0) ? -bn : bn;
   const T SsL = SM - abn / sqL, SsR = SM + abn / sqR;
 
-  auto starU = [&](int side, T v, T w, T by, T bz, T E, T* U) {
-    U[0] = rs[side]; U[1] = rs[side] * SM; U[2] = rs[side] * v; U[3] = rs[side] * w;
-    U[4] = E; U[5] = bn; U[6] = by; U[7] = bz;
-  };
-
-  if (SsL >= T(0) || (SM < T(0) && SsR < T(0))) {
-    // single-starred region on the left (SL <= 0 <= SsL) or right (SsR <= 0 <= SR) or outside
-    if (SsL >= T(0)) {
-      T Us[8];
-      starU(0, vs[0], ws[0], bys[0], bzs[0], Es[0], Us);
-      for (int k = 0; k < 8; ++k) out[k] = FL[k] + SL * (Us[k] - UL[k]);
-      return;
-    }
-    if (SR >= T(0)) {
-      T Us[8];
-      starU(1, vs[1], ws[1], bys[1], bzs[1], Es[1], Us);
-      for (int k = 0; k < 8; ++k) out[k] = FR[k] + SR * (Us[k] - UR[k]);
-      return;
-    }
-    for (int k = 0; k < 8; ++k) out[k] = FR[k];
+  if (SsL >= T(0)) {  // left single-starred region
+    const T Us[8] = {rsL, rsL * SM, rsL * vsL, rsL * wsL, EsL, bn, bysL, bzsL};
+    for (int k = 0; k < 8; ++k) out[k] = FL[k] + SL * (Us[k] - UL[k]);
     return;
   }
-  // double-starred states (SsL < 0 and (SM >= 0 or SsR >= 0))
+  if (SM < T(0) && SsR < T(0)) {
+    if (SR >= T(0)) {  // right single-starred region
+      const T Us[8] = {rsR, rsR * SM, rsR * vsR, rsR * wsR, EsR, bn, bysR, bzsR};
+      for (int k = 0; k < 8; ++k) out[k] = FR[k] + SR * (Us[k] - UR[k]);
+    } else {
+      for (int k = 0; k < 8; ++k) out[k] = FR[k];
+    }
+    return;
+  }
+  // double-starred states
   const T inv = T(1) / (sqL + sqR);
-  const T vss = (sqL * vs[0] + sqR * vs[1] + (bys[1] - bys[0]) * sgn) * inv;
-  const T wss = (sqL * ws[0] + sqR * ws[1] + (bzs[1] - bzs[0]) * sgn) * inv;
-  const T byss = (sqL * bys[1] + sqR * bys[0] + sqL * sqR * (vs[1] - vs[0]) * sgn) * inv;
-  const T bzss = (sqL * bzs[1] + sqR * bzs[0] + sqL * sqR * (ws[1] - ws[0]) * sgn) * inv;
+  const T vss = (sqL * vsL + sqR * vsR + (bysR - bysL) * sgn) * inv;
+  const T wss = (sqL * wsL + sqR * wsR + (bzsR - bzsL) * sgn) * inv;
+  const T byss = (sqL * bysR + sqR * bysL + sqL * sqR * (vsR - vsL) * sgn) * inv;
+  const T bzss = (sqL * bzsR + sqR * bzsL + sqL * sqR * (wsR - wsL) * sgn) * inv;
   const T vbss = SM * bn + vss * byss + wss * bzss;
-  const int side = SM >= T(0) ? 0 : 1;
-  const T S = side ? SR : SL;
-  const T Ss = side ? SsR : SsL;
-  const T sq = side ? sqR : sqL;
-  const T vbs = SM * bn + vs[side] * bys[side] + ws[side] * bzs[side];
-  const T Ess = side ? Es[1] + sq * (vbs - vbss) * sgn : Es[0] - sq * (vbs - vbss) * sgn;
-  T Us[8], Uss[8];
-  starU(side, vs[side], ws[side], bys[side], bzs[side], Es[side], Us);
-  starU(side, vss, wss, byss, bzss, Ess, Uss);
-  const T* F0 = side ? FR : FL;
-  const T* U0 = side ? UR : UL;
-  for (int k = 0; k < 8; ++k) out[k] = F0[k] + S * (Us[k] - U0[k]) + Ss * (Uss[k] - Us[k]);
+  if (SM >= T(0)) {
+    const T Ess = EsL - sqL * (vbsL - vbss) * sgn;
+    const T Us[8] = {rsL, rsL * SM, rsL * vsL, rsL * wsL, EsL, bn, bysL, bzsL};
+    const T Uss[8] = {rsL, rsL * SM, rsL * vss, rsL * wss, Ess, bn, byss, bzss};
+    for (int k = 0; k < 8; ++k) out[k] = FL[k] + SL * (Us[k] - UL[k]) + SsL * (Uss[k] - Us[k]);
+  } else {
+    const T Ess = EsR + sqR * (vbsR - vbss) * sgn;
+    const T Us[8] = {rsR, rsR * SM, rsR * vsR, rsR * wsR, EsR, bn, bysR, bzsR};
+    const T Uss[8] = {rsR, rsR * SM, rsR * vss, rsR * wss, Ess, bn, byss, bzss};
+    for (int k = 0; k < 8; ++k) out[k] = FR[k] + SR * (Us[k] - UR[k]) + SsR * (Uss[k] - Us[k]);
+  }
 }
 
 // Face flux for a face normal to `a` from conserved traces uL, uR (xyz frame).

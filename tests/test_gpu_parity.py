@@ -38,14 +38,40 @@ def _fn(name, nvar):
     raise KeyError(name)
 
 
-def _setup(D, d, divb, ncell, fname, precision="fp64"):
+def _setup(D, d, divb, ncell, fname, precision="fp64", generic=0):
     import torch
     from paper_1806_02343_gb300.binding import Solver, DG_PREC_FP32MIX, DG_PREC_FP64
     S = Scheme(D, d, divb, G, ncell)
     w0 = S.project(_fn(fname, S.V))
     prec = DG_PREC_FP32MIX if precision == "fp32" else DG_PREC_FP64
-    sol = Solver(D, ncell, d, divb, gamma=G, box_len=S.L, precision=prec)
+    sol = Solver(D, ncell, d, divb, gamma=G, box_len=S.L, precision=prec, generic_kernels=generic)
     return S, w0, sol
+
+
+# GLM in 3D has specialised kernels; the generic ones stay covered too
+GLM3D = [(3, 1, "glm", (9, 8, 7), "fourier"), CASES[2], CASES[3]]
+
+
+@pytest.mark.parametrize("generic", [0, 1])
+@pytest.mark.parametrize("D,d,divb,ncell,fname", GLM3D)
+def test_rhs_glm3d_both_kernel_paths(D, d, divb, ncell, fname, generic):
+    for prec, tol in (("fp64", 1e-12), ("fp32", 2e-4)):
+        S, w0, sol = _setup(D, d, divb, ncell, fname, precision=prec, generic=generic)
+        sol.set_glm(2.7, 1.3)
+        w = to_device(w0, sol)
+        out = torch_empty_like(w)
+        if prec == "fp32":
+            wm = means_to_device(w0, sol, S)
+            om = torch_empty_like(wm)
+            sol.rhs(w, wm, out, om)
+            from gpu_helpers import mean_rows
+            ref = S.rhs(w0, 2.7, 1.3)
+            # the FP64 mean rows of the FP32 form carry FP64-accumulated face sums
+            assert rel_err(om[:, : sol.ncell].cpu().numpy().T, ref[:, mean_rows(S)]) < 2e-5
+        else:
+            sol.rhs(w, None, out)
+            ref = S.rhs(w0, 2.7, 1.3)
+        assert rel_err(from_device(out, sol), ref) < tol
 
 
 @pytest.mark.parametrize("D,d,divb,ncell,fname", CASES)

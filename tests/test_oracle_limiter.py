@@ -1,0 +1,173 @@
+"""Pins of the oracle's limiters (Sec. 4.2, 4.3) -- no GPU."""
+import numpy as np
+import pytest
+
+from oracle import mhd
+from oracle.dg import Scheme
+from oracle.limiter import Limiter, eigensystem, dU_dW, dW_dU
+
+G = 5.0 / 3.0
+
+
+def _jac_fd(f, U, h=1e-6):
+    n = len(U)
+    J = np.zeros((n, n))
+    for k in range(n):
+        e = np.zeros(n)
+        e[k] = h * max(1.0, abs(U[k]))
+        J[:, k] = (f(U + e) - f(U - e)) / (2 * e[k])
+    return J
+
+
+STATES = [
+    (1.3, (0.4, -0.7, 0.2), 0.8, (0.6, 0.3, -0.5)),
+    (0.7, (-1.1, 0.2, 0.5), 2.0, (1.5, 0.0, 0.0)),      # B_t = 0 (alpha / beta degeneracy)
+    (1.0, (0.3, 0.1, -0.2), 0.5, (0.0, 0.8, 0.4)),       # B_n = 0
+    (2.0, (0.0, 0.0, 0.0), 1.0, (0.0, 0.0, 0.0)),       # no field
+]
+
+
+@pytest.mark.parametrize("st", STATES)
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_powell_eigensystem_diagonalises_8wave_jacobian(st, axis):
+    rho, v, p, Bv = st
+    U = mhd.conserved(np.array(rho), np.array(v), np.array(p), np.array(Bv), G)
+    R, L, lam = eigensystem(U, axis, G)
+    assert np.allclose(L @ R, np.eye(8), atol=1e-10)
+    # Powell system: du/dt + (df/du + q e_Bn^T) du/dx = 0 (eq. powell-src in 1D)
+    A = _jac_fd(lambda x: mhd.flux(x, axis, G), U)
+    A[:, mhd.BX + axis] += mhd.powell_q(U, G)
+    assert np.allclose(R @ np.diag(lam) @ L, A, atol=1e-6 * max(1.0, np.abs(A).max()))
+
+
+@pytest.mark.parametrize("st", STATES[:3])
+@pytest.mark.parametrize("axis", [0, 2])
+def test_glm_eigensystem(st, axis):
+    rho, v, p, Bv = st
+    ch = 4.0
+    U = mhd.conserved(np.array(rho), np.array(v), np.array(p), np.array(Bv), G, psi=np.array(0.3))
+    R, L, lam = eigensystem(U, axis, G, ch)
+    assert np.allclose(L @ R, np.eye(9), atol=1e-10)
+    # the MHD waves are those of the Powell-form system; the (B_n, psi) pair
+    # is the linear GLM subsystem dB_n/dt + dpsi/dx = 0, dpsi/dt + c_h^2 dB_n/dx = 0
+    A8 = _jac_fd(lambda x: mhd.flux(x, axis, G), U[:8])
+    A8[:, mhd.BX + axis] += mhd.powell_q(U[:8], G)
+    AW = dW_dU(U, G)[:8, :8] @ A8 @ dU_dW(U, G)[:8, :8]
+    W9 = np.zeros((9, 9))
+    W9[:8, :8] = AW
+    b = mhd.BX + axis
+    W9[b, :] = 0.0
+    W9[:, b] = 0.0
+    W9[b, 8] = 1.0
+    W9[8, b] = ch * ch
+    A = dU_dW(U, G) @ W9 @ dW_dU(U, G)
+    assert np.allclose(R @ np.diag(lam) @ L, A, atol=1e-6 * max(1.0, np.abs(A).max()))
+    assert np.isclose(sorted(lam)[0], -ch) and np.isclose(sorted(lam)[-1], ch)
+
+
+def _linear_field(x, nvar=8):
+    rho = 1.0 + 0.05 * x[..., 0]
+    one = np.ones_like(rho)
+    return mhd.conserved(rho, np.stack([0.1 * one, 0 * one, 0 * one], -1), one,
+                         np.stack([0.5 * one, 0.2 * one, 0 * one], -1), G)
+
+
+@pytest.mark.parametrize("divb", ["powell", "glm"])
+def test_tvb_not_triggered_on_linear_data_and_keeps_means(divb):
+    S = Scheme(3, 2, divb, G, (12, 3, 3))
+    nv = S.V
+    fn = lambda x: np.concatenate([_linear_field(x), np.zeros(x.shape[:-1] + (nv - 8,))], -1)
+    w = S.project(fn)
+    lim = Limiter(S, tvb=True, positivity=False)
+    out, troubled = lim.tvb_limit(w, ch=3.0)
+    ix = np.arange(S.C) % 12
+    interior = (ix > 0) & (ix < 11)
+    assert not troubled[interior].any()
+    assert np.allclose(S.means(out), S.means(w), atol=1e-14)
+    # slopes below M~ dx are never limited (Sec. 4.2.1); with M~ = 0 the
+    # periodic wrap -- a jump -- is limited while linear data still is not
+    S.P.Mtilde = 0.0
+    out, troubled = lim.tvb_limit(w, ch=3.0)
+    assert not troubled[interior].any()
+    assert troubled[~interior].any()
+
+
+def _step_field(x, nvar=8):
+    rho = np.where(x[..., 0] < 0.47, 1.0, 0.125)   # jump inside cell 7 of 16
+    p = np.where(x[..., 0] < 0.47, 1.0, 0.1)
+    one = np.ones_like(rho)
+    u = mhd.conserved(rho, np.stack([0 * one, 0 * one, 0 * one], -1), p,
+                      np.stack([0.75 * one, 1.0 * one, 0 * one], -1), G)
+    if nvar == 9:
+        u = np.concatenate([u, np.zeros(u.shape[:-1] + (1,))], -1)
+    return u
+
+
+@pytest.mark.parametrize("divb", ["powell", "glm"])
+def test_tvb_limits_a_jump_conservatively(divb):
+    S = Scheme(3, 2, divb, G, (16, 2, 2))
+    w = S.project(lambda x: _step_field(x, S.V))
+    S.P.Mtilde = 0.5
+    lim = Limiter(S, tvb=True, positivity=False)
+    out, troubled = lim.tvb_limit(w, ch=3.0)
+    ix = np.arange(S.C) % 16
+    assert troubled[ix == 7].all()
+    assert not troubled[(ix > 0) & (ix < 15) & (np.abs(ix - 7) > 1)].any()
+    assert np.allclose(S.means(out), S.means(w), atol=1e-14)
+    # limited cells: every weight of degree >= 2 is zero
+    deg = np.array([sum(S.modes[i]) if k == "L" else (lim.ldf_deg[i] if k == "B" else 0)
+                    for k, v, i in S.rows])
+    assert np.all(out[troubled][:, deg >= 2] == 0.0)
+    # the limited density slope along x lies within the TVD bounds of the means
+    m = S.means(out)
+    sl = lim.slopes(out)
+    for c in np.where(troubled)[0]:
+        cp, cm = S.nbr_plus[0][c], S.nbr_minus[0][c]
+        lo = min(m[cp, 0], m[cm, 0], m[c, 0])
+        hi = max(m[cp, 0], m[cm, 0], m[c, 0])
+        for s in (-1, 1):
+            val = m[c, 0] + s * sl[c, 0, 0]
+            assert lo - 1e-12 <= val <= hi + 1e-12
+
+
+def test_ldf_fix_is_divergence_free_and_diminishing():
+    S = Scheme(3, 2, "powell", G, (4, 4, 4))
+    lim = Limiter(S)
+    rng = np.random.default_rng(5)
+    out = np.zeros((1, S.N))
+    mean = np.zeros(8)
+    mean[mhd.BX:mhd.BX + 3] = [0.3, -0.2, 0.5]
+    sl = rng.normal(size=(3, 8))           # divergent limited slopes: diag sum != 0
+    lim._assign(out, 0, mean, sl)
+    got = lim.slopes(out)[0]
+    diag = np.array([got[a, mhd.BX + a] for a in range(3)])
+    orig = np.array([sl[a, mhd.BX + a] for a in range(3)])
+    assert abs(diag.sum()) < 1e-13
+    assert np.all(np.abs(diag) <= np.abs(orig) + 1e-14)
+    # off-diagonal slopes are untouched; cell mean of B is the given mean
+    for a in range(3):
+        for c in range(3):
+            if a != c:
+                assert abs(got[a, mhd.BX + c] - sl[a, mhd.BX + c]) < 1e-13
+    assert np.allclose(S.means(out)[0, mhd.BX:mhd.BX + 3], mean[mhd.BX:mhd.BX + 3], atol=1e-14)
+
+
+def test_positivity_limiter():
+    S = Scheme(3, 2, "glm", G, (3, 3, 3))
+    rng = np.random.default_rng(7)
+    w = S.project(lambda x: np.concatenate([mhd.conserved(np.ones(x.shape[:-1]), np.zeros(x.shape[:-1] + (3,)),
+                                                          np.ones(x.shape[:-1]), 0.3 * np.ones(x.shape[:-1] + (3,)),
+                                                          G), np.zeros(x.shape[:-1] + (1,))], -1))
+    # strong high-order perturbations of rho and E in some cells
+    bad = [0, 5, 13]
+    w[bad, 4] += 0.8          # a degree-1 rho mode
+    w[bad, 4 * S.n + 7] += 3.0  # a degree-2 E mode
+    lim = Limiter(S, tvb=False, positivity=True)
+    out = lim.positivity(w)
+    u = np.einsum("cr,rqv->cqv", out, lim.Spos)
+    rho, v, p, _ = mhd.primitives(u, G)
+    assert rho.min() >= S.P.eps_rho - 1e-15 and p.min() >= S.P.eps_p - 1e-12
+    assert np.allclose(S.means(out), S.means(w), atol=1e-14)
+    good = [c for c in range(S.C) if c not in bad]
+    assert np.array_equal(out[good], w[good])   # tau = 1 where already positive
+    assert not np.array_equal(out[bad], w[bad])
