@@ -145,9 +145,11 @@ int dg_mhd_limit(dg_mhd_ctx* ctx, void* w, double* wmean, uint8_t* troubled, voi
 int dg_mhd_dt(dg_mhd_ctx* ctx, const void* w, const double* wmean, double* dt_dev, void* stream);
 
 /* One SSP-RK3 step (Shu-Osher form, Sec. 3.6) in place on w (and wmean).
- * dt_dev: DEVICE scalar with the step, or NULL to compute it first with
- * dg_mhd_dt (then read it back with dg_mhd_last_dt). Limiters, if enabled,
- * are applied to every stage input before it is evaluated (Sec. 4.3). */
+ * dt_dev: DEVICE scalar with the step, or NULL to compute it from the limited
+ * input with dg_mhd_dt (then read it back with dg_mhd_last_dt). Limiters, if
+ * enabled, are applied to every stage input before it is evaluated (Sec. 4.3).
+ * GLM: with dt_dev given, c_h follows from it before the first limiter pass;
+ * with dt computed, the first limiter pass uses the c_h of the previous step. */
 int dg_mhd_step(dg_mhd_ctx* ctx, void* w, double* wmean, const double* dt_dev, void* stream);
 
 /* Device address of the timestep computed by the last dg_mhd_dt/step call. */

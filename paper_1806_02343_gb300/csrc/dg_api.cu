@@ -465,6 +465,7 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
     dg_mhd_destroy(ctx);
     return DG_E_CUDA;
   }
+  upload_limiter_tables(c);
   // specialised GLM kernels for uniform 3D meshes
   if (g.glm && g.D == 3 && !prm.generic_kernels) {
     if (fp32(c)) {
@@ -658,12 +659,16 @@ int dg_mhd_step(dg_mhd_ctx* ctx, void* w, double* wmean, const double* dt_dev, v
   if (fp32(c) && !wmean) return DG_E_ARG;
   cudaStream_t st = S(stream);
   int e;
-  if ((e = limit_pass(c, w, wmean, nullptr, st))) return e;
   if (dt_dev) {
+    // the step's dt (and GLM c_h) first, so the limiter sees this step's c_h
     c.prof.launches[2] += 1;
     launch_dt_from_value(c.g, c.p, dt_dev, c.sc, st);
+    if ((e = limit_pass(c, w, wmean, nullptr, st))) return e;
+  } else {
+    // dt from the limited state; the limiter uses the c_h of the previous step
+    if ((e = limit_pass(c, w, wmean, nullptr, st))) return e;
+    if ((e = dt_pass(c, w, wmean, nullptr, st))) return e;
   }
-  else if ((e = dt_pass(c, w, wmean, nullptr, st))) return e;
   void* s1 = c.stage_buf[0];
   void* s2 = c.stage_buf[1];
   double* m1 = c.stage_mean[0];

@@ -56,6 +56,22 @@ struct DevScalars {
   unsigned long long smax_bits;
   int status;      // latched dg_status bits
   int floor_used;
+  double inj_mass;    // mass added by the positivity floors (Sec. 4.3)
+  double inj_energy;  // energy added by the positivity floors
+};
+
+// Limiter tables (kernel parameters): degree-1 Legendre mode per axis, mode
+// degrees, LDF degrees, LDF component means of degree-0 rows, LDF linear slopes
+// <phi_jc, xi_a>/<xi_a, xi_a>, and the exact projection of constant / linear
+// fields onto the LDF rows: <phi_jc, 1>/M_j and <phi_jc, xi_a>/M_j.
+struct LimTabs {
+  int deg1[3];
+  int mdeg[64];
+  int ldf_deg[64];
+  double ldf_mean0[64 * 3];
+  double ldf_slope[64 * 9];
+  double ldf_pc[64 * 3];
+  double ldf_pl[64 * 9];
 };
 
 // Launch accounting: counts every kernel launch; with `on`, records a CUDA
@@ -77,6 +93,7 @@ struct Prof {
 
 struct Ctx {
   Prof prof;
+  LimTabs lim;
   Geom g;
   dg_mhd_params p;
   Basis* hb = nullptr;  // host basis (kept for projection tables)

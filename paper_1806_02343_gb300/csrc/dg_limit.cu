@@ -1,11 +1,529 @@
-// Limiters of Sec. 4.2 (TVB-characteristic, LDF slope fix) and Sec. 4.3 (positivity).
+// Limiters of Sec. 4.2 (characteristic TVB + LDF slope fix) and Sec. 4.3
+// (positivity), one thread per cell, state rows read and written coalesced.
+//
+// k_tvb  reads the cell's mean state, its degree-1 slopes (LDF slopes through
+//        the exact table <phi_j,c, xi_a>/<xi_a, xi_a>) and the 2D neighbour
+//        means; per direction converts slopes and mean differences to
+//        primitive variables (dW/dU at the mean), applies the closed-form left
+//        eigenvectors of the Roe & Balsara (1996) normalised 7-wave system plus
+//        the divergence wave (Powell) or the (B_n, psi) GLM pair, limits every
+//        field with the TVB minmod rule (eq. tvb-limiter), and on a trigger
+//        writes R sigma back; any trigger zeroes all weights of degree >= 2 and
+//        (Powell) rebuilds the LDF rows of degree <= 1 from the fixed slopes.
+// k_pos  floors the cell means (recording injected mass and energy), then
+//        tau_rho over all volume and face Gauss points and tau_p from the
+//        density-limited state (eq. tau_rho, tau_press), w <- tau w + (1-tau) w_mean.
+//        Pressures are screened in the working precision and every point whose
+//        pressure may be near or below the floor is re-evaluated in FP64.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstring>
+#include <vector>
+
 #include "dg_limit.cuh"
 
 namespace dgmhd {
 
+namespace {
+
+__device__ __forceinline__ int64_t nb(const Geom& g, int64_t c, int a, int dir) {
+  int ix = (int)(c % g.nx);
+  int64_t r = c / g.nx;
+  int iy = (int)(r % g.ny);
+  int iz = (int)(r / g.ny);
+  if (a == 0) ix = (ix + dir + g.nx) % g.nx;
+  else if (a == 1) iy = (iy + dir + g.ny) % g.ny;
+  else iz = (iz + dir + g.nz) % g.nz;
+  return ((int64_t)iz * g.ny + iy) * g.nx + ix;
+}
+
+__device__ __forceinline__ int lmean_row(const Geom& g, int m) {
+  if (g.glm) return m * g.n;
+  if (m < 5) return m * g.n;
+  if (g.D == 3) return g.ldf0 + (m - 5);
+  return m < 7 ? g.ldf0 + (m - 5) : g.bz2d;
+}
+
+// cell-mean conserved state of cell c (V values)
+template <typename T>
+__device__ __forceinline__ void cell_mean(const Geom& g, const LimTabs& lt, const T* w, const double* wmean,
+                                          int64_t c, double* m) {
+  const int64_t S = g.stride;
+  const int nm = g.glm ? 9 : 8;
+  double raw[9];
+  for (int k = 0; k < nm; ++k) raw[k] = wmean ? wmean[k * S + c] : (double)w[(int64_t)lmean_row(g, k) * S + c];
+  for (int k = 0; k < 9; ++k) m[k] = 0.0;
+  for (int k = 0; k < 5; ++k) m[k] = raw[k];
+  if (g.glm) {
+    for (int k = 5; k < 9; ++k) m[k] = raw[k];
+  } else {
+    for (int j = 0; j < g.D; ++j)
+      for (int cc = 0; cc < g.D; ++cc) m[5 + cc] += raw[5 + j] * lt.ldf_mean0[j * 3 + cc];
+    if (g.D == 2) m[7] = raw[7];
+  }
+}
+
+__device__ __forceinline__ double minmod3(double a, double b, double c) {
+  if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
+  if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
+  return 0.0;
+}
+
+// Characteristic basis at mean state m along axis a (primitive variables).
+struct Eig {
+  double rho, sr, a2, a, cf, cs, af, as, by, bz, S, ch;
+  int n, t1, t2;
+  bool glm;
+};
+
+__device__ __forceinline__ void eig_setup(const double* m, int axis, double gamma, bool glm, double ch, double rel,
+                                          Eig& e) {
+  e.n = axis; e.t1 = (axis + 1) % 3; e.t2 = (axis + 2) % 3;
+  e.glm = glm; e.ch = ch;
+  const double rho = m[0];
+  const double v[3] = {m[1] / rho, m[2] / rho, m[3] / rho};
+  const double B[3] = {m[5], m[6], m[7]};
+  const double p = (gamma - 1.0) * (m[4] - 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) -
+                                    0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
+  e.rho = rho;
+  e.sr = sqrt(rho);
+  e.a2 = gamma * p / rho;
+  e.a = sqrt(e.a2);
+  const double bn = B[e.n], bt1 = B[e.t1], bt2 = B[e.t2];
+  const double bt2sq = bt1 * bt1 + bt2 * bt2;
+  const double b2 = (bn * bn + bt2sq) / rho, cax2 = bn * bn / rho;
+  const double disc = sqrt(fmax((e.a2 + b2) * (e.a2 + b2) - 4.0 * e.a2 * cax2, 0.0));
+  const double cf2 = 0.5 * (e.a2 + b2 + disc);
+  const double cs2 = fmax(0.5 * (e.a2 + b2 - disc), 0.0);
+  e.cf = sqrt(cf2);
+  e.cs = sqrt(cs2);
+  if (cf2 - cs2 > rel * cf2) {
+    e.af = sqrt(fmax(e.a2 - cs2, 0.0) / (cf2 - cs2));
+    e.as = sqrt(fmax(cf2 - e.a2, 0.0) / (cf2 - cs2));
+  } else {
+    e.af = 1.0;
+    e.as = 0.0;
+  }
+  const double bt = sqrt(bt2sq);
+  if (bt > rel * sqrt(rho * cf2)) {
+    e.by = bt1 / bt;
+    e.bz = bt2 / bt;
+  } else {
+    e.by = e.bz = 0.70710678118654752440;
+  }
+  e.S = bn >= 0.0 ? 1.0 : -1.0;
+}
+
+// conserved increment dU -> characteristic amplitudes c (V values)
+__device__ __forceinline__ void to_char(const Eig& e, const double* m, double gamma, const double* dU, double* c,
+                                        int V) {
+  const double rho = m[0];
+  const double v[3] = {m[1] / rho, m[2] / rho, m[3] / rho};
+  const double B[3] = {m[5], m[6], m[7]};
+  // dW = dW/dU dU
+  double dW[9];
+  dW[0] = dU[0];
+  for (int i = 0; i < 3; ++i) dW[1 + i] = (dU[1 + i] - v[i] * dU[0]) / rho;
+  const double g1 = gamma - 1.0;
+  dW[4] = g1 * (0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * dU[0] - (v[0] * dU[1] + v[1] * dU[2] + v[2] * dU[3]) +
+                dU[4] - (B[0] * dU[5] + B[1] * dU[6] + B[2] * dU[7]));
+  for (int i = 5; i < V; ++i) dW[i] = dU[i];
+  const double dr = dW[0], du = dW[1 + e.n], dv = dW[1 + e.t1], dw = dW[1 + e.t2], dp = dW[4];
+  const double dby = dW[5 + e.t1], dbz = dW[5 + e.t2];
+  const double ia2 = 1.0 / e.a2;
+  const double vpar = e.by * dv + e.bz * dw, bpar = e.by * dby + e.bz * dbz;
+  const double vperp = -e.bz * dv + e.by * dw, bperp = -e.bz * dby + e.by * dbz;
+  const double sra = e.sr * e.a;
+  // fast -, alfven -, slow -, entropy, slow +, alfven +, fast +
+  c[0] = 0.5 * ia2 * (-e.af * e.cf * du + e.as * e.cs * e.S * vpar) + 0.5 * (e.af * dp / (e.rho * e.a2) + e.as * bpar / sra);
+  c[6] = 0.5 * ia2 * (e.af * e.cf * du - e.as * e.cs * e.S * vpar) + 0.5 * (e.af * dp / (e.rho * e.a2) + e.as * bpar / sra);
+  c[2] = 0.5 * ia2 * (-e.as * e.cs * du - e.af * e.cf * e.S * vpar) + 0.5 * (e.as * dp / (e.rho * e.a2) - e.af * bpar / sra);
+  c[4] = 0.5 * ia2 * (e.as * e.cs * du + e.af * e.cf * e.S * vpar) + 0.5 * (e.as * dp / (e.rho * e.a2) - e.af * bpar / sra);
+  c[1] = 0.5 * vperp + 0.5 * e.S * bperp / e.sr;
+  c[5] = 0.5 * vperp - 0.5 * e.S * bperp / e.sr;
+  c[3] = dr - dp * ia2;
+  const double dbn = dW[5 + e.n];
+  if (!e.glm) {
+    c[7] = dbn;
+  } else if (e.ch > 0.0) {
+    const double dpsi = dW[8];
+    c[7] = 0.5 * (dbn - dpsi / e.ch);
+    c[8] = 0.5 * (dbn + dpsi / e.ch);
+  } else {  // no c_h set yet: B_n and psi as separate fields
+    c[7] = dbn;
+    c[8] = dW[8];
+  }
+}
+
+// characteristic amplitudes -> conserved increment
+__device__ __forceinline__ void from_char(const Eig& e, const double* m, double gamma, const double* c, double* dU,
+                                          int V) {
+  const double rho = e.rho, sr = e.sr, a2 = e.a2, a = e.a, S = e.S;
+  double dW7[7] = {0, 0, 0, 0, 0, 0, 0};  // rho, u, v, w, p, By, Bz (rotated)
+  auto add = [&](double amp, double r0, double r1, double r2, double r3, double r4, double r5, double r6) {
+    dW7[0] += amp * r0; dW7[1] += amp * r1; dW7[2] += amp * r2; dW7[3] += amp * r3;
+    dW7[4] += amp * r4; dW7[5] += amp * r5; dW7[6] += amp * r6;
+  };
+  add(c[0], rho * e.af, -e.af * e.cf, e.as * e.cs * e.by * S, e.as * e.cs * e.bz * S, rho * e.af * a2,
+      e.as * sr * a * e.by, e.as * sr * a * e.bz);
+  add(c[1], 0, 0, -e.bz, e.by, 0, -e.bz * S * sr, e.by * S * sr);
+  add(c[2], rho * e.as, -e.as * e.cs, -e.af * e.cf * e.by * S, -e.af * e.cf * e.bz * S, rho * e.as * a2,
+      -e.af * sr * a * e.by, -e.af * sr * a * e.bz);
+  add(c[3], 1, 0, 0, 0, 0, 0, 0);
+  add(c[4], rho * e.as, e.as * e.cs, e.af * e.cf * e.by * S, e.af * e.cf * e.bz * S, rho * e.as * a2,
+      -e.af * sr * a * e.by, -e.af * sr * a * e.bz);
+  add(c[5], 0, 0, -e.bz, e.by, 0, e.bz * S * sr, -e.by * S * sr);
+  add(c[6], rho * e.af, e.af * e.cf, -e.as * e.cs * e.by * S, -e.as * e.cs * e.bz * S, rho * e.af * a2,
+      e.as * sr * a * e.by, e.as * sr * a * e.bz);
+  double dW[9];
+  dW[0] = dW7[0];
+  dW[1 + e.n] = dW7[1];
+  dW[1 + e.t1] = dW7[2];
+  dW[1 + e.t2] = dW7[3];
+  dW[4] = dW7[4];
+  dW[5 + e.t1] = dW7[5];
+  dW[5 + e.t2] = dW7[6];
+  if (!e.glm) {
+    dW[5 + e.n] = c[7];
+  } else if (e.ch > 0.0) {
+    dW[5 + e.n] = c[7] + c[8];
+    dW[8] = e.ch * (c[8] - c[7]);
+  } else {
+    dW[5 + e.n] = c[7];
+    dW[8] = c[8];
+  }
+  // dU = dU/dW dW
+  const double v[3] = {m[1] / m[0], m[2] / m[0], m[3] / m[0]};
+  const double B[3] = {m[5], m[6], m[7]};
+  dU[0] = dW[0];
+  for (int i = 0; i < 3; ++i) dU[1 + i] = v[i] * dW[0] + rho * dW[1 + i];
+  dU[4] = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * dW[0] + rho * (v[0] * dW[1] + v[1] * dW[2] + v[2] * dW[3]) +
+          dW[4] / (gamma - 1.0) + B[0] * dW[5] + B[1] * dW[6] + B[2] * dW[7];
+  for (int i = 5; i < V; ++i) dU[i] = dW[i];
+}
+
+template <typename T>
+__global__ void k_tvb(Geom g, LimTabs lt, T* w, double* wmean, uint8_t* troubled, dg_mhd_params p,
+                      const DevScalars* __restrict__ sc) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const int64_t S = g.stride;
+  const int V = g.V;
+  double m[9];
+  cell_mean(g, lt, (const T*)w, wmean, c, m);
+  // degree-1 slopes u_xi[a][v]
+  double sl[3][9];
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 9; ++k) sl[a][k] = 0.0;
+  const int nleg = g.glm ? 9 : 5;
+  for (int a = 0; a < g.D; ++a) {
+    for (int v = 0; v < nleg; ++v) sl[a][v] = (double)w[(int64_t)(v * g.n + lt.deg1[a]) * S + c];
+    if (g.bz2d >= 0) sl[a][7] = (double)w[(int64_t)(g.bz2d + lt.deg1[a]) * S + c];
+  }
+  if (!g.glm) {
+    for (int j = 0; j < g.ndiv; ++j) {
+      if (lt.ldf_deg[j] == 0) continue;
+      const double wj = (double)w[(int64_t)(g.ldf0 + j) * S + c];
+      for (int cc = 0; cc < g.D; ++cc)
+        for (int a = 0; a < g.D; ++a) sl[a][5 + cc] += wj * lt.ldf_slope[(j * 3 + cc) * 3 + a];
+    }
+  }
+  const double thr = p.Mtilde * g.dx;
+  const double ch = g.glm ? sc->ch : 0.0;
+  const double rel = sizeof(T) == 4 ? 1e-6 : 1e-12;
+  bool any = false;
+  double nsl[3][9];
+  for (int a = 0; a < g.D; ++a) {
+    double mp[9], mm[9];
+    cell_mean(g, lt, (const T*)w, wmean, nb(g, c, a, +1), mp);
+    cell_mean(g, lt, (const T*)w, wmean, nb(g, c, a, -1), mm);
+    double dpl[9], dmi[9];
+    for (int k = 0; k < 9; ++k) {
+      dpl[k] = 0.5 * (mp[k] - m[k]);
+      dmi[k] = 0.5 * (m[k] - mm[k]);
+    }
+    Eig e;
+    eig_setup(m, a, g.gamma, g.glm != 0, ch, rel, e);
+    double cx[9], cp[9], cm[9], sg[9];
+    to_char(e, m, g.gamma, sl[a], cx, V);
+    to_char(e, m, g.gamma, dpl, cp, V);
+    to_char(e, m, g.gamma, dmi, cm, V);
+    bool trig = false;
+    for (int k = 0; k < V; ++k) {
+      sg[k] = cx[k];
+      if (fabs(cx[k]) > thr) sg[k] = minmod3(cx[k], p.beta * cp[k], p.beta * cm[k]);
+      if (fabs(sg[k] - cx[k]) > p.tvb_eps) trig = true;
+    }
+    if (trig) {
+      from_char(e, m, g.gamma, sg, nsl[a], V);
+      any = true;
+    } else {
+      for (int k = 0; k < 9; ++k) nsl[a][k] = sl[a][k];
+    }
+  }
+  if (troubled) troubled[c] = any ? 1 : 0;
+  if (!any) return;
+  // Legendre rows: degree-1 slopes, degree >= 2 zeroed
+  for (int r = 0; r < g.nrows; ++r) {
+    const bool ldf = g.ldf0 >= 0 && r >= g.ldf0 && r < g.ldf0 + g.ndiv;
+    if (ldf) continue;
+    int v, l;
+    if (g.bz2d >= 0 && r >= g.bz2d) { v = 7; l = r - g.bz2d; }
+    else { v = r / g.n; l = r % g.n; }
+    const int dg = lt.mdeg[l];
+    if (dg == 0) continue;
+    double val = 0.0;
+    if (dg == 1) {
+      for (int a = 0; a < g.D; ++a)
+        if (lt.deg1[a] == l) val = nsl[a][v];
+    }
+    w[(int64_t)r * S + c] = (T)val;
+  }
+  if (!g.glm) {
+    // LDF slope fix (Sec. 4.2.4) and exact projection onto LDF degree <= 1
+    double Bs[3][3];
+    for (int cc = 0; cc < g.D; ++cc)
+      for (int a = 0; a < g.D; ++a) Bs[cc][a] = nsl[a][5 + cc];
+    double dpos = 0.0, dneg = 0.0, dsum = 0.0;
+    for (int k = 0; k < g.D; ++k) {
+      dsum += Bs[k][k];
+      dpos += fmax(Bs[k][k], 0.0);
+      dneg += fmax(-Bs[k][k], 0.0);
+    }
+    if (dsum > 0.0) {
+      const double f = dneg / dpos;
+      for (int k = 0; k < g.D; ++k)
+        if (Bs[k][k] > 0.0) Bs[k][k] *= f;
+    } else if (dsum < 0.0) {
+      const double f = dpos / dneg;
+      for (int k = 0; k < g.D; ++k)
+        if (Bs[k][k] < 0.0) Bs[k][k] *= f;
+    }
+    for (int j = 0; j < g.ndiv; ++j) {
+      const int64_t i = (int64_t)(g.ldf0 + j) * S + c;
+      if (lt.ldf_deg[j] == 0) continue;  // means kept
+      if (lt.ldf_deg[j] > 1) {
+        w[i] = T(0);
+        continue;
+      }
+      double val = 0.0;
+      for (int cc = 0; cc < g.D; ++cc) {
+        val += lt.ldf_pc[j * 3 + cc] * m[5 + cc];
+        for (int a = 0; a < g.D; ++a) val += lt.ldf_pl[(j * 3 + cc) * 3 + a] * Bs[cc][a];
+      }
+      w[i] = (T)val;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ positivity
+template <typename T>
+__device__ __forceinline__ void point_state(const Geom& g, const Tables<T>& tb, const T* w, const double* mr,
+                                            int64_t c, int pt, double* u, bool dbl) {
+  // pt < Qv: volume point; else face point (f, p)
+  const T* P;
+  const T* Lt;
+  int stride, idx;
+  if (pt < g.Qv) {
+    P = tb.Pv; Lt = tb.Lv; stride = g.Qv; idx = pt;
+  } else {
+    const int fp = pt - g.Qv, f = fp / g.Qf;
+    P = tb.Pf + (size_t)f * g.n * g.Qf;
+    Lt = tb.Lf + (size_t)f * g.ndiv * g.DB * g.Qf;
+    stride = g.Qf; idx = fp % g.Qf;
+  }
+  const int64_t S = g.stride;
+  for (int k = 0; k < 9; ++k) u[k] = 0.0;
+  const int nleg = g.glm ? 9 : 5;
+  for (int v = 0; v < nleg; ++v) {
+    double s = mr[v];  // mode 0 (P_0 = 1) from the authoritative mean
+    if (dbl) {
+      for (int l = 1; l < g.n; ++l) s += (double)w[(int64_t)(v * g.n + l) * S + c] * (double)P[l * stride + idx];
+    } else {
+      T st = T(0);
+      for (int l = 1; l < g.n; ++l) st += w[(int64_t)(v * g.n + l) * S + c] * P[l * stride + idx];
+      s += (double)st;
+    }
+    u[v] = s;
+  }
+  if (!g.glm) {
+    for (int j = 0; j < g.ndiv; ++j) {
+      const double wj = j < g.D ? mr[5 + j] : (double)w[(int64_t)(g.ldf0 + j) * S + c];
+      for (int cc = 0; cc < g.DB; ++cc) u[5 + cc] += wj * (double)Lt[(j * g.DB + cc) * stride + idx];
+    }
+    if (g.bz2d >= 0) {
+      double s = mr[7];
+      for (int l = 1; l < g.n; ++l) s += (double)w[(int64_t)(g.bz2d + l) * S + c] * (double)P[l * stride + idx];
+      u[7] = s;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_pos(Geom g, Tables<T> tb, T* w, double* wmean, dg_mhd_params p, DevScalars* sc) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const int64_t S = g.stride;
+  const int nm = g.glm ? 9 : 8;
+  const bool mix = wmean != nullptr;
+  // raw mean rows (Legendre mode 0 / degree-0 LDF weights)
+  double mr[9];
+  for (int k = 0; k < nm; ++k) mr[k] = mix ? wmean[k * S + c] : (double)w[(int64_t)lmean_row(g, k) * S + c];
+  // physical mean state
+  double m[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int k = 0; k < 5; ++k) m[k] = mr[k];
+  if (g.glm) {
+    for (int k = 5; k < 9; ++k) m[k] = mr[k];
+  } else {
+    for (int j = 0; j < g.D; ++j)
+      for (int cc = 0; cc < g.DB; ++cc) m[5 + cc] += mr[5 + j] * (double)tb.L0[j * g.DB + cc];
+    if (g.bz2d >= 0) m[7] = mr[7];
+  }
+  const double gm1 = g.gamma - 1.0;
+  double vol = 1.0;
+  for (int a = 0; a < g.D; ++a) vol *= g.dx;
+  bool changed_mean = false;
+  if (m[0] < p.eps_rho) {
+    atomicAdd(&sc->inj_mass, (p.eps_rho - m[0]) * vol);
+    m[0] = mr[0] = p.eps_rho;
+    changed_mean = true;
+  }
+  auto pres = [&](const double* u) {
+    return gm1 * (u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0] -
+                  0.5 * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]));
+  };
+  const double pm = pres(m);
+  if (pm < p.eps_p) {
+    const double dE = (p.eps_p - pm) / gm1;
+    atomicAdd(&sc->inj_energy, dE * vol);
+    m[4] += dE;
+    mr[4] += dE;
+    changed_mean = true;
+  }
+  if (changed_mean) {
+    atomicOr(&sc->floor_used, 1);
+    for (int k = 0; k < nm; ++k) {
+      const int r = lmean_row(g, k);
+      if (mix) wmean[k * S + c] = mr[k];
+      w[(int64_t)r * S + c] = (T)mr[k];
+    }
+  }
+  const int npt = g.Qv + 2 * g.D * g.Qf;
+  const bool dbl = sizeof(T) == 8;
+  const double pmean = pres(m);
+  // tau_rho
+  double tau = 1.0;
+  for (int pt = 0; pt < npt; ++pt) {
+    double u[9];
+    point_state(g, tb, (const T*)w, mr, c, pt, u, dbl);
+    const double rq = u[0];
+    if (rq < p.eps_rho) tau = fmin(tau, (m[0] - p.eps_rho) / (m[0] - rq));
+  }
+  tau = fmax(tau, 0.0);
+  // tau_p from the density-limited state u' = m + tau (u - m)
+  double taup = 1.0;
+  const double screen = sizeof(T) == 4 ? 1e-4 : 0.0;
+  for (int pt = 0; pt < npt; ++pt) {
+    double u[9];
+    point_state(g, tb, (const T*)w, mr, c, pt, u, dbl);
+    for (int k = 0; k < 9; ++k) u[k] = m[k] + tau * (u[k] - m[k]);
+    double pq = pres(u);
+    if (!dbl && pq < p.eps_p + screen * fabs(u[4])) {
+      // FP64 recovery of this point's pressure (E - kinetic - magnetic cancels)
+      point_state(g, tb, (const T*)w, mr, c, pt, u, true);
+      for (int k = 0; k < 9; ++k) u[k] = m[k] + tau * (u[k] - m[k]);
+      pq = pres(u);
+    }
+    if (pq < p.eps_p) taup = fmin(taup, (pmean - p.eps_p) / (pmean - pq));
+  }
+  taup = fmax(taup, 0.0);
+  const double t = tau * taup;
+  if (t >= 1.0) return;
+  // scale every non-mean row by tau
+  for (int r = 0; r < g.nrows; ++r) {
+    bool mean = false;
+    for (int k = 0; k < nm; ++k)
+      if (lmean_row(g, k) == r) mean = true;
+    if (mean) continue;
+    const int64_t i = (int64_t)r * S + c;
+    w[i] = (T)(t * (double)w[i]);
+  }
+}
+
+}  // namespace
+
+int upload_limiter_tables(Ctx& c) {
+  const Basis& B = *c.hb;
+  const Geom& g = c.g;
+  LimTabs lt;
+  std::memset(&lt, 0, sizeof(lt));
+  for (int a = 0; a < g.D; ++a)
+    for (int l = 0; l < g.n; ++l) {
+      const auto& k = B.modes[l];
+      if (k[0] + k[1] + k[2] == 1 && k[a] == 1) lt.deg1[a] = l;
+    }
+  for (int l = 0; l < g.n && l < 64; ++l) lt.mdeg[l] = B.modes[l][0] + B.modes[l][1] + B.modes[l][2];
+  for (int j = 0; j < g.ndiv && j < 64; ++j) {
+    lt.ldf_deg[j] = B.ldf_deg[j];
+    // mean of each component (degree 0 rows only are non-zero)
+    for (int cc = 0; cc < g.D; ++cc) {
+      double z[3] = {0, 0, 0};
+      lt.ldf_mean0[j * 3 + cc] = B.ldf_deg[j] == 0 ? B.eval(B.ldf[j][cc], z) : 0.0;
+    }
+  }
+  // slope and projection tables by exact monomial integration
+  const auto& ms = B.ms;
+  auto integ = [&](const std::vector<double>& poly, int axis) {
+    // int poly * xi_axis (axis < 0: int poly) over [-1,1]^D
+    double s = 0.0;
+    for (size_t i = 0; i < ms.exps.size(); ++i) {
+      if (poly[i] == 0.0) continue;
+      double t = poly[i];
+      for (int ax = 0; ax < g.D; ++ax) {
+        const int k = ms.exps[i][ax] + (ax == axis ? 1 : 0);
+        t *= (k & 1) ? 0.0 : 2.0 / (k + 1.0);
+      }
+      s += t;
+    }
+    return s;
+  };
+  double xi2 = 1.0;
+  for (int ax = 0; ax < g.D; ++ax) xi2 *= ax == 0 ? 2.0 / 3.0 : 2.0;
+  for (int j = 0; j < g.ndiv && j < 64; ++j)
+    for (int cc = 0; cc < g.D; ++cc) {
+      const double Mj = B.ldf_mass[j];
+      lt.ldf_pc[j * 3 + cc] = integ(B.ldf[j][cc], -1) / Mj;
+      for (int a = 0; a < g.D; ++a) {
+        const double ia = integ(B.ldf[j][cc], a);
+        lt.ldf_slope[(j * 3 + cc) * 3 + a] = ia / xi2;
+        lt.ldf_pl[(j * 3 + cc) * 3 + a] = ia / Mj;
+      }
+    }
+  c.lim = lt;
+  return DG_OK;
+}
+
 int run_limiter(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t st) {
-  (void)c; (void)w; (void)wmean; (void)troubled; (void)st;
-  return DG_E_UNSUPPORTED;
+  const Geom& g = c.g;
+  const unsigned nb = (unsigned)((g.ncell + 127) / 128);
+  if (c.p.limiter == DG_LIMIT_TVB || c.p.limiter == DG_LIMIT_MLP) {
+    c.prof.begin(3, st);
+    if (c.p.precision == DG_PREC_FP32MIX)
+      k_tvb<float><<<nb, 128, 0, st>>>(g, c.lim, (float*)w, wmean, troubled, c.p, c.sc);
+    else
+      k_tvb<double><<<nb, 128, 0, st>>>(g, c.lim, (double*)w, nullptr, troubled, c.p, c.sc);
+    c.prof.end(3, st);
+  }
+  if (c.p.positivity) {
+    c.prof.begin(3, st);
+    if (c.p.precision == DG_PREC_FP32MIX)
+      k_pos<float><<<nb, 128, 0, st>>>(g, c.t32, (float*)w, wmean, c.p, c.sc);
+    else
+      k_pos<double><<<nb, 128, 0, st>>>(g, c.t64, (double*)w, nullptr, c.p, c.sc);
+    c.prof.end(3, st);
+  }
+  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
 }
 
 }  // namespace dgmhd
