@@ -23,7 +23,8 @@ EXPORTS = [
     "dg_mhd_default_params", "dg_mhd_init", "dg_mhd_state_layout", "dg_mhd_project", "dg_mhd_set_glm",
     "dg_mhd_rhs", "dg_mhd_limit", "dg_mhd_dt", "dg_mhd_step", "dg_mhd_last_dt", "dg_mhd_status",
     "dg_mhd_profile", "dg_mhd_profile_read", "dg_mhd_launch_count", "dg_mhd_rhs_noalloc", "dg_mhd_destroy",
-    "dg_mhd_strerror",
+    "dg_mhd_strerror", "dg_mhd_mlp_features", "dg_mhd_mlp_set_weights", "dg_mhd_mlp_infer", "dg_mhd_mlp_loss_grad",
+    "dg_mhd_mlp_train",
 ]
 KIND_FACE, KIND_CELL, KIND_DT, KIND_LIMIT, KIND_PROJECT = range(5)
 
@@ -70,6 +71,14 @@ def lib():
     L.dg_mhd_launch_count.restype = ctypes.c_int64
     L.dg_mhd_rhs_noalloc.argtypes = [ctypes.POINTER(MeshDesc), ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.POINTER(Params), ctypes.c_double, ctypes.c_double, vp, vp, vp]
+    L.dg_mhd_mlp_features.argtypes = [vp, vp, dp, vp, ctypes.c_int, vp]
+    L.dg_mhd_mlp_set_weights.argtypes = [vp, vp, ctypes.c_int, ctypes.c_float]
+    L.dg_mhd_mlp_infer.argtypes = [vp, vp, dp, vp, vp, vp]
+    L.dg_mhd_mlp_loss_grad.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64, ctypes.c_int, vp, ctypes.c_float, vp,
+                                       vp, vp]
+    L.dg_mhd_mlp_train.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64, ctypes.c_int, vp, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_uint64,
+                                   ctypes.POINTER(ctypes.c_double), vp]
     L.dg_mhd_destroy.argtypes = [vp]
     L.dg_mhd_destroy.restype = None
     L.dg_mhd_strerror.argtypes = [ctypes.c_int]
@@ -120,6 +129,23 @@ def rhs_noalloc(dim, n, degree, divb, w, out, gamma=5.0 / 3.0, box_len=1.0, c_h=
     _check(lib().dg_mhd_rhs_noalloc(ctypes.byref(m), degree, DG_DIVB_GLM if divb == "glm" else DG_DIVB_POWELL,
                                     gamma, None, c_h, damping_rate, _ptr(w), _ptr(out), _stream()),
            "dg_mhd_rhs_noalloc")
+
+
+def mlp_loss_grad(X, y, theta, nin, pos_weight=1.0):
+    """Loss and gradient of the indicator network on the device (FP32)."""
+    import torch
+    grad = torch.zeros_like(theta)
+    loss = torch.zeros(1, dtype=torch.float64, device=theta.device)
+    _check(lib().dg_mhd_mlp_loss_grad(_ptr(X), X.shape[1], _ptr(y), X.shape[0], nin, _ptr(theta), pos_weight,
+                                      _ptr(grad), _ptr(loss), _stream()), "dg_mhd_mlp_loss_grad")
+    return float(loss.item()), grad
+
+
+def mlp_train(X, y, theta, nin, epochs, batch, lr=1e-3, pos_weight=1.0, seed=0):
+    last = ctypes.c_double()
+    _check(lib().dg_mhd_mlp_train(_ptr(X), X.shape[1], _ptr(y), X.shape[0], nin, _ptr(theta), epochs, batch, lr,
+                                  pos_weight, seed, ctypes.byref(last), _stream()), "dg_mhd_mlp_train")
+    return last.value
 
 
 def default_params(**kw) -> Params:
@@ -212,6 +238,22 @@ class Solver:
 
     def launch_count(self):
         return lib().dg_mhd_launch_count(self.h)
+
+    # --------------------------------------------------------- learned indicator
+    def n_features(self):
+        return 8 * {2: {0: 1, 1: 3, 2: 6, 3: 10}, 3: {0: 1, 1: 4, 2: 10, 3: 20}}[self.dim][self.degree] + 2 * self.dim
+
+    def mlp_features(self, w, wmean, X, ldx):
+        _check(lib().dg_mhd_mlp_features(self.h, _ptr(w), _ptr(wmean), _ptr(X), ldx, _stream()),
+               "dg_mhd_mlp_features")
+
+    def mlp_set_weights(self, theta, threshold=0.5):
+        _check(lib().dg_mhd_mlp_set_weights(self.h, _ptr(theta), self.n_features(), threshold),
+               "dg_mhd_mlp_set_weights")
+
+    def mlp_infer(self, w, wmean=None, flags=None, prob=None):
+        _check(lib().dg_mhd_mlp_infer(self.h, _ptr(w), _ptr(wmean), _ptr(flags), _ptr(prob), _stream()),
+               "dg_mhd_mlp_infer")
 
     def status(self, sync=True):
         return lib().dg_mhd_status(self.h, 1 if sync else 0)

@@ -13,6 +13,7 @@
 #include "dg_fast.cuh"
 #include "dg_kernels.cuh"
 #include "dg_limit.cuh"
+#include "dg_mlp.cuh"
 
 using namespace dgmhd;
 
@@ -370,7 +371,7 @@ void dg_mhd_destroy(dg_mhd_ctx* ctx) {
   free_tables(c.t32);
   void* ptrs[] = {c.sc, c.face_buf, c.face_buf32, c.stage_buf[0], c.stage_buf[1], c.stage_buf[2],
                   c.stage_mean[0], c.stage_mean[1], c.stage_mean[2], c.cellscratch, c.proj_tab, c.proj_w,
-                  c.troubled};
+                  c.troubled, c.mlp_w1, c.mlp_w2, c.mlp_bias};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c.hb;
@@ -466,6 +467,7 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
     return DG_E_CUDA;
   }
   upload_limiter_tables(c);
+  mlp_build_tables(c);
   // specialised GLM kernels for uniform 3D meshes
   if (g.glm && g.D == 3 && !prm.generic_kernels) {
     if (fp32(c)) {
@@ -682,6 +684,48 @@ int dg_mhd_step(dg_mhd_ctx* ctx, void* w, double* wmean, const double* dt_dev, v
   // u^{n+1} = 1/3 u + 2/3 (u2 + dt L(u2))
   if ((e = operator_pass(c, s2, m2, w, wmean, w, wmean, 1.0 / 3.0, 2.0 / 3.0, 1, st))) return e;
   return DG_OK;
+}
+
+int dg_mhd_mlp_features(dg_mhd_ctx* ctx, const void* w, const double* wmean, float* X, int ldx, void* stream) {
+  if (!ctx || !w || !X) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  if (fp32(c) && !wmean) return DG_E_ARG;
+  if (ldx < 8 * c.g.n + 2 * c.g.D) return DG_E_ARG;
+  c.prof.launches[3] += 1;
+  return mlp_features_launch(c, w, wmean, X, ldx, S(stream));
+}
+
+int dg_mhd_mlp_set_weights(dg_mhd_ctx* ctx, const float* theta, int nin, float threshold) {
+  if (!ctx || !theta || !(threshold > 0.f && threshold < 1.f)) return DG_E_ARG;
+  return mlp_set_weights(ctx->c, theta, nin, threshold);
+}
+
+int dg_mhd_mlp_infer(dg_mhd_ctx* ctx, const void* w, const double* wmean, uint8_t* flags, float* prob,
+                     void* stream) {
+  if (!ctx || !w) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  if (fp32(c) && !wmean) return DG_E_ARG;
+  c.prof.launches[3] += 1;
+  return mlp_infer_launch(c, w, wmean, flags, prob, S(stream));
+}
+
+int dg_mhd_mlp_loss_grad(const float* X, int ldx, const uint8_t* y, int64_t n, int nin, const float* theta,
+                         float pos_weight, float* grad, double* loss, void* stream) {
+  if (!X || !y || !theta || !grad || n < 1 || nin < 1 || ldx < nin || n > (int64_t)1 << 30) return DG_E_ARG;
+  void* scratch = nullptr;
+  if (cudaMalloc(&scratch, mlp_scratch_bytes((int)n)) != cudaSuccess) return DG_E_CUDA;
+  cudaStream_t st = S(stream);
+  if (loss) cudaMemsetAsync(loss, 0, sizeof(double), st);
+  int e = mlp_loss_grad_dev(X, ldx, y, nullptr, 0, (int)n, nin, theta, grad, loss, pos_weight, (float)n, scratch, st);
+  cudaStreamSynchronize(st);
+  cudaFree(scratch);
+  return e;
+}
+
+int dg_mhd_mlp_train(const float* X, int ldx, const uint8_t* y, int64_t n, int nin, float* theta, int epochs,
+                     int batch, float lr, float pos_weight, uint64_t seed, double* last_loss, void* stream) {
+  if (!X || !y || !theta || n < batch || batch < 1 || epochs < 1 || ldx < nin) return DG_E_ARG;
+  return mlp_train_dev(X, ldx, y, n, nin, theta, epochs, batch, lr, pos_weight, seed, last_loss, S(stream));
 }
 
 int dg_mhd_status(dg_mhd_ctx* ctx, int sync) {

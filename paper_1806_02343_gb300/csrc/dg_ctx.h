@@ -91,9 +91,23 @@ struct Prof {
   void release();
 };
 
+// Learned indicator: exact LDF -> per-component Legendre map
+// l2l[(j*3 + c)*MLP_MAXN + l] = <phi_j,c, P_l> / M_l.
+constexpr int MLP_MAXN = 20;
+constexpr int MLP_MAXIN = 176;
+struct MlpTabs {
+  float l2l[64 * 3 * MLP_MAXN];
+};
+
 struct Ctx {
   Prof prof;
   LimTabs lim;
+  MlpTabs mlp;
+  void* mlp_w1 = nullptr;     // bf16 [64][kp]
+  void* mlp_w2 = nullptr;     // bf16 [64][64]
+  float* mlp_bias = nullptr;  // b1, b2, w3, b3
+  int mlp_kp = 0;
+  float mlp_thresh = 0.5f;
   Geom g;
   dg_mhd_params p;
   Basis* hb = nullptr;  // host basis (kept for projection tables)

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "dg_limit.cuh"
+#include "dg_mlp.cuh"
 
 namespace dgmhd {
 
@@ -204,10 +205,14 @@ __device__ __forceinline__ void from_char(const Eig& e, const double* m, double 
 }
 
 template <typename T>
-__global__ void k_tvb(Geom g, LimTabs lt, T* w, double* wmean, uint8_t* troubled, dg_mhd_params p,
-                      const DevScalars* __restrict__ sc) {
+__global__ void k_tvb(Geom g, LimTabs lt, T* w, double* wmean, uint8_t* troubled, const uint8_t* __restrict__ gate,
+                      dg_mhd_params p, const DevScalars* __restrict__ sc) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
+  if (gate && !gate[c]) {  // learned detection: cells not flagged skip the TVB procedure
+    if (troubled) troubled[c] = 0;
+    return;
+  }
   const int64_t S = g.stride;
   const int V = g.V;
   double m[9];
@@ -508,11 +513,19 @@ int run_limiter(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t 
   const Geom& g = c.g;
   const unsigned nb = (unsigned)((g.ncell + 127) / 128);
   if (c.p.limiter == DG_LIMIT_TVB || c.p.limiter == DG_LIMIT_MLP) {
+    const uint8_t* gate = nullptr;
     c.prof.begin(3, st);
+    if (c.p.limiter == DG_LIMIT_MLP) {
+      if (!c.mlp_w1) return DG_E_ARG;  // no weights set
+      const int e = mlp_infer_launch(c, w, wmean, c.troubled, nullptr, st);
+      if (e) return e;
+      gate = c.troubled;
+      c.prof.launches[3] += 1;
+    }
     if (c.p.precision == DG_PREC_FP32MIX)
-      k_tvb<float><<<nb, 128, 0, st>>>(g, c.lim, (float*)w, wmean, troubled, c.p, c.sc);
+      k_tvb<float><<<nb, 128, 0, st>>>(g, c.lim, (float*)w, wmean, troubled, gate, c.p, c.sc);
     else
-      k_tvb<double><<<nb, 128, 0, st>>>(g, c.lim, (double*)w, nullptr, troubled, c.p, c.sc);
+      k_tvb<double><<<nb, 128, 0, st>>>(g, c.lim, (double*)w, nullptr, troubled, gate, c.p, c.sc);
     c.prof.end(3, st);
   }
   if (c.p.positivity) {

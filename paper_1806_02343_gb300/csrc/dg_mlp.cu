@@ -1,0 +1,555 @@
+// Learned troubled-cell indicator: features, BF16 tensor-core inference fused
+// with the feature pass, and FP32 training kernels (forward, backward, Adam).
+//
+// Detection is its own step of the limiter (Sec. 4.2: first detect troubled
+// cells, then limit them); this network replaces the TVB detection and only the
+// cells it flags go through the characteristic TVB procedure.
+//
+// Features of a cell (nin = 8 n(d) + 2D): Legendre coefficients of the 8 MHD
+// variables (LDF B mapped exactly to per-component Legendre coefficients), each
+// variable divided by s_v = |mean_v| + max_nb |mean_nb,v - mean_v| + 1e-12,
+// then rho_nb / rho - 1 for the neighbours -x, +x, -y, +y (, -z, +z).
+// Network: nin -> 64 -> 64 -> 1, ReLU, sigmoid. Weights (flat FP32):
+// W1[64][nin], b1[64], W2[64][64], b2[64], w3[64], b3.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "dg_mlp.cuh"
+
+namespace dgmhd {
+
+namespace {
+
+constexpr int HID = 64;
+
+__device__ __forceinline__ int64_t nbc(const Geom& g, int64_t c, int a, int dir) {
+  int ix = (int)(c % g.nx);
+  int64_t r = c / g.nx;
+  int iy = (int)(r % g.ny);
+  int iz = (int)(r / g.ny);
+  if (a == 0) ix = (ix + dir + g.nx) % g.nx;
+  else if (a == 1) iy = (iy + dir + g.ny) % g.ny;
+  else iz = (iz + dir + g.nz) % g.nz;
+  return ((int64_t)iz * g.ny + iy) * g.nx + ix;
+}
+
+__device__ __forceinline__ int mrow(const Geom& g, int m) {
+  if (g.glm) return m * g.n;
+  if (m < 5) return m * g.n;
+  if (g.D == 3) return g.ldf0 + (m - 5);
+  return m < 7 ? g.ldf0 + (m - 5) : g.bz2d;
+}
+
+// physical cell means of the 8 MHD variables
+template <typename T>
+__device__ __forceinline__ void means8(const Geom& g, const MlpTabs& mt, const T* w, const double* wmean, int64_t c,
+                                       float* m) {
+  const int64_t S = g.stride;
+  float raw[8];
+  for (int k = 0; k < 8; ++k) raw[k] = wmean ? (float)wmean[k * S + c] : (float)w[(int64_t)mrow(g, k) * S + c];
+  for (int k = 0; k < 5; ++k) m[k] = raw[k];
+  if (g.glm) {
+    for (int k = 5; k < 8; ++k) m[k] = raw[k];
+  } else {
+    m[5] = m[6] = m[7] = 0.f;
+    for (int j = 0; j < g.D; ++j)
+      for (int cc = 0; cc < g.D; ++cc) m[5 + cc] += raw[5 + j] * mt.l2l[(j * 3 + cc) * MLP_MAXN + 0];
+    if (g.D == 2) m[7] = raw[7];
+  }
+}
+
+// features of cell c into x[0..nin)
+template <typename T>
+__device__ __forceinline__ void cell_features(const Geom& g, const MlpTabs& mt, const T* w, const double* wmean,
+                                              int64_t c, float* x) {
+  const int64_t S = g.stride;
+  const int n = g.n;
+  float m[8];
+  means8(g, mt, w, wmean, c, m);
+  float dmax[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  float ratio[6];
+  for (int a = 0; a < g.D; ++a)
+    for (int s = 0; s < 2; ++s) {
+      float mn[8];
+      means8(g, mt, w, wmean, nbc(g, c, a, s ? 1 : -1), mn);
+      for (int k = 0; k < 8; ++k) dmax[k] = fmaxf(dmax[k], fabsf(mn[k] - m[k]));
+      ratio[2 * a + s] = mn[0] / m[0] - 1.f;
+    }
+  float inv[8];
+  for (int k = 0; k < 8; ++k) inv[k] = 1.f / (fabsf(m[k]) + dmax[k] + 1e-12f);
+  const int nleg = g.glm ? 8 : 5;
+  for (int v = 0; v < nleg; ++v)
+    for (int l = 0; l < n; ++l) {
+      const float a = (l == 0) ? m[v] : (float)w[(int64_t)(v * n + l) * S + c];
+      x[v * n + l] = a * inv[v];
+    }
+  if (!g.glm) {
+    for (int cc = 0; cc < g.D; ++cc)
+      for (int l = 0; l < n; ++l) x[(5 + cc) * n + l] = 0.f;
+    for (int j = 0; j < g.ndiv; ++j) {
+      const float wj = j < g.D ? (wmean ? (float)wmean[(5 + j) * S + c] : (float)w[(int64_t)(g.ldf0 + j) * S + c])
+                               : (float)w[(int64_t)(g.ldf0 + j) * S + c];
+      for (int cc = 0; cc < g.D; ++cc)
+        for (int l = 0; l < n; ++l) x[(5 + cc) * n + l] += wj * mt.l2l[(j * 3 + cc) * MLP_MAXN + l] * inv[5 + cc];
+    }
+    if (g.D == 2) {
+      for (int l = 0; l < n; ++l) {
+        const float a = (l == 0) ? m[7] : (float)w[(int64_t)(g.bz2d + l) * S + c];
+        x[7 * n + l] = a * inv[7];
+      }
+    }
+  }
+  for (int k = 0; k < 2 * g.D; ++k) x[8 * n + k] = ratio[k];
+}
+
+template <typename T>
+__global__ void k_features(Geom g, MlpTabs mt, const T* __restrict__ w, const double* __restrict__ wmean,
+                           float* __restrict__ X, int ldx) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  float x[MLP_MAXIN];
+  cell_features(g, mt, w, wmean, c, x);
+  const int nin = 8 * g.n + 2 * g.D;
+  for (int k = 0; k < ldx; ++k) X[c * ldx + k] = k < nin ? x[k] : 0.f;
+}
+
+// ---------------------------------------------------------------- inference (BF16 mma.sync)
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// One warp infers 32 cells (two m16 tiles); KP = padded input width (multiple of 16).
+// Shared layout: W1s[64][KP+8] bf16, W2s[64][72] bf16, Xs[warps][32][KP+8] bf16, biases f32.
+template <typename T, int KP>
+__global__ void __launch_bounds__(128) k_mlp_infer(Geom g, MlpTabs mt, const T* __restrict__ w,
+                                                   const double* __restrict__ wmean,
+                                                   const __nv_bfloat16* __restrict__ W1,
+                                                   const __nv_bfloat16* __restrict__ W2,
+                                                   const float* __restrict__ bias, float thresh,
+                                                   uint8_t* __restrict__ flag, float* __restrict__ prob) {
+  constexpr int LD1 = KP + 8, LD2 = HID + 8;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(smraw);
+  __nv_bfloat16* W2s = W1s + HID * LD1;
+  __nv_bfloat16* Xs = W2s + HID * LD2;
+  float* bs = reinterpret_cast<float*>(Xs + 4 * 32 * LD1);  // b1[64], b2[64], w3[64], b3
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  for (int i = t; i < HID * KP; i += 128) W1s[(i / KP) * LD1 + i % KP] = W1[i];
+  for (int i = t; i < HID * HID; i += 128) W2s[(i / HID) * LD2 + i % HID] = W2[i];
+  for (int i = t; i < 3 * HID + 1; i += 128) bs[i] = bias[i];
+  // features of this thread's cell
+  const int64_t c = (int64_t)blockIdx.x * 128 + t;
+  const bool live = c < g.ncell;
+  {
+    float x[MLP_MAXIN];
+    const int nin = 8 * g.n + 2 * g.D;
+    if (live) cell_features(g, mt, w, wmean, c, x);
+    __nv_bfloat16* xr = Xs + (warp * 32 + lane) * LD1;
+    for (int k = 0; k < KP; ++k) xr[k] = __float2bfloat16_rn(live && k < nin ? x[k] : 0.f);
+  }
+  __syncthreads();
+  const int gq = lane >> 2, tq = lane & 3;
+  for (int tile = 0; tile < 2; ++tile) {
+    const __nv_bfloat16* Xt = Xs + (warp * 32 + tile * 16) * LD1;
+    float h1[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      h1[j][0] = bs[8 * j + 2 * tq];
+      h1[j][1] = bs[8 * j + 2 * tq + 1];
+      h1[j][2] = bs[8 * j + 2 * tq];
+      h1[j][3] = bs[8 * j + 2 * tq + 1];
+    }
+#pragma unroll
+    for (int kk = 0; kk < KP / 16; ++kk) {
+      uint32_t a[4];
+      a[0] = *reinterpret_cast<const uint32_t*>(Xt + gq * LD1 + 16 * kk + 2 * tq);
+      a[1] = *reinterpret_cast<const uint32_t*>(Xt + (gq + 8) * LD1 + 16 * kk + 2 * tq);
+      a[2] = *reinterpret_cast<const uint32_t*>(Xt + gq * LD1 + 16 * kk + 8 + 2 * tq);
+      a[3] = *reinterpret_cast<const uint32_t*>(Xt + (gq + 8) * LD1 + 16 * kk + 8 + 2 * tq);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        uint32_t b[2];
+        b[0] = *reinterpret_cast<const uint32_t*>(W1s + (8 * j + gq) * LD1 + 16 * kk + 2 * tq);
+        b[1] = *reinterpret_cast<const uint32_t*>(W1s + (8 * j + gq) * LD1 + 16 * kk + 8 + 2 * tq);
+        mma_bf16(h1[j], a, b);
+      }
+    }
+    // ReLU; accumulator tiles 2kk, 2kk+1 form the A fragment of layer 2's k-step kk
+    float h2[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      h2[j][0] = bs[HID + 8 * j + 2 * tq];
+      h2[j][1] = bs[HID + 8 * j + 2 * tq + 1];
+      h2[j][2] = bs[HID + 8 * j + 2 * tq];
+      h2[j][3] = bs[HID + 8 * j + 2 * tq + 1];
+    }
+#pragma unroll
+    for (int kk = 0; kk < HID / 16; ++kk) {
+      uint32_t a[4];
+      a[0] = pack_bf16(fmaxf(h1[2 * kk][0], 0.f), fmaxf(h1[2 * kk][1], 0.f));
+      a[1] = pack_bf16(fmaxf(h1[2 * kk][2], 0.f), fmaxf(h1[2 * kk][3], 0.f));
+      a[2] = pack_bf16(fmaxf(h1[2 * kk + 1][0], 0.f), fmaxf(h1[2 * kk + 1][1], 0.f));
+      a[3] = pack_bf16(fmaxf(h1[2 * kk + 1][2], 0.f), fmaxf(h1[2 * kk + 1][3], 0.f));
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        uint32_t b[2];
+        b[0] = *reinterpret_cast<const uint32_t*>(W2s + (8 * j + gq) * LD2 + 16 * kk + 2 * tq);
+        b[1] = *reinterpret_cast<const uint32_t*>(W2s + (8 * j + gq) * LD2 + 16 * kk + 8 + 2 * tq);
+        mma_bf16(h2[j], a, b);
+      }
+    }
+    // output layer: rows gq and gq+8 of the tile, reduced over the quad
+    float o0 = 0.f, o1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float w0 = bs[2 * HID + 8 * j + 2 * tq], w1 = bs[2 * HID + 8 * j + 2 * tq + 1];
+      o0 += fmaxf(h2[j][0], 0.f) * w0 + fmaxf(h2[j][1], 0.f) * w1;
+      o1 += fmaxf(h2[j][2], 0.f) * w0 + fmaxf(h2[j][3], 0.f) * w1;
+    }
+    o0 += __shfl_xor_sync(0xffffffffu, o0, 1);
+    o0 += __shfl_xor_sync(0xffffffffu, o0, 2);
+    o1 += __shfl_xor_sync(0xffffffffu, o1, 1);
+    o1 += __shfl_xor_sync(0xffffffffu, o1, 2);
+    if (tq == 0) {
+      const float b3 = bs[3 * HID];
+      const int64_t c0 = (int64_t)blockIdx.x * 128 + warp * 32 + tile * 16 + gq;
+      const float p0 = 1.f / (1.f + __expf(-(o0 + b3)));
+      const float p1 = 1.f / (1.f + __expf(-(o1 + b3)));
+      if (c0 < g.ncell) {
+        if (flag) flag[c0] = p0 > thresh ? 1 : 0;
+        if (prob) prob[c0] = p0;
+      }
+      if (c0 + 8 < g.ncell) {
+        if (flag) flag[c0 + 8] = p1 > thresh ? 1 : 0;
+        if (prob) prob[c0 + 8] = p1;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- training (FP32)
+// Z[b][o] = sum_k A[idx(b)][k] W[o][k] + bias[o] (A rows gathered through perm if given)
+__global__ void k_dense(const float* __restrict__ A, int lda, const int64_t* __restrict__ perm, int64_t off,
+                        const float* __restrict__ W, const float* __restrict__ bias, float* __restrict__ Z, int nb,
+                        int nin, int nout, int relu_in) {
+  const int o = threadIdx.x % nout;
+  const int b = blockIdx.x * (blockDim.x / nout) + threadIdx.x / nout;
+  if (b >= nb || threadIdx.x >= (blockDim.x / nout) * nout) return;
+  const int64_t row = perm ? perm[off + b] : off + b;
+  const float* a = A + row * lda;
+  float s = bias[o];
+  for (int k = 0; k < nin; ++k) {
+    float x = a[k];
+    if (relu_in) x = fmaxf(x, 0.f);
+    s += x * W[o * nin + k];
+  }
+  Z[(int64_t)b * nout + o] = s;
+}
+
+// output layer, loss and delta3 = (p - y) * weight / n
+__global__ void k_out(const float* __restrict__ Z2, const float* __restrict__ w3, float b3,
+                      const uint8_t* __restrict__ y, const int64_t* __restrict__ perm, int64_t off, int nb,
+                      float pos_weight, float inv_n, float* __restrict__ d3, double* __restrict__ loss) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  float z = b3;
+  for (int k = 0; k < HID; ++k) z += fmaxf(Z2[(int64_t)b * HID + k], 0.f) * w3[k];
+  const float p = 1.f / (1.f + expf(-z));
+  const int64_t row = perm ? perm[off + b] : off + b;
+  const float yy = y[row] ? 1.f : 0.f;
+  // weighted BCE: -(pw y log p + (1-y) log(1-p)); dL/dz = pw y (p - 1) + (1 - y) p
+  d3[b] = (pos_weight * yy * (p - 1.f) + (1.f - yy) * p) * inv_n;
+  if (loss) {
+    const double l = -(pos_weight * yy * log((double)p + 1e-12) + (1.0 - yy) * log(1.0 - (double)p + 1e-12));
+    atomicAdd(loss, l * (double)inv_n);
+  }
+}
+
+// delta2[b][k] = d3[b] * w3[k] * (Z2 > 0)
+__global__ void k_back2(const float* __restrict__ d3, const float* __restrict__ w3, const float* __restrict__ Z2,
+                        float* __restrict__ d2, int nb) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)nb * HID) return;
+  const int k = (int)(i % HID);
+  const int64_t b = i / HID;
+  d2[i] = Z2[i] > 0.f ? d3[b] * w3[k] : 0.f;
+}
+
+// delta1[b][k] = sum_o d2[b][o] W2[o][k] * (Z1 > 0)
+__global__ void k_back1(const float* __restrict__ d2, const float* __restrict__ W2, const float* __restrict__ Z1,
+                        float* __restrict__ d1, int nb) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)nb * HID) return;
+  const int k = (int)(i % HID);
+  const int64_t b = i / HID;
+  float s = 0.f;
+  for (int o = 0; o < HID; ++o) s += d2[b * HID + o] * W2[o * HID + k];
+  d1[i] = Z1[i] > 0.f ? s : 0.f;
+}
+
+// gW[o][k] = sum_b delta[b][o] act(A[row(b)][k]); gb[o] = sum_b delta[b][o] (fixed order)
+__global__ void k_wgrad(const float* __restrict__ delta, int nout, const float* __restrict__ A, int lda,
+                        const int64_t* __restrict__ perm, int64_t off, int nin, int relu_in, int nb,
+                        float* __restrict__ gW, float* __restrict__ gb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nout * (nin + 1)) return;
+  const int o = i / (nin + 1), k = i % (nin + 1);
+  float s = 0.f;
+  for (int b = 0; b < nb; ++b) {
+    const float d = delta[(int64_t)b * nout + o];
+    if (k == nin) {
+      s += d;
+    } else {
+      const int64_t row = perm ? perm[off + b] : off + b;
+      float x = A[row * lda + k];
+      if (relu_in) x = fmaxf(x, 0.f);
+      s += d * x;
+    }
+  }
+  if (k == nin) gb[o] = s;
+  else gW[o * nin + k] = s;
+}
+
+__global__ void k_gout(const float* __restrict__ d3, const float* __restrict__ Z2, int nb, float* __restrict__ gw3,
+                       float* __restrict__ gb3) {
+  const int k = threadIdx.x;
+  if (k > HID) return;
+  float s = 0.f;
+  for (int b = 0; b < nb; ++b) s += k == HID ? d3[b] : d3[b] * fmaxf(Z2[(int64_t)b * HID + k], 0.f);
+  if (k == HID) *gb3 = s;
+  else gw3[k] = s;
+}
+
+__global__ void k_adam(float* __restrict__ th, const float* __restrict__ gr, float* __restrict__ m,
+                       float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float g = gr[i];
+  const float mi = b1 * m[i] + (1.f - b1) * g;
+  const float vi = b2 * v[i] + (1.f - b2) * g * g;
+  m[i] = mi;
+  v[i] = vi;
+  th[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int rows, int cols,
+                          int ldd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * ldd) return;
+  const int r = i / ldd, k = i % ldd;
+  dst[i] = __float2bfloat16_rn(k < cols ? src[r * cols + k] : 0.f);
+}
+
+struct Scratch {
+  float *Z1 = nullptr, *Z2 = nullptr, *d1 = nullptr, *d2 = nullptr, *d3 = nullptr;
+};
+
+}  // namespace
+
+// full-batch (or mini-batch) loss and gradient; grad layout = theta layout
+int mlp_loss_grad_dev(const float* X, int ldx, const uint8_t* y, const int64_t* perm, int64_t off, int nb, int nin,
+                      const float* theta, float* grad, double* loss, float pos_weight, float norm_n, void* scratch,
+                      cudaStream_t st) {
+  const float* W1 = theta;
+  const float* b1 = W1 + HID * nin;
+  const float* W2 = b1 + HID;
+  const float* b2 = W2 + HID * HID;
+  const float* w3 = b2 + HID;
+  float* gW1 = grad;
+  float* gb1 = gW1 + HID * nin;
+  float* gW2 = gb1 + HID;
+  float* gb2 = gW2 + HID * HID;
+  float* gw3 = gb2 + HID;
+  float* gb3 = gw3 + HID;
+  float* s = static_cast<float*>(scratch);
+  float* Z1 = s;
+  float* Z2 = Z1 + (size_t)nb * HID;
+  float* d1 = Z2 + (size_t)nb * HID;
+  float* d2 = d1 + (size_t)nb * HID;
+  float* d3 = d2 + (size_t)nb * HID;
+  float b3;
+  if (cudaMemcpyAsync(&b3, w3 + HID, sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess) return -3;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -3;
+  const int per = 256 / HID;
+  k_dense<<<(nb + per - 1) / per, per * HID, 0, st>>>(X, ldx, perm, off, W1, b1, Z1, nb, nin, HID, 0);
+  k_dense<<<(nb + per - 1) / per, per * HID, 0, st>>>(Z1, HID, nullptr, 0, W2, b2, Z2, nb, HID, HID, 1);
+  k_out<<<(nb + 255) / 256, 256, 0, st>>>(Z2, w3, b3, y, perm, off, nb, pos_weight, 1.f / norm_n, d3, loss);
+  const int64_t nh = (int64_t)nb * HID;
+  k_back2<<<(unsigned)((nh + 255) / 256), 256, 0, st>>>(d3, w3, Z2, d2, nb);
+  k_back1<<<(unsigned)((nh + 255) / 256), 256, 0, st>>>(d2, W2, Z1, d1, nb);
+  k_gout<<<1, 128, 0, st>>>(d3, Z2, nb, gw3, gb3);
+  k_wgrad<<<(HID * (HID + 1) + 127) / 128, 128, 0, st>>>(d2, HID, Z1, HID, nullptr, 0, HID, 1, nb, gW2, gb2);
+  k_wgrad<<<(HID * (nin + 1) + 127) / 128, 128, 0, st>>>(d1, HID, X, ldx, perm, off, nin, 0, nb, gW1, gb1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+size_t mlp_scratch_bytes(int nb) { return ((size_t)nb * HID * 4 + nb) * sizeof(float); }
+
+int mlp_train_dev(const float* X, int ldx, const uint8_t* y, int64_t n, int nin, float* theta, int epochs,
+                  int batch, float lr, float pos_weight, uint64_t seed, double* last_loss, cudaStream_t st) {
+  const int np = mlp_n_params(nin);
+  float *grad = nullptr, *m = nullptr, *v = nullptr;
+  void* scratch = nullptr;
+  int64_t* perm = nullptr;
+  double* dloss = nullptr;
+  int e = 0;
+  if (cudaMalloc(&grad, np * sizeof(float)) || cudaMalloc(&m, np * sizeof(float)) ||
+      cudaMalloc(&v, np * sizeof(float)) || cudaMalloc(&scratch, mlp_scratch_bytes(batch)) ||
+      cudaMalloc(&perm, n * sizeof(int64_t)) || cudaMalloc(&dloss, sizeof(double)))
+    e = -3;
+  if (!e) {
+    cudaMemsetAsync(m, 0, np * sizeof(float), st);
+    cudaMemsetAsync(v, 0, np * sizeof(float), st);
+    std::vector<int64_t> hp(n);
+    for (int64_t i = 0; i < n; ++i) hp[i] = i;
+    std::mt19937_64 rng(seed);
+    int t = 0;
+    for (int ep = 0; ep < epochs && !e; ++ep) {
+      std::shuffle(hp.begin(), hp.end(), rng);
+      if (cudaMemcpyAsync(perm, hp.data(), n * sizeof(int64_t), cudaMemcpyHostToDevice, st)) e = -3;
+      cudaMemsetAsync(dloss, 0, sizeof(double), st);
+      for (int64_t off = 0; off + batch <= n && !e; off += batch) {
+        ++t;
+        e = mlp_loss_grad_dev(X, ldx, y, perm, off, batch, nin, theta, grad, ep == epochs - 1 ? dloss : nullptr,
+                              pos_weight, (float)batch, scratch, st);
+        const float c1 = 1.f - powf(0.9f, (float)t), c2 = 1.f - powf(0.999f, (float)t);
+        k_adam<<<(np + 255) / 256, 256, 0, st>>>(theta, grad, m, v, np, lr, 0.9f, 0.999f, 1e-8f, c1, c2);
+      }
+      if (cudaStreamSynchronize(st) != cudaSuccess) e = -3;
+    }
+    if (!e && last_loss) {
+      double l = 0.0;
+      cudaMemcpy(&l, dloss, sizeof(double), cudaMemcpyDeviceToHost);
+      const int64_t nbat = n / batch;
+      *last_loss = nbat ? l / (double)nbat : 0.0;
+    }
+  }
+  cudaFree(grad);
+  cudaFree(m);
+  cudaFree(v);
+  cudaFree(scratch);
+  cudaFree(perm);
+  cudaFree(dloss);
+  return e;
+}
+
+int mlp_build_tables(Ctx& c) {
+  const Basis& B = *c.hb;
+  const Geom& g = c.g;
+  MlpTabs mt;
+  std::memset(&mt, 0, sizeof(mt));
+  if (g.n > MLP_MAXN || 8 * g.n + 2 * g.D > MLP_MAXIN) return -7;
+  if (!g.glm) {
+    // <phi_j,c, P_l> / M_l by exact monomial integration
+    const auto& ms = B.ms;
+    for (int j = 0; j < g.ndiv && j < 64; ++j)
+      for (int cc = 0; cc < g.D; ++cc)
+        for (int l = 0; l < g.n; ++l) {
+          double s = 0.0;
+          for (size_t i = 0; i < ms.exps.size(); ++i) {
+            const double a = B.ldf[j][cc][i];
+            if (a == 0.0) continue;
+            for (size_t k = 0; k < ms.exps.size(); ++k) {
+              const double b = B.leg[l][k];
+              if (b == 0.0) continue;
+              double t = a * b;
+              for (int ax = 0; ax < g.D; ++ax) {
+                const int e = ms.exps[i][ax] + ms.exps[k][ax];
+                t *= (e & 1) ? 0.0 : 2.0 / (e + 1.0);
+              }
+              s += t;
+            }
+          }
+          mt.l2l[(j * 3 + cc) * MLP_MAXN + l] = (float)(s / B.leg_mass[l]);
+        }
+  }
+  c.mlp = mt;
+  return 0;
+}
+
+int mlp_features_launch(Ctx& c, const void* w, const double* wmean, float* X, int ldx, cudaStream_t st) {
+  const Geom& g = c.g;
+  const unsigned nb = (unsigned)((g.ncell + 127) / 128);
+  if (c.p.precision == DG_PREC_FP32MIX)
+    k_features<float><<<nb, 128, 0, st>>>(g, c.mlp, (const float*)w, wmean, X, ldx);
+  else
+    k_features<double><<<nb, 128, 0, st>>>(g, c.mlp, (const double*)w, nullptr, X, ldx);
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int mlp_set_weights(Ctx& c, const float* theta_dev, int nin, float thresh) {
+  const Geom& g = c.g;
+  if (nin != 8 * g.n + 2 * g.D) return -1;
+  const int kp = (nin + 15) / 16 * 16;
+  if (kp != 48 && kp != 64 && kp != 96 && kp != 176) return -7;
+  if (!c.mlp_w1) {
+    if (cudaMalloc(&c.mlp_w1, (size_t)HID * kp * 2) || cudaMalloc(&c.mlp_w2, (size_t)HID * HID * 2) ||
+        cudaMalloc(&c.mlp_bias, (3 * HID + 1) * sizeof(float)))
+      return -3;
+  }
+  const float* W1 = theta_dev;
+  const float* b1 = W1 + HID * nin;
+  const float* W2 = b1 + HID;
+  const float* b2 = W2 + HID * HID;
+  const float* w3 = b2 + HID;
+  k_to_bf16<<<(HID * kp + 255) / 256, 256>>>(W1, (__nv_bfloat16*)c.mlp_w1, HID, nin, kp);
+  k_to_bf16<<<(HID * HID + 255) / 256, 256>>>(W2, (__nv_bfloat16*)c.mlp_w2, HID, HID, HID);
+  cudaMemcpy(c.mlp_bias, b1, HID * sizeof(float), cudaMemcpyDeviceToDevice);
+  cudaMemcpy(c.mlp_bias + HID, b2, HID * sizeof(float), cudaMemcpyDeviceToDevice);
+  cudaMemcpy(c.mlp_bias + 2 * HID, w3, (HID + 1) * sizeof(float), cudaMemcpyDeviceToDevice);
+  c.mlp_kp = kp;
+  c.mlp_thresh = thresh;
+  return cudaDeviceSynchronize() == cudaSuccess ? 0 : -3;
+}
+
+template <typename T, int KP>
+static void infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* flag, float* prob, cudaStream_t st) {
+  const Geom& g = c.g;
+  const size_t sm = (size_t)HID * (KP + 8) * 2 + (size_t)HID * (HID + 8) * 2 + (size_t)4 * 32 * (KP + 8) * 2 +
+                    (3 * HID + 1) * sizeof(float);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_mlp_infer<T, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  const unsigned nb = (unsigned)((g.ncell + 127) / 128);
+  k_mlp_infer<T, KP><<<nb, 128, sm, st>>>(g, c.mlp, (const T*)w, wmean, (const __nv_bfloat16*)c.mlp_w1,
+                                           (const __nv_bfloat16*)c.mlp_w2, c.mlp_bias, c.mlp_thresh, flag, prob);
+}
+
+int mlp_infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* flag, float* prob, cudaStream_t st) {
+  if (!c.mlp_w1) return -1;
+  const bool f32 = c.p.precision == DG_PREC_FP32MIX;
+  switch (c.mlp_kp) {
+#define KPCASE(K)                                                                 \
+  case K:                                                                         \
+    if (f32) infer_launch<float, K>(c, w, wmean, flag, prob, st);                 \
+    else infer_launch<double, K>(c, w, nullptr, flag, prob, st);                  \
+    break;
+    KPCASE(48)
+    KPCASE(64)
+    KPCASE(96)
+    KPCASE(176)
+#undef KPCASE
+    default:
+      return -7;
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+}  // namespace dgmhd

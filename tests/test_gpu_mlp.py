@@ -1,0 +1,140 @@
+"""Learned troubled-cell indicator on the GPU against the FP64 oracle.
+
+* features: same definition, FP32 on the device: 2e-5 absolute
+* loss and gradient (FP32 forward/backward): 1e-4 relative to the FP64 oracle
+* BF16 tensor-core inference: probabilities within 0.03 of the FP64 network,
+  flags equal wherever |p - 0.5| > 0.05
+* training reduces the loss; gating with everything flagged equals plain TVB,
+  with nothing flagged leaves the state unchanged
+"""
+import numpy as np
+import pytest
+
+from oracle import mhd
+from oracle import mlp as M
+from oracle.dg import Scheme
+from oracle.limiter import Limiter
+
+from gpu_helpers import from_device, means_to_device, rel_err, to_device
+
+pytestmark = pytest.mark.gpu
+G = 5.0 / 3.0
+
+
+def _shock(nvar):
+    def fn(x):
+        r = np.sqrt((x[..., 0] - 0.45) ** 2 + (x[..., 1] - 0.5) ** 2 + (x[..., 2] - 0.55) ** 2)
+        inside = r < 0.27
+        one = np.ones_like(r)
+        u = mhd.conserved(np.where(inside, 1.0, 0.3), np.stack([0.3 * one, -0.2 * one, 0.1 * one], -1),
+                          np.where(inside, 5.0, 0.2), np.stack([0.8 * one, 0.3 * one, np.where(inside, 0.2, -0.4)], -1),
+                          G)
+        if nvar == 9:
+            u = np.concatenate([u, 0.01 * np.sin(6 * x[..., :1])], -1)
+        return u
+    return fn
+
+
+def _solver(S, prec="fp64", **kw):
+    from paper_1806_02343_gb300.binding import Solver, DG_PREC_FP32MIX, DG_PREC_FP64
+    return Solver(S.D, S.ncell, S.d, S.divb, gamma=G, box_len=S.L,
+                  precision=DG_PREC_FP32MIX if prec == "fp32" else DG_PREC_FP64, **kw)
+
+
+@pytest.mark.parametrize("divb,prec", [("powell", "fp64"), ("glm", "fp64"), ("glm", "fp32"), ("powell", "fp32")])
+def test_features(divb, prec):
+    import torch
+    S = Scheme(3, 2, divb, G, (7, 6, 5))
+    w0 = S.project(_shock(S.V))
+    sol = _solver(S, prec)
+    w = to_device(w0, sol)
+    wm = means_to_device(w0, sol, S) if prec == "fp32" else None
+    X = torch.full((sol.ncell, 96), float("nan"), dtype=torch.float32, device="cuda")
+    sol.mlp_features(w, wm, X, 96)
+    ref = M.features(S, w0)
+    got = X.cpu().numpy()
+    assert np.max(np.abs(got[:, :86] - ref)) < 2e-5 * max(1.0, np.abs(ref).max())
+    assert np.all(got[:, 86:] == 0.0)
+
+
+def test_loss_and_gradient_match_oracle():
+    import torch
+    from paper_1806_02343_gb300.binding import mlp_loss_grad
+    rng = np.random.default_rng(3)
+    n, nin = 3000, 86
+    X = rng.normal(size=(n, nin))
+    y = (X[:, 0] - X[:, 5] > 0.3).astype(np.uint8)
+    th = M.init_params(nin, seed=4)
+    th[M.H * nin:M.H * nin + M.H] = rng.normal(0, 0.1, M.H)
+    loss_ref, g_ref = M.loss_and_grad(th, X, y.astype(float), pos_weight=3.0)
+    Xd = torch.as_tensor(X, dtype=torch.float32, device="cuda")
+    yd = torch.as_tensor(y, device="cuda")
+    thd = torch.as_tensor(th, dtype=torch.float32, device="cuda")
+    loss, g = mlp_loss_grad(Xd, yd, thd, nin, pos_weight=3.0)
+    assert abs(loss - loss_ref) < 1e-5 * abs(loss_ref)
+    assert rel_err(g.cpu().numpy().astype(np.float64), g_ref) < 1e-4
+
+
+def _train_synthetic(nin=86, n=20000, seed=0):
+    import torch
+    from paper_1806_02343_gb300.binding import mlp_train, mlp_loss_grad
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(n, nin)).astype(np.float32)
+    y = (X[:, 2] + 0.5 * X[:, 7] - 0.3 * X[:, 80] > 0.8).astype(np.uint8)
+    Xd = torch.as_tensor(X, device="cuda")
+    yd = torch.as_tensor(y, device="cuda")
+    th = torch.as_tensor(M.init_params(nin, seed=1), dtype=torch.float32, device="cuda")
+    l0, _ = mlp_loss_grad(Xd, yd, th, nin)
+    mlp_train(Xd, yd, th, nin, epochs=8, batch=512, lr=2e-3)
+    l1, _ = mlp_loss_grad(Xd, yd, th, nin)
+    return l0, l1
+
+
+def test_training_reduces_loss():
+    l0, l1 = _train_synthetic()
+    assert l1 < 0.25 * l0
+
+
+@pytest.mark.parametrize("divb", ["powell", "glm"])
+def test_bf16_inference_matches_fp64_network(divb):
+    import torch
+    S = Scheme(3, 2, divb, G, (9, 8, 7))
+    w0 = S.project(_shock(S.V))
+    rng = np.random.default_rng(9)
+    th = M.init_params(86, seed=5)
+    th[-1] = -0.2
+    sol = _solver(S)
+    thd = torch.as_tensor(th, dtype=torch.float32, device="cuda")
+    sol.mlp_set_weights(thd, 0.5)
+    w = to_device(w0, sol)
+    flags = torch.zeros(sol.stride, dtype=torch.uint8, device="cuda")
+    prob = torch.zeros(sol.stride, dtype=torch.float32, device="cuda")
+    sol.mlp_infer(w, None, flags, prob)
+    z, _ = M.forward(th, M.features(S, w0))
+    p_ref = M.sigmoid(z)
+    p = prob[: sol.ncell].cpu().numpy()
+    assert np.max(np.abs(p - p_ref)) < 0.03
+    sure = np.abs(p_ref - 0.5) > 0.05
+    assert np.array_equal(flags[: sol.ncell].cpu().numpy()[sure].astype(bool), (p_ref > 0.5)[sure])
+
+
+@pytest.mark.parametrize("divb", ["powell", "glm"])
+def test_gated_tvb_limits(divb):
+    import torch
+    S = Scheme(3, 2, divb, G, (8, 7, 6))
+    S.P.Mtilde = 0.5
+    w0 = S.project(_shock(S.V))
+    ref, trig = Limiter(S, tvb=True, positivity=False).tvb_limit(w0, 3.0)
+    th = M.init_params(86, seed=5)
+    for b3, expect in ((40.0, ref), (-40.0, w0)):
+        th[-1] = b3
+        sol = _solver(S, limiter=2, Mtilde=0.5)
+        if divb == "glm":
+            sol.set_glm(3.0, 1.0)
+        sol.mlp_set_weights(torch.as_tensor(th, dtype=torch.float32, device="cuda"), 0.5)
+        w = to_device(w0, sol)
+        flags = torch.zeros(sol.stride, dtype=torch.uint8, device="cuda")
+        sol.limit(w, None, flags)
+        assert rel_err(from_device(w, sol), expect) < 1e-12
+        f = flags[: sol.ncell].cpu().numpy().astype(bool)
+        assert np.array_equal(f, trig if b3 > 0 else np.zeros_like(trig))

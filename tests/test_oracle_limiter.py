@@ -171,3 +171,55 @@ def test_positivity_limiter():
     good = [c for c in range(S.C) if c not in bad]
     assert np.array_equal(out[good], w[good])   # tau = 1 where already positive
     assert not np.array_equal(out[bad], w[bad])
+
+
+# ------------------------------------------------------------------ learned indicator (oracle)
+from oracle import mlp as M
+
+
+def test_mlp_gradient_matches_central_differences():
+    rng = np.random.default_rng(11)
+    nin = 86
+    X = rng.normal(size=(40, nin))
+    y = (rng.uniform(size=40) < 0.3).astype(float)
+    th = M.init_params(nin, seed=2)
+    th[M.H * nin: M.H * nin + M.H] += 0.05    # nonzero biases
+    loss, g = M.loss_and_grad(th, X, y)
+    idx = rng.choice(len(th), 60, replace=False)
+    for i in idx:
+        e = np.zeros_like(th)
+        e[i] = 1e-6
+        num = (M.loss_and_grad(th + e, X, y)[0] - M.loss_and_grad(th - e, X, y)[0]) / 2e-6
+        assert abs(num - g[i]) <= 1e-6 + 1e-5 * abs(g[i])
+
+
+def test_mlp_features_ldf_map_is_exact():
+    # the componentwise Legendre coefficients rebuild the LDF field exactly
+    S = Scheme(3, 2, "powell", G, (3, 3, 3))
+    w = S.project(lambda x: np.stack(np.broadcast_arrays(
+        np.ones(x.shape[:-1]), 0.1 * x[..., 0], 0 * x[..., 0], 0 * x[..., 0], 2.0 + x[..., 1] ** 2,
+        np.cos(3 * x[..., 1]), np.sin(2 * x[..., 2]), np.cos(x[..., 0])), -1))
+    a = M.coefficients(S, w)
+    u = S.eval_points(w, S.Sv)
+    P = np.array([[float(v) for v in [0]] for _ in range(1)])
+    from oracle import basis as OB
+    Pv = np.array([OB.peval(p, S.qv) for p in S.legendre])   # [l, q]
+    for c in range(3):
+        rec = a[:, mhd.BX + c, :] @ Pv
+        assert np.max(np.abs(rec - u[:, :, mhd.BX + c])) < 1e-12
+    X = M.features(S, w)
+    assert X.shape == (S.C, 86)
+
+
+def test_mlp_training_reduces_loss():
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(512, 20))
+    y = (X[:, 0] + 0.5 * X[:, 3] > 0.2).astype(float)
+    th = M.init_params(20, seed=1)
+    m = np.zeros_like(th)
+    v = np.zeros_like(th)
+    l0 = M.loss_and_grad(th, X, y)[0]
+    for t in range(1, 200):
+        loss, g = M.loss_and_grad(th, X, y)
+        th, m, v = M.adam_step(th, g, m, v, t, lr=3e-3)
+    assert loss < 0.3 * l0
