@@ -159,21 +159,27 @@ const double* dg_mhd_last_dt(const dg_mhd_ctx* ctx);
  * clear the word after reading. Returns DG_OK, a latched error or DG_W_FLOOR. */
 int dg_mhd_status(dg_mhd_ctx* ctx, int sync);
 
+/* Positivity diagnostics (Sec. 4.3): cells rescaled by the positivity limiter
+ * (tau < 1) and the mass and energy injected by the mean floors, accumulated
+ * since the last reset. Synchronises the device; reset = 1 clears them. */
+int dg_mhd_counters(dg_mhd_ctx* ctx, int64_t* pos_cells, double* inj_mass, double* inj_energy, int reset);
+
 /* Learned troubled-cell indicator. The paper makes troubled-cell detection
  * a separate step of limiting, judged by sensitivity and specificity (Sec. 4.2);
  * the network is not in the paper. With limiter = DG_LIMIT_MLP, a network
  * (nin -> 64 -> 64 -> 1, ReLU, sigmoid; BF16 weights, FP32 accumulation on the
  * tensor cores) flags cells, and only flagged cells go through the TVB
- * procedure. Features of a cell, nin = 8 n(d) + 2*dim: Legendre coefficients of
- * the 8 MHD variables (LDF B mapped exactly to per-component Legendre
+ * procedure. Features of a cell, nin = 8 n(d) + 10*dim: Legendre coefficients
+ * of the 8 MHD variables (LDF B mapped exactly to per-component Legendre
  * coefficients), variable v divided by |mean_v| + max_nb |mean_nb,v - mean_v|
- * + 1e-12, then rho_nb/rho - 1 for neighbours -x, +x, -y, +y (, -z, +z).
+ * + 1e-12, then rho_nb/rho - 1 for neighbours -x, +x, -y, +y (, -z, +z), then
+ * for each direction the 8 degree-1 coefficients divided by M~ dx.
  * theta (DEVICE, FP32, flat): W1[64][nin], b1[64], W2[64][64], b2[64],
  * w3[64], b3. */
 /* X[cell*ldx + k] (DEVICE float, ldx >= nin; padding written as 0). */
 int dg_mhd_mlp_features(dg_mhd_ctx* ctx, const void* w, const double* wmean, float* X, int ldx, void* stream);
 /* Copies theta (DEVICE) into the context as BF16; flag = sigmoid > threshold.
- * Synchronous. nin must equal 8 n(d) + 2*dim. */
+ * Synchronous. nin must equal 8 n(d) + 10*dim. */
 int dg_mhd_mlp_set_weights(dg_mhd_ctx* ctx, const float* theta, int nin, float threshold);
 /* Features + inference for every cell: flags (nullable, uint8) and prob
  * (nullable, float) per cell (DEVICE). */
@@ -191,7 +197,8 @@ int dg_mhd_mlp_train(const float* X, int ldx, const uint8_t* y, int64_t n, int n
                      int batch, float lr, float pos_weight, uint64_t seed, double* last_loss, void* stream);
 
 /* Measurement support (no counterpart in the paper). Kernel kinds:
- * 0 face flux, 1 cell update, 2 timestep, 3 limiter, 4 projection.
+ * 0 face flux, 1 cell update, 2 timestep, 3 TVB limiter, 4 projection,
+ * 5 positivity limiter, 6 learned indicator (features + inference).
  * dg_mhd_profile(ctx, 1) resets the counters and, from then on, records a
  * CUDA event pair on the launch stream around every kernel launch;
  * dg_mhd_profile(ctx, 0) stops recording (launches are still counted).

@@ -6,12 +6,13 @@ indicator replaces the TVB detection with a small multilayer perceptron that
 decides which cells the TVB procedure processes; the plain TVB trigger is the
 label and the judge. Nothing here is printed in the paper; the choices are:
 
-* features of a cell (8 n(d) + 2D values): the Legendre coefficients of the 8
-  MHD conserved variables (for the LDF basis, B is first mapped exactly to
-  per-component Legendre coefficients), each variable divided by
+* features of a cell (8 n(d) + 2D + 8D values): the Legendre coefficients of
+  the 8 MHD conserved variables (for the LDF basis, B is first mapped exactly
+  to per-component Legendre coefficients), each variable divided by
   s_v = |mean_v| + max over the 2D face neighbours |mean_nb,v - mean_v| + 1e-12,
   then the neighbour density ratios rho_nb/rho - 1 in the order
-  -x, +x, -y, +y, -z, +z;
+  -x, +x, -y, +y, -z, +z, then for each direction a and variable v the
+  degree-1 coefficient along a divided by M~ dx (the TVB slope scale);
 * network: in -> 64 -> 64 -> 1, ReLU hidden layers, sigmoid output;
 * loss: mean binary cross-entropy; optimiser: Adam.
 Weights are one flat vector: W1[64][in], b1[64], W2[64][64], b2[64], w3[64], b3.
@@ -28,7 +29,7 @@ H = 64
 
 
 def n_in(S):
-    return 8 * S.n + 2 * S.D
+    return 8 * S.n + 2 * S.D + 8 * S.D
 
 
 def n_params(nin):
@@ -93,7 +94,9 @@ def features(S, w):
             ratios.append(m[nbr, 0] / m[:, 0] - 1.0)
     s = np.abs(m) + dmax + 1e-12
     X = (a / s[:, :, None]).reshape(S.C, -1)
-    return np.concatenate([X, np.stack(ratios, -1)], -1)
+    deg1 = [S.modes.index(tuple(1 if i == ax else 0 for i in range(S.D))) for ax in range(S.D)]
+    sl = np.concatenate([a[:, :, deg1[ax]] for ax in range(S.D)], -1) / (S.P.Mtilde * S.dx)
+    return np.concatenate([X, np.stack(ratios, -1), sl], -1)
 
 
 def forward(theta, X):

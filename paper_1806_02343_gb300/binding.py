@@ -24,9 +24,9 @@ EXPORTS = [
     "dg_mhd_rhs", "dg_mhd_limit", "dg_mhd_dt", "dg_mhd_step", "dg_mhd_last_dt", "dg_mhd_status",
     "dg_mhd_profile", "dg_mhd_profile_read", "dg_mhd_launch_count", "dg_mhd_rhs_noalloc", "dg_mhd_destroy",
     "dg_mhd_strerror", "dg_mhd_mlp_features", "dg_mhd_mlp_set_weights", "dg_mhd_mlp_infer", "dg_mhd_mlp_loss_grad",
-    "dg_mhd_mlp_train",
+    "dg_mhd_mlp_train", "dg_mhd_counters",
 ]
-KIND_FACE, KIND_CELL, KIND_DT, KIND_LIMIT, KIND_PROJECT = range(5)
+KIND_FACE, KIND_CELL, KIND_DT, KIND_LIMIT, KIND_PROJECT, KIND_POSITIVITY, KIND_MLP = range(7)
 
 
 class MeshDesc(ctypes.Structure):
@@ -79,6 +79,8 @@ def lib():
     L.dg_mhd_mlp_train.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64, ctypes.c_int, vp, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_uint64,
                                    ctypes.POINTER(ctypes.c_double), vp]
+    L.dg_mhd_counters.argtypes = [vp, i64p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.c_int]
     L.dg_mhd_destroy.argtypes = [vp]
     L.dg_mhd_destroy.restype = None
     L.dg_mhd_strerror.argtypes = [ctypes.c_int]
@@ -241,7 +243,7 @@ class Solver:
 
     # --------------------------------------------------------- learned indicator
     def n_features(self):
-        return 8 * {2: {0: 1, 1: 3, 2: 6, 3: 10}, 3: {0: 1, 1: 4, 2: 10, 3: 20}}[self.dim][self.degree] + 2 * self.dim
+        return 8 * {2: {0: 1, 1: 3, 2: 6, 3: 10}, 3: {0: 1, 1: 4, 2: 10, 3: 20}}[self.dim][self.degree] + 10 * self.dim
 
     def mlp_features(self, w, wmean, X, ldx):
         _check(lib().dg_mhd_mlp_features(self.h, _ptr(w), _ptr(wmean), _ptr(X), ldx, _stream()),
@@ -254,6 +256,12 @@ class Solver:
     def mlp_infer(self, w, wmean=None, flags=None, prob=None):
         _check(lib().dg_mhd_mlp_infer(self.h, _ptr(w), _ptr(wmean), _ptr(flags), _ptr(prob), _stream()),
                "dg_mhd_mlp_infer")
+
+    def counters(self, reset=False):
+        n, m, e = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().dg_mhd_counters(self.h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(e), 1 if reset else 0),
+               "dg_mhd_counters")
+        return {"pos_cells": n.value, "inj_mass": m.value, "inj_energy": e.value}
 
     def status(self, sync=True):
         return lib().dg_mhd_status(self.h, 1 if sync else 0)

@@ -728,6 +728,23 @@ int dg_mhd_mlp_train(const float* X, int ldx, const uint8_t* y, int64_t n, int n
   return mlp_train_dev(X, ldx, y, n, nin, theta, epochs, batch, lr, pos_weight, seed, last_loss, S(stream));
 }
 
+int dg_mhd_counters(dg_mhd_ctx* ctx, int64_t* pos_cells, double* inj_mass, double* inj_energy, int reset) {
+  if (!ctx) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  if (cudaDeviceSynchronize() != cudaSuccess) return DG_E_CUDA;
+  DevScalars h;
+  if (cudaMemcpy(&h, c.sc, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return DG_E_CUDA;
+  if (pos_cells) *pos_cells = (int64_t)h.pos_cells;
+  if (inj_mass) *inj_mass = h.inj_mass;
+  if (inj_energy) *inj_energy = h.inj_energy;
+  if (reset) {
+    h.pos_cells = 0;
+    h.inj_mass = h.inj_energy = 0.0;
+    if (cudaMemcpy(c.sc, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) return DG_E_CUDA;
+  }
+  return DG_OK;
+}
+
 int dg_mhd_status(dg_mhd_ctx* ctx, int sync) {
   if (!ctx) return DG_E_ARG;
   Ctx& c = ctx->c;

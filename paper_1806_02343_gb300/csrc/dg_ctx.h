@@ -58,6 +58,7 @@ struct DevScalars {
   int floor_used;
   double inj_mass;    // mass added by the positivity floors (Sec. 4.3)
   double inj_energy;  // energy added by the positivity floors
+  unsigned long long pos_cells;  // cells the positivity limiter rescaled (tau < 1)
 };
 
 // Limiter tables (kernel parameters): degree-1 Legendre mode per axis, mode
@@ -77,10 +78,10 @@ struct LimTabs {
 // Launch accounting: counts every kernel launch; with `on`, records a CUDA
 // event pair on the launch stream around each launch of a given kind.
 struct Prof {
-  static constexpr int KINDS = 5;
+  static constexpr int KINDS = 7;
   bool on = false;
-  int64_t launches[KINDS] = {0, 0, 0, 0, 0};
-  double ms[KINDS] = {0, 0, 0, 0, 0};
+  int64_t launches[KINDS] = {0, 0, 0, 0, 0, 0, 0};
+  double ms[KINDS] = {0, 0, 0, 0, 0, 0, 0};
   std::vector<cudaEvent_t> pool;
   std::vector<int> kind;   // kind of each recorded pair
   size_t used = 0;         // events in use (2 per pair)
@@ -94,9 +95,11 @@ struct Prof {
 // Learned indicator: exact LDF -> per-component Legendre map
 // l2l[(j*3 + c)*MLP_MAXN + l] = <phi_j,c, P_l> / M_l.
 constexpr int MLP_MAXN = 20;
-constexpr int MLP_MAXIN = 176;
+constexpr int MLP_MAXIN = 192;
 struct MlpTabs {
   float l2l[64 * 3 * MLP_MAXN];
+  int deg1[3];      // degree-1 Legendre mode along each axis
+  float inv_mdx;    // 1 / (M~ dx)
 };
 
 struct Ctx {

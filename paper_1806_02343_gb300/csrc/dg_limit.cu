@@ -417,34 +417,99 @@ __global__ void k_pos(Geom g, Tables<T> tb, T* w, double* wmean, dg_mhd_params p
   const int npt = g.Qv + 2 * g.D * g.Qf;
   const bool dbl = sizeof(T) == 8;
   const double pmean = pres(m);
-  // tau_rho
+  // basis value of Legendre mode l / LDF row j component cc at point pt
+  auto Pval = [&](int l, int pt) -> T {
+    if (pt < g.Qv) return tb.Pv[l * g.Qv + pt];
+    const int fp = pt - g.Qv, f = fp / g.Qf;
+    return tb.Pf[((size_t)f * g.n + l) * g.Qf + fp % g.Qf];
+  };
+  auto Lval = [&](int j, int cc, int pt) -> T {
+    if (pt < g.Qv) return tb.Lv[(j * g.DB + cc) * g.Qv + pt];
+    const int fp = pt - g.Qv, f = fp / g.Qf;
+    return tb.Lf[(((size_t)f * g.ndiv + j) * g.DB + cc) * g.Qf + fp % g.Qf];
+  };
+  constexpr int PC = 8;  // points per pass: each state row is loaded once per pass
+  // tau_rho (eq. tau_rho) over all volume and face points
   double tau = 1.0;
-  for (int pt = 0; pt < npt; ++pt) {
-    double u[9];
-    point_state(g, tb, (const T*)w, mr, c, pt, u, dbl);
-    const double rq = u[0];
-    if (rq < p.eps_rho) tau = fmin(tau, (m[0] - p.eps_rho) / (m[0] - rq));
+  for (int p0 = 0; p0 < npt; p0 += PC) {
+    T acc[PC];
+#pragma unroll
+    for (int k = 0; k < PC; ++k) acc[k] = T(0);
+    for (int l = 1; l < g.n; ++l) {
+      const T wv = w[(int64_t)l * S + c];
+#pragma unroll
+      for (int k = 0; k < PC; ++k)
+        if (p0 + k < npt) acc[k] += wv * Pval(l, p0 + k);
+    }
+#pragma unroll
+    for (int k = 0; k < PC; ++k) {
+      if (p0 + k >= npt) continue;
+      const double rq = mr[0] + (double)acc[k];
+      if (rq < p.eps_rho) tau = fmin(tau, (m[0] - p.eps_rho) / (m[0] - rq));
+    }
   }
   tau = fmax(tau, 0.0);
-  // tau_p from the density-limited state u' = m + tau (u - m)
+  // tau_p (eq. tau_press) from the density-limited state u' = m + tau (u - m)
   double taup = 1.0;
-  const double screen = sizeof(T) == 4 ? 1e-4 : 0.0;
-  for (int pt = 0; pt < npt; ++pt) {
-    double u[9];
-    point_state(g, tb, (const T*)w, mr, c, pt, u, dbl);
-    for (int k = 0; k < 9; ++k) u[k] = m[k] + tau * (u[k] - m[k]);
-    double pq = pres(u);
-    if (!dbl && pq < p.eps_p + screen * fabs(u[4])) {
-      // FP64 recovery of this point's pressure (E - kinetic - magnetic cancels)
-      point_state(g, tb, (const T*)w, mr, c, pt, u, true);
-      for (int k = 0; k < 9; ++k) u[k] = m[k] + tau * (u[k] - m[k]);
-      pq = pres(u);
+  const double screen = dbl ? 0.0 : 1e-4;
+  const int nleg = g.glm ? 8 : 5;
+  for (int p0 = 0; p0 < npt; p0 += PC) {
+    // register accumulators: every index below is a compile-time constant
+    T acc[PC][8];
+#pragma unroll
+    for (int k = 0; k < PC; ++k)
+#pragma unroll
+      for (int v = 0; v < 8; ++v) acc[k][v] = T(0);
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      if (v >= nleg) continue;
+      for (int l = 1; l < g.n; ++l) {
+        const T wv = w[(int64_t)(v * g.n + l) * S + c];
+#pragma unroll
+        for (int k = 0; k < PC; ++k)
+          if (p0 + k < npt) acc[k][v] += wv * Pval(l, p0 + k);
+      }
     }
-    if (pq < p.eps_p) taup = fmin(taup, (pmean - p.eps_p) / (pmean - pq));
+    if (!g.glm) {
+      for (int j = g.D; j < g.ndiv; ++j) {
+        const T wj = w[(int64_t)(g.ldf0 + j) * S + c];
+#pragma unroll
+        for (int k = 0; k < PC; ++k)
+          if (p0 + k < npt) {
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc)
+              if (cc < g.DB) acc[k][5 + cc] += wj * Lval(j, cc, p0 + k);
+          }
+      }
+      if (g.bz2d >= 0)
+        for (int l = 1; l < g.n; ++l) {
+          const T wv = w[(int64_t)(g.bz2d + l) * S + c];
+#pragma unroll
+          for (int k = 0; k < PC; ++k)
+            if (p0 + k < npt) acc[k][7] += wv * Pval(l, p0 + k);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PC; ++k) {
+      if (p0 + k >= npt) continue;
+      double u[9];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) u[v] = m[v] + tau * (double)acc[k][v];  // acc holds u - mean
+      u[8] = 0.0;
+      double pq = pres(u);
+      if (!dbl && pq < p.eps_p + screen * fabs(u[4])) {
+        // FP64 recovery of this point's pressure (E - kinetic - magnetic cancels)
+        point_state(g, tb, (const T*)w, mr, c, p0 + k, u, true);
+        for (int v = 0; v < 9; ++v) u[v] = m[v] + tau * (u[v] - m[v]);
+        pq = pres(u);
+      }
+      if (pq < p.eps_p) taup = fmin(taup, (pmean - p.eps_p) / (pmean - pq));
+    }
   }
   taup = fmax(taup, 0.0);
   const double t = tau * taup;
   if (t >= 1.0) return;
+  atomicAdd(&sc->pos_cells, 1ull);
   // scale every non-mean row by tau
   for (int r = 0; r < g.nrows; ++r) {
     bool mean = false;
@@ -514,14 +579,15 @@ int run_limiter(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t 
   const unsigned nb = (unsigned)((g.ncell + 127) / 128);
   if (c.p.limiter == DG_LIMIT_TVB || c.p.limiter == DG_LIMIT_MLP) {
     const uint8_t* gate = nullptr;
-    c.prof.begin(3, st);
     if (c.p.limiter == DG_LIMIT_MLP) {
       if (!c.mlp_w1) return DG_E_ARG;  // no weights set
+      c.prof.begin(6, st);
       const int e = mlp_infer_launch(c, w, wmean, c.troubled, nullptr, st);
+      c.prof.end(6, st);
       if (e) return e;
       gate = c.troubled;
-      c.prof.launches[3] += 1;
     }
+    c.prof.begin(3, st);
     if (c.p.precision == DG_PREC_FP32MIX)
       k_tvb<float><<<nb, 128, 0, st>>>(g, c.lim, (float*)w, wmean, troubled, gate, c.p, c.sc);
     else
@@ -529,12 +595,12 @@ int run_limiter(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t 
     c.prof.end(3, st);
   }
   if (c.p.positivity) {
-    c.prof.begin(3, st);
+    c.prof.begin(5, st);
     if (c.p.precision == DG_PREC_FP32MIX)
       k_pos<float><<<nb, 128, 0, st>>>(g, c.t32, (float*)w, wmean, c.p, c.sc);
     else
       k_pos<double><<<nb, 128, 0, st>>>(g, c.t64, (double*)w, nullptr, c.p, c.sc);
-    c.prof.end(3, st);
+    c.prof.end(5, st);
   }
   return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
 }

@@ -5,10 +5,11 @@
 // cells, then limit them); this network replaces the TVB detection and only the
 // cells it flags go through the characteristic TVB procedure.
 //
-// Features of a cell (nin = 8 n(d) + 2D): Legendre coefficients of the 8 MHD
+// Features of a cell (nin = 8 n(d) + 10 D): Legendre coefficients of the 8 MHD
 // variables (LDF B mapped exactly to per-component Legendre coefficients), each
 // variable divided by s_v = |mean_v| + max_nb |mean_nb,v - mean_v| + 1e-12,
-// then rho_nb / rho - 1 for the neighbours -x, +x, -y, +y (, -z, +z).
+// then rho_nb / rho - 1 for the neighbours -x, +x, -y, +y (, -z, +z), then the
+// degree-1 coefficient of each variable along each direction over M~ dx.
 // Network: nin -> 64 -> 64 -> 1, ReLU, sigmoid. Weights (flat FP32):
 // W1[64][nin], b1[64], W2[64][64], b2[64], w3[64], b3.
 #include <cuda_bf16.h>
@@ -106,6 +107,13 @@ __device__ __forceinline__ void cell_features(const Geom& g, const MlpTabs& mt, 
     }
   }
   for (int k = 0; k < 2 * g.D; ++k) x[8 * n + k] = ratio[k];
+  // degree-1 coefficient along each direction divided by M~ dx (TVB slope scale):
+  // undo the per-variable normalisation of the coefficients written above
+  for (int a = 0; a < g.D; ++a)
+    for (int v = 0; v < 8; ++v) {
+      const float sv = fabsf(m[v]) + dmax[v] + 1e-12f;
+      x[8 * n + 2 * g.D + 8 * a + v] = x[v * n + mt.deg1[a]] * sv * mt.inv_mdx;
+    }
 }
 
 template <typename T>
@@ -115,7 +123,7 @@ __global__ void k_features(Geom g, MlpTabs mt, const T* __restrict__ w, const do
   if (c >= g.ncell) return;
   float x[MLP_MAXIN];
   cell_features(g, mt, w, wmean, c, x);
-  const int nin = 8 * g.n + 2 * g.D;
+  const int nin = 8 * g.n + 10 * g.D;
   for (int k = 0; k < ldx; ++k) X[c * ldx + k] = k < nin ? x[k] : 0.f;
 }
 
@@ -157,7 +165,7 @@ __global__ void __launch_bounds__(128) k_mlp_infer(Geom g, MlpTabs mt, const T* 
   const bool live = c < g.ncell;
   {
     float x[MLP_MAXIN];
-    const int nin = 8 * g.n + 2 * g.D;
+    const int nin = 8 * g.n + 10 * g.D;
     if (live) cell_features(g, mt, w, wmean, c, x);
     __nv_bfloat16* xr = Xs + (warp * 32 + lane) * LD1;
     for (int k = 0; k < KP; ++k) xr[k] = __float2bfloat16_rn(live && k < nin ? x[k] : 0.f);
@@ -453,7 +461,13 @@ int mlp_build_tables(Ctx& c) {
   const Geom& g = c.g;
   MlpTabs mt;
   std::memset(&mt, 0, sizeof(mt));
-  if (g.n > MLP_MAXN || 8 * g.n + 2 * g.D > MLP_MAXIN) return -7;
+  if (g.n > MLP_MAXN || 8 * g.n + 10 * g.D > MLP_MAXIN) return -7;
+  for (int a = 0; a < g.D; ++a)
+    for (int l = 0; l < g.n; ++l) {
+      const auto& k = B.modes[l];
+      if (k[0] + k[1] + k[2] == 1 && k[a] == 1) mt.deg1[a] = l;
+    }
+  mt.inv_mdx = (float)(1.0 / (c.p.Mtilde * g.dx));
   if (!g.glm) {
     // <phi_j,c, P_l> / M_l by exact monomial integration
     const auto& ms = B.ms;
@@ -494,9 +508,9 @@ int mlp_features_launch(Ctx& c, const void* w, const double* wmean, float* X, in
 
 int mlp_set_weights(Ctx& c, const float* theta_dev, int nin, float thresh) {
   const Geom& g = c.g;
-  if (nin != 8 * g.n + 2 * g.D) return -1;
+  if (nin != 8 * g.n + 10 * g.D) return -1;
   const int kp = (nin + 15) / 16 * 16;
-  if (kp != 48 && kp != 64 && kp != 96 && kp != 176) return -7;
+  if (kp != 64 && kp != 80 && kp != 112 && kp != 192) return -7;
   if (!c.mlp_w1) {
     if (cudaMalloc(&c.mlp_w1, (size_t)HID * kp * 2) || cudaMalloc(&c.mlp_w2, (size_t)HID * HID * 2) ||
         cudaMalloc(&c.mlp_bias, (3 * HID + 1) * sizeof(float)))
@@ -541,10 +555,10 @@ int mlp_infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* flag, 
     if (f32) infer_launch<float, K>(c, w, wmean, flag, prob, st);                 \
     else infer_launch<double, K>(c, w, nullptr, flag, prob, st);                  \
     break;
-    KPCASE(48)
     KPCASE(64)
-    KPCASE(96)
-    KPCASE(176)
+    KPCASE(80)
+    KPCASE(112)
+    KPCASE(192)
 #undef KPCASE
     default:
       return -7;

@@ -168,12 +168,27 @@ def orszag_tang_3d(x, gamma=5.0 / 3.0, nvar=8):
 
 def blast_3d(x, gamma=5.0 / 3.0, nvar=8, center=(0.5, 0.5, 0.5), r0=0.1, p_in=100.0, p_out=0.1,
              B0=(10.0 / math.sqrt(4.0 * math.pi), 0.0, 0.0)):
+    """MHD blast: p = p_in inside r < r0, p_out outside, rho = 1, v = 0, uniform B0."""
     xp = _xp(x)
     r2 = (x[..., 0] - center[0]) ** 2 + (x[..., 1] - center[1]) ** 2 + (x[..., 2] - center[2]) ** 2
     one = xp.ones_like(r2)
-    p = xp.where(r2 < r0 * r0, p_in * one, p_out * one)
+    p = p_out * one + (p_in - p_out) * (r2 < r0 * r0)
     zero = 0.0 * one
     return _assemble(xp, one, zero, zero, zero, p, B0[0] * one, B0[1] * one, B0[2] * one, gamma, nvar)
+
+
+def blast_params(seed):
+    """Seeded blast variant for indicator training: centre in [0.3, 0.7]^3,
+    radius 0.05-0.15, pressure ratio 10^2-10^4 (outside p = 0.1), field of
+    strength 0-10/sqrt(4 pi) along a random direction."""
+    rng = np.random.default_rng(seed)
+    center = tuple(rng.uniform(0.3, 0.7, 3))
+    r0 = rng.uniform(0.05, 0.15)
+    ratio = 10.0 ** rng.uniform(2.0, 4.0)
+    d = rng.normal(size=3)
+    d /= np.linalg.norm(d)
+    bmag = rng.uniform(0.0, 10.0 / math.sqrt(4.0 * math.pi))
+    return dict(center=center, r0=r0, p_in=0.1 * ratio, p_out=0.1, B0=tuple(bmag * d))
 
 
 # ---------------------------------------------------------------------------
@@ -270,3 +285,32 @@ class Turbulence3D:
         ph = np.exp(2j * np.pi * np.einsum("...a,k->...ak", x, ks))  # [..., 3, nk]
         v = np.einsum("abcd,...a,...b,...c->...d", self.A, ph[..., 0, :], ph[..., 1, :], ph[..., 2, :]).real
         return self.state_from_velocity(self.scale * v)
+
+
+# ---------------------------------------------------------------------------
+# point values at the Gauss points of every cell of a uniform box (input
+# layout of dg_mhd_project: [var][q][cell], cell x-fastest, q last-axis-fastest)
+# ---------------------------------------------------------------------------
+
+
+def gauss_nodal(fn, n, npts, D=3, stride=None, device="cuda"):
+    """Evaluates fn (torch-capable) at the npts^D Gauss-Legendre points of each
+    cell of an n^D periodic unit box; returns a float64 tensor [V][Q][stride]."""
+    import torch
+    g1, _ = np.polynomial.legendre.leggauss(npts)
+    c1 = ((torch.arange(n, device=device, dtype=torch.float64)[:, None] + 0.5
+           + 0.5 * torch.as_tensor(g1, device=device)[None, :]) / n).reshape(-1)
+    if D == 3:
+        X, Y, Z = torch.meshgrid(c1, c1, c1, indexing="ij")
+        U = fn(torch.stack([X, Y, Z], -1))
+        V = U.shape[-1]
+        U = U.reshape(n, npts, n, npts, n, npts, V).permute(6, 1, 3, 5, 4, 2, 0).reshape(V, npts ** 3, n ** 3)
+    else:
+        X, Y = torch.meshgrid(c1, c1, indexing="ij")
+        U = fn(torch.stack([X, Y], -1))
+        V = U.shape[-1]
+        U = U.reshape(n, npts, n, npts, V).permute(4, 1, 3, 2, 0).reshape(V, npts ** 2, n ** 2)
+    stride = stride or U.shape[-1]
+    out = torch.zeros((V, U.shape[1], stride), dtype=torch.float64, device=device)
+    out[:, :, : U.shape[-1]] = U
+    return out

@@ -1,0 +1,25 @@
+"""End-to-end learned indicator on solver-generated data (small sizes):
+labels from the plain TVB detector on seeded blasts, training with the
+library's kernels, then the gated run against the plain run. The gain shown
+is the limiter time: the TVB procedure runs only on flagged cells."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_indicator_pipeline_and_gain():
+    import torch
+    from paper_1806_02343_gb300 import indicator as I
+    X, y, nin = I.generate("powell", 2, n=32, seeds=(1, 2, 3), steps=5)
+    assert X.shape[0] == 3 * 5 * 32 ** 3 and int(y.sum()) > 100
+    theta, info = I.train(X, y, nin, epochs=20, batch=1024, lr=2e-3)
+    assert info["loss_last_epoch"] < 0.5 * info["loss_initial"]
+    rep = I.evaluate(theta, nin, "powell", 2, n=40, steps=4, threshold=0.1)
+    assert rep["status"]["plain"] == 0 and rep["status"]["mlp"] == 0
+    assert rep["troubled_plain"] > 0
+    assert rep["missed_cell_rate"] < 0.3
+    assert rep["false_positive_rate"] < 0.1
+    # the gain: detection + TVB on flagged cells is cheaper than TVB detection on all cells
+    assert rep["limiter_ms"]["mlp"] < rep["limiter_ms"]["plain"]
+    assert max(rep["l1_rel_final_means"][:5]) < 5e-2

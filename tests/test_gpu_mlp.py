@@ -49,12 +49,13 @@ def test_features(divb, prec):
     sol = _solver(S, prec)
     w = to_device(w0, sol)
     wm = means_to_device(w0, sol, S) if prec == "fp32" else None
-    X = torch.full((sol.ncell, 96), float("nan"), dtype=torch.float32, device="cuda")
-    sol.mlp_features(w, wm, X, 96)
+    X = torch.full((sol.ncell, 112), float("nan"), dtype=torch.float32, device="cuda")
+    sol.mlp_features(w, wm, X, 112)
     ref = M.features(S, w0)
     got = X.cpu().numpy()
-    assert np.max(np.abs(got[:, :86] - ref)) < 2e-5 * max(1.0, np.abs(ref).max())
-    assert np.all(got[:, 86:] == 0.0)
+    assert ref.shape[1] == 110
+    assert np.max(np.abs(got[:, :110] - ref)) < 2e-5 * max(1.0, np.abs(ref).max())
+    assert np.all(got[:, 110:] == 0.0)
 
 
 def test_loss_and_gradient_match_oracle():
@@ -101,7 +102,7 @@ def test_bf16_inference_matches_fp64_network(divb):
     S = Scheme(3, 2, divb, G, (9, 8, 7))
     w0 = S.project(_shock(S.V))
     rng = np.random.default_rng(9)
-    th = M.init_params(86, seed=5)
+    th = M.init_params(110, seed=5)
     th[-1] = -0.2
     sol = _solver(S)
     thd = torch.as_tensor(th, dtype=torch.float32, device="cuda")
@@ -125,7 +126,7 @@ def test_gated_tvb_limits(divb):
     S.P.Mtilde = 0.5
     w0 = S.project(_shock(S.V))
     ref, trig = Limiter(S, tvb=True, positivity=False).tvb_limit(w0, 3.0)
-    th = M.init_params(86, seed=5)
+    th = M.init_params(110, seed=5)
     for b3, expect in ((40.0, ref), (-40.0, w0)):
         th[-1] = b3
         sol = _solver(S, limiter=2, Mtilde=0.5)

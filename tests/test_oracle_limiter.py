@@ -208,7 +208,7 @@ def test_mlp_features_ldf_map_is_exact():
         rec = a[:, mhd.BX + c, :] @ Pv
         assert np.max(np.abs(rec - u[:, :, mhd.BX + c])) < 1e-12
     X = M.features(S, w)
-    assert X.shape == (S.C, 86)
+    assert X.shape == (S.C, 86 + 24)
 
 
 def test_mlp_training_reduces_loss():
