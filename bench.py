@@ -157,8 +157,18 @@ def run_ours(args, cfg, rank, world, device):
     ncell = n ** D
     res = {}
 
-    def make(prec):
-        sol = Solver(D, (n,) * D, d, divb, precision=prec)
+    def make(prec, limiter):
+        kw = {}
+        if limiter == "mlp":
+            kw = dict(limiter=Bd.DG_LIMIT_MLP, positivity=1)
+        elif limiter == "tvb":
+            kw = dict(limiter=Bd.DG_LIMIT_TVB, positivity=1)
+        sol = Solver(D, (n,) * D, d, divb, precision=prec, **kw)
+        if limiter == "mlp":
+            import numpy as np
+            from paper_1806_02343_gb300 import indicator
+            th = torch.as_tensor(np.load(indicator.weights_path(divb, d)), dtype=torch.float32, device=device)
+            sol.mlp_set_weights(th, args.threshold)
         w, wm = sol.alloc_state(device)
         builder = build_turbulence if "turb" in cfg["name"] else build_fourier
         nodal, npts = builder(sol, cfg, device)
@@ -173,7 +183,7 @@ def run_ours(args, cfg, rank, world, device):
             dist.barrier()
 
     # ------------------------------------------------------------ FP32 form (value)
-    sol, w, wm = make(Bd.DG_PREC_FP32MIX)
+    sol, w, wm = make(Bd.DG_PREC_FP32MIX, args.limiter)
     dof = ncell * sol.nrows
     for _ in range(args.warmup):
         sol.step(w, wm)
@@ -195,7 +205,9 @@ def run_ours(args, cfg, rank, world, device):
     ms = ev0.elapsed_time(ev1)
     launches = sol.launch_count()
     kern = {}
-    for k, name in ((Bd.KIND_FACE, "face_flux"), (Bd.KIND_CELL, "cell_update"), (Bd.KIND_DT, "timestep")):
+    for k, name in ((Bd.KIND_FACE, "face_flux"), (Bd.KIND_CELL, "cell_update"), (Bd.KIND_DT, "timestep"),
+                    (Bd.KIND_LIMIT, "tvb_limiter"), (Bd.KIND_MLP, "indicator"),
+                    (Bd.KIND_POSITIVITY, "positivity")):
         t, nl = sol.profile_read(k)
         kern[name] = {"ms_total": t, "launches": nl, "ms_per_launch": t / max(nl, 1)}
     sol.profile(False)
@@ -253,7 +265,7 @@ def run_ours(args, cfg, rank, world, device):
 
     # ------------------------------------------------------------ plain FP64 path, same workload
     if not args.skip_fp64:
-        sol, w, _ = make(Bd.DG_PREC_FP64)
+        sol, w, _ = make(Bd.DG_PREC_FP64, "tvb" if args.limiter != "off" else "off")
         sol.step(w)
         torch.cuda.synchronize()
         k64 = max(1, args.fp64_steps)
@@ -264,7 +276,8 @@ def run_ours(args, cfg, rank, world, device):
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1)
         res["fp64_plain"] = {"value": dof * 3 * k64 / (ms64 * 1e-3), "unit": "DoF-updates/s",
-                             "ms_per_step": ms64 / k64, "steps": k64, "status": sol.status()}
+                             "ms_per_step": ms64 / k64, "steps": k64, "status": sol.status(),
+                             "limiter": "plain TVB detection + positivity" if args.limiter != "off" else "off"}
         del sol, w
         torch.cuda.empty_cache()
     return res
@@ -323,14 +336,18 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=24)
+    ap.add_argument("--limiter", default="mlp", choices=["mlp", "tvb", "off"])
+    ap.add_argument("--threshold", type=float, default=0.1)
     args = ap.parse_args()
     cfg = dict(CONFIGS[args.config])
     cfg["name"] = args.config
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    lim_desc = {"mlp": "learned indicator gating TVB-characteristic + positivity",
+                "tvb": "TVB-characteristic + positivity", "off": "off"}[args.limiter]
     config = {"workload": cfg["workload"], "cells": cfg["n"] ** cfg["D"], "degree": cfg["d"],
-              "divb": cfg["divb"], "limiter": "off", "rk": "SSP-RK3",
+              "divb": cfg["divb"], "limiter": lim_desc, "rk": "SSP-RK3",
               "l2_flush": "inputs larger than L2 (state >= 6 GB)", "replicas_per_gpu": 1}
 
     if args.impl == "reference":

@@ -34,7 +34,7 @@ int upload(T** dst, const std::vector<double>& src) {
 }
 
 struct HostTables {
-  std::vector<double> Pv, dPv, Pf, Lv, dLv, Lf, L0, wv, wf, minv;
+  std::vector<double> Pv, dPv, Pf, Lv, dLv, Lf, L0, wv, wf, minv, Pp, Lp;
 };
 
 // reference coordinates of volume point q (tensor rule, last axis fastest)
@@ -120,6 +120,17 @@ void build_host_tables(const Basis& B, const Geom& g, HostTables& h) {
         h.L0[(size_t)j * DB + c] = B.eval(B.ldf[j][c], z);
       }
     }
+  // all volume then all face points, contiguous per mode (positivity limiter)
+  const int npos = Qv + 2 * D * Qf;
+  h.Pp.assign((size_t)n * npos, 0.0);
+  h.Lp.assign((size_t)std::max(1, nd * DB * npos), 0.0);
+  for (int pt = 0; pt < npos; ++pt) {
+    if (pt < Qv) vol_point(D, x1, pt, xi);
+    else face_point(D, x1, (pt - Qv) / Qf, (pt - Qv) % Qf, xi);
+    for (int l = 0; l < n; ++l) h.Pp[(size_t)l * npos + pt] = B.eval(B.leg[l], xi);
+    for (int j = 0; j < nd; ++j)
+      for (int c = 0; c < DB; ++c) h.Lp[((size_t)j * DB + c) * npos + pt] = B.eval(B.ldf[j][c], xi);
+  }
   h.minv.assign(g.nrows, 0.0);
   for (int r = 0; r < g.nrows; ++r) {
     double m;
@@ -143,12 +154,14 @@ int upload_tables(const HostTables& h, Tables<T>& t) {
   if ((e = upload(&t.wv, h.wv))) return e;
   if ((e = upload(&t.wf, h.wf))) return e;
   if ((e = upload(&t.minv, h.minv))) return e;
+  if ((e = upload(&t.Pp, h.Pp))) return e;
+  if ((e = upload(&t.Lp, h.Lp))) return e;
   return DG_OK;
 }
 
 template <typename T>
 void free_tables(Tables<T>& t) {
-  T* ptrs[] = {t.Pv, t.dPv, t.Pf, t.Lv, t.dLv, t.Lf, t.L0, t.wv, t.wf, t.minv};
+  T* ptrs[] = {t.Pv, t.dPv, t.Pf, t.Lv, t.dLv, t.Lf, t.L0, t.wv, t.wf, t.minv, t.Pp, t.Lp};
   for (T* p : ptrs)
     if (p) cudaFree(p);
   t = Tables<T>();

@@ -25,11 +25,14 @@ constexpr int MAXROWS = 180;  // 9 * n(3)
 //   dLv[((a*nd+j)*DB+c)*Qv+q]
 //   Lf[((f*nd+j)*DB+c)*Qf+p]
 //   wv[q], wf[p], minv[r] = 1/M_r, L0[j*DB+c] = cell mean of LDF component
+//   Pp[l*npos + pt], Lp[(j*DB+c)*npos + pt]: values at all volume points and then
+//   all face points (npos = Qv + 2D*Qf), for the positivity limiter
 template <typename T>
 struct Tables {
   T *Pv = nullptr, *dPv = nullptr, *Pf = nullptr;
   T *Lv = nullptr, *dLv = nullptr, *Lf = nullptr, *L0 = nullptr;
   T *wv = nullptr, *wf = nullptr, *minv = nullptr;
+  T *Pp = nullptr, *Lp = nullptr;
 };
 
 // Kernel-facing description of the discretisation (passed by value).
@@ -73,6 +76,7 @@ struct LimTabs {
   double ldf_slope[64 * 9];
   double ldf_pc[64 * 3];
   double ldf_pl[64 * 9];
+  double ldf_maxabs[64 * 3];  // upper bound of |phi_j,c| on the cell (sum of |monomial coefficients|)
 };
 
 // Launch accounting: counts every kernel launch; with `on`, records a CUDA

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <cfloat>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -65,92 +66,101 @@ __device__ __forceinline__ void cell_mean(const Geom& g, const LimTabs& lt, cons
   }
 }
 
-__device__ __forceinline__ double minmod3(double a, double b, double c) {
-  if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
-  if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
-  return 0.0;
+template <typename R>
+__device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
+template <typename R>
+__device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
+__device__ __forceinline__ double rsq(double x) { return sqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return sqrtf(x); }
+
+template <typename R>
+__device__ __forceinline__ R minmod3(R a, R b, R c) {
+  if (a > R(0) && b > R(0) && c > R(0)) return a < b ? (a < c ? a : c) : (b < c ? b : c);
+  if (a < R(0) && b < R(0) && c < R(0)) return a > b ? (a > c ? a : c) : (b > c ? b : c);
+  return R(0);
 }
 
 // Characteristic basis at mean state m along axis a (primitive variables).
+template <typename R>
 struct Eig {
-  double rho, sr, a2, a, cf, cs, af, as, by, bz, S, ch;
+  R rho, sr, a2, a, cf, cs, af, as, by, bz, S, ch;
   int n, t1, t2;
   bool glm;
 };
 
-__device__ __forceinline__ void eig_setup(const double* m, int axis, double gamma, bool glm, double ch, double rel,
-                                          Eig& e) {
+template <typename R>
+__device__ __forceinline__ void eig_setup(const R* m, int axis, R gamma, bool glm, R ch, R rel, Eig<R>& e) {
   e.n = axis; e.t1 = (axis + 1) % 3; e.t2 = (axis + 2) % 3;
   e.glm = glm; e.ch = ch;
-  const double rho = m[0];
-  const double v[3] = {m[1] / rho, m[2] / rho, m[3] / rho};
-  const double B[3] = {m[5], m[6], m[7]};
-  const double p = (gamma - 1.0) * (m[4] - 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) -
-                                    0.5 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
+  const R rho = m[0];
+  const R v[3] = {m[1] / rho, m[2] / rho, m[3] / rho};
+  const R B[3] = {m[5], m[6], m[7]};
+  const R p = (gamma - R(1.0)) * (m[4] - R(0.5) * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) -
+                                    R(0.5) * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
   e.rho = rho;
-  e.sr = sqrt(rho);
+  e.sr = rsq(rho);
   e.a2 = gamma * p / rho;
-  e.a = sqrt(e.a2);
-  const double bn = B[e.n], bt1 = B[e.t1], bt2 = B[e.t2];
-  const double bt2sq = bt1 * bt1 + bt2 * bt2;
-  const double b2 = (bn * bn + bt2sq) / rho, cax2 = bn * bn / rho;
-  const double disc = sqrt(fmax((e.a2 + b2) * (e.a2 + b2) - 4.0 * e.a2 * cax2, 0.0));
-  const double cf2 = 0.5 * (e.a2 + b2 + disc);
-  const double cs2 = fmax(0.5 * (e.a2 + b2 - disc), 0.0);
-  e.cf = sqrt(cf2);
-  e.cs = sqrt(cs2);
+  e.a = rsq(e.a2);
+  const R bn = B[e.n], bt1 = B[e.t1], bt2 = B[e.t2];
+  const R bt2sq = bt1 * bt1 + bt2 * bt2;
+  const R b2 = (bn * bn + bt2sq) / rho, cax2 = bn * bn / rho;
+  const R disc = rsq(rmax((e.a2 + b2) * (e.a2 + b2) - R(4.0) * e.a2 * cax2, R(0.0)));
+  const R cf2 = R(0.5) * (e.a2 + b2 + disc);
+  const R cs2 = rmax(R(0.5) * (e.a2 + b2 - disc), R(0.0));
+  e.cf = rsq(cf2);
+  e.cs = rsq(cs2);
   if (cf2 - cs2 > rel * cf2) {
-    e.af = sqrt(fmax(e.a2 - cs2, 0.0) / (cf2 - cs2));
-    e.as = sqrt(fmax(cf2 - e.a2, 0.0) / (cf2 - cs2));
+    e.af = rsq(rmax(e.a2 - cs2, R(0.0)) / (cf2 - cs2));
+    e.as = rsq(rmax(cf2 - e.a2, R(0.0)) / (cf2 - cs2));
   } else {
-    e.af = 1.0;
-    e.as = 0.0;
+    e.af = R(1.0);
+    e.as = R(0.0);
   }
-  const double bt = sqrt(bt2sq);
-  if (bt > rel * sqrt(rho * cf2)) {
+  const R bt = rsq(bt2sq);
+  if (bt > rel * rsq(rho * cf2)) {
     e.by = bt1 / bt;
     e.bz = bt2 / bt;
   } else {
-    e.by = e.bz = 0.70710678118654752440;
+    e.by = e.bz = R(0.70710678118654752440);
   }
-  e.S = bn >= 0.0 ? 1.0 : -1.0;
+  e.S = bn >= R(0.0) ? R(1.0) : -R(1.0);
 }
 
 // conserved increment dU -> characteristic amplitudes c (V values)
-__device__ __forceinline__ void to_char(const Eig& e, const double* m, double gamma, const double* dU, double* c,
-                                        int V) {
-  const double rho = m[0];
-  const double v[3] = {m[1] / rho, m[2] / rho, m[3] / rho};
-  const double B[3] = {m[5], m[6], m[7]};
+template <typename R>
+__device__ __forceinline__ void to_char(const Eig<R>& e, const R* m, R gamma, const R* dU, R* c, int V) {
+  const R rho = m[0];
+  const R v[3] = {m[1] / rho, m[2] / rho, m[3] / rho};
+  const R B[3] = {m[5], m[6], m[7]};
   // dW = dW/dU dU
-  double dW[9];
+  R dW[9];
   dW[0] = dU[0];
   for (int i = 0; i < 3; ++i) dW[1 + i] = (dU[1 + i] - v[i] * dU[0]) / rho;
-  const double g1 = gamma - 1.0;
-  dW[4] = g1 * (0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * dU[0] - (v[0] * dU[1] + v[1] * dU[2] + v[2] * dU[3]) +
+  const R g1 = gamma - R(1.0);
+  dW[4] = g1 * (R(0.5) * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * dU[0] - (v[0] * dU[1] + v[1] * dU[2] + v[2] * dU[3]) +
                 dU[4] - (B[0] * dU[5] + B[1] * dU[6] + B[2] * dU[7]));
   for (int i = 5; i < V; ++i) dW[i] = dU[i];
-  const double dr = dW[0], du = dW[1 + e.n], dv = dW[1 + e.t1], dw = dW[1 + e.t2], dp = dW[4];
-  const double dby = dW[5 + e.t1], dbz = dW[5 + e.t2];
-  const double ia2 = 1.0 / e.a2;
-  const double vpar = e.by * dv + e.bz * dw, bpar = e.by * dby + e.bz * dbz;
-  const double vperp = -e.bz * dv + e.by * dw, bperp = -e.bz * dby + e.by * dbz;
-  const double sra = e.sr * e.a;
+  const R dr = dW[0], du = dW[1 + e.n], dv = dW[1 + e.t1], dw = dW[1 + e.t2], dp = dW[4];
+  const R dby = dW[5 + e.t1], dbz = dW[5 + e.t2];
+  const R ia2 = R(1.0) / e.a2;
+  const R vpar = e.by * dv + e.bz * dw, bpar = e.by * dby + e.bz * dbz;
+  const R vperp = -e.bz * dv + e.by * dw, bperp = -e.bz * dby + e.by * dbz;
+  const R sra = e.sr * e.a;
   // fast -, alfven -, slow -, entropy, slow +, alfven +, fast +
-  c[0] = 0.5 * ia2 * (-e.af * e.cf * du + e.as * e.cs * e.S * vpar) + 0.5 * (e.af * dp / (e.rho * e.a2) + e.as * bpar / sra);
-  c[6] = 0.5 * ia2 * (e.af * e.cf * du - e.as * e.cs * e.S * vpar) + 0.5 * (e.af * dp / (e.rho * e.a2) + e.as * bpar / sra);
-  c[2] = 0.5 * ia2 * (-e.as * e.cs * du - e.af * e.cf * e.S * vpar) + 0.5 * (e.as * dp / (e.rho * e.a2) - e.af * bpar / sra);
-  c[4] = 0.5 * ia2 * (e.as * e.cs * du + e.af * e.cf * e.S * vpar) + 0.5 * (e.as * dp / (e.rho * e.a2) - e.af * bpar / sra);
-  c[1] = 0.5 * vperp + 0.5 * e.S * bperp / e.sr;
-  c[5] = 0.5 * vperp - 0.5 * e.S * bperp / e.sr;
+  c[0] = R(0.5) * ia2 * (-e.af * e.cf * du + e.as * e.cs * e.S * vpar) + R(0.5) * (e.af * dp / (e.rho * e.a2) + e.as * bpar / sra);
+  c[6] = R(0.5) * ia2 * (e.af * e.cf * du - e.as * e.cs * e.S * vpar) + R(0.5) * (e.af * dp / (e.rho * e.a2) + e.as * bpar / sra);
+  c[2] = R(0.5) * ia2 * (-e.as * e.cs * du - e.af * e.cf * e.S * vpar) + R(0.5) * (e.as * dp / (e.rho * e.a2) - e.af * bpar / sra);
+  c[4] = R(0.5) * ia2 * (e.as * e.cs * du + e.af * e.cf * e.S * vpar) + R(0.5) * (e.as * dp / (e.rho * e.a2) - e.af * bpar / sra);
+  c[1] = R(0.5) * vperp + R(0.5) * e.S * bperp / e.sr;
+  c[5] = R(0.5) * vperp - R(0.5) * e.S * bperp / e.sr;
   c[3] = dr - dp * ia2;
-  const double dbn = dW[5 + e.n];
+  const R dbn = dW[5 + e.n];
   if (!e.glm) {
     c[7] = dbn;
-  } else if (e.ch > 0.0) {
-    const double dpsi = dW[8];
-    c[7] = 0.5 * (dbn - dpsi / e.ch);
-    c[8] = 0.5 * (dbn + dpsi / e.ch);
+  } else if (e.ch > R(0.0)) {
+    const R dpsi = dW[8];
+    c[7] = R(0.5) * (dbn - dpsi / e.ch);
+    c[8] = R(0.5) * (dbn + dpsi / e.ch);
   } else {  // no c_h set yet: B_n and psi as separate fields
     c[7] = dbn;
     c[8] = dW[8];
@@ -158,11 +168,11 @@ __device__ __forceinline__ void to_char(const Eig& e, const double* m, double ga
 }
 
 // characteristic amplitudes -> conserved increment
-__device__ __forceinline__ void from_char(const Eig& e, const double* m, double gamma, const double* c, double* dU,
-                                          int V) {
-  const double rho = e.rho, sr = e.sr, a2 = e.a2, a = e.a, S = e.S;
-  double dW7[7] = {0, 0, 0, 0, 0, 0, 0};  // rho, u, v, w, p, By, Bz (rotated)
-  auto add = [&](double amp, double r0, double r1, double r2, double r3, double r4, double r5, double r6) {
+template <typename R>
+__device__ __forceinline__ void from_char(const Eig<R>& e, const R* m, R gamma, const R* c, R* dU, int V) {
+  const R rho = e.rho, sr = e.sr, a2 = e.a2, a = e.a, S = e.S;
+  R dW7[7] = {0, 0, 0, 0, 0, 0, 0};  // rho, u, v, w, p, By, Bz (rotated)
+  auto add = [&](R amp, R r0, R r1, R r2, R r3, R r4, R r5, R r6) {
     dW7[0] += amp * r0; dW7[1] += amp * r1; dW7[2] += amp * r2; dW7[3] += amp * r3;
     dW7[4] += amp * r4; dW7[5] += amp * r5; dW7[6] += amp * r6;
   };
@@ -177,7 +187,7 @@ __device__ __forceinline__ void from_char(const Eig& e, const double* m, double 
   add(c[5], 0, 0, -e.bz, e.by, 0, e.bz * S * sr, -e.by * S * sr);
   add(c[6], rho * e.af, e.af * e.cf, -e.as * e.cs * e.by * S, -e.as * e.cs * e.bz * S, rho * e.af * a2,
       e.as * sr * a * e.by, e.as * sr * a * e.bz);
-  double dW[9];
+  R dW[9];
   dW[0] = dW7[0];
   dW[1 + e.n] = dW7[1];
   dW[1 + e.t1] = dW7[2];
@@ -187,7 +197,7 @@ __device__ __forceinline__ void from_char(const Eig& e, const double* m, double 
   dW[5 + e.t2] = dW7[6];
   if (!e.glm) {
     dW[5 + e.n] = c[7];
-  } else if (e.ch > 0.0) {
+  } else if (e.ch > R(0.0)) {
     dW[5 + e.n] = c[7] + c[8];
     dW[8] = e.ch * (c[8] - c[7]);
   } else {
@@ -195,12 +205,12 @@ __device__ __forceinline__ void from_char(const Eig& e, const double* m, double 
     dW[8] = c[8];
   }
   // dU = dU/dW dW
-  const double v[3] = {m[1] / m[0], m[2] / m[0], m[3] / m[0]};
-  const double B[3] = {m[5], m[6], m[7]};
+  const R v[3] = {m[1] / m[0], m[2] / m[0], m[3] / m[0]};
+  const R B[3] = {m[5], m[6], m[7]};
   dU[0] = dW[0];
   for (int i = 0; i < 3; ++i) dU[1 + i] = v[i] * dW[0] + rho * dW[1 + i];
-  dU[4] = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * dW[0] + rho * (v[0] * dW[1] + v[1] * dW[2] + v[2] * dW[3]) +
-          dW[4] / (gamma - 1.0) + B[0] * dW[5] + B[1] * dW[6] + B[2] * dW[7];
+  dU[4] = R(0.5) * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) * dW[0] + rho * (v[0] * dW[1] + v[1] * dW[2] + v[2] * dW[3]) +
+          dW[4] / (gamma - R(1.0)) + B[0] * dW[5] + B[1] * dW[6] + B[2] * dW[7];
   for (int i = 5; i < V; ++i) dU[i] = dW[i];
 }
 
@@ -234,34 +244,44 @@ __global__ void k_tvb(Geom g, LimTabs lt, T* w, double* wmean, uint8_t* troubled
         for (int a = 0; a < g.D; ++a) sl[a][5 + cc] += wj * lt.ldf_slope[(j * 3 + cc) * 3 + a];
     }
   }
-  const double thr = p.Mtilde * g.dx;
-  const double ch = g.glm ? sc->ch : 0.0;
-  const double rel = sizeof(T) == 4 ? 1e-6 : 1e-12;
+  // characteristic limiting in the working precision of the state
+  using R = T;
+  const R thr = (R)(p.Mtilde * g.dx);
+  const R ch = g.glm ? (R)sc->ch : R(0);
+  const R rel = sizeof(T) == 4 ? R(1e-6) : R(1e-12);
+  const R gam = (R)g.gamma, beta = (R)p.beta, teps = (R)p.tvb_eps;
+  R mR[9];
+  for (int k = 0; k < 9; ++k) mR[k] = (R)m[k];
   bool any = false;
   double nsl[3][9];
   for (int a = 0; a < g.D; ++a) {
     double mp[9], mm[9];
     cell_mean(g, lt, (const T*)w, wmean, nb(g, c, a, +1), mp);
     cell_mean(g, lt, (const T*)w, wmean, nb(g, c, a, -1), mm);
-    double dpl[9], dmi[9];
+    R dpl[9], dmi[9], sla[9];
     for (int k = 0; k < 9; ++k) {
-      dpl[k] = 0.5 * (mp[k] - m[k]);
-      dmi[k] = 0.5 * (m[k] - mm[k]);
+      dpl[k] = (R)(0.5 * (mp[k] - m[k]));
+      dmi[k] = (R)(0.5 * (m[k] - mm[k]));
+      sla[k] = (R)sl[a][k];
     }
-    Eig e;
-    eig_setup(m, a, g.gamma, g.glm != 0, ch, rel, e);
-    double cx[9], cp[9], cm[9], sg[9];
-    to_char(e, m, g.gamma, sl[a], cx, V);
-    to_char(e, m, g.gamma, dpl, cp, V);
-    to_char(e, m, g.gamma, dmi, cm, V);
+    Eig<R> e;
+    eig_setup(mR, a, gam, g.glm != 0, ch, rel, e);
+    R cx[9], cp[9], cm[9], sg[9];
+    to_char(e, mR, gam, sla, cx, V);
+    to_char(e, mR, gam, dpl, cp, V);
+    to_char(e, mR, gam, dmi, cm, V);
     bool trig = false;
     for (int k = 0; k < V; ++k) {
       sg[k] = cx[k];
-      if (fabs(cx[k]) > thr) sg[k] = minmod3(cx[k], p.beta * cp[k], p.beta * cm[k]);
-      if (fabs(sg[k] - cx[k]) > p.tvb_eps) trig = true;
+      const R ax = cx[k] < R(0) ? -cx[k] : cx[k];
+      if (ax > thr) sg[k] = minmod3(cx[k], beta * cp[k], beta * cm[k]);
+      const R df = sg[k] - cx[k];
+      if ((df < R(0) ? -df : df) > teps) trig = true;
     }
     if (trig) {
-      from_char(e, m, g.gamma, sg, nsl[a], V);
+      R out[9];
+      from_char(e, mR, gam, sg, out, V);
+      for (int k = 0; k < 9; ++k) nsl[a][k] = k < V ? (double)out[k] : 0.0;
       any = true;
     } else {
       for (int k = 0; k < 9; ++k) nsl[a][k] = sl[a][k];
@@ -366,7 +386,7 @@ __device__ __forceinline__ void point_state(const Geom& g, const Tables<T>& tb, 
 }
 
 template <typename T>
-__global__ void k_pos(Geom g, Tables<T> tb, T* w, double* wmean, dg_mhd_params p, DevScalars* sc) {
+__global__ void k_pos(Geom g, Tables<T> tb, LimTabs lt, T* w, double* wmean, dg_mhd_params p, DevScalars* sc) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
   const int64_t S = g.stride;
@@ -417,18 +437,59 @@ __global__ void k_pos(Geom g, Tables<T> tb, T* w, double* wmean, dg_mhd_params p
   const int npt = g.Qv + 2 * g.D * g.Qf;
   const bool dbl = sizeof(T) == 8;
   const double pmean = pres(m);
+  {
+    // Rigorous screen: |P_l| <= 1 on the cell, |phi_j,c| <= ldf_maxabs, so
+    // |u_v(x) - mean_v| <= dev_v everywhere; if the resulting lower bounds of
+    // rho and p clear the floors, every point does and tau = 1.
+    T devt[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+    const int nlg = g.glm ? 8 : 5;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      if (v >= nlg) continue;
+      for (int l = 1; l < g.n; ++l) {
+        const T x = w[(int64_t)(v * g.n + l) * S + c];
+        devt[v] += x < T(0) ? -x : x;
+      }
+    }
+    if (!g.glm) {
+      for (int j = g.D; j < g.ndiv; ++j) {
+        T aj = w[(int64_t)(g.ldf0 + j) * S + c];
+        aj = aj < T(0) ? -aj : aj;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc)
+          if (cc < g.D) devt[5 + cc] += aj * (T)lt.ldf_maxabs[j * 3 + cc];
+      }
+      if (g.bz2d >= 0)
+        for (int l = 1; l < g.n; ++l) {
+          const T x = w[(int64_t)(g.bz2d + l) * S + c];
+          devt[7] += x < T(0) ? -x : x;
+        }
+    }
+    double dev[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) dev[v] = (double)devt[v];
+    // margin for the rounding of the bounds themselves in the working precision
+    const double rel = sizeof(T) == 4 ? 1e-5 : 1e-12;
+    for (int v = 0; v < 8; ++v) dev[v] = dev[v] * (1.0 + rel) + rel * fabs(m[v]);
+    const double rho_lo = m[0] - dev[0];
+    if (rho_lo > p.eps_rho) {
+      double kin = 0.0, mag = 0.0;
+      for (int i = 0; i < 3; ++i) {
+        const double mu = fabs(m[1 + i]) + dev[1 + i], bu = fabs(m[5 + i]) + dev[5 + i];
+        kin += mu * mu;
+        mag += bu * bu;
+      }
+      const double p_lo = gm1 * (m[4] - dev[4] - 0.5 * kin / rho_lo - 0.5 * mag);
+      if (p_lo > p.eps_p) return;
+    }
+  }
   // basis value of Legendre mode l / LDF row j component cc at point pt
-  auto Pval = [&](int l, int pt) -> T {
-    if (pt < g.Qv) return tb.Pv[l * g.Qv + pt];
-    const int fp = pt - g.Qv, f = fp / g.Qf;
-    return tb.Pf[((size_t)f * g.n + l) * g.Qf + fp % g.Qf];
-  };
-  auto Lval = [&](int j, int cc, int pt) -> T {
-    if (pt < g.Qv) return tb.Lv[(j * g.DB + cc) * g.Qv + pt];
-    const int fp = pt - g.Qv, f = fp / g.Qf;
-    return tb.Lf[(((size_t)f * g.ndiv + j) * g.DB + cc) * g.Qf + fp % g.Qf];
-  };
+  auto Pval = [&](int l, int pt) -> T { return tb.Pp[l * npt + pt]; };
+  auto Lval = [&](int j, int cc, int pt) -> T { return tb.Lp[(j * g.DB + cc) * npt + pt]; };
   constexpr int PC = 8;  // points per pass: each state row is loaded once per pass
+  // screening margin of the working precision: points within it of a floor are
+  // re-evaluated in FP64, all others decided in the working precision
+  const T screen_t = sizeof(T) == 4 ? T(1e-4) : T(0);
   // tau_rho (eq. tau_rho) over all volume and face points
   double tau = 1.0;
   for (int p0 = 0; p0 < npt; p0 += PC) {
@@ -444,14 +505,18 @@ __global__ void k_pos(Geom g, Tables<T> tb, T* w, double* wmean, dg_mhd_params p
 #pragma unroll
     for (int k = 0; k < PC; ++k) {
       if (p0 + k >= npt) continue;
-      const double rq = mr[0] + (double)acc[k];
-      if (rq < p.eps_rho) tau = fmin(tau, (m[0] - p.eps_rho) / (m[0] - rq));
+      const T rq = (T)mr[0] + acc[k];
+      if (rq < (T)p.eps_rho + screen_t * (T)m[0]) {
+        // near or below the floor: decide in FP64
+        double rd = mr[0];
+        for (int l = 1; l < g.n; ++l) rd += (double)w[(int64_t)l * S + c] * (double)Pval(l, p0 + k);
+        if (rd < p.eps_rho) tau = fmin(tau, (m[0] - p.eps_rho) / (m[0] - rd));
+      }
     }
   }
   tau = fmax(tau, 0.0);
   // tau_p (eq. tau_press) from the density-limited state u' = m + tau (u - m)
   double taup = 1.0;
-  const double screen = dbl ? 0.0 : 1e-4;
   const int nleg = g.glm ? 8 : 5;
   for (int p0 = 0; p0 < npt; p0 += PC) {
     // register accumulators: every index below is a compile-time constant
@@ -489,21 +554,24 @@ __global__ void k_pos(Geom g, Tables<T> tb, T* w, double* wmean, dg_mhd_params p
             if (p0 + k < npt) acc[k][7] += wv * Pval(l, p0 + k);
         }
     }
+    const T gm1t = (T)gm1;
 #pragma unroll
     for (int k = 0; k < PC; ++k) {
       if (p0 + k >= npt) continue;
-      double u[9];
+      const T tt = (T)tau;
+      T uu[8];
 #pragma unroll
-      for (int v = 0; v < 8; ++v) u[v] = m[v] + tau * (double)acc[k][v];  // acc holds u - mean
-      u[8] = 0.0;
-      double pq = pres(u);
-      if (!dbl && pq < p.eps_p + screen * fabs(u[4])) {
+      for (int v = 0; v < 8; ++v) uu[v] = (T)m[v] + tt * acc[k][v];  // acc holds u - mean
+      const T pt = gm1t * (uu[4] - T(0.5) * (uu[1] * uu[1] + uu[2] * uu[2] + uu[3] * uu[3]) / uu[0] -
+                           T(0.5) * (uu[5] * uu[5] + uu[6] * uu[6] + uu[7] * uu[7]));
+      if (pt < (T)p.eps_p + screen_t * (uu[4] < T(0) ? -uu[4] : uu[4])) {
         // FP64 recovery of this point's pressure (E - kinetic - magnetic cancels)
+        double u[9];
         point_state(g, tb, (const T*)w, mr, c, p0 + k, u, true);
         for (int v = 0; v < 9; ++v) u[v] = m[v] + tau * (u[v] - m[v]);
-        pq = pres(u);
+        const double pq = pres(u);
+        if (pq < p.eps_p) taup = fmin(taup, (pmean - p.eps_p) / (pmean - pq));
       }
-      if (pq < p.eps_p) taup = fmin(taup, (pmean - p.eps_p) / (pmean - pq));
     }
   }
   taup = fmax(taup, 0.0);
@@ -569,6 +637,9 @@ int upload_limiter_tables(Ctx& c) {
         lt.ldf_slope[(j * 3 + cc) * 3 + a] = ia / xi2;
         lt.ldf_pl[(j * 3 + cc) * 3 + a] = ia / Mj;
       }
+      double mx = 0.0;
+      for (double v : B.ldf[j][cc]) mx += std::fabs(v);
+      lt.ldf_maxabs[j * 3 + cc] = mx;
     }
   c.lim = lt;
   return DG_OK;
@@ -597,9 +668,9 @@ int run_limiter(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t 
   if (c.p.positivity) {
     c.prof.begin(5, st);
     if (c.p.precision == DG_PREC_FP32MIX)
-      k_pos<float><<<nb, 128, 0, st>>>(g, c.t32, (float*)w, wmean, c.p, c.sc);
+      k_pos<float><<<nb, 128, 0, st>>>(g, c.t32, c.lim, (float*)w, wmean, c.p, c.sc);
     else
-      k_pos<double><<<nb, 128, 0, st>>>(g, c.t64, (double*)w, nullptr, c.p, c.sc);
+      k_pos<double><<<nb, 128, 0, st>>>(g, c.t64, c.lim, (double*)w, nullptr, c.p, c.sc);
     c.prof.end(5, st);
   }
   return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;

@@ -65,55 +65,64 @@ __device__ __forceinline__ void means8(const Geom& g, const MlpTabs& mt, const T
   }
 }
 
-// features of cell c into x[0..nin)
-template <typename T>
+// features of cell c, written through put(k, value) for k in [0, nin)
+template <typename T, typename Put>
 __device__ __forceinline__ void cell_features(const Geom& g, const MlpTabs& mt, const T* w, const double* wmean,
-                                              int64_t c, float* x) {
+                                              int64_t c, Put put) {
   const int64_t S = g.stride;
   const int n = g.n;
   float m[8];
   means8(g, mt, w, wmean, c, m);
   float dmax[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  float ratio[6];
-  for (int a = 0; a < g.D; ++a)
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a >= g.D) break;
+#pragma unroll
     for (int s = 0; s < 2; ++s) {
       float mn[8];
       means8(g, mt, w, wmean, nbc(g, c, a, s ? 1 : -1), mn);
+#pragma unroll
       for (int k = 0; k < 8; ++k) dmax[k] = fmaxf(dmax[k], fabsf(mn[k] - m[k]));
-      ratio[2 * a + s] = mn[0] / m[0] - 1.f;
+      put(8 * n + 2 * a + s, mn[0] / m[0] - 1.f);
     }
+  }
   float inv[8];
+#pragma unroll
   for (int k = 0; k < 8; ++k) inv[k] = 1.f / (fabsf(m[k]) + dmax[k] + 1e-12f);
+  const float imdx = mt.inv_mdx;
   const int nleg = g.glm ? 8 : 5;
-  for (int v = 0; v < nleg; ++v)
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    const bool leg = v < nleg || (!g.glm && g.D == 2 && v == 7);
+    if (!leg) continue;
+    const int r0 = (v == 7 && !g.glm) ? g.bz2d : v * n;
     for (int l = 0; l < n; ++l) {
-      const float a = (l == 0) ? m[v] : (float)w[(int64_t)(v * n + l) * S + c];
-      x[v * n + l] = a * inv[v];
+      const float av = (l == 0) ? m[v] : (float)w[(int64_t)(r0 + l) * S + c];
+      put(v * n + l, av * inv[v]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (a < g.D && l == mt.deg1[a]) put(8 * n + 2 * g.D + 8 * a + v, av * imdx);
     }
+  }
   if (!g.glm) {
-    for (int cc = 0; cc < g.D; ++cc)
-      for (int l = 0; l < n; ++l) x[(5 + cc) * n + l] = 0.f;
-    for (int j = 0; j < g.ndiv; ++j) {
-      const float wj = j < g.D ? (wmean ? (float)wmean[(5 + j) * S + c] : (float)w[(int64_t)(g.ldf0 + j) * S + c])
-                               : (float)w[(int64_t)(g.ldf0 + j) * S + c];
-      for (int cc = 0; cc < g.D; ++cc)
-        for (int l = 0; l < n; ++l) x[(5 + cc) * n + l] += wj * mt.l2l[(j * 3 + cc) * MLP_MAXN + l] * inv[5 + cc];
-    }
-    if (g.D == 2) {
+    // LDF B -> per-component Legendre coefficients (exact map)
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      if (cc >= g.D) break;
       for (int l = 0; l < n; ++l) {
-        const float a = (l == 0) ? m[7] : (float)w[(int64_t)(g.bz2d + l) * S + c];
-        x[7 * n + l] = a * inv[7];
+        float acc = 0.f;
+        for (int j = 0; j < g.ndiv; ++j) {
+          const float wj = j < g.D ? (wmean ? (float)wmean[(5 + j) * S + c] : (float)w[(int64_t)(g.ldf0 + j) * S + c])
+                                   : (float)w[(int64_t)(g.ldf0 + j) * S + c];
+          acc += wj * mt.l2l[(j * 3 + cc) * MLP_MAXN + l];
+        }
+        put((5 + cc) * n + l, acc * inv[5 + cc]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          if (a < g.D && l == mt.deg1[a]) put(8 * n + 2 * g.D + 8 * a + 5 + cc, acc * imdx);
       }
     }
   }
-  for (int k = 0; k < 2 * g.D; ++k) x[8 * n + k] = ratio[k];
-  // degree-1 coefficient along each direction divided by M~ dx (TVB slope scale):
-  // undo the per-variable normalisation of the coefficients written above
-  for (int a = 0; a < g.D; ++a)
-    for (int v = 0; v < 8; ++v) {
-      const float sv = fabsf(m[v]) + dmax[v] + 1e-12f;
-      x[8 * n + 2 * g.D + 8 * a + v] = x[v * n + mt.deg1[a]] * sv * mt.inv_mdx;
-    }
 }
 
 template <typename T>
@@ -121,10 +130,10 @@ __global__ void k_features(Geom g, MlpTabs mt, const T* __restrict__ w, const do
                            float* __restrict__ X, int ldx) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
-  float x[MLP_MAXIN];
-  cell_features(g, mt, w, wmean, c, x);
   const int nin = 8 * g.n + 10 * g.D;
-  for (int k = 0; k < ldx; ++k) X[c * ldx + k] = k < nin ? x[k] : 0.f;
+  float* xr = X + c * ldx;
+  for (int k = nin; k < ldx; ++k) xr[k] = 0.f;
+  cell_features(g, mt, w, wmean, c, [&](int k, float v) { xr[k] = v; });
 }
 
 // ---------------------------------------------------------------- inference (BF16 mma.sync)
@@ -164,11 +173,10 @@ __global__ void __launch_bounds__(128) k_mlp_infer(Geom g, MlpTabs mt, const T* 
   const int64_t c = (int64_t)blockIdx.x * 128 + t;
   const bool live = c < g.ncell;
   {
-    float x[MLP_MAXIN];
     const int nin = 8 * g.n + 10 * g.D;
-    if (live) cell_features(g, mt, w, wmean, c, x);
     __nv_bfloat16* xr = Xs + (warp * 32 + lane) * LD1;
-    for (int k = 0; k < KP; ++k) xr[k] = __float2bfloat16_rn(live && k < nin ? x[k] : 0.f);
+    for (int k = live ? nin : 0; k < KP; ++k) xr[k] = __float2bfloat16_rn(0.f);
+    if (live) cell_features(g, mt, w, wmean, c, [&](int k, float v) { xr[k] = __float2bfloat16_rn(v); });
   }
   __syncthreads();
   const int gq = lane >> 2, tq = lane & 3;
