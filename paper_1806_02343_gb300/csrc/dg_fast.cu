@@ -31,20 +31,35 @@ __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fm
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 constexpr int NT = 9 * TC;    // threads per block: one per (variable, cell)
 
-__device__ __forceinline__ int64_t nbr(const FastGeom& g, int64_t c, int a, int dir) {
-  int ix = (int)(c % g.nx);
-  int64_t r = c / g.nx;
-  int iy = (int)(r % g.ny);
-  int iz = (int)(r / g.ny);
-  if (a == 0) ix = (ix + dir + g.nx) % g.nx;
-  else if (a == 1) iy = (iy + dir + g.ny) % g.ny;
-  else iz = (iz + dir + g.nz) % g.nz;
-  return ((int64_t)iz * g.ny + iy) * g.nx + ix;
+// Cell coordinates, computed once per thread in 32-bit arithmetic (cell
+// counts stay below 2^31), and periodic neighbours by add-and-wrap.
+struct Coord {
+  int ix, iy, iz;
+};
+
+__device__ __forceinline__ Coord coord_of(const FastGeom& g, int64_t c) {
+  const unsigned cc = (unsigned)c, nx = (unsigned)g.nx, ny = (unsigned)g.ny;
+  const unsigned r = cc / nx;
+  return Coord{(int)(cc - r * nx), (int)(r % ny), (int)(r / ny)};
+}
+
+__device__ __forceinline__ int64_t nbr(const FastGeom& g, Coord k, int a, int dir) {
+  if (a == 0) {
+    k.ix += dir;
+    k.ix = k.ix < 0 ? k.ix + g.nx : (k.ix >= g.nx ? k.ix - g.nx : k.ix);
+  } else if (a == 1) {
+    k.iy += dir;
+    k.iy = k.iy < 0 ? k.iy + g.ny : (k.iy >= g.ny ? k.iy - g.ny : k.iy);
+  } else {
+    k.iz += dir;
+    k.iz = k.iz < 0 ? k.iz + g.nz : (k.iz >= g.nz ? k.iz - g.nz : k.iz);
+  }
+  return ((int64_t)k.iz * g.ny + k.iy) * g.nx + k.ix;
 }
 
 // ------------------------------------------------------------------ faces
 template <typename T, int DEG, int A>
-__global__ void __launch_bounds__(NT) k_face_glm(const FaceTabs<T, DEG> tb, const FastGeom g,
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_face_glm(const FaceTabs<T, DEG> tb, const FastGeom g,
                                                  const T* __restrict__ w, T* __restrict__ F,
                                                  const DevScalars* __restrict__ sc, T eps) {
   constexpr int N = FastDims<DEG>::N, QF = FastDims<DEG>::QF, NR = 9 * N;
@@ -59,7 +74,7 @@ __global__ void __launch_bounds__(NT) k_face_glm(const FaceTabs<T, DEG> tb, cons
   const int64_t c = c0 + f;
   const bool live = c < g.ncell;
   const int64_t S = g.stride;
-  const int64_t cl = live ? nbr(g, c, A, -1) : 0;
+  const int64_t cl = live ? nbr(g, coord_of(g, c), A, -1) : 0;
   // stage both cells' coefficients (coalesced along cells)
   for (int r = v; r < NR; r += 9) {
     WR[r * TC + f] = live ? w[r * S + c] : T(1);
@@ -105,7 +120,7 @@ __global__ void __launch_bounds__(NT) k_face_glm(const FaceTabs<T, DEG> tb, cons
 enum { SL_RHO = 0, SL_B = 5, SL_PSI = 8, SL_V = 9, SL_PT = 12, SL_VB = 13, SL_EPT = 14, SL_ZERO = 15, NSL = 16 };
 
 template <typename T, int DEG>
-__global__ void __launch_bounds__(NT) k_cell_glm(const CellTabs<T, DEG> tb, const FastGeom g,
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_cell_glm(const CellTabs<T, DEG> tb, const FastGeom g,
                                                  const T* __restrict__ w, const T* __restrict__ F, T* out,
                                                  const T* w0, double ca, double cb, int combine,
                                                  const DevScalars* __restrict__ sc,
@@ -129,7 +144,7 @@ __global__ void __launch_bounds__(NT) k_cell_glm(const CellTabs<T, DEG> tb, cons
   T wl[N];
 #pragma unroll
   for (int l = 0; l < N; ++l) wl[l] = live ? w[(int64_t)(v * N + l) * S + c] : (v == 0 && l == 0 ? T(1) : T(0));
-  if (mix && live) wl[0] = (T)wmean[(int64_t)v * S + c];
+  // (FP32 form: wl[0] is the float mirror of the FP64 mean, an exact copy)
   if (!live && v == 4) wl[0] = T(1);  // keep dummy cells physical (rho = 1, E = 1)
 
   // flux of variable v: f_a = alpha v_a + beta B_a + (a == gax ? gamma_v : 0)
@@ -197,12 +212,13 @@ __global__ void __launch_bounds__(NT) k_cell_glm(const CellTabs<T, DEG> tb, cons
   // cells of the face, so the two contributions cancel exactly -- and adds the
   // six face sums in FP64 (conservation of the cell means to FP64 rounding).
   double mean_acc = 0.0;
+  const Coord kc = coord_of(g, live ? c : 0);
   if (live) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
-        const int64_t fc = s ? nbr(g, c, a, +1) : c;
+        const int64_t fc = s ? nbr(g, kc, a, +1) : c;
         T fs = T(0);
 #pragma unroll
         for (int p = 0; p < QF; ++p) {

@@ -392,6 +392,62 @@ __global__ void k_pos(Geom g, Tables<T> tb, LimTabs lt, T* w, double* wmean, dg_
   const int64_t S = g.stride;
   const int nm = g.glm ? 9 : 8;
   const bool mix = wmean != nullptr;
+  if (mix) {
+    // FP32 form: rigorous screen in the working precision from the float
+    // mirror of the means (|P_l| <= 1, |phi_j,c| <= ldf_maxabs on the cell,
+    // relative margin 1e-4 for the rounding of the bound); cells that clear
+    // the floors everywhere are done without any FP64 work
+    T mt[8];
+    for (int k = 0; k < 5; ++k) mt[k] = w[(int64_t)lmean_row(g, k) * S + c];
+    if (g.glm) {
+      for (int k = 5; k < 8; ++k) mt[k] = w[(int64_t)lmean_row(g, k) * S + c];
+    } else {
+      mt[5] = mt[6] = mt[7] = T(0);
+      for (int j = 0; j < g.D; ++j)
+        for (int cc = 0; cc < g.D; ++cc) mt[5 + cc] += w[(int64_t)(g.ldf0 + j) * S + c] * (T)lt.ldf_mean0[j * 3 + cc];
+      if (g.bz2d >= 0) mt[7] = w[(int64_t)g.bz2d * S + c];
+    }
+    T dv[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+    const int nlg = g.glm ? 8 : 5;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      if (v >= nlg) continue;
+      for (int l = 1; l < g.n; ++l) {
+        const T x = w[(int64_t)(v * g.n + l) * S + c];
+        dv[v] += x < T(0) ? -x : x;
+      }
+    }
+    if (!g.glm) {
+      for (int j = g.D; j < g.ndiv; ++j) {
+        T aj = w[(int64_t)(g.ldf0 + j) * S + c];
+        aj = aj < T(0) ? -aj : aj;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc)
+          if (cc < g.D) dv[5 + cc] += aj * (T)lt.ldf_maxabs[j * 3 + cc];
+      }
+      if (g.bz2d >= 0)
+        for (int l = 1; l < g.n; ++l) {
+          const T x = w[(int64_t)(g.bz2d + l) * S + c];
+          dv[7] += x < T(0) ? -x : x;
+        }
+    }
+    const T mg = T(1e-4);
+#pragma unroll
+    for (int v = 0; v < 8; ++v) dv[v] = dv[v] * (T(1) + mg) + mg * (mt[v] < T(0) ? -mt[v] : mt[v]);
+    const T rlo = mt[0] - dv[0];
+    if (rlo > (T)p.eps_rho * T(2)) {
+      T kin = T(0), mag = T(0);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const T mu = (mt[1 + i] < T(0) ? -mt[1 + i] : mt[1 + i]) + dv[1 + i];
+        const T bu = (mt[5 + i] < T(0) ? -mt[5 + i] : mt[5 + i]) + dv[5 + i];
+        kin += mu * mu;
+        mag += bu * bu;
+      }
+      const T plo = (T)(g.gamma - 1.0) * (mt[4] - dv[4] - T(0.5) * kin / rlo - T(0.5) * mag);
+      if (plo > (T)p.eps_p * T(2) + mg * (mt[4] < T(0) ? -mt[4] : mt[4])) return;
+    }
+  }
   // raw mean rows (Legendre mode 0 / degree-0 LDF weights)
   double mr[9];
   for (int k = 0; k < nm; ++k) mr[k] = mix ? wmean[k * S + c] : (double)w[(int64_t)lmean_row(g, k) * S + c];
@@ -659,8 +715,10 @@ int run_limiter(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t 
       gate = c.troubled;
     }
     c.prof.begin(3, st);
+    // FP32 form: the float mode-0 rows mirror the FP64 means exactly; reading
+    // them avoids FP64 conversions (the limiter never changes the means)
     if (c.p.precision == DG_PREC_FP32MIX)
-      k_tvb<float><<<nb, 128, 0, st>>>(g, c.lim, (float*)w, wmean, troubled, gate, c.p, c.sc);
+      k_tvb<float><<<nb, 128, 0, st>>>(g, c.lim, (float*)w, nullptr, troubled, gate, c.p, c.sc);
     else
       k_tvb<double><<<nb, 128, 0, st>>>(g, c.lim, (double*)w, nullptr, troubled, gate, c.p, c.sc);
     c.prof.end(3, st);

@@ -508,7 +508,7 @@ int mlp_features_launch(Ctx& c, const void* w, const double* wmean, float* X, in
   const Geom& g = c.g;
   const unsigned nb = (unsigned)((g.ncell + 127) / 128);
   if (c.p.precision == DG_PREC_FP32MIX)
-    k_features<float><<<nb, 128, 0, st>>>(g, c.mlp, (const float*)w, wmean, X, ldx);
+    k_features<float><<<nb, 128, 0, st>>>(g, c.mlp, (const float*)w, nullptr, X, ldx);
   else
     k_features<double><<<nb, 128, 0, st>>>(g, c.mlp, (const double*)w, nullptr, X, ldx);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
@@ -557,10 +557,11 @@ static void infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* fl
 int mlp_infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* flag, float* prob, cudaStream_t st) {
   if (!c.mlp_w1) return -1;
   const bool f32 = c.p.precision == DG_PREC_FP32MIX;
+  // FP32 form: features read the float mirror of the FP64 means (exact copies)
   switch (c.mlp_kp) {
 #define KPCASE(K)                                                                 \
   case K:                                                                         \
-    if (f32) infer_launch<float, K>(c, w, wmean, flag, prob, st);                 \
+    if (f32) infer_launch<float, K>(c, w, nullptr, flag, prob, st);               \
     else infer_launch<double, K>(c, w, nullptr, flag, prob, st);                  \
     break;
     KPCASE(64)
