@@ -75,10 +75,25 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_fa
   const bool live = c < g.ncell;
   const int64_t S = g.stride;
   const int64_t cl = live ? nbr(g, coord_of(g, c), A, -1) : 0;
-  // stage both cells' coefficients (coalesced along cells)
-  for (int r = v; r < NR; r += 9) {
-    WR[r * TC + f] = live ? w[r * S + c] : T(1);
-    WL[r * TC + f] = live ? w[r * S + cl] : T(1);
+  // stage both cells' coefficients (coalesced along cells); all loads of a
+  // thread are issued before the first shared-memory store
+  {
+    constexpr int PER = (NR + 8) / 9;
+    T a[PER], b[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int r = v + 9 * i;
+      a[i] = (live && r < NR) ? w[r * S + c] : T(1);
+      b[i] = (live && r < NR) ? w[r * S + cl] : T(1);
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int r = v + 9 * i;
+      if (r < NR) {
+        WR[r * TC + f] = a[i];
+        WL[r * TC + f] = b[i];
+      }
+    }
   }
   __syncthreads();
   // traces: thread (v, f) evaluates variable v of both sides at the QF points
@@ -212,6 +227,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_ce
   // cells of the face, so the two contributions cancel exactly -- and adds the
   // six face sums in FP64 (conservation of the cell means to FP64 rounding).
   double mean_acc = 0.0;
+  T fsum[6];
   const Coord kc = coord_of(g, live ? c : 0);
   if (live) {
 #pragma unroll
@@ -228,9 +244,12 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_ce
 #pragma unroll
           for (int l = 1; l < N; ++l) racc[l] += Fv * tb.Pfw[2 * a + s][l][p];
         }
-        mean_acc += s ? -(double)fs : (double)fs;
+        fsum[2 * a + s] = s ? -fs : fs;
       }
     }
+    // six face sums added in FP64 as a balanced tree (short dependency chain)
+    mean_acc = ((double)fsum[0] + (double)fsum[1]) + ((double)fsum[2] + (double)fsum[3]) +
+               ((double)fsum[4] + (double)fsum[5]);
   }
   if (!live) return;
   const double dt = sc->dt;
