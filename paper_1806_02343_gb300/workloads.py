@@ -314,3 +314,70 @@ def gauss_nodal(fn, n, npts, D=3, stride=None, device="cuda"):
     out = torch.zeros((V, U.shape[1], stride), dtype=torch.float64, device=device)
     out[:, :, : U.shape[-1]] = U
     return out
+
+
+# ---------------------------------------------------------------------------
+# static octree meshes (input description: leaves, refinement and 2:1 balance)
+# ---------------------------------------------------------------------------
+
+
+def octree_leaves(D, base_level, max_level, refine):
+    """Leaves [(level, (i, j[, k]))] of a periodic unit box: start uniform at
+    base_level, split every leaf for which refine(center, dx, level) is true
+    (level by level up to max_level), then split coarse leaves until every face
+    neighbour of a leaf is at most one level coarser (2:1 balance).
+    Returned in Morton (Z-curve) order of the leaf's lower corner."""
+    leaves = set()
+    n0 = 2 ** base_level
+    for k in np.ndindex(*([n0] * D)):
+        leaves.add((base_level, tuple(int(x) for x in k)))
+    for lvl in range(base_level, max_level):
+        new = set()
+        for (l, k) in leaves:
+            if l == lvl:
+                dx = 1.0 / 2 ** l
+                ctr = np.array([(x + 0.5) * dx for x in k])
+                if refine(ctr, dx, l):
+                    for ch in np.ndindex(*([2] * D)):
+                        new.add((l + 1, tuple(2 * x + int(c) for x, c in zip(k, ch))))
+                    continue
+            new.add((l, k))
+        leaves = new
+
+    def cover(l, k):
+        for j in range(l + 1):
+            key = (l - j, tuple(x >> j for x in k))
+            if key in leaves:
+                return key
+        return None
+
+    changed = True
+    while changed:
+        changed = False
+        for (l, k) in list(leaves):
+            if (l, k) not in leaves:
+                continue
+            n = 2 ** l
+            for a in range(D):
+                for s in (-1, 1):
+                    kk = list(k)
+                    kk[a] = (kk[a] + s) % n
+                    cv = cover(l, tuple(kk))
+                    if cv is not None and cv[0] < l - 1:
+                        cl, ck = cv
+                        leaves.discard(cv)
+                        for ch in np.ndindex(*([2] * D)):
+                            leaves.add((cl + 1, tuple(2 * x + int(c) for x, c in zip(ck, ch))))
+                        changed = True
+
+    def morton(item):
+        l, k = item
+        sh = max_level - l
+        key = 0
+        coords = [x << sh for x in k]
+        for bit in range(max_level, -1, -1):
+            for a in range(D - 1, -1, -1):
+                key = (key << 1) | ((coords[a] >> bit) & 1)
+        return (key, l)
+
+    return sorted(leaves, key=morton)
