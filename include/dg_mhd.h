@@ -68,14 +68,24 @@ enum { DG_DIVB_POWELL = 0, DG_DIVB_GLM = 1 };
 enum { DG_PREC_FP64 = 0, DG_PREC_FP32MIX = 1 };
 enum { DG_LIMIT_OFF = 0, DG_LIMIT_TVB = 1, DG_LIMIT_MLP = 2 };
 
-/* Mesh: a uniform periodic box of n[0] x n[1] (x n[2]) cubic cells, cells
- * numbered x-fastest (Sec. 3.1: non-overlapping cubes; the octree of
- * Sec. 4.4 with every leaf on one level). Host memory, copied at init. */
+/* Mesh (Sec. 3.1: non-overlapping cubic cells of an octree, Sec. 4.4).
+ * Uniform (level == NULL): a periodic box of n[0] x n[1] (x n[2]) cells,
+ * numbered x-fastest, cell size box_len / n[0].
+ * Octree (level != NULL): n_leaves leaves of a periodic cube of side box_len;
+ * leaf c has refinement level level[c] (cell size box_len / 2^level) and
+ * integer coordinates ijk[c*dim + a] in [0, 2^level); the leaves must tile
+ * the box without overlap and be 2:1 balanced across faces (DG_E_MESH
+ * otherwise). Cells are numbered in the given order. Host memory, copied at
+ * init. Faces: same-level, and coarse-fine faces integrated at the fine face's
+ * Gauss points (coarse side at the mapped sub-face points, weights / 2^(dim-1)). */
 typedef struct {
-  int dim;            /* 2 or 3                                             */
-  int32_t n[3];       /* cells per axis (n[2] ignored for dim 2)            */
-  double box_len;     /* physical side length of a cell row along x: n[0]*dx */
-  int periodic;       /* must be 1                                           */
+  int dim;               /* 2 or 3                                             */
+  int32_t n[3];          /* uniform: cells per axis (n[2] ignored for dim 2)   */
+  double box_len;        /* uniform: n[0]*dx; octree: side of the cube         */
+  int periodic;          /* must be 1                                          */
+  int64_t n_leaves;      /* octree: number of leaves                           */
+  const int8_t* level;   /* octree: n_leaves levels (NULL: uniform mesh)       */
+  const int32_t* ijk;    /* octree: n_leaves*dim integer coordinates           */
 } dg_mesh_desc;
 
 /* Parameters of Sec. 3.6, 4.1, 4.2, 4.3, 5.1 (defaults in brackets). */

@@ -31,7 +31,8 @@ KIND_FACE, KIND_CELL, KIND_DT, KIND_LIMIT, KIND_PROJECT, KIND_POSITIVITY, KIND_M
 
 class MeshDesc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int32 * 3), ("box_len", ctypes.c_double),
-                ("periodic", ctypes.c_int)]
+                ("periodic", ctypes.c_int), ("n_leaves", ctypes.c_int64),
+                ("level", ctypes.POINTER(ctypes.c_int8)), ("ijk", ctypes.POINTER(ctypes.c_int32))]
 
 
 class Params(ctypes.Structure):
@@ -115,6 +116,7 @@ def _stream():
 
 def mesh_desc(dim, n, box_len=1.0) -> MeshDesc:
     m = MeshDesc()
+    m.n_leaves = 0
     m.dim = dim
     nn = list(n) + [1] * (3 - len(n))
     for a in range(3):
@@ -164,16 +166,25 @@ class Solver:
     """Owns one dg_mhd_ctx. State tensors are allocated by the caller (torch) with
     the layout reported by dg_mhd_state_layout: w[row][cell_stride]."""
 
-    def __init__(self, dim, n, degree, divb, gamma=5.0 / 3.0, box_len=1.0, **params):
+    def __init__(self, dim, n, degree, divb, gamma=5.0 / 3.0, box_len=1.0, leaves=None, **params):
+        """n: cells per axis of a uniform box, or None with `leaves` =
+        [(level, (i, j[, k]))] for an octree mesh of a cube of side box_len."""
+        import numpy as np
         import torch
         L = lib()
         m = MeshDesc()
         m.dim = dim
-        nn = list(n) + [1] * (3 - len(n))
+        nn = (list(n) if n is not None else [1, 1, 1]) + [1] * (3 - len(n or []))
         for a in range(3):
             m.n[a] = nn[a]
         m.box_len = box_len
         m.periodic = 1
+        if leaves is not None:
+            self._lev = np.ascontiguousarray(np.array([l for l, _ in leaves], dtype=np.int8))
+            self._ijk = np.ascontiguousarray(np.array([k for _, k in leaves], dtype=np.int32).reshape(-1))
+            m.n_leaves = len(leaves)
+            m.level = self._lev.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
+            m.ijk = self._ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         self.params = default_params(**params)
         self.divb = divb
         h = ctypes.c_void_p()

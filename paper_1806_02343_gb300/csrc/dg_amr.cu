@@ -1,0 +1,566 @@
+// Static octree meshes (Sec. 4.4): face lists, coarse-fine sub-face tables
+// and the face-list kernels of the DG operator (Sec. 3.5 eq. wdot).
+//
+// Faces: same-level faces once (from the right cell's -a side); coarse-fine
+// faces once per fine cell side, integrated at the FINE face's Gauss points.
+// The coarse side evaluates its state at the same physical points, i.e. at
+// reference coordinates xi_t = (xi_t,fine + (bit ? 1 : -1)) / 2 of its own
+// face, and weighs them by w_p / 2^(D-1) (its reference face measure is 2^(D-1)
+// times larger). F* is computed once per point and used by both cells, so the
+// discretisation stays conservative. Each cell uses its own metric 2/dx_K.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+#include <vector>
+
+#include "dg_amr.cuh"
+#include "dg_phys.cuh"
+
+namespace dgmhd {
+
+namespace {
+
+constexpr int WPB = 4;  // warps (cells) per block
+
+__device__ __forceinline__ int mrow_a(const Geom& g, int m) {
+  if (g.glm) return m * g.n;
+  if (m < 5) return m * g.n;
+  if (g.D == 3) return g.ldf0 + (m - 5);
+  return m < 7 ? g.ldf0 + (m - 5) : g.bz2d;
+}
+
+__device__ __forceinline__ int mindex_a(const Geom& g, int r) {
+  const int nm = g.glm ? 9 : 8;
+  for (int m = 0; m < nm; ++m)
+    if (mrow_a(g, m) == r) return m;
+  return -1;
+}
+
+template <typename T, typename F>
+__device__ __forceinline__ void eval_pt(const Geom& g, const T* __restrict__ P, const T* __restrict__ L, int npt,
+                                        int pt, F coef, T* u) {
+  for (int v = 0; v < g.V; ++v) u[v] = T(0);
+  const int nleg = g.glm ? 9 : 5;
+  for (int v = 0; v < nleg; ++v) {
+    T s = T(0);
+    for (int l = 0; l < g.n; ++l) s += coef(v * g.n + l) * P[l * npt + pt];
+    u[v] = s;
+  }
+  if (!g.glm) {
+    T b[3] = {T(0), T(0), T(0)};
+    for (int j = 0; j < g.ndiv; ++j) {
+      const T wj = coef(g.ldf0 + j);
+      for (int c = 0; c < g.DB; ++c) b[c] += wj * L[(j * g.DB + c) * npt + pt];
+    }
+    for (int c = 0; c < g.DB; ++c) u[5 + c] = b[c];
+    if (g.bz2d >= 0) {
+      T s = T(0);
+      for (int l = 0; l < g.n; ++l) s += coef(g.bz2d + l) * P[l * npt + pt];
+      u[7] = s;
+    }
+  }
+}
+
+// table of side (cell is L: its +a face; R: its -a face), standard or sub-face
+template <typename T>
+struct SideTab {
+  const T* P;
+  const T* L;
+  bool coarse;
+};
+
+template <typename T>
+__device__ __forceinline__ SideTab<T> side_tab(const Geom& g, const Tables<T>& tb, const AmrDev<T>& am, int meta,
+                                              int side) {
+  const int a = meta & 3, kind = (meta >> 2) & 3, sub = meta >> 4;
+  const int f = side == 0 ? 2 * a + 1 : 2 * a;
+  const bool coarse = (side == 0 && kind == 1) || (side == 1 && kind == 2);
+  SideTab<T> t;
+  if (coarse) {
+    t.P = am.Psub + ((size_t)(f * am.nsub + sub) * g.n) * g.Qf;
+    t.L = am.Lsub + ((size_t)(f * am.nsub + sub) * g.ndiv * g.DB) * g.Qf;
+  } else {
+    t.P = tb.Pf + (size_t)f * g.n * g.Qf;
+    t.L = tb.Lf + (size_t)f * g.ndiv * g.DB * g.Qf;
+  }
+  t.coarse = coarse;
+  return t;
+}
+
+template <typename T>
+__global__ void k_face_list(Geom g, Tables<T> tb, AmrDev<T> am, const T* __restrict__ w, T* __restrict__ fbuf,
+                            const DevScalars* __restrict__ sc, T eps) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= am.nface * g.Qf) return;
+  const int64_t f = tid / g.Qf;
+  const int p = (int)(tid % g.Qf);
+  const int meta = am.fmeta[f];
+  const int a = meta & 3;
+  const int64_t cL = am.fL[f], cR = am.fR[f], S = g.stride;
+  const SideTab<T> tl = side_tab(g, tb, am, meta, 0), tr = side_tab(g, tb, am, meta, 1);
+  T uL[MAXV], uR[MAXV], F[MAXV];
+  eval_pt(g, tl.P, tl.L, g.Qf, p, [&](int r) { return w[r * S + cL]; }, uL);
+  eval_pt(g, tr.P, tr.L, g.Qf, p, [&](int r) { return w[r * S + cR]; }, uR);
+  const T ch = g.glm ? (T)sc->ch : T(0);
+  const T bnF = face_flux(uL, uR, a, (T)g.gamma, g.glm != 0, ch, eps, F);
+  T* o = fbuf + tid * 9;
+  for (int k = 0; k < g.V; ++k) o[k] = F[k];
+  if (!g.glm) o[8] = bnF;
+}
+
+template <typename T>
+__global__ void k_cell_list(Geom g, Tables<T> tb, AmrDev<T> am, const T* __restrict__ w,
+                            const T* __restrict__ fbuf, T* out, const T* w0, double ca, double cb, int combine,
+                            const DevScalars* __restrict__ sc, const double* __restrict__ wmean, const double* w0mean,
+                            double* outmean) {
+  // out / outmean may alias w0 / w0mean: each element is read, then written, by one lane.
+  extern __shared__ unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t c = (int64_t)blockIdx.x * WPB + warp;
+  const int per_warp = g.nrows + g.D * g.V * g.Qv + am.maxent * g.Qf * g.V + am.maxent * g.Qf;
+  T* wc = reinterpret_cast<T*>(smraw) + (size_t)warp * per_warp;
+  T* G = wc + g.nrows;
+  T* FS = G + g.D * g.V * g.Qv;
+  T* PJ = FS + am.maxent * g.Qf * g.V;
+  if (c >= g.ncell) return;
+  const int64_t S = g.stride;
+  const bool mix = wmean != nullptr;
+  for (int r = lane; r < g.nrows; r += 32) wc[r] = w[r * S + c];
+  __syncwarp();
+  if (mix && lane < (g.glm ? 9 : 8)) wc[mrow_a(g, lane)] = (T)wmean[lane * S + c];
+  __syncwarp();
+  const T gamma = (T)g.gamma;
+  const T ch = g.glm ? (T)sc->ch : T(0);
+  for (int q = lane; q < g.Qv; q += 32) {
+    T u[MAXV];
+    eval_pt(g, tb.Pv, tb.Lv, g.Qv, q, [&](int r) { return wc[r]; }, u);
+    const T wq = tb.wv[q];
+    for (int a = 0; a < g.D; ++a) {
+      T f[MAXV];
+      flux_dir(u, a, gamma, g.glm != 0, ch * ch, f);
+      for (int v = 0; v < g.V; ++v) G[(a * g.V + v) * g.Qv + q] = wq * f[v];
+    }
+  }
+  const int e0 = am.cstart[c], ne = am.cstart[c + 1] - e0;
+  const T subw = T(1) / T(am.nsub);
+  for (int idx = lane; idx < ne * g.Qf; idx += 32) {
+    const int e = idx / g.Qf, p = idx % g.Qf;
+    const int ent = am.centry[e0 + e];
+    const int64_t f = ent >> 1;
+    const int side = ent & 1;
+    const int meta = am.fmeta[f];
+    const int a = meta & 3;
+    const SideTab<T> t = side_tab(g, tb, am, meta, side);
+    const T* F = fbuf + (f * g.Qf + p) * 9;
+    // outward normal: +e_a for the left cell, -e_a for the right cell
+    const T sgn = side == 0 ? T(1) : T(-1);
+    const T wp = tb.wf[p] * (t.coarse ? subw : T(1));
+    for (int v = 0; v < g.V; ++v) FS[(e * g.Qf + p) * g.V + v] = sgn * wp * F[v];
+    if (!g.glm) {
+      T ba = T(0);
+      for (int j = 0; j < g.ndiv; ++j) ba += wc[g.ldf0 + j] * t.L[(j * g.DB + a) * g.Qf + p];
+      PJ[e * g.Qf + p] = wp * sgn * (F[8] - ba);
+    }
+  }
+  __syncwarp();
+  T qv[MAXV];
+  if (!g.glm) {
+    const T rho = wc[0];
+    const T vx = wc[g.n] / rho, vy = wc[2 * g.n] / rho, vz = wc[3 * g.n] / rho;
+    T b[3] = {T(0), T(0), T(0)};
+    for (int j = 0; j < g.DB; ++j)
+      for (int cc = 0; cc < g.DB; ++cc) b[cc] += wc[g.ldf0 + j] * tb.L0[j * g.DB + cc];
+    if (g.bz2d >= 0) b[2] = wc[g.bz2d];
+    qv[0] = T(0); qv[1] = b[0]; qv[2] = b[1]; qv[3] = b[2];
+    qv[4] = vx * b[0] + vy * b[1] + vz * b[2];
+    qv[5] = vx; qv[6] = vy; qv[7] = vz; qv[8] = T(0);
+  }
+  const double dt = sc->dt;
+  const double kappa = g.glm ? sc->kappa : 0.0;
+  const double metric = 2.0 / am.dxc[c];
+  for (int r = lane; r < g.nrows; r += 32) {
+    double acc = 0.0;
+    const bool ldf = g.ldf0 >= 0 && r >= g.ldf0 && r < g.ldf0 + g.ndiv;
+    if (!ldf) {
+      const int v = (g.bz2d >= 0 && r >= g.bz2d) ? 7 : r / g.n;
+      const int l = (g.bz2d >= 0 && r >= g.bz2d) ? r - g.bz2d : r % g.n;
+      T s = T(0);
+      if (l != 0)
+        for (int a = 0; a < g.D; ++a) {
+          const T* Gp = G + (a * g.V + v) * g.Qv;
+          const T* Dp = tb.dPv + ((size_t)a * g.n + l) * g.Qv;
+          for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
+        }
+      acc += (double)s;
+      for (int e = 0; e < ne; ++e) {
+        const int ent = am.centry[e0 + e];
+        const SideTab<T> t = side_tab(g, tb, am, am.fmeta[ent >> 1], ent & 1);
+        const T* Pp = t.P + (size_t)l * g.Qf;
+        T sf = T(0);
+        for (int p = 0; p < g.Qf; ++p) {
+          T term = FS[(e * g.Qf + p) * g.V + v];
+          if (!g.glm) term += PJ[e * g.Qf + p] * qv[v];
+          sf += term * Pp[p];
+        }
+        acc -= (double)sf;
+      }
+    } else {
+      const int j = r - g.ldf0;
+      T s = T(0);
+      for (int a = 0; a < g.D; ++a)
+        for (int cc = 0; cc < g.DB; ++cc) {
+          const T* Gp = G + (a * g.V + 5 + cc) * g.Qv;
+          const T* Dp = tb.dLv + (((size_t)a * g.ndiv + j) * g.DB + cc) * g.Qv;
+          for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
+        }
+      acc += (double)s;
+      for (int e = 0; e < ne; ++e) {
+        const int ent = am.centry[e0 + e];
+        const SideTab<T> t = side_tab(g, tb, am, am.fmeta[ent >> 1], ent & 1);
+        T sf = T(0);
+        for (int cc = 0; cc < g.DB; ++cc) {
+          const T* Lp = t.L + ((size_t)j * g.DB + cc) * g.Qf;
+          for (int p = 0; p < g.Qf; ++p)
+            sf += (FS[(e * g.Qf + p) * g.V + 5 + cc] + PJ[e * g.Qf + p] * qv[5 + cc]) * Lp[p];
+        }
+        acc -= (double)sf;
+      }
+    }
+    double rhs = metric * (double)tb.minv[r] * acc;
+    if (g.glm && r >= 8 * g.n) rhs -= kappa * (double)wc[r];
+    const int m = mix ? mindex_a(g, r) : -1;
+    if (!combine) {
+      out[r * S + c] = (T)rhs;
+      if (m >= 0) outmean[m * S + c] = rhs;
+    } else if (m >= 0) {
+      const double o = ca * w0mean[m * S + c] + cb * (wmean[m * S + c] + dt * rhs);
+      outmean[m * S + c] = o;
+      out[r * S + c] = (T)o;
+    } else {
+      out[r * S + c] = (T)(ca * (double)w0[r * S + c] + cb * ((double)wc[r] + dt * rhs));
+    }
+  }
+}
+
+// |B^n_F - B^n_K| weighted by w_p at every face point, for both sides
+template <typename T>
+__global__ void k_divb_list(Geom g, Tables<T> tb, AmrDev<T> am, const T* __restrict__ w, T* __restrict__ jbuf) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= am.nface * g.Qf) return;
+  const int64_t f = tid / g.Qf;
+  const int p = (int)(tid % g.Qf);
+  const int meta = am.fmeta[f];
+  const int a = meta & 3;
+  const int64_t cL = am.fL[f], cR = am.fR[f], S = g.stride;
+  const SideTab<T> tl = side_tab(g, tb, am, meta, 0), tr = side_tab(g, tb, am, meta, 1);
+  T rL = T(0), rR = T(0), bL = T(0), bR = T(0);
+  for (int l = 0; l < g.n; ++l) {
+    rL += w[l * S + cL] * tl.P[l * g.Qf + p];
+    rR += w[l * S + cR] * tr.P[l * g.Qf + p];
+  }
+  for (int j = 0; j < g.ndiv; ++j) {
+    bL += w[(g.ldf0 + j) * S + cL] * tl.L[(j * g.DB + a) * g.Qf + p];
+    bR += w[(g.ldf0 + j) * S + cR] * tr.L[(j * g.DB + a) * g.Qf + p];
+  }
+  const T bF = bn_face(rL, rR, bL, bR);
+  const T wp = tb.wf[p];
+  jbuf[tid * 2 + 0] = wp * (bF > bL ? bF - bL : bL - bF);
+  jbuf[tid * 2 + 1] = wp * (bF > bR ? bF - bR : bR - bF);
+}
+
+__device__ __forceinline__ unsigned long long dbits_a(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+template <typename T>
+__global__ void k_dt_list(Geom g, Tables<T> tb, AmrDev<T> am, const T* __restrict__ w,
+                          const double* __restrict__ wmean, const T* __restrict__ jbuf, dg_mhd_params p,
+                          DevScalars* __restrict__ sc) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double dtc = DBL_MAX, smax = 0.0;
+  if (c < g.ncell) {
+    const int64_t S = g.stride;
+    auto mean = [&](int m) { return wmean ? wmean[m * S + c] : (double)w[(int64_t)mrow_a(g, m) * S + c]; };
+    const double rho = mean(0);
+    const double vx = mean(1) / rho, vy = mean(2) / rho, vz = mean(3) / rho;
+    const double E = mean(4);
+    double b[3];
+    if (g.glm) {
+      b[0] = mean(5); b[1] = mean(6); b[2] = mean(7);
+    } else {
+      b[0] = b[1] = b[2] = 0.0;
+      for (int j = 0; j < g.DB; ++j)
+        for (int cc = 0; cc < g.DB; ++cc) b[cc] += mean(5 + j) * (double)tb.L0[j * g.DB + cc];
+      if (g.bz2d >= 0) b[2] = mean(7);
+    }
+    const double dx = am.dxc[c];
+    const double b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    const double pr = (g.gamma - 1.0) * (E - 0.5 * rho * (vx * vx + vy * vy + vz * vz) - 0.5 * b2);
+    const double cs = sqrt(g.gamma * pr / rho + b2 / rho);
+    const double av[3] = {fabs(vx), fabs(vy), fabs(vz)};
+    double s = 0.0;
+    for (int a = 0; a < g.D; ++a) s += (av[a] + cs) / dx;
+    dtc = p.cfl / (2.0 * g.d + 1.0) / s;
+    smax = s * dx / g.D;
+    if (!g.glm) {
+      double acc = 0.0;
+      for (int e = am.cstart[c]; e < am.cstart[c + 1]; ++e) {
+        const int ent = am.centry[e];
+        const int64_t f = ent >> 1;
+        const double dxf = fmin(am.dxc[am.fL[f]], am.dxc[am.fR[f]]);
+        double area = 1.0;
+        for (int a = 0; a < g.D - 1; ++a) area *= 0.5 * dxf;
+        double js = 0.0;
+        for (int q = 0; q < g.Qf; ++q) js += (double)jbuf[(f * g.Qf + q) * 2 + (ent & 1)];
+        acc += area * js;
+      }
+      double divb = acc;
+      for (int a = 0; a < g.D; ++a) divb /= dx;
+      const double rate = divb * fabs(vx * b[0] + vy * b[1] + vz * b[2]) / E;
+      if (rate > 0.0) dtc = fmin(dtc, p.eta_powell / rate);
+    }
+    if (!(dtc > 0.0) || !isfinite(dtc)) {
+      atomicOr(&sc->status, 1);
+      dtc = DBL_MAX;
+    }
+  }
+  __shared__ double red[256];
+  __shared__ double reds[256];
+  red[threadIdx.x] = dtc;
+  reds[threadIdx.x] = smax;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + o]);
+      reds[threadIdx.x] = fmax(reds[threadIdx.x], reds[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicMin(&sc->dt_bits, dbits_a(red[0]));
+    atomicMax(&sc->smax_bits, dbits_a(reds[0]));
+  }
+}
+
+template <typename T>
+int upload_vec(T** dst, const std::vector<T>& v) {
+  if (cudaMalloc(dst, std::max<size_t>(1, v.size()) * sizeof(T)) != cudaSuccess) return DG_E_CUDA;
+  if (!v.empty() && cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    return DG_E_CUDA;
+  return DG_OK;
+}
+
+}  // namespace
+
+// -------------------------------------------------------------------- host
+int build_amr(Ctx& c, const dg_mesh_desc* mesh) {
+  Geom& g = c.g;
+  const int D = mesh->dim;
+  const int64_t N = mesh->n_leaves;
+  if (N < 1 || N > ((int64_t)1 << 30)) return DG_E_MESH;
+  // key: level and coordinates (levels <= 20 so coordinates fit 21 bits)
+  auto key = [&](int l, int64_t i, int64_t j, int64_t k) -> uint64_t {
+    return ((uint64_t)l << 58) | ((uint64_t)i << 38) | ((uint64_t)j << 18) | (uint64_t)k;
+  };
+  std::unordered_map<uint64_t, int32_t> idx;
+  idx.reserve((size_t)N * 2);
+  int maxl = 0;
+  for (int64_t cidx = 0; cidx < N; ++cidx) {
+    const int l = mesh->level[cidx];
+    if (l < 0 || l > 17) return DG_E_MESH;
+    maxl = std::max(maxl, l);
+    int64_t k[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) {
+      k[a] = mesh->ijk[cidx * D + a];
+      if (k[a] < 0 || k[a] >= ((int64_t)1 << l)) return DG_E_MESH;
+    }
+    if (!idx.emplace(key(l, k[0], k[1], k[2]), (int32_t)cidx).second) return DG_E_MESH;  // duplicate
+  }
+  // complete, non-overlapping cover: volumes sum to the box and no leaf has a leaf ancestor
+  unsigned long long vol = 0;
+  for (int64_t cidx = 0; cidx < N; ++cidx) {
+    const int l = mesh->level[cidx];
+    vol += 1ull << (D * (maxl - l));
+    int64_t k[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) k[a] = mesh->ijk[cidx * D + a];
+    for (int j = 1; j <= l; ++j)
+      if (idx.count(key(l - j, k[0] >> j, k[1] >> j, k[2] >> j))) return DG_E_MESH;
+  }
+  if (vol != (1ull << (D * maxl))) return DG_E_MESH;
+  // faces
+  std::vector<int32_t> fL, fR, fmeta;
+  std::vector<std::vector<int32_t>> cell_ent(N);
+  for (int64_t cidx = 0; cidx < N; ++cidx) {
+    const int l = mesh->level[cidx];
+    const int64_t n = (int64_t)1 << l;
+    int64_t k[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) k[a] = mesh->ijk[cidx * D + a];
+    for (int a = 0; a < D; ++a) {
+      int others[2], no = 0;
+      for (int b = 0; b < D; ++b)
+        if (b != a) others[no++] = b;
+      for (int s = -1; s <= 1; s += 2) {
+        int64_t kk[3] = {k[0], k[1], k[2]};
+        kk[a] = (kk[a] + s + n) % n;
+        auto it = idx.find(key(l, kk[0], kk[1], kk[2]));
+        if (it != idx.end()) {
+          if (s < 0) {
+            fL.push_back(it->second);
+            fR.push_back((int32_t)cidx);
+            fmeta.push_back(a);
+          }
+          continue;
+        }
+        if (l > 0) {
+          auto ip = idx.find(key(l - 1, kk[0] >> 1, kk[1] >> 1, kk[2] >> 1));
+          if (ip != idx.end()) {
+            int sub = 0;
+            for (int j = 0; j < no; ++j) sub |= (int)(k[others[j]] & 1) << j;
+            if (s < 0) {
+              fL.push_back(ip->second);
+              fR.push_back((int32_t)cidx);
+              fmeta.push_back(a | (1 << 2) | (sub << 4));
+            } else {
+              fL.push_back((int32_t)cidx);
+              fR.push_back(ip->second);
+              fmeta.push_back(a | (2 << 2) | (sub << 4));
+            }
+            continue;
+          }
+        }
+        // refined neighbour: all adjacent children must be leaves (2:1 balance)
+        for (int t = 0; t < (1 << (D - 1)); ++t) {
+          int64_t ch[3] = {2 * kk[0], 2 * kk[1], 2 * kk[2]};
+          ch[a] += s < 0 ? 1 : 0;
+          for (int j = 0; j < no; ++j) ch[others[j]] += (t >> j) & 1;
+          if (!idx.count(key(l + 1, ch[0], ch[1], ch[2]))) return DG_E_MESH;
+        }
+      }
+    }
+  }
+  const int64_t nf = (int64_t)fL.size();
+  for (int64_t f = 0; f < nf; ++f) {
+    cell_ent[fL[f]].push_back((int32_t)(f << 1));
+    cell_ent[fR[f]].push_back((int32_t)((f << 1) | 1));
+  }
+  std::vector<int32_t> cstart(N + 1, 0), centry;
+  int maxent = 0;
+  for (int64_t cidx = 0; cidx < N; ++cidx) {
+    cstart[cidx + 1] = cstart[cidx] + (int32_t)cell_ent[cidx].size();
+    maxent = std::max(maxent, (int)cell_ent[cidx].size());
+    for (int32_t e : cell_ent[cidx]) centry.push_back(e);
+  }
+  std::vector<double> dxc(N);
+  for (int64_t cidx = 0; cidx < N; ++cidx) dxc[cidx] = mesh->box_len / (double)(1ll << mesh->level[cidx]);
+  // sub-face tables (coarse side), for each face f of the coarse cell and sub-face s
+  const Basis& B = *c.hb;
+  std::vector<double> x1, w1;
+  gauss_legendre(g.nq1, x1, w1);
+  const int nsub = 1 << (D - 1);
+  std::vector<double> Ps((size_t)2 * D * nsub * g.n * g.Qf, 0.0);
+  std::vector<double> Ls((size_t)std::max(1, 2 * D * nsub * g.ndiv * g.DB * g.Qf), 0.0);
+  for (int f = 0; f < 2 * D; ++f) {
+    const int a = f >> 1;
+    int others[2], no = 0;
+    for (int b = 0; b < D; ++b)
+      if (b != a) others[no++] = b;
+    for (int sb = 0; sb < nsub; ++sb)
+      for (int p = 0; p < g.Qf; ++p) {
+        double xi[3] = {0, 0, 0};
+        int pp = p;
+        for (int j = no - 1; j >= 0; --j) {
+          const double xf = x1[pp % g.nq1];
+          pp /= g.nq1;
+          xi[others[j]] = 0.5 * (xf + (((sb >> j) & 1) ? 1.0 : -1.0));
+        }
+        xi[a] = (f & 1) ? 1.0 : -1.0;
+        for (int l = 0; l < g.n; ++l) Ps[((size_t)(f * nsub + sb) * g.n + l) * g.Qf + p] = B.eval(B.leg[l], xi);
+        for (int j = 0; j < g.ndiv; ++j)
+          for (int cc = 0; cc < g.DB; ++cc)
+            Ls[(((size_t)(f * nsub + sb) * g.ndiv + j) * g.DB + cc) * g.Qf + p] = B.eval(B.ldf[j][cc], xi);
+      }
+  }
+  AmrHost& h = c.amr;
+  h.on = true;
+  h.nface = nf;
+  h.maxent = maxent;
+  h.nsub = nsub;
+  int e;
+  if ((e = upload_vec(&h.fL, fL)) || (e = upload_vec(&h.fR, fR)) || (e = upload_vec(&h.fmeta, fmeta)) ||
+      (e = upload_vec(&h.cstart, cstart)) || (e = upload_vec(&h.centry, centry)) || (e = upload_vec(&h.dxc, dxc)))
+    return e;
+  std::vector<float> Psf(Ps.begin(), Ps.end()), Lsf(Ls.begin(), Ls.end());
+  if ((e = upload_vec(&h.Psub64, Ps)) || (e = upload_vec(&h.Lsub64, Ls)) || (e = upload_vec(&h.Psub32, Psf)) ||
+      (e = upload_vec(&h.Lsub32, Lsf)))
+    return e;
+  double dmin = DBL_MAX;
+  for (double d : dxc) dmin = std::min(dmin, d);
+  g.dx = dmin;
+  return DG_OK;
+}
+
+void free_amr(Ctx& c) {
+  AmrHost& h = c.amr;
+  void* ptrs[] = {h.fL, h.fR, h.fmeta, h.cstart, h.centry, h.dxc, h.Psub64, h.Lsub64, h.Psub32, h.Lsub32};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  h = AmrHost();
+}
+
+template <typename T>
+AmrDev<T> amr_dev(const Ctx& c);
+template <>
+AmrDev<double> amr_dev<double>(const Ctx& c) {
+  const AmrHost& h = c.amr;
+  return AmrDev<double>{h.fL, h.fR, h.fmeta, h.cstart, h.centry, h.dxc, h.Psub64, h.Lsub64, h.nface, h.maxent, h.nsub};
+}
+template <>
+AmrDev<float> amr_dev<float>(const Ctx& c) {
+  const AmrHost& h = c.amr;
+  return AmrDev<float>{h.fL, h.fR, h.fmeta, h.cstart, h.centry, h.dxc, h.Psub32, h.Lsub32, h.nface, h.maxent, h.nsub};
+}
+
+template <typename T>
+void launch_amr_operator(const Ctx& c, const Tables<T>& tb, const T* w, T* fbuf, T* out, const T* w0, double ca,
+                         double cb, int combine, const DevScalars* sc, const double* wmean, const double* w0mean,
+                         double* outmean, double eps, cudaStream_t st) {
+  const Geom& g = c.g;
+  const AmrDev<T> am = amr_dev<T>(c);
+  const int64_t np = am.nface * g.Qf;
+  k_face_list<T><<<(unsigned)((np + 127) / 128), 128, 0, st>>>(g, tb, am, w, fbuf, sc, (T)eps);
+  const int per_warp = g.nrows + g.D * g.V * g.Qv + am.maxent * g.Qf * g.V + am.maxent * g.Qf;
+  const size_t sm = (size_t)per_warp * WPB * sizeof(T);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_cell_list<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_cell_list<T><<<(unsigned)((g.ncell + WPB - 1) / WPB), 32 * WPB, sm, st>>>(g, tb, am, w, fbuf, out, w0, ca, cb,
+                                                                              combine, sc, wmean, w0mean, outmean);
+}
+
+template <typename T>
+void launch_amr_dt(const Ctx& c, const Tables<T>& tb, const T* w, const double* wmean, T* jbuf,
+                   const dg_mhd_params& p, DevScalars* sc, cudaStream_t st) {
+  const Geom& g = c.g;
+  const AmrDev<T> am = amr_dev<T>(c);
+  if (!g.glm) {
+    const int64_t np = am.nface * g.Qf;
+    k_divb_list<T><<<(unsigned)((np + 127) / 128), 128, 0, st>>>(g, tb, am, w, jbuf);
+  }
+  k_dt_list<T><<<(unsigned)((g.ncell + 255) / 256), 256, 0, st>>>(g, tb, am, w, wmean, jbuf, p, sc);
+}
+
+template void launch_amr_operator<double>(const Ctx&, const Tables<double>&, const double*, double*, double*,
+                                          const double*, double, double, int, const DevScalars*, const double*,
+                                          const double*, double*, double, cudaStream_t);
+template void launch_amr_operator<float>(const Ctx&, const Tables<float>&, const float*, float*, float*,
+                                         const float*, double, double, int, const DevScalars*, const double*,
+                                         const double*, double*, double, cudaStream_t);
+template void launch_amr_dt<double>(const Ctx&, const Tables<double>&, const double*, const double*, double*,
+                                    const dg_mhd_params&, DevScalars*, cudaStream_t);
+template void launch_amr_dt<float>(const Ctx&, const Tables<float>&, const float*, const double*, float*,
+                                   const dg_mhd_params&, DevScalars*, cudaStream_t);
+
+}  // namespace dgmhd

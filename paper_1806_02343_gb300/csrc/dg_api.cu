@@ -1,6 +1,7 @@
 // C ABI of the DG-MHD library (see include/dg_mhd.h for the contract).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -8,6 +9,7 @@
 #include <vector>
 
 #include "../../include/dg_mhd.h"
+#include "dg_amr.cuh"
 #include "dg_basis.h"
 #include "dg_ctx.h"
 #include "dg_fast.cuh"
@@ -224,6 +226,7 @@ namespace dgmhd {
 // no context (the allocation-free entry point); mirrors the set-up in init.
 int make_geom(const dg_mesh_desc* mesh, int degree, int divB_scheme, double gamma, Basis& B, Geom& g) {
   if (mesh->dim != 2 && mesh->dim != 3) return DG_E_MESH;
+  if (mesh->level) return DG_E_UNSUPPORTED;  // uniform meshes only
   if (!mesh->periodic) return DG_E_UNSUPPORTED;
   if (degree < 0 || degree > MAXD) return DG_E_UNSUPPORTED;
   if (divB_scheme != DG_DIVB_POWELL && divB_scheme != DG_DIVB_GLM) return DG_E_ARG;
@@ -379,6 +382,7 @@ void dg_mhd_destroy(dg_mhd_ctx* ctx) {
   if (!ctx) return;
   Ctx& c = ctx->c;
   c.prof.release();
+  free_amr(c);
   free_fast_tabs(c);
   free_tables(c.t64);
   free_tables(c.t32);
@@ -400,14 +404,19 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
   if (degree < 0 || degree > MAXD) return DG_E_UNSUPPORTED;
   if (divB_scheme != DG_DIVB_POWELL && divB_scheme != DG_DIVB_GLM) return DG_E_ARG;
   if (!(gamma > 1.0)) return DG_E_ARG;
-  for (int a = 0; a < mesh->dim; ++a)
-    if (mesh->n[a] < 1) return DG_E_MESH;
+  const bool octree = mesh->level != nullptr;
+  if (octree && !mesh->ijk) return DG_E_MESH;
+  if (!octree)
+    for (int a = 0; a < mesh->dim; ++a)
+      if (mesh->n[a] < 1) return DG_E_MESH;
   if (!(mesh->box_len > 0.0)) return DG_E_MESH;
   dg_mhd_params prm;
   if (p) prm = *p;
   else dg_mhd_default_params(&prm);
   if (prm.precision != DG_PREC_FP64 && prm.precision != DG_PREC_FP32MIX) return DG_E_ARG;
   if (!(prm.cfl > 0.0) || !(prm.cfl_glm > 0.0)) return DG_E_ARG;
+  // octree meshes: a global, time-independent c_h (Sec. 4.1.5)
+  if (octree && divB_scheme == DG_DIVB_GLM && !(prm.c_h_fixed > 0.0)) return DG_E_ARG;
 
   dg_mhd_ctx* ctx = new (std::nothrow) dg_mhd_ctx();
   if (!ctx) return DG_E_ARG;
@@ -443,13 +452,20 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
       g.nrows += g.n;
     }
   }
-  g.nx = mesh->n[0];
-  g.ny = mesh->n[1];
-  g.nz = g.D == 3 ? mesh->n[2] : 1;
-  g.ncell = (int64_t)g.nx * g.ny * g.nz;
+  g.nx = octree ? 1 : mesh->n[0];
+  g.ny = octree ? 1 : mesh->n[1];
+  g.nz = octree ? 1 : (g.D == 3 ? mesh->n[2] : 1);
+  g.ncell = octree ? mesh->n_leaves : (int64_t)g.nx * g.ny * g.nz;
   g.stride = (g.ncell + 31) / 32 * 32;
-  g.dx = mesh->box_len / g.nx;
+  g.dx = octree ? mesh->box_len : mesh->box_len / g.nx;
   g.gamma = gamma;
+  if (octree) {
+    const int e = build_amr(c, mesh);
+    if (e) {
+      dg_mhd_destroy(ctx);
+      return e;
+    }
+  }
 
   HostTables h;
   build_host_tables(*c.hb, g, h);
@@ -460,7 +476,8 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
   }
   const size_t esz = fp32(c) ? sizeof(float) : sizeof(double);
   const size_t state_bytes = (size_t)g.nrows * g.stride * esz;
-  const size_t face_elems = (size_t)g.D * g.stride * g.Qf * 9;
+  size_t face_elems = (size_t)g.D * g.stride * g.Qf * 9;
+  if (c.amr.on) face_elems = std::max(face_elems, (size_t)c.amr.nface * g.Qf * 9);
   bool ok = cudaMalloc(&c.sc, sizeof(DevScalars)) == cudaSuccess &&
             cudaMemset(c.sc, 0, sizeof(DevScalars)) == cudaSuccess &&
             cudaMalloc(&c.stage_buf[0], state_bytes) == cudaSuccess &&
@@ -482,7 +499,7 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
   upload_limiter_tables(c);
   mlp_build_tables(c);
   // specialised GLM kernels for uniform 3D meshes
-  if (g.glm && g.D == 3 && !prm.generic_kernels) {
+  if (g.glm && g.D == 3 && !prm.generic_kernels && !c.amr.on) {
     if (fp32(c)) {
       if (degree == 1) c.fast_tabs = make_fast_tabs<float, 1>(h, g);
       if (degree == 2) c.fast_tabs = make_fast_tabs<float, 2>(h, g);
@@ -574,6 +591,18 @@ namespace {
 int operator_pass(Ctx& c, const void* w, const double* wmean, void* out, double* outmean, const void* w0,
                   const double* w0mean, double ca, double cb, int combine, cudaStream_t st) {
   const Geom& g = c.g;
+  if (c.amr.on) {
+    c.prof.begin(1, st);
+    if (fp32(c))
+      launch_amr_operator<float>(c, c.t32, (const float*)w, c.face_buf32, (float*)out, (const float*)w0, ca, cb,
+                                 combine, c.sc, wmean, w0mean, outmean, c.p.eps_hlld, st);
+    else
+      launch_amr_operator<double>(c, c.t64, (const double*)w, c.face_buf, (double*)out, (const double*)w0, ca, cb,
+                                  combine, c.sc, nullptr, nullptr, nullptr, c.p.eps_hlld, st);
+    c.prof.end(1, st);
+    c.prof.launches[1] += 1;
+    return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
+  }
   if (c.fast) {
     const FastGeom fg = fast_geom(g);
 #define FASTCASE(code, T, DEG, FB)                                                                          \
@@ -621,6 +650,16 @@ int operator_pass(Ctx& c, const void* w, const double* wmean, void* out, double*
 
 int dt_pass(Ctx& c, const void* w, const double* wmean, double* dt_out, cudaStream_t st) {
   const Geom& g = c.g;
+  if (c.amr.on) {
+    c.prof.begin(2, st);
+    launch_dt_init(c.sc, st);
+    if (fp32(c)) launch_amr_dt<float>(c, c.t32, (const float*)w, wmean, c.face_buf32, c.p, c.sc, st);
+    else launch_amr_dt<double>(c, c.t64, (const double*)w, nullptr, c.face_buf, c.p, c.sc, st);
+    launch_dt_finalize(g, c.p, c.sc, dt_out, st);
+    c.prof.end(2, st);
+    c.prof.launches[2] += g.glm ? 2 : 3;
+    return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
+  }
   c.prof.begin(2, st);
   if (fp32(c)) {
     if (!g.glm) launch_divb_face<float>(g, c.t32, (const float*)w, c.face_buf32, st);
@@ -637,6 +676,9 @@ int dt_pass(Ctx& c, const void* w, const double* wmean, double* dt_out, cudaStre
 
 int limit_pass(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t st) {
   if (c.p.limiter == DG_LIMIT_OFF && !c.p.positivity) return DG_OK;
+  // octree meshes: the cell-local positivity limiter only (TVB needs the
+  // neighbour means across coarse-fine faces, not built)
+  if (c.amr.on && c.p.limiter != DG_LIMIT_OFF) return DG_E_UNSUPPORTED;
   return run_limiter(c, w, wmean, troubled, st);
 }
 

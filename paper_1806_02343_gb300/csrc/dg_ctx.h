@@ -106,7 +106,19 @@ struct MlpTabs {
   float inv_mdx;    // 1 / (M~ dx)
 };
 
+// Octree mesh data owned by a context (device arrays; see dg_amr.cuh).
+struct AmrHost {
+  bool on = false;
+  int64_t nface = 0;
+  int maxent = 0, nsub = 0;
+  int32_t *fL = nullptr, *fR = nullptr, *fmeta = nullptr, *cstart = nullptr, *centry = nullptr;
+  double* dxc = nullptr;
+  double *Psub64 = nullptr, *Lsub64 = nullptr;
+  float *Psub32 = nullptr, *Lsub32 = nullptr;
+};
+
 struct Ctx {
+  AmrHost amr;
   Prof prof;
   LimTabs lim;
   MlpTabs mlp;

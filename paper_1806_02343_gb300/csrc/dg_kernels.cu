@@ -495,6 +495,12 @@ void launch_dt_from_value(const Geom& g, const dg_mhd_params& p, const double* d
   k_dt_finalize<<<1, 1, 0, st>>>(g, p, sc, dt_in, nullptr);
 }
 
+void launch_dt_init(DevScalars* sc, cudaStream_t st) { k_dt_init<<<1, 1, 0, st>>>(sc); }
+
+void launch_dt_finalize(const Geom& g, const dg_mhd_params& p, DevScalars* sc, double* dt_out, cudaStream_t st) {
+  k_dt_finalize<<<1, 1, 0, st>>>(g, p, sc, nullptr, dt_out);
+}
+
 void launch_set_glm(DevScalars* sc, double ch, double kappa, cudaStream_t st) {
   k_set_glm<<<1, 1, 0, st>>>(sc, ch, kappa);
 }

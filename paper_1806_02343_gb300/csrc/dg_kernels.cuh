@@ -23,6 +23,8 @@ void launch_dt(const Geom& g, const Tables<T>& tb, const T* w, const double* wme
 void launch_dt_from_value(const Geom& g, const dg_mhd_params& p, const double* dt_in, DevScalars* sc,
                           cudaStream_t st);
 void launch_set_glm(DevScalars* sc, double ch, double kappa, cudaStream_t st);
+void launch_dt_init(DevScalars* sc, cudaStream_t st);
+void launch_dt_finalize(const Geom& g, const dg_mhd_params& p, DevScalars* sc, double* dt_out, cudaStream_t st);
 template <typename T>
 void launch_mirror_means(const Geom& g, const double* wmean, T* w, cudaStream_t st);
 

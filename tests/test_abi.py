@@ -59,3 +59,32 @@ def test_init_rejects_bad_arguments(lib):
     assert lib.dg_mhd_init(None, 2, 0, 1.4, None, ctypes.byref(h)) == -1
     assert lib.dg_mhd_rhs(None, None, None, None, None, None) == -1
     assert lib.dg_mhd_step(None, None, None, None, None) == -1
+
+
+def test_octree_mesh_validation_rejects_bad_meshes(lib):
+    import ctypes
+    import numpy as np
+    from paper_1806_02343_gb300 import binding
+
+    def init(leaves, D=3):
+        m = binding.MeshDesc()
+        m.dim = D
+        m.box_len = 1.0
+        m.periodic = 1
+        lev = np.array([l for l, _ in leaves], dtype=np.int8)
+        ijk = np.array([k for _, k in leaves], dtype=np.int32).reshape(-1)
+        m.n_leaves = len(leaves)
+        m.level = lev.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
+        m.ijk = ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        h = ctypes.c_void_p()
+        return lib.dg_mhd_init(ctypes.byref(m), 1, 0, 5.0 / 3.0, None, ctypes.byref(h))
+
+    full = [(1, k) for k in np.ndindex(2, 2, 2)]
+    assert init(full[:-1]) == -2                        # incomplete cover
+    assert init(full + [(2, (0, 0, 0))]) == -2          # overlap
+    assert init(full + [full[0]]) == -2                 # duplicate leaf
+    # unbalanced: one level-1 cell refined twice next to level-1 neighbours
+    deep = [(1, k) for k in np.ndindex(2, 2, 2) if k != (0, 0, 0)]
+    deep += [(2, k) for k in np.ndindex(2, 2, 2) if k != (1, 1, 1)]
+    deep += [(3, tuple(2 + x for x in k)) for k in np.ndindex(2, 2, 2)]
+    assert init(deep) == -2
