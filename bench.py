@@ -103,30 +103,11 @@ class ClockSampler:
 
 
 def build_turbulence(sol, cfg, device):
-    """Project the turbulence start onto the basis with the library's own
-    projection kernel; point values are built on the GPU slab by slab."""
-    import torch
+    """Turbulence start at the Gauss points (built on the GPU), projected by the
+    library's own projection kernel."""
     from paper_1806_02343_gb300 import workloads as W
-    n, d = cfg["n"], cfg["d"]
-    npts = d + 1
-    gx1, _ = __import__("numpy").polynomial.legendre.leggauss(npts)
-    T = W.Turbulence3D(nvar=9)
-    coords = ((torch.arange(n, device=device, dtype=torch.float64)[:, None] + 0.5
-               + 0.5 * torch.as_tensor(gx1, device=device)[None, :]) / n).reshape(-1)  # [n*npts]
-    Q = npts ** 3
-    nodal = torch.empty((9, Q, sol.stride), dtype=torch.float64, device=device)
-    zs = max(1, 2 ** 22 // (n * n))  # cells per z-slab
-    for z0 in range(0, n, zs):
-        z1 = min(n, z0 + zs)
-        gz = coords[z0 * npts:z1 * npts]
-        v = T.grid_velocity(coords, coords, gz)          # [x, y, z, 3]
-        U = T.state_from_velocity(v)                      # [x, y, z, 9]
-        nz = z1 - z0
-        U = U.reshape(n, npts, n, npts, nz, npts, 9)      # ix qx iy qy iz qz var
-        U = U.permute(6, 1, 3, 5, 4, 2, 0).reshape(9, Q, nz * n * n)
-        nodal[:, :, z0 * n * n:z1 * n * n] = U
-        del v, U
-    return nodal, npts
+    npts = cfg["d"] + 1
+    return W.turbulence_nodal(cfg["n"], npts, sol.stride, device), npts
 
 
 def build_fourier(sol, cfg, device):

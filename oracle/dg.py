@@ -223,6 +223,48 @@ class Scheme:
             out[:, psi_rows] -= kappa * w[:, psi_rows]
         return out
 
+    def rhs_local(self, wc, wnb, ch=None, kappa=0.0):
+        """dw/dt of eq. wdot for a batch of cells given only their own weights
+        wc[b, r] and their face neighbours' weights wnb[b, 2*axis + side, r]
+        (side 0: the -axis neighbour, 1: the +axis neighbour). Same steps as
+        `rhs`, for sampling a large box without holding all of it."""
+        g = self.gamma
+        glm = self.divb == "glm"
+        ch2 = ch * ch if glm else None
+        nb = len(wc)
+        u = self.eval_points(wc, self.Sv)
+        R = np.zeros_like(wc)
+        for a in range(self.D):
+            f = mhd.flux(u, a, g, ch2)
+            R += np.einsum("cqv,q,rqv->cr", f, self.wv, self.Gv[a])
+        if not glm:
+            q = np.zeros((nb, self.V))
+            q[:, :8] = mhd.powell_q(self.means(wc), g)
+        for a in range(self.D):
+            for side in (0, 1):
+                wn = wnb[:, 2 * a + side]
+                if side == 0:   # face with the -a neighbour: this cell is R
+                    uL = self.eval_points(wn, self.Sf[(a, 1)])
+                    uR = self.eval_points(wc, self.Sf[(a, -1)])
+                    F, BnF = self.face_state(uL, uR, a, ch)
+                    R += np.einsum("cpv,p,rpv->cr", F, self.wf, self.Sf[(a, -1)])
+                    if not glm:
+                        jump = -(BnF - uR[..., mhd.BX + a])
+                        R -= np.einsum("cpr,cp,p->cr", np.einsum("cv,rpv->cpr", q, self.Sf[(a, -1)]), jump, self.wf)
+                else:           # face with the +a neighbour: this cell is L
+                    uL = self.eval_points(wc, self.Sf[(a, 1)])
+                    uR = self.eval_points(wn, self.Sf[(a, -1)])
+                    F, BnF = self.face_state(uL, uR, a, ch)
+                    R -= np.einsum("cpv,p,rpv->cr", F, self.wf, self.Sf[(a, 1)])
+                    if not glm:
+                        jump = BnF - uL[..., mhd.BX + a]
+                        R -= np.einsum("cpr,cp,p->cr", np.einsum("cv,rpv->cpr", q, self.Sf[(a, 1)]), jump, self.wf)
+        out = (2.0 / self.dx) * R / self.mass
+        if glm:
+            psi_rows = [r for r, (k, v, i) in enumerate(self.rows) if k == "L" and v == mhd.PSI]
+            out[:, psi_rows] -= kappa * wc[:, psi_rows]
+        return out
+
     # --------------------------------------------------------------------- dt
     def divb_face(self, w):
         """Face part of |div B|_K (App. C eq. divb-cell) in physical units:

@@ -381,3 +381,25 @@ def octree_leaves(D, base_level, max_level, refine):
         return (key, l)
 
     return sorted(leaves, key=morton)
+
+
+def turbulence_nodal(n, npts, stride, device="cuda", seed=1234, nvar=9):
+    """Decaying-turbulence start at the npts^3 Gauss points of every cell of an
+    n^3 box, laid out [var][q][stride] (built slab by slab on the device)."""
+    import torch
+    g1, _ = np.polynomial.legendre.leggauss(npts)
+    T = Turbulence3D(seed=seed, nvar=nvar)
+    coords = ((torch.arange(n, device=device, dtype=torch.float64)[:, None] + 0.5
+               + 0.5 * torch.as_tensor(g1, device=device)[None, :]) / n).reshape(-1)
+    Q = npts ** 3
+    nodal = torch.zeros((nvar, Q, stride), dtype=torch.float64, device=device)
+    zs = max(1, 2 ** 22 // (n * n))
+    for z0 in range(0, n, zs):
+        z1 = min(n, z0 + zs)
+        v = T.grid_velocity(coords, coords, coords[z0 * npts:z1 * npts])
+        U = T.state_from_velocity(v)
+        nz = z1 - z0
+        U = U.reshape(n, npts, n, npts, nz, npts, nvar).permute(6, 1, 3, 5, 4, 2, 0).reshape(nvar, Q, nz * n * n)
+        nodal[:, :, z0 * n * n:z1 * n * n] = U
+        del v, U
+    return nodal

@@ -211,3 +211,16 @@ def test_powell_face_term_vanishes_for_continuous_normal_field():
     fn = lambda x: W.entropy_wave(x, D=3, v0=(0.5, 0.5, 0.5), k=(1, 0, 1), nvar=8)
     w = S.project(fn)
     assert np.max(S.divb_face(w)) < 1e-13
+
+
+@pytest.mark.parametrize("divb", ["glm", "powell"])
+def test_rhs_local_equals_rhs(divb):
+    # the per-cell evaluation used for sampled parity equals the full operator
+    S = Scheme(3, 2, divb, G, (5, 4, 3))
+    w = S.project(W.SmoothFourier3D(nvar=S.V))
+    full = S.rhs(w, 2.5, 0.7)
+    cells = np.array([0, 7, 23, 59])
+    wnb = np.stack([w[S.nbr_minus[a][cells]] if s == 0 else w[S.nbr_plus[a][cells]]
+                    for a in range(3) for s in (0, 1)], 1)
+    loc = S.rhs_local(w[cells], wnb, 2.5, 0.7)
+    assert np.max(np.abs(loc - full[cells])) < 1e-13 * np.abs(full).max()
