@@ -213,6 +213,40 @@ class Limiter:
                             out[:, a, mhd.BX + c] += w[:, r] * self.ldf_slope[i, c, a]
         return out
 
+    # ----------------------------------------------------- neighbour differences
+    def mean_differences(self, m):
+        """D+[c, a], D-[c, a]: mean differences per direction in units of the
+        reference half-width. Uniform mesh: (u_{a+} - u)/2 and (u - u_{a-})/2.
+        Octree (reading of Sec. 4.4, which defers to Schaal et al. 2015): the
+        neighbour mean (the average of the adjacent finer leaves when refined)
+        divided by the centre distance in units of dx_K/2: 2 same level, 3 for
+        a coarser neighbour, 1.5 for finer ones."""
+        S = self.S
+        if not hasattr(S, "faces"):
+            dp = np.stack([0.5 * (m[S.nbr_plus[a]] - m) for a in range(S.D)], 1)
+            dm = np.stack([0.5 * (m - m[S.nbr_minus[a]]) for a in range(S.D)], 1)
+            return dp, dm
+        C, D, V = S.C, S.D, m.shape[1]
+        acc = np.zeros((C, D, 2, V))
+        cnt = np.zeros((C, D, 2))
+        fac = np.zeros((C, D, 2))
+        for cL, cR, a, kind, sub in S.faces:
+            # cR sees cL on its -a side; cL sees cR on its +a side
+            for cell, nb, side in ((cR, cL, 0), (cL, cR, 1)):
+                acc[cell, a, side] += m[nb]
+                cnt[cell, a, side] += 1
+                if kind == 0:
+                    f = 2.0
+                elif (kind == 1 and cell == cL) or (kind == 2 and cell == cR):
+                    f = 1.5          # this cell is coarse: finer neighbours
+                else:
+                    f = 3.0          # the neighbour is coarse
+                fac[cell, a, side] = f
+        nbm = acc / cnt[..., None]
+        dp = (nbm[:, :, 1] - m[:, None, :]) / fac[:, :, 1, None]
+        dm = (m[:, None, :] - nbm[:, :, 0]) / fac[:, :, 0, None]
+        return dp, dm
+
     # ----------------------------------------------------- TVB-characteristic
     def tvb_limit(self, w, ch=None):
         S, P = self.S, self.S.P
@@ -220,13 +254,15 @@ class Limiter:
         sl = self.slopes(w)
         out = w.copy()
         troubled = np.zeros(S.C, dtype=bool)
-        thr = P.Mtilde * S.dx
+        dpa, dma = self.mean_differences(m)
+        dxc = S.dxc if hasattr(S, "dxc") else np.full(S.C, S.dx)
         for c in range(S.C):
+            thr = P.Mtilde * dxc[c]
             new_sl = sl[c].copy()
             hit = False
             for a in range(S.D):
-                dp = 0.5 * (m[S.nbr_plus[a][c]] - m[c])
-                dm = 0.5 * (m[c] - m[S.nbr_minus[a][c]])
+                dp = dpa[c, a]
+                dm = dma[c, a]
                 R, L, _ = eigensystem(m[c], a, S.gamma, ch)
                 cx, cp, cm = L @ sl[c, a], L @ dp, L @ dm
                 sig = cx.copy()

@@ -166,7 +166,8 @@ class Solver:
     """Owns one dg_mhd_ctx. State tensors are allocated by the caller (torch) with
     the layout reported by dg_mhd_state_layout: w[row][cell_stride]."""
 
-    def __init__(self, dim, n, degree, divb, gamma=5.0 / 3.0, box_len=1.0, leaves=None, **params):
+    def __init__(self, dim, n, degree, divb, gamma=5.0 / 3.0, box_len=1.0, leaves=None, levels=None, ijk=None,
+                 **params):
         """n: cells per axis of a uniform box, or None with `leaves` =
         [(level, (i, j[, k]))] for an octree mesh of a cube of side box_len."""
         import numpy as np
@@ -180,9 +181,12 @@ class Solver:
         m.box_len = box_len
         m.periodic = 1
         if leaves is not None:
-            self._lev = np.ascontiguousarray(np.array([l for l, _ in leaves], dtype=np.int8))
-            self._ijk = np.ascontiguousarray(np.array([k for _, k in leaves], dtype=np.int32).reshape(-1))
-            m.n_leaves = len(leaves)
+            levels = [l for l, _ in leaves]
+            ijk = [k for _, k in leaves]
+        if levels is not None:
+            self._lev = np.ascontiguousarray(np.asarray(levels, dtype=np.int8))
+            self._ijk = np.ascontiguousarray(np.asarray(ijk, dtype=np.int32).reshape(-1))
+            m.n_leaves = len(self._lev)
             m.level = self._lev.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
             m.ijk = self._ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         self.params = default_params(**params)

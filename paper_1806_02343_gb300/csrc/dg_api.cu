@@ -676,9 +676,9 @@ int dt_pass(Ctx& c, const void* w, const double* wmean, double* dt_out, cudaStre
 
 int limit_pass(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t st) {
   if (c.p.limiter == DG_LIMIT_OFF && !c.p.positivity) return DG_OK;
-  // octree meshes: the cell-local positivity limiter only (TVB needs the
-  // neighbour means across coarse-fine faces, not built)
-  if (c.amr.on && c.p.limiter != DG_LIMIT_OFF) return DG_E_UNSUPPORTED;
+  // octree meshes: TVB with neighbour means across coarse-fine faces; the
+  // learned detector's features assume uniform neighbours
+  if (c.amr.on && c.p.limiter == DG_LIMIT_MLP) return DG_E_UNSUPPORTED;
   return run_limiter(c, w, wmean, troubled, st);
 }
 

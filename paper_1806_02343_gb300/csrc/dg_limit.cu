@@ -214,9 +214,20 @@ __device__ __forceinline__ void from_char(const Eig<R>& e, const R* m, R gamma, 
   for (int i = 5; i < V; ++i) dU[i] = dW[i];
 }
 
+// Octree neighbours for the limiter: face lists (see dg_amr.cuh) and cell sizes.
+struct AmrNb {
+  const int32_t* fL;
+  const int32_t* fR;
+  const int32_t* fmeta;
+  const int32_t* cstart;
+  const int32_t* centry;
+  const double* dxc;
+  int on;
+};
+
 template <typename T>
 __global__ void k_tvb(Geom g, LimTabs lt, T* w, double* wmean, uint8_t* troubled, const uint8_t* __restrict__ gate,
-                      dg_mhd_params p, const DevScalars* __restrict__ sc) {
+                      dg_mhd_params p, const DevScalars* __restrict__ sc, AmrNb an) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
   if (gate && !gate[c]) {  // learned detection: cells not flagged skip the TVB procedure
@@ -246,7 +257,7 @@ __global__ void k_tvb(Geom g, LimTabs lt, T* w, double* wmean, uint8_t* troubled
   }
   // characteristic limiting in the working precision of the state
   using R = T;
-  const R thr = (R)(p.Mtilde * g.dx);
+  const R thr = (R)(p.Mtilde * (an.on ? an.dxc[c] : g.dx));
   const R ch = g.glm ? (R)sc->ch : R(0);
   const R rel = sizeof(T) == 4 ? R(1e-6) : R(1e-12);
   const R gam = (R)g.gamma, beta = (R)p.beta, teps = (R)p.tvb_eps;
@@ -256,12 +267,44 @@ __global__ void k_tvb(Geom g, LimTabs lt, T* w, double* wmean, uint8_t* troubled
   double nsl[3][9];
   for (int a = 0; a < g.D; ++a) {
     double mp[9], mm[9];
-    cell_mean(g, lt, (const T*)w, wmean, nb(g, c, a, +1), mp);
-    cell_mean(g, lt, (const T*)w, wmean, nb(g, c, a, -1), mm);
+    double fp = 2.0, fm = 2.0;  // centre distance in units of dx_K / 2
+    if (!an.on) {
+      cell_mean(g, lt, (const T*)w, wmean, nb(g, c, a, +1), mp);
+      cell_mean(g, lt, (const T*)w, wmean, nb(g, c, a, -1), mm);
+    } else {
+      // octree: average of the leaves across each side; 2 same level, 3 coarser, 1.5 finer
+      int np_ = 0, nm_ = 0;
+      for (int k = 0; k < 9; ++k) mp[k] = mm[k] = 0.0;
+      for (int e = an.cstart[c]; e < an.cstart[c + 1]; ++e) {
+        const int ent = an.centry[e];
+        const int f = ent >> 1, side = ent & 1;
+        const int meta = an.fmeta[f];
+        if ((meta & 3) != a) continue;
+        const int kind = (meta >> 2) & 3;
+        const int64_t nbc = side == 0 ? an.fR[f] : an.fL[f];
+        double mn[9];
+        cell_mean(g, lt, (const T*)w, wmean, nbc, mn);
+        const bool self_coarse = (side == 0 && kind == 1) || (side == 1 && kind == 2);
+        const double fac = kind == 0 ? 2.0 : (self_coarse ? 1.5 : 3.0);
+        if (side == 0) {
+          for (int k = 0; k < 9; ++k) mp[k] += mn[k];
+          ++np_;
+          fp = fac;
+        } else {
+          for (int k = 0; k < 9; ++k) mm[k] += mn[k];
+          ++nm_;
+          fm = fac;
+        }
+      }
+      for (int k = 0; k < 9; ++k) {
+        mp[k] /= (double)(np_ > 0 ? np_ : 1);
+        mm[k] /= (double)(nm_ > 0 ? nm_ : 1);
+      }
+    }
     R dpl[9], dmi[9], sla[9];
     for (int k = 0; k < 9; ++k) {
-      dpl[k] = (R)(0.5 * (mp[k] - m[k]));
-      dmi[k] = (R)(0.5 * (m[k] - mm[k]));
+      dpl[k] = (R)((mp[k] - m[k]) / fp);
+      dmi[k] = (R)((m[k] - mm[k]) / fm);
       sla[k] = (R)sl[a][k];
     }
     Eig<R> e;
@@ -717,10 +760,11 @@ int run_limiter(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t 
     c.prof.begin(3, st);
     // FP32 form: the float mode-0 rows mirror the FP64 means exactly; reading
     // them avoids FP64 conversions (the limiter never changes the means)
+    const AmrNb an{c.amr.fL, c.amr.fR, c.amr.fmeta, c.amr.cstart, c.amr.centry, c.amr.dxc, c.amr.on ? 1 : 0};
     if (c.p.precision == DG_PREC_FP32MIX)
-      k_tvb<float><<<nb, 128, 0, st>>>(g, c.lim, (float*)w, nullptr, troubled, gate, c.p, c.sc);
+      k_tvb<float><<<nb, 128, 0, st>>>(g, c.lim, (float*)w, nullptr, troubled, gate, c.p, c.sc, an);
     else
-      k_tvb<double><<<nb, 128, 0, st>>>(g, c.lim, (double*)w, nullptr, troubled, gate, c.p, c.sc);
+      k_tvb<double><<<nb, 128, 0, st>>>(g, c.lim, (double*)w, nullptr, troubled, gate, c.p, c.sc, an);
     c.prof.end(3, st);
   }
   if (c.p.positivity) {

@@ -403,3 +403,76 @@ def turbulence_nodal(n, npts, stride, device="cuda", seed=1234, nvar=9):
         nodal[:, :, z0 * n * n:z1 * n * n] = U
         del v, U
     return nodal
+
+
+def morton_order(levels, ijk, D, max_level):
+    """Permutation sorting leaves by the Z-curve key of their lower corner."""
+    lv = np.asarray(levels, dtype=np.int64)
+    k = np.asarray(ijk, dtype=np.int64).reshape(len(lv), D) << (max_level - lv)[:, None]
+    key = np.zeros(len(lv), dtype=np.uint64)
+    for bit in range(max_level, -1, -1):
+        for a in range(D - 1, -1, -1):
+            key = (key << np.uint64(1)) | ((k[:, a] >> bit) & 1).astype(np.uint64)
+    return np.lexsort((lv, key))
+
+
+def orszag_tang_octree(lo=4, hi=7, target=1_500_000, tol=0.1):
+    """Static octree for the 3D Orszag-Tang extrusion: a 2:1-balanced quadtree
+    in (x, y) refined where dx * max|grad B| of the initial field exceeds a
+    threshold (the density is uniform at t = 0, so B drives the refinement),
+    extruded along z (cubic cells: a leaf of level l spans 2^l cells in z).
+    The threshold is bisected to reach about `target` leaves.
+    Returns (levels int8 [N], ijk int32 [N, 3]) in Morton order."""
+    s = 1.0 / math.sqrt(4.0 * math.pi)
+
+    def grad(c):
+        return max(2 * math.pi * s * abs(math.cos(2 * math.pi * c[1])),
+                   4 * math.pi * s * abs(math.cos(4 * math.pi * c[0])))
+
+    def build(theta):
+        q = octree_leaves(2, lo, hi, lambda c, dx, l: dx * grad(c) > theta)
+        return q, sum(2 ** l for l, _ in q)
+
+    a, b = 0.0, 10.0
+    q, n = build(0.5 * (a + b))
+    for _ in range(30):
+        th = 0.5 * (a + b)
+        q, n = build(th)
+        if abs(n - target) <= tol * target:
+            break
+        if n > target:
+            a = th
+        else:
+            b = th
+    lev, ijk = [], []
+    for l, (i, j) in q:
+        nz = 2 ** l
+        lev.append(np.full(nz, l, dtype=np.int8))
+        ijk.append(np.stack([np.full(nz, i), np.full(nz, j), np.arange(nz)], 1))
+    lev = np.concatenate(lev)
+    ijk = np.concatenate(ijk).astype(np.int32)
+    perm = morton_order(lev, ijk, 3, hi)
+    return lev[perm], ijk[perm]
+
+
+def leaf_nodal(fn, levels, ijk, npts, stride, D=3, device="cuda"):
+    """fn at the npts^D Gauss points of every leaf (unit box), laid out
+    [var][q][stride] (q: last axis fastest)."""
+    import torch
+    g1, _ = np.polynomial.legendre.leggauss(npts)
+    qp = np.stack(np.meshgrid(*([g1] * D), indexing="ij"), -1).reshape(-1, D)
+    lv = torch.as_tensor(np.asarray(levels, dtype=np.float64), device=device)
+    dx = torch.pow(2.0, -lv)
+    k = torch.as_tensor(np.asarray(ijk, dtype=np.float64).reshape(len(levels), D), device=device)
+    ctr = (k + 0.5) * dx[:, None]
+    N = len(levels)
+    out = None
+    chunk = 1 << 20
+    for c0 in range(0, N, chunk):
+        c1 = min(N, c0 + chunk)
+        x = ctr[c0:c1, None, :] + 0.5 * dx[c0:c1, None, None] * torch.as_tensor(qp, device=device)[None]
+        U = fn(x)                                   # [cells, Q, V]
+        if out is None:
+            out = torch.zeros((U.shape[-1], qp.shape[0], stride), dtype=torch.float64, device=device)
+        out[:, :, c0:c1] = U.permute(2, 1, 0)
+    return out

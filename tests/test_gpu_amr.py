@@ -85,3 +85,40 @@ def test_amr_fp32_form_steps(D, divb):
         sol.step(w, wm, torch.tensor([dto], dtype=torch.float64, device="cuda"))
         wo, _ = A.step(wo, dto)
     assert rel_err(from_device(w, sol), wo) < 1e-5
+
+
+def _shock(nvar):
+    from oracle import mhd
+    def fn(x):
+        r = np.sqrt(((x - 0.45) ** 2).sum(-1))
+        inside = r < 0.27
+        one = np.ones_like(r)
+        D = x.shape[-1]
+        u = mhd.conserved(np.where(inside, 1.0, 0.3), np.stack([0.3 * one, -0.2 * one, 0.1 * one], -1),
+                          np.where(inside, 5.0, 0.2), np.stack([0.8 * one, 0.3 * one, np.where(inside, 0.2, -0.4)], -1),
+                          G)
+        if nvar == 9:
+            u = np.concatenate([u, 0.01 * np.sin(6 * x[..., :1])], -1)
+        return u
+    return fn
+
+
+@pytest.mark.parametrize("D,divb", [(3, "powell"), (3, "glm"), (2, "powell")])
+def test_amr_tvb_and_positivity_fp64(D, divb):
+    import torch
+    from oracle.limiter import Limiter
+    leaves = _mesh(D)
+    A = AMRScheme(D, 2, divb, G, leaves)
+    A.P.Mtilde = 0.5
+    A.P.c_h_fixed = 3.0
+    w0 = A.project(_shock(A.V))
+    ref, trig = Limiter(A, tvb=True, positivity=False).tvb_limit(w0, 3.0)
+    sol = _solver(A, leaves, limiter=1, Mtilde=0.5, c_h_fixed=3.0)
+    if divb == "glm":
+        sol.set_glm(3.0, 1.0)
+    w = to_device(w0, sol)
+    flags = torch.zeros(sol.stride, dtype=torch.uint8, device="cuda")
+    sol.limit(w, None, flags)
+    assert trig.sum() > 5
+    assert np.array_equal(flags[: sol.ncell].cpu().numpy().astype(bool), trig)
+    assert rel_err(from_device(w, sol), ref) < 1e-12

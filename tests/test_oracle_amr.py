@@ -68,3 +68,33 @@ def test_amr_alfven_2d_static_refinement_converges():
         errs.append(e[5])
     order = np.log2(errs[0] / errs[1])
     assert 2.5 < order < 3.7, order
+
+
+def test_amr_mean_differences_reduce_to_uniform():
+    from oracle.limiter import Limiter
+    leaves = W.octree_leaves(3, 2, 2, lambda c, dx, l: False)
+    A = AMRScheme(3, 2, "powell", G, leaves)
+    U = Scheme(3, 2, "powell", G, 4)
+    perm = [(k[2] * 4 + k[1]) * 4 + k[0] for _, k in leaves]
+    fn = W.SmoothFourier3D(nvar=8)
+    wa, wu = A.project(fn), U.project(fn)
+    da = Limiter(A).mean_differences(A.means(wa))
+    du = Limiter(U).mean_differences(U.means(wu))
+    assert np.allclose(da[0], du[0][perm], atol=1e-15) and np.allclose(da[1], du[1][perm], atol=1e-15)
+
+
+def test_amr_mean_differences_exact_for_linear_field():
+    # a linear field has D+ = D- = slope along the axis (in reference units) at
+    # every cell, whatever the neighbour levels (distance-weighted differences)
+    from oracle.limiter import Limiter
+    from oracle import mhd
+    leaves = W.octree_leaves(3, 2, 3, lambda c, dx, l: c[0] < 0.5)
+    A = AMRScheme(3, 1, "powell", G, leaves)
+    m = np.zeros((A.C, 8))
+    m[:, 0] = 1.0 + 0.3 * A.centers[:, 0]
+    dp, dm = Limiter(A).mean_differences(m)
+    ix = A.centers[:, 0]
+    inner = (ix > 0.2) & (ix < 0.8)          # away from the periodic wrap in x
+    expect = 0.3 * A.dxc / 2
+    assert np.allclose(dp[inner, 0, 0], expect[inner], atol=1e-14)
+    assert np.allclose(dm[inner, 0, 0], expect[inner], atol=1e-14)
