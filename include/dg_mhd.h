@@ -77,7 +77,8 @@ enum { DG_LIMIT_OFF = 0, DG_LIMIT_TVB = 1, DG_LIMIT_MLP = 2 };
  * the box without overlap and be 2:1 balanced across faces (DG_E_MESH
  * otherwise). Cells are numbered in the given order. Host memory, copied at
  * init. Faces: same-level, and coarse-fine faces integrated at the fine face's
- * Gauss points (coarse side at the mapped sub-face points, weights / 2^(dim-1)). */
+ * Gauss points (coarse side at the mapped sub-face points, weights / 2^(dim-1)).
+ * At most 2^31 - 65 cells (indices are 32-bit on the device): DG_E_MESH beyond. */
 typedef struct {
   int dim;               /* 2 or 3                                             */
   int32_t n[3];          /* uniform: cells per axis (n[2] ignored for dim 2)   */
@@ -173,6 +174,14 @@ int dg_mhd_status(dg_mhd_ctx* ctx, int sync);
  * (tau < 1) and the mass and energy injected by the mean floors, accumulated
  * since the last reset. Synchronises the device; reset = 1 clears them. */
 int dg_mhd_counters(dg_mhd_ctx* ctx, int64_t* pos_cells, double* inj_mass, double* inj_energy, int reset);
+
+/* Troubled-cell statistics of the TVB limiter (Sec. 4.2 judges a detector by
+ * its sensitivity and specificity; these counts give its workload), summed
+ * since the last reset: limiter passes that ran the TVB procedure, cells that
+ * went through it (flagged by the learned indicator, or every cell with the
+ * plain detector), and cells whose slopes it changed. Any pointer may be
+ * NULL. Synchronises the device; reset = 1 clears the counts. */
+int dg_mhd_limiter_counts(dg_mhd_ctx* ctx, int64_t* passes, int64_t* flagged, int64_t* limited, int reset);
 
 /* Learned troubled-cell indicator. The paper makes troubled-cell detection
  * a separate step of limiting, judged by sensitivity and specificity (Sec. 4.2);

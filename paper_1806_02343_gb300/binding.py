@@ -24,7 +24,7 @@ EXPORTS = [
     "dg_mhd_rhs", "dg_mhd_limit", "dg_mhd_dt", "dg_mhd_step", "dg_mhd_last_dt", "dg_mhd_status",
     "dg_mhd_profile", "dg_mhd_profile_read", "dg_mhd_launch_count", "dg_mhd_rhs_noalloc", "dg_mhd_destroy",
     "dg_mhd_strerror", "dg_mhd_mlp_features", "dg_mhd_mlp_set_weights", "dg_mhd_mlp_infer", "dg_mhd_mlp_loss_grad",
-    "dg_mhd_mlp_train", "dg_mhd_counters",
+    "dg_mhd_mlp_train", "dg_mhd_counters", "dg_mhd_limiter_counts",
 ]
 KIND_FACE, KIND_CELL, KIND_DT, KIND_LIMIT, KIND_PROJECT, KIND_POSITIVITY, KIND_MLP = range(7)
 
@@ -82,6 +82,8 @@ def lib():
                                    ctypes.POINTER(ctypes.c_double), vp]
     L.dg_mhd_counters.argtypes = [vp, i64p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                   ctypes.c_int]
+    L.dg_mhd_limiter_counts.argtypes = [vp, i64p, i64p, i64p, ctypes.c_int]
+    L.dg_mhd_limiter_counts.restype = ctypes.c_int
     L.dg_mhd_destroy.argtypes = [vp]
     L.dg_mhd_destroy.restype = None
     L.dg_mhd_strerror.argtypes = [ctypes.c_int]
@@ -277,6 +279,12 @@ class Solver:
         _check(lib().dg_mhd_counters(self.h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(e), 1 if reset else 0),
                "dg_mhd_counters")
         return {"pos_cells": n.value, "inj_mass": m.value, "inj_energy": e.value}
+
+    def limiter_counts(self, reset=False):
+        p, f, l = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().dg_mhd_limiter_counts(self.h, ctypes.byref(p), ctypes.byref(f), ctypes.byref(l),
+                                           1 if reset else 0), "dg_mhd_limiter_counts")
+        return {"passes": p.value, "flagged": f.value, "limited": l.value}
 
     def status(self, sync=True):
         return lib().dg_mhd_status(self.h, 1 if sync else 0)

@@ -1,6 +1,8 @@
 // C ABI of the DG-MHD library (see include/dg_mhd.h for the contract).
 #include <cuda_runtime.h>
 
+#include <climits>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -213,6 +215,7 @@ FastGeom fast_geom(const Geom& g) {
   f.nx = g.nx; f.ny = g.ny; f.nz = g.nz;
   f.ncell = g.ncell; f.stride = g.stride;
   f.dx = g.dx; f.gamma = g.gamma;
+  f.metric = 2.0 / g.dx;
   return f;
 }
 
@@ -388,7 +391,7 @@ void dg_mhd_destroy(dg_mhd_ctx* ctx) {
   free_tables(c.t32);
   void* ptrs[] = {c.sc, c.face_buf, c.face_buf32, c.stage_buf[0], c.stage_buf[1], c.stage_buf[2],
                   c.stage_mean[0], c.stage_mean[1], c.stage_mean[2], c.cellscratch, c.proj_tab, c.proj_w,
-                  c.troubled, c.mlp_w1, c.mlp_w2, c.mlp_bias};
+                  c.troubled, c.flag_list, c.pos_list, c.mlp_w1, c.mlp_w2, c.mlp_bias};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c.hb;
@@ -410,6 +413,12 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
     for (int a = 0; a < mesh->dim; ++a)
       if (mesh->n[a] < 1) return DG_E_MESH;
   if (!(mesh->box_len > 0.0)) return DG_E_MESH;
+  {
+    // cell indices are 32-bit inside the kernels
+    const int64_t cells = octree ? mesh->n_leaves
+                                 : (int64_t)mesh->n[0] * mesh->n[1] * (mesh->dim == 3 ? mesh->n[2] : 1);
+    if (cells < 1 || cells > (int64_t)INT32_MAX - 64) return DG_E_MESH;
+  }
   dg_mhd_params prm;
   if (p) prm = *p;
   else dg_mhd_default_params(&prm);
@@ -482,7 +491,15 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
             cudaMemset(c.sc, 0, sizeof(DevScalars)) == cudaSuccess &&
             cudaMalloc(&c.stage_buf[0], state_bytes) == cudaSuccess &&
             cudaMalloc(&c.stage_buf[1], state_bytes) == cudaSuccess &&
-            cudaMalloc(&c.troubled, (size_t)g.stride) == cudaSuccess;
+            cudaMalloc(&c.troubled, (size_t)g.stride) == cudaSuccess &&
+            cudaMalloc(&c.flag_list, (size_t)g.stride * sizeof(int32_t)) == cudaSuccess &&
+            cudaMalloc(&c.pos_list, (size_t)g.stride * sizeof(int32_t)) == cudaSuccess;
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+      c.nsm = nsm;
+  }
   if (ok) {
     if (fp32(c)) {
       ok = cudaMalloc(&c.face_buf32, face_elems * sizeof(float)) == cudaSuccess &&
@@ -795,6 +812,23 @@ int dg_mhd_counters(dg_mhd_ctx* ctx, int64_t* pos_cells, double* inj_mass, doubl
   if (reset) {
     h.pos_cells = 0;
     h.inj_mass = h.inj_energy = 0.0;
+    if (cudaMemcpy(c.sc, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) return DG_E_CUDA;
+  }
+  return DG_OK;
+}
+
+int dg_mhd_limiter_counts(dg_mhd_ctx* ctx, int64_t* passes, int64_t* flagged, int64_t* limited, int reset) {
+  if (!ctx) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  if (cudaDeviceSynchronize() != cudaSuccess) return DG_E_CUDA;
+  DevScalars h;
+  if (cudaMemcpy(&h, c.sc, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return DG_E_CUDA;
+  if (passes) *passes = c.lim_passes;
+  if (flagged) *flagged = (int64_t)h.cnt_flagged + c.lim_plain_cells;
+  if (limited) *limited = (int64_t)h.cnt_limited;
+  if (reset) {
+    h.cnt_flagged = h.cnt_limited = 0;
+    c.lim_passes = c.lim_plain_cells = 0;
     if (cudaMemcpy(c.sc, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) return DG_E_CUDA;
   }
   return DG_OK;

@@ -62,6 +62,10 @@ struct DevScalars {
   double inj_mass;    // mass added by the positivity floors (Sec. 4.3)
   double inj_energy;  // energy added by the positivity floors
   unsigned long long pos_cells;  // cells the positivity limiter rescaled (tau < 1)
+  unsigned int nflag;            // cells the indicator flagged in the current limiter pass
+  unsigned int npos;             // cells the FP32 positivity screen listed in the current pass
+  unsigned long long cnt_flagged;  // cells flagged by the indicator, summed over passes
+  unsigned long long cnt_limited;  // cells whose slopes the TVB procedure changed, summed over passes
 };
 
 // Limiter tables (kernel parameters): degree-1 Legendre mode per axis, mode
@@ -142,6 +146,11 @@ struct Ctx {
   double* proj_tab = nullptr;      // projection table [r][q][comp]
   double* proj_w = nullptr;
   uint8_t* troubled = nullptr;     // per-cell limiter flags (scratch)
+  int32_t* flag_list = nullptr;    // cells flagged by the indicator in the current pass
+  int32_t* pos_list = nullptr;     // cells the positivity screen could not clear in the current pass
+  int64_t lim_passes = 0;          // limiter passes with TVB since the last counter reset
+  int64_t lim_plain_cells = 0;     // cells the plain TVB detection examined since the last reset
+  int nsm = 152;                   // streaming multiprocessors of the device
   int fast = 0;                    // specialised GLM path: 10*prec + degree, 0 = none
   void* fast_tabs = nullptr;       // host FastAll<T, DEG> (kernel parameters)
 };

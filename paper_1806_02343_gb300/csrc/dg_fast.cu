@@ -223,10 +223,10 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_ce
     __syncthreads();
   }
   // surface integral: -oint F* . n P_l over the six faces. The mean row sums
-  // each face in FP32 in a fixed order -- the same products and order in both
-  // cells of the face, so the two contributions cancel exactly -- and adds the
-  // six face sums in FP64 (conservation of the cell means to FP64 rounding).
-  double mean_acc = 0.0;
+  // each face in the working precision in a fixed order -- the same products
+  // and order in both cells of the face, so the two contributions cancel
+  // exactly -- and the six face sums are then combined with more precision
+  // than one rounding per face (conservation of the cell means).
   T fsum[6];
   const Coord kc = coord_of(g, live ? c : 0);
   if (live) {
@@ -247,29 +247,56 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_ce
         fsum[2 * a + s] = s ? -fs : fs;
       }
     }
-    // six face sums added in FP64 as a balanced tree (short dependency chain)
-    mean_acc = ((double)fsum[0] + (double)fsum[1]) + ((double)fsum[2] + (double)fsum[3]) +
-               ((double)fsum[4] + (double)fsum[5]);
   }
   if (!live) return;
   const double dt = sc->dt;
   const double kappa = sc->kappa;
-  const double metric = 2.0 / g.dx;
+  const double metric = g.metric;
   // mode 0 (cell mean)
   {
-    double rhs = metric * (double)tb.minv[0] * mean_acc;
     const int64_t i = (int64_t)(v * N) * S + c;
-    const double wz = mix ? wmean[(int64_t)v * S + c] : (double)wl[0];
-    if (v == 8) rhs -= kappa * wz;
-    if (!combine) {
-      out[i] = (T)rhs;
-      if (mix) outmean[(int64_t)v * S + c] = rhs;
-    } else if (mix) {
-      const double o = ca * w0mean[(int64_t)v * S + c] + cb * (wz + dt * rhs);
-      outmean[(int64_t)v * S + c] = o;
-      out[i] = (T)o;
+    if (sizeof(T) == 4 && mix) {
+      // FP32 form. The six face sums are added as an unevaluated float pair
+      // (Knuth's TwoSum: s + e equals a + b exactly), so the cell's total is
+      // accurate to about 2^-48 of the face sums; it enters the FP64 mean
+      // through one conversion. GB300's FP64 rate is 1/64 of FP32: the FP64
+      // work here is a handful of operations per (cell, variable).
+      float hi = (float)fsum[0], lo = 0.f;
+#pragma unroll
+      for (int k = 1; k < 6; ++k) {
+        const float b = (float)fsum[k];
+        const float s2 = __fadd_rn(hi, b);
+        const float bb = __fsub_rn(s2, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s2, bb)), __fsub_rn(b, bb));
+        hi = s2;
+        lo = __fadd_rn(lo, e);
+      }
+      const double tot = (double)hi + (double)lo;
+      const double k1 = metric * (double)tb.minv[0];
+      const double wz = wmean[(int64_t)v * S + c];
+      if (!combine) {
+        double rhs = k1 * tot;
+        if (v == 8) rhs = fma(-kappa, wz, rhs);
+        out[i] = (T)rhs;
+        outmean[(int64_t)v * S + c] = rhs;
+      } else {
+        // o = ca w0 + cb (wz + dt rhs), rhs = k1 tot (- kappa wz for psi)
+        const double kd = cb * dt;
+        double base = cb * wz;
+        if (ca != 0.0) base = fma(ca, w0mean[(int64_t)v * S + c], base);
+        if (v == 8) base = fma(-kd * kappa, wz, base);
+        const double o = fma(kd * k1, tot, base);
+        outmean[(int64_t)v * S + c] = o;
+        out[i] = (T)o;
+      }
     } else {
-      out[i] = (T)(ca * (double)w0[i] + cb * (wz + dt * rhs));
+      const double mean_acc = ((double)fsum[0] + (double)fsum[1]) + ((double)fsum[2] + (double)fsum[3]) +
+                              ((double)fsum[4] + (double)fsum[5]);
+      double rhs = metric * (double)tb.minv[0] * mean_acc;
+      const double wz = (double)wl[0];
+      if (v == 8) rhs -= kappa * wz;
+      if (!combine) out[i] = (T)rhs;
+      else out[i] = (T)(ca * (double)w0[i] + cb * (wz + dt * rhs));
     }
   }
   const T tm = (T)metric, tdt = (T)dt, tca = (T)ca, tcb = (T)cb, tk = (T)kappa;

@@ -41,6 +41,7 @@ struct FastGeom {
   int nx, ny, nz;
   int64_t ncell, stride;
   double dx, gamma;
+  double metric;  // 2 / dx
 };
 
 template <typename T, int DEG>

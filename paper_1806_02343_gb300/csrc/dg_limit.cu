@@ -17,6 +17,7 @@
 //        pressure may be near or below the floor is re-evaluated in FP64.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <cstring>
@@ -29,14 +30,15 @@ namespace dgmhd {
 
 namespace {
 
+// periodic face neighbour on the uniform mesh (32-bit index arithmetic: cell
+// counts stay below 2^31)
 __device__ __forceinline__ int64_t nb(const Geom& g, int64_t c, int a, int dir) {
-  int ix = (int)(c % g.nx);
-  int64_t r = c / g.nx;
-  int iy = (int)(r % g.ny);
-  int iz = (int)(r / g.ny);
-  if (a == 0) ix = (ix + dir + g.nx) % g.nx;
-  else if (a == 1) iy = (iy + dir + g.ny) % g.ny;
-  else iz = (iz + dir + g.nz) % g.nz;
+  const unsigned cc = (unsigned)c, nx = (unsigned)g.nx, ny = (unsigned)g.ny;
+  const unsigned r = cc / nx;
+  int ix = (int)(cc - r * nx), iy = (int)(r % ny), iz = (int)(r / ny);
+  if (a == 0) { ix += dir; ix = ix < 0 ? ix + g.nx : (ix >= g.nx ? ix - g.nx : ix); }
+  else if (a == 1) { iy += dir; iy = iy < 0 ? iy + g.ny : (iy >= g.ny ? iy - g.ny : iy); }
+  else { iz += dir; iz = iz < 0 ? iz + g.nz : (iz >= g.nz ? iz - g.nz : iz); }
   return ((int64_t)iz * g.ny + iy) * g.nx + ix;
 }
 
@@ -225,15 +227,10 @@ struct AmrNb {
   int on;
 };
 
+// The TVB procedure on cell c; returns whether any slope changed.
 template <typename T>
-__global__ void k_tvb(Geom g, LimTabs lt, T* w, double* wmean, uint8_t* troubled, const uint8_t* __restrict__ gate,
-                      dg_mhd_params p, const DevScalars* __restrict__ sc, AmrNb an) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.ncell) return;
-  if (gate && !gate[c]) {  // learned detection: cells not flagged skip the TVB procedure
-    if (troubled) troubled[c] = 0;
-    return;
-  }
+__device__ bool tvb_cell(const Geom& g, const LimTabs& lt, T* w, const double* wmean, const dg_mhd_params& p,
+                         const DevScalars* __restrict__ sc, const AmrNb& an, int64_t c) {
   const int64_t S = g.stride;
   const int V = g.V;
   double m[9];
@@ -330,8 +327,7 @@ __global__ void k_tvb(Geom g, LimTabs lt, T* w, double* wmean, uint8_t* troubled
       for (int k = 0; k < 9; ++k) nsl[a][k] = sl[a][k];
     }
   }
-  if (troubled) troubled[c] = any ? 1 : 0;
-  if (!any) return;
+  if (!any) return false;
   // Legendre rows: degree-1 slopes, degree >= 2 zeroed
   for (int r = 0; r < g.nrows; ++r) {
     const bool ldf = g.ldf0 >= 0 && r >= g.ldf0 && r < g.ldf0 + g.ndiv;
@@ -383,6 +379,26 @@ __global__ void k_tvb(Geom g, LimTabs lt, T* w, double* wmean, uint8_t* troubled
       w[i] = (T)val;
     }
   }
+  return true;
+}
+
+// TVB over every cell (list == nullptr: the plain detector) or over the cells
+// the learned indicator listed (list[0 .. sc->nflag)); grid-stride, so any
+// grid covers the work. Counts the cells whose slopes changed.
+template <typename T>
+__global__ void k_tvb(Geom g, LimTabs lt, T* w, double* wmean, uint8_t* troubled, const int32_t* __restrict__ list,
+                      dg_mhd_params p, DevScalars* sc, AmrNb an) {
+  const int64_t total = list ? (int64_t)sc->nflag : g.ncell;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  unsigned limited = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += step) {
+    const int64_t c = list ? (int64_t)list[i] : i;
+    const bool any = tvb_cell(g, lt, w, wmean, p, sc, an, c);
+    if (troubled) troubled[c] = any ? 1 : 0;
+    limited += any ? 1u : 0u;
+  }
+  limited = __reduce_add_sync(0xffffffffu, limited);
+  if ((threadIdx.x & 31) == 0 && limited) atomicAdd(&sc->cnt_limited, (unsigned long long)limited);
 }
 
 // ------------------------------------------------------------------ positivity
@@ -428,69 +444,88 @@ __device__ __forceinline__ void point_state(const Geom& g, const Tables<T>& tb, 
   }
 }
 
+// FP32 form: rigorous screen in the working precision from the float mirror
+// of the means (|P_l| <= 1, |phi_j,c| <= ldf_maxabs on the cell, relative
+// margin 1e-4 for the rounding of the bound). True: the cell clears the floors
+// at every point and needs no further work.
 template <typename T>
-__global__ void k_pos(Geom g, Tables<T> tb, LimTabs lt, T* w, double* wmean, dg_mhd_params p, DevScalars* sc) {
+__device__ __forceinline__ bool pos_screen(const Geom& g, const LimTabs& lt, const T* w, const dg_mhd_params& p,
+                                           int64_t c) {
+  const int64_t S = g.stride;
+  T mt[8];
+  for (int k = 0; k < 5; ++k) mt[k] = w[(int64_t)lmean_row(g, k) * S + c];
+  if (g.glm) {
+    for (int k = 5; k < 8; ++k) mt[k] = w[(int64_t)lmean_row(g, k) * S + c];
+  } else {
+    mt[5] = mt[6] = mt[7] = T(0);
+    for (int j = 0; j < g.D; ++j)
+      for (int cc = 0; cc < g.D; ++cc) mt[5 + cc] += w[(int64_t)(g.ldf0 + j) * S + c] * (T)lt.ldf_mean0[j * 3 + cc];
+    if (g.bz2d >= 0) mt[7] = w[(int64_t)g.bz2d * S + c];
+  }
+  T dv[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+  const int nlg = g.glm ? 8 : 5;
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    if (v >= nlg) continue;
+    for (int l = 1; l < g.n; ++l) {
+      const T x = w[(int64_t)(v * g.n + l) * S + c];
+      dv[v] += x < T(0) ? -x : x;
+    }
+  }
+  if (!g.glm) {
+    for (int j = g.D; j < g.ndiv; ++j) {
+      T aj = w[(int64_t)(g.ldf0 + j) * S + c];
+      aj = aj < T(0) ? -aj : aj;
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc)
+        if (cc < g.D) dv[5 + cc] += aj * (T)lt.ldf_maxabs[j * 3 + cc];
+    }
+    if (g.bz2d >= 0)
+      for (int l = 1; l < g.n; ++l) {
+        const T x = w[(int64_t)(g.bz2d + l) * S + c];
+        dv[7] += x < T(0) ? -x : x;
+      }
+  }
+  const T mg = T(1e-4);
+#pragma unroll
+  for (int v = 0; v < 8; ++v) dv[v] = dv[v] * (T(1) + mg) + mg * (mt[v] < T(0) ? -mt[v] : mt[v]);
+  const T rlo = mt[0] - dv[0];
+  if (rlo > (T)p.eps_rho * T(2)) {
+    T kin = T(0), mag = T(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const T mu = (mt[1 + i] < T(0) ? -mt[1 + i] : mt[1 + i]) + dv[1 + i];
+      const T bu = (mt[5 + i] < T(0) ? -mt[5 + i] : mt[5 + i]) + dv[5 + i];
+      kin += mu * mu;
+      mag += bu * bu;
+    }
+    const T plo = (T)(g.gamma - 1.0) * (mt[4] - dv[4] - T(0.5) * kin / rlo - T(0.5) * mag);
+    if (plo > (T)p.eps_p * T(2) + mg * (mt[4] < T(0) ? -mt[4] : mt[4])) return true;
+  }
+  return false;
+}
+
+// FP32 form: screen every cell; the cells that do not clear it are appended to
+// list[0 .. sc->npos) (ballot + one atomic per warp) for k_pos.
+__global__ void k_pos_screen(Geom g, LimTabs lt, const float* __restrict__ w, dg_mhd_params p, DevScalars* sc,
+                             int32_t* __restrict__ list) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.ncell) return;
+  const bool fail = c < g.ncell && !pos_screen(g, lt, w, p, c);
+  const unsigned bal = __ballot_sync(0xffffffffu, fail);
+  const int lane = threadIdx.x & 31;
+  unsigned at = 0;
+  if (lane == 0 && bal) at = atomicAdd(&sc->npos, (unsigned)__popc(bal));
+  at = __shfl_sync(0xffffffffu, at, 0);
+  if (fail) list[at + __popc(bal & ((1u << lane) - 1u))] = (int32_t)c;
+}
+
+// Positivity procedure of one cell (Sec. 4.3).
+template <typename T>
+__device__ void pos_cell(const Geom& g, const Tables<T>& tb, const LimTabs& lt, T* w, double* wmean,
+                         const dg_mhd_params& p, DevScalars* sc, int64_t c) {
   const int64_t S = g.stride;
   const int nm = g.glm ? 9 : 8;
   const bool mix = wmean != nullptr;
-  if (mix) {
-    // FP32 form: rigorous screen in the working precision from the float
-    // mirror of the means (|P_l| <= 1, |phi_j,c| <= ldf_maxabs on the cell,
-    // relative margin 1e-4 for the rounding of the bound); cells that clear
-    // the floors everywhere are done without any FP64 work
-    T mt[8];
-    for (int k = 0; k < 5; ++k) mt[k] = w[(int64_t)lmean_row(g, k) * S + c];
-    if (g.glm) {
-      for (int k = 5; k < 8; ++k) mt[k] = w[(int64_t)lmean_row(g, k) * S + c];
-    } else {
-      mt[5] = mt[6] = mt[7] = T(0);
-      for (int j = 0; j < g.D; ++j)
-        for (int cc = 0; cc < g.D; ++cc) mt[5 + cc] += w[(int64_t)(g.ldf0 + j) * S + c] * (T)lt.ldf_mean0[j * 3 + cc];
-      if (g.bz2d >= 0) mt[7] = w[(int64_t)g.bz2d * S + c];
-    }
-    T dv[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-    const int nlg = g.glm ? 8 : 5;
-#pragma unroll
-    for (int v = 0; v < 8; ++v) {
-      if (v >= nlg) continue;
-      for (int l = 1; l < g.n; ++l) {
-        const T x = w[(int64_t)(v * g.n + l) * S + c];
-        dv[v] += x < T(0) ? -x : x;
-      }
-    }
-    if (!g.glm) {
-      for (int j = g.D; j < g.ndiv; ++j) {
-        T aj = w[(int64_t)(g.ldf0 + j) * S + c];
-        aj = aj < T(0) ? -aj : aj;
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc)
-          if (cc < g.D) dv[5 + cc] += aj * (T)lt.ldf_maxabs[j * 3 + cc];
-      }
-      if (g.bz2d >= 0)
-        for (int l = 1; l < g.n; ++l) {
-          const T x = w[(int64_t)(g.bz2d + l) * S + c];
-          dv[7] += x < T(0) ? -x : x;
-        }
-    }
-    const T mg = T(1e-4);
-#pragma unroll
-    for (int v = 0; v < 8; ++v) dv[v] = dv[v] * (T(1) + mg) + mg * (mt[v] < T(0) ? -mt[v] : mt[v]);
-    const T rlo = mt[0] - dv[0];
-    if (rlo > (T)p.eps_rho * T(2)) {
-      T kin = T(0), mag = T(0);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const T mu = (mt[1 + i] < T(0) ? -mt[1 + i] : mt[1 + i]) + dv[1 + i];
-        const T bu = (mt[5 + i] < T(0) ? -mt[5 + i] : mt[5 + i]) + dv[5 + i];
-        kin += mu * mu;
-        mag += bu * bu;
-      }
-      const T plo = (T)(g.gamma - 1.0) * (mt[4] - dv[4] - T(0.5) * kin / rlo - T(0.5) * mag);
-      if (plo > (T)p.eps_p * T(2) + mg * (mt[4] < T(0) ? -mt[4] : mt[4])) return;
-    }
-  }
   // raw mean rows (Legendre mode 0 / degree-0 LDF weights)
   double mr[9];
   for (int k = 0; k < nm; ++k) mr[k] = mix ? wmean[k * S + c] : (double)w[(int64_t)lmean_row(g, k) * S + c];
@@ -688,6 +723,16 @@ __global__ void k_pos(Geom g, Tables<T> tb, LimTabs lt, T* w, double* wmean, dg_
   }
 }
 
+// Every cell (list == nullptr) or the listed cells list[0 .. sc->npos); grid-stride.
+template <typename T>
+__global__ void k_pos(Geom g, Tables<T> tb, LimTabs lt, T* w, double* wmean, dg_mhd_params p, DevScalars* sc,
+                      const int32_t* __restrict__ list) {
+  const int64_t total = list ? (int64_t)sc->npos : g.ncell;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += step)
+    pos_cell(g, tb, lt, w, wmean, p, sc, list ? (int64_t)list[i] : i);
+}
+
 }  // namespace
 
 int upload_limiter_tables(Ctx& c) {
@@ -748,31 +793,47 @@ int run_limiter(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t 
   const Geom& g = c.g;
   const unsigned nb = (unsigned)((g.ncell + 127) / 128);
   if (c.p.limiter == DG_LIMIT_TVB || c.p.limiter == DG_LIMIT_MLP) {
-    const uint8_t* gate = nullptr;
+    const int32_t* list = nullptr;
+    unsigned nbt = nb;
+    ++c.lim_passes;
     if (c.p.limiter == DG_LIMIT_MLP) {
       if (!c.mlp_w1) return DG_E_ARG;  // no weights set
+      // the indicator appends the cells it flags to flag_list; only those go
+      // through the TVB procedure (a persistent grid walks the list)
+      if (troubled) cudaMemsetAsync(troubled, 0, (size_t)g.ncell, st);
+      cudaMemsetAsync(&c.sc->nflag, 0, sizeof(unsigned), st);
       c.prof.begin(6, st);
-      const int e = mlp_infer_launch(c, w, wmean, c.troubled, nullptr, st);
+      const int e = mlp_infer_launch(c, w, wmean, nullptr, nullptr, st, c.flag_list);
       c.prof.end(6, st);
       if (e) return e;
-      gate = c.troubled;
+      list = c.flag_list;
+      nbt = (unsigned)std::min<int64_t>(nb, (int64_t)c.nsm * 16);
+    } else {
+      c.lim_plain_cells += g.ncell;
     }
     c.prof.begin(3, st);
     // FP32 form: the float mode-0 rows mirror the FP64 means exactly; reading
     // them avoids FP64 conversions (the limiter never changes the means)
     const AmrNb an{c.amr.fL, c.amr.fR, c.amr.fmeta, c.amr.cstart, c.amr.centry, c.amr.dxc, c.amr.on ? 1 : 0};
     if (c.p.precision == DG_PREC_FP32MIX)
-      k_tvb<float><<<nb, 128, 0, st>>>(g, c.lim, (float*)w, nullptr, troubled, gate, c.p, c.sc, an);
+      k_tvb<float><<<nbt, 128, 0, st>>>(g, c.lim, (float*)w, nullptr, troubled, list, c.p, c.sc, an);
     else
-      k_tvb<double><<<nb, 128, 0, st>>>(g, c.lim, (double*)w, nullptr, troubled, gate, c.p, c.sc, an);
+      k_tvb<double><<<nbt, 128, 0, st>>>(g, c.lim, (double*)w, nullptr, troubled, list, c.p, c.sc, an);
     c.prof.end(3, st);
   }
   if (c.p.positivity) {
     c.prof.begin(5, st);
-    if (c.p.precision == DG_PREC_FP32MIX)
-      k_pos<float><<<nb, 128, 0, st>>>(g, c.t32, c.lim, (float*)w, wmean, c.p, c.sc);
-    else
-      k_pos<double><<<nb, 128, 0, st>>>(g, c.t64, c.lim, (double*)w, nullptr, c.p, c.sc);
+    if (c.p.precision == DG_PREC_FP32MIX) {
+      // cheap FP32 screen over every cell; the full procedure only on the few
+      // cells it lists (so a warp never waits on one lane's FP64 recovery)
+      cudaMemsetAsync(&c.sc->npos, 0, sizeof(unsigned), st);
+      k_pos_screen<<<nb, 128, 0, st>>>(g, c.lim, (const float*)w, c.p, c.sc, c.pos_list);
+      const unsigned nbl = (unsigned)std::min<int64_t>(nb, (int64_t)c.nsm * 16);
+      k_pos<float><<<nbl, 128, 0, st>>>(g, c.t32, c.lim, (float*)w, wmean, c.p, c.sc, c.pos_list);
+      c.prof.launches[5] += 1;
+    } else {
+      k_pos<double><<<nb, 128, 0, st>>>(g, c.t64, c.lim, (double*)w, nullptr, c.p, c.sc, nullptr);
+    }
     c.prof.end(5, st);
   }
   return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;

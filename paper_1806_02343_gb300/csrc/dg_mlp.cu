@@ -29,14 +29,15 @@ namespace {
 
 constexpr int HID = 64;
 
+// periodic face neighbour on the uniform mesh (cell counts stay below 2^31,
+// so the index arithmetic is 32-bit)
 __device__ __forceinline__ int64_t nbc(const Geom& g, int64_t c, int a, int dir) {
-  int ix = (int)(c % g.nx);
-  int64_t r = c / g.nx;
-  int iy = (int)(r % g.ny);
-  int iz = (int)(r / g.ny);
-  if (a == 0) ix = (ix + dir + g.nx) % g.nx;
-  else if (a == 1) iy = (iy + dir + g.ny) % g.ny;
-  else iz = (iz + dir + g.nz) % g.nz;
+  const unsigned cc = (unsigned)c, nx = (unsigned)g.nx, ny = (unsigned)g.ny;
+  const unsigned r = cc / nx;
+  int ix = (int)(cc - r * nx), iy = (int)(r % ny), iz = (int)(r / ny);
+  if (a == 0) { ix += dir; ix = ix < 0 ? ix + g.nx : (ix >= g.nx ? ix - g.nx : ix); }
+  else if (a == 1) { iy += dir; iy = iy < 0 ? iy + g.ny : (iy >= g.ny ? iy - g.ny : iy); }
+  else { iz += dir; iz = iz < 0 ? iz + g.nz : (iz >= g.nz ? iz - g.nz : iz); }
   return ((int64_t)iz * g.ny + iy) * g.nx + ix;
 }
 
@@ -151,110 +152,135 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint
 }
 
 // One warp infers 32 cells (two m16 tiles); KP = padded input width (multiple of 16).
-// Shared layout: W1s[64][KP+8] bf16, W2s[64][72] bf16, Xs[warps][32][KP+8] bf16, biases f32.
+// Shared layout: W1s[64][KP+8] bf16, W2s[64][72] bf16, Xs[warps][32][KP+8] bf16, biases f32,
+// flags of the warp's 32 cells. Persistent: the weights are staged once per block and the
+// block walks 128-cell tiles with a grid stride. With `list`, each warp appends its flagged
+// cells (ballot + one atomic per warp) to list and counts them in sc.
 template <typename T, int KP>
 __global__ void __launch_bounds__(128) k_mlp_infer(Geom g, MlpTabs mt, const T* __restrict__ w,
                                                    const double* __restrict__ wmean,
                                                    const __nv_bfloat16* __restrict__ W1,
                                                    const __nv_bfloat16* __restrict__ W2,
                                                    const float* __restrict__ bias, float thresh,
-                                                   uint8_t* __restrict__ flag, float* __restrict__ prob) {
+                                                   uint8_t* __restrict__ flag, float* __restrict__ prob,
+                                                   int32_t* __restrict__ list, DevScalars* __restrict__ sc) {
   constexpr int LD1 = KP + 8, LD2 = HID + 8;
   extern __shared__ __align__(16) unsigned char smraw[];
   __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(smraw);
   __nv_bfloat16* W2s = W1s + HID * LD1;
   __nv_bfloat16* Xs = W2s + HID * LD2;
   float* bs = reinterpret_cast<float*>(Xs + 4 * 32 * LD1);  // b1[64], b2[64], w3[64], b3
+  uint8_t* fl = reinterpret_cast<uint8_t*>(bs + 3 * HID + 1);  // [4][32]
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   for (int i = t; i < HID * KP; i += 128) W1s[(i / KP) * LD1 + i % KP] = W1[i];
   for (int i = t; i < HID * HID; i += 128) W2s[(i / HID) * LD2 + i % HID] = W2[i];
   for (int i = t; i < 3 * HID + 1; i += 128) bs[i] = bias[i];
-  // features of this thread's cell
-  const int64_t c = (int64_t)blockIdx.x * 128 + t;
-  const bool live = c < g.ncell;
-  {
-    const int nin = 8 * g.n + 10 * g.D;
-    __nv_bfloat16* xr = Xs + (warp * 32 + lane) * LD1;
-    for (int k = live ? nin : 0; k < KP; ++k) xr[k] = __float2bfloat16_rn(0.f);
-    if (live) cell_features(g, mt, w, wmean, c, [&](int k, float v) { xr[k] = __float2bfloat16_rn(v); });
-  }
   __syncthreads();
   const int gq = lane >> 2, tq = lane & 3;
-  for (int tile = 0; tile < 2; ++tile) {
-    const __nv_bfloat16* Xt = Xs + (warp * 32 + tile * 16) * LD1;
-    float h1[8][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      h1[j][0] = bs[8 * j + 2 * tq];
-      h1[j][1] = bs[8 * j + 2 * tq + 1];
-      h1[j][2] = bs[8 * j + 2 * tq];
-      h1[j][3] = bs[8 * j + 2 * tq + 1];
+  const int nin = 8 * g.n + 10 * g.D;
+  for (int64_t base = (int64_t)blockIdx.x * 128; base < g.ncell; base += (int64_t)gridDim.x * 128) {
+    // features of this thread's cell (rows of Xs are private to the warp)
+    const int64_t c = base + t;
+    const bool live = c < g.ncell;
+    {
+      __nv_bfloat16* xr = Xs + (warp * 32 + lane) * LD1;
+      for (int k = live ? nin : 0; k < KP; ++k) xr[k] = __float2bfloat16_rn(0.f);
+      if (live) cell_features(g, mt, w, wmean, c, [&](int k, float v) { xr[k] = __float2bfloat16_rn(v); });
     }
-#pragma unroll
-    for (int kk = 0; kk < KP / 16; ++kk) {
-      uint32_t a[4];
-      a[0] = *reinterpret_cast<const uint32_t*>(Xt + gq * LD1 + 16 * kk + 2 * tq);
-      a[1] = *reinterpret_cast<const uint32_t*>(Xt + (gq + 8) * LD1 + 16 * kk + 2 * tq);
-      a[2] = *reinterpret_cast<const uint32_t*>(Xt + gq * LD1 + 16 * kk + 8 + 2 * tq);
-      a[3] = *reinterpret_cast<const uint32_t*>(Xt + (gq + 8) * LD1 + 16 * kk + 8 + 2 * tq);
+    __syncwarp();
+    for (int tile = 0; tile < 2; ++tile) {
+      const __nv_bfloat16* Xt = Xs + (warp * 32 + tile * 16) * LD1;
+      float h1[8][4];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        uint32_t b[2];
-        b[0] = *reinterpret_cast<const uint32_t*>(W1s + (8 * j + gq) * LD1 + 16 * kk + 2 * tq);
-        b[1] = *reinterpret_cast<const uint32_t*>(W1s + (8 * j + gq) * LD1 + 16 * kk + 8 + 2 * tq);
-        mma_bf16(h1[j], a, b);
+        h1[j][0] = bs[8 * j + 2 * tq];
+        h1[j][1] = bs[8 * j + 2 * tq + 1];
+        h1[j][2] = bs[8 * j + 2 * tq];
+        h1[j][3] = bs[8 * j + 2 * tq + 1];
       }
-    }
-    // ReLU; accumulator tiles 2kk, 2kk+1 form the A fragment of layer 2's k-step kk
-    float h2[8][4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      h2[j][0] = bs[HID + 8 * j + 2 * tq];
-      h2[j][1] = bs[HID + 8 * j + 2 * tq + 1];
-      h2[j][2] = bs[HID + 8 * j + 2 * tq];
-      h2[j][3] = bs[HID + 8 * j + 2 * tq + 1];
-    }
+      for (int kk = 0; kk < KP / 16; ++kk) {
+        uint32_t a[4];
+        a[0] = *reinterpret_cast<const uint32_t*>(Xt + gq * LD1 + 16 * kk + 2 * tq);
+        a[1] = *reinterpret_cast<const uint32_t*>(Xt + (gq + 8) * LD1 + 16 * kk + 2 * tq);
+        a[2] = *reinterpret_cast<const uint32_t*>(Xt + gq * LD1 + 16 * kk + 8 + 2 * tq);
+        a[3] = *reinterpret_cast<const uint32_t*>(Xt + (gq + 8) * LD1 + 16 * kk + 8 + 2 * tq);
 #pragma unroll
-    for (int kk = 0; kk < HID / 16; ++kk) {
-      uint32_t a[4];
-      a[0] = pack_bf16(fmaxf(h1[2 * kk][0], 0.f), fmaxf(h1[2 * kk][1], 0.f));
-      a[1] = pack_bf16(fmaxf(h1[2 * kk][2], 0.f), fmaxf(h1[2 * kk][3], 0.f));
-      a[2] = pack_bf16(fmaxf(h1[2 * kk + 1][0], 0.f), fmaxf(h1[2 * kk + 1][1], 0.f));
-      a[3] = pack_bf16(fmaxf(h1[2 * kk + 1][2], 0.f), fmaxf(h1[2 * kk + 1][3], 0.f));
+        for (int j = 0; j < 8; ++j) {
+          uint32_t b[2];
+          b[0] = *reinterpret_cast<const uint32_t*>(W1s + (8 * j + gq) * LD1 + 16 * kk + 2 * tq);
+          b[1] = *reinterpret_cast<const uint32_t*>(W1s + (8 * j + gq) * LD1 + 16 * kk + 8 + 2 * tq);
+          mma_bf16(h1[j], a, b);
+        }
+      }
+      // ReLU; accumulator tiles 2kk, 2kk+1 form the A fragment of layer 2's k-step kk
+      float h2[8][4];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        uint32_t b[2];
-        b[0] = *reinterpret_cast<const uint32_t*>(W2s + (8 * j + gq) * LD2 + 16 * kk + 2 * tq);
-        b[1] = *reinterpret_cast<const uint32_t*>(W2s + (8 * j + gq) * LD2 + 16 * kk + 8 + 2 * tq);
-        mma_bf16(h2[j], a, b);
+        h2[j][0] = bs[HID + 8 * j + 2 * tq];
+        h2[j][1] = bs[HID + 8 * j + 2 * tq + 1];
+        h2[j][2] = bs[HID + 8 * j + 2 * tq];
+        h2[j][3] = bs[HID + 8 * j + 2 * tq + 1];
       }
-    }
-    // output layer: rows gq and gq+8 of the tile, reduced over the quad
-    float o0 = 0.f, o1 = 0.f;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float w0 = bs[2 * HID + 8 * j + 2 * tq], w1 = bs[2 * HID + 8 * j + 2 * tq + 1];
-      o0 += fmaxf(h2[j][0], 0.f) * w0 + fmaxf(h2[j][1], 0.f) * w1;
-      o1 += fmaxf(h2[j][2], 0.f) * w0 + fmaxf(h2[j][3], 0.f) * w1;
-    }
-    o0 += __shfl_xor_sync(0xffffffffu, o0, 1);
-    o0 += __shfl_xor_sync(0xffffffffu, o0, 2);
-    o1 += __shfl_xor_sync(0xffffffffu, o1, 1);
-    o1 += __shfl_xor_sync(0xffffffffu, o1, 2);
-    if (tq == 0) {
-      const float b3 = bs[3 * HID];
-      const int64_t c0 = (int64_t)blockIdx.x * 128 + warp * 32 + tile * 16 + gq;
-      const float p0 = 1.f / (1.f + __expf(-(o0 + b3)));
-      const float p1 = 1.f / (1.f + __expf(-(o1 + b3)));
-      if (c0 < g.ncell) {
-        if (flag) flag[c0] = p0 > thresh ? 1 : 0;
-        if (prob) prob[c0] = p0;
+      for (int kk = 0; kk < HID / 16; ++kk) {
+        uint32_t a[4];
+        a[0] = pack_bf16(fmaxf(h1[2 * kk][0], 0.f), fmaxf(h1[2 * kk][1], 0.f));
+        a[1] = pack_bf16(fmaxf(h1[2 * kk][2], 0.f), fmaxf(h1[2 * kk][3], 0.f));
+        a[2] = pack_bf16(fmaxf(h1[2 * kk + 1][0], 0.f), fmaxf(h1[2 * kk + 1][1], 0.f));
+        a[3] = pack_bf16(fmaxf(h1[2 * kk + 1][2], 0.f), fmaxf(h1[2 * kk + 1][3], 0.f));
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          uint32_t b[2];
+          b[0] = *reinterpret_cast<const uint32_t*>(W2s + (8 * j + gq) * LD2 + 16 * kk + 2 * tq);
+          b[1] = *reinterpret_cast<const uint32_t*>(W2s + (8 * j + gq) * LD2 + 16 * kk + 8 + 2 * tq);
+          mma_bf16(h2[j], a, b);
+        }
       }
-      if (c0 + 8 < g.ncell) {
-        if (flag) flag[c0 + 8] = p1 > thresh ? 1 : 0;
-        if (prob) prob[c0 + 8] = p1;
+      // output layer: rows gq and gq+8 of the tile, reduced over the quad
+      float o0 = 0.f, o1 = 0.f;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float w0 = bs[2 * HID + 8 * j + 2 * tq], w1 = bs[2 * HID + 8 * j + 2 * tq + 1];
+        o0 += fmaxf(h2[j][0], 0.f) * w0 + fmaxf(h2[j][1], 0.f) * w1;
+        o1 += fmaxf(h2[j][2], 0.f) * w0 + fmaxf(h2[j][3], 0.f) * w1;
+      }
+      o0 += __shfl_xor_sync(0xffffffffu, o0, 1);
+      o0 += __shfl_xor_sync(0xffffffffu, o0, 2);
+      o1 += __shfl_xor_sync(0xffffffffu, o1, 1);
+      o1 += __shfl_xor_sync(0xffffffffu, o1, 2);
+      if (tq == 0) {
+        const float b3 = bs[3 * HID];
+        const int r0 = tile * 16 + gq;
+        const int64_t c0 = base + warp * 32 + r0;
+        const float p0 = 1.f / (1.f + __expf(-(o0 + b3)));
+        const float p1 = 1.f / (1.f + __expf(-(o1 + b3)));
+        fl[warp * 32 + r0] = p0 > thresh ? 1 : 0;
+        fl[warp * 32 + r0 + 8] = p1 > thresh ? 1 : 0;
+        if (c0 < g.ncell) {
+          if (flag) flag[c0] = p0 > thresh ? 1 : 0;
+          if (prob) prob[c0] = p0;
+        }
+        if (c0 + 8 < g.ncell) {
+          if (flag) flag[c0 + 8] = p1 > thresh ? 1 : 0;
+          if (prob) prob[c0 + 8] = p1;
+        }
       }
     }
+    __syncwarp();
+    if (list) {
+      const bool mine = live && fl[warp * 32 + lane] != 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, mine);
+      const int cnt = __popc(bal);
+      unsigned at = 0;
+      if (lane == 0 && cnt) {
+        at = atomicAdd(&sc->nflag, (unsigned)cnt);
+        atomicAdd(&sc->cnt_flagged, (unsigned long long)cnt);
+      }
+      at = __shfl_sync(0xffffffffu, at, 0);
+      if (mine) list[at + __popc(bal & ((1u << lane) - 1u))] = (int32_t)c;
+    }
+    __syncwarp();
   }
 }
 
@@ -540,29 +566,34 @@ int mlp_set_weights(Ctx& c, const float* theta_dev, int nin, float thresh) {
 }
 
 template <typename T, int KP>
-static void infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* flag, float* prob, cudaStream_t st) {
+static void infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* flag, float* prob, cudaStream_t st,
+                         int32_t* list) {
   const Geom& g = c.g;
   const size_t sm = (size_t)HID * (KP + 8) * 2 + (size_t)HID * (HID + 8) * 2 + (size_t)4 * 32 * (KP + 8) * 2 +
-                    (3 * HID + 1) * sizeof(float);
+                    (3 * HID + 1) * sizeof(float) + 128;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_mlp_infer<T, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
   }
-  const unsigned nb = (unsigned)((g.ncell + 127) / 128);
+  // persistent grid: a few blocks per SM (the weights are staged once per block)
+  const int64_t tiles = (g.ncell + 127) / 128;
+  const unsigned nb = (unsigned)std::min<int64_t>(tiles, (int64_t)c.nsm * 4);
   k_mlp_infer<T, KP><<<nb, 128, sm, st>>>(g, c.mlp, (const T*)w, wmean, (const __nv_bfloat16*)c.mlp_w1,
-                                           (const __nv_bfloat16*)c.mlp_w2, c.mlp_bias, c.mlp_thresh, flag, prob);
+                                           (const __nv_bfloat16*)c.mlp_w2, c.mlp_bias, c.mlp_thresh, flag, prob,
+                                           list, c.sc);
 }
 
-int mlp_infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* flag, float* prob, cudaStream_t st) {
+int mlp_infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* flag, float* prob, cudaStream_t st,
+                     int32_t* list) {
   if (!c.mlp_w1) return -1;
   const bool f32 = c.p.precision == DG_PREC_FP32MIX;
   // FP32 form: features read the float mirror of the FP64 means (exact copies)
   switch (c.mlp_kp) {
 #define KPCASE(K)                                                                 \
   case K:                                                                         \
-    if (f32) infer_launch<float, K>(c, w, nullptr, flag, prob, st);               \
-    else infer_launch<double, K>(c, w, nullptr, flag, prob, st);                  \
+    if (f32) infer_launch<float, K>(c, w, nullptr, flag, prob, st, list);         \
+    else infer_launch<double, K>(c, w, nullptr, flag, prob, st, list);            \
     break;
     KPCASE(64)
     KPCASE(80)

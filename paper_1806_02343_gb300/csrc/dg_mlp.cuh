@@ -9,7 +9,10 @@ inline int mlp_n_params(int nin) { return 64 * nin + 64 + 64 * 64 + 64 + 64 + 1;
 int mlp_build_tables(Ctx& c);
 int mlp_features_launch(Ctx& c, const void* w, const double* wmean, float* X, int ldx, cudaStream_t st);
 int mlp_set_weights(Ctx& c, const float* theta_dev, int nin, float thresh);
-int mlp_infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* flag, float* prob, cudaStream_t st);
+// flag / prob / list may be null; with list, the flagged cells are appended to
+// list[0 .. c.sc->nflag) (the caller zeroes nflag first).
+int mlp_infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* flag, float* prob, cudaStream_t st,
+                     int32_t* list = nullptr);
 size_t mlp_scratch_bytes(int nb);
 int mlp_loss_grad_dev(const float* X, int ldx, const uint8_t* y, const int64_t* perm, int64_t off, int nb, int nin,
                       const float* theta, float* grad, double* loss, float pos_weight, float norm_n, void* scratch,

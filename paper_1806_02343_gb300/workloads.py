@@ -383,12 +383,12 @@ def octree_leaves(D, base_level, max_level, refine):
     return sorted(leaves, key=morton)
 
 
-def turbulence_nodal(n, npts, stride, device="cuda", seed=1234, nvar=9):
+def turbulence_nodal(n, npts, stride, device="cuda", seed=1234, nvar=9, mach=2.0):
     """Decaying-turbulence start at the npts^3 Gauss points of every cell of an
     n^3 box, laid out [var][q][stride] (built slab by slab on the device)."""
     import torch
     g1, _ = np.polynomial.legendre.leggauss(npts)
-    T = Turbulence3D(seed=seed, nvar=nvar)
+    T = Turbulence3D(seed=seed, nvar=nvar, mach=mach)
     coords = ((torch.arange(n, device=device, dtype=torch.float64)[:, None] + 0.5
                + 0.5 * torch.as_tensor(g1, device=device)[None, :]) / n).reshape(-1)
     Q = npts ** 3

@@ -57,6 +57,9 @@ def test_init_rejects_bad_arguments(lib):
     assert lib.dg_mhd_init(ctypes.byref(m), 2, 5, 5.0 / 3.0, None, ctypes.byref(h)) == -1
     assert lib.dg_mhd_init(ctypes.byref(m), 2, 0, 1.0, None, ctypes.byref(h)) == -1
     assert lib.dg_mhd_init(None, 2, 0, 1.4, None, ctypes.byref(h)) == -1
+    m.n[0] = m.n[1] = 2048
+    m.n[2] = 1024                                        # 2^32 cells: beyond 32-bit indices
+    assert lib.dg_mhd_init(ctypes.byref(m), 2, 0, 5.0 / 3.0, None, ctypes.byref(h)) == -2
     assert lib.dg_mhd_rhs(None, None, None, None, None, None) == -1
     assert lib.dg_mhd_step(None, None, None, None, None) == -1
 

@@ -139,3 +139,36 @@ def test_gated_tvb_limits(divb):
         assert rel_err(from_device(w, sol), expect) < 1e-12
         f = flags[: sol.ncell].cpu().numpy().astype(bool)
         assert np.array_equal(f, trig if b3 > 0 else np.zeros_like(trig))
+
+
+@pytest.mark.parametrize("divb", ["powell", "glm"])
+def test_gated_tvb_partial_flags_and_counts(divb):
+    """Part of the cells flagged: flagged cells get the TVB result, the others
+    stay unchanged; the list-driven TVB pass counts flagged and limited cells."""
+    import torch
+    S = Scheme(3, 2, divb, G, (9, 7, 6))
+    S.P.Mtilde = 0.5
+    w0 = S.project(_shock(S.V))
+    ref, trig = Limiter(S, tvb=True, positivity=False).tvb_limit(w0, 3.0)
+    th = M.init_params(110, seed=7)
+    z, _ = M.forward(th, M.features(S, w0))
+    th[-1] -= float(np.median(z))
+    sol = _solver(S, limiter=2, Mtilde=0.5)
+    if divb == "glm":
+        sol.set_glm(3.0, 1.0)
+    sol.mlp_set_weights(torch.as_tensor(th, dtype=torch.float32, device="cuda"), 0.5)
+    w = to_device(w0, sol)
+    gate = torch.zeros(sol.stride, dtype=torch.uint8, device="cuda")
+    sol.mlp_infer(w, None, gate, None)
+    g = gate[: sol.ncell].cpu().numpy().astype(bool)
+    assert 0.05 < g.mean() < 0.95
+    sol.limiter_counts(reset=True)
+    flags = torch.zeros(sol.stride, dtype=torch.uint8, device="cuda")
+    sol.limit(w, None, flags)
+    out = from_device(w, sol)
+    expect = np.where(g[:, None], ref, w0)
+    assert rel_err(out, expect) < 1e-12
+    f = flags[: sol.ncell].cpu().numpy().astype(bool)
+    assert np.array_equal(f, trig & g)
+    cnt = sol.limiter_counts()
+    assert cnt == {"passes": 1, "flagged": int(g.sum()), "limited": int((trig & g).sum())}
