@@ -174,8 +174,14 @@ void free_tables(Tables<T>& t) {
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 template <typename T, int DEG>
-void* make_fast_tabs(const HostTables& h, const Geom& g) {
+void* make_fast_tabs(const HostTables& h, const Geom& g, const Basis& B) {
   using Dm = FastDims<DEG>;
+  // the kernels unroll over the mode exponents known at compile time
+  constexpr ModeTab<DEG> MT{};
+  if ((int)B.modes.size() != Dm::N) return nullptr;
+  for (int l = 0; l < Dm::N; ++l)
+    for (int a = 0; a < 3; ++a)
+      if (B.modes[l][a] != MT.k[l][a]) return nullptr;
   auto* ft = new FastAll<T, DEG>();
   const int n = g.n, Qv = g.Qv, Qf = g.Qf;
   for (int a = 0; a < 3; ++a)
@@ -185,15 +191,23 @@ void* make_fast_tabs(const HostTables& h, const Geom& g) {
         ft->face[a].PR[l][p] = (T)h.Pf[((size_t)(2 * a) * n + l) * Qf + p];
       }
   for (int l = 0; l < n; ++l) {
-    for (int q = 0; q < Qv; ++q) {
-      ft->cell.P[l][q] = (T)h.Pv[(size_t)l * Qv + q];
-      for (int a = 0; a < 3; ++a) ft->cell.dPw[a][l][q] = (T)(h.dPv[((size_t)a * n + l) * Qv + q] * h.wv[q]);
-    }
+    for (int q = 0; q < Qv; ++q) ft->cell.P[l][q] = (T)h.Pv[(size_t)l * Qv + q];
     for (int f = 0; f < 6; ++f)
-      for (int p = 0; p < Qf; ++p) ft->cell.Pfw[f][l][p] = (T)(h.Pf[((size_t)f * n + l) * Qf + p] * h.wf[p]);
+      for (int p = 0; p < Qf; ++p) ft->cell.Pfw[f][p][l] = (T)(h.Pf[((size_t)f * n + l) * Qf + p] * h.wf[p]);
     ft->cell.minv[l] = (T)h.minv[l];
   }
+  // gradient pairs: modes with k_a >= 1, in pairs (the last one of an odd
+  // count is paired with a zero entry)
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i < MT.cnt[a]; ++i) {
+      const int l = MT.nz[a][i];
+      for (int q = 0; q < Qv; ++q) ft->cell.dP2[a][i / 2][q][i % 2] = (T)(h.dPv[((size_t)a * n + l) * Qv + q] * h.wv[q]);
+    }
   static_assert(Dm::N > 0, "");
+  if (fast_to_constant<T, DEG>(*ft)) {
+    delete ft;
+    return nullptr;
+  }
   return ft;
 }
 
@@ -216,6 +230,9 @@ FastGeom fast_geom(const Geom& g) {
   f.ncell = g.ncell; f.stride = g.stride;
   f.dx = g.dx; f.gamma = g.gamma;
   f.metric = 2.0 / g.dx;
+  f.kmean = f.metric / 8.0;
+  f.gamma32 = (float)g.gamma;
+  f.metric32 = (float)f.metric;
   return f;
 }
 
@@ -518,13 +535,13 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
   // specialised GLM kernels for uniform 3D meshes
   if (g.glm && g.D == 3 && !prm.generic_kernels && !c.amr.on) {
     if (fp32(c)) {
-      if (degree == 1) c.fast_tabs = make_fast_tabs<float, 1>(h, g);
-      if (degree == 2) c.fast_tabs = make_fast_tabs<float, 2>(h, g);
-      if (degree == 3) c.fast_tabs = make_fast_tabs<float, 3>(h, g);
+      if (degree == 1) c.fast_tabs = make_fast_tabs<float, 1>(h, g, *c.hb);
+      if (degree == 2) c.fast_tabs = make_fast_tabs<float, 2>(h, g, *c.hb);
+      if (degree == 3) c.fast_tabs = make_fast_tabs<float, 3>(h, g, *c.hb);
       if (c.fast_tabs) c.fast = 10 + degree;
     } else {
-      if (degree == 1) c.fast_tabs = make_fast_tabs<double, 1>(h, g);
-      if (degree == 2) c.fast_tabs = make_fast_tabs<double, 2>(h, g);
+      if (degree == 1) c.fast_tabs = make_fast_tabs<double, 1>(h, g, *c.hb);
+      if (degree == 2) c.fast_tabs = make_fast_tabs<double, 2>(h, g, *c.hb);
       if (c.fast_tabs) c.fast = 20 + degree;
     }
   }

@@ -66,7 +66,16 @@ struct DevScalars {
   unsigned int npos;             // cells the FP32 positivity screen listed in the current pass
   unsigned long long cnt_flagged;  // cells flagged by the indicator, summed over passes
   unsigned long long cnt_limited;  // cells whose slopes the TVB procedure changed, summed over passes
+  float dt32, ch32, kappa32;       // FP32 copies of dt, ch, kappa (written with them)
+  float pad32;
 };
+
+// a device scalar in the working precision T (FP32 kernels read the float copy)
+template <typename T>
+__host__ __device__ __forceinline__ T pick_prec(double d, float f) {
+  if constexpr (sizeof(T) == 4) return f;
+  else return d;
+}
 
 // Limiter tables (kernel parameters): degree-1 Legendre mode per axis, mode
 // degrees, LDF degrees, LDF component means of degree-0 rows, LDF linear slopes

@@ -18,6 +18,9 @@
 //   k_cell_glm reads coalesced.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+#include <utility>
+
 #include "dg_fast.cuh"
 #include "dg_phys.cuh"
 
@@ -27,8 +30,78 @@ namespace {
 
 constexpr int TC = 32;        // cells (or faces) per block
 
+// Reference-element tables in the constant bank. They depend only on the
+// scheme and the degree (not on the mesh), so one copy serves every context;
+// indexed with compile-time offsets, each table value is a constant operand of
+// its FMA. Degree 3 in FP32 (28 KB) stays a kernel parameter: the constant
+// bank holds 64 KB per module.
+__constant__ FastAll<float, 1> c_fast_f1;
+__constant__ FastAll<float, 2> c_fast_f2;
+__constant__ FastAll<double, 1> c_fast_d1;
+__constant__ FastAll<double, 2> c_fast_d2;
+
+template <typename T, int DEG>
+struct FastConst {
+  static constexpr bool on = false;
+};
+#define FAST_CONST(T, DEG, SYM)                                                        \
+  template <>                                                                          \
+  struct FastConst<T, DEG> {                                                           \
+    static constexpr bool on = true;                                                   \
+    __device__ static const FastAll<T, DEG>& get() { return SYM; }                      \
+    static cudaError_t upload(const FastAll<T, DEG>& t) {                              \
+      return cudaMemcpyToSymbol(SYM, &t, sizeof(t));                                   \
+    }                                                                                  \
+  };
+FAST_CONST(float, 1, c_fast_f1)
+FAST_CONST(float, 2, c_fast_f2)
+FAST_CONST(double, 1, c_fast_d1)
+FAST_CONST(double, 2, c_fast_d2)
+#undef FAST_CONST
+
+template <typename T, int DEG, int A>
+__device__ __forceinline__ const FaceTabs<T, DEG>& face_tabs(const FaceTabs<T, DEG>& param) {
+  if constexpr (FastConst<T, DEG>::on) return FastConst<T, DEG>::get().face[A];
+  else return param;
+}
+
+template <typename T, int DEG>
+__device__ __forceinline__ const CellTabs<T, DEG>& cell_tabs(const CellTabs<T, DEG>& param) {
+  if constexpr (FastConst<T, DEG>::on) return FastConst<T, DEG>::get().cell;
+  else return param;
+}
+
+// compile-time loop: f(std::integral_constant<int, i>) for i = 0 .. n-1
+template <typename F, int... Is>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, Is...>) {
+  (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int Nn, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, Nn>{});
+}
+
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Two independent fused multiply-adds, x = a p + x and y = b q + y, each
+// rounded once. FP32: one packed f32x2 instruction (sm_100 and later), which
+// halves the instruction count of the contractions; FP64: two DFMAs.
+__device__ __forceinline__ void fma2(float& x, float& y, float a, float b, float p, float q) {
+  asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%0, %1};\n\t"
+      "fma.rn.f32x2 rc, ra, rb, rc;\n\t"
+      "mov.b64 {%0, %1}, rc;\n\t}"
+      : "+f"(x), "+f"(y)
+      : "f"(a), "f"(b), "f"(p), "f"(q));
+}
+__device__ __forceinline__ void fma2(double& x, double& y, double a, double b, double p, double q) {
+  x = __fma_rn(a, p, x);
+  y = __fma_rn(b, q, y);
+}
+
 constexpr int NT = 9 * TC;    // threads per block: one per (variable, cell)
 
 // Cell coordinates, computed once per thread in 32-bit arithmetic (cell
@@ -59,10 +132,11 @@ __device__ __forceinline__ int64_t nbr(const FastGeom& g, Coord k, int a, int di
 
 // ------------------------------------------------------------------ faces
 template <typename T, int DEG, int A>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_face_glm(const FaceTabs<T, DEG> tb, const FastGeom g,
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_face_glm(const FaceTabs<T, DEG> tbp, const FastGeom g,
                                                  const T* __restrict__ w, T* __restrict__ F,
                                                  const DevScalars* __restrict__ sc, T eps) {
   constexpr int N = FastDims<DEG>::N, QF = FastDims<DEG>::QF, NR = 9 * N;
+  const FaceTabs<T, DEG>& tb = face_tabs<T, DEG, A>(tbp);
   extern __shared__ __align__(16) unsigned char smraw[];
   T* WL = reinterpret_cast<T*>(smraw);       // [NR][TC]
   T* WR = WL + NR * TC;                      // [NR][TC]
@@ -103,18 +177,27 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_fa
     T wl[N];
 #pragma unroll
     for (int l = 0; l < N; ++l) wl[l] = Ws[(v * N + l) * TC + f];
+    const auto& Pt = s ? tb.PR : tb.PL;
+    // two face points per packed FMA
 #pragma unroll
-    for (int p = 0; p < QF; ++p) {
+    for (int p = 0; p + 1 < QF; p += 2) {
+      T a0 = T(0), a1 = T(0);
+#pragma unroll
+      for (int l = 0; l < N; ++l) fma2(a0, a1, wl[l], wl[l], Pt[l][p], Pt[l][p + 1]);
+      TR[((s * QF + p) * 9 + v) * TC + f] = a0;
+      TR[((s * QF + p + 1) * 9 + v) * TC + f] = a1;
+    }
+    if (QF & 1) {
       T acc = T(0);
 #pragma unroll
-      for (int l = 0; l < N; ++l) acc += wl[l] * (s ? tb.PR[l][p] : tb.PL[l][p]);
-      TR[((s * QF + p) * 9 + v) * TC + f] = acc;
+      for (int l = 0; l < N; ++l) acc = fma_rn(wl[l], Pt[l][QF - 1], acc);
+      TR[((s * QF + QF - 1) * 9 + v) * TC + f] = acc;
     }
   }
   __syncthreads();
   // HLLD per face point
-  const T ch = (T)sc->ch;
-  const T gamma = (T)g.gamma;
+  const T ch = pick_prec<T>(sc->ch, sc->ch32);
+  const T gamma = pick_prec<T>(g.gamma, g.gamma32);
   for (int p = v; p < QF; p += 9) {
     T uL[9], uR[9], Fo[9];
 #pragma unroll
@@ -135,15 +218,18 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_fa
 enum { SL_RHO = 0, SL_B = 5, SL_PSI = 8, SL_V = 9, SL_PT = 12, SL_VB = 13, SL_EPT = 14, SL_ZERO = 15, NSL = 16 };
 
 template <typename T, int DEG>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_cell_glm(const CellTabs<T, DEG> tb, const FastGeom g,
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_cell_glm(const CellTabs<T, DEG> tbp, const FastGeom g,
                                                  const T* __restrict__ w, const T* __restrict__ F, T* out,
-                                                 const T* w0, double ca, double cb, int combine,
+                                                 const T* w0, double ca, double cb, float ca32, float cb32,
+                                                 int cmode,
                                                  const DevScalars* __restrict__ sc,
                                                  const double* __restrict__ wmean, const double* w0mean,
                                                  double* outmean) {
   // out / outmean may alias w0 / w0mean: each element is read, then written, by one thread.
   constexpr int N = FastDims<DEG>::N, QV = FastDims<DEG>::QV, QF = FastDims<DEG>::QF;
   constexpr int QC = FastDims<DEG>::QC;  // volume points per pass
+  const CellTabs<T, DEG>& tb = cell_tabs<T, DEG>(tbp);
+  static_assert(N % 2 == 0, "mode pairs");
   extern __shared__ __align__(16) unsigned char smraw[];
   T* PR = reinterpret_cast<T*>(smraw);  // [QC][NSL][TC]
   const int t = threadIdx.x;
@@ -153,8 +239,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_ce
   const bool live = c < g.ncell;
   const int64_t S = g.stride;
   const bool mix = wmean != nullptr;
-  const T gamma = (T)g.gamma;
-  const T ch = (T)sc->ch;
+  const T gamma = pick_prec<T>(g.gamma, g.gamma32);
+  const T ch = pick_prec<T>(sc->ch, sc->ch32);
 
   T wl[N];
 #pragma unroll
@@ -178,19 +264,27 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_ce
 #pragma unroll
   for (int q0 = 0; q0 < QV; q0 += QC) {
     // projection of variable v to the points of this pass
+    // two volume points per packed FMA
 #pragma unroll
-    for (int qq = 0; qq < QC; ++qq) {
+    for (int qq = 0; qq + 1 < QC; qq += 2) {
+      T u0 = T(0), u1 = T(0);
+#pragma unroll
+      for (int l = 0; l < N; ++l) fma2(u0, u1, wl[l], wl[l], tb.P[l][q0 + qq], tb.P[l][q0 + qq + 1]);
+      PR[(qq * NSL + v) * TC + f] = u0;
+      PR[((qq + 1) * NSL + v) * TC + f] = u1;
+    }
+    if (QC & 1) {
       T u = T(0);
 #pragma unroll
-      for (int l = 0; l < N; ++l) u += wl[l] * tb.P[l][q0 + qq];
-      PR[(qq * NSL + v) * TC + f] = u;
+      for (int l = 0; l < N; ++l) u = fma_rn(wl[l], tb.P[l][q0 + QC - 1], u);
+      PR[((QC - 1) * NSL + v) * TC + f] = u;
     }
     __syncthreads();
     // primitives per point
     for (int idx = t; idx < QC * TC; idx += NT) {
       const int qq = idx / TC, ff = idx % TC;
       T* pr = PR + qq * NSL * TC + ff;
-      const T rho = pr[0], ir = T(1) / rho;
+      const T rho = pr[0], ir = rcp(rho);
       const T vx = pr[1 * TC] * ir, vy = pr[2 * TC] * ir, vz = pr[3 * TC] * ir;
       const T bx = pr[5 * TC], by = pr[6 * TC], bz = pr[7 * TC];
       const T b2 = bx * bx + by * by + bz * bz;
@@ -213,12 +307,25 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_ce
       const T al = pr[aidx * TC];
       const T be = bs * pr[bidx * TC] + bconst;
       const T ga = pr[gidx * TC];
-      T fa[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) fa[a] = al * pr[(SL_V + a) * TC] + be * pr[(SL_B + a) * TC] + (a == gax ? ga : T(0));
-#pragma unroll
-      for (int l = 1; l < N; ++l)
-        racc[l] += fa[0] * tb.dPw[0][l][q0 + qq] + fa[1] * tb.dPw[1][l][q0 + qq] + fa[2] * tb.dPw[2][l][q0 + qq];
+      T fa[3] = {gax == 0 ? ga : T(0), gax == 1 ? ga : T(0), gax == 2 ? ga : T(0)};
+      fma2(fa[0], fa[1], be, be, pr[SL_B * TC], pr[(SL_B + 1) * TC]);
+      fma2(fa[0], fa[1], al, al, pr[SL_V * TC], pr[(SL_V + 1) * TC]);
+      fa[2] = fma_rn(al, pr[(SL_V + 2) * TC], fma_rn(be, pr[(SL_B + 2) * TC], fa[2]));
+      // only the modes with a non-zero derivative along a, two per packed FMA
+      // (mode indices are template constants: racc stays in registers)
+      const int q = q0 + qq;
+      static_for<3>([&](auto A) {
+        constexpr int a = decltype(A)::value;
+        constexpr int cnt = kModes<DEG>.cnt[a];
+        static_for<(cnt + 1) / 2>([&](auto I) {
+          constexpr int i = decltype(I)::value;
+          constexpr int l0 = kModes<DEG>.nz[a][2 * i];
+          // odd count: the last pair's second slot is mode 0 with a zero
+          // weight (racc[0] is not an output: the mean comes from the faces)
+          constexpr int l1 = 2 * i + 1 < cnt ? kModes<DEG>.nz[a][2 * i + 1] : 0;
+          fma2(racc[l0], racc[l1], fa[a], fa[a], tb.dP2[a][i][q][0], tb.dP2[a][i][q][1]);
+        });
+      });
     }
     __syncthreads();
   }
@@ -235,23 +342,24 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_ce
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         const int64_t fc = s ? nbr(g, kc, a, +1) : c;
+        // fs: this face's mean-row sum. The weights of mode 0 are w_p on both
+        // sides (P_0 = 1) and round-to-nearest is symmetric, so the sum of
+        // -F w_p here is bitwise the negation of the neighbour's sum of F w_p.
         T fs = T(0);
 #pragma unroll
         for (int p = 0; p < QF; ++p) {
           const T Fr = F[((int64_t)(a * QF + p) * 9 + v) * S + fc];
-          fs = fma_rn(Fr, tb.Pfw[2 * a][0][p], fs);  // P_0 = 1: same weight on both sides
           const T Fv = s ? -Fr : Fr;
+          const T* Pw = tb.Pfw[2 * a + s][p];
+          fma2(fs, racc[1], Fv, Fv, Pw[0], Pw[1]);
 #pragma unroll
-          for (int l = 1; l < N; ++l) racc[l] += Fv * tb.Pfw[2 * a + s][l][p];
+          for (int l = 2; l + 1 < N; l += 2) fma2(racc[l], racc[l + 1], Fv, Fv, Pw[l], Pw[l + 1]);
         }
-        fsum[2 * a + s] = s ? -fs : fs;
+        fsum[2 * a + s] = fs;
       }
     }
   }
   if (!live) return;
-  const double dt = sc->dt;
-  const double kappa = sc->kappa;
-  const double metric = g.metric;
   // mode 0 (cell mean)
   {
     const int64_t i = (int64_t)(v * N) * S + c;
@@ -260,7 +368,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_ce
       // (Knuth's TwoSum: s + e equals a + b exactly), so the cell's total is
       // accurate to about 2^-48 of the face sums; it enters the FP64 mean
       // through one conversion. GB300's FP64 rate is 1/64 of FP32: the FP64
-      // work here is a handful of operations per (cell, variable).
+      // work here is a handful of operations per (cell, variable), and no
+      // thread converts a uniform FP64 scalar (float copies are passed).
       float hi = (float)fsum[0], lo = 0.f;
 #pragma unroll
       for (int k = 1; k < 6; ++k) {
@@ -272,40 +381,41 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_ce
         lo = __fadd_rn(lo, e);
       }
       const double tot = (double)hi + (double)lo;
-      const double k1 = metric * (double)tb.minv[0];
       const double wz = wmean[(int64_t)v * S + c];
-      if (!combine) {
-        double rhs = k1 * tot;
-        if (v == 8) rhs = fma(-kappa, wz, rhs);
+      if (cmode == 0) {
+        double rhs = g.kmean * tot;
+        if (v == 8) rhs = fma(-sc->kappa, wz, rhs);
         out[i] = (T)rhs;
         outmean[(int64_t)v * S + c] = rhs;
       } else {
-        // o = ca w0 + cb (wz + dt rhs), rhs = k1 tot (- kappa wz for psi)
-        const double kd = cb * dt;
+        // o = ca w0 + cb (wz + dt rhs), rhs = kmean tot (- kappa wz for psi)
+        const double kd = cb * sc->dt;
         double base = cb * wz;
-        if (ca != 0.0) base = fma(ca, w0mean[(int64_t)v * S + c], base);
-        if (v == 8) base = fma(-kd * kappa, wz, base);
-        const double o = fma(kd * k1, tot, base);
+        if (cmode == 2) base = fma(ca, w0mean[(int64_t)v * S + c], base);
+        if (v == 8) base = fma(-kd * sc->kappa, wz, base);
+        const double o = fma(kd * g.kmean, tot, base);
         outmean[(int64_t)v * S + c] = o;
         out[i] = (T)o;
       }
     } else {
+      const double dt = sc->dt, kappa = sc->kappa;
       const double mean_acc = ((double)fsum[0] + (double)fsum[1]) + ((double)fsum[2] + (double)fsum[3]) +
                               ((double)fsum[4] + (double)fsum[5]);
-      double rhs = metric * (double)tb.minv[0] * mean_acc;
+      double rhs = g.metric * (double)tb.minv[0] * mean_acc;
       const double wz = (double)wl[0];
       if (v == 8) rhs -= kappa * wz;
-      if (!combine) out[i] = (T)rhs;
+      if (cmode == 0) out[i] = (T)rhs;
       else out[i] = (T)(ca * (double)w0[i] + cb * (wz + dt * rhs));
     }
   }
-  const T tm = (T)metric, tdt = (T)dt, tca = (T)ca, tcb = (T)cb, tk = (T)kappa;
+  const T tm = pick_prec<T>(g.metric, g.metric32), tdt = pick_prec<T>(sc->dt, sc->dt32);
+  const T tca = pick_prec<T>(ca, ca32), tcb = pick_prec<T>(cb, cb32), tk = pick_prec<T>(sc->kappa, sc->kappa32);
 #pragma unroll
   for (int l = 1; l < N; ++l) {
     T rhs = tm * tb.minv[l] * racc[l];
     if (v == 8) rhs -= tk * wl[l];
     const int64_t i = (int64_t)(v * N + l) * S + c;
-    if (!combine) out[i] = rhs;
+    if (cmode == 0) out[i] = rhs;
     else out[i] = tca * w0[i] + tcb * (wl[l] + tdt * rhs);
   }
 }
@@ -356,7 +466,16 @@ void launch_cell_glm(const FastAll<T, DEG>& tabs, const FastGeom& g, const T* w,
     set_smem_attr<T>((const void*)k_cell_glm<T, DEG>, sm);
     attr = true;
   }
-  k_cell_glm<T, DEG><<<nb, NT, sm, st>>>(tabs.cell, g, w, F, out, w0, ca, cb, combine, sc, wmean, w0mean, outmean);
+  // cmode: 0 plain rhs, 1 SSP combination with ca == 0, 2 with ca != 0
+  const int cmode = combine ? (ca != 0.0 ? 2 : 1) : 0;
+  k_cell_glm<T, DEG><<<nb, NT, sm, st>>>(tabs.cell, g, w, F, out, w0, ca, cb, (float)ca, (float)cb, cmode, sc,
+                                         wmean, w0mean, outmean);
+}
+
+template <typename T, int DEG>
+int fast_to_constant(const FastAll<T, DEG>& tabs) {
+  if constexpr (FastConst<T, DEG>::on) return FastConst<T, DEG>::upload(tabs) == cudaSuccess ? 0 : -3;
+  return 0;
 }
 
 #define INSTF(T, DEG)                                                                                         \
@@ -364,7 +483,8 @@ void launch_cell_glm(const FastAll<T, DEG>& tabs, const FastGeom& g, const T* w,
                                         const DevScalars*, double, cudaStream_t);                          \
   template void launch_cell_glm<T, DEG>(const FastAll<T, DEG>&, const FastGeom&, const T*, const T*, T*,    \
                                         const T*, double, double, int, const DevScalars*, const double*,    \
-                                        const double*, double*, cudaStream_t);
+                                        const double*, double*, cudaStream_t);          \
+  template int fast_to_constant<T, DEG>(const FastAll<T, DEG>&);
 INSTF(float, 1)
 INSTF(float, 2)
 INSTF(float, 3)

@@ -406,6 +406,89 @@ __global__ void k_dt(Geom g, Tables<T> tb, const T* __restrict__ w, const double
   }
 }
 
+// FP32 form on uniform meshes: the same CFL and Powell bounds from the float
+// mirror of the cell means, in single precision (the step length is a bound,
+// not a conserved quantity: a relative 1e-7 in dt is harmless), with the
+// FP64 means used only where the FP32 pressure would lose its digits to the
+// cancellation E - kinetic - magnetic. Warp minimum, one atomic per warp.
+__global__ void k_dt32(Geom g, Tables<float> tb, const float* __restrict__ w, const double* __restrict__ wmean,
+                       const float* __restrict__ jbuf, dg_mhd_params p, DevScalars* __restrict__ sc) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float dtc = FLT_MAX, smax = 0.f;
+  if (c < g.ncell) {
+    const int64_t S = g.stride;
+    auto mean = [&](int m) { return w[(int64_t)mean_row(g, m) * S + c]; };
+    const float rho = mean(0), ir = 1.f / rho;
+    const float vx = mean(1) * ir, vy = mean(2) * ir, vz = mean(3) * ir;
+    const float E = mean(4);
+    float b[3];
+    if (g.glm) {
+      b[0] = mean(5); b[1] = mean(6); b[2] = mean(7);
+    } else {
+      b[0] = b[1] = b[2] = 0.f;
+      for (int j = 0; j < g.DB; ++j)
+        for (int cc = 0; cc < g.DB; ++cc) b[cc] += mean(5 + j) * tb.L0[j * g.DB + cc];
+      if (g.bz2d >= 0) b[2] = mean(7);
+    }
+    const float gam = (float)g.gamma;
+    const float b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    const float kin = 0.5f * rho * (vx * vx + vy * vy + vz * vz);
+    float pr = (gam - 1.f) * (E - kin - 0.5f * b2);
+    if (!(pr > 1e-3f * E)) {
+      // cancellation (or a non-positive mean pressure): FP64 from the means
+      auto md = [&](int m) { return wmean[m * S + c]; };
+      const double rd = md(0);
+      const double mx = md(1), my = md(2), mz = md(3);
+      double bd[3];
+      if (g.glm) {
+        bd[0] = md(5); bd[1] = md(6); bd[2] = md(7);
+      } else {
+        bd[0] = bd[1] = bd[2] = 0.0;
+        for (int j = 0; j < g.DB; ++j)
+          for (int cc = 0; cc < g.DB; ++cc) bd[cc] += md(5 + j) * (double)tb.L0[j * g.DB + cc];
+        if (g.bz2d >= 0) bd[2] = md(7);
+      }
+      pr = (float)((g.gamma - 1.0) * (md(4) - 0.5 * (mx * mx + my * my + mz * mz) / rd -
+                                      0.5 * (bd[0] * bd[0] + bd[1] * bd[1] + bd[2] * bd[2])));
+    }
+    const float cs = sqrtf((gam * pr + b2) * ir);
+    const float av[3] = {fabsf(vx), fabsf(vy), fabsf(vz)};
+    float sum = 0.f;
+    for (int a = 0; a < g.D; ++a) sum += av[a] + cs;
+    const float idx = (float)(1.0 / g.dx);
+    const float s = sum * idx;
+    dtc = (float)(p.cfl / (2.0 * g.d + 1.0)) / s;
+    smax = sum / (float)g.D;
+    if (!g.glm) {
+      // (1/V_K) oint |B^n_F - B^n_K| dS: this cell's 2D faces in fixed order
+      float acc = 0.f;
+      for (int a = 0; a < g.D; ++a) {
+        const int64_t cp = neighbour(g, c, a, +1);
+        for (int q = 0; q < g.Qf; ++q) {
+          acc += jbuf[(((int64_t)a * g.ncell + c) * g.Qf + q) * 2 + 1];
+          acc += jbuf[(((int64_t)a * g.ncell + cp) * g.Qf + q) * 2 + 0];
+        }
+      }
+      // face measure (dx/2)^(D-1) over the volume dx^D: 2^(1-D) / dx
+      const float divb = acc * (g.D == 3 ? 0.25f : 0.5f) * idx;
+      const float rate = divb * fabsf(vx * b[0] + vy * b[1] + vz * b[2]) / E;
+      if (rate > 0.f) dtc = fminf(dtc, (float)p.eta_powell / rate);
+    }
+    if (!(dtc > 0.f) || !isfinite(dtc)) {
+      atomicOr(&sc->status, 1);
+      dtc = FLT_MAX;
+    }
+  }
+  // positive floats order as their bit patterns
+  const unsigned mn = __reduce_min_sync(0xffffffffu, __float_as_uint(dtc));
+  const unsigned mxs = __reduce_max_sync(0xffffffffu, __float_as_uint(smax));
+  if ((threadIdx.x & 31) == 0) {
+    const float dm = __uint_as_float(mn);
+    if (dm < FLT_MAX) atomicMin(&sc->dt_bits, dbits((double)dm));
+    atomicMax(&sc->smax_bits, dbits((double)__uint_as_float(mxs)));
+  }
+}
+
 __global__ void k_dt_init(DevScalars* sc) {
   sc->dt_bits = dbits(DBL_MAX);
   sc->smax_bits = 0ull;
@@ -417,12 +500,15 @@ __global__ void k_dt_finalize(Geom g, dg_mhd_params p, DevScalars* sc, const dou
     atomicOr(&sc->status, 1);
   }
   sc->dt = dt;
+  sc->dt32 = (float)dt;
   if (dt_out) *dt_out = dt;
   if (g.glm) {
     double ch = p.c_h_fixed > 0.0 ? p.c_h_fixed : p.cfl_glm / (2.0 * g.d + 1.0) * g.dx / (g.D * dt);
     sc->ch = ch;
+    sc->ch32 = (float)ch;
     const double tau = fmax(p.c_r / ch, 3.0 * dt);
     sc->kappa = 1.0 / tau;
+    sc->kappa32 = (float)sc->kappa;
     if (p.c_h_fixed > 0.0 && !dt_in) {
       const double smax = __longlong_as_double((long long)sc->smax_bits);
       if (ch < smax) atomicOr(&sc->status, 4);
@@ -433,6 +519,8 @@ __global__ void k_dt_finalize(Geom g, dg_mhd_params p, DevScalars* sc, const dou
 __global__ void k_set_glm(DevScalars* sc, double ch, double kappa) {
   sc->ch = ch;
   sc->kappa = kappa;
+  sc->ch32 = (float)ch;
+  sc->kappa32 = (float)kappa;
 }
 
 }  // namespace
@@ -486,6 +574,13 @@ template <typename T>
 void launch_dt(const Geom& g, const Tables<T>& tb, const T* w, const double* wmean, const T* jbuf,
                const dg_mhd_params& p, DevScalars* sc, double* dt_out, cudaStream_t st) {
   k_dt_init<<<1, 1, 0, st>>>(sc);
+  if constexpr (sizeof(T) == 4) {
+    if (wmean) {
+      k_dt32<<<nblocks(g.ncell, 256), 256, 0, st>>>(g, tb, w, wmean, jbuf, p, sc);
+      k_dt_finalize<<<1, 1, 0, st>>>(g, p, sc, nullptr, dt_out);
+      return;
+    }
+  }
   k_dt<T><<<nblocks(g.ncell, 256), 256, 0, st>>>(g, tb, w, wmean, jbuf, p, sc);
   k_dt_finalize<<<1, 1, 0, st>>>(g, p, sc, nullptr, dt_out);
 }

@@ -18,10 +18,26 @@ __device__ __forceinline__ T dsqrt(T x) { return sqrt(x); }
 template <>
 __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
 
+// Reciprocals and quotients: exact IEEE operations in FP64; in FP32 the fast
+// hardware reciprocal forms (__fdividef, rsqrtf: a few ulp), far inside the
+// FP32 form's tolerance and a fraction of the instructions of an IEEE division.
+template <typename T>
+__device__ __forceinline__ T rcp(T x) { return T(1) / x; }
+template <>
+__device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.f, x); }
+template <typename T>
+__device__ __forceinline__ T quot(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ float quot<float>(float a, float b) { return __fdividef(a, b); }
+template <typename T>
+__device__ __forceinline__ T rsq(T x) { return T(1) / sqrt(x); }
+template <>
+__device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+
 template <typename T>
 __device__ __forceinline__ void flux_dir(const T* u, int a, T gamma, bool glm, T ch2, T* f) {
   const T rho = u[0];
-  const T ir = T(1) / rho;
+  const T ir = rcp(rho);
   const T vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
   const T bx = u[5], by = u[6], bz = u[7];
   const T b2 = bx * bx + by * by + bz * bz;
@@ -47,8 +63,8 @@ __device__ __forceinline__ void flux_dir(const T* u, int a, T gamma, bool glm, T
 
 template <typename T>
 __device__ __forceinline__ T bn_face(T rL, T rR, T bL, T bR) {
-  const T sL = T(1) / dsqrt(rL), sR = T(1) / dsqrt(rR);
-  return (bL * sL + bR * sR) / (sL + sR);
+  const T sL = rsq(rL), sR = rsq(rR);
+  return quot(bL * sL + bR * sR, sL + sR);
 }
 
 // Rotated-frame state: rho, u (normal), v, w (tangential), p, By, Bz (tangential)
@@ -60,7 +76,7 @@ struct Prim {
 // HLLD flux in the rotated frame; out[0..7] = (rho, m_n, m_t1, m_t2, E, B_n, B_t1, B_t2).
 template <typename T>
 __device__ __forceinline__ void hlld(const Prim<T>& L, const Prim<T>& R, T bn, T gamma, T eps, T* out) {
-  const T gm1i = T(1) / (gamma - T(1));
+  const T gm1i = rcp(gamma - T(1));
   const T bn2 = bn * bn;
   const T b2L = bn2 + L.by * L.by + L.bz * L.bz;
   const T b2R = bn2 + R.by * R.by + R.bz * R.bz;
@@ -70,13 +86,14 @@ __device__ __forceinline__ void hlld(const Prim<T>& L, const Prim<T>& R, T bn, T
   // fast speeds
   T cfL, cfR;
   {
-    T a2 = gamma * L.p / L.r, bb = b2L / L.r, bn2r = bn2 / L.r;
+    const T irL = rcp(L.r), irR = rcp(R.r);
+    T a2 = gamma * L.p * irL, bb = b2L * irL, bn2r = bn2 * irL;
     T disc = (a2 + bb) * (a2 + bb) - T(4) * a2 * bn2r;
     disc = disc > T(0) ? disc : T(0);
     cfL = dsqrt(T(0.5) * (a2 + bb + dsqrt(disc)));
-    a2 = gamma * R.p / R.r;
-    bb = b2R / R.r;
-    bn2r = bn2 / R.r;
+    a2 = gamma * R.p * irR;
+    bb = b2R * irR;
+    bn2r = bn2 * irR;
     disc = (a2 + bb) * (a2 + bb) - T(4) * a2 * bn2r;
     disc = disc > T(0) ? disc : T(0);
     cfR = dsqrt(T(0.5) * (a2 + bb + dsqrt(disc)));
@@ -109,13 +126,14 @@ __device__ __forceinline__ void hlld(const Prim<T>& L, const Prim<T>& R, T bn, T
   phys(L, EL, pTL, FL, UL);
   phys(R, ER, pTR, FR, UR);
   const T dL = SL - L.u, dR = SR - R.u;
-  const T den = dR * R.r - dL * L.r;
-  const T SM = (dR * R.r * R.u - dL * L.r * L.u - pTR + pTL) / den;
-  const T pTs = (dR * R.r * pTL - dL * L.r * pTR + L.r * R.r * dR * dL * (R.u - L.u)) / den;
+  const T iden = rcp(dR * R.r - dL * L.r);
+  const T SM = (dR * R.r * R.u - dL * L.r * L.u - pTR + pTL) * iden;
+  const T pTs = (dR * R.r * pTL - dL * L.r * pTR + L.r * R.r * dR * dL * (R.u - L.u)) * iden;
 
   // single-starred states (Miyoshi & Kusano 2005), side by side without
   // run-time indexing so that everything stays in registers
-  const T rsL = L.r * dL / (SL - SM), rsR = R.r * dR / (SR - SM);
+  const T islm = rcp(SL - SM), isrm = rcp(SR - SM);
+  const T rsL = L.r * dL * islm, rsR = R.r * dR * isrm;
   T vsL, wsL, bysL, bzsL, vsR, wsR, bysR, bzsR;
   {
     const T q = L.r * dL * (SL - SM), dd = q - bn2;
@@ -123,7 +141,8 @@ __device__ __forceinline__ void hlld(const Prim<T>& L, const Prim<T>& R, T bn, T
     if (add < eps * (aq + bn2)) {
       vsL = L.v; wsL = L.w; bysL = L.by; bzsL = L.bz;
     } else {
-      const T fv = bn * (SM - L.u) / dd, fb = (L.r * dL * dL - bn2) / dd;
+      const T idd = rcp(dd);
+      const T fv = bn * (SM - L.u) * idd, fb = (L.r * dL * dL - bn2) * idd;
       vsL = L.v - L.by * fv; wsL = L.w - L.bz * fv; bysL = L.by * fb; bzsL = L.bz * fb;
     }
   }
@@ -133,18 +152,20 @@ __device__ __forceinline__ void hlld(const Prim<T>& L, const Prim<T>& R, T bn, T
     if (add < eps * (aq + bn2)) {
       vsR = R.v; wsR = R.w; bysR = R.by; bzsR = R.bz;
     } else {
-      const T fv = bn * (SM - R.u) / dd, fb = (R.r * dR * dR - bn2) / dd;
+      const T idd = rcp(dd);
+      const T fv = bn * (SM - R.u) * idd, fb = (R.r * dR * dR - bn2) * idd;
       vsR = R.v - R.by * fv; wsR = R.w - R.bz * fv; bysR = R.by * fb; bzsR = R.bz * fb;
     }
   }
   const T vbL = L.u * bn + L.v * L.by + L.w * L.bz, vbR = R.u * bn + R.v * R.by + R.w * R.bz;
   const T vbsL = SM * bn + vsL * bysL + wsL * bzsL, vbsR = SM * bn + vsR * bysR + wsR * bzsR;
-  const T EsL = (dL * EL - pTL * L.u + pTs * SM + bn * (vbL - vbsL)) / (SL - SM);
-  const T EsR = (dR * ER - pTR * R.u + pTs * SM + bn * (vbR - vbsR)) / (SR - SM);
-  const T sqL = dsqrt(rsL), sqR = dsqrt(rsR);
+  const T EsL = (dL * EL - pTL * L.u + pTs * SM + bn * (vbL - vbsL)) * islm;
+  const T EsR = (dR * ER - pTR * R.u + pTs * SM + bn * (vbR - vbsR)) * isrm;
+  const T isqL = rsq(rsL), isqR = rsq(rsR);
+  const T sqL = rsL * isqL, sqR = rsR * isqR;
   const T sgn = bn >= T(0) ? T(1) : T(-1);
   const T abn = bn < T(0) ? -bn : bn;
-  const T SsL = SM - abn / sqL, SsR = SM + abn / sqR;
+  const T SsL = SM - abn * isqL, SsR = SM + abn * isqR;
 
   if (SsL >= T(0)) {  // left single-starred region
     const T Us[8] = {rsL, rsL * SM, rsL * vsL, rsL * wsL, EsL, bn, bysL, bzsL};
@@ -161,7 +182,7 @@ __device__ __forceinline__ void hlld(const Prim<T>& L, const Prim<T>& R, T bn, T
     return;
   }
   // double-starred states
-  const T inv = T(1) / (sqL + sqR);
+  const T inv = rcp(sqL + sqR);
   const T vss = (sqL * vsL + sqR * vsR + (bysR - bysL) * sgn) * inv;
   const T wss = (sqL * wsL + sqR * wsR + (bzsR - bzsL) * sgn) * inv;
   const T byss = (sqL * bysR + sqR * bysL + sqL * sqR * (vsR - vsL) * sgn) * inv;
@@ -188,7 +209,7 @@ __device__ __forceinline__ T face_flux(const T* uL, const T* uR, int a, T gamma,
   const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
   Prim<T> L, R;
   {
-    const T ir = T(1) / uL[0];
+    const T ir = rcp(uL[0]);
     const T v0 = uL[1] * ir, v1 = uL[2] * ir, v2 = uL[3] * ir;
     const T b2 = uL[5] * uL[5] + uL[6] * uL[6] + uL[7] * uL[7];
     L.r = uL[0];
@@ -198,7 +219,7 @@ __device__ __forceinline__ T face_flux(const T* uL, const T* uR, int a, T gamma,
     L.by = uL[5 + t1]; L.bz = uL[5 + t2];
   }
   {
-    const T ir = T(1) / uR[0];
+    const T ir = rcp(uR[0]);
     const T v0 = uR[1] * ir, v1 = uR[2] * ir, v2 = uR[3] * ir;
     const T b2 = uR[5] * uR[5] + uR[6] * uR[6] + uR[7] * uR[7];
     R.r = uR[0];
@@ -216,7 +237,7 @@ __device__ __forceinline__ T face_flux(const T* uL, const T* uR, int a, T gamma,
   F[4] = Fr[4];
   F[5 + a] = Fr[5]; F[5 + t1] = Fr[6]; F[5 + t2] = Fr[7];
   if (glm) {
-    const T bstar = T(0.5) * (bnL + bnR) - (uR[8] - uL[8]) / (T(2) * ch);
+    const T bstar = T(0.5) * (bnL + bnR) - quot(uR[8] - uL[8], T(2) * ch);
     const T pstar = T(0.5) * (uL[8] + uR[8]) - T(0.5) * ch * (bnR - bnL);
     F[5 + a] = pstar;
     F[8] = ch * ch * bstar;

@@ -342,7 +342,7 @@ if __name__ == "__main__":
                         pos_weight=args.pos_weight)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    rep = {"samples": int(X.shape[0]), "positives": int(y.sum()),
+    rep = {"args": vars(args), "samples": int(X.shape[0]), "positives": int(y.sum()),
            "samples_by_source": {"blast": int((src == 0).sum()), "turbulence": int((src == 1).sum())},
            "positives_by_source": {"blast": int(y[src == 0].sum()), "turbulence": int(y[src == 1].sum())},
            "turbulence_sources": turb, "gen_s": t1 - t0, "train_s": t2 - t1, **info}

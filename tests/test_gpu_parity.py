@@ -114,6 +114,26 @@ def test_dt_fp64(D, d, divb, ncell, fname):
     assert abs(dt - ref) <= 1e-12 * ref
 
 
+@pytest.mark.parametrize("D,d,divb,ncell,fname", CASES)
+def test_dt_fp32_form(D, d, divb, ncell, fname):
+    """FP32 form: the step length from the float mirror of the means. The CFL
+    bound is a few float operations per cell (relative error ~1e-6); the Powell
+    bound divides by the face jumps |B^n_F - B^n_K| of FP32 traces, whose
+    relative error is eps32 |B| / |jump| (~1e-3 on smooth data, where the
+    jumps are O(dx^(d+1)))."""
+    S, w0, sol = _setup(D, d, divb, ncell, fname, precision="fp32")
+    w = to_device(w0, sol)
+    wm = means_to_device(w0, sol, S)
+    dt = sol.dt(w, wm).item()
+    ref = S.dt(w0)
+    eta = S.P.eta_powell
+    S.P.eta_powell = float("inf")
+    cfl_only = S.dt(w0)
+    S.P.eta_powell = eta
+    tol = 1e-5 if (divb == "glm" or cfl_only == ref) else 5e-3
+    assert abs(dt - ref) <= tol * ref
+
+
 @pytest.mark.parametrize("D,d,divb,ncell,fname", CASES[:1] + CASES[2:3] + CASES[4:5])
 def test_step_fp64(D, d, divb, ncell, fname):
     import torch
