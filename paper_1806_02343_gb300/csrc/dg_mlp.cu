@@ -48,40 +48,55 @@ __device__ __forceinline__ int mrow(const Geom& g, int m) {
   return m < 7 ? g.ldf0 + (m - 5) : g.bz2d;
 }
 
-// physical cell means of the 8 MHD variables
-template <typename T>
-__device__ __forceinline__ void means8(const Geom& g, const MlpTabs& mt, const T* w, const double* wmean, int64_t c,
-                                       float* m) {
-  const int64_t S = g.stride;
-  float raw[8];
-  for (int k = 0; k < 8; ++k) raw[k] = wmean ? (float)wmean[k * S + c] : (float)w[(int64_t)mrow(g, k) * S + c];
+// physical cell means of the 8 MHD variables from the raw mean rows
+__device__ __forceinline__ void phys_means(const Geom& g, const MlpTabs& mt, const float* raw, float* m) {
   for (int k = 0; k < 5; ++k) m[k] = raw[k];
   if (g.glm) {
     for (int k = 5; k < 8; ++k) m[k] = raw[k];
   } else {
     m[5] = m[6] = m[7] = 0.f;
-    for (int j = 0; j < g.D; ++j)
-      for (int cc = 0; cc < g.D; ++cc) m[5 + cc] += raw[5 + j] * mt.l2l[(j * 3 + cc) * MLP_MAXN + 0];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc)
+        if (j < g.D && cc < g.D) m[5 + cc] += raw[5 + j] * mt.l2l[(j * 3 + cc) * MLP_MAXN + 0];
     if (g.D == 2) m[7] = raw[7];
   }
 }
 
-// features of cell c, written through put(k, value) for k in [0, nin)
-template <typename T, typename Put>
-__device__ __forceinline__ void cell_features(const Geom& g, const MlpTabs& mt, const T* w, const double* wmean,
-                                              int64_t c, Put put) {
-  const int64_t S = g.stride;
+// State of one cell and of its face neighbours read straight from the state
+// rows (FP32 form: the float mode-0 rows mirror the FP64 means exactly).
+template <typename T>
+struct GlobalSrc {
+  const Geom& g;
+  const T* w;
+  int64_t c;
+  __device__ float row(int r) const { return (float)w[(int64_t)r * g.stride + c]; }
+  __device__ void nbraw(int a, int s, float* raw) const {
+    const int64_t cn = nbc(g, c, a, s ? 1 : -1);
+    for (int k = 0; k < 8; ++k) raw[k] = (float)w[(int64_t)mrow(g, k) * g.stride + cn];
+  }
+};
+
+// features of one cell, written through put(k, value) for k in [0, nin)
+template <typename Src, typename Put>
+__device__ __forceinline__ void features_of(const Geom& g, const MlpTabs& mt, const Src& src, Put put) {
   const int n = g.n;
   float m[8];
-  means8(g, mt, w, wmean, c, m);
+  {
+    float raw[8];
+    for (int k = 0; k < 8; ++k) raw[k] = src.row(mrow(g, k));
+    phys_means(g, mt, raw, m);
+  }
   float dmax[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (a >= g.D) break;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      float mn[8];
-      means8(g, mt, w, wmean, nbc(g, c, a, s ? 1 : -1), mn);
+      float raw[8], mn[8];
+      src.nbraw(a, s, raw);
+      phys_means(g, mt, raw, mn);
 #pragma unroll
       for (int k = 0; k < 8; ++k) dmax[k] = fmaxf(dmax[k], fabsf(mn[k] - m[k]));
       put(8 * n + 2 * a + s, mn[0] / m[0] - 1.f);
@@ -98,7 +113,7 @@ __device__ __forceinline__ void cell_features(const Geom& g, const MlpTabs& mt, 
     if (!leg) continue;
     const int r0 = (v == 7 && !g.glm) ? g.bz2d : v * n;
     for (int l = 0; l < n; ++l) {
-      const float av = (l == 0) ? m[v] : (float)w[(int64_t)(r0 + l) * S + c];
+      const float av = (l == 0) ? m[v] : src.row(r0 + l);
       put(v * n + l, av * inv[v]);
 #pragma unroll
       for (int a = 0; a < 3; ++a)
@@ -112,11 +127,7 @@ __device__ __forceinline__ void cell_features(const Geom& g, const MlpTabs& mt, 
       if (cc >= g.D) break;
       for (int l = 0; l < n; ++l) {
         float acc = 0.f;
-        for (int j = 0; j < g.ndiv; ++j) {
-          const float wj = j < g.D ? (wmean ? (float)wmean[(5 + j) * S + c] : (float)w[(int64_t)(g.ldf0 + j) * S + c])
-                                   : (float)w[(int64_t)(g.ldf0 + j) * S + c];
-          acc += wj * mt.l2l[(j * 3 + cc) * MLP_MAXN + l];
-        }
+        for (int j = 0; j < g.ndiv; ++j) acc += src.row(g.ldf0 + j) * mt.l2l[(j * 3 + cc) * MLP_MAXN + l];
         put((5 + cc) * n + l, acc * inv[5 + cc]);
 #pragma unroll
         for (int a = 0; a < 3; ++a)
@@ -124,6 +135,12 @@ __device__ __forceinline__ void cell_features(const Geom& g, const MlpTabs& mt, 
       }
     }
   }
+}
+
+template <typename T, typename Put>
+__device__ __forceinline__ void cell_features(const Geom& g, const MlpTabs& mt, const T* w, const double* /*wmean*/,
+                                              int64_t c, Put put) {
+  features_of(g, mt, GlobalSrc<T>{g, w, c}, put);
 }
 
 template <typename T>
@@ -151,6 +168,113 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// Network on the 32 cells of one warp: rows Xw[0..32) of bf16 features (row
+// stride LD1) -> probabilities; writes the flags of the 32 cells to flw[0..32)
+// and, for live cells, flag / prob. base = first cell of the warp.
+template <int KP>
+__device__ __forceinline__ void infer_warp(const __nv_bfloat16* Xw, const __nv_bfloat16* W1s,
+                                           const __nv_bfloat16* W2s, const float* bs, uint8_t* flw, int64_t base,
+                                           int64_t ncell, float thresh, uint8_t* __restrict__ flag,
+                                           float* __restrict__ prob) {
+  constexpr int LD1 = KP + 8, LD2 = HID + 8;
+  const int lane = threadIdx.x & 31;
+  const int gq = lane >> 2, tq = lane & 3;
+  for (int tile = 0; tile < 2; ++tile) {
+    const __nv_bfloat16* Xt = Xw + tile * 16 * LD1;
+    float h1[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      h1[j][0] = bs[8 * j + 2 * tq];
+      h1[j][1] = bs[8 * j + 2 * tq + 1];
+      h1[j][2] = bs[8 * j + 2 * tq];
+      h1[j][3] = bs[8 * j + 2 * tq + 1];
+    }
+#pragma unroll
+    for (int kk = 0; kk < KP / 16; ++kk) {
+      uint32_t a[4];
+      a[0] = *reinterpret_cast<const uint32_t*>(Xt + gq * LD1 + 16 * kk + 2 * tq);
+      a[1] = *reinterpret_cast<const uint32_t*>(Xt + (gq + 8) * LD1 + 16 * kk + 2 * tq);
+      a[2] = *reinterpret_cast<const uint32_t*>(Xt + gq * LD1 + 16 * kk + 8 + 2 * tq);
+      a[3] = *reinterpret_cast<const uint32_t*>(Xt + (gq + 8) * LD1 + 16 * kk + 8 + 2 * tq);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        uint32_t b[2];
+        b[0] = *reinterpret_cast<const uint32_t*>(W1s + (8 * j + gq) * LD1 + 16 * kk + 2 * tq);
+        b[1] = *reinterpret_cast<const uint32_t*>(W1s + (8 * j + gq) * LD1 + 16 * kk + 8 + 2 * tq);
+        mma_bf16(h1[j], a, b);
+      }
+    }
+    // ReLU; accumulator tiles 2kk, 2kk+1 form the A fragment of layer 2's k-step kk
+    float h2[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      h2[j][0] = bs[HID + 8 * j + 2 * tq];
+      h2[j][1] = bs[HID + 8 * j + 2 * tq + 1];
+      h2[j][2] = bs[HID + 8 * j + 2 * tq];
+      h2[j][3] = bs[HID + 8 * j + 2 * tq + 1];
+    }
+#pragma unroll
+    for (int kk = 0; kk < HID / 16; ++kk) {
+      uint32_t a[4];
+      a[0] = pack_bf16(fmaxf(h1[2 * kk][0], 0.f), fmaxf(h1[2 * kk][1], 0.f));
+      a[1] = pack_bf16(fmaxf(h1[2 * kk][2], 0.f), fmaxf(h1[2 * kk][3], 0.f));
+      a[2] = pack_bf16(fmaxf(h1[2 * kk + 1][0], 0.f), fmaxf(h1[2 * kk + 1][1], 0.f));
+      a[3] = pack_bf16(fmaxf(h1[2 * kk + 1][2], 0.f), fmaxf(h1[2 * kk + 1][3], 0.f));
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        uint32_t b[2];
+        b[0] = *reinterpret_cast<const uint32_t*>(W2s + (8 * j + gq) * LD2 + 16 * kk + 2 * tq);
+        b[1] = *reinterpret_cast<const uint32_t*>(W2s + (8 * j + gq) * LD2 + 16 * kk + 8 + 2 * tq);
+        mma_bf16(h2[j], a, b);
+      }
+    }
+    // output layer: rows gq and gq+8 of the tile, reduced over the quad
+    float o0 = 0.f, o1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float w0 = bs[2 * HID + 8 * j + 2 * tq], w1 = bs[2 * HID + 8 * j + 2 * tq + 1];
+      o0 += fmaxf(h2[j][0], 0.f) * w0 + fmaxf(h2[j][1], 0.f) * w1;
+      o1 += fmaxf(h2[j][2], 0.f) * w0 + fmaxf(h2[j][3], 0.f) * w1;
+    }
+    o0 += __shfl_xor_sync(0xffffffffu, o0, 1);
+    o0 += __shfl_xor_sync(0xffffffffu, o0, 2);
+    o1 += __shfl_xor_sync(0xffffffffu, o1, 1);
+    o1 += __shfl_xor_sync(0xffffffffu, o1, 2);
+    if (tq == 0) {
+      const float b3 = bs[3 * HID];
+      const int r0 = tile * 16 + gq;
+      const int64_t c0 = base + r0;
+      const float p0 = 1.f / (1.f + __expf(-(o0 + b3)));
+      const float p1 = 1.f / (1.f + __expf(-(o1 + b3)));
+      flw[r0] = p0 > thresh ? 1 : 0;
+      flw[r0 + 8] = p1 > thresh ? 1 : 0;
+      if (c0 < ncell) {
+        if (flag) flag[c0] = p0 > thresh ? 1 : 0;
+        if (prob) prob[c0] = p0;
+      }
+      if (c0 + 8 < ncell) {
+        if (flag) flag[c0 + 8] = p1 > thresh ? 1 : 0;
+        if (prob) prob[c0 + 8] = p1;
+      }
+    }
+  }
+}
+
+// appends the warp's flagged live cells to list (ballot + one atomic per warp)
+__device__ __forceinline__ void compact_warp(bool mine, int64_t c, int32_t* __restrict__ list,
+                                             DevScalars* __restrict__ sc) {
+  const int lane = threadIdx.x & 31;
+  const unsigned bal = __ballot_sync(0xffffffffu, mine);
+  const int cnt = __popc(bal);
+  unsigned at = 0;
+  if (lane == 0 && cnt) {
+    at = atomicAdd(&sc->nflag, (unsigned)cnt);
+    atomicAdd(&sc->cnt_flagged, (unsigned long long)cnt);
+  }
+  at = __shfl_sync(0xffffffffu, at, 0);
+  if (mine) list[at + __popc(bal & ((1u << lane) - 1u))] = (int32_t)c;
+}
+
 // One warp infers 32 cells (two m16 tiles); KP = padded input width (multiple of 16).
 // Shared layout: W1s[64][KP+8] bf16, W2s[64][72] bf16, Xs[warps][32][KP+8] bf16, biases f32,
 // flags of the warp's 32 cells. Persistent: the weights are staged once per block and the
@@ -176,7 +300,6 @@ __global__ void __launch_bounds__(128) k_mlp_infer(Geom g, MlpTabs mt, const T* 
   for (int i = t; i < HID * HID; i += 128) W2s[(i / HID) * LD2 + i % HID] = W2[i];
   for (int i = t; i < 3 * HID + 1; i += 128) bs[i] = bias[i];
   __syncthreads();
-  const int gq = lane >> 2, tq = lane & 3;
   const int nin = 8 * g.n + 10 * g.D;
   for (int64_t base = (int64_t)blockIdx.x * 128; base < g.ncell; base += (int64_t)gridDim.x * 128) {
     // features of this thread's cell (rows of Xs are private to the warp)
@@ -188,98 +311,10 @@ __global__ void __launch_bounds__(128) k_mlp_infer(Geom g, MlpTabs mt, const T* 
       if (live) cell_features(g, mt, w, wmean, c, [&](int k, float v) { xr[k] = __float2bfloat16_rn(v); });
     }
     __syncwarp();
-    for (int tile = 0; tile < 2; ++tile) {
-      const __nv_bfloat16* Xt = Xs + (warp * 32 + tile * 16) * LD1;
-      float h1[8][4];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        h1[j][0] = bs[8 * j + 2 * tq];
-        h1[j][1] = bs[8 * j + 2 * tq + 1];
-        h1[j][2] = bs[8 * j + 2 * tq];
-        h1[j][3] = bs[8 * j + 2 * tq + 1];
-      }
-#pragma unroll
-      for (int kk = 0; kk < KP / 16; ++kk) {
-        uint32_t a[4];
-        a[0] = *reinterpret_cast<const uint32_t*>(Xt + gq * LD1 + 16 * kk + 2 * tq);
-        a[1] = *reinterpret_cast<const uint32_t*>(Xt + (gq + 8) * LD1 + 16 * kk + 2 * tq);
-        a[2] = *reinterpret_cast<const uint32_t*>(Xt + gq * LD1 + 16 * kk + 8 + 2 * tq);
-        a[3] = *reinterpret_cast<const uint32_t*>(Xt + (gq + 8) * LD1 + 16 * kk + 8 + 2 * tq);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          uint32_t b[2];
-          b[0] = *reinterpret_cast<const uint32_t*>(W1s + (8 * j + gq) * LD1 + 16 * kk + 2 * tq);
-          b[1] = *reinterpret_cast<const uint32_t*>(W1s + (8 * j + gq) * LD1 + 16 * kk + 8 + 2 * tq);
-          mma_bf16(h1[j], a, b);
-        }
-      }
-      // ReLU; accumulator tiles 2kk, 2kk+1 form the A fragment of layer 2's k-step kk
-      float h2[8][4];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        h2[j][0] = bs[HID + 8 * j + 2 * tq];
-        h2[j][1] = bs[HID + 8 * j + 2 * tq + 1];
-        h2[j][2] = bs[HID + 8 * j + 2 * tq];
-        h2[j][3] = bs[HID + 8 * j + 2 * tq + 1];
-      }
-#pragma unroll
-      for (int kk = 0; kk < HID / 16; ++kk) {
-        uint32_t a[4];
-        a[0] = pack_bf16(fmaxf(h1[2 * kk][0], 0.f), fmaxf(h1[2 * kk][1], 0.f));
-        a[1] = pack_bf16(fmaxf(h1[2 * kk][2], 0.f), fmaxf(h1[2 * kk][3], 0.f));
-        a[2] = pack_bf16(fmaxf(h1[2 * kk + 1][0], 0.f), fmaxf(h1[2 * kk + 1][1], 0.f));
-        a[3] = pack_bf16(fmaxf(h1[2 * kk + 1][2], 0.f), fmaxf(h1[2 * kk + 1][3], 0.f));
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          uint32_t b[2];
-          b[0] = *reinterpret_cast<const uint32_t*>(W2s + (8 * j + gq) * LD2 + 16 * kk + 2 * tq);
-          b[1] = *reinterpret_cast<const uint32_t*>(W2s + (8 * j + gq) * LD2 + 16 * kk + 8 + 2 * tq);
-          mma_bf16(h2[j], a, b);
-        }
-      }
-      // output layer: rows gq and gq+8 of the tile, reduced over the quad
-      float o0 = 0.f, o1 = 0.f;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float w0 = bs[2 * HID + 8 * j + 2 * tq], w1 = bs[2 * HID + 8 * j + 2 * tq + 1];
-        o0 += fmaxf(h2[j][0], 0.f) * w0 + fmaxf(h2[j][1], 0.f) * w1;
-        o1 += fmaxf(h2[j][2], 0.f) * w0 + fmaxf(h2[j][3], 0.f) * w1;
-      }
-      o0 += __shfl_xor_sync(0xffffffffu, o0, 1);
-      o0 += __shfl_xor_sync(0xffffffffu, o0, 2);
-      o1 += __shfl_xor_sync(0xffffffffu, o1, 1);
-      o1 += __shfl_xor_sync(0xffffffffu, o1, 2);
-      if (tq == 0) {
-        const float b3 = bs[3 * HID];
-        const int r0 = tile * 16 + gq;
-        const int64_t c0 = base + warp * 32 + r0;
-        const float p0 = 1.f / (1.f + __expf(-(o0 + b3)));
-        const float p1 = 1.f / (1.f + __expf(-(o1 + b3)));
-        fl[warp * 32 + r0] = p0 > thresh ? 1 : 0;
-        fl[warp * 32 + r0 + 8] = p1 > thresh ? 1 : 0;
-        if (c0 < g.ncell) {
-          if (flag) flag[c0] = p0 > thresh ? 1 : 0;
-          if (prob) prob[c0] = p0;
-        }
-        if (c0 + 8 < g.ncell) {
-          if (flag) flag[c0 + 8] = p1 > thresh ? 1 : 0;
-          if (prob) prob[c0 + 8] = p1;
-        }
-      }
-    }
+    infer_warp<KP>(Xs + warp * 32 * LD1, W1s, W2s, bs, fl + warp * 32, base + warp * 32, g.ncell, thresh, flag,
+                   prob);
     __syncwarp();
-    if (list) {
-      const bool mine = live && fl[warp * 32 + lane] != 0;
-      const unsigned bal = __ballot_sync(0xffffffffu, mine);
-      const int cnt = __popc(bal);
-      unsigned at = 0;
-      if (lane == 0 && cnt) {
-        at = atomicAdd(&sc->nflag, (unsigned)cnt);
-        atomicAdd(&sc->cnt_flagged, (unsigned long long)cnt);
-      }
-      at = __shfl_sync(0xffffffffu, at, 0);
-      if (mine) list[at + __popc(bal & ((1u << lane) - 1u))] = (int32_t)c;
-    }
+    if (list) compact_warp(live && fl[warp * 32 + lane] != 0, c, list, sc);
     __syncwarp();
   }
 }
@@ -400,6 +435,143 @@ __global__ void k_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restri
 struct Scratch {
   float *Z1 = nullptr, *Z2 = nullptr, *d1 = nullptr, *d2 = nullptr, *d3 = nullptr;
 };
+
+// ---------------------------------------------------------------- staged inference
+// FP32 form on uniform 3D meshes whose x-rows hold whole 128-cell tiles: the
+// state rows of a tile (128 consecutive cells, 512 B per row) and the mean
+// rows of its four y/z neighbour tiles are fetched by bulk asynchronous copies
+// (cp.async.bulk, completion counted on an mbarrier) into shared memory; the
+// features are then built from shared memory, so each block keeps ~57 KB of
+// loads in flight instead of each thread walking 80+ dependent global loads.
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// global -> shared bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// a cell of the staged tile: own rows st[r][t], y/z neighbour means nbm[q][k][t]
+// (q = 2 (axis - 1) + side), x neighbours inside the tile or, at its two ends,
+// xe[side][k]
+struct StagedSrc {
+  const Geom& g;
+  const float* st;
+  const float* nbm;
+  const float* xe;
+  int t;
+  __device__ float row(int r) const { return st[r * 128 + t]; }
+  __device__ void nbraw(int a, int s, float* raw) const {
+    if (a == 0) {
+      const int tt = t + (s ? 1 : -1);
+      if (tt < 0 || tt > 127)
+        for (int k = 0; k < 8; ++k) raw[k] = xe[s * 8 + k];
+      else
+        for (int k = 0; k < 8; ++k) raw[k] = st[mrow(g, k) * 128 + tt];
+    } else {
+      const int q = 2 * (a - 1) + s;
+      for (int k = 0; k < 8; ++k) raw[k] = nbm[(q * 8 + k) * 128 + t];
+    }
+  }
+};
+
+constexpr long long kWaitCycles = 2000000000ll;  // about one second at GB300 clocks
+
+template <int KP>
+__global__ void __launch_bounds__(128) k_mlp_staged(Geom g, MlpTabs mt, const float* __restrict__ w,
+                                                    const __nv_bfloat16* __restrict__ W1,
+                                                    const __nv_bfloat16* __restrict__ W2,
+                                                    const float* __restrict__ bias, float thresh,
+                                                    uint8_t* __restrict__ flag, float* __restrict__ prob,
+                                                    int32_t* __restrict__ list, DevScalars* __restrict__ sc,
+                                                    int nrs) {
+  constexpr int LD1 = KP + 8, LD2 = HID + 8;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  float* st = reinterpret_cast<float*>(smraw);  // [nrs][128]
+  float* nbm = st + nrs * 128;                   // [4][8][128]
+  float* xe = nbm + 32 * 128;                    // [2][8]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(xe + 16);
+  __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(bar + 2);
+  __nv_bfloat16* W2s = W1s + HID * LD1;
+  __nv_bfloat16* Xs = W2s + HID * LD2;
+  float* bs = reinterpret_cast<float*>(Xs + 128 * LD1);
+  uint8_t* fl = reinterpret_cast<uint8_t*>(bs + 3 * HID + 1);
+  const int t = threadIdx.x, warp = t >> 5;
+  for (int i = t; i < HID * KP; i += 128) W1s[(i / KP) * LD1 + i % KP] = W1[i];
+  for (int i = t; i < HID * HID; i += 128) W2s[(i / HID) * LD2 + i % HID] = W2[i];
+  for (int i = t; i < 3 * HID + 1; i += 128) bs[i] = bias[i];
+  if (t == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int64_t S = g.stride;
+  const int nin = 8 * g.n + 10 * g.D;
+  const unsigned bytes = (unsigned)(nrs + 32) * 512u;
+  const int64_t ntile = g.ncell / 128;
+  unsigned parity = 0;
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int64_t c0 = tile * 128;
+    if (t == 0) {
+      // the previous tile's reads (generic proxy) are ordered before these writes
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive_expect_tx(bar, bytes);
+      for (int r = 0; r < nrs; ++r) bulk_g2s(st + r * 128, w + (int64_t)r * S + c0, 512u, bar);
+      for (int q = 0; q < 4; ++q) {
+        const int64_t cn = nbc(g, c0, 1 + (q >> 1), (q & 1) ? 1 : -1);  // the whole tile shifts
+        for (int k = 0; k < 8; ++k) bulk_g2s(nbm + (q * 8 + k) * 128, w + (int64_t)mrow(g, k) * S + cn, 512u, bar);
+      }
+    }
+    if (t < 16) {
+      const int sd = t >> 3, k = t & 7;
+      xe[t] = w[(int64_t)mrow(g, k) * S + nbc(g, c0 + (sd ? 127 : 0), 0, sd ? 1 : -1)];
+    }
+    // bounded wait for the tile's bytes
+    bool ok = false;
+    const long long t0 = clock64();
+    while (!(ok = mbar_try_wait(bar, parity)))
+      if (clock64() - t0 > kWaitCycles) break;
+    if (!__syncthreads_and(ok)) {
+      if (t == 0) atomicOr(&sc->status, 8);
+      return;
+    }
+    parity ^= 1u;
+    {
+      __nv_bfloat16* xr = Xs + t * LD1;
+      for (int k = nin; k < KP; ++k) xr[k] = __float2bfloat16_rn(0.f);
+      features_of(g, mt, StagedSrc{g, st, nbm, xe, t}, [&](int k, float v) { xr[k] = __float2bfloat16_rn(v); });
+    }
+    __syncwarp();
+    infer_warp<KP>(Xs + warp * 32 * LD1, W1s, W2s, bs, fl + warp * 32, c0 + warp * 32, g.ncell, thresh, flag,
+                   prob);
+    __syncwarp();
+    if (list) compact_warp(fl[t] != 0, c0 + t, list, sc);
+    __syncthreads();  // every read of st / nbm / xe done before the next tile's copies
+  }
+}
 
 }  // namespace
 
@@ -565,9 +737,45 @@ int mlp_set_weights(Ctx& c, const float* theta_dev, int nin, float thresh) {
   return cudaDeviceSynchronize() == cudaSuccess ? 0 : -3;
 }
 
+// shared memory of k_mlp_staged for nrs staged rows
+template <int KP>
+static size_t staged_smem(int nrs) {
+  return (size_t)(nrs + 32) * 512 + 16 * 4 + 16 + (size_t)HID * (KP + 8) * 2 + (size_t)HID * (HID + 8) * 2 +
+         (size_t)128 * (KP + 8) * 2 + (3 * HID + 1) * sizeof(float) + 128;
+}
+
+// the staged kernel applies: FP32 form, uniform 3D mesh, x-rows of whole
+// 128-cell tiles, and the shared memory fits
+template <int KP>
+static bool staged_ok(const Ctx& c, int* nrs) {
+  const Geom& g = c.g;
+  if (c.p.precision != DG_PREC_FP32MIX || c.amr.on || g.D != 3 || g.nx % 128 != 0) return false;
+  *nrs = g.glm ? 8 * g.n : g.nrows;
+  return staged_smem<KP>(*nrs) <= 227 * 1024;
+}
+
 template <typename T, int KP>
 static void infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* flag, float* prob, cudaStream_t st,
                          int32_t* list) {
+  int nrs = 0;
+  if (sizeof(T) == 4 && staged_ok<KP>(c, &nrs)) {
+    const Geom& g = c.g;
+    const size_t sm = staged_smem<KP>(nrs);
+    static size_t attr = 0;
+    if (attr < sm) {
+      cudaFuncSetAttribute(k_mlp_staged<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = sm;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_staged<KP>, 128, sm) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    const unsigned nb = (unsigned)std::min<int64_t>(g.ncell / 128, (int64_t)c.nsm * per_sm);
+    k_mlp_staged<KP><<<nb, 128, sm, st>>>(g, c.mlp, (const float*)w, (const __nv_bfloat16*)c.mlp_w1,
+                                           (const __nv_bfloat16*)c.mlp_w2, c.mlp_bias, c.mlp_thresh, flag, prob,
+                                           list, c.sc, nrs);
+    return;
+  }
   const Geom& g = c.g;
   const size_t sm = (size_t)HID * (KP + 8) * 2 + (size_t)HID * (HID + 8) * 2 + (size_t)4 * 32 * (KP + 8) * 2 +
                     (3 * HID + 1) * sizeof(float) + 128;
