@@ -229,9 +229,17 @@ def run_ours(args, cfg, rank, world, device):
     dom = max(("face_flux", "cell_update"), key=lambda k: kern[k]["ms_total"])
     per_launch_ms = kern["cell_update"]["ms_per_launch"]
     achieved = bytes_cell * ncell / (per_launch_ms * 1e-3) / 1e9
+    # DRAM bytes (read + write) per launch of k_cell_glm<float, 2> per cell, from the ncu
+    # capture of one launch on the 128^3 GLM degree-2 turbulence workload (3.843 GB for
+    # 2,097,152 cells); traffic grows with the cells, so it is scaled by the cell count
+    traffic = None
+    if cfg["divb"] == "glm" and d == 2 and not cfg.get("amr"):
+        traffic = 1832.4 * ncell
     res["roofline"] = {"bound": "hbm", "kernel": "k_cell (stage algorithmic bytes)", "dominant_kernel": dom,
                        "achieved": achieved, "peak": hbm, "peak_source": src, "unit": "GB/s",
-                       "frac": achieved / hbm, "traffic": None,
+                       "frac": achieved / hbm, "traffic": traffic,
+                       "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_cell_glm "
+                                         "launch at 128^3, scaled per cell" if traffic else None,
                        "bytes_per_cell_stage": bytes_cell,
                        "stage_frac": bytes_cell * ncell * stages / (ms * 1e-3) / 1e9 / hbm}
 
