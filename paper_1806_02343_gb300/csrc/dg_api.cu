@@ -216,7 +216,6 @@ void free_fast_tabs(Ctx& c) {
   switch (c.fast) {
     case 11: delete (FastAll<float, 1>*)c.fast_tabs; break;
     case 12: delete (FastAll<float, 2>*)c.fast_tabs; break;
-    case 13: delete (FastAll<float, 3>*)c.fast_tabs; break;
     case 21: delete (FastAll<double, 1>*)c.fast_tabs; break;
     case 22: delete (FastAll<double, 2>*)c.fast_tabs; break;
   }
@@ -537,7 +536,8 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
     if (fp32(c)) {
       if (degree == 1) c.fast_tabs = make_fast_tabs<float, 1>(h, g, *c.hb);
       if (degree == 2) c.fast_tabs = make_fast_tabs<float, 2>(h, g, *c.hb);
-      if (degree == 3) c.fast_tabs = make_fast_tabs<float, 3>(h, g, *c.hb);
+      // degree 3 runs the generic kernels: its fully unrolled specialisation
+      // costs minutes of compilation for a secondary workload
       if (c.fast_tabs) c.fast = 10 + degree;
     } else {
       if (degree == 1) c.fast_tabs = make_fast_tabs<double, 1>(h, g, *c.hb);
@@ -655,7 +655,6 @@ int operator_pass(Ctx& c, const void* w, const double* wmean, void* out, double*
     switch (c.fast) {
       FASTCASE(11, float, 1, c.face_buf32)
       FASTCASE(12, float, 2, c.face_buf32)
-      FASTCASE(13, float, 3, c.face_buf32)
       FASTCASE(21, double, 1, c.face_buf)
       FASTCASE(22, double, 2, c.face_buf)
     }

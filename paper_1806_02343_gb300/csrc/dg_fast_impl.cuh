@@ -1,4 +1,5 @@
-// Specialised kernels of the DG operator for the GLM scheme on uniform 3D
+// Specialised kernels of the DG operator (included once per precision and
+// degree by the dg_fast_*.cu units) for the GLM scheme on uniform 3D
 // meshes (Sec. 3.5 eq. wdot; Sec. 4.1.2 HLLD; Sec. 4.1.5 GLM).
 //
 // Same arithmetic as the generic kernels, organised for the hardware:
@@ -22,6 +23,10 @@
 #include <utility>
 
 #include "dg_fast.cuh"
+
+#if !defined(DG_FAST_T) || !defined(DG_FAST_DEG) || !defined(DG_FAST_CONST)
+#error "include from a dg_fast_<precision><degree>.cu unit that defines DG_FAST_T, DG_FAST_DEG, DG_FAST_CONST"
+#endif
 #include "dg_phys.cuh"
 
 namespace dgmhd {
@@ -33,31 +38,23 @@ constexpr int TC = 32;        // cells (or faces) per block
 // Reference-element tables in the constant bank. They depend only on the
 // scheme and the degree (not on the mesh), so one copy serves every context;
 // indexed with compile-time offsets, each table value is a constant operand of
-// its FMA. Degree 3 in FP32 (28 KB) stays a kernel parameter: the constant
-// bank holds 64 KB per module.
-__constant__ FastAll<float, 1> c_fast_f1;
-__constant__ FastAll<float, 2> c_fast_f2;
-__constant__ FastAll<double, 1> c_fast_d1;
-__constant__ FastAll<double, 2> c_fast_d2;
-
+// its FMA. Each (precision, degree) is its own translation unit (they compile
+// in parallel) with its own copy.
 template <typename T, int DEG>
 struct FastConst {
   static constexpr bool on = false;
 };
-#define FAST_CONST(T, DEG, SYM)                                                        \
-  template <>                                                                          \
-  struct FastConst<T, DEG> {                                                           \
-    static constexpr bool on = true;                                                   \
-    __device__ static const FastAll<T, DEG>& get() { return SYM; }                      \
-    static cudaError_t upload(const FastAll<T, DEG>& t) {                              \
-      return cudaMemcpyToSymbol(SYM, &t, sizeof(t));                                   \
-    }                                                                                  \
-  };
-FAST_CONST(float, 1, c_fast_f1)
-FAST_CONST(float, 2, c_fast_f2)
-FAST_CONST(double, 1, c_fast_d1)
-FAST_CONST(double, 2, c_fast_d2)
-#undef FAST_CONST
+#if DG_FAST_CONST
+__constant__ FastAll<DG_FAST_T, DG_FAST_DEG> c_fast;
+template <>
+struct FastConst<DG_FAST_T, DG_FAST_DEG> {
+  static constexpr bool on = true;
+  __device__ static const FastAll<DG_FAST_T, DG_FAST_DEG>& get() { return c_fast; }
+  static cudaError_t upload(const FastAll<DG_FAST_T, DG_FAST_DEG>& t) {
+    return cudaMemcpyToSymbol(c_fast, &t, sizeof(t));
+  }
+};
+#endif
 
 template <typename T, int DEG, int A>
 __device__ __forceinline__ const FaceTabs<T, DEG>& face_tabs(const FaceTabs<T, DEG>& param) {
@@ -485,10 +482,6 @@ int fast_to_constant(const FastAll<T, DEG>& tabs) {
                                         const T*, double, double, int, const DevScalars*, const double*,    \
                                         const double*, double*, cudaStream_t);          \
   template int fast_to_constant<T, DEG>(const FastAll<T, DEG>&);
-INSTF(float, 1)
-INSTF(float, 2)
-INSTF(float, 3)
-INSTF(double, 1)
-INSTF(double, 2)
+INSTF(DG_FAST_T, DG_FAST_DEG)
 
 }  // namespace dgmhd

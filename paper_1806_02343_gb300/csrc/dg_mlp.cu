@@ -48,10 +48,45 @@ __device__ __forceinline__ int mrow(const Geom& g, int m) {
   return m < 7 ? g.ldf0 + (m - 5) : g.bz2d;
 }
 
+// Discretisation sizes seen by the feature code: RtDims reads them from the
+// Geom at run time; CtDims<GLM, DEG> fixes them at compile time (3D), so the
+// loops over variables and modes unroll and every row index is a constant.
+struct RtDims {
+  const Geom& g;
+  const MlpTabs& mt;
+  __device__ int n() const { return g.n; }
+  __device__ bool glm() const { return g.glm != 0; }
+  __device__ int D() const { return g.D; }
+  __device__ int ldf0() const { return g.ldf0; }
+  __device__ int ndiv() const { return g.ndiv; }
+  __device__ int bz2d() const { return g.bz2d; }
+  __device__ int deg1(int a) const { return mt.deg1[a]; }
+  __device__ int mrow(int k) const { return dgmhd::mrow(g, k); }
+};
+
+template <bool GLM, int DEG>
+struct CtDims {
+  static constexpr int N = (DEG + 1) * (DEG + 2) * (DEG + 3) / 6;
+  // LDF basis size in 3D (Table A1): 3, 11, 26, 50 for degrees 0..3
+  static constexpr int NDIV = DEG == 0 ? 3 : DEG == 1 ? 11 : DEG == 2 ? 26 : 50;
+  __device__ static constexpr int n() { return N; }
+  __device__ static constexpr bool glm() { return GLM; }
+  __device__ static constexpr int D() { return 3; }
+  __device__ static constexpr int ldf0() { return GLM ? -1 : 5 * N; }
+  __device__ static constexpr int ndiv() { return GLM ? 0 : NDIV; }
+  __device__ static constexpr int bz2d() { return -1; }
+  // degree-1 modes in the basis order: (1,0,0), (0,1,0), (0,0,1)
+  __device__ static constexpr int deg1(int a) { return 1 + a; }
+  __device__ static constexpr int mrow(int k) { return (GLM || k < 5) ? k * N : 5 * N + (k - 5); }
+};
+
 // physical cell means of the 8 MHD variables from the raw mean rows
-__device__ __forceinline__ void phys_means(const Geom& g, const MlpTabs& mt, const float* raw, float* m) {
+template <typename Dm>
+__device__ __forceinline__ void phys_means(const Dm& dm, const MlpTabs& mt, const float* raw, float* m) {
+#pragma unroll
   for (int k = 0; k < 5; ++k) m[k] = raw[k];
-  if (g.glm) {
+  if (dm.glm()) {
+#pragma unroll
     for (int k = 5; k < 8; ++k) m[k] = raw[k];
   } else {
     m[5] = m[6] = m[7] = 0.f;
@@ -59,8 +94,8 @@ __device__ __forceinline__ void phys_means(const Geom& g, const MlpTabs& mt, con
     for (int j = 0; j < 3; ++j)
 #pragma unroll
       for (int cc = 0; cc < 3; ++cc)
-        if (j < g.D && cc < g.D) m[5 + cc] += raw[5 + j] * mt.l2l[(j * 3 + cc) * MLP_MAXN + 0];
-    if (g.D == 2) m[7] = raw[7];
+        if (j < dm.D() && cc < dm.D()) m[5 + cc] += raw[5 + j] * mt.l2l[(j * 3 + cc) * MLP_MAXN + 0];
+    if (dm.D() == 2) m[7] = raw[7];
   }
 }
 
@@ -79,24 +114,25 @@ struct GlobalSrc {
 };
 
 // features of one cell, written through put(k, value) for k in [0, nin)
-template <typename Src, typename Put>
-__device__ __forceinline__ void features_of(const Geom& g, const MlpTabs& mt, const Src& src, Put put) {
-  const int n = g.n;
+template <typename Dm, typename Src, typename Put>
+__device__ __forceinline__ void features_of(const Dm& dm, const MlpTabs& mt, const Src& src, Put put) {
+  const int n = dm.n();
   float m[8];
   {
     float raw[8];
-    for (int k = 0; k < 8; ++k) raw[k] = src.row(mrow(g, k));
-    phys_means(g, mt, raw, m);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) raw[k] = src.row(dm.mrow(k));
+    phys_means(dm, mt, raw, m);
   }
   float dmax[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    if (a >= g.D) break;
+    if (a >= dm.D()) break;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       float raw[8], mn[8];
       src.nbraw(a, s, raw);
-      phys_means(g, mt, raw, mn);
+      phys_means(dm, mt, raw, mn);
 #pragma unroll
       for (int k = 0; k < 8; ++k) dmax[k] = fmaxf(dmax[k], fabsf(mn[k] - m[k]));
       put(8 * n + 2 * a + s, mn[0] / m[0] - 1.f);
@@ -106,32 +142,34 @@ __device__ __forceinline__ void features_of(const Geom& g, const MlpTabs& mt, co
 #pragma unroll
   for (int k = 0; k < 8; ++k) inv[k] = 1.f / (fabsf(m[k]) + dmax[k] + 1e-12f);
   const float imdx = mt.inv_mdx;
-  const int nleg = g.glm ? 8 : 5;
+  const int nleg = dm.glm() ? 8 : 5;
 #pragma unroll
   for (int v = 0; v < 8; ++v) {
-    const bool leg = v < nleg || (!g.glm && g.D == 2 && v == 7);
+    const bool leg = v < nleg || (!dm.glm() && dm.D() == 2 && v == 7);
     if (!leg) continue;
-    const int r0 = (v == 7 && !g.glm) ? g.bz2d : v * n;
+    const int r0 = (v == 7 && !dm.glm()) ? dm.bz2d() : v * n;
+#pragma unroll
     for (int l = 0; l < n; ++l) {
       const float av = (l == 0) ? m[v] : src.row(r0 + l);
       put(v * n + l, av * inv[v]);
 #pragma unroll
       for (int a = 0; a < 3; ++a)
-        if (a < g.D && l == mt.deg1[a]) put(8 * n + 2 * g.D + 8 * a + v, av * imdx);
+        if (a < dm.D() && l == dm.deg1(a)) put(8 * n + 2 * dm.D() + 8 * a + v, av * imdx);
     }
   }
-  if (!g.glm) {
+  if (!dm.glm()) {
     // LDF B -> per-component Legendre coefficients (exact map)
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
-      if (cc >= g.D) break;
+      if (cc >= dm.D()) break;
+#pragma unroll
       for (int l = 0; l < n; ++l) {
         float acc = 0.f;
-        for (int j = 0; j < g.ndiv; ++j) acc += src.row(g.ldf0 + j) * mt.l2l[(j * 3 + cc) * MLP_MAXN + l];
+        for (int j = 0; j < dm.ndiv(); ++j) acc += src.row(dm.ldf0() + j) * mt.l2l[(j * 3 + cc) * MLP_MAXN + l];
         put((5 + cc) * n + l, acc * inv[5 + cc]);
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-          if (a < g.D && l == mt.deg1[a]) put(8 * n + 2 * g.D + 8 * a + 5 + cc, acc * imdx);
+          if (a < dm.D() && l == dm.deg1(a)) put(8 * n + 2 * dm.D() + 8 * a + 5 + cc, acc * imdx);
       }
     }
   }
@@ -140,7 +178,7 @@ __device__ __forceinline__ void features_of(const Geom& g, const MlpTabs& mt, co
 template <typename T, typename Put>
 __device__ __forceinline__ void cell_features(const Geom& g, const MlpTabs& mt, const T* w, const double* /*wmean*/,
                                               int64_t c, Put put) {
-  features_of(g, mt, GlobalSrc<T>{g, w, c}, put);
+  features_of(RtDims{g, mt}, mt, GlobalSrc<T>{g, w, c}, put);
 }
 
 template <typename T>
@@ -477,8 +515,9 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 // a cell of the staged tile: own rows st[r][t], y/z neighbour means nbm[q][k][t]
 // (q = 2 (axis - 1) + side), x neighbours inside the tile or, at its two ends,
 // xe[side][k]
+template <typename Dm>
 struct StagedSrc {
-  const Geom& g;
+  Dm dm;
   const float* st;
   const float* nbm;
   const float* xe;
@@ -490,7 +529,7 @@ struct StagedSrc {
       if (tt < 0 || tt > 127)
         for (int k = 0; k < 8; ++k) raw[k] = xe[s * 8 + k];
       else
-        for (int k = 0; k < 8; ++k) raw[k] = st[mrow(g, k) * 128 + tt];
+        for (int k = 0; k < 8; ++k) raw[k] = st[dm.mrow(k) * 128 + tt];
     } else {
       const int q = 2 * (a - 1) + s;
       for (int k = 0; k < 8; ++k) raw[k] = nbm[(q * 8 + k) * 128 + t];
@@ -500,7 +539,7 @@ struct StagedSrc {
 
 constexpr long long kWaitCycles = 2000000000ll;  // about one second at GB300 clocks
 
-template <int KP>
+template <int KP, bool GLM, int DEG>
 __global__ void __launch_bounds__(128) k_mlp_staged(Geom g, MlpTabs mt, const float* __restrict__ w,
                                                     const __nv_bfloat16* __restrict__ W1,
                                                     const __nv_bfloat16* __restrict__ W2,
@@ -562,7 +601,9 @@ __global__ void __launch_bounds__(128) k_mlp_staged(Geom g, MlpTabs mt, const fl
     {
       __nv_bfloat16* xr = Xs + t * LD1;
       for (int k = nin; k < KP; ++k) xr[k] = __float2bfloat16_rn(0.f);
-      features_of(g, mt, StagedSrc{g, st, nbm, xe, t}, [&](int k, float v) { xr[k] = __float2bfloat16_rn(v); });
+      using Dm = CtDims<GLM, DEG>;
+      features_of(Dm{}, mt, StagedSrc<Dm>{Dm{}, st, nbm, xe, t},
+                  [&](int k, float v) { xr[k] = __float2bfloat16_rn(v); });
     }
     __syncwarp();
     infer_warp<KP>(Xs + warp * 32 * LD1, W1s, W2s, bs, fl + warp * 32, c0 + warp * 32, g.ncell, thresh, flag,
@@ -754,27 +795,42 @@ static bool staged_ok(const Ctx& c, int* nrs) {
   return staged_smem<KP>(*nrs) <= 227 * 1024;
 }
 
+template <int KP, bool GLM, int DEG>
+static void staged_launch(Ctx& c, const void* w, uint8_t* flag, float* prob, cudaStream_t st, int32_t* list,
+                          int nrs) {
+  const Geom& g = c.g;
+  const size_t sm = staged_smem<KP>(nrs);
+  static size_t attr = 0;
+  if (attr < sm) {
+    cudaFuncSetAttribute(k_mlp_staged<KP, GLM, DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = sm;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_staged<KP, GLM, DEG>, 128, sm) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const unsigned nb = (unsigned)std::min<int64_t>(g.ncell / 128, (int64_t)c.nsm * per_sm);
+  k_mlp_staged<KP, GLM, DEG><<<nb, 128, sm, st>>>(g, c.mlp, (const float*)w, (const __nv_bfloat16*)c.mlp_w1,
+                                                   (const __nv_bfloat16*)c.mlp_w2, c.mlp_bias, c.mlp_thresh, flag,
+                                                   prob, list, c.sc, nrs);
+}
+
 template <typename T, int KP>
 static void infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* flag, float* prob, cudaStream_t st,
                          int32_t* list) {
   int nrs = 0;
-  if (sizeof(T) == 4 && staged_ok<KP>(c, &nrs)) {
-    const Geom& g = c.g;
-    const size_t sm = staged_smem<KP>(nrs);
-    static size_t attr = 0;
-    if (attr < sm) {
-      cudaFuncSetAttribute(k_mlp_staged<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      attr = sm;
+  if constexpr (sizeof(T) == 4) {
+    if (staged_ok<KP>(c, &nrs)) {
+      // compile-time feature code for the scheme and degree (KP follows the degree)
+      constexpr int DEG = KP == 64 ? 1 : KP == 112 ? 2 : KP == 192 ? 3 : 0;
+      if constexpr (DEG > 0) {
+        if (c.g.d == DEG) {
+          if (c.g.glm) staged_launch<KP, true, DEG>(c, w, flag, prob, st, list, nrs);
+          else staged_launch<KP, false, DEG>(c, w, flag, prob, st, list, nrs);
+          return;
+        }
+      }
     }
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_staged<KP>, 128, sm) != cudaSuccess ||
-        per_sm < 1)
-      per_sm = 1;
-    const unsigned nb = (unsigned)std::min<int64_t>(g.ncell / 128, (int64_t)c.nsm * per_sm);
-    k_mlp_staged<KP><<<nb, 128, sm, st>>>(g, c.mlp, (const float*)w, (const __nv_bfloat16*)c.mlp_w1,
-                                           (const __nv_bfloat16*)c.mlp_w2, c.mlp_bias, c.mlp_thresh, flag, prob,
-                                           list, c.sc, nrs);
-    return;
   }
   const Geom& g = c.g;
   const size_t sm = (size_t)HID * (KP + 8) * 2 + (size_t)HID * (HID + 8) * 2 + (size_t)4 * 32 * (KP + 8) * 2 +
