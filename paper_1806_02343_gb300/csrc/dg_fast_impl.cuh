@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_fa
 enum { SL_RHO = 0, SL_B = 5, SL_PSI = 8, SL_V = 9, SL_PT = 12, SL_VB = 13, SL_EPT = 14, SL_ZERO = 15, NSL = 16 };
 
 template <typename T, int DEG>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_cell_glm(const CellTabs<T, DEG> tbp, const FastGeom g,
+__global__ void __launch_bounds__(NT, 3) k_cell_glm(const CellTabs<T, DEG> tbp, const FastGeom g,
                                                  const T* __restrict__ w, const T* __restrict__ F, T* out,
                                                  const T* w0, double ca, double cb, float ca32, float cb32,
                                                  int cmode,
@@ -244,6 +244,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_ce
   for (int l = 0; l < N; ++l) wl[l] = live ? w[(int64_t)(v * N + l) * S + c] : (v == 0 && l == 0 ? T(1) : T(0));
   // (FP32 form: wl[0] is the float mirror of the FP64 mean, an exact copy)
   if (!live && v == 4) wl[0] = T(1);  // keep dummy cells physical (rho = 1, E = 1)
+
 
   // flux of variable v: f_a = alpha v_a + beta B_a + (a == gax ? gamma_v : 0)
   int aidx, bidx, gidx, gax;

@@ -546,13 +546,14 @@ __global__ void __launch_bounds__(128) k_mlp_staged(Geom g, MlpTabs mt, const fl
                                                     const float* __restrict__ bias, float thresh,
                                                     uint8_t* __restrict__ flag, float* __restrict__ prob,
                                                     int32_t* __restrict__ list, DevScalars* __restrict__ sc,
-                                                    int nrs) {
+                                                    int nrs, int nbuf) {
   constexpr int LD1 = KP + 8, LD2 = HID + 8;
   extern __shared__ __align__(128) unsigned char smraw[];
-  float* st = reinterpret_cast<float*>(smraw);  // [nrs][128]
-  float* nbm = st + nrs * 128;                   // [4][8][128]
-  float* xe = nbm + 32 * 128;                    // [2][8]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(xe + 16);
+  // nbuf tile buffers, each [nrs][128] own rows then [4][8][128] neighbour means
+  float* buf = reinterpret_cast<float*>(smraw);
+  const int bufsz = (nrs + 32) * 128;
+  float* xe = buf + nbuf * bufsz;                // [2][8]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(xe + 16);  // [2]
   __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(bar + 2);
   __nv_bfloat16* W2s = W1s + HID * LD1;
   __nv_bfloat16* Xs = W2s + HID * LD2;
@@ -564,6 +565,7 @@ __global__ void __launch_bounds__(128) k_mlp_staged(Geom g, MlpTabs mt, const fl
   for (int i = t; i < 3 * HID + 1; i += 128) bs[i] = bias[i];
   if (t == 0) {
     mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -571,18 +573,32 @@ __global__ void __launch_bounds__(128) k_mlp_staged(Geom g, MlpTabs mt, const fl
   const int nin = 8 * g.n + 10 * g.D;
   const unsigned bytes = (unsigned)(nrs + 32) * 512u;
   const int64_t ntile = g.ncell / 128;
-  unsigned parity = 0;
-  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+  // thread 0: bulk copies of tile `tl` into buffer b, completion counted on bar[b]
+  auto issue = [&](int64_t tl, int b) {
+    float* st = buf + b * bufsz;
+    float* nbm = st + nrs * 128;
+    const int64_t c0 = tl * 128;
+    // the buffer's previous reads (generic proxy) are ordered before these writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive_expect_tx(bar + b, bytes);
+    for (int r = 0; r < nrs; ++r) bulk_g2s(st + r * 128, w + (int64_t)r * S + c0, 512u, bar + b);
+    for (int q = 0; q < 4; ++q) {
+      const int64_t cn = nbc(g, c0, 1 + (q >> 1), (q & 1) ? 1 : -1);  // the whole tile shifts
+      for (int k = 0; k < 8; ++k)
+        bulk_g2s(nbm + (q * 8 + k) * 128, w + (int64_t)mrow(g, k) * S + cn, 512u, bar + b);
+    }
+  };
+  // two buffers: the next tile's copies run while this one is computed
+  if (nbuf == 2 && t == 0 && blockIdx.x < ntile) issue(blockIdx.x, 0);
+  unsigned par = 0;  // bit b: phase parity of bar[b]
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x, ++it) {
     const int64_t c0 = tile * 128;
+    const int b = nbuf == 2 ? (it & 1) : 0;
+    const int64_t next = tile + gridDim.x;
     if (t == 0) {
-      // the previous tile's reads (generic proxy) are ordered before these writes
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive_expect_tx(bar, bytes);
-      for (int r = 0; r < nrs; ++r) bulk_g2s(st + r * 128, w + (int64_t)r * S + c0, 512u, bar);
-      for (int q = 0; q < 4; ++q) {
-        const int64_t cn = nbc(g, c0, 1 + (q >> 1), (q & 1) ? 1 : -1);  // the whole tile shifts
-        for (int k = 0; k < 8; ++k) bulk_g2s(nbm + (q * 8 + k) * 128, w + (int64_t)mrow(g, k) * S + cn, 512u, bar);
-      }
+      if (nbuf == 1) issue(tile, 0);
+      else if (next < ntile) issue(next, b ^ 1);  // released by the previous iteration's barrier
     }
     if (t < 16) {
       const int sd = t >> 3, k = t & 7;
@@ -591,18 +607,19 @@ __global__ void __launch_bounds__(128) k_mlp_staged(Geom g, MlpTabs mt, const fl
     // bounded wait for the tile's bytes
     bool ok = false;
     const long long t0 = clock64();
-    while (!(ok = mbar_try_wait(bar, parity)))
+    while (!(ok = mbar_try_wait(bar + b, (par >> b) & 1u)))
       if (clock64() - t0 > kWaitCycles) break;
     if (!__syncthreads_and(ok)) {
       if (t == 0) atomicOr(&sc->status, 8);
       return;
     }
-    parity ^= 1u;
+    par ^= 1u << b;
     {
+      const float* st = buf + b * bufsz;
       __nv_bfloat16* xr = Xs + t * LD1;
       for (int k = nin; k < KP; ++k) xr[k] = __float2bfloat16_rn(0.f);
       using Dm = CtDims<GLM, DEG>;
-      features_of(Dm{}, mt, StagedSrc<Dm>{Dm{}, st, nbm, xe, t},
+      features_of(Dm{}, mt, StagedSrc<Dm>{Dm{}, st, st + nrs * 128, xe, t},
                   [&](int k, float v) { xr[k] = __float2bfloat16_rn(v); });
     }
     __syncwarp();
@@ -610,7 +627,7 @@ __global__ void __launch_bounds__(128) k_mlp_staged(Geom g, MlpTabs mt, const fl
                    prob);
     __syncwarp();
     if (list) compact_warp(fl[t] != 0, c0 + t, list, sc);
-    __syncthreads();  // every read of st / nbm / xe done before the next tile's copies
+    __syncthreads();  // every read of this buffer and of xe done before they are refilled
   }
 }
 
@@ -778,28 +795,32 @@ int mlp_set_weights(Ctx& c, const float* theta_dev, int nin, float thresh) {
   return cudaDeviceSynchronize() == cudaSuccess ? 0 : -3;
 }
 
-// shared memory of k_mlp_staged for nrs staged rows
+// shared memory of k_mlp_staged for nrs staged rows and nbuf tile buffers
 template <int KP>
-static size_t staged_smem(int nrs) {
-  return (size_t)(nrs + 32) * 512 + 16 * 4 + 16 + (size_t)HID * (KP + 8) * 2 + (size_t)HID * (HID + 8) * 2 +
-         (size_t)128 * (KP + 8) * 2 + (3 * HID + 1) * sizeof(float) + 128;
+static size_t staged_smem(int nrs, int nbuf) {
+  return (size_t)nbuf * (nrs + 32) * 512 + 16 * 4 + 16 + (size_t)HID * (KP + 8) * 2 +
+         (size_t)HID * (HID + 8) * 2 + (size_t)128 * (KP + 8) * 2 + (3 * HID + 1) * sizeof(float) + 128;
 }
 
 // the staged kernel applies: FP32 form, uniform 3D mesh, x-rows of whole
-// 128-cell tiles, and the shared memory fits
+// 128-cell tiles, and the shared memory fits. Two tile buffers only where two
+// blocks still fit on an SM: measured at degree 2, one double-buffered block
+// of 4 warps per SM is twice as slow as two single-buffered ones (the feature
+// code needs the warps to hide its latencies).
 template <int KP>
-static bool staged_ok(const Ctx& c, int* nrs) {
+static bool staged_ok(const Ctx& c, int* nrs, int* nbuf) {
   const Geom& g = c.g;
   if (c.p.precision != DG_PREC_FP32MIX || c.amr.on || g.D != 3 || g.nx % 128 != 0) return false;
   *nrs = g.glm ? 8 * g.n : g.nrows;
-  return staged_smem<KP>(*nrs) <= 227 * 1024;
+  *nbuf = 2 * (staged_smem<KP>(*nrs, 2) + 1024) <= 228 * 1024 ? 2 : 1;
+  return staged_smem<KP>(*nrs, *nbuf) <= 227 * 1024;
 }
 
 template <int KP, bool GLM, int DEG>
 static void staged_launch(Ctx& c, const void* w, uint8_t* flag, float* prob, cudaStream_t st, int32_t* list,
-                          int nrs) {
+                          int nrs, int nbuf) {
   const Geom& g = c.g;
-  const size_t sm = staged_smem<KP>(nrs);
+  const size_t sm = staged_smem<KP>(nrs, nbuf);
   static size_t attr = 0;
   if (attr < sm) {
     cudaFuncSetAttribute(k_mlp_staged<KP, GLM, DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -812,21 +833,21 @@ static void staged_launch(Ctx& c, const void* w, uint8_t* flag, float* prob, cud
   const unsigned nb = (unsigned)std::min<int64_t>(g.ncell / 128, (int64_t)c.nsm * per_sm);
   k_mlp_staged<KP, GLM, DEG><<<nb, 128, sm, st>>>(g, c.mlp, (const float*)w, (const __nv_bfloat16*)c.mlp_w1,
                                                    (const __nv_bfloat16*)c.mlp_w2, c.mlp_bias, c.mlp_thresh, flag,
-                                                   prob, list, c.sc, nrs);
+                                                   prob, list, c.sc, nrs, nbuf);
 }
 
 template <typename T, int KP>
 static void infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* flag, float* prob, cudaStream_t st,
                          int32_t* list) {
-  int nrs = 0;
+  int nrs = 0, nbuf = 1;
   if constexpr (sizeof(T) == 4) {
-    if (staged_ok<KP>(c, &nrs)) {
+    if (staged_ok<KP>(c, &nrs, &nbuf)) {
       // compile-time feature code for the scheme and degree (KP follows the degree)
       constexpr int DEG = KP == 64 ? 1 : KP == 112 ? 2 : KP == 192 ? 3 : 0;
       if constexpr (DEG > 0) {
         if (c.g.d == DEG) {
-          if (c.g.glm) staged_launch<KP, true, DEG>(c, w, flag, prob, st, list, nrs);
-          else staged_launch<KP, false, DEG>(c, w, flag, prob, st, list, nrs);
+          if (c.g.glm) staged_launch<KP, true, DEG>(c, w, flag, prob, st, list, nrs, nbuf);
+          else staged_launch<KP, false, DEG>(c, w, flag, prob, st, list, nrs, nbuf);
           return;
         }
       }
