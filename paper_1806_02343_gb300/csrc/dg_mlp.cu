@@ -114,8 +114,13 @@ struct GlobalSrc {
 };
 
 // features of one cell, written through put(k, value) for k in [0, nin)
+// part < 0: every feature; part 0 / 1: the two halves of the work (for two
+// threads per cell): part 0 writes the neighbour-density features and the
+// variables below `vsplit`, part 1 the others (and the LDF-mapped B).
 template <typename Dm, typename Src, typename Put>
-__device__ __forceinline__ void features_of(const Dm& dm, const MlpTabs& mt, const Src& src, Put put) {
+__device__ __forceinline__ void features_of(const Dm& dm, const MlpTabs& mt, const Src& src, Put put,
+                                            int part = -1) {
+  const int vsplit = dm.glm() ? 4 : 5;
   const int n = dm.n();
   float m[8];
   {
@@ -135,7 +140,7 @@ __device__ __forceinline__ void features_of(const Dm& dm, const MlpTabs& mt, con
       phys_means(dm, mt, raw, mn);
 #pragma unroll
       for (int k = 0; k < 8; ++k) dmax[k] = fmaxf(dmax[k], fabsf(mn[k] - m[k]));
-      put(8 * n + 2 * a + s, mn[0] / m[0] - 1.f);
+      if (part <= 0) put(8 * n + 2 * a + s, mn[0] / m[0] - 1.f);
     }
   }
   float inv[8];
@@ -147,6 +152,7 @@ __device__ __forceinline__ void features_of(const Dm& dm, const MlpTabs& mt, con
   for (int v = 0; v < 8; ++v) {
     const bool leg = v < nleg || (!dm.glm() && dm.D() == 2 && v == 7);
     if (!leg) continue;
+    if (part >= 0 && (v < vsplit) != (part == 0)) continue;
     const int r0 = (v == 7 && !dm.glm()) ? dm.bz2d() : v * n;
 #pragma unroll
     for (int l = 0; l < n; ++l) {
@@ -157,7 +163,7 @@ __device__ __forceinline__ void features_of(const Dm& dm, const MlpTabs& mt, con
         if (a < dm.D() && l == dm.deg1(a)) put(8 * n + 2 * dm.D() + 8 * a + v, av * imdx);
     }
   }
-  if (!dm.glm()) {
+  if (!dm.glm() && part != 0) {
     // LDF B -> per-component Legendre coefficients (exact map)
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
@@ -209,7 +215,7 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint
 // Network on the 32 cells of one warp: rows Xw[0..32) of bf16 features (row
 // stride LD1) -> probabilities; writes the flags of the 32 cells to flw[0..32)
 // and, for live cells, flag / prob. base = first cell of the warp.
-template <int KP>
+template <int KP, int NTILE = 2>
 __device__ __forceinline__ void infer_warp(const __nv_bfloat16* Xw, const __nv_bfloat16* W1s,
                                            const __nv_bfloat16* W2s, const float* bs, uint8_t* flw, int64_t base,
                                            int64_t ncell, float thresh, uint8_t* __restrict__ flag,
@@ -217,7 +223,7 @@ __device__ __forceinline__ void infer_warp(const __nv_bfloat16* Xw, const __nv_b
   constexpr int LD1 = KP + 8, LD2 = HID + 8;
   const int lane = threadIdx.x & 31;
   const int gq = lane >> 2, tq = lane & 3;
-  for (int tile = 0; tile < 2; ++tile) {
+  for (int tile = 0; tile < NTILE; ++tile) {
     const __nv_bfloat16* Xt = Xw + tile * 16 * LD1;
     float h1[8][4];
 #pragma unroll
@@ -540,7 +546,7 @@ struct StagedSrc {
 constexpr long long kWaitCycles = 2000000000ll;  // about one second at GB300 clocks
 
 template <int KP, bool GLM, int DEG>
-__global__ void __launch_bounds__(128) k_mlp_staged(Geom g, MlpTabs mt, const float* __restrict__ w,
+__global__ void __launch_bounds__(256) k_mlp_staged(Geom g, MlpTabs mt, const float* __restrict__ w,
                                                     const __nv_bfloat16* __restrict__ W1,
                                                     const __nv_bfloat16* __restrict__ W2,
                                                     const float* __restrict__ bias, float thresh,
@@ -559,10 +565,12 @@ __global__ void __launch_bounds__(128) k_mlp_staged(Geom g, MlpTabs mt, const fl
   __nv_bfloat16* Xs = W2s + HID * LD2;
   float* bs = reinterpret_cast<float*>(Xs + 128 * LD1);
   uint8_t* fl = reinterpret_cast<uint8_t*>(bs + 3 * HID + 1);
-  const int t = threadIdx.x, warp = t >> 5;
-  for (int i = t; i < HID * KP; i += 128) W1s[(i / KP) * LD1 + i % KP] = W1[i];
-  for (int i = t; i < HID * HID; i += 128) W2s[(i / HID) * LD2 + i % HID] = W2[i];
-  for (int i = t; i < 3 * HID + 1; i += 128) bs[i] = bias[i];
+  // two threads per cell: t = cell + 128 * half; the halves split the feature work
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int cell = t & 127, half = t >> 7;
+  for (int i = t; i < HID * KP; i += 256) W1s[(i / KP) * LD1 + i % KP] = W1[i];
+  for (int i = t; i < HID * HID; i += 256) W2s[(i / HID) * LD2 + i % HID] = W2[i];
+  for (int i = t; i < 3 * HID + 1; i += 256) bs[i] = bias[i];
   if (t == 0) {
     mbar_init(bar, 1);
     mbar_init(bar + 1, 1);
@@ -616,17 +624,19 @@ __global__ void __launch_bounds__(128) k_mlp_staged(Geom g, MlpTabs mt, const fl
     par ^= 1u << b;
     {
       const float* st = buf + b * bufsz;
-      __nv_bfloat16* xr = Xs + t * LD1;
-      for (int k = nin; k < KP; ++k) xr[k] = __float2bfloat16_rn(0.f);
+      __nv_bfloat16* xr = Xs + cell * LD1;
+      if (half)
+        for (int q = nin; q < KP; ++q) xr[q] = __float2bfloat16_rn(0.f);
       using Dm = CtDims<GLM, DEG>;
-      features_of(Dm{}, mt, StagedSrc<Dm>{Dm{}, st, st + nrs * 128, xe, t},
-                  [&](int k, float v) { xr[k] = __float2bfloat16_rn(v); });
+      features_of(Dm{}, mt, StagedSrc<Dm>{Dm{}, st, st + nrs * 128, xe, cell},
+                  [&](int q, float v) { xr[q] = __float2bfloat16_rn(v); }, half);
     }
+    __syncthreads();  // both halves of every row written
+    // eight warps, 16 cells (one m16 tile) each
+    infer_warp<KP, 1>(Xs + warp * 16 * LD1, W1s, W2s, bs, fl + warp * 16, c0 + warp * 16, g.ncell, thresh, flag,
+                      prob);
     __syncwarp();
-    infer_warp<KP>(Xs + warp * 32 * LD1, W1s, W2s, bs, fl + warp * 32, c0 + warp * 32, g.ncell, thresh, flag,
-                   prob);
-    __syncwarp();
-    if (list) compact_warp(fl[t] != 0, c0 + t, list, sc);
+    if (list) compact_warp(lane < 16 && fl[warp * 16 + (lane & 15)] != 0, c0 + warp * 16 + lane, list, sc);
     __syncthreads();  // every read of this buffer and of xe done before they are refilled
   }
 }
@@ -827,11 +837,11 @@ static void staged_launch(Ctx& c, const void* w, uint8_t* flag, float* prob, cud
     attr = sm;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_staged<KP, GLM, DEG>, 128, sm) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_staged<KP, GLM, DEG>, 256, sm) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   const unsigned nb = (unsigned)std::min<int64_t>(g.ncell / 128, (int64_t)c.nsm * per_sm);
-  k_mlp_staged<KP, GLM, DEG><<<nb, 128, sm, st>>>(g, c.mlp, (const float*)w, (const __nv_bfloat16*)c.mlp_w1,
+  k_mlp_staged<KP, GLM, DEG><<<nb, 256, sm, st>>>(g, c.mlp, (const float*)w, (const __nv_bfloat16*)c.mlp_w1,
                                                    (const __nv_bfloat16*)c.mlp_w2, c.mlp_bias, c.mlp_thresh, flag,
                                                    prob, list, c.sc, nrs, nbuf);
 }
