@@ -151,11 +151,14 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_fa
   {
     constexpr int PER = (NR + 8) / 9;
     T a[PER], b[PER];
+    const int64_t S9 = 9 * S;
+    const T* pa = w + (int64_t)v * S + c;
+    const T* pb = w + (int64_t)v * S + cl;
 #pragma unroll
-    for (int i = 0; i < PER; ++i) {
+    for (int i = 0; i < PER; ++i, pa += S9, pb += S9) {
       const int r = v + 9 * i;
-      a[i] = (live && r < NR) ? w[r * S + c] : T(1);
-      b[i] = (live && r < NR) ? w[r * S + cl] : T(1);
+      a[i] = (live && r < NR) ? *pa : T(1);
+      b[i] = (live && r < NR) ? *pb : T(1);
     }
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
@@ -241,7 +244,11 @@ __global__ void __launch_bounds__(NT, 3) k_cell_glm(const CellTabs<T, DEG> tbp, 
 
   T wl[N];
 #pragma unroll
-  for (int l = 0; l < N; ++l) wl[l] = live ? w[(int64_t)(v * N + l) * S + c] : (v == 0 && l == 0 ? T(1) : T(0));
+  {
+    // pointer steps of one row (S elements) instead of a 64-bit index per load
+    const T* pw = w + (int64_t)(v * N) * S + c;
+    for (int l = 0; l < N; ++l, pw += S) wl[l] = live ? *pw : (v == 0 && l == 0 ? T(1) : T(0));
+  }
   // (FP32 form: wl[0] is the float mirror of the FP64 mean, an exact copy)
   if (!live && v == 4) wl[0] = T(1);  // keep dummy cells physical (rho = 1, E = 1)
 
@@ -335,18 +342,26 @@ __global__ void __launch_bounds__(NT, 3) k_cell_glm(const CellTabs<T, DEG> tbp, 
   T fsum[6];
   const Coord kc = coord_of(g, live ? c : 0);
   if (live) {
+    const int64_t S9 = 9 * S;  // between the points of one variable's face rows
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         const int64_t fc = s ? nbr(g, kc, a, +1) : c;
+        // the face's QF values, loaded back to back
+        T Fp[QF];
+        {
+          const T* q = F + (int64_t)v * S + (int64_t)(a * QF) * S9 + fc;
+#pragma unroll
+          for (int p = 0; p < QF; ++p, q += S9) Fp[p] = *q;
+        }
         // fs: this face's mean-row sum. The weights of mode 0 are w_p on both
         // sides (P_0 = 1) and round-to-nearest is symmetric, so the sum of
         // -F w_p here is bitwise the negation of the neighbour's sum of F w_p.
         T fs = T(0);
 #pragma unroll
         for (int p = 0; p < QF; ++p) {
-          const T Fr = F[((int64_t)(a * QF + p) * 9 + v) * S + fc];
+          const T Fr = Fp[p];
           const T Fv = s ? -Fr : Fr;
           const T* Pw = tb.Pfw[2 * a + s][p];
           fma2(fs, racc[1], Fv, Fv, Pw[0], Pw[1]);
@@ -408,13 +423,21 @@ __global__ void __launch_bounds__(NT, 3) k_cell_glm(const CellTabs<T, DEG> tbp, 
   }
   const T tm = pick_prec<T>(g.metric, g.metric32), tdt = pick_prec<T>(sc->dt, sc->dt32);
   const T tca = pick_prec<T>(ca, ca32), tcb = pick_prec<T>(cb, cb32), tk = pick_prec<T>(sc->kappa, sc->kappa32);
+  {
+    const int64_t i1 = (int64_t)(v * N + 1) * S + c;
+    T* po = out + i1;
+    const T* p0 = cmode == 0 ? nullptr : w0 + i1;
 #pragma unroll
-  for (int l = 1; l < N; ++l) {
-    T rhs = tm * tb.minv[l] * racc[l];
-    if (v == 8) rhs -= tk * wl[l];
-    const int64_t i = (int64_t)(v * N + l) * S + c;
-    if (cmode == 0) out[i] = rhs;
-    else out[i] = tca * w0[i] + tcb * (wl[l] + tdt * rhs);
+    for (int l = 1; l < N; ++l, po += S) {
+      T rhs = tm * tb.minv[l] * racc[l];
+      if (v == 8) rhs -= tk * wl[l];
+      if (cmode == 0) {
+        *po = rhs;
+      } else {
+        *po = tca * *p0 + tcb * (wl[l] + tdt * rhs);
+        p0 += S;
+      }
+    }
   }
 }
 

@@ -240,3 +240,48 @@ def test_staged_inference_and_gating(divb):
     same = f == (trig & g)
     assert same.mean() > 0.99
     assert rel_err(out[same], expect[same]) < 1e-5
+
+
+@pytest.mark.parametrize("divb", ["powell", "glm"])
+def test_staged_gating_with_positivity(divb):
+    """FP32 form, learned gating and positivity on the staged-kernel mesh: the
+    indicator kernel screens positivity on the state it stages (unflagged cells)
+    and the TVB pass lists the flagged ones. Result: positivity applied to
+    (TVB on the flagged cells, the rest unchanged), with planted negative
+    densities and pressures in flagged and unflagged cells."""
+    import torch
+    S = Scheme(3, 2, divb, G, (128, 4, 3))
+    S.P.Mtilde = 0.5
+    w0 = S.project(_slab(S))
+    rng = np.random.default_rng(11)
+    bad = rng.choice(S.C, 40, replace=False)
+    w0[bad, 1] += 0.6 * np.abs(w0[bad, 0])      # rho: degree-1 mode along x
+    w0[bad, 4 * S.n + 8] += 6.0 * np.abs(w0[bad, 4 * S.n])  # E: a degree-2 mode
+    th = M.init_params(110, seed=7)
+    z, _ = M.forward(th, M.features(S, w0))
+    u = np.unique(z)
+    k = max(1, int(np.searchsorted(u, np.sort(z)[int(0.3 * len(z))])))
+    cut = 0.5 * (u[k - 1] + u[k])
+    th[-1] -= cut
+    sol = _solver(S, "fp32", limiter=2, positivity=1, Mtilde=0.5)
+    if divb == "glm":
+        sol.set_glm(3.0, 1.0)
+    sol.mlp_set_weights(torch.as_tensor(th, dtype=torch.float32, device="cuda"), 0.5)
+    w = to_device(w0, sol)
+    wm = means_to_device(w0, sol, S)
+    gate = torch.zeros(sol.stride, dtype=torch.uint8, device="cuda")
+    sol.mlp_infer(w, wm, gate, None)
+    g = gate[: sol.ncell].cpu().numpy().astype(bool)
+    assert g[bad].any() and (~g[bad]).any()
+    ref_tvb, trig = Limiter(S, tvb=True, positivity=False).tvb_limit(w0, 3.0)
+    expect = Limiter(S, tvb=False, positivity=True).positivity(np.where(g[:, None], ref_tvb, w0))
+    sol.counters(reset=True)
+    flags = torch.zeros(sol.stride, dtype=torch.uint8, device="cuda")
+    sol.limit(w, wm, flags)
+    assert sol.status() in (0, 1)
+    assert sol.counters()["pos_cells"] > 0
+    f = flags[: sol.ncell].cpu().numpy().astype(bool)
+    same = f == (trig & g)
+    assert same.mean() > 0.99
+    out = from_device(w, sol)
+    assert rel_err(out[same], expect[same]) < 1e-5
