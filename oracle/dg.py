@@ -45,6 +45,44 @@ class Params:
     tvb_eps: float = 1e-8
     eps_rho: float = 1e-12
     eps_p: float = 1e-12
+    rk_order: int = 3         # SSP-RK order 1..4 (Sec. 3.6); 0: d + 1, the paper's default
+
+
+def ssp_rk_step(u, L, dt, order, lim=None):
+    """One strong-stability-preserving Runge-Kutta step of order 1..4 for
+    du/dt = L(u) (Sec. 3.6 uses SSP schemes of selectable order, see Gottlieb,
+    Shu & Tadmor). u is the (already limited) step input; `lim` is applied to
+    every later stage input before L evaluates it (Sec. 4.3).
+    1: forward Euler.  2: SSPRK(2,2) and 3: SSPRK(3,3), Shu-Osher forms.
+    4: Ketcheson's ten-stage SSPRK(10,4) in its low-storage form (Ketcheson
+    2008): five forward-Euler stages of dt/6, a combination of the two
+    registers, four more stages of dt/6 and a final stage of dt/10."""
+    lim = lim or (lambda x: x)
+    u0 = u
+    if order == 1:
+        return u0 + dt * L(u0)
+    if order == 2:
+        u1 = lim(u0 + dt * L(u0))
+        return 0.5 * u0 + 0.5 * (u1 + dt * L(u1))
+    if order == 3:
+        u1 = lim(u0 + dt * L(u0))
+        u2 = lim(0.75 * u0 + 0.25 * (u1 + dt * L(u1)))
+        return u0 / 3.0 + 2.0 / 3.0 * (u2 + dt * L(u2))
+    if order == 4:
+        q1 = u0
+        q2 = q1.copy()
+        for i in range(5):
+            if i:
+                q1 = lim(q1)
+            q1 = q1 + dt / 6.0 * L(q1)
+        q2 = q2 / 25.0 + 9.0 / 25.0 * q1
+        q1 = 15.0 * q2 - 5.0 * q1
+        for _ in range(4):
+            q1 = lim(q1)
+            q1 = q1 + dt / 6.0 * L(q1)
+        q1 = lim(q1)
+        return q2 + 0.6 * q1 + dt / 10.0 * L(q1)
+    raise ValueError(f"SSP-RK order {order} not in 1..4")
 
 
 class Scheme:
@@ -301,19 +339,19 @@ class Scheme:
         return float(dt)
 
     # ------------------------------------------------------------------- step
+    def rk_order(self):
+        """SSP-RK order of a step: Params.rk_order, or d + 1 (at most 4) when 0."""
+        return self.P.rk_order or min(self.d + 1, 4)
+
     def step(self, w, dt=None, limiter=None):
-        """One SSP-RK3 step (Shu-Osher form, Sec. 3.6). `limiter(w)` if given is
-        applied to each stage input before it is evaluated (Sec. 4.3)."""
+        """One SSP-RK step of order rk_order() (Sec. 3.6; `ssp_rk_step`).
+        `limiter(w)` if given is applied to each stage input before it is
+        evaluated (Sec. 4.3); dt (if not given) comes from the limited input."""
         lim = limiter or (lambda x: x)
         w0 = lim(w)
         dt = dt if dt is not None else self.dt(w0)
         ch, kappa = self.glm_speeds(dt) if self.divb == "glm" else (None, 0.0)
-        w1 = w0 + dt * self.rhs(w0, ch, kappa)
-        w1 = lim(w1)
-        w2 = 0.75 * w0 + 0.25 * (w1 + dt * self.rhs(w1, ch, kappa))
-        w2 = lim(w2)
-        w3 = w0 / 3.0 + 2.0 / 3.0 * (w2 + dt * self.rhs(w2, ch, kappa))
-        return w3, dt
+        return ssp_rk_step(w0, lambda x: self.rhs(x, ch, kappa), dt, self.rk_order(), lim), dt
 
     # ------------------------------------------------------------------ norms
     def l1_error(self, w, fn_ref, npts=None):

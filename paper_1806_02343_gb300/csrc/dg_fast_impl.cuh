@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_fa
     face_flux(uL, uR, A, gamma, true, ch, eps, Fo);
     if (live) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) F[((int64_t)(A * QF + p) * 9 + k) * S + c] = Fo[k];
+      for (int k = 0; k < 9; ++k) F[((int64_t)(A * QF + p) * 9) * S + c + (int64_t)k * S] = Fo[k];
     }
   }
 }

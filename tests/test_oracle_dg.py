@@ -224,3 +224,55 @@ def test_rhs_local_equals_rhs(divb):
                     for a in range(3) for s in (0, 1)], 1)
     loc = S.rhs_local(w[cells], wnb, 2.5, 0.7)
     assert np.max(np.abs(loc - full[cells])) < 1e-13 * np.abs(full).max()
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
+def test_ssp_rk_order_on_a_nonlinear_ode(order):
+    """u' = -u^2 has u(t) = u0 / (1 + u0 t). Halving dt divides the error by
+    2^order; for orders <= 4 a scalar autonomous problem exercises every
+    Runge-Kutta order condition, so a wrong coefficient of the ten-stage
+    fourth-order scheme shows here."""
+    from oracle.dg import ssp_rk_step
+    u0, T = 1.0, 1.0
+    exact = u0 / (1.0 + u0 * T)
+
+    def err(nsteps):
+        u, dt = np.array([u0]), T / nsteps
+        for _ in range(nsteps):
+            u = ssp_rk_step(u, lambda x: -x * x, dt, order)
+        return abs(u[0] - exact)
+
+    e1, e2 = err(10), err(20)
+    assert abs(math.log2(e1 / e2) - order) < 0.25, (order, e1, e2)
+
+
+def test_ssp_rk4_linear_stability_polynomial():
+    """On u' = z u one step multiplies by R(z) = sum_k z^k / k! + O(z^5)."""
+    from oracle.dg import ssp_rk_step
+    for z in (-0.3, 0.2j, -0.1 + 0.15j):
+        R = ssp_rk_step(np.array([1.0 + 0j]), lambda x: z * x, 1.0, 4)[0]
+        taylor = sum(z ** k / math.factorial(k) for k in range(5))
+        assert abs(R - taylor) < 0.02 * abs(z) ** 5
+
+
+@pytest.mark.parametrize("divb", ["powell", "glm"])
+def test_alfven_2d_degree3_rk4_converges_at_order_4(divb):
+    """Sec. 5.2: degree d with RK order d + 1 (the paper's default) converges at
+    order d + 1; degree 3 takes the fourth-order SSP scheme (8 -> 16 cells:
+    3.93 Powell, 3.75 GLM)."""
+    def error(n):
+        S = Scheme(2, 3, divb, G, n)
+        S.P.rk_order = 0
+        assert S.rk_order() == 4
+        w = S.project(lambda x: W.alfven_2d(x, nvar=S.V))
+        t, T = 0.0, 0.05
+        while t < T - 1e-14:
+            dt = min(S.dt(w), T - t)
+            w, _ = S.step(w, dt)
+            t += dt
+        e, _ = S.l1_error(w, lambda x: W.alfven_2d(x, t=t, nvar=S.V))
+        return e[mhd.BX]
+
+    e8, e16 = error(8), error(16)
+    order = math.log2(e8 / e16)
+    assert 3.5 < order < 4.5, (order, e8, e16)
