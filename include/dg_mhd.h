@@ -107,6 +107,8 @@ typedef struct {
   int positivity;     /* 1: positivity limiter on                    [0]    */
   int generic_kernels;/* 1: force the generic kernels even where a    [0]
                          specialised kernel exists (testing)                 */
+  int rk_order;       /* SSP-RK order of dg_mhd_step, 1..4 (Sec. 3.6); [3]
+                         0: degree + 1 (at most 4), the paper's default      */
 } dg_mhd_params;
 
 /* Fills *p with the defaults listed above. */
@@ -155,7 +157,10 @@ int dg_mhd_limit(dg_mhd_ctx* ctx, void* w, double* wmean, uint8_t* troubled, voi
  * DEVICE scalar *dt_dev and, for GLM, sets c_h and the damping rate. */
 int dg_mhd_dt(dg_mhd_ctx* ctx, const void* w, const double* wmean, double* dt_dev, void* stream);
 
-/* One SSP-RK3 step (Shu-Osher form, Sec. 3.6) in place on w (and wmean).
+/* One SSP-RK step (Sec. 3.6) of order rk_order in place on w (and wmean):
+ * 1 forward Euler, 2 and 3 the Shu-Osher SSPRK(2,2) and SSPRK(3,3), 4 the
+ * ten-stage SSPRK(10,4) of Ketcheson (2008) in its two-register form (ten
+ * operator evaluations of dt/6 each). Scratch: the context's stage buffers.
  * dt_dev: DEVICE scalar with the step, or NULL to compute it from the limited
  * input with dg_mhd_dt (then read it back with dg_mhd_last_dt). Limiters, if
  * enabled, are applied to every stage input before it is evaluated (Sec. 4.3).

@@ -380,6 +380,7 @@ void dg_mhd_default_params(dg_mhd_params* p) {
   p->precision = DG_PREC_FP64;
   p->limiter = DG_LIMIT_OFF;
   p->positivity = 0;
+  p->rk_order = 3;
 }
 
 const char* dg_mhd_strerror(int s) {
@@ -440,6 +441,8 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
   else dg_mhd_default_params(&prm);
   if (prm.precision != DG_PREC_FP64 && prm.precision != DG_PREC_FP32MIX) return DG_E_ARG;
   if (!(prm.cfl > 0.0) || !(prm.cfl_glm > 0.0)) return DG_E_ARG;
+  if (prm.rk_order < 0 || prm.rk_order > 4) return DG_E_ARG;
+  if (prm.rk_order == 0) prm.rk_order = degree + 1 < 4 ? degree + 1 : 4;
   // octree meshes: a global, time-independent c_h (Sec. 4.1.5)
   if (octree && divB_scheme == DG_DIVB_GLM && !(prm.c_h_fixed > 0.0)) return DG_E_ARG;
 
@@ -763,6 +766,59 @@ int dg_mhd_step(dg_mhd_ctx* ctx, void* w, double* wmean, const double* dt_dev, v
   void* s2 = c.stage_buf[1];
   double* m1 = c.stage_mean[0];
   double* m2 = c.stage_mean[1];
+  const int order = c.p.rk_order;
+  auto axpby = [&](double a, const void* x, const double* xm, double b, const void* y, const double* ym, void* o,
+                   double* om) {
+    c.prof.launches[1] += 1;
+    if (fp32(c))
+      launch_axpby<float>(c.g, a, (const float*)x, b, (const float*)y, (float*)o, xm, ym, om, st);
+    else
+      launch_axpby<double>(c.g, a, (const double*)x, b, (const double*)y, (double*)o, nullptr, nullptr, nullptr,
+                           st);
+  };
+  if (order == 1) {
+    // u^{n+1} = u + dt L(u), staged through s1
+    if ((e = operator_pass(c, w, wmean, s1, m1, w, wmean, 0.0, 1.0, 1, st))) return e;
+    axpby(1.0, s1, m1, 0.0, s1, m1, w, wmean);
+    return DG_OK;
+  }
+  if (order == 2) {
+    // u1 = u + dt L(u);  u^{n+1} = 1/2 u + 1/2 (u1 + dt L(u1))
+    if ((e = operator_pass(c, w, wmean, s1, m1, w, wmean, 0.0, 1.0, 1, st))) return e;
+    if ((e = limit_pass(c, s1, m1, nullptr, st))) return e;
+    return operator_pass(c, s1, m1, w, wmean, w, wmean, 0.5, 0.5, 1, st);
+  }
+  if (order == 4) {
+    // Ketcheson's SSPRK(10,4), two registers: q1 (ping-pong between w and s1)
+    // and q2 (s2); every operator evaluation advances by dt/6.
+    c.prof.launches[2] += 1;
+    launch_dt_scale(c.sc, 1.0 / 6.0, st);
+    axpby(1.0, w, wmean, 0.0, w, wmean, s2, m2);  // q2 = u
+    void* q = w;
+    double* qm = wmean;
+    auto forward = [&](bool limit_first) -> int {
+      void* o = q == w ? s1 : w;
+      double* om = q == w ? m1 : wmean;
+      int r;
+      if (limit_first && (r = limit_pass(c, q, qm, nullptr, st))) return r;
+      if ((r = operator_pass(c, q, qm, o, om, q, qm, 0.0, 1.0, 1, st))) return r;
+      q = o;
+      qm = om;
+      return DG_OK;
+    };
+    for (int i = 0; i < 5; ++i)
+      if ((e = forward(i > 0))) return e;
+    axpby(1.0 / 25.0, s2, m2, 9.0 / 25.0, q, qm, s2, m2);  // q2 = q2/25 + 9 q1/25
+    axpby(15.0, s2, m2, -5.0, q, qm, q, qm);              // q1 = 15 q2 - 5 q1
+    for (int i = 0; i < 4; ++i)
+      if ((e = forward(true))) return e;
+    if ((e = limit_pass(c, q, qm, nullptr, st))) return e;
+    // u^{n+1} = q2 + 3/5 q1 + dt/10 L(q1) = q2 + 3/5 (q1 + dt/6 L(q1)); q1 is in s1 here
+    if ((e = operator_pass(c, q, qm, w, wmean, s2, m2, 1.0, 0.6, 1, st))) return e;
+    c.prof.launches[2] += 1;
+    launch_dt_scale(c.sc, 1.0, st);
+    return DG_OK;
+  }
   // u1 = u + dt L(u)
   if ((e = operator_pass(c, w, wmean, s1, m1, w, wmean, 0.0, 1.0, 1, st))) return e;
   if ((e = limit_pass(c, s1, m1, nullptr, st))) return e;

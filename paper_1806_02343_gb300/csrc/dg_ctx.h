@@ -68,6 +68,7 @@ struct DevScalars {
   unsigned long long cnt_limited;  // cells whose slopes the TVB procedure changed, summed over passes
   float dt32, ch32, kappa32;       // FP32 copies of dt, ch, kappa (written with them)
   float pad32;
+  double dt_step;                  // the step's dt; dt itself may be a fraction of it for some stages
 };
 
 // a device scalar in the working precision T (FP32 kernels read the float copy)

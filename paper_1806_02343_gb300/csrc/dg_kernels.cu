@@ -500,6 +500,7 @@ __global__ void k_dt_finalize(Geom g, dg_mhd_params p, DevScalars* sc, const dou
     atomicOr(&sc->status, 1);
   }
   sc->dt = dt;
+  sc->dt_step = dt;
   sc->dt32 = (float)dt;
   if (dt_out) *dt_out = dt;
   if (g.glm) {
@@ -514,6 +515,35 @@ __global__ void k_dt_finalize(Geom g, dg_mhd_params p, DevScalars* sc, const dou
       if (ch < smax) atomicOr(&sc->status, 4);
     }
   }
+}
+
+// stages of a fraction f of the step (the fourth-order scheme's dt/6)
+__global__ void k_dt_scale(DevScalars* sc, double f) {
+  sc->dt = sc->dt_step * f;
+  sc->dt32 = (float)sc->dt;
+}
+
+// out = a x + b y on every state row (blockIdx.y = row); FP32 form: the mean
+// rows in FP64 from xm, ym (om written, its float mirror in out)
+template <typename T>
+__global__ void k_axpby(Geom g, double a, const T* __restrict__ x, double b, const T* __restrict__ y, T* out,
+                        const double* __restrict__ xm, const double* __restrict__ ym, double* om) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const int r = blockIdx.y;
+  const int64_t i = (int64_t)r * g.stride + c;
+  if (om) {
+    const int nm = g.glm ? 9 : 8;
+    for (int m = 0; m < nm; ++m)
+      if (mean_row(g, m) == r) {
+        const int64_t j = (int64_t)m * g.stride + c;
+        const double o = a * xm[j] + b * ym[j];
+        om[j] = o;
+        out[i] = (T)o;
+        return;
+      }
+  }
+  out[i] = (T)a * x[i] + (T)b * y[i];
 }
 
 __global__ void k_set_glm(DevScalars* sc, double ch, double kappa) {
@@ -591,6 +621,19 @@ void launch_dt_from_value(const Geom& g, const dg_mhd_params& p, const double* d
 }
 
 void launch_dt_init(DevScalars* sc, cudaStream_t st) { k_dt_init<<<1, 1, 0, st>>>(sc); }
+
+void launch_dt_scale(DevScalars* sc, double f, cudaStream_t st) { k_dt_scale<<<1, 1, 0, st>>>(sc, f); }
+
+template <typename T>
+void launch_axpby(const Geom& g, double a, const T* x, double b, const T* y, T* out, const double* xm,
+                  const double* ym, double* om, cudaStream_t st) {
+  const dim3 grid((unsigned)((g.ncell + 255) / 256), (unsigned)g.nrows);
+  k_axpby<T><<<grid, 256, 0, st>>>(g, a, x, b, y, out, xm, ym, om);
+}
+template void launch_axpby<float>(const Geom&, double, const float*, double, const float*, float*, const double*,
+                                  const double*, double*, cudaStream_t);
+template void launch_axpby<double>(const Geom&, double, const double*, double, const double*, double*,
+                                   const double*, const double*, double*, cudaStream_t);
 
 void launch_dt_finalize(const Geom& g, const dg_mhd_params& p, DevScalars* sc, double* dt_out, cudaStream_t st) {
   k_dt_finalize<<<1, 1, 0, st>>>(g, p, sc, nullptr, dt_out);

@@ -24,6 +24,12 @@ void launch_dt_from_value(const Geom& g, const dg_mhd_params& p, const double* d
                           cudaStream_t st);
 void launch_set_glm(DevScalars* sc, double ch, double kappa, cudaStream_t st);
 void launch_dt_init(DevScalars* sc, cudaStream_t st);
+// sets the device dt to f times the step's dt (and its FP32 copy)
+void launch_dt_scale(DevScalars* sc, double f, cudaStream_t st);
+// out = a x + b y over all state rows; FP32 form: FP64 means from xm, ym into om
+template <typename T>
+void launch_axpby(const Geom& g, double a, const T* x, double b, const T* y, T* out, const double* xm,
+                  const double* ym, double* om, cudaStream_t st);
 void launch_dt_finalize(const Geom& g, const dg_mhd_params& p, DevScalars* sc, double* dt_out, cudaStream_t st);
 template <typename T>
 void launch_mirror_means(const Geom& g, const double* wmean, T* w, cudaStream_t st);

@@ -37,7 +37,7 @@ def test_default_params_and_strerror(lib):
     p = binding.default_params()
     assert p.cfl == 0.3 and p.cfl_glm == 0.9 and p.c_r == 0.18 and p.eta_powell == 0.2
     assert p.Mtilde == 5.0 and p.beta == 2.0 and p.tvb_eps == 1e-8
-    assert p.eps_rho == 1e-12 and p.eps_p == 1e-12
+    assert p.eps_rho == 1e-12 and p.eps_p == 1e-12 and p.rk_order == 3
     assert lib.dg_mhd_strerror(0) == b"ok"
     assert lib.dg_mhd_strerror(-4).startswith(b"non-finite")
 
@@ -56,6 +56,8 @@ def test_init_rejects_bad_arguments(lib):
     assert lib.dg_mhd_init(ctypes.byref(m), 7, 0, 5.0 / 3.0, None, ctypes.byref(h)) == -7
     assert lib.dg_mhd_init(ctypes.byref(m), 2, 5, 5.0 / 3.0, None, ctypes.byref(h)) == -1
     assert lib.dg_mhd_init(ctypes.byref(m), 2, 0, 1.0, None, ctypes.byref(h)) == -1
+    bad = binding.default_params(rk_order=5)             # SSP-RK orders are 1..4 (0: degree + 1)
+    assert lib.dg_mhd_init(ctypes.byref(m), 2, 0, 5.0 / 3.0, ctypes.byref(bad), ctypes.byref(h)) == -1
     assert lib.dg_mhd_init(None, 2, 0, 1.4, None, ctypes.byref(h)) == -1
     m.n[0] = m.n[1] = 2048
     m.n[2] = 1024                                        # 2^32 cells: beyond 32-bit indices

@@ -75,13 +75,17 @@ def test_positivity_fp64(divb):
     assert rel_err(from_device(w, sol), ref) < 1e-12
 
 
+@pytest.mark.parametrize("order", [3, 4])
 @pytest.mark.parametrize("divb", ["powell", "glm"])
-def test_step_with_limiters_fp64(divb):
+def test_step_with_limiters_fp64(divb, order):
+    """Limiters before every stage evaluation (Sec. 4.3), SSP-RK3 and the
+    ten-stage fourth-order scheme."""
     S = Scheme(3, 2, divb, G, (8, 7, 6))
     S.P.Mtilde = 0.5
+    S.P.rk_order = order
     w0 = S.project(_shock_field(S.V))
     lim = Limiter(S, tvb=True, positivity=True)
-    sol = _solver(S, (8, 7, 6), limiter=1, positivity=1, Mtilde=0.5)
+    sol = _solver(S, (8, 7, 6), limiter=1, positivity=1, Mtilde=0.5, rk_order=order)
     w = to_device(w0, sol)
     wo = w0.copy()
     for _ in range(2):

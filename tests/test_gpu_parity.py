@@ -187,3 +187,51 @@ def test_step_fp32_form(D, d, divb, ncell, fname):
     from gpu_helpers import mean_rows
     got_means = wm[:, : sol.ncell].cpu().numpy().T
     assert rel_err(got_means, wo[:, mean_rows(S)]) < 1e-6
+
+
+@pytest.mark.parametrize("order", [1, 2, 4])
+@pytest.mark.parametrize("D,d,divb,ncell,fname", [CASES[0], CASES[2], CASES[4], CASES[3]])
+def test_step_rk_orders(D, d, divb, ncell, fname, order):
+    """SSP-RK orders 1, 2 and 4 (Sec. 3.6) against the oracle's steps: FP64 to
+    1e-11 (two steps, dt computed on both sides); the FP32 form to 1e-5 (dt
+    from the oracle)."""
+    import torch
+    from paper_1806_02343_gb300.binding import Solver, DG_PREC_FP32MIX
+    S = Scheme(D, d, divb, G, ncell)
+    S.P.rk_order = order
+    w0 = S.project(_fn(fname, S.V))
+    sol = Solver(D, ncell, d, divb, gamma=G, box_len=S.L, rk_order=order)
+    w = to_device(w0, sol)
+    wo = w0.copy()
+    for _ in range(2):
+        sol.step(w)
+        wo, _ = S.step(wo)
+    assert rel_err(from_device(w, sol), wo) < 1e-11
+    assert sol.status() == 0
+    sol = Solver(D, ncell, d, divb, gamma=G, box_len=S.L, rk_order=order, precision=DG_PREC_FP32MIX)
+    w = to_device(w0, sol)
+    wm = means_to_device(w0, sol, S)
+    wo = w0.copy()
+    for _ in range(2):
+        dto = S.dt(wo)
+        sol.step(w, wm, torch.tensor([dto], dtype=torch.float64, device="cuda"))
+        wo, _ = S.step(wo, dto)
+    assert rel_err(from_device(w, sol), wo) < 1e-5
+    from gpu_helpers import mean_rows
+    assert rel_err(wm[:, : sol.ncell].cpu().numpy().T, wo[:, mean_rows(S)]) < 1e-6
+
+
+def test_rk_order_default_is_degree_plus_one():
+    """rk_order = 0 selects d + 1 (at most 4), the paper's default."""
+    import torch
+    from paper_1806_02343_gb300.binding import Solver
+    D, d, divb, ncell, fname = CASES[3]
+    S = Scheme(D, d, divb, G, ncell)
+    S.P.rk_order = 0
+    w0 = S.project(_fn(fname, S.V))
+    sol = Solver(D, ncell, d, divb, gamma=G, box_len=S.L, rk_order=0)
+    w = to_device(w0, sol)
+    sol.step(w)
+    wo, _ = S.step(w0)
+    assert S.rk_order() == 4
+    assert rel_err(from_device(w, sol), wo) < 1e-11
