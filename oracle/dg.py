@@ -322,6 +322,34 @@ class Scheme:
         # reference face measure -> physical: (dx/2)^(D-1); 1/V_K = dx^-D
         return acc * (0.5 * self.dx) ** (self.D - 1) / self.dx ** self.D
 
+    def divb_norms(self, w):
+        """Divergence diagnostics of App. C:
+        cell:       |div B|_K, eq. divb-cell: (1/V_K) int_K |div B| (Gauss
+                    points of the scheme) plus the face part (`divb_face`);
+        total:      ||div B||_1 = (1/V) sum_K V_K |div B|_K, eq. divb-total;
+        normalized: |div B|_K dx / |mean B|_K, eq. divb-normalized;
+        signed:     (div B)_K = (1/V_K) oint B^n_F dS (outward normals),
+                    eq. divb-gauss read with the cell volume V_K."""
+        D, dx = self.D, self.dx
+        div = sum(self.eval_points(w, self.Gv[a])[..., mhd.BX + a] for a in range(D)) * (2.0 / dx)
+        vol = (np.abs(div) @ self.wv) / 2.0 ** D
+        face = self.divb_face(w)
+        sg = np.zeros(self.C)
+        for a in range(D):
+            L = self.nbr_minus[a]
+            uL = self.eval_points(w[L], self.Sf[(a, 1)])
+            uR = self.eval_points(w, self.Sf[(a, -1)])
+            BnF = mhd.bn_face(uL[..., mhd.RHO], uR[..., mhd.RHO], uL[..., mhd.BX + a], uR[..., mhd.BX + a])
+            flux = BnF @ self.wf
+            np.add.at(sg, L, flux)      # +a face of the left cell
+            sg -= flux                  # -a face of this cell
+        sg *= (0.5 * dx) ** (D - 1) / dx ** D
+        cell = vol + face
+        Bm = mhd.primitives(self.means(w), self.gamma)[3]
+        bmag = np.sqrt(np.sum(Bm * Bm, -1))
+        return {"cell": cell, "volume": vol, "face": face, "signed": sg, "total": float(np.mean(cell)),
+                "normalized": cell * dx / bmag}
+
     def dt(self, w):
         """Global dt: eq. cfl from cell means, and eq. powell_dt for Powell."""
         g = self.gamma

@@ -276,3 +276,62 @@ def test_alfven_2d_degree3_rk4_converges_at_order_4(divb):
     e8, e16 = error(8), error(16)
     order = math.log2(e8 / e16)
     assert 3.5 < order < 4.5, (order, e8, e16)
+
+
+def _bfield_state(bx_fn, nvar):
+    def fn(x):
+        one = np.ones(x.shape[:-1])
+        B = np.stack([bx_fn(x), 0.0 * one, 0.0 * one], -1)
+        u = mhd.conserved(one, np.zeros(x.shape[:-1] + (3,)), one, B, G)
+        if nvar == 9:
+            u = np.concatenate([u, 0.0 * one[..., None]], -1)
+        return u
+    return fn
+
+
+@pytest.mark.parametrize("divb", ["powell", "glm"])
+def test_divb_diagnostics_uniform_field_is_zero(divb):
+    S = Scheme(3, 2, divb, G, (5, 4, 3))
+    w = S.project(lambda x: W.uniform_state(x, nvar=S.V))
+    r = S.divb_norms(w)
+    assert r["total"] < 1e-13 and np.max(np.abs(r["signed"])) < 1e-12
+
+
+@pytest.mark.parametrize("D,divb", [(2, "powell"), (3, "powell"), (2, "glm"), (3, "glm")])
+def test_divb_diagnostics_jump_closed_form(D, divb):
+    """B_x = 1 for x < 1/2, 2 beyond (cell-aligned, equal densities, so B^n_F
+    = 3/2 on the two jump planes): no volume part; each plane adds
+    |3/2 - 1| + |3/2 - 2| per unit area, so ||div B||_1 = 2 (App. C eq.
+    divb-total); the cells beside a plane have |div B|_K = 1/(2 dx), a
+    normalised divergence of 1/2 |B|^-1, and signed divergence +-1/(2 dx)."""
+    n = 8
+    S = Scheme(D, 1, divb, G, n)
+    w = S.project(_bfield_state(lambda x: np.where(x[..., 0] < 0.5, 1.0, 2.0), S.V))
+    r = S.divb_norms(w)
+    assert abs(r["total"] - 2.0) < 1e-12
+    assert np.max(r["volume"]) < 1e-12
+    ix = np.rint(S.centers[:, 0] / S.dx - 0.5).astype(int)
+    dx = S.dx
+    for i, val in ((n // 2 - 1, 0.5 / dx), (n // 2, 0.5 / dx), (0, -0.5 / dx), (n - 1, -0.5 / dx)):
+        assert np.allclose(r["signed"][ix == i], val, rtol=1e-12, atol=1e-12)
+        assert np.allclose(r["cell"][ix == i], 0.5 / dx, rtol=1e-12)
+    bx = np.where(ix < n // 2, 1.0, 2.0)
+    side = np.isin(ix, (0, n // 2 - 1, n // 2, n - 1))
+    assert np.allclose(r["normalized"][side], 0.5 / bx[side], rtol=1e-12)
+    assert np.max(np.abs(r["signed"][~side])) < 1e-12
+    assert abs(np.sum(r["signed"])) < 1e-9      # Gauss: the face terms cancel in pairs
+
+
+def test_divb_diagnostics_volume_part_converges():
+    """GLM, B = (cos 2 pi x, 0, 0): div B = -2 pi sin 2 pi x and
+    int_0^1 |div B| dx = 4; the volume part carries it (metric 2/dx), the face
+    jumps vanish with the resolution."""
+    out = []
+    for n in (16, 32):
+        S = Scheme(2, 2, "glm", G, n)
+        w = S.project(_bfield_state(lambda x: np.cos(2 * np.pi * x[..., 0]), S.V))
+        out.append(S.divb_norms(w))
+    assert abs(np.mean(out[1]["volume"]) - 4.0) < 0.005
+    # |div B|_K's face part is a jump of O(dx^3) over dx: second order
+    ratio = np.mean(out[0]["face"]) / np.mean(out[1]["face"])
+    assert 3.5 < ratio < 4.5, ratio
