@@ -180,6 +180,20 @@ int dg_mhd_status(dg_mhd_ctx* ctx, int sync);
  * since the last reset. Synchronises the device; reset = 1 clears them. */
 int dg_mhd_counters(dg_mhd_ctx* ctx, int64_t* pos_cells, double* inj_mass, double* inj_energy, int reset);
 
+/* Divergence diagnostics of App. C on a uniform mesh (DG_E_UNSUPPORTED on
+ * octrees), from the state w (and wmean in the FP32 form):
+ * res (DEVICE, 4 doubles): [0] ||div B||_1 = (1/V) sum_K V_K |div B|_K
+ * (eq. divb-total) with |div B|_K of eq. divb-cell: the L1 norm of div B over
+ * the cell (the scheme's Gauss points) plus the face jumps |B^n_F - B^n_K|
+ * over its boundary, both divided by V_K; [1] the volume average and [2] the
+ * maximum of the normalised divergence |div B|_K dx / |mean B|_K
+ * (eq. divb-normalized; 0 where the mean field vanishes); [3] the maximum of
+ * |(div B)_K|, the signed divergence (1/V_K) oint B^n_F dS (eq. divb-gauss,
+ * read with the cell volume). per_cell (DEVICE, 3 rows of cell_stride
+ * doubles, or NULL): |div B|_K, (div B)_K and the normalised divergence.
+ * Uses the context's face scratch; asynchronous on stream. */
+int dg_mhd_divb(dg_mhd_ctx* ctx, const void* w, const double* wmean, double* res, double* per_cell, void* stream);
+
 /* Troubled-cell statistics of the TVB limiter (Sec. 4.2 judges a detector by
  * its sensitivity and specificity; these counts give its workload), summed
  * since the last reset: limiter passes that ran the TVB procedure, cells that

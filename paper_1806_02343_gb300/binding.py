@@ -24,7 +24,7 @@ EXPORTS = [
     "dg_mhd_rhs", "dg_mhd_limit", "dg_mhd_dt", "dg_mhd_step", "dg_mhd_last_dt", "dg_mhd_status",
     "dg_mhd_profile", "dg_mhd_profile_read", "dg_mhd_launch_count", "dg_mhd_rhs_noalloc", "dg_mhd_destroy",
     "dg_mhd_strerror", "dg_mhd_mlp_features", "dg_mhd_mlp_set_weights", "dg_mhd_mlp_infer", "dg_mhd_mlp_loss_grad",
-    "dg_mhd_mlp_train", "dg_mhd_counters", "dg_mhd_limiter_counts",
+    "dg_mhd_mlp_train", "dg_mhd_counters", "dg_mhd_limiter_counts", "dg_mhd_divb",
 ]
 KIND_FACE, KIND_CELL, KIND_DT, KIND_LIMIT, KIND_PROJECT, KIND_POSITIVITY, KIND_MLP = range(7)
 
@@ -83,6 +83,7 @@ def lib():
     L.dg_mhd_counters.argtypes = [vp, i64p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                   ctypes.c_int]
     L.dg_mhd_limiter_counts.argtypes = [vp, i64p, i64p, i64p, ctypes.c_int]
+    L.dg_mhd_divb.argtypes = [vp, vp, vp, vp, vp, vp]
     L.dg_mhd_limiter_counts.restype = ctypes.c_int
     L.dg_mhd_destroy.argtypes = [vp]
     L.dg_mhd_destroy.restype = None
@@ -279,6 +280,20 @@ class Solver:
         _check(lib().dg_mhd_counters(self.h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(e), 1 if reset else 0),
                "dg_mhd_counters")
         return {"pos_cells": n.value, "inj_mass": m.value, "inj_energy": e.value}
+
+    def divb_norms(self, w, wmean=None, per_cell=False):
+        """Divergence diagnostics (App. C): dict with the global norm, mean and
+        maximum normalised divergence, maximum |signed divergence| and, with
+        per_cell, the device rows (|div B|_K, (div B)_K, normalised)."""
+        import torch
+        res = torch.zeros(4, dtype=torch.float64, device=w.device)
+        pc = torch.zeros((3, self.stride), dtype=torch.float64, device=w.device) if per_cell else None
+        _check(lib().dg_mhd_divb(self.h, _ptr(w), _ptr(wmean), _ptr(res), _ptr(pc), _stream()), "dg_mhd_divb")
+        r = res.cpu().tolist()
+        out = {"total": r[0], "normalized_mean": r[1], "normalized_max": r[2], "signed_max": r[3]}
+        if per_cell:
+            out["per_cell"] = pc
+        return out
 
     def limiter_counts(self, reset=False):
         p, f, l = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

@@ -889,6 +889,21 @@ int dg_mhd_counters(dg_mhd_ctx* ctx, int64_t* pos_cells, double* inj_mass, doubl
   return DG_OK;
 }
 
+int dg_mhd_divb(dg_mhd_ctx* ctx, const void* w, const double* wmean, double* res, double* per_cell,
+                void* stream) {
+  if (!ctx || !w || !res) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  if (fp32(c) && !wmean) return DG_E_ARG;
+  if (c.amr.on) return DG_E_UNSUPPORTED;
+  c.prof.launches[2] += 2;
+  if (fp32(c))
+    launch_divb_diag<float>(c.g, c.t32, (const float*)w, wmean, reinterpret_cast<double*>(c.face_buf32), res,
+                            per_cell, S(stream));
+  else
+    launch_divb_diag<double>(c.g, c.t64, (const double*)w, nullptr, c.face_buf, res, per_cell, S(stream));
+  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
+}
+
 int dg_mhd_limiter_counts(dg_mhd_ctx* ctx, int64_t* passes, int64_t* flagged, int64_t* limited, int reset) {
   if (!ctx) return DG_E_ARG;
   Ctx& c = ctx->c;

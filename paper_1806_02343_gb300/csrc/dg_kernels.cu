@@ -335,6 +335,140 @@ __global__ void k_divb_face(Geom g, Tables<T> tb, const T* __restrict__ w, T* __
 // ---------------------------------------------------------------- dt
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
+// ---------------------------------------------------------------- div B diagnostics (App. C)
+// normal component a of B on face f of cell c at face point p (GLM: Legendre
+// rows of B_a; Powell: the LDF rows)
+template <typename T>
+__device__ double bn_trace(const Geom& g, const Tables<T>& tb, const T* w, int64_t c, int f, int a, int p) {
+  const int64_t S = g.stride;
+  double b = 0.0;
+  if (g.glm) {
+    for (int l = 0; l < g.n; ++l)
+      b += (double)w[(int64_t)((5 + a) * g.n + l) * S + c] * (double)tb.Pf[((size_t)f * g.n + l) * g.Qf + p];
+  } else {
+    for (int j = 0; j < g.ndiv; ++j)
+      b += (double)w[(int64_t)(g.ldf0 + j) * S + c] *
+           (double)tb.Lf[(((size_t)f * g.ndiv + j) * g.DB + a) * g.Qf + p];
+  }
+  return b;
+}
+
+// per face point of every face (axis a, right cell c, left cell its -a
+// neighbour): w_p |B^n_F - B^n_L|, w_p |B^n_F - B^n_R| and w_p B^n_F
+template <typename T>
+__global__ void k_divb_diag_face(Geom g, Tables<T> tb, const T* __restrict__ w, double* __restrict__ fb) {
+  const int64_t total = (int64_t)g.D * g.ncell * g.Qf;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= total) return;
+  const int p = (int)(tid % g.Qf);
+  const int64_t fc = tid / g.Qf;
+  const int64_t c = fc % g.ncell;
+  const int a = (int)(fc / g.ncell);
+  const int64_t cl = neighbour(g, c, a, -1);
+  const int64_t S = g.stride;
+  double rL = 0.0, rR = 0.0;
+  for (int l = 0; l < g.n; ++l) {
+    rL += (double)w[l * S + cl] * (double)tb.Pf[((size_t)(2 * a + 1) * g.n + l) * g.Qf + p];
+    rR += (double)w[l * S + c] * (double)tb.Pf[((size_t)(2 * a) * g.n + l) * g.Qf + p];
+  }
+  const double bL = bn_trace(g, tb, w, cl, 2 * a + 1, a, p);
+  const double bR = bn_trace(g, tb, w, c, 2 * a, a, p);
+  const double bF = bn_face(rL, rR, bL, bR);
+  const double wp = (double)tb.wf[p];
+  double* o = fb + tid * 3;
+  o[0] = wp * fabs(bF - bL);
+  o[1] = wp * fabs(bF - bR);
+  o[2] = wp * bF;
+}
+
+// per cell: |div B|_K (eq. divb-cell), signed (eq. divb-gauss, 1/V_K) and
+// normalised (eq. divb-normalized); block sums / maxima into res:
+// res[0] += sum |div B|_K / ncell (eq. divb-total: equal volumes),
+// res[1] += sum normalised / ncell, res[2] = max normalised, res[3] = max |signed|
+template <typename T>
+__global__ void k_divb_diag_cell(Geom g, Tables<T> tb, const T* __restrict__ w, const double* __restrict__ wmean,
+                                 const double* __restrict__ fb, double* res, double* per_cell) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double cell = 0.0, nrm = 0.0, sga = 0.0;
+  if (c < g.ncell) {
+    const int64_t S = g.stride;
+    // (1/V_K) int_K |div B| = 2^-D sum_q w_q |div B(q)|, div B = (2/dx) sum_a dB_a/dxi_a
+    double vol = 0.0;
+    for (int q = 0; q < g.Qv; ++q) {
+      double dv = 0.0;
+      for (int a = 0; a < g.D; ++a) {
+        if (g.glm) {
+          for (int l = 0; l < g.n; ++l)
+            dv += (double)w[(int64_t)((5 + a) * g.n + l) * S + c] * (double)tb.dPv[((size_t)a * g.n + l) * g.Qv + q];
+        } else {
+          for (int j = 0; j < g.ndiv; ++j)
+            dv += (double)w[(int64_t)(g.ldf0 + j) * S + c] *
+                  (double)tb.dLv[(((size_t)a * g.ndiv + j) * g.DB + a) * g.Qv + q];
+        }
+      }
+      vol += (double)tb.wv[q] * fabs(dv);
+    }
+    vol *= (2.0 / g.dx) / (double)(1 << g.D);
+    double face = 0.0, sg = 0.0;
+    for (int a = 0; a < g.D; ++a) {
+      const int64_t cp = neighbour(g, c, a, +1);
+      for (int p = 0; p < g.Qf; ++p) {
+        const double* om = fb + (((int64_t)a * g.ncell + c) * g.Qf + p) * 3;   // own -a face: R side
+        const double* op = fb + (((int64_t)a * g.ncell + cp) * g.Qf + p) * 3;  // own +a face: L side
+        face += om[1] + op[0];
+        sg += op[2] - om[2];
+      }
+    }
+    double meas = 1.0;
+    for (int a = 0; a < g.D - 1; ++a) meas *= 0.5 * g.dx;
+    for (int a = 0; a < g.D; ++a) meas /= g.dx;
+    face *= meas;
+    sg *= meas;
+    cell = vol + face;
+    // |mean B|
+    double bm[3] = {0.0, 0.0, 0.0};
+    if (g.glm) {
+      for (int a = 0; a < 3; ++a) bm[a] = wmean ? wmean[(int64_t)(5 + a) * S + c] : (double)w[(int64_t)(5 + a) * g.n * S + c];
+    } else {
+      for (int j = 0; j < g.D; ++j) {
+        const double wj = wmean ? wmean[(int64_t)(5 + j) * S + c] : (double)w[(int64_t)(g.ldf0 + j) * S + c];
+        for (int cc = 0; cc < g.DB; ++cc) bm[cc] += wj * (double)tb.L0[j * g.DB + cc];
+      }
+      if (g.bz2d >= 0) bm[2] = wmean ? wmean[(int64_t)7 * S + c] : (double)w[(int64_t)g.bz2d * S + c];
+    }
+    const double bmag = sqrt(bm[0] * bm[0] + bm[1] * bm[1] + bm[2] * bm[2]);
+    nrm = bmag > 0.0 ? cell * g.dx / bmag : 0.0;
+    sga = fabs(sg);
+    if (per_cell) {
+      per_cell[c] = cell;
+      per_cell[S + c] = sg;
+      per_cell[2 * S + c] = nrm;
+    }
+  }
+  __shared__ double r0[256], r1[256], r2[256], r3[256];
+  r0[threadIdx.x] = cell;
+  r1[threadIdx.x] = nrm;
+  r2[threadIdx.x] = nrm;
+  r3[threadIdx.x] = sga;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      r0[threadIdx.x] += r0[threadIdx.x + o];
+      r1[threadIdx.x] += r1[threadIdx.x + o];
+      r2[threadIdx.x] = fmax(r2[threadIdx.x], r2[threadIdx.x + o]);
+      r3[threadIdx.x] = fmax(r3[threadIdx.x], r3[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(res, r0[0] / (double)g.ncell);
+    atomicAdd(res + 1, r1[0] / (double)g.ncell);
+    // non-negative doubles order as their bit patterns
+    atomicMax(reinterpret_cast<unsigned long long*>(res + 2), dbits(r2[0]));
+    atomicMax(reinterpret_cast<unsigned long long*>(res + 3), dbits(r3[0]));
+  }
+}
+
 template <typename T>
 __global__ void k_dt(Geom g, Tables<T> tb, const T* __restrict__ w, const double* __restrict__ wmean,
                      const T* __restrict__ jbuf, dg_mhd_params p, DevScalars* __restrict__ sc) {
@@ -623,6 +757,19 @@ void launch_dt_from_value(const Geom& g, const dg_mhd_params& p, const double* d
 void launch_dt_init(DevScalars* sc, cudaStream_t st) { k_dt_init<<<1, 1, 0, st>>>(sc); }
 
 void launch_dt_scale(DevScalars* sc, double f, cudaStream_t st) { k_dt_scale<<<1, 1, 0, st>>>(sc, f); }
+
+template <typename T>
+void launch_divb_diag(const Geom& g, const Tables<T>& tb, const T* w, const double* wmean, double* scratch,
+                      double* res, double* per_cell, cudaStream_t st) {
+  cudaMemsetAsync(res, 0, 4 * sizeof(double), st);
+  const int64_t total = (int64_t)g.D * g.ncell * g.Qf;
+  k_divb_diag_face<T><<<nblocks(total, 128), 128, 0, st>>>(g, tb, w, scratch);
+  k_divb_diag_cell<T><<<nblocks(g.ncell, 256), 256, 0, st>>>(g, tb, w, wmean, scratch, res, per_cell);
+}
+template void launch_divb_diag<float>(const Geom&, const Tables<float>&, const float*, const double*, double*,
+                                      double*, double*, cudaStream_t);
+template void launch_divb_diag<double>(const Geom&, const Tables<double>&, const double*, const double*, double*,
+                                       double*, double*, cudaStream_t);
 
 template <typename T>
 void launch_axpby(const Geom& g, double a, const T* x, double b, const T* y, T* out, const double* xm,

@@ -24,6 +24,11 @@ void launch_dt_from_value(const Geom& g, const dg_mhd_params& p, const double* d
                           cudaStream_t st);
 void launch_set_glm(DevScalars* sc, double ch, double kappa, cudaStream_t st);
 void launch_dt_init(DevScalars* sc, cudaStream_t st);
+// div B diagnostics of App. C (uniform meshes): res[4] on the device, per_cell
+// [3][stride] or null; scratch: 3 doubles per face point
+template <typename T>
+void launch_divb_diag(const Geom& g, const Tables<T>& tb, const T* w, const double* wmean, double* scratch,
+                      double* res, double* per_cell, cudaStream_t st);
 // sets the device dt to f times the step's dt (and its FP32 copy)
 void launch_dt_scale(DevScalars* sc, double f, cudaStream_t st);
 // out = a x + b y over all state rows; FP32 form: FP64 means from xm, ym into om

@@ -64,6 +64,7 @@ def test_init_rejects_bad_arguments(lib):
     assert lib.dg_mhd_init(ctypes.byref(m), 2, 0, 5.0 / 3.0, None, ctypes.byref(h)) == -2
     assert lib.dg_mhd_rhs(None, None, None, None, None, None) == -1
     assert lib.dg_mhd_step(None, None, None, None, None) == -1
+    assert lib.dg_mhd_divb(None, None, None, None, None, None) == -1
 
 
 def test_octree_mesh_validation_rejects_bad_meshes(lib):

@@ -264,3 +264,42 @@ def test_alfven_2d_degree3_rk4_converges_at_order_4(divb):
     e16, e32 = error(16), error(32)
     order = math.log2(e16 / e32)
     assert 3.5 < order < 4.6, (order, e16, e32)
+
+
+@pytest.mark.parametrize("D,d,divb,ncell,fname", [CASES[0], CASES[1], CASES[2], CASES[4]])
+def test_divb_diagnostics_fp64(D, d, divb, ncell, fname):
+    """dg_mhd_divb against the oracle's App. C diagnostics, per cell and reduced."""
+    S, w0, sol = _setup(D, d, divb, ncell, fname)
+    w = to_device(w0, sol)
+    got = sol.divb_norms(w, None, per_cell=True)
+    ref = S.divb_norms(w0)
+    pc = got["per_cell"][:, : sol.ncell].cpu().numpy()
+    assert rel_err(pc[0], ref["cell"]) < 1e-10
+    assert np.max(np.abs(pc[1] - ref["signed"])) < 1e-10 * max(np.max(np.abs(ref["signed"])), np.max(ref["cell"]))
+    assert rel_err(pc[2], ref["normalized"]) < 1e-10
+    assert abs(got["total"] - ref["total"]) < 1e-10 * ref["total"]
+    assert abs(got["normalized_mean"] - np.mean(ref["normalized"])) < 1e-10 * np.mean(ref["normalized"])
+    assert abs(got["normalized_max"] - np.max(ref["normalized"])) < 1e-10 * np.max(ref["normalized"])
+    assert abs(got["signed_max"] - np.max(np.abs(ref["signed"]))) < 1e-10 * np.max(ref["cell"])
+
+
+@pytest.mark.parametrize("divb", ["powell", "glm"])
+def test_divb_diagnostics_fp32_form_jump(divb):
+    """FP32 form on the cell-aligned jump of B_x (closed form ||div B||_1 = 2)."""
+    from paper_1806_02343_gb300.binding import Solver, DG_PREC_FP32MIX
+    S = Scheme(3, 2, divb, G, (8, 4, 4))
+    one = lambda x: np.ones(x.shape[:-1])
+
+    def fn(x):
+        B = np.stack([np.where(x[..., 0] < 0.5, 1.0, 2.0), 0.3 * one(x), -0.2 * one(x)], -1)
+        u = mhd.conserved(one(x), np.zeros(x.shape[:-1] + (3,)), one(x), B, G)
+        return np.concatenate([u, 0.0 * one(x)[..., None]], -1) if S.V == 9 else u
+
+    w0 = S.project(fn)
+    sol = Solver(3, (8, 4, 4), 2, divb, gamma=G, box_len=S.L, precision=DG_PREC_FP32MIX)
+    w = to_device(w0, sol)
+    wm = means_to_device(w0, sol, S)
+    got = sol.divb_norms(w, wm)
+    assert abs(got["total"] - 2.0) < 1e-5
+    ref = S.divb_norms(w0)
+    assert abs(got["signed_max"] - np.max(np.abs(ref["signed"]))) < 1e-5 * np.max(np.abs(ref["signed"]))
