@@ -286,6 +286,32 @@ def run_ours(args, cfg, rank, world, device):
                              "limiter": "plain TVB detection + positivity" if args.limiter != "off" else "off"}
         del sol, w
         torch.cuda.empty_cache()
+
+    # ------------------------------------------------------------ accuracy of the FP32+learned form
+    # the same start advanced by both forms with the same dt sequence (taken from
+    # the plain FP64 run): L1 difference of the cell means per variable
+    if not args.skip_fp64 and args.l1_steps > 0:
+        s64, w64, _ = make(Bd.DG_PREC_FP64, "tvb" if args.limiter != "off" else "off")
+        s32, w32, wm32 = make(Bd.DG_PREC_FP32MIX, args.limiter)
+        for _ in range(args.l1_steps):
+            dt = s64.dt(w64)
+            s64.step(w64, None, dt)
+            s32.step(w32, wm32, dt)
+        torch.cuda.synchronize()
+        rows = [v * (s64.nrows // 9) for v in range(9)] if divb == "glm" else None
+        if rows is not None:
+            m64 = w64[rows, :ncell]
+            m32 = wm32[:, :ncell]
+            num = (m32 - m64).abs().sum(1)
+            den = m64.abs().sum(1)
+            scale = den.max()
+            l1 = torch.where(den > 1e-6 * scale, num / den, num / scale)
+            res["l1_fp32_learned_vs_fp64_plain"] = {
+                "steps": args.l1_steps, "quantity": "cell means, per variable: sum|a-b| / sum|b| "
+                "(variables with sum|b| < 1e-6 of the largest: / the largest)",
+                "values": [float(x) for x in l1.cpu()], "status": [s64.status(), s32.status()]}
+        del s64, w64, s32, w32, wm32
+        torch.cuda.empty_cache()
     return res
 
 
@@ -343,6 +369,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="turb256", choices=sorted(CONFIGS))
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--l1-steps", type=int, default=2,
+                    help="steps of the FP32+learned vs plain FP64 accuracy comparison (0: off)")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=24)
     ap.add_argument("--limiter", default=None, choices=["mlp", "tvb", "off"],
@@ -405,6 +433,7 @@ def main():
         "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
         "clocks": res["clocks"], "gpu_launches": res["launches"], "kernels": res["kern"],
         "fp64_plain": res.get("fp64_plain"), "status": res["status"], "finite": res["finite"],
+        "l1_fp32_learned_vs_fp64_plain": res.get("l1_fp32_learned_vs_fp64_plain"),
         "dof": res["dof"],
         "kernel_path": ("octree face-list kernels (k_face_list, k_cell_list)" if cfg.get("amr") else
                         "specialised GLM 3D kernels (k_face_glm, k_cell_glm)" if cfg["divb"] == "glm" else
