@@ -34,6 +34,8 @@ CONFIGS = {
                     divb="glm"),
     "fourier64": dict(workload="3D 64^3 periodic, degree 3, GLM, seeded smooth Fourier state", D=3, n=64, d=3,
                       divb="glm"),
+    "blast128": dict(workload="3D 128^3 periodic, degree 2, Powell/LDF, MHD blast (p=100 in r<0.1, 0.1 outside, "
+                              "rho=1, B=(10/sqrt(4 pi),0,0))", D=3, n=128, d=2, divb="powell"),
     "ot_amr": dict(workload="3D Orszag-Tang extrusion on a static octree, levels 5-7 (1,387,520 leaves), "
                             "degree 2, Powell/LDF", D=3, n=None, d=2, divb="powell", amr=True),
 }
@@ -164,6 +166,10 @@ def run_ours(args, cfg, rank, world, device):
             from paper_1806_02343_gb300 import workloads as W
             nodal = W.leaf_nodal(lambda x: W.orszag_tang_3d(x, nvar=8), amr_mesh[0], amr_mesh[1], d + 1, sol.stride,
                                  3, device)
+            npts = d + 1
+        elif "blast" in cfg["name"]:
+            from paper_1806_02343_gb300 import workloads as W
+            nodal = W.gauss_nodal(lambda x: W.blast_3d(x, nvar=8), n, d + 1, 3, sol.stride, device)
             npts = d + 1
         else:
             builder = build_turbulence if "turb" in cfg["name"] else build_fourier
@@ -298,7 +304,12 @@ def run_ours(args, cfg, rank, world, device):
             s64.step(w64, None, dt)
             s32.step(w32, wm32, dt)
         torch.cuda.synchronize()
-        rows = [v * (s64.nrows // 9) for v in range(9)] if divb == "glm" else None
+        nm = (d + 1) * (d + 2) * (d + 3) // 6  # Legendre modes per variable (3D)
+        # the degree-0 rows: Legendre variables' mode 0, then (Powell) the degree-0 LDF rows
+        rows = [v * nm for v in range(9)] if divb == "glm" else [v * nm for v in range(5)] + [5 * nm + j
+                                                                                         for j in range(3)]
+        if cfg.get("amr") or D != 3:
+            rows = None
         if rows is not None:
             m64 = w64[rows, :ncell]
             m32 = wm32[:, :ncell]
@@ -325,6 +336,8 @@ def _oracle_sample(cfg, nsample):
     npts = cfg["d"] + 1
     if cfg.get("amr"):
         w = S.project(lambda x: W.orszag_tang_3d(x, nvar=8), npts=npts)
+    elif "blast" in cfg["name"]:
+        w = S.project(lambda x: W.blast_3d(x, nvar=8), npts=npts)
     elif "turb" in cfg["name"]:
         T = W.Turbulence3D(nvar=9)
         g1, _ = np.polynomial.legendre.leggauss(npts)

@@ -181,8 +181,14 @@ __global__ void k_cell_list(Geom g, Tables<T> tb, AmrDev<T> am, const T* __restr
   const double dt = sc->dt;
   const double kappa = g.glm ? sc->kappa : 0.0;
   const double metric = 2.0 / am.dxc[c];
+  // FP32 form: rows other than the degree-0 ones accumulate and combine in
+  // FP32 (GB300's FP64 rate is 1/64 of FP32); the degree-0 rows keep FP64
+  const T tm = (T)metric, tdt = (T)dt, tca = (T)ca, tcb = (T)cb;
   for (int r = lane; r < g.nrows; r += 32) {
+    const int m = mix ? mindex_a(g, r) : -1;
+    const bool lowp = sizeof(T) == 4 && m < 0;
     double acc = 0.0;
+    T acct = T(0);
     const bool ldf = g.ldf0 >= 0 && r >= g.ldf0 && r < g.ldf0 + g.ndiv;
     if (!ldf) {
       const int v = (g.bz2d >= 0 && r >= g.bz2d) ? 7 : r / g.n;
@@ -194,7 +200,7 @@ __global__ void k_cell_list(Geom g, Tables<T> tb, AmrDev<T> am, const T* __restr
           const T* Dp = tb.dPv + ((size_t)a * g.n + l) * g.Qv;
           for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
         }
-      acc += (double)s;
+      if (lowp) acct += s; else acc += (double)s;
       for (int e = 0; e < ne; ++e) {
         const int ent = am.centry[e0 + e];
         const SideTab<T> t = side_tab(g, tb, am, am.fmeta[ent >> 1], ent & 1);
@@ -205,7 +211,7 @@ __global__ void k_cell_list(Geom g, Tables<T> tb, AmrDev<T> am, const T* __restr
           if (!g.glm) term += PJ[e * g.Qf + p] * qv[v];
           sf += term * Pp[p];
         }
-        acc -= (double)sf;
+        if (lowp) acct -= sf; else acc -= (double)sf;
       }
     } else {
       const int j = r - g.ldf0;
@@ -216,7 +222,7 @@ __global__ void k_cell_list(Geom g, Tables<T> tb, AmrDev<T> am, const T* __restr
           const T* Dp = tb.dLv + (((size_t)a * g.ndiv + j) * g.DB + cc) * g.Qv;
           for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
         }
-      acc += (double)s;
+      if (lowp) acct += s; else acc += (double)s;
       for (int e = 0; e < ne; ++e) {
         const int ent = am.centry[e0 + e];
         const SideTab<T> t = side_tab(g, tb, am, am.fmeta[ent >> 1], ent & 1);
@@ -226,12 +232,18 @@ __global__ void k_cell_list(Geom g, Tables<T> tb, AmrDev<T> am, const T* __restr
           for (int p = 0; p < g.Qf; ++p)
             sf += (FS[(e * g.Qf + p) * g.V + 5 + cc] + PJ[e * g.Qf + p] * qv[5 + cc]) * Lp[p];
         }
-        acc -= (double)sf;
+        if (lowp) acct -= sf; else acc -= (double)sf;
       }
+    }
+    if (lowp) {
+      T rt = tm * tb.minv[r] * acct;
+      if (g.glm && r >= 8 * g.n) rt -= (T)kappa * wc[r];
+      if (!combine) out[r * S + c] = rt;
+      else out[r * S + c] = tca * w0[r * S + c] + tcb * (wc[r] + tdt * rt);
+      continue;
     }
     double rhs = metric * (double)tb.minv[r] * acc;
     if (g.glm && r >= 8 * g.n) rhs -= kappa * (double)wc[r];
-    const int m = mix ? mindex_a(g, r) : -1;
     if (!combine) {
       out[r * S + c] = (T)rhs;
       if (m >= 0) outmean[m * S + c] = rhs;

@@ -197,8 +197,14 @@ __global__ void k_cell(Geom g, Tables<T> tb, const T* __restrict__ w, const T* _
   const double dt = sc->dt;
   const double kappa = g.glm ? sc->kappa : 0.0;
   const double metric = 2.0 / g.dx;
+  // FP32 form: rows other than the degree-0 ones accumulate and combine in
+  // FP32 (GB300's FP64 rate is 1/64 of FP32); the degree-0 rows keep FP64
+  const T tm = (T)metric, tdt = (T)dt, tca = (T)ca, tcb = (T)cb;
   for (int r = lane; r < g.nrows; r += 32) {
+    const int m = mix ? mean_index(g, r) : -1;
+    const bool lowp = sizeof(T) == 4 && m < 0;
     double acc = 0.0;  // double accumulation: exact conservation of the mean rows
+    T acct = T(0);
     if (!is_ldf_row(g, r)) {
       const int v = legendre_var(g, r);
       const int l = (g.bz2d >= 0 && r >= g.bz2d) ? r - g.bz2d : r % g.n;
@@ -210,7 +216,7 @@ __global__ void k_cell(Geom g, Tables<T> tb, const T* __restrict__ w, const T* _
           for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
         }
       }
-      acc += (double)s;
+      if (lowp) acct += s; else acc += (double)s;
       for (int f = 0; f < 2 * g.D; ++f) {
         const T* Pp = tb.Pf + ((size_t)f * g.n + l) * g.Qf;
         T sf = T(0);
@@ -219,7 +225,7 @@ __global__ void k_cell(Geom g, Tables<T> tb, const T* __restrict__ w, const T* _
           if (!g.glm) term += PJ[f * g.Qf + p] * qv[v];
           sf += term * Pp[p];
         }
-        acc -= (double)sf;
+        if (lowp) acct -= sf; else acc -= (double)sf;
       }
     } else {
       const int j = r - g.ldf0;
@@ -230,7 +236,7 @@ __global__ void k_cell(Geom g, Tables<T> tb, const T* __restrict__ w, const T* _
           const T* Dp = tb.dLv + (((size_t)a * g.ndiv + j) * g.DB + cc) * g.Qv;
           for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
         }
-      acc += (double)s;
+      if (lowp) acct += s; else acc += (double)s;
       for (int f = 0; f < 2 * g.D; ++f) {
         T sf = T(0);
         for (int cc = 0; cc < g.DB; ++cc) {
@@ -238,12 +244,18 @@ __global__ void k_cell(Geom g, Tables<T> tb, const T* __restrict__ w, const T* _
           for (int p = 0; p < g.Qf; ++p)
             sf += (FS[(f * g.Qf + p) * g.V + 5 + cc] + PJ[f * g.Qf + p] * qv[5 + cc]) * Lp[p];
         }
-        acc -= (double)sf;
+        if (lowp) acct -= sf; else acc -= (double)sf;
       }
+    }
+    if (lowp) {
+      T rt = tm * tb.minv[r] * acct;
+      if (g.glm && r >= 8 * g.n) rt -= (T)kappa * wc[r];
+      if (!combine) out[r * S + c] = rt;
+      else out[r * S + c] = tca * w0[r * S + c] + tcb * (wc[r] + tdt * rt);
+      continue;
     }
     double rhs = metric * (double)tb.minv[r] * acc;
     if (g.glm && r >= 8 * g.n) rhs -= kappa * (double)wc[r];
-    const int m = mix ? mean_index(g, r) : -1;
     if (!combine) {
       out[r * S + c] = (T)rhs;
       if (m >= 0) outmean[m * S + c] = rhs;

@@ -612,14 +612,12 @@ __global__ void __launch_bounds__(256) k_mlp_staged(Geom g, MlpTabs mt, const fl
       const int sd = t >> 3, k = t & 7;
       xe[t] = w[(int64_t)mrow(g, k) * S + nbc(g, c0 + (sd ? 127 : 0), 0, sd ? 1 : -1)];
     }
-    // bounded wait for the tile's bytes: one warp polls the barrier, the
-    // others wait at the block barrier (no issue slots spent polling)
-    bool ok = true;
-    if (warp == 0) {
-      const long long t0 = clock64();
-      while (!(ok = mbar_try_wait(bar + b, (par >> b) & 1u)))
-        if (clock64() - t0 > kWaitCycles) break;
-    }
+    // bounded wait for the tile's bytes (every thread polls: measured faster
+    // than one polling warp and a block barrier)
+    bool ok = false;
+    const long long t0 = clock64();
+    while (!(ok = mbar_try_wait(bar + b, (par >> b) & 1u)))
+      if (clock64() - t0 > kWaitCycles) break;
     if (!__syncthreads_and(ok)) {
       if (t == 0) atomicOr(&sc->status, 8);
       return;
