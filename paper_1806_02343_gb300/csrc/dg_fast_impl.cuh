@@ -128,16 +128,15 @@ __device__ __forceinline__ int64_t nbr(const FastGeom& g, Coord k, int a, int di
 }
 
 // ------------------------------------------------------------------ faces
-template <typename T, int DEG, int A>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_face_glm(const FaceTabs<T, DEG> tbp, const FastGeom g,
-                                                 const T* __restrict__ w, T* __restrict__ F,
-                                                 const DevScalars* __restrict__ sc, T eps) {
+// The faces normal to axis A whose right cells are the block's 32 cells:
+// stage the left cells' (and, with own, this block's) coefficients, traces,
+// HLLD. WR keeps this block's coefficients between calls.
+template <typename T, int DEG, int A, bool OWN>
+__device__ __forceinline__ void face_axis(const FaceTabs<T, DEG>& tbp, const FastGeom& g, const T* __restrict__ w,
+                                          T* __restrict__ F, const DevScalars* __restrict__ sc, T eps, T* WL, T* WR,
+                                          T* TR) {
   constexpr int N = FastDims<DEG>::N, QF = FastDims<DEG>::QF, NR = 9 * N;
   const FaceTabs<T, DEG>& tb = face_tabs<T, DEG, A>(tbp);
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* WL = reinterpret_cast<T*>(smraw);       // [NR][TC]
-  T* WR = WL + NR * TC;                      // [NR][TC]
-  T* TR = WR + NR * TC;                      // [2][QF][9][TC]
   const int t = threadIdx.x;
   const int f = t & (TC - 1);
   const int v = t >> 5;  // warp-uniform
@@ -157,14 +156,14 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_fa
 #pragma unroll
     for (int i = 0; i < PER; ++i, pa += S9, pb += S9) {
       const int r = v + 9 * i;
-      a[i] = (live && r < NR) ? *pa : T(1);
+      if (OWN) a[i] = (live && r < NR) ? *pa : T(1);
       b[i] = (live && r < NR) ? *pb : T(1);
     }
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
       const int r = v + 9 * i;
       if (r < NR) {
-        WR[r * TC + f] = a[i];
+        if (OWN) WR[r * TC + f] = a[i];
         WL[r * TC + f] = b[i];
       }
     }
@@ -211,6 +210,37 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_fa
       for (int k = 0; k < 9; ++k) F[((int64_t)(A * QF + p) * 9) * S + c + (int64_t)k * S] = Fo[k];
     }
   }
+}
+
+template <typename T, int DEG, int A>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_face_glm(const FaceTabs<T, DEG> tbp, const FastGeom g,
+                                                 const T* __restrict__ w, T* __restrict__ F,
+                                                 const DevScalars* __restrict__ sc, T eps) {
+  constexpr int NR = 9 * FastDims<DEG>::N;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* WL = reinterpret_cast<T*>(smraw);       // [NR][TC]
+  T* WR = WL + NR * TC;                      // [NR][TC]
+  T* TR = WR + NR * TC;                      // [2][QF][9][TC]
+  face_axis<T, DEG, A, true>(tbp, g, w, F, sc, eps, WL, WR, TR);
+}
+
+// All three axes in one pass: the block's own coefficients are read once and
+// kept in shared memory for the x, y and z faces (one state read fewer per
+// face than three separate passes).
+template <typename T, int DEG>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_face_glm3(
+    const FaceTabs<T, DEG> tb0, const FaceTabs<T, DEG> tb1, const FaceTabs<T, DEG> tb2, const FastGeom g,
+    const T* __restrict__ w, T* __restrict__ F, const DevScalars* __restrict__ sc, T eps) {
+  constexpr int NR = 9 * FastDims<DEG>::N;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* WL = reinterpret_cast<T*>(smraw);
+  T* WR = WL + NR * TC;
+  T* TR = WR + NR * TC;
+  face_axis<T, DEG, 0, true>(tb0, g, w, F, sc, eps, WL, WR, TR);
+  __syncthreads();
+  face_axis<T, DEG, 1, false>(tb1, g, w, F, sc, eps, WL, WR, TR);
+  __syncthreads();
+  face_axis<T, DEG, 2, false>(tb2, g, w, F, sc, eps, WL, WR, TR);
 }
 
 // ------------------------------------------------------------------ cells
@@ -471,9 +501,12 @@ void launch_face_glm(const FastAll<T, DEG>& tabs, const FastGeom& g, const T* w,
     set_smem_attr<T>((const void*)k_face_glm<T, DEG, 2>, sm);
     attr = true;
   }
-  k_face_glm<T, DEG, 0><<<nb, NT, sm, st>>>(tabs.face[0], g, w, F, sc, (T)eps);
-  k_face_glm<T, DEG, 1><<<nb, NT, sm, st>>>(tabs.face[1], g, w, F, sc, (T)eps);
-  k_face_glm<T, DEG, 2><<<nb, NT, sm, st>>>(tabs.face[2], g, w, F, sc, (T)eps);
+  static bool attr3 = false;
+  if (!attr3) {
+    set_smem_attr<T>((const void*)k_face_glm3<T, DEG>, sm);
+    attr3 = true;
+  }
+  k_face_glm3<T, DEG><<<nb, NT, sm, st>>>(tabs.face[0], tabs.face[1], tabs.face[2], g, w, F, sc, (T)eps);
 }
 
 template <typename T, int DEG>
