@@ -90,9 +90,10 @@ __device__ __forceinline__ SideTab<T> side_tab(const Geom& g, const Tables<T>& t
   return t;
 }
 
-template <typename T>
-__global__ void k_face_list(Geom g, Tables<T> tb, AmrDev<T> am, const T* __restrict__ w, T* __restrict__ fbuf,
+template <typename T, int DEG, int GLMF>
+__global__ void k_face_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __restrict__ w, T* __restrict__ fbuf,
                             const DevScalars* __restrict__ sc, T eps) {
+  const Geom g = pin_geom<DEG, GLMF>(gin);
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= am.nface * g.Qf) return;
   const int64_t f = tid / g.Qf;
@@ -111,11 +112,12 @@ __global__ void k_face_list(Geom g, Tables<T> tb, AmrDev<T> am, const T* __restr
   if (!g.glm) o[8] = bnF;
 }
 
-template <typename T>
-__global__ void k_cell_list(Geom g, Tables<T> tb, AmrDev<T> am, const T* __restrict__ w,
+template <typename T, int DEG, int GLMF>
+__global__ void k_cell_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __restrict__ w,
                             const T* __restrict__ fbuf, T* out, const T* w0, double ca, double cb, int combine,
                             const DevScalars* __restrict__ sc, const double* __restrict__ wmean, const double* w0mean,
                             double* outmean) {
+  const Geom g = pin_geom<DEG, GLMF>(gin);
   // out / outmean may alias w0 / w0mean: each element is read, then written, by one lane.
   extern __shared__ unsigned char smraw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -540,16 +542,21 @@ void launch_amr_operator(const Ctx& c, const Tables<T>& tb, const T* w, T* fbuf,
   const Geom& g = c.g;
   const AmrDev<T> am = amr_dev<T>(c);
   const int64_t np = am.nface * g.Qf;
-  k_face_list<T><<<(unsigned)((np + 127) / 128), 128, 0, st>>>(g, tb, am, w, fbuf, sc, (T)eps);
   const int per_warp = g.nrows + g.D * g.V * g.Qv + am.maxent * g.Qf * g.V + am.maxent * g.Qf;
   const size_t sm = (size_t)per_warp * WPB * sizeof(T);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_cell_list<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
-  k_cell_list<T><<<(unsigned)((g.ncell + WPB - 1) / WPB), 32 * WPB, sm, st>>>(g, tb, am, w, fbuf, out, w0, ca, cb,
-                                                                              combine, sc, wmean, w0mean, outmean);
+  auto run = [&](auto face_k, auto cell_k) {
+    face_k<<<(unsigned)((np + 127) / 128), 128, 0, st>>>(g, tb, am, w, fbuf, sc, (T)eps);
+    cudaFuncSetAttribute(cell_k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cell_k<<<(unsigned)((g.ncell + WPB - 1) / WPB), 32 * WPB, sm, st>>>(g, tb, am, w, fbuf, out, w0, ca, cb, combine,
+                                                                       sc, wmean, w0mean, outmean);
+  };
+  // compile-time sizes for the 3D degree-1 and degree-2 schemes
+  if (!pinned_sizes_ok(g)) run(k_face_list<T, -1, 0>, k_cell_list<T, -1, 0>);
+  else if (g.D == 3 && g.d == 2 && !g.glm) run(k_face_list<T, 2, 0>, k_cell_list<T, 2, 0>);
+  else if (g.D == 3 && g.d == 2 && g.glm) run(k_face_list<T, 2, 1>, k_cell_list<T, 2, 1>);
+  else if (g.D == 3 && g.d == 1 && !g.glm) run(k_face_list<T, 1, 0>, k_cell_list<T, 1, 0>);
+  else if (g.D == 3 && g.d == 1 && g.glm) run(k_face_list<T, 1, 1>, k_cell_list<T, 1, 1>);
+  else run(k_face_list<T, -1, 0>, k_cell_list<T, -1, 0>);
 }
 
 template <typename T>

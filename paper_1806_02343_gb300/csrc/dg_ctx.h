@@ -49,6 +49,43 @@ struct Geom {
   double dx, gamma;
 };
 
+// Sizes fixed at compile time (3D, degree DEG >= 0, GLM or Powell): the
+// kernel's copy of the Geom gets constant fields, so every loop over modes,
+// points and rows has a constant trip count and unrolls. DEG < 0: the sizes
+// stay those of the run-time Geom.
+template <int DEG, int GLMF>
+__device__ __forceinline__ Geom pin_geom(const Geom& gin) {
+  Geom g = gin;
+  if constexpr (DEG >= 0) {
+    constexpr int N = (DEG + 1) * (DEG + 2) * (DEG + 3) / 6;
+    constexpr int NDIV = DEG == 0 ? 3 : DEG == 1 ? 11 : DEG == 2 ? 26 : 50;  // Table A1, D = 3
+    g.D = 3;
+    g.d = DEG;
+    g.n = N;
+    g.DB = 3;
+    g.nq1 = DEG + 1;
+    g.Qv = (DEG + 1) * (DEG + 1) * (DEG + 1);
+    g.Qf = (DEG + 1) * (DEG + 1);
+    g.glm = GLMF;
+    g.V = GLMF ? 9 : 8;
+    g.ndiv = GLMF ? 0 : NDIV;
+    g.ldf0 = GLMF ? -1 : 5 * N;
+    g.nrows = GLMF ? 9 * N : 5 * N + NDIV;
+    g.bz2d = -1;
+  }
+  return g;
+}
+
+// the run-time Geom agrees with pin_geom<g.d, g.glm> (3D, degree 1 or 2)
+inline bool pinned_sizes_ok(const Geom& g) {
+  if (g.D != 3 || (g.d != 1 && g.d != 2)) return false;
+  const int nm = g.d == 1 ? 4 : 10, nd = g.d == 1 ? 11 : 26;
+  return g.n == nm && g.DB == 3 && g.bz2d < 0 && g.nq1 == g.d + 1 && g.Qv == (g.d + 1) * (g.d + 1) * (g.d + 1) &&
+         g.Qf == (g.d + 1) * (g.d + 1) && g.V == (g.glm ? 9 : 8) &&
+         (g.glm ? (g.ndiv == 0 && g.nrows == 9 * nm && g.ldf0 == -1)
+                : (g.ndiv == nd && g.nrows == 5 * nm + nd && g.ldf0 == 5 * nm));
+}
+
 // Scalars kept on the device so that a step never waits for the host.
 struct DevScalars {
   double dt;       // current timestep

@@ -100,9 +100,10 @@ __device__ __forceinline__ void eval_state(const Geom& g, const T* __restrict__ 
 }
 
 // ---------------------------------------------------------------- face fluxes
-template <typename T>
-__global__ void k_face(Geom g, Tables<T> tb, const T* __restrict__ w, T* __restrict__ fbuf,
+template <typename T, int DEG, int GLMF>
+__global__ void k_face(Geom gin, Tables<T> tb, const T* __restrict__ w, T* __restrict__ fbuf,
                        const DevScalars* __restrict__ sc, T eps) {
+  const Geom g = pin_geom<DEG, GLMF>(gin);
   const int64_t total = (int64_t)g.D * g.ncell * g.Qf;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= total) return;
@@ -127,10 +128,11 @@ __global__ void k_face(Geom g, Tables<T> tb, const T* __restrict__ w, T* __restr
 }
 
 // ---------------------------------------------------------------- cell update
-template <typename T>
-__global__ void k_cell(Geom g, Tables<T> tb, const T* __restrict__ w, const T* __restrict__ fbuf, T* out,
+template <typename T, int DEG, int GLMF>
+__global__ void k_cell(Geom gin, Tables<T> tb, const T* __restrict__ w, const T* __restrict__ fbuf, T* out,
                        const T* w0, double ca, double cb, int combine, const DevScalars* __restrict__ sc,
                        const double* __restrict__ wmean, const double* w0mean, double* outmean) {
+  const Geom g = pin_geom<DEG, GLMF>(gin);
   // out may alias w0 (in-place final stage): each element is read and then
   // written by the same thread.
   extern __shared__ unsigned char smem_raw[];
@@ -708,7 +710,11 @@ template <typename T>
 void launch_face(const Geom& g, const Tables<T>& tb, const T* w, T* fbuf, const DevScalars* sc, double eps,
                  cudaStream_t st) {
   const int64_t total = (int64_t)g.D * g.ncell * g.Qf;
-  k_face<T><<<nblocks(total, 128), 128, 0, st>>>(g, tb, w, fbuf, sc, (T)eps);
+  // compile-time sizes for the 3D degree-1 and degree-2 schemes
+  auto run = [&](auto k) { k<<<nblocks(total, 128), 128, 0, st>>>(g, tb, w, fbuf, sc, (T)eps); };
+  if (!pinned_sizes_ok(g)) run(k_face<T, -1, 0>);
+  else if (g.d == 2) g.glm ? run(k_face<T, 2, 1>) : run(k_face<T, 2, 0>);
+  else g.glm ? run(k_face<T, 1, 1>) : run(k_face<T, 1, 0>);
 }
 
 template <typename T>
@@ -722,13 +728,15 @@ void launch_cell(const Geom& g, const Tables<T>& tb, const T* w, const T* fbuf, 
                  double ca, double cb, int combine, const DevScalars* sc, const double* wmean,
                  const double* w0mean, double* outmean, cudaStream_t st) {
   const size_t sm = cell_smem<T>(g);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_cell<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
-  k_cell<T><<<nblocks(g.ncell, WARPS_PER_BLOCK), 32 * WARPS_PER_BLOCK, sm, st>>>(
-      g, tb, w, fbuf, out, w0, ca, cb, combine, sc, wmean, w0mean, outmean);
+  auto run = [&](auto k) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    k<<<nblocks(g.ncell, WARPS_PER_BLOCK), 32 * WARPS_PER_BLOCK, sm, st>>>(g, tb, w, fbuf, out, w0, ca, cb, combine,
+                                                                        sc, wmean, w0mean, outmean);
+  };
+  // compile-time sizes for the 3D degree-1 and degree-2 schemes
+  if (!pinned_sizes_ok(g)) run(k_cell<T, -1, 0>);
+  else if (g.d == 2) g.glm ? run(k_cell<T, 2, 1>) : run(k_cell<T, 2, 0>);
+  else g.glm ? run(k_cell<T, 1, 1>) : run(k_cell<T, 1, 0>);
 }
 
 template <typename T>
