@@ -39,7 +39,17 @@ int upload(T** dst, const std::vector<double>& src) {
 
 struct HostTables {
   std::vector<double> Pv, dPv, Pf, Lv, dLv, Lf, L0, wv, wf, minv, Pp, Lp;
+  std::vector<double> dPv4, dLv4, Pf4, Lf4;  // point index padded to a multiple of 4
 };
+
+// rows of length len copied into rows of length lenp (zero padding)
+std::vector<double> pad_rows(const std::vector<double>& src, int len, int lenp) {
+  const size_t rows = src.size() / (size_t)len;
+  std::vector<double> out(rows * (size_t)lenp, 0.0);
+  for (size_t r = 0; r < rows; ++r)
+    for (int k = 0; k < len; ++k) out[r * lenp + k] = src[r * len + k];
+  return out;
+}
 
 // reference coordinates of volume point q (tensor rule, last axis fastest)
 void vol_point(int D, const std::vector<double>& x1, int q, double* xi) {
@@ -135,6 +145,10 @@ void build_host_tables(const Basis& B, const Geom& g, HostTables& h) {
     for (int j = 0; j < nd; ++j)
       for (int c = 0; c < DB; ++c) h.Lp[((size_t)j * DB + c) * npos + pt] = B.eval(B.ldf[j][c], xi);
   }
+  h.dPv4 = pad_rows(h.dPv, Qv, pad4(Qv));
+  h.dLv4 = pad_rows(h.dLv, Qv, pad4(Qv));
+  h.Pf4 = pad_rows(h.Pf, Qf, pad4(Qf));
+  h.Lf4 = pad_rows(h.Lf, Qf, pad4(Qf));
   h.minv.assign(g.nrows, 0.0);
   for (int r = 0; r < g.nrows; ++r) {
     double m;
@@ -160,12 +174,17 @@ int upload_tables(const HostTables& h, Tables<T>& t) {
   if ((e = upload(&t.minv, h.minv))) return e;
   if ((e = upload(&t.Pp, h.Pp))) return e;
   if ((e = upload(&t.Lp, h.Lp))) return e;
+  if ((e = upload(&t.dPv4, h.dPv4))) return e;
+  if ((e = upload(&t.dLv4, h.dLv4))) return e;
+  if ((e = upload(&t.Pf4, h.Pf4))) return e;
+  if ((e = upload(&t.Lf4, h.Lf4))) return e;
   return DG_OK;
 }
 
 template <typename T>
 void free_tables(Tables<T>& t) {
-  T* ptrs[] = {t.Pv, t.dPv, t.Pf, t.Lv, t.dLv, t.Lf, t.L0, t.wv, t.wf, t.minv, t.Pp, t.Lp};
+  T* ptrs[] = {t.Pv, t.dPv, t.Pf, t.Lv, t.dLv, t.Lf, t.L0, t.wv, t.wf, t.minv, t.Pp, t.Lp,
+               t.dPv4, t.dLv4, t.Pf4, t.Lf4};
   for (T* p : ptrs)
     if (p) cudaFree(p);
   t = Tables<T>();

@@ -33,7 +33,14 @@ struct Tables {
   T *Lv = nullptr, *dLv = nullptr, *Lf = nullptr, *L0 = nullptr;
   T *wv = nullptr, *wf = nullptr, *minv = nullptr;
   T *Pp = nullptr, *Lp = nullptr;
+  // the same tables with the point index padded to a multiple of 4 (zeros),
+  // for 16-byte vector loads: dPv4[(a*n+l)*QVP+q], dLv4[((a*nd+j)*DB+c)*QVP+q],
+  // Pf4[(f*n+l)*QFP+p], Lf4[((f*nd+j)*DB+c)*QFP+p]; null where not built
+  T *dPv4 = nullptr, *dLv4 = nullptr, *Pf4 = nullptr, *Lf4 = nullptr;
 };
+
+// point counts padded to a multiple of 4
+__host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
 
 // Kernel-facing description of the discretisation (passed by value).
 struct Geom {

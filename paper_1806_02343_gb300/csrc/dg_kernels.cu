@@ -128,22 +128,66 @@ __global__ void k_face(Geom gin, Tables<T> tb, const T* __restrict__ w, T* __res
 }
 
 // ---------------------------------------------------------------- cell update
-template <typename T, int DEG, int GLMF>
+// LEN-point dot product of two 16-byte aligned arrays (LEN a multiple of 4)
+template <typename T, int LEN>
+__device__ __forceinline__ T dotp(const T* a, const T* b) {
+  T s = T(0);
+  if constexpr (sizeof(T) == 4) {
+    const float4* A = reinterpret_cast<const float4*>(a);
+    const float4* B = reinterpret_cast<const float4*>(b);
+#pragma unroll
+    for (int k = 0; k < LEN / 4; ++k) {
+      const float4 x = A[k], y = B[k];
+      s = fmaf(x.x, y.x, s);
+      s = fmaf(x.y, y.y, s);
+      s = fmaf(x.z, y.z, s);
+      s = fmaf(x.w, y.w, s);
+    }
+  } else {
+    const double2* A = reinterpret_cast<const double2*>(a);
+    const double2* B = reinterpret_cast<const double2*>(b);
+#pragma unroll
+    for (int k = 0; k < LEN / 2; ++k) {
+      const double2 x = A[k], y = B[k];
+      s = fma(x.x, y.x, s);
+      s = fma(x.y, y.y, s);
+    }
+  }
+  return s;
+}
+
+// Per-warp shared memory of k_cell (elements): state rows, weighted volume
+// fluxes G, face terms FS and Powell jump terms PJ. VEC: point indices padded
+// to a multiple of 4 and every region 16-byte aligned (vector loads).
+__host__ __device__ inline int cell_warp_elems(const Geom& g, bool vec) {
+  const int qv = vec ? pad4(g.Qv) : g.Qv, qf = vec ? pad4(g.Qf) : g.Qf;
+  const int nr = vec ? pad4(g.nrows) : g.nrows;
+  const int e = nr + g.D * g.V * qv + 2 * g.D * qf * g.V + 2 * g.D * qf;
+  return vec ? pad4(e) : e;
+}
+
+// VEC (3D, sizes fixed at compile time, padded tables present): the row
+// contractions run as 16-byte vector loads of the fluxes and the tables
+// (four multiply-adds per pair of loads instead of one).
+template <typename T, int DEG, int GLMF, bool VEC>
 __global__ void k_cell(Geom gin, Tables<T> tb, const T* __restrict__ w, const T* __restrict__ fbuf, T* out,
                        const T* w0, double ca, double cb, int combine, const DevScalars* __restrict__ sc,
                        const double* __restrict__ wmean, const double* w0mean, double* outmean) {
   const Geom g = pin_geom<DEG, GLMF>(gin);
   // out may alias w0 (in-place final stage): each element is read and then
   // written by the same thread.
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t c = (int64_t)blockIdx.x * WARPS_PER_BLOCK + warp;
-  const int per_warp = g.nrows + g.D * g.V * g.Qv + 2 * g.D * g.Qf * g.V + 2 * g.D * g.Qf;
+  const int QVP = VEC ? pad4(g.Qv) : g.Qv, QFP = VEC ? pad4(g.Qf) : g.Qf;
+  const int per_warp = cell_warp_elems(g, VEC);
   T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)warp * per_warp;
   T* wc = sm;
-  T* G = wc + g.nrows;
-  T* FS = G + g.D * g.V * g.Qv;
-  T* PJ = FS + 2 * g.D * g.Qf * g.V;
+  T* G = wc + (VEC ? pad4(g.nrows) : g.nrows);
+  T* FS = G + g.D * g.V * QVP;
+  T* PJ = FS + 2 * g.D * QFP * g.V;
+  // face term of (face f, point p, variable v)
+  auto fsi = [&](int f, int p, int v) { return VEC ? (f * g.V + v) * QFP + p : (f * g.Qf + p) * g.V + v; };
   if (c >= g.ncell) return;
   const int64_t S = g.stride;
   const bool mix = (wmean != nullptr);
@@ -162,7 +206,17 @@ __global__ void k_cell(Geom gin, Tables<T> tb, const T* __restrict__ w, const T*
     for (int a = 0; a < g.D; ++a) {
       T f[MAXV];
       flux_dir(u, a, gamma, g.glm != 0, ch2, f);
-      for (int v = 0; v < g.V; ++v) G[(a * g.V + v) * g.Qv + q] = wq * f[v];
+      for (int v = 0; v < g.V; ++v) G[(a * g.V + v) * QVP + q] = wq * f[v];
+    }
+  }
+  if (VEC) {
+    // zero padding of the point index (the padded tables are zero there too)
+    for (int i = lane; i < g.D * g.V * (QVP - g.Qv); i += 32)
+      G[(i / (QVP - g.Qv)) * QVP + g.Qv + i % (QVP - g.Qv)] = T(0);
+    for (int i = lane; i < 2 * g.D * (g.V + 1) * (QFP - g.Qf); i += 32) {
+      const int row = i / (QFP - g.Qf), pp = g.Qf + i % (QFP - g.Qf);
+      if (row < 2 * g.D * g.V) FS[row * QFP + pp] = T(0);
+      else PJ[(row - 2 * g.D * g.V) * QFP + pp] = T(0);
     }
   }
   // faces: outward-normal flux times weights, Powell jump terms
@@ -173,13 +227,13 @@ __global__ void k_cell(Geom gin, Tables<T> tb, const T* __restrict__ w, const T*
     const T* F = fbuf + (((int64_t)a * g.ncell + fc) * g.Qf + p) * 9;
     const T sgn = side ? T(1) : T(-1);
     const T wp = tb.wf[p];
-    for (int v = 0; v < g.V; ++v) FS[(f * g.Qf + p) * g.V + v] = sgn * wp * F[v];
+    for (int v = 0; v < g.V; ++v) FS[fsi(f, p, v)] = sgn * wp * F[v];
     if (!g.glm) {
       // own normal field B_a at this face point (LDF rows)
       T ba = T(0);
       for (int j = 0; j < g.ndiv; ++j)
         ba += wc[g.ldf0 + j] * tb.Lf[(((size_t)f * g.ndiv + j) * g.DB + a) * g.Qf + p];
-      PJ[f * g.Qf + p] = wp * sgn * (F[8] - ba);
+      PJ[f * QFP + p] = wp * sgn * (F[8] - ba);
     }
   }
   __syncwarp();
@@ -213,19 +267,30 @@ __global__ void k_cell(Geom gin, Tables<T> tb, const T* __restrict__ w, const T*
       T s = T(0);
       if (l != 0) {
         for (int a = 0; a < g.D; ++a) {
-          const T* Gp = G + (a * g.V + v) * g.Qv;
-          const T* Dp = tb.dPv + ((size_t)a * g.n + l) * g.Qv;
-          for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
+          const T* Gp = G + (a * g.V + v) * QVP;
+          if constexpr (VEC) {
+            s += dotp<T, pad4((DEG + 1) * (DEG + 1) * (DEG + 1))>(Gp, tb.dPv4 + ((size_t)a * g.n + l) * QVP);
+          } else {
+            const T* Dp = tb.dPv + ((size_t)a * g.n + l) * g.Qv;
+            for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
+          }
         }
       }
       if (lowp) acct += s; else acc += (double)s;
       for (int f = 0; f < 2 * g.D; ++f) {
-        const T* Pp = tb.Pf + ((size_t)f * g.n + l) * g.Qf;
         T sf = T(0);
-        for (int p = 0; p < g.Qf; ++p) {
-          T term = FS[(f * g.Qf + p) * g.V + v];
-          if (!g.glm) term += PJ[f * g.Qf + p] * qv[v];
-          sf += term * Pp[p];
+        if constexpr (VEC) {
+          constexpr int QF4 = pad4((DEG + 1) * (DEG + 1));
+          const T* Pp = tb.Pf4 + ((size_t)f * g.n + l) * QFP;
+          sf = dotp<T, QF4>(FS + (f * g.V + v) * QFP, Pp);
+          if (!g.glm) sf += qv[v] * dotp<T, QF4>(PJ + f * QFP, Pp);
+        } else {
+          const T* Pp = tb.Pf + ((size_t)f * g.n + l) * g.Qf;
+          for (int p = 0; p < g.Qf; ++p) {
+            T term = FS[fsi(f, p, v)];
+            if (!g.glm) term += PJ[f * QFP + p] * qv[v];
+            sf += term * Pp[p];
+          }
         }
         if (lowp) acct -= sf; else acc -= (double)sf;
       }
@@ -234,17 +299,28 @@ __global__ void k_cell(Geom gin, Tables<T> tb, const T* __restrict__ w, const T*
       T s = T(0);
       for (int a = 0; a < g.D; ++a)
         for (int cc = 0; cc < g.DB; ++cc) {
-          const T* Gp = G + (a * g.V + 5 + cc) * g.Qv;
-          const T* Dp = tb.dLv + (((size_t)a * g.ndiv + j) * g.DB + cc) * g.Qv;
-          for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
+          const T* Gp = G + (a * g.V + 5 + cc) * QVP;
+          if constexpr (VEC) {
+            s += dotp<T, pad4((DEG + 1) * (DEG + 1) * (DEG + 1))>(
+                Gp, tb.dLv4 + (((size_t)a * g.ndiv + j) * g.DB + cc) * QVP);
+          } else {
+            const T* Dp = tb.dLv + (((size_t)a * g.ndiv + j) * g.DB + cc) * g.Qv;
+            for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
+          }
         }
       if (lowp) acct += s; else acc += (double)s;
       for (int f = 0; f < 2 * g.D; ++f) {
         T sf = T(0);
         for (int cc = 0; cc < g.DB; ++cc) {
-          const T* Lp = tb.Lf + (((size_t)f * g.ndiv + j) * g.DB + cc) * g.Qf;
-          for (int p = 0; p < g.Qf; ++p)
-            sf += (FS[(f * g.Qf + p) * g.V + 5 + cc] + PJ[f * g.Qf + p] * qv[5 + cc]) * Lp[p];
+          if constexpr (VEC) {
+            constexpr int QF4 = pad4((DEG + 1) * (DEG + 1));
+            const T* Lp = tb.Lf4 + (((size_t)f * g.ndiv + j) * g.DB + cc) * QFP;
+            sf += dotp<T, QF4>(FS + (f * g.V + 5 + cc) * QFP, Lp) + qv[5 + cc] * dotp<T, QF4>(PJ + f * QFP, Lp);
+          } else {
+            const T* Lp = tb.Lf + (((size_t)f * g.ndiv + j) * g.DB + cc) * g.Qf;
+            for (int p = 0; p < g.Qf; ++p)
+              sf += (FS[fsi(f, p, 5 + cc)] + PJ[f * QFP + p] * qv[5 + cc]) * Lp[p];
+          }
         }
         if (lowp) acct -= sf; else acc -= (double)sf;
       }
@@ -718,25 +794,27 @@ void launch_face(const Geom& g, const Tables<T>& tb, const T* w, T* fbuf, const 
 }
 
 template <typename T>
-static size_t cell_smem(const Geom& g) {
-  const int per_warp = g.nrows + g.D * g.V * g.Qv + 2 * g.D * g.Qf * g.V + 2 * g.D * g.Qf;
-  return (size_t)per_warp * WARPS_PER_BLOCK * sizeof(T);
+static size_t cell_smem(const Geom& g, bool vec = false) {
+  return (size_t)cell_warp_elems(g, vec) * WARPS_PER_BLOCK * sizeof(T);
 }
 
 template <typename T>
 void launch_cell(const Geom& g, const Tables<T>& tb, const T* w, const T* fbuf, T* out, const T* w0,
                  double ca, double cb, int combine, const DevScalars* sc, const double* wmean,
                  const double* w0mean, double* outmean, cudaStream_t st) {
-  const size_t sm = cell_smem<T>(g);
+  const bool vec = pinned_sizes_ok(g) && tb.dPv4 && tb.dLv4 && tb.Pf4 && tb.Lf4;
+  const size_t sm = cell_smem<T>(g, vec);
   auto run = [&](auto k) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     k<<<nblocks(g.ncell, WARPS_PER_BLOCK), 32 * WARPS_PER_BLOCK, sm, st>>>(g, tb, w, fbuf, out, w0, ca, cb, combine,
                                                                         sc, wmean, w0mean, outmean);
   };
   // compile-time sizes for the 3D degree-1 and degree-2 schemes
-  if (!pinned_sizes_ok(g)) run(k_cell<T, -1, 0>);
-  else if (g.d == 2) g.glm ? run(k_cell<T, 2, 1>) : run(k_cell<T, 2, 0>);
-  else g.glm ? run(k_cell<T, 1, 1>) : run(k_cell<T, 1, 0>);
+  if (!pinned_sizes_ok(g)) run(k_cell<T, -1, 0, false>);
+  else if (!vec) g.d == 2 ? (g.glm ? run(k_cell<T, 2, 1, false>) : run(k_cell<T, 2, 0, false>))
+                          : (g.glm ? run(k_cell<T, 1, 1, false>) : run(k_cell<T, 1, 0, false>));
+  else if (g.d == 2) g.glm ? run(k_cell<T, 2, 1, true>) : run(k_cell<T, 2, 0, true>);
+  else g.glm ? run(k_cell<T, 1, 1, true>) : run(k_cell<T, 1, 0, true>);
 }
 
 template <typename T>
