@@ -69,6 +69,8 @@ template <typename T>
 struct SideTab {
   const T* P;
   const T* L;
+  const T* P4;  // the same rows with the point index padded to pad4(Qf)
+  const T* L4;
   bool coarse;
 };
 
@@ -79,12 +81,17 @@ __device__ __forceinline__ SideTab<T> side_tab(const Geom& g, const Tables<T>& t
   const int f = side == 0 ? 2 * a + 1 : 2 * a;
   const bool coarse = (side == 0 && kind == 1) || (side == 1 && kind == 2);
   SideTab<T> t;
+  const int qf4 = pad4(g.Qf);
   if (coarse) {
     t.P = am.Psub + ((size_t)(f * am.nsub + sub) * g.n) * g.Qf;
     t.L = am.Lsub + ((size_t)(f * am.nsub + sub) * g.ndiv * g.DB) * g.Qf;
+    t.P4 = am.Psub4 + ((size_t)(f * am.nsub + sub) * g.n) * qf4;
+    t.L4 = am.Lsub4 + ((size_t)(f * am.nsub + sub) * g.ndiv * g.DB) * qf4;
   } else {
     t.P = tb.Pf + (size_t)f * g.n * g.Qf;
     t.L = tb.Lf + (size_t)f * g.ndiv * g.DB * g.Qf;
+    t.P4 = tb.Pf4 + (size_t)f * g.n * qf4;
+    t.L4 = tb.Lf4 + (size_t)f * g.ndiv * g.DB * qf4;
   }
   t.coarse = coarse;
   return t;
@@ -112,21 +119,36 @@ __global__ void k_face_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __res
   if (!g.glm) o[8] = bnF;
 }
 
-template <typename T, int DEG, int GLMF>
+// Per-warp shared memory of k_cell_list (elements): state rows, weighted
+// volume fluxes, face terms and Powell jump terms of up to maxent face
+// entries. VEC: point indices padded to a multiple of 4, regions 16-byte aligned.
+__host__ __device__ inline int cell_list_warp_elems(const Geom& g, int maxent, bool vec) {
+  const int qv = vec ? pad4(g.Qv) : g.Qv, qf = vec ? pad4(g.Qf) : g.Qf;
+  const int nr = vec ? pad4(g.nrows) : g.nrows;
+  const int e = nr + g.D * g.V * qv + maxent * qf * g.V + maxent * qf;
+  return vec ? pad4(e) : e;
+}
+
+// VEC (3D, sizes fixed at compile time, padded tables present): the row
+// contractions run as 16-byte vector loads.
+template <typename T, int DEG, int GLMF, bool VEC>
 __global__ void k_cell_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __restrict__ w,
                             const T* __restrict__ fbuf, T* out, const T* w0, double ca, double cb, int combine,
                             const DevScalars* __restrict__ sc, const double* __restrict__ wmean, const double* w0mean,
                             double* outmean) {
   const Geom g = pin_geom<DEG, GLMF>(gin);
   // out / outmean may alias w0 / w0mean: each element is read, then written, by one lane.
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t c = (int64_t)blockIdx.x * WPB + warp;
-  const int per_warp = g.nrows + g.D * g.V * g.Qv + am.maxent * g.Qf * g.V + am.maxent * g.Qf;
+  const int QVP = VEC ? pad4(g.Qv) : g.Qv, QFP = VEC ? pad4(g.Qf) : g.Qf;
+  const int per_warp = cell_list_warp_elems(g, am.maxent, VEC);
   T* wc = reinterpret_cast<T*>(smraw) + (size_t)warp * per_warp;
-  T* G = wc + g.nrows;
-  T* FS = G + g.D * g.V * g.Qv;
-  T* PJ = FS + am.maxent * g.Qf * g.V;
+  T* G = wc + (VEC ? pad4(g.nrows) : g.nrows);
+  T* FS = G + g.D * g.V * QVP;
+  T* PJ = FS + am.maxent * QFP * g.V;
+  // face term of (entry e, point p, variable v)
+  auto fsi = [&](int e, int p, int v) { return VEC ? (e * g.V + v) * QFP + p : (e * g.Qf + p) * g.V + v; };
   if (c >= g.ncell) return;
   const int64_t S = g.stride;
   const bool mix = wmean != nullptr;
@@ -143,10 +165,20 @@ __global__ void k_cell_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __res
     for (int a = 0; a < g.D; ++a) {
       T f[MAXV];
       flux_dir(u, a, gamma, g.glm != 0, ch * ch, f);
-      for (int v = 0; v < g.V; ++v) G[(a * g.V + v) * g.Qv + q] = wq * f[v];
+      for (int v = 0; v < g.V; ++v) G[(a * g.V + v) * QVP + q] = wq * f[v];
     }
   }
   const int e0 = am.cstart[c], ne = am.cstart[c + 1] - e0;
+  if (VEC) {
+    // zero padding of the point index (the padded tables are zero there too)
+    for (int i = lane; i < g.D * g.V * (QVP - g.Qv); i += 32)
+      G[(i / (QVP - g.Qv)) * QVP + g.Qv + i % (QVP - g.Qv)] = T(0);
+    for (int i = lane; i < ne * (g.V + 1) * (QFP - g.Qf); i += 32) {
+      const int row = i / (QFP - g.Qf), pp = g.Qf + i % (QFP - g.Qf);
+      if (row < ne * g.V) FS[row * QFP + pp] = T(0);
+      else PJ[(row - ne * g.V) * QFP + pp] = T(0);
+    }
+  }
   const T subw = T(1) / T(am.nsub);
   for (int idx = lane; idx < ne * g.Qf; idx += 32) {
     const int e = idx / g.Qf, p = idx % g.Qf;
@@ -160,11 +192,11 @@ __global__ void k_cell_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __res
     // outward normal: +e_a for the left cell, -e_a for the right cell
     const T sgn = side == 0 ? T(1) : T(-1);
     const T wp = tb.wf[p] * (t.coarse ? subw : T(1));
-    for (int v = 0; v < g.V; ++v) FS[(e * g.Qf + p) * g.V + v] = sgn * wp * F[v];
+    for (int v = 0; v < g.V; ++v) FS[fsi(e, p, v)] = sgn * wp * F[v];
     if (!g.glm) {
       T ba = T(0);
       for (int j = 0; j < g.ndiv; ++j) ba += wc[g.ldf0 + j] * t.L[(j * g.DB + a) * g.Qf + p];
-      PJ[e * g.Qf + p] = wp * sgn * (F[8] - ba);
+      PJ[e * QFP + p] = wp * sgn * (F[8] - ba);
     }
   }
   __syncwarp();
@@ -198,20 +230,31 @@ __global__ void k_cell_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __res
       T s = T(0);
       if (l != 0)
         for (int a = 0; a < g.D; ++a) {
-          const T* Gp = G + (a * g.V + v) * g.Qv;
-          const T* Dp = tb.dPv + ((size_t)a * g.n + l) * g.Qv;
-          for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
+          const T* Gp = G + (a * g.V + v) * QVP;
+          if constexpr (VEC) {
+            s += dotp<T, pad4((DEG + 1) * (DEG + 1) * (DEG + 1))>(Gp, tb.dPv4 + ((size_t)a * g.n + l) * QVP);
+          } else {
+            const T* Dp = tb.dPv + ((size_t)a * g.n + l) * g.Qv;
+            for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
+          }
         }
       if (lowp) acct += s; else acc += (double)s;
       for (int e = 0; e < ne; ++e) {
         const int ent = am.centry[e0 + e];
         const SideTab<T> t = side_tab(g, tb, am, am.fmeta[ent >> 1], ent & 1);
-        const T* Pp = t.P + (size_t)l * g.Qf;
         T sf = T(0);
-        for (int p = 0; p < g.Qf; ++p) {
-          T term = FS[(e * g.Qf + p) * g.V + v];
-          if (!g.glm) term += PJ[e * g.Qf + p] * qv[v];
-          sf += term * Pp[p];
+        if constexpr (VEC) {
+          constexpr int QF4 = pad4((DEG + 1) * (DEG + 1));
+          const T* Pp = t.P4 + (size_t)l * QFP;
+          sf = dotp<T, QF4>(FS + (e * g.V + v) * QFP, Pp);
+          if (!g.glm) sf += qv[v] * dotp<T, QF4>(PJ + e * QFP, Pp);
+        } else {
+          const T* Pp = t.P + (size_t)l * g.Qf;
+          for (int p = 0; p < g.Qf; ++p) {
+            T term = FS[fsi(e, p, v)];
+            if (!g.glm) term += PJ[e * QFP + p] * qv[v];
+            sf += term * Pp[p];
+          }
         }
         if (lowp) acct -= sf; else acc -= (double)sf;
       }
@@ -220,9 +263,14 @@ __global__ void k_cell_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __res
       T s = T(0);
       for (int a = 0; a < g.D; ++a)
         for (int cc = 0; cc < g.DB; ++cc) {
-          const T* Gp = G + (a * g.V + 5 + cc) * g.Qv;
-          const T* Dp = tb.dLv + (((size_t)a * g.ndiv + j) * g.DB + cc) * g.Qv;
-          for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
+          const T* Gp = G + (a * g.V + 5 + cc) * QVP;
+          if constexpr (VEC) {
+            s += dotp<T, pad4((DEG + 1) * (DEG + 1) * (DEG + 1))>(
+                Gp, tb.dLv4 + (((size_t)a * g.ndiv + j) * g.DB + cc) * QVP);
+          } else {
+            const T* Dp = tb.dLv + (((size_t)a * g.ndiv + j) * g.DB + cc) * g.Qv;
+            for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
+          }
         }
       if (lowp) acct += s; else acc += (double)s;
       for (int e = 0; e < ne; ++e) {
@@ -230,9 +278,15 @@ __global__ void k_cell_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __res
         const SideTab<T> t = side_tab(g, tb, am, am.fmeta[ent >> 1], ent & 1);
         T sf = T(0);
         for (int cc = 0; cc < g.DB; ++cc) {
-          const T* Lp = t.L + ((size_t)j * g.DB + cc) * g.Qf;
-          for (int p = 0; p < g.Qf; ++p)
-            sf += (FS[(e * g.Qf + p) * g.V + 5 + cc] + PJ[e * g.Qf + p] * qv[5 + cc]) * Lp[p];
+          if constexpr (VEC) {
+            constexpr int QF4 = pad4((DEG + 1) * (DEG + 1));
+            const T* Lp = t.L4 + ((size_t)j * g.DB + cc) * QFP;
+            sf += dotp<T, QF4>(FS + (e * g.V + 5 + cc) * QFP, Lp) + qv[5 + cc] * dotp<T, QF4>(PJ + e * QFP, Lp);
+          } else {
+            const T* Lp = t.L + ((size_t)j * g.DB + cc) * g.Qf;
+            for (int p = 0; p < g.Qf; ++p)
+              sf += (FS[fsi(e, p, 5 + cc)] + PJ[e * QFP + p] * qv[5 + cc]) * Lp[p];
+          }
         }
         if (lowp) acct -= sf; else acc -= (double)sf;
       }
@@ -508,6 +562,19 @@ int build_amr(Ctx& c, const dg_mesh_desc* mesh) {
   if ((e = upload_vec(&h.Psub64, Ps)) || (e = upload_vec(&h.Lsub64, Ls)) || (e = upload_vec(&h.Psub32, Psf)) ||
       (e = upload_vec(&h.Lsub32, Lsf)))
     return e;
+  // point index padded to a multiple of 4 (zeros), for the vector contractions
+  const int qf4 = pad4(g.Qf);
+  auto padded = [&](const std::vector<double>& src) {
+    std::vector<double> out(src.size() / g.Qf * qf4, 0.0);
+    for (size_t r = 0; r < src.size() / g.Qf; ++r)
+      for (int k = 0; k < g.Qf; ++k) out[r * qf4 + k] = src[r * g.Qf + k];
+    return out;
+  };
+  const std::vector<double> Ps4 = padded(Ps), Ls4 = padded(Ls);
+  std::vector<float> Ps4f(Ps4.begin(), Ps4.end()), Ls4f(Ls4.begin(), Ls4.end());
+  if ((e = upload_vec(&h.Psub64p, Ps4)) || (e = upload_vec(&h.Lsub64p, Ls4)) || (e = upload_vec(&h.Psub32p, Ps4f)) ||
+      (e = upload_vec(&h.Lsub32p, Ls4f)))
+    return e;
   double dmin = DBL_MAX;
   for (double d : dxc) dmin = std::min(dmin, d);
   g.dx = dmin;
@@ -516,7 +583,8 @@ int build_amr(Ctx& c, const dg_mesh_desc* mesh) {
 
 void free_amr(Ctx& c) {
   AmrHost& h = c.amr;
-  void* ptrs[] = {h.fL, h.fR, h.fmeta, h.cstart, h.centry, h.dxc, h.Psub64, h.Lsub64, h.Psub32, h.Lsub32};
+  void* ptrs[] = {h.fL,     h.fR,     h.fmeta,   h.cstart,  h.centry,  h.dxc,     h.Psub64,
+                  h.Lsub64, h.Psub32, h.Lsub32, h.Psub64p, h.Lsub64p, h.Psub32p, h.Lsub32p};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h = AmrHost();
@@ -527,12 +595,14 @@ AmrDev<T> amr_dev(const Ctx& c);
 template <>
 AmrDev<double> amr_dev<double>(const Ctx& c) {
   const AmrHost& h = c.amr;
-  return AmrDev<double>{h.fL, h.fR, h.fmeta, h.cstart, h.centry, h.dxc, h.Psub64, h.Lsub64, h.nface, h.maxent, h.nsub};
+  return AmrDev<double>{h.fL, h.fR, h.fmeta, h.cstart, h.centry, h.dxc, h.Psub64, h.Lsub64, h.Psub64p, h.Lsub64p,
+                         h.nface, h.maxent, h.nsub};
 }
 template <>
 AmrDev<float> amr_dev<float>(const Ctx& c) {
   const AmrHost& h = c.amr;
-  return AmrDev<float>{h.fL, h.fR, h.fmeta, h.cstart, h.centry, h.dxc, h.Psub32, h.Lsub32, h.nface, h.maxent, h.nsub};
+  return AmrDev<float>{h.fL, h.fR, h.fmeta, h.cstart, h.centry, h.dxc, h.Psub32, h.Lsub32, h.Psub32p, h.Lsub32p,
+                        h.nface, h.maxent, h.nsub};
 }
 
 template <typename T>
@@ -542,8 +612,10 @@ void launch_amr_operator(const Ctx& c, const Tables<T>& tb, const T* w, T* fbuf,
   const Geom& g = c.g;
   const AmrDev<T> am = amr_dev<T>(c);
   const int64_t np = am.nface * g.Qf;
-  const int per_warp = g.nrows + g.D * g.V * g.Qv + am.maxent * g.Qf * g.V + am.maxent * g.Qf;
-  const size_t sm = (size_t)per_warp * WPB * sizeof(T);
+  // FP32 only: FP64 is bound by its multiply-add rate, which the padding would raise
+  const bool vec = sizeof(T) == 4 && pinned_sizes_ok(g) && tb.dPv4 && tb.dLv4 && tb.Pf4 && tb.Lf4 && am.Psub4 &&
+                   am.Lsub4;
+  const size_t sm = (size_t)cell_list_warp_elems(g, am.maxent, vec) * WPB * sizeof(T);
   auto run = [&](auto face_k, auto cell_k) {
     face_k<<<(unsigned)((np + 127) / 128), 128, 0, st>>>(g, tb, am, w, fbuf, sc, (T)eps);
     cudaFuncSetAttribute(cell_k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -551,12 +623,17 @@ void launch_amr_operator(const Ctx& c, const Tables<T>& tb, const T* w, T* fbuf,
                                                                        sc, wmean, w0mean, outmean);
   };
   // compile-time sizes for the 3D degree-1 and degree-2 schemes
-  if (!pinned_sizes_ok(g)) run(k_face_list<T, -1, 0>, k_cell_list<T, -1, 0>);
-  else if (g.D == 3 && g.d == 2 && !g.glm) run(k_face_list<T, 2, 0>, k_cell_list<T, 2, 0>);
-  else if (g.D == 3 && g.d == 2 && g.glm) run(k_face_list<T, 2, 1>, k_cell_list<T, 2, 1>);
-  else if (g.D == 3 && g.d == 1 && !g.glm) run(k_face_list<T, 1, 0>, k_cell_list<T, 1, 0>);
-  else if (g.D == 3 && g.d == 1 && g.glm) run(k_face_list<T, 1, 1>, k_cell_list<T, 1, 1>);
-  else run(k_face_list<T, -1, 0>, k_cell_list<T, -1, 0>);
+  if (!pinned_sizes_ok(g)) run(k_face_list<T, -1, 0>, k_cell_list<T, -1, 0, false>);
+  else if (!vec) {
+    if (g.d == 2) g.glm ? run(k_face_list<T, 2, 1>, k_cell_list<T, 2, 1, false>)
+                        : run(k_face_list<T, 2, 0>, k_cell_list<T, 2, 0, false>);
+    else g.glm ? run(k_face_list<T, 1, 1>, k_cell_list<T, 1, 1, false>)
+               : run(k_face_list<T, 1, 0>, k_cell_list<T, 1, 0, false>);
+  } else if (g.d == 2) {
+    g.glm ? run(k_face_list<T, 2, 1>, k_cell_list<T, 2, 1, true>) : run(k_face_list<T, 2, 0>, k_cell_list<T, 2, 0, true>);
+  } else {
+    g.glm ? run(k_face_list<T, 1, 1>, k_cell_list<T, 1, 1, true>) : run(k_face_list<T, 1, 0>, k_cell_list<T, 1, 0, true>);
+  }
 }
 
 template <typename T>

@@ -20,6 +20,8 @@ struct AmrDev {
   const double* dxc;
   const T* Psub;
   const T* Lsub;
+  const T* Psub4;  // Psub / Lsub with the point index padded to pad4(Qf)
+  const T* Lsub4;
   int64_t nface;
   int maxent;
   int nsub;

@@ -173,6 +173,9 @@ struct AmrHost {
   double* dxc = nullptr;
   double *Psub64 = nullptr, *Lsub64 = nullptr;
   float *Psub32 = nullptr, *Lsub32 = nullptr;
+  // the same with the point index zero-padded to a multiple of 4
+  double *Psub64p = nullptr, *Lsub64p = nullptr;
+  float *Psub32p = nullptr, *Lsub32p = nullptr;
 };
 
 struct Ctx {

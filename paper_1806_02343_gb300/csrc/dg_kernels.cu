@@ -128,34 +128,6 @@ __global__ void k_face(Geom gin, Tables<T> tb, const T* __restrict__ w, T* __res
 }
 
 // ---------------------------------------------------------------- cell update
-// LEN-point dot product of two 16-byte aligned arrays (LEN a multiple of 4)
-template <typename T, int LEN>
-__device__ __forceinline__ T dotp(const T* a, const T* b) {
-  T s = T(0);
-  if constexpr (sizeof(T) == 4) {
-    const float4* A = reinterpret_cast<const float4*>(a);
-    const float4* B = reinterpret_cast<const float4*>(b);
-#pragma unroll
-    for (int k = 0; k < LEN / 4; ++k) {
-      const float4 x = A[k], y = B[k];
-      s = fmaf(x.x, y.x, s);
-      s = fmaf(x.y, y.y, s);
-      s = fmaf(x.z, y.z, s);
-      s = fmaf(x.w, y.w, s);
-    }
-  } else {
-    const double2* A = reinterpret_cast<const double2*>(a);
-    const double2* B = reinterpret_cast<const double2*>(b);
-#pragma unroll
-    for (int k = 0; k < LEN / 2; ++k) {
-      const double2 x = A[k], y = B[k];
-      s = fma(x.x, y.x, s);
-      s = fma(x.y, y.y, s);
-    }
-  }
-  return s;
-}
-
 // Per-warp shared memory of k_cell (elements): state rows, weighted volume
 // fluxes G, face terms FS and Powell jump terms PJ. VEC: point indices padded
 // to a multiple of 4 and every region 16-byte aligned (vector loads).
@@ -802,7 +774,8 @@ template <typename T>
 void launch_cell(const Geom& g, const Tables<T>& tb, const T* w, const T* fbuf, T* out, const T* w0,
                  double ca, double cb, int combine, const DevScalars* sc, const double* wmean,
                  const double* w0mean, double* outmean, cudaStream_t st) {
-  const bool vec = pinned_sizes_ok(g) && tb.dPv4 && tb.dLv4 && tb.Pf4 && tb.Lf4;
+  // FP32 only: FP64 is bound by its multiply-add rate, which the padding would raise
+  const bool vec = sizeof(T) == 4 && pinned_sizes_ok(g) && tb.dPv4 && tb.dLv4 && tb.Pf4 && tb.Lf4;
   const size_t sm = cell_smem<T>(g, vec);
   auto run = [&](auto k) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

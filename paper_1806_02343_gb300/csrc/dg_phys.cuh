@@ -245,4 +245,32 @@ __device__ __forceinline__ T face_flux(const T* uL, const T* uR, int a, T gamma,
   return bnF;
 }
 
+// LEN-point dot product of two 16-byte aligned arrays (LEN a multiple of 4)
+template <typename T, int LEN>
+__device__ __forceinline__ T dotp(const T* a, const T* b) {
+  T s = T(0);
+  if constexpr (sizeof(T) == 4) {
+    const float4* A = reinterpret_cast<const float4*>(a);
+    const float4* B = reinterpret_cast<const float4*>(b);
+#pragma unroll
+    for (int k = 0; k < LEN / 4; ++k) {
+      const float4 x = A[k], y = B[k];
+      s = fmaf(x.x, y.x, s);
+      s = fmaf(x.y, y.y, s);
+      s = fmaf(x.z, y.z, s);
+      s = fmaf(x.w, y.w, s);
+    }
+  } else {
+    const double2* A = reinterpret_cast<const double2*>(a);
+    const double2* B = reinterpret_cast<const double2*>(b);
+#pragma unroll
+    for (int k = 0; k < LEN / 2; ++k) {
+      const double2 x = A[k], y = B[k];
+      s = fma(x.x, y.x, s);
+      s = fma(x.y, y.y, s);
+    }
+  }
+  return s;
+}
+
 }  // namespace dgmhd
