@@ -135,6 +135,11 @@ struct LimTabs {
   double ldf_pc[64 * 3];
   double ldf_pl[64 * 9];
   double ldf_maxabs[64 * 3];  // upper bound of |phi_j,c| on the cell (sum of |monomial coefficients|)
+  // FP32 copies for the FP32 form's limiter arithmetic
+  float ldf_mean0_f[64 * 3];
+  float ldf_slope_f[64 * 9];
+  float ldf_pc_f[64 * 3];
+  float ldf_pl_f[64 * 9];
 };
 
 // Launch accounting: counts every kernel launch; with `on`, records a CUDA

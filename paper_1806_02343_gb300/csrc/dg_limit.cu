@@ -49,21 +49,29 @@ __device__ __forceinline__ int lmean_row(const Geom& g, int m) {
   return m < 7 ? g.ldf0 + (m - 5) : g.bz2d;
 }
 
-// cell-mean conserved state of cell c (V values)
-template <typename T>
+// table entry in the working precision R (FP32 copy or the FP64 table)
+template <typename R>
+__device__ __forceinline__ R ltab(const double* d, const float* f, int i) {
+  if constexpr (sizeof(R) == 4) return f[i];
+  else return d[i];
+}
+
+// cell means of the conserved variables (B from the degree-0 LDF rows) in the
+// working precision R of the limiter
+template <typename R, typename T>
 __device__ __forceinline__ void cell_mean(const Geom& g, const LimTabs& lt, const T* w, const double* wmean,
-                                          int64_t c, double* m) {
+                                          int64_t c, R* m) {
   const int64_t S = g.stride;
   const int nm = g.glm ? 9 : 8;
-  double raw[9];
-  for (int k = 0; k < nm; ++k) raw[k] = wmean ? wmean[k * S + c] : (double)w[(int64_t)lmean_row(g, k) * S + c];
-  for (int k = 0; k < 9; ++k) m[k] = 0.0;
+  R raw[9];
+  for (int k = 0; k < nm; ++k) raw[k] = wmean ? (R)wmean[k * S + c] : (R)w[(int64_t)lmean_row(g, k) * S + c];
+  for (int k = 0; k < 9; ++k) m[k] = R(0);
   for (int k = 0; k < 5; ++k) m[k] = raw[k];
   if (g.glm) {
     for (int k = 5; k < 9; ++k) m[k] = raw[k];
   } else {
     for (int j = 0; j < g.D; ++j)
-      for (int cc = 0; cc < g.D; ++cc) m[5 + cc] += raw[5 + j] * lt.ldf_mean0[j * 3 + cc];
+      for (int cc = 0; cc < g.D; ++cc) m[5 + cc] += raw[5 + j] * ltab<R>(lt.ldf_mean0, lt.ldf_mean0_f, j * 3 + cc);
     if (g.D == 2) m[7] = raw[7];
   }
 }
@@ -227,51 +235,51 @@ struct AmrNb {
   int on;
 };
 
-// The TVB procedure on cell c; returns whether any slope changed.
+// The TVB procedure on cell c; returns whether any slope changed. All of it
+// runs in the working precision of the state (the FP32 form reads the float
+// mirror of the means, which the limiter never changes).
 template <typename T>
 __device__ bool tvb_cell(const Geom& g, const LimTabs& lt, T* w, const double* wmean, const dg_mhd_params& p,
                          const DevScalars* __restrict__ sc, const AmrNb& an, int64_t c) {
+  using R = T;
   const int64_t S = g.stride;
   const int V = g.V;
-  double m[9];
-  cell_mean(g, lt, (const T*)w, wmean, c, m);
+  R m[9];
+  cell_mean<R>(g, lt, (const T*)w, wmean, c, m);
   // degree-1 slopes u_xi[a][v]
-  double sl[3][9];
+  R sl[3][9];
   for (int a = 0; a < 3; ++a)
-    for (int k = 0; k < 9; ++k) sl[a][k] = 0.0;
+    for (int k = 0; k < 9; ++k) sl[a][k] = R(0);
   const int nleg = g.glm ? 9 : 5;
   for (int a = 0; a < g.D; ++a) {
-    for (int v = 0; v < nleg; ++v) sl[a][v] = (double)w[(int64_t)(v * g.n + lt.deg1[a]) * S + c];
-    if (g.bz2d >= 0) sl[a][7] = (double)w[(int64_t)(g.bz2d + lt.deg1[a]) * S + c];
+    for (int v = 0; v < nleg; ++v) sl[a][v] = (R)w[(int64_t)(v * g.n + lt.deg1[a]) * S + c];
+    if (g.bz2d >= 0) sl[a][7] = (R)w[(int64_t)(g.bz2d + lt.deg1[a]) * S + c];
   }
   if (!g.glm) {
     for (int j = 0; j < g.ndiv; ++j) {
       if (lt.ldf_deg[j] == 0) continue;
-      const double wj = (double)w[(int64_t)(g.ldf0 + j) * S + c];
+      const R wj = (R)w[(int64_t)(g.ldf0 + j) * S + c];
       for (int cc = 0; cc < g.D; ++cc)
-        for (int a = 0; a < g.D; ++a) sl[a][5 + cc] += wj * lt.ldf_slope[(j * 3 + cc) * 3 + a];
+        for (int a = 0; a < g.D; ++a) sl[a][5 + cc] += wj * ltab<R>(lt.ldf_slope, lt.ldf_slope_f, (j * 3 + cc) * 3 + a);
     }
   }
-  // characteristic limiting in the working precision of the state
-  using R = T;
+  // characteristic limiting
   const R thr = (R)(p.Mtilde * (an.on ? an.dxc[c] : g.dx));
   const R ch = g.glm ? (R)sc->ch : R(0);
   const R rel = sizeof(T) == 4 ? R(1e-6) : R(1e-12);
   const R gam = (R)g.gamma, beta = (R)p.beta, teps = (R)p.tvb_eps;
-  R mR[9];
-  for (int k = 0; k < 9; ++k) mR[k] = (R)m[k];
   bool any = false;
-  double nsl[3][9];
+  R nsl[3][9];
   for (int a = 0; a < g.D; ++a) {
-    double mp[9], mm[9];
-    double fp = 2.0, fm = 2.0;  // centre distance in units of dx_K / 2
+    R mp[9], mm[9];
+    R fp = R(2), fm = R(2);  // centre distance in units of dx_K / 2
     if (!an.on) {
-      cell_mean(g, lt, (const T*)w, wmean, nb(g, c, a, +1), mp);
-      cell_mean(g, lt, (const T*)w, wmean, nb(g, c, a, -1), mm);
+      cell_mean<R>(g, lt, (const T*)w, wmean, nb(g, c, a, +1), mp);
+      cell_mean<R>(g, lt, (const T*)w, wmean, nb(g, c, a, -1), mm);
     } else {
       // octree: average of the leaves across each side; 2 same level, 3 coarser, 1.5 finer
       int np_ = 0, nm_ = 0;
-      for (int k = 0; k < 9; ++k) mp[k] = mm[k] = 0.0;
+      for (int k = 0; k < 9; ++k) mp[k] = mm[k] = R(0);
       for (int e = an.cstart[c]; e < an.cstart[c + 1]; ++e) {
         const int ent = an.centry[e];
         const int f = ent >> 1, side = ent & 1;
@@ -279,10 +287,10 @@ __device__ bool tvb_cell(const Geom& g, const LimTabs& lt, T* w, const double* w
         if ((meta & 3) != a) continue;
         const int kind = (meta >> 2) & 3;
         const int64_t nbc = side == 0 ? an.fR[f] : an.fL[f];
-        double mn[9];
-        cell_mean(g, lt, (const T*)w, wmean, nbc, mn);
+        R mn[9];
+        cell_mean<R>(g, lt, (const T*)w, wmean, nbc, mn);
         const bool self_coarse = (side == 0 && kind == 1) || (side == 1 && kind == 2);
-        const double fac = kind == 0 ? 2.0 : (self_coarse ? 1.5 : 3.0);
+        const R fac = kind == 0 ? R(2) : (self_coarse ? R(1.5) : R(3));
         if (side == 0) {
           for (int k = 0; k < 9; ++k) mp[k] += mn[k];
           ++np_;
@@ -293,23 +301,26 @@ __device__ bool tvb_cell(const Geom& g, const LimTabs& lt, T* w, const double* w
           fm = fac;
         }
       }
+      // 1 or 2^(D-1) leaves: exact reciprocals
+      const R ip = R(1) / (R)(np_ > 0 ? np_ : 1), im = R(1) / (R)(nm_ > 0 ? nm_ : 1);
       for (int k = 0; k < 9; ++k) {
-        mp[k] /= (double)(np_ > 0 ? np_ : 1);
-        mm[k] /= (double)(nm_ > 0 ? nm_ : 1);
+        mp[k] *= ip;
+        mm[k] *= im;
       }
     }
-    R dpl[9], dmi[9], sla[9];
+    // one reciprocal per side (exact for the distance 2 of equal cells)
+    const R ifp = R(1) / fp, ifm = R(1) / fm;
+    R dpl[9], dmi[9];
     for (int k = 0; k < 9; ++k) {
-      dpl[k] = (R)((mp[k] - m[k]) / fp);
-      dmi[k] = (R)((m[k] - mm[k]) / fm);
-      sla[k] = (R)sl[a][k];
+      dpl[k] = (mp[k] - m[k]) * ifp;
+      dmi[k] = (m[k] - mm[k]) * ifm;
     }
     Eig<R> e;
-    eig_setup(mR, a, gam, g.glm != 0, ch, rel, e);
+    eig_setup(m, a, gam, g.glm != 0, ch, rel, e);
     R cx[9], cp[9], cm[9], sg[9];
-    to_char(e, mR, gam, sla, cx, V);
-    to_char(e, mR, gam, dpl, cp, V);
-    to_char(e, mR, gam, dmi, cm, V);
+    to_char(e, m, gam, sl[a], cx, V);
+    to_char(e, m, gam, dpl, cp, V);
+    to_char(e, m, gam, dmi, cm, V);
     bool trig = false;
     for (int k = 0; k < V; ++k) {
       sg[k] = cx[k];
@@ -320,8 +331,8 @@ __device__ bool tvb_cell(const Geom& g, const LimTabs& lt, T* w, const double* w
     }
     if (trig) {
       R out[9];
-      from_char(e, mR, gam, sg, out, V);
-      for (int k = 0; k < 9; ++k) nsl[a][k] = k < V ? (double)out[k] : 0.0;
+      from_char(e, m, gam, sg, out, V);
+      for (int k = 0; k < 9; ++k) nsl[a][k] = k < V ? out[k] : R(0);
       any = true;
     } else {
       for (int k = 0; k < 9; ++k) nsl[a][k] = sl[a][k];
@@ -337,7 +348,7 @@ __device__ bool tvb_cell(const Geom& g, const LimTabs& lt, T* w, const double* w
     else { v = r / g.n; l = r % g.n; }
     const int dg = lt.mdeg[l];
     if (dg == 0) continue;
-    double val = 0.0;
+    R val = R(0);
     if (dg == 1) {
       for (int a = 0; a < g.D; ++a)
         if (lt.deg1[a] == l) val = nsl[a][v];
@@ -346,23 +357,23 @@ __device__ bool tvb_cell(const Geom& g, const LimTabs& lt, T* w, const double* w
   }
   if (!g.glm) {
     // LDF slope fix (Sec. 4.2.4) and exact projection onto LDF degree <= 1
-    double Bs[3][3];
+    R Bs[3][3];
     for (int cc = 0; cc < g.D; ++cc)
       for (int a = 0; a < g.D; ++a) Bs[cc][a] = nsl[a][5 + cc];
-    double dpos = 0.0, dneg = 0.0, dsum = 0.0;
+    R dpos = R(0), dneg = R(0), dsum = R(0);
     for (int k = 0; k < g.D; ++k) {
       dsum += Bs[k][k];
-      dpos += fmax(Bs[k][k], 0.0);
-      dneg += fmax(-Bs[k][k], 0.0);
+      dpos += rmax(Bs[k][k], R(0));
+      dneg += rmax(-Bs[k][k], R(0));
     }
-    if (dsum > 0.0) {
-      const double f = dneg / dpos;
+    if (dsum > R(0)) {
+      const R f = dneg / dpos;
       for (int k = 0; k < g.D; ++k)
-        if (Bs[k][k] > 0.0) Bs[k][k] *= f;
-    } else if (dsum < 0.0) {
-      const double f = dpos / dneg;
+        if (Bs[k][k] > R(0)) Bs[k][k] *= f;
+    } else if (dsum < R(0)) {
+      const R f = dpos / dneg;
       for (int k = 0; k < g.D; ++k)
-        if (Bs[k][k] < 0.0) Bs[k][k] *= f;
+        if (Bs[k][k] < R(0)) Bs[k][k] *= f;
     }
     for (int j = 0; j < g.ndiv; ++j) {
       const int64_t i = (int64_t)(g.ldf0 + j) * S + c;
@@ -371,10 +382,10 @@ __device__ bool tvb_cell(const Geom& g, const LimTabs& lt, T* w, const double* w
         w[i] = T(0);
         continue;
       }
-      double val = 0.0;
+      R val = R(0);
       for (int cc = 0; cc < g.D; ++cc) {
-        val += lt.ldf_pc[j * 3 + cc] * m[5 + cc];
-        for (int a = 0; a < g.D; ++a) val += lt.ldf_pl[(j * 3 + cc) * 3 + a] * Bs[cc][a];
+        val += ltab<R>(lt.ldf_pc, lt.ldf_pc_f, j * 3 + cc) * m[5 + cc];
+        for (int a = 0; a < g.D; ++a) val += ltab<R>(lt.ldf_pl, lt.ldf_pl_f, (j * 3 + cc) * 3 + a) * Bs[cc][a];
       }
       w[i] = (T)val;
     }
@@ -785,6 +796,14 @@ int upload_limiter_tables(Ctx& c) {
       for (double v : B.ldf[j][cc]) mx += std::fabs(v);
       lt.ldf_maxabs[j * 3 + cc] = mx;
     }
+  for (int i = 0; i < 64 * 3; ++i) {
+    lt.ldf_mean0_f[i] = (float)lt.ldf_mean0[i];
+    lt.ldf_pc_f[i] = (float)lt.ldf_pc[i];
+  }
+  for (int i = 0; i < 64 * 9; ++i) {
+    lt.ldf_slope_f[i] = (float)lt.ldf_slope[i];
+    lt.ldf_pl_f[i] = (float)lt.ldf_pl[i];
+  }
   c.lim = lt;
   return DG_OK;
 }
