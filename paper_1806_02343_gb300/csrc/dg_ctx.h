@@ -142,6 +142,13 @@ struct LimTabs {
   float ldf_pl_f[64 * 9];
 };
 
+// Tables and floors of the FP32 positivity screen (kernel parameter).
+struct PosScreen {
+  float ldf_mean0[9];       // component means of the degree-0 LDF rows j < D, [j*3 + c]
+  float ldf_maxabs[64 * 3]; // bound of |phi_j,c| on the cell
+  float eps_rho, eps_p, gm1;
+};
+
 // Launch accounting: counts every kernel launch; with `on`, records a CUDA
 // event pair on the launch stream around each launch of a given kind.
 struct Prof {
@@ -210,6 +217,7 @@ struct Ctx {
   uint8_t* troubled = nullptr;     // per-cell limiter flags (scratch)
   int32_t* flag_list = nullptr;    // cells flagged by the indicator in the current pass
   int32_t* pos_list = nullptr;     // cells the positivity screen could not clear in the current pass
+  PosScreen pscr;                  // FP32 positivity screen tables
   int64_t lim_passes = 0;          // limiter passes with TVB since the last counter reset
   int64_t lim_plain_cells = 0;     // cells the plain TVB detection examined since the last reset
   int nsm = 152;                   // streaming multiprocessors of the device

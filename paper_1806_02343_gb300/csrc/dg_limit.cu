@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "dg_limit.cuh"
+#include "dg_pos.cuh"
 #include "dg_mlp.cuh"
 
 namespace dgmhd {
@@ -396,20 +397,31 @@ __device__ bool tvb_cell(const Geom& g, const LimTabs& lt, T* w, const double* w
 // TVB over every cell (list == nullptr: the plain detector) or over the cells
 // the learned indicator listed (list[0 .. sc->nflag)); grid-stride, so any
 // grid covers the work. Counts the cells whose slopes changed.
-template <typename T>
+template <typename T, bool SCREEN>
 __global__ void k_tvb(Geom g, LimTabs lt, T* w, double* wmean, uint8_t* troubled, const int32_t* __restrict__ list,
-                      dg_mhd_params p, DevScalars* sc, AmrNb an) {
+                      dg_mhd_params p, DevScalars* sc, AmrNb an, int32_t* __restrict__ plist, PosScreen ps) {
   const int64_t total = list ? (int64_t)sc->nflag : g.ncell;
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t S = g.stride;
   unsigned limited = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += step) {
-    const int64_t c = list ? (int64_t)list[i] : i;
-    const bool any = tvb_cell(g, lt, w, wmean, p, sc, an, c);
-    if (troubled) troubled[c] = any ? 1 : 0;
-    limited += any ? 1u : 0u;
+  // warp-uniform trip count (the positivity append below is a warp ballot)
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < total; i0 += step) {
+    const int64_t i = i0 + lane;
+    bool fail = false;
+    if (i < total) {
+      const int64_t c = list ? (int64_t)list[i] : i;
+      const bool any = tvb_cell(g, lt, w, wmean, p, sc, an, c);
+      if (troubled) troubled[c] = any ? 1 : 0;
+      limited += any ? 1u : 0u;
+      // FP32 form with the learned indicator: the flagged cells take the
+      // positivity screen here, on their limited rows
+      if constexpr (SCREEN) fail = !pos_screen_rows(g, ps, [&](int r) { return (float)w[(int64_t)r * S + c]; });
+    }
+    if constexpr (SCREEN) append_cells(fail, i < total ? (list ? (int64_t)list[i] : i) : 0, plist, &sc->npos);
   }
   limited = __reduce_add_sync(0xffffffffu, limited);
-  if ((threadIdx.x & 31) == 0 && limited) atomicAdd(&sc->cnt_limited, (unsigned long long)limited);
+  if (lane == 0 && limited) atomicAdd(&sc->cnt_limited, (unsigned long long)limited);
 }
 
 // ------------------------------------------------------------------ positivity
@@ -455,79 +467,16 @@ __device__ __forceinline__ void point_state(const Geom& g, const Tables<T>& tb, 
   }
 }
 
-// FP32 form: rigorous screen in the working precision from the float mirror
-// of the means (|P_l| <= 1, |phi_j,c| <= ldf_maxabs on the cell, relative
-// margin 1e-4 for the rounding of the bound). True: the cell clears the floors
-// at every point and needs no further work.
-template <typename T>
-__device__ __forceinline__ bool pos_screen(const Geom& g, const LimTabs& lt, const T* w, const dg_mhd_params& p,
-                                           int64_t c) {
-  const int64_t S = g.stride;
-  T mt[8];
-  for (int k = 0; k < 5; ++k) mt[k] = w[(int64_t)lmean_row(g, k) * S + c];
-  if (g.glm) {
-    for (int k = 5; k < 8; ++k) mt[k] = w[(int64_t)lmean_row(g, k) * S + c];
-  } else {
-    mt[5] = mt[6] = mt[7] = T(0);
-    for (int j = 0; j < g.D; ++j)
-      for (int cc = 0; cc < g.D; ++cc) mt[5 + cc] += w[(int64_t)(g.ldf0 + j) * S + c] * (T)lt.ldf_mean0[j * 3 + cc];
-    if (g.bz2d >= 0) mt[7] = w[(int64_t)g.bz2d * S + c];
-  }
-  T dv[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-  const int nlg = g.glm ? 8 : 5;
-#pragma unroll
-  for (int v = 0; v < 8; ++v) {
-    if (v >= nlg) continue;
-    for (int l = 1; l < g.n; ++l) {
-      const T x = w[(int64_t)(v * g.n + l) * S + c];
-      dv[v] += x < T(0) ? -x : x;
-    }
-  }
-  if (!g.glm) {
-    for (int j = g.D; j < g.ndiv; ++j) {
-      T aj = w[(int64_t)(g.ldf0 + j) * S + c];
-      aj = aj < T(0) ? -aj : aj;
-#pragma unroll
-      for (int cc = 0; cc < 3; ++cc)
-        if (cc < g.D) dv[5 + cc] += aj * (T)lt.ldf_maxabs[j * 3 + cc];
-    }
-    if (g.bz2d >= 0)
-      for (int l = 1; l < g.n; ++l) {
-        const T x = w[(int64_t)(g.bz2d + l) * S + c];
-        dv[7] += x < T(0) ? -x : x;
-      }
-  }
-  const T mg = T(1e-4);
-#pragma unroll
-  for (int v = 0; v < 8; ++v) dv[v] = dv[v] * (T(1) + mg) + mg * (mt[v] < T(0) ? -mt[v] : mt[v]);
-  const T rlo = mt[0] - dv[0];
-  if (rlo > (T)p.eps_rho * T(2)) {
-    T kin = T(0), mag = T(0);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const T mu = (mt[1 + i] < T(0) ? -mt[1 + i] : mt[1 + i]) + dv[1 + i];
-      const T bu = (mt[5 + i] < T(0) ? -mt[5 + i] : mt[5 + i]) + dv[5 + i];
-      kin += mu * mu;
-      mag += bu * bu;
-    }
-    const T plo = (T)(g.gamma - 1.0) * (mt[4] - dv[4] - T(0.5) * kin / rlo - T(0.5) * mag);
-    if (plo > (T)p.eps_p * T(2) + mg * (mt[4] < T(0) ? -mt[4] : mt[4])) return true;
-  }
-  return false;
-}
-
 // FP32 form: screen every cell; the cells that do not clear it are appended to
 // list[0 .. sc->npos) (ballot + one atomic per warp) for k_pos.
-__global__ void k_pos_screen(Geom g, LimTabs lt, const float* __restrict__ w, dg_mhd_params p, DevScalars* sc,
+template <int DEG, int GLMF>
+__global__ void k_pos_screen(Geom gin, PosScreen ps, const float* __restrict__ w, DevScalars* sc,
                              int32_t* __restrict__ list) {
+  const Geom g = pin_geom<DEG, GLMF>(gin);
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool fail = c < g.ncell && !pos_screen(g, lt, w, p, c);
-  const unsigned bal = __ballot_sync(0xffffffffu, fail);
-  const int lane = threadIdx.x & 31;
-  unsigned at = 0;
-  if (lane == 0 && bal) at = atomicAdd(&sc->npos, (unsigned)__popc(bal));
-  at = __shfl_sync(0xffffffffu, at, 0);
-  if (fail) list[at + __popc(bal & ((1u << lane) - 1u))] = (int32_t)c;
+  const int64_t S = g.stride;
+  const bool fail = c < g.ncell && !pos_screen_rows(g, ps, [&](int r) { return w[(int64_t)r * S + c]; });
+  append_cells(fail, c, list, &sc->npos);
 }
 
 // Positivity procedure of one cell (Sec. 4.3).
@@ -744,6 +693,189 @@ __global__ void k_pos(Geom g, Tables<T> tb, LimTabs lt, T* w, double* wmean, dg_
     pos_cell(g, tb, lt, w, wmean, p, sc, list ? (int64_t)list[i] : i);
 }
 
+// FP32 form, 3D degrees 1-2: the positivity procedure of pos_cell on the
+// listed cells. A warp takes 32 list entries: each lane stages its cell's rows
+// (coalesced where the listed cells are neighbours), applies the mean floors
+// and the rigorous screen; the cells that stay open are then done one at a
+// time by the whole warp, lanes over the volume and face points, the limiting
+// factors being warp minima. Every point value is accumulated in the same
+// order as in pos_cell, so the two agree bit for bit.
+template <int DEG, int GLMF>
+__global__ void __launch_bounds__(128) k_pos_list(Geom gin, Tables<float> tb, LimTabs lt, float* w, double* wmean,
+                                                  dg_mhd_params p, DevScalars* sc, const int32_t* __restrict__ list) {
+  const Geom g = pin_geom<DEG, GLMF>(gin);
+  constexpr int N = (DEG + 1) * (DEG + 2) * (DEG + 3) / 6;
+  constexpr int NR = GLMF ? 9 * N : 5 * N + (DEG == 1 ? 11 : 26);
+  __shared__ float rows[4][NR][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float(*R)[32] = rows[warp];
+  const int64_t S = g.stride;
+  const int nm = g.glm ? 9 : 8;
+  const int npt = g.Qv + 2 * g.D * g.Qf;
+  const double gm1 = g.gamma - 1.0;
+  const float gm1t = (float)gm1;
+  const float screen_t = 1e-4f;
+  const double vol = g.dx * g.dx * g.dx;
+  auto pres = [&](const double* u) {
+    return gm1 * (u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0] -
+                  0.5 * (u[5] * u[5] + u[6] * u[6] + u[7] * u[7]));
+  };
+  auto wmin = [](double v) {
+    for (int o = 16; o; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+  };
+  const int64_t total = (int64_t)sc->npos;
+  for (int64_t i0 = ((int64_t)blockIdx.x * 4 + warp) * 32; i0 < total; i0 += (int64_t)gridDim.x * 4 * 32) {
+    const bool valid = i0 + lane < total;
+    const int64_t c = valid ? (int64_t)list[i0 + lane] : 0;
+    __syncwarp();  // the previous group's reads of R are done
+    double mr[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, m[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double pmean = 0.0;
+    bool open = false;
+    if (valid) {
+#pragma unroll
+      for (int r = 0; r < NR; ++r) R[r][lane] = w[(int64_t)r * S + c];
+      for (int k = 0; k < nm; ++k) mr[k] = wmean[k * S + c];
+      // physical mean state and the mean floors
+      for (int k = 0; k < 5; ++k) m[k] = mr[k];
+      if (g.glm) {
+        for (int k = 5; k < 9; ++k) m[k] = mr[k];
+      } else {
+        for (int j = 0; j < g.D; ++j)
+          for (int cc = 0; cc < g.DB; ++cc) m[5 + cc] += mr[5 + j] * (double)tb.L0[j * g.DB + cc];
+      }
+      bool changed_mean = false;
+      if (m[0] < p.eps_rho) {
+        atomicAdd(&sc->inj_mass, (p.eps_rho - m[0]) * vol);
+        m[0] = mr[0] = p.eps_rho;
+        changed_mean = true;
+      }
+      const double pm = pres(m);
+      if (pm < p.eps_p) {
+        const double dE = (p.eps_p - pm) / gm1;
+        atomicAdd(&sc->inj_energy, dE * vol);
+        m[4] += dE;
+        mr[4] += dE;
+        changed_mean = true;
+      }
+      if (changed_mean) {
+        atomicOr(&sc->floor_used, 1);
+        for (int k = 0; k < nm; ++k) {
+          wmean[k * S + c] = mr[k];
+          w[(int64_t)lmean_row(g, k) * S + c] = (float)mr[k];
+        }
+      }
+      pmean = pres(m);
+      // the rigorous screen of pos_cell
+      float devt[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      const int nlg = g.glm ? 8 : 5;
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        if (v >= nlg) continue;
+        for (int l = 1; l < g.n; ++l) devt[v] += fabsf(R[v * g.n + l][lane]);
+      }
+      if (!g.glm)
+        for (int j = g.D; j < g.ndiv; ++j) {
+          const float aj = fabsf(R[g.ldf0 + j][lane]);
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) devt[5 + cc] += aj * (float)lt.ldf_maxabs[j * 3 + cc];
+        }
+      double dev[8];
+      for (int v = 0; v < 8; ++v) dev[v] = (double)devt[v] * (1.0 + 1e-5) + 1e-5 * fabs(m[v]);
+      open = true;
+      const double rho_lo = m[0] - dev[0];
+      if (rho_lo > p.eps_rho) {
+        double kin = 0.0, mag = 0.0;
+        for (int k = 0; k < 3; ++k) {
+          const double mu = fabs(m[1 + k]) + dev[1 + k], bu = fabs(m[5 + k]) + dev[5 + k];
+          kin += mu * mu;
+          mag += bu * bu;
+        }
+        if (gm1 * (m[4] - dev[4] - 0.5 * kin / rho_lo - 0.5 * mag) > p.eps_p) open = false;
+      }
+    }
+    __syncwarp();  // R complete
+    unsigned todo = __ballot_sync(0xffffffffu, open);
+    while (todo) {
+      const int o = __ffs(todo) - 1;
+      todo &= todo - 1;
+      // the open cell of lane o, done by the whole warp
+      const int64_t co = __shfl_sync(0xffffffffu, c, o);
+      double mo[9], mro[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        mo[k] = __shfl_sync(0xffffffffu, m[k], o);
+        mro[k] = __shfl_sync(0xffffffffu, mr[k], o);
+      }
+      const double pmo = __shfl_sync(0xffffffffu, pmean, o);
+      // tau_rho over the volume and face points
+      double tau = 1.0;
+      for (int pt = lane; pt < npt; pt += 32) {
+        float acc = 0.f;
+        for (int l = 1; l < g.n; ++l) acc += R[l][o] * tb.Pp[l * npt + pt];
+        if ((float)mro[0] + acc < (float)p.eps_rho + screen_t * (float)mo[0]) {
+          double rd = mro[0];
+          for (int l = 1; l < g.n; ++l) rd += (double)R[l][o] * (double)tb.Pp[l * npt + pt];
+          if (rd < p.eps_rho) tau = fmin(tau, (mo[0] - p.eps_rho) / (mo[0] - rd));
+        }
+      }
+      tau = fmax(wmin(tau), 0.0);
+      // tau_p from the density-limited state m + tau (u - m)
+      double taup = 1.0;
+      const int nleg = g.glm ? 8 : 5;
+      for (int pt = lane; pt < npt; pt += 32) {
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          if (v >= nleg) continue;
+          for (int l = 1; l < g.n; ++l) acc[v] += R[v * g.n + l][o] * tb.Pp[l * npt + pt];
+        }
+        if (!g.glm)
+          for (int j = g.D; j < g.ndiv; ++j) {
+            const float wj = R[g.ldf0 + j][o];
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) acc[5 + cc] += wj * tb.Lp[(j * g.DB + cc) * npt + pt];
+          }
+        const float tt = (float)tau;
+        float uu[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) uu[v] = (float)mo[v] + tt * acc[v];
+        const float pq32 = gm1t * (uu[4] - 0.5f * (uu[1] * uu[1] + uu[2] * uu[2] + uu[3] * uu[3]) / uu[0] -
+                                   0.5f * (uu[5] * uu[5] + uu[6] * uu[6] + uu[7] * uu[7]));
+        if (pq32 < (float)p.eps_p + screen_t * fabsf(uu[4])) {
+          // FP64 recovery of this point's pressure
+          double u[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+          const int nps = g.glm ? 9 : 5;
+          for (int v = 0; v < nps; ++v) {
+            double sv = mro[v];
+            for (int l = 1; l < g.n; ++l) sv += (double)R[v * g.n + l][o] * (double)tb.Pp[l * npt + pt];
+            u[v] = sv;
+          }
+          if (!g.glm)
+            for (int j = 0; j < g.ndiv; ++j) {
+              const double wj = j < g.D ? mro[5 + j] : (double)R[g.ldf0 + j][o];
+              for (int cc = 0; cc < g.DB; ++cc) u[5 + cc] += wj * (double)tb.Lp[(j * g.DB + cc) * npt + pt];
+            }
+          for (int v = 0; v < 9; ++v) u[v] = mo[v] + tau * (u[v] - mo[v]);
+          const double pq = pres(u);
+          if (pq < p.eps_p) taup = fmin(taup, (pmo - p.eps_p) / (pmo - pq));
+        }
+      }
+      taup = fmax(wmin(taup), 0.0);
+      const double t = tau * taup;
+      if (t >= 1.0) continue;
+      if (lane == 0) atomicAdd(&sc->pos_cells, 1ull);
+      // scale every non-mean row by tau
+      for (int r = lane; r < NR; r += 32) {
+        bool mean = false;
+        for (int k = 0; k < nm; ++k)
+          if (lmean_row(g, k) == r) mean = true;
+        if (!mean) w[(int64_t)r * S + co] = (float)(t * (double)R[r][o]);
+      }
+    }
+  }
+}
+
 }  // namespace
 
 int upload_limiter_tables(Ctx& c) {
@@ -805,12 +937,20 @@ int upload_limiter_tables(Ctx& c) {
     lt.ldf_pl_f[i] = (float)lt.ldf_pl[i];
   }
   c.lim = lt;
+  PosScreen& ps = c.pscr;
+  std::memset(&ps, 0, sizeof(ps));
+  for (int i = 0; i < 9; ++i) ps.ldf_mean0[i] = (float)lt.ldf_mean0[i];
+  for (int i = 0; i < 64 * 3; ++i) ps.ldf_maxabs[i] = (float)lt.ldf_maxabs[i];
+  ps.eps_rho = (float)c.p.eps_rho;
+  ps.eps_p = (float)c.p.eps_p;
+  ps.gm1 = (float)(g.gamma - 1.0);
   return DG_OK;
 }
 
 int run_limiter(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t st) {
   const Geom& g = c.g;
   const unsigned nb = (unsigned)((g.ncell + 127) / 128);
+  bool screened = false;  // the positivity screen already ran (indicator: unflagged cells, TVB: flagged ones)
   if (c.p.limiter == DG_LIMIT_TVB || c.p.limiter == DG_LIMIT_MLP) {
     const int32_t* list = nullptr;
     unsigned nbt = nb;
@@ -821,8 +961,12 @@ int run_limiter(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t 
       // through the TVB procedure (a persistent grid walks the list)
       if (troubled) cudaMemsetAsync(troubled, 0, (size_t)g.ncell, st);
       cudaMemsetAsync(&c.sc->nflag, 0, sizeof(unsigned), st);
+      // FP32 form: the indicator's kernel also screens positivity on the rows it stages
+      const bool fuse_pos = c.p.positivity && c.p.precision == DG_PREC_FP32MIX;
+      if (fuse_pos) cudaMemsetAsync(&c.sc->npos, 0, sizeof(unsigned), st);
       c.prof.begin(6, st);
-      const int e = mlp_infer_launch(c, w, wmean, nullptr, nullptr, st, c.flag_list);
+      const int e =
+          mlp_infer_launch(c, w, wmean, nullptr, nullptr, st, c.flag_list, fuse_pos ? c.pos_list : nullptr, &screened);
       c.prof.end(6, st);
       if (e) return e;
       list = c.flag_list;
@@ -835,9 +979,13 @@ int run_limiter(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t 
     // them avoids FP64 conversions (the limiter never changes the means)
     const AmrNb an{c.amr.fL, c.amr.fR, c.amr.fmeta, c.amr.cstart, c.amr.centry, c.amr.dxc, c.amr.on ? 1 : 0};
     if (c.p.precision == DG_PREC_FP32MIX)
-      k_tvb<float><<<nbt, 128, 0, st>>>(g, c.lim, (float*)w, nullptr, troubled, list, c.p, c.sc, an);
+      screened ? k_tvb<float, true><<<nbt, 128, 0, st>>>(g, c.lim, (float*)w, nullptr, troubled, list, c.p, c.sc,
+                                                          an, c.pos_list, c.pscr)
+               : k_tvb<float, false><<<nbt, 128, 0, st>>>(g, c.lim, (float*)w, nullptr, troubled, list, c.p, c.sc,
+                                                           an, nullptr, c.pscr);
     else
-      k_tvb<double><<<nbt, 128, 0, st>>>(g, c.lim, (double*)w, nullptr, troubled, list, c.p, c.sc, an);
+      k_tvb<double, false><<<nbt, 128, 0, st>>>(g, c.lim, (double*)w, nullptr, troubled, list, c.p, c.sc, an,
+                                                nullptr, c.pscr);
     c.prof.end(3, st);
   }
   if (c.p.positivity) {
@@ -845,10 +993,20 @@ int run_limiter(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t 
     if (c.p.precision == DG_PREC_FP32MIX) {
       // cheap FP32 screen over every cell; the full procedure only on the few
       // cells it lists (so a warp never waits on one lane's FP64 recovery)
-      cudaMemsetAsync(&c.sc->npos, 0, sizeof(unsigned), st);
-      k_pos_screen<<<nb, 128, 0, st>>>(g, c.lim, (const float*)w, c.p, c.sc, c.pos_list);
+      if (!screened) {
+        cudaMemsetAsync(&c.sc->npos, 0, sizeof(unsigned), st);
+        auto scr = [&](auto k) { k<<<nb, 128, 0, st>>>(g, c.pscr, (const float*)w, c.sc, c.pos_list); };
+        if (!pinned_sizes_ok(g)) scr(k_pos_screen<-1, 0>);
+        else if (g.d == 2) g.glm ? scr(k_pos_screen<2, 1>) : scr(k_pos_screen<2, 0>);
+        else g.glm ? scr(k_pos_screen<1, 1>) : scr(k_pos_screen<1, 0>);
+      }
       const unsigned nbl = (unsigned)std::min<int64_t>(nb, (int64_t)c.nsm * 16);
-      k_pos<float><<<nbl, 128, 0, st>>>(g, c.t32, c.lim, (float*)w, wmean, c.p, c.sc, c.pos_list);
+      auto pw = [&](auto k) { k<<<(unsigned)c.nsm * 8, 128, 0, st>>>(g, c.t32, c.lim, (float*)w, wmean, c.p, c.sc,
+                                                                    c.pos_list); };
+      if (!pinned_sizes_ok(g) || !wmean)
+        k_pos<float><<<nbl, 128, 0, st>>>(g, c.t32, c.lim, (float*)w, wmean, c.p, c.sc, c.pos_list);
+      else if (g.d == 2) g.glm ? pw(k_pos_list<2, 1>) : pw(k_pos_list<2, 0>);
+      else g.glm ? pw(k_pos_list<1, 1>) : pw(k_pos_list<1, 0>);
       c.prof.launches[5] += 1;
     } else {
       k_pos<double><<<nb, 128, 0, st>>>(g, c.t64, c.lim, (double*)w, nullptr, c.p, c.sc, nullptr);

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "dg_mlp.cuh"
+#include "dg_pos.cuh"
 
 namespace dgmhd {
 
@@ -552,7 +553,7 @@ __global__ void __launch_bounds__(256) k_mlp_staged(Geom g, MlpTabs mt, const fl
                                                     const float* __restrict__ bias, float thresh,
                                                     uint8_t* __restrict__ flag, float* __restrict__ prob,
                                                     int32_t* __restrict__ list, DevScalars* __restrict__ sc,
-                                                    int nrs, int nbuf) {
+                                                    int nrs, int nbuf, int32_t* __restrict__ plist, PosScreen ps) {
   constexpr int LD1 = KP + 8, LD2 = HID + 8;
   extern __shared__ __align__(128) unsigned char smraw[];
   // nbuf tile buffers, each [nrs][128] own rows then [4][8][128] neighbour means
@@ -638,6 +639,18 @@ __global__ void __launch_bounds__(256) k_mlp_staged(Geom g, MlpTabs mt, const fl
                       prob);
     __syncwarp();
     if (list) compact_warp(lane < 16 && fl[warp * 16 + (lane & 15)] != 0, c0 + warp * 16 + lane, list, sc);
+    if (plist) {
+      // FP32 positivity screen on the staged rows (they hold every row the
+      // screen reads) of the cells not flagged; the TVB kernel screens the
+      // flagged ones after limiting them
+      Geom gp = g;
+      if constexpr (DEG <= 2) gp = pin_geom<DEG, GLM ? 1 : 0>(g);
+      const float* stb = buf + b * bufsz;
+      const int cl = warp * 16 + (lane & 15);
+      const bool need =
+          lane < 16 && fl[cl] == 0 && !pos_screen_rows(gp, ps, [&](int r) { return stb[r * 128 + cl]; });
+      append_cells(need, c0 + cl, plist, &sc->npos);
+    }
     __syncthreads();  // every read of this buffer and of xe done before they are refilled
   }
 }
@@ -829,7 +842,7 @@ static bool staged_ok(const Ctx& c, int* nrs, int* nbuf) {
 
 template <int KP, bool GLM, int DEG>
 static void staged_launch(Ctx& c, const void* w, uint8_t* flag, float* prob, cudaStream_t st, int32_t* list,
-                          int nrs, int nbuf) {
+                          int nrs, int nbuf, int32_t* plist) {
   const Geom& g = c.g;
   const size_t sm = staged_smem<KP>(nrs, nbuf);
   static size_t attr = 0;
@@ -844,12 +857,12 @@ static void staged_launch(Ctx& c, const void* w, uint8_t* flag, float* prob, cud
   const unsigned nb = (unsigned)std::min<int64_t>(g.ncell / 128, (int64_t)c.nsm * per_sm);
   k_mlp_staged<KP, GLM, DEG><<<nb, 256, sm, st>>>(g, c.mlp, (const float*)w, (const __nv_bfloat16*)c.mlp_w1,
                                                    (const __nv_bfloat16*)c.mlp_w2, c.mlp_bias, c.mlp_thresh, flag,
-                                                   prob, list, c.sc, nrs, nbuf);
+                                                   prob, list, c.sc, nrs, nbuf, plist, c.pscr);
 }
 
 template <typename T, int KP>
 static void infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* flag, float* prob, cudaStream_t st,
-                         int32_t* list) {
+                         int32_t* list, int32_t* plist, bool* screened) {
   int nrs = 0, nbuf = 1;
   if constexpr (sizeof(T) == 4) {
     if (staged_ok<KP>(c, &nrs, &nbuf)) {
@@ -857,8 +870,9 @@ static void infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* fl
       constexpr int DEG = KP == 64 ? 1 : KP == 112 ? 2 : KP == 192 ? 3 : 0;
       if constexpr (DEG > 0) {
         if (c.g.d == DEG) {
-          if (c.g.glm) staged_launch<KP, true, DEG>(c, w, flag, prob, st, list, nrs, nbuf);
-          else staged_launch<KP, false, DEG>(c, w, flag, prob, st, list, nrs, nbuf);
+          if (c.g.glm) staged_launch<KP, true, DEG>(c, w, flag, prob, st, list, nrs, nbuf, plist);
+          else staged_launch<KP, false, DEG>(c, w, flag, prob, st, list, nrs, nbuf, plist);
+          if (screened) *screened = plist != nullptr;
           return;
         }
       }
@@ -881,15 +895,16 @@ static void infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* fl
 }
 
 int mlp_infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* flag, float* prob, cudaStream_t st,
-                     int32_t* list) {
+                     int32_t* list, int32_t* pos_list, bool* screened) {
+  if (screened) *screened = false;
   if (!c.mlp_w1) return -1;
   const bool f32 = c.p.precision == DG_PREC_FP32MIX;
   // FP32 form: features read the float mirror of the FP64 means (exact copies)
   switch (c.mlp_kp) {
 #define KPCASE(K)                                                                 \
   case K:                                                                         \
-    if (f32) infer_launch<float, K>(c, w, nullptr, flag, prob, st, list);         \
-    else infer_launch<double, K>(c, w, nullptr, flag, prob, st, list);            \
+    if (f32) infer_launch<float, K>(c, w, nullptr, flag, prob, st, list, pos_list, screened); \
+    else infer_launch<double, K>(c, w, nullptr, flag, prob, st, list, nullptr, nullptr);      \
     break;
     KPCASE(64)
     KPCASE(80)
