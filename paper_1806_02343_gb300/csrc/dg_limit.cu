@@ -479,6 +479,31 @@ __global__ void k_pos_screen(Geom gin, PosScreen ps, const float* __restrict__ w
   append_cells(fail, c, list, &sc->npos);
 }
 
+// Whether the pressure of a point must be decided in FP64. uu: the point's
+// state in the working precision, m: the cell means, dev: per variable the sum
+// of |coefficients| beyond the mean times the basis bound, tt: the density
+// factor. scale_v = |m_v| + tt dev_v bounds every partial sum of u_v, so the
+// rounding of u_v is a few ulp of scale_v. The pressure is decided in the
+// working precision only if the density carries at most two digits of
+// cancellation and the pressure clears the floor by screen_t times the scale
+// of each of its terms (energy, kinetic, magnetic); screen_t = 0 (FP64): only
+// points below the floor.
+template <typename T>
+__device__ __forceinline__ bool pos_point_open(const T* uu, const double* m, const T* dev, T tt, T gm1, T eps_p,
+                                               T screen_t) {
+  T sc[8];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) sc[v] = (T)fabs(m[v]) + tt * dev[v];
+  const T kin = T(0.5) * (uu[1] * uu[1] + uu[2] * uu[2] + uu[3] * uu[3]) / uu[0];
+  const T mag = T(0.5) * (uu[5] * uu[5] + uu[6] * uu[6] + uu[7] * uu[7]);
+  const T pq = gm1 * (uu[4] - kin - mag);
+  if (screen_t == T(0)) return pq < eps_p;
+  if (uu[0] < T(1e-2) * sc[0]) return true;
+  const T kin_s = T(0.5) * (sc[1] * sc[1] + sc[2] * sc[2] + sc[3] * sc[3]) / uu[0];
+  const T mag_s = T(0.5) * (sc[5] * sc[5] + sc[6] * sc[6] + sc[7] * sc[7]);
+  return pq < eps_p + screen_t * gm1 * (sc[4] + kin_s + mag_s);
+}
+
 // Positivity procedure of one cell (Sec. 4.3).
 template <typename T>
 __device__ void pos_cell(const Geom& g, const Tables<T>& tb, const LimTabs& lt, T* w, double* wmean,
@@ -531,11 +556,13 @@ __device__ void pos_cell(const Geom& g, const Tables<T>& tb, const LimTabs& lt, 
   const int npt = g.Qv + 2 * g.D * g.Qf;
   const bool dbl = sizeof(T) == 8;
   const double pmean = pres(m);
+  // per variable, sum of |coefficients| beyond the mean (x |basis| bound): with
+  // |mean|, the scale of every point value, which bounds its rounding
+  T devt[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
   {
     // Rigorous screen: |P_l| <= 1 on the cell, |phi_j,c| <= ldf_maxabs, so
     // |u_v(x) - mean_v| <= dev_v everywhere; if the resulting lower bounds of
     // rho and p clear the floors, every point does and tau = 1.
-    T devt[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
     const int nlg = g.glm ? 8 : 5;
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
@@ -600,7 +627,7 @@ __device__ void pos_cell(const Geom& g, const Tables<T>& tb, const LimTabs& lt, 
     for (int k = 0; k < PC; ++k) {
       if (p0 + k >= npt) continue;
       const T rq = (T)mr[0] + acc[k];
-      if (rq < (T)p.eps_rho + screen_t * (T)m[0]) {
+      if (rq < (T)p.eps_rho + screen_t * ((T)fabs(m[0]) + devt[0])) {
         // near or below the floor: decide in FP64
         double rd = mr[0];
         for (int l = 1; l < g.n; ++l) rd += (double)w[(int64_t)l * S + c] * (double)Pval(l, p0 + k);
@@ -656,9 +683,7 @@ __device__ void pos_cell(const Geom& g, const Tables<T>& tb, const LimTabs& lt, 
       T uu[8];
 #pragma unroll
       for (int v = 0; v < 8; ++v) uu[v] = (T)m[v] + tt * acc[k][v];  // acc holds u - mean
-      const T pt = gm1t * (uu[4] - T(0.5) * (uu[1] * uu[1] + uu[2] * uu[2] + uu[3] * uu[3]) / uu[0] -
-                           T(0.5) * (uu[5] * uu[5] + uu[6] * uu[6] + uu[7] * uu[7]));
-      if (pt < (T)p.eps_p + screen_t * (uu[4] < T(0) ? -uu[4] : uu[4])) {
+      if (pos_point_open(uu, m, devt, tt, gm1t, (T)p.eps_p, screen_t)) {
         // FP64 recovery of this point's pressure (E - kinetic - magnetic cancels)
         double u[9];
         point_state(g, tb, (const T*)w, mr, c, p0 + k, u, true);
@@ -732,6 +757,9 @@ __global__ void __launch_bounds__(128) k_pos_list(Geom gin, Tables<float> tb, Li
     double mr[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, m[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     double pmean = 0.0;
     bool open = false;
+    // per variable, sum of |coefficients| beyond the mean (x |basis| bound): with
+    // |mean|, the scale of every point value, which bounds its FP32 rounding
+    float devt[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (valid) {
 #pragma unroll
       for (int r = 0; r < NR; ++r) R[r][lane] = w[(int64_t)r * S + c];
@@ -767,7 +795,6 @@ __global__ void __launch_bounds__(128) k_pos_list(Geom gin, Tables<float> tb, Li
       }
       pmean = pres(m);
       // the rigorous screen of pos_cell
-      float devt[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const int nlg = g.glm ? 8 : 5;
 #pragma unroll
       for (int v = 0; v < 8; ++v) {
@@ -808,12 +835,15 @@ __global__ void __launch_bounds__(128) k_pos_list(Geom gin, Tables<float> tb, Li
         mro[k] = __shfl_sync(0xffffffffu, mr[k], o);
       }
       const double pmo = __shfl_sync(0xffffffffu, pmean, o);
+      float dvo[8];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) dvo[v] = __shfl_sync(0xffffffffu, devt[v], o);
       // tau_rho over the volume and face points
       double tau = 1.0;
       for (int pt = lane; pt < npt; pt += 32) {
         float acc = 0.f;
         for (int l = 1; l < g.n; ++l) acc += R[l][o] * tb.Pp[l * npt + pt];
-        if ((float)mro[0] + acc < (float)p.eps_rho + screen_t * (float)mo[0]) {
+        if ((float)mro[0] + acc < (float)p.eps_rho + screen_t * (fabsf((float)mo[0]) + dvo[0])) {
           double rd = mro[0];
           for (int l = 1; l < g.n; ++l) rd += (double)R[l][o] * (double)tb.Pp[l * npt + pt];
           if (rd < p.eps_rho) tau = fmin(tau, (mo[0] - p.eps_rho) / (mo[0] - rd));
@@ -840,9 +870,7 @@ __global__ void __launch_bounds__(128) k_pos_list(Geom gin, Tables<float> tb, Li
         float uu[8];
 #pragma unroll
         for (int v = 0; v < 8; ++v) uu[v] = (float)mo[v] + tt * acc[v];
-        const float pq32 = gm1t * (uu[4] - 0.5f * (uu[1] * uu[1] + uu[2] * uu[2] + uu[3] * uu[3]) / uu[0] -
-                                   0.5f * (uu[5] * uu[5] + uu[6] * uu[6] + uu[7] * uu[7]));
-        if (pq32 < (float)p.eps_p + screen_t * fabsf(uu[4])) {
+        if (pos_point_open(uu, mo, dvo, tt, gm1t, (float)p.eps_p, screen_t)) {
           // FP64 recovery of this point's pressure
           double u[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
           const int nps = g.glm ? 9 : 5;

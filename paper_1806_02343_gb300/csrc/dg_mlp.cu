@@ -23,6 +23,7 @@
 
 #include "dg_mlp.cuh"
 #include "dg_pos.cuh"
+#include "dg_tc.cuh"
 
 namespace dgmhd {
 
@@ -554,30 +555,40 @@ __global__ void __launch_bounds__(256) k_mlp_staged(Geom g, MlpTabs mt, const fl
                                                     uint8_t* __restrict__ flag, float* __restrict__ prob,
                                                     int32_t* __restrict__ list, DevScalars* __restrict__ sc,
                                                     int nrs, int nbuf, int32_t* __restrict__ plist, PosScreen ps) {
-  constexpr int LD1 = KP + 8, LD2 = HID + 8;
   extern __shared__ __align__(128) unsigned char smraw[];
   // nbuf tile buffers, each [nrs][128] own rows then [4][8][128] neighbour means
   float* buf = reinterpret_cast<float*>(smraw);
   const int bufsz = (nrs + 32) * 128;
-  float* xe = buf + nbuf * bufsz;                // [2][8]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(xe + 16);  // [2]
-  __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(bar + 2);
-  __nv_bfloat16* W2s = W1s + HID * LD1;
-  __nv_bfloat16* Xs = W2s + HID * LD2;
-  float* bs = reinterpret_cast<float*>(Xs + 128 * LD1);
-  uint8_t* fl = reinterpret_cast<uint8_t*>(bs + 3 * HID + 1);
+  float* xe = buf + nbuf * bufsz;                        // [2][8]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(xe + 16);  // [0], [1]: tile copies; [2]: MMA completion
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 3);
+  // tensor-core operands in the K-major core-matrix layout (dg_tc.cuh)
+  __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(xe + 32);  // [HID][KP]
+  __nv_bfloat16* W2s = W1s + HID * KP;                              // [HID][HID]
+  __nv_bfloat16* Xs = W2s + HID * HID;  // [128][KP] features; then layer 1's output [128][HID]
+  float* bs = reinterpret_cast<float*>(Xs + 128 * KP);  // b1[64], b2[64], w3[64], b3
+  float* part = bs + 3 * HID + 1;                       // [2][128] halves of the output layer
+  uint8_t* fl = reinterpret_cast<uint8_t*>(part + 256);  // [128] flags of the tile
+  uint8_t* sfail = fl + 128;                              // [128] positivity screen not cleared
   // two threads per cell: t = cell + 128 * half; the halves split the feature work
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int cell = t & 127, half = t >> 7;
-  for (int i = t; i < HID * KP; i += 256) W1s[(i / KP) * LD1 + i % KP] = W1[i];
-  for (int i = t; i < HID * HID; i += 256) W2s[(i / HID) * LD2 + i % HID] = W2[i];
+  for (int i = t; i < HID * KP; i += 256) W1s[tc::kmajor_index(i / KP, i % KP, KP)] = W1[i];
+  for (int i = t; i < HID * HID; i += 256) W2s[tc::kmajor_index(i / HID, i % HID, HID)] = W2[i];
   for (int i = t; i < 3 * HID + 1; i += 256) bs[i] = bias[i];
   if (t == 0) {
     mbar_init(bar, 1);
     mbar_init(bar + 1, 1);
+    mbar_init(bar + 2, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // 128 tensor-memory columns: layer 1's accumulator [128 x 64], then layer 2's
+  if (warp == 0) tc::tmem_alloc(tslot, 128);
+  tc::fence_before_sync();
   __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tm = *tslot;
+  constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, HID);
   const int64_t S = g.stride;
   const int nin = 8 * g.n + 10 * g.D;
   const unsigned bytes = (unsigned)(nrs + 32) * 512u;
@@ -597,10 +608,19 @@ __global__ void __launch_bounds__(256) k_mlp_staged(Geom g, MlpTabs mt, const fl
         bulk_g2s(nbm + (q * 8 + k) * 128, w + (int64_t)mrow(g, k) * S + cn, 512u, bar + b);
     }
   };
+  // bounded wait of every thread on an mbarrier phase; false on timeout (all threads agree)
+  auto wait_all = [&](uint64_t* b, unsigned parity) {
+    bool ok = false;
+    const long long t0 = clock64();
+    while (!(ok = mbar_try_wait(b, parity)))
+      if (clock64() - t0 > kWaitCycles) break;
+    return __syncthreads_and(ok) != 0;
+  };
   // two buffers: the next tile's copies run while this one is computed
   if (nbuf == 2 && t == 0 && blockIdx.x < ntile) issue(blockIdx.x, 0);
   unsigned par = 0;  // bit b: phase parity of bar[b]
   int it = 0;
+  int mma_pending = -1;  // parity of an MMA commit not yet observed (timeout path), else -1
   for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x, ++it) {
     const int64_t c0 = tile * 128;
     const int b = nbuf == 2 ? (it & 1) : 0;
@@ -615,44 +635,122 @@ __global__ void __launch_bounds__(256) k_mlp_staged(Geom g, MlpTabs mt, const fl
     }
     // bounded wait for the tile's bytes (every thread polls: measured faster
     // than one polling warp and a block barrier)
-    bool ok = false;
-    const long long t0 = clock64();
-    while (!(ok = mbar_try_wait(bar + b, (par >> b) & 1u)))
-      if (clock64() - t0 > kWaitCycles) break;
-    if (!__syncthreads_and(ok)) {
+    if (!wait_all(bar + b, (par >> b) & 1u)) {
       if (t == 0) atomicOr(&sc->status, 8);
-      return;
+      break;
     }
     par ^= 1u << b;
+    const float* st = buf + b * bufsz;
     {
-      const float* st = buf + b * bufsz;
-      __nv_bfloat16* xr = Xs + cell * LD1;
-      if (half)
-        for (int q = nin; q < KP; ++q) xr[q] = __float2bfloat16_rn(0.f);
       using Dm = CtDims<GLM, DEG>;
+      if (half)
+        for (int q = nin; q < KP; ++q) Xs[tc::kmajor_index(cell, q, KP)] = __float2bfloat16_rn(0.f);
       features_of(Dm{}, mt, StagedSrc<Dm>{Dm{}, st, st + nrs * 128, xe, cell},
-                  [&](int q, float v) { xr[q] = __float2bfloat16_rn(v); }, half);
+                  [&](int q, float v) { Xs[tc::kmajor_index(cell, q, KP)] = __float2bfloat16_rn(v); }, half);
     }
-    __syncthreads();  // both halves of every row written
-    // eight warps, 16 cells (one m16 tile) each
-    infer_warp<KP, 1>(Xs + warp * 16 * LD1, W1s, W2s, bs, fl + warp * 16, c0 + warp * 16, g.ncell, thresh, flag,
-                      prob);
-    __syncwarp();
-    if (list) compact_warp(lane < 16 && fl[warp * 16 + (lane & 15)] != 0, c0 + warp * 16 + lane, list, sc);
-    if (plist) {
+    tc::fence_proxy_async();  // the features, written by every thread, become tensor-core operands
+    __syncthreads();
+    // layer 1 on the tensor core: D1[128 x 64] = X[128 x KP] W1^T (FP32 in tensor memory)
+    if (t == 0) {
+      tc::fence_after_sync();
+#pragma unroll
+      for (int kk = 0; kk < KP / 16; ++kk)
+        tc::mma_bf16(tm, tc::smem_desc(tc::smem_u32(Xs + kk * 128), 128, KP * 16),
+                     tc::smem_desc(tc::smem_u32(W1s + kk * 128), 128, KP * 16), IDESC, kk > 0);
+      tc::commit(bar + 2);
+    }
+    mma_pending = 0;
+    if (plist && t < 128) {
       // FP32 positivity screen on the staged rows (they hold every row the
-      // screen reads) of the cells not flagged; the TVB kernel screens the
-      // flagged ones after limiting them
+      // screen reads), while the tensor core runs layer 1; only the cells the
+      // indicator does not flag are listed from it (the TVB kernel screens the
+      // flagged ones after limiting them)
       Geom gp = g;
       if constexpr (DEG <= 2) gp = pin_geom<DEG, GLM ? 1 : 0>(g);
-      const float* stb = buf + b * bufsz;
-      const int cl = warp * 16 + (lane & 15);
-      const bool need =
-          lane < 16 && fl[cl] == 0 && !pos_screen_rows(gp, ps, [&](int r) { return stb[r * 128 + cl]; });
-      append_cells(need, c0 + cl, plist, &sc->npos);
+      sfail[t] = pos_screen_rows(gp, ps, [&](int r) { return st[r * 128 + t]; }) ? 0 : 1;
     }
-    __syncthreads();  // every read of this buffer and of xe done before they are refilled
+    if (!wait_all(bar + 2, 0)) {
+      if (t == 0) atomicOr(&sc->status, 8);
+      break;
+    }
+    mma_pending = -1;
+    tc::fence_after_sync();
+    // epilogue 1: warp w reads lanes 32 (w % 4).. of columns 32 (w / 4)..; bias,
+    // ReLU, BF16 into layer 2's A operand (over the features: layer 1 is done)
+    const int quarter = warp & 3, colh = warp >> 2, row = 32 * quarter + lane;
+    const uint32_t tlane = (uint32_t)(32 * quarter) << 16;
+    {
+      float v[32];
+      tc::ld32(tm + tlane + 32 * colh, v);
+      // 16-byte stores of eight BF16 values: the 8 rows of a core matrix fill 128 contiguous bytes
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        uint4 pk;
+        uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int k = 32 * colh + 8 * j + 2 * e;
+          pw[e] = pack_bf16(fmaxf(v[8 * j + 2 * e] + bs[k], 0.f), fmaxf(v[8 * j + 2 * e + 1] + bs[k + 1], 0.f));
+        }
+        *reinterpret_cast<uint4*>(Xs + tc::kmajor_index(row, 32 * colh + 8 * j, HID)) = pk;
+      }
+    }
+    tc::fence_before_sync();
+    tc::fence_proxy_async();
+    __syncthreads();
+    // layer 2: D2[128 x 64] = H1[128 x 64] W2^T, in columns 64..127
+    if (t == 0) {
+      tc::fence_after_sync();
+#pragma unroll
+      for (int kk = 0; kk < HID / 16; ++kk)
+        tc::mma_bf16(tm + HID, tc::smem_desc(tc::smem_u32(Xs + kk * 128), 128, HID * 16),
+                     tc::smem_desc(tc::smem_u32(W2s + kk * 128), 128, HID * 16), IDESC, kk > 0);
+      tc::commit(bar + 2);
+    }
+    mma_pending = 1;
+    if (!wait_all(bar + 2, 1)) {
+      if (t == 0) atomicOr(&sc->status, 8);
+      break;
+    }
+    mma_pending = -1;
+    tc::fence_after_sync();
+    // epilogue 2: bias, ReLU and this warp's half of the output layer's dot product
+    {
+      float v[32];
+      tc::ld32(tm + tlane + HID + 32 * colh, v);
+      float o = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) o += fmaxf(v[j] + bs[HID + 32 * colh + j], 0.f) * bs[2 * HID + 32 * colh + j];
+      part[colh * 128 + row] = o;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (t < 128) {
+      const float p = 1.f / (1.f + __expf(-(part[t] + part[128 + t] + bs[3 * HID])));
+      fl[t] = p > thresh ? 1 : 0;
+      const int64_t cc = c0 + t;
+      if (cc < g.ncell) {
+        if (flag) flag[cc] = p > thresh ? 1 : 0;
+        if (prob) prob[cc] = p;
+      }
+    }
+    __syncthreads();  // the flags of the tile are written
+    if (list) compact_warp(lane < 16 && fl[warp * 16 + (lane & 15)] != 0, c0 + warp * 16 + lane, list, sc);
+    if (plist) {
+      const int cl = warp * 16 + (lane & 15);
+      append_cells(lane < 16 && fl[cl] == 0 && sfail[cl] != 0, c0 + cl, plist, &sc->npos);
+    }
+    __syncthreads();  // every read of this buffer, of xe and of the flags done before they are refilled
   }
+  if (mma_pending >= 0) {
+    // a commit not observed in time: wait once more (bounded) before the columns are freed
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar + 2, (unsigned)mma_pending))
+      if (clock64() - t0 > kWaitCycles) break;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tm, 128);
 }
 
 }  // namespace
@@ -822,8 +920,8 @@ int mlp_set_weights(Ctx& c, const float* theta_dev, int nin, float thresh) {
 // shared memory of k_mlp_staged for nrs staged rows and nbuf tile buffers
 template <int KP>
 static size_t staged_smem(int nrs, int nbuf) {
-  return (size_t)nbuf * (nrs + 32) * 512 + 16 * 4 + 16 + (size_t)HID * (KP + 8) * 2 +
-         (size_t)HID * (HID + 8) * 2 + (size_t)128 * (KP + 8) * 2 + (3 * HID + 1) * sizeof(float) + 128;
+  return (size_t)nbuf * (nrs + 32) * 512 + 128 + (size_t)HID * KP * 2 + (size_t)HID * HID * 2 + (size_t)128 * KP * 2 +
+         (3 * HID + 1) * sizeof(float) + 256 * sizeof(float) + 256;
 }
 
 // the staged kernel applies: FP32 form, uniform 3D mesh, x-rows of whole
@@ -850,11 +948,23 @@ static void staged_launch(Ctx& c, const void* w, uint8_t* flag, float* prob, cud
     cudaFuncSetAttribute(k_mlp_staged<KP, GLM, DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = sm;
   }
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_staged<KP, GLM, DEG>, 256, sm) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  const unsigned nb = (unsigned)std::min<int64_t>(g.ncell / 128, (int64_t)c.nsm * per_sm);
+  // resident blocks per SM from the SM's shared memory (1 KB reserved per
+  // block) and the kernel's registers
+  static int per_sm = 0;
+  static size_t per_sm_smem = 0;
+  if (per_sm_smem != sm) {
+    per_sm_smem = sm;
+    int dev = 0, smem_sm = 0;
+    cudaFuncAttributes fa;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    per_sm = smem_sm / (int)(sm + 1024);
+    if (cudaFuncGetAttributes(&fa, k_mlp_staged<KP, GLM, DEG>) == cudaSuccess && fa.numRegs > 0)
+      per_sm = std::min(per_sm, 65536 / (fa.numRegs * 256));
+    per_sm = std::max(per_sm, 1);
+  }
+  // at most four blocks per SM: each holds 128 of the SM's 512 tensor-memory columns
+  const unsigned nb = (unsigned)std::min<int64_t>(g.ncell / 128, (int64_t)c.nsm * std::min(per_sm, 4));
   k_mlp_staged<KP, GLM, DEG><<<nb, 256, sm, st>>>(g, c.mlp, (const float*)w, (const __nv_bfloat16*)c.mlp_w1,
                                                    (const __nv_bfloat16*)c.mlp_w2, c.mlp_bias, c.mlp_thresh, flag,
                                                    prob, list, c.sc, nrs, nbuf, plist, c.pscr);
