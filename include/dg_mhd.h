@@ -270,6 +270,59 @@ int dg_mhd_rhs_noalloc(const dg_mesh_desc* mesh, int degree, int divB_scheme, do
                        const dg_mhd_params* p, double c_h, double damping_rate, const double* w,
                        double* rhs, void* stream);
 
+/* ---- Dynamic regridding of octree meshes (Sec. 5, adaptive mesh refinement) ----
+ * A regrid step: dg_mhd_amr_marks -> copy the marks to the host ->
+ * dg_mhd_regrid_plan (new leaves and their sources) -> dg_mhd_init on the new
+ * leaves -> copy the sources to the device -> dg_mhd_remap from the old
+ * context's state into the new context's state -> destroy the old context.
+ *
+ * Smoothness indicator (Sec. 5): s_max[c] = max over the monitored conserved
+ * components u (bit v of field_mask, v < 8, 9 with GLM psi; in the Powell form
+ * the B components are those of the LDF rows) and the directions a of
+ * S_a(u) = sum_{k=1..d} 2^(2k-1) int_[-1,1]^dim (d^k u / dxi_a^k)^2, in FP64.
+ * w, wmean: the state (layout of dg_mhd_rhs; wmean nullable); s_max: DEVICE
+ * FP64 array of n_cells. Any mesh. DG_E_ARG for an empty or out-of-range mask. */
+int dg_mhd_smoothness(dg_mhd_ctx* ctx, const void* w, const double* wmean, int field_mask, double* s_max,
+                      void* stream);
+
+/* Refinement marks of an octree context (Sec. 5): marks[c] (DEVICE int8,
+ * n_cells) = +1 if s_max[c] > 2 s_tilde and level < max_level; -1 for every
+ * member of a group of 2^dim sibling leaves whose restriction (the L2
+ * projection of the group onto the parent's basis) has S_a(u) < s_tilde / 2
+ * for every monitored u and direction, whose parent level is >= min_level and
+ * none of whose members is marked +1; 0 otherwise. s_max: caller-owned DEVICE
+ * FP64 scratch of n_cells (receives the smoothness indicator). Uniform
+ * contexts: DG_E_UNSUPPORTED. */
+int dg_mhd_amr_marks(dg_mhd_ctx* ctx, const void* w, const double* wmean, int field_mask, double s_tilde,
+                     int min_level, int max_level, int8_t* marks, double* s_max, void* stream);
+
+/* New leaf list from the marks (HOST arrays; synchronous, host only):
+ * refinement of the leaves marked +1 (up to level 17), 2:1 balance across
+ * faces by refining every leaf two levels coarser than a face neighbour until
+ * none is, then coarsening of the sibling groups with all members marked -1
+ * where the parent keeps the balance, to a fixed point. Writes *n_new and, if
+ * new_level, new_ijk and src are non-NULL and cap >= *n_new, the new leaves
+ * in Morton order (level, ijk[n_new*dim]) and per new leaf its source
+ * src[2i] = kind | octant << 4 (kind 0 copy, 1 prolongation from the old leaf
+ * src[2i+1] into child `octant`, 2 restriction of old sibling group src[2i+1])
+ * -- the array dg_mhd_remap takes. DG_E_ARG if cap is too small (*n_new is
+ * still set: call with NULL arrays to query the size). */
+int dg_mhd_regrid_plan(const dg_mhd_ctx* ctx, const int8_t* marks, int64_t cap, int8_t* new_level,
+                       int32_t* new_ijk, int32_t* src, int64_t* n_new);
+
+/* State of the new context from the old one (asynchronous on stream): per new
+ * leaf a copy, an L2 prolongation (parent octant onto the child's basis; the
+ * LDF rows under the vector inner product of eq. innerp) or an L2 restriction
+ * (the 2^dim children onto the parent's basis). src: DEVICE copy of the plan's
+ * src array; w_old/wmean_old and w_new/wmean_new: the two contexts' state
+ * buffers (wmean both NULL or both non-NULL; FP32 form: the means are
+ * remapped in FP64 and mirrored into the float rows). Both contexts must have
+ * the same dimension, degree, scheme and precision, the old one an octree.
+ * Source entries out of range are skipped and latch DG_E_ARG in the new
+ * context's status word. */
+int dg_mhd_remap(const dg_mhd_ctx* old_ctx, dg_mhd_ctx* new_ctx, const int32_t* src, const void* w_old,
+                 const double* wmean_old, void* w_new, double* wmean_new, void* stream);
+
 /* Releases every device allocation of ctx. ctx may be NULL. */
 void dg_mhd_destroy(dg_mhd_ctx* ctx);
 

@@ -24,7 +24,8 @@ EXPORTS = [
     "dg_mhd_rhs", "dg_mhd_limit", "dg_mhd_dt", "dg_mhd_step", "dg_mhd_last_dt", "dg_mhd_status",
     "dg_mhd_profile", "dg_mhd_profile_read", "dg_mhd_launch_count", "dg_mhd_rhs_noalloc", "dg_mhd_destroy",
     "dg_mhd_strerror", "dg_mhd_mlp_features", "dg_mhd_mlp_set_weights", "dg_mhd_mlp_infer", "dg_mhd_mlp_loss_grad",
-    "dg_mhd_mlp_train", "dg_mhd_counters", "dg_mhd_limiter_counts", "dg_mhd_divb",
+    "dg_mhd_mlp_train", "dg_mhd_counters", "dg_mhd_limiter_counts", "dg_mhd_divb", "dg_mhd_smoothness",
+    "dg_mhd_amr_marks", "dg_mhd_regrid_plan", "dg_mhd_remap",
 ]
 KIND_FACE, KIND_CELL, KIND_DT, KIND_LIMIT, KIND_PROJECT, KIND_POSITIVITY, KIND_MLP = range(7)
 
@@ -85,6 +86,10 @@ def lib():
     L.dg_mhd_limiter_counts.argtypes = [vp, i64p, i64p, i64p, ctypes.c_int]
     L.dg_mhd_divb.argtypes = [vp, vp, vp, vp, vp, vp]
     L.dg_mhd_limiter_counts.restype = ctypes.c_int
+    L.dg_mhd_smoothness.argtypes = [vp, vp, dp, ctypes.c_int, vp, vp]
+    L.dg_mhd_amr_marks.argtypes = [vp, vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+    L.dg_mhd_regrid_plan.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp, i64p]
+    L.dg_mhd_remap.argtypes = [vp, vp, vp, vp, dp, vp, dp, vp]
     L.dg_mhd_destroy.argtypes = [vp]
     L.dg_mhd_destroy.restype = None
     L.dg_mhd_strerror.argtypes = [ctypes.c_int]
@@ -205,6 +210,7 @@ class Solver:
         self.fp32 = self.params.precision == DG_PREC_FP32MIX
         self.dtype = torch.float32 if self.fp32 else torch.float64
         self.dim, self.degree = dim, degree
+        self.gamma, self.box_len = gamma, box_len
 
     def __del__(self):
         try:
@@ -280,6 +286,60 @@ class Solver:
         _check(lib().dg_mhd_counters(self.h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(e), 1 if reset else 0),
                "dg_mhd_counters")
         return {"pos_cells": n.value, "inj_mass": m.value, "inj_energy": e.value}
+
+    # ------------------------------------------------------------ regridding
+    def smoothness(self, w, wmean=None, fields=(0, 5, 6, 7)):
+        """Smoothness indicator (Sec. 5): per cell the max over the monitored
+        conserved components `fields` and the directions (FP64 device tensor)."""
+        import torch
+        s = torch.zeros(self.stride, dtype=torch.float64, device=w.device)
+        mask = sum(1 << f for f in fields)
+        _check(lib().dg_mhd_smoothness(self.h, _ptr(w), _ptr(wmean), mask, _ptr(s), _stream()), "dg_mhd_smoothness")
+        return s[: self.ncell]
+
+    def amr_marks(self, w, wmean=None, fields=(0, 5, 6, 7), s_tilde=0.03, min_level=0, max_level=17):
+        """Refinement marks (+1 refine, -1 coarsen with the sibling group, 0) and
+        the smoothness indicator, as device tensors."""
+        import torch
+        marks = torch.zeros(self.stride, dtype=torch.int8, device=w.device)
+        s = torch.zeros(self.stride, dtype=torch.float64, device=w.device)
+        mask = sum(1 << f for f in fields)
+        _check(lib().dg_mhd_amr_marks(self.h, _ptr(w), _ptr(wmean), mask, s_tilde, min_level, max_level,
+                                      _ptr(marks), _ptr(s), _stream()), "dg_mhd_amr_marks")
+        return marks[: self.ncell], s[: self.ncell]
+
+    def regrid_plan(self, marks):
+        """New leaves (levels int8, ijk int32 [n, dim]) and their sources
+        (int32 [n, 2]) from host or device marks."""
+        import numpy as np
+        mk = np.ascontiguousarray(marks.cpu().numpy() if hasattr(marks, "cpu") else np.asarray(marks), dtype=np.int8)
+        n = ctypes.c_int64()
+        _check(lib().dg_mhd_regrid_plan(self.h, mk.ctypes.data, 0, None, None, None, ctypes.byref(n)),
+               "dg_mhd_regrid_plan")
+        lev = np.zeros(n.value, dtype=np.int8)
+        ijk = np.zeros((n.value, self.dim), dtype=np.int32)
+        src = np.zeros((n.value, 2), dtype=np.int32)
+        _check(lib().dg_mhd_regrid_plan(self.h, mk.ctypes.data, n.value, lev.ctypes.data, ijk.ctypes.data,
+                                        src.ctypes.data, ctypes.byref(n)), "dg_mhd_regrid_plan")
+        return lev, ijk, src
+
+    def regrid(self, w, wmean=None, marks=None, **mark_args):
+        """One regrid step: marks (computed unless given), plan, a new Solver on
+        the new leaves with the same parameters, and the remapped state.
+        Returns (solver, w_new, wmean_new)."""
+        import torch
+        if marks is None:
+            marks, _ = self.amr_marks(w, wmean, **mark_args)
+        lev, ijk, src = self.regrid_plan(marks)
+        prm = {k: getattr(self.params, k) for k, _ in Params._fields_}
+        new = Solver(self.dim, None, self.degree, self.divb, gamma=self.gamma, box_len=self.box_len,
+                     levels=lev, ijk=ijk, **prm)
+        wn, wmn = new.alloc_state(w.device)
+        src_d = torch.as_tensor(src, device=w.device)
+        _check(lib().dg_mhd_remap(self.h, new.h, _ptr(src_d), _ptr(w), _ptr(wmean), _ptr(wn), _ptr(wmn), _stream()),
+               "dg_mhd_remap")
+        new.regrid_src = src
+        return new, wn, wmn
 
     def divb_norms(self, w, wmean=None, per_cell=False):
         """Divergence diagnostics (App. C): dict with the global norm, mean and

@@ -551,6 +551,9 @@ int build_amr(Ctx& c, const dg_mesh_desc* mesh) {
   }
   AmrHost& h = c.amr;
   h.on = true;
+  h.D = D;
+  h.hlevel.assign(mesh->level, mesh->level + N);
+  h.hijk.assign(mesh->ijk, mesh->ijk + N * D);
   h.nface = nf;
   h.maxent = maxent;
   h.nsub = nsub;
@@ -583,8 +586,8 @@ int build_amr(Ctx& c, const dg_mesh_desc* mesh) {
 
 void free_amr(Ctx& c) {
   AmrHost& h = c.amr;
-  void* ptrs[] = {h.fL,     h.fR,     h.fmeta,   h.cstart,  h.centry,  h.dxc,     h.Psub64,
-                  h.Lsub64, h.Psub32, h.Lsub32, h.Psub64p, h.Lsub64p, h.Psub32p, h.Lsub32p};
+  void* ptrs[] = {h.fL,     h.fR,     h.fmeta,    h.cstart,   h.centry,   h.dxc,    h.Psub64, h.Lsub64,
+                  h.Psub32, h.Lsub32, h.Psub64p, h.Lsub64p, h.Psub32p, h.Lsub32p, h.groups, h.lev_dev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h = AmrHost();

@@ -427,7 +427,7 @@ void dg_mhd_destroy(dg_mhd_ctx* ctx) {
   free_tables(c.t32);
   void* ptrs[] = {c.sc, c.face_buf, c.face_buf32, c.stage_buf[0], c.stage_buf[1], c.stage_buf[2],
                   c.stage_mean[0], c.stage_mean[1], c.stage_mean[2], c.cellscratch, c.proj_tab, c.proj_w,
-                  c.troubled, c.flag_list, c.pos_list, c.mlp_w1, c.mlp_w2, c.mlp_bias};
+                  c.troubled, c.flag_list, c.pos_list, c.mlp_w1, c.mlp_w2, c.mlp_bias, c.rg_tabs};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c.hb;
@@ -955,6 +955,7 @@ int dg_mhd_status(dg_mhd_ctx* ctx, int sync) {
   if (st & 1) return DG_E_NONFINITE;
   if (st & 4) return DG_E_CH;
   if (st & 8) return DG_E_TIMEOUT;
+  if (st & 16) return DG_E_ARG;  // a device-side argument check failed (remap sources)
   if (fl) return DG_W_FLOOR;
   return DG_OK;
 }

@@ -188,6 +188,16 @@ struct AmrHost {
   // the same with the point index zero-padded to a multiple of 4
   double *Psub64p = nullptr, *Lsub64p = nullptr;
   float *Psub32p = nullptr, *Lsub32p = nullptr;
+  // host copies of the leaves (regridding plans) and, built on first use, the
+  // groups of 2^D sibling leaves (octant order; sorted by parent level and
+  // coordinates) with the leaf levels on the device
+  int D = 0;
+  std::vector<int8_t> hlevel;
+  std::vector<int32_t> hijk;
+  int64_t ngroups = -1;
+  std::vector<int32_t> hgroups;
+  int32_t* groups = nullptr;
+  int8_t* lev_dev = nullptr;
 };
 
 struct Ctx {
@@ -218,6 +228,7 @@ struct Ctx {
   int32_t* flag_list = nullptr;    // cells flagged by the indicator in the current pass
   int32_t* pos_list = nullptr;     // cells the positivity screen could not clear in the current pass
   PosScreen pscr;                  // FP32 positivity screen tables
+  double* rg_tabs = nullptr;       // regridding tables (dg_regrid.cu), built on first use
   int64_t lim_passes = 0;          // limiter passes with TVB since the last counter reset
   int64_t lim_plain_cells = 0;     // cells the plain TVB detection examined since the last reset
   int nsm = 152;                   // streaming multiprocessors of the device

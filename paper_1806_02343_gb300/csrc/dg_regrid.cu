@@ -1,0 +1,654 @@
+// Dynamic regridding of octree meshes (Sec. 5, adaptive mesh refinement):
+// the smoothness indicator S_a(u) = sum_{k=1..d} 2^(2k-1) int (d^k u/dxi_a^k)^2
+// over the reference cell, refinement marks (refine a leaf if S_a(u) > 2 S~ for
+// some monitored field u and direction a; coarsen a group of sibling leaves if
+// the restriction of the group has S_a(u) < S~/2 for all), the new 2:1-balanced
+// leaf list, and the remap of the state by L2 prolongation (parent octant onto
+// the child's basis) and restriction (the children onto the parent's basis) --
+// per variable for the Legendre rows, under the vector inner product of eq.
+// innerp for the LDF rows.
+//
+// Tables (double, built here from the library's basis): S_a as quadratic forms
+// of a field's coefficients, QL[a][l][l'] for a Legendre variable and
+// QB[c][a][j][j'] for the B component c of the LDF rows; the prolongation
+// blocks PL[o][l][l'], PB[o][j][j'] (child row from parent row) and the
+// restriction blocks RL[o][l][l'], RB[o][j][j'] (parent row from child o's
+// row). Octant o: bit a set = upper half along axis a; child point xi maps to
+// the parent's (xi + s)/2, s_a = +1 or -1. All integrands are polynomials of
+// degree <= 2d: the Gauss rule with d+1 points per dimension is exact.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/dg_mhd.h"
+#include "dg_amr.cuh"
+#include "dg_basis.h"
+
+namespace dgmhd {
+
+namespace {
+
+// k-th derivative along `axis` of a basis polynomial at x
+double deriv_k(const Basis& B, const std::vector<double>& poly, int axis, int k, const double* x) {
+  double s = 0.0;
+  for (size_t i = 0; i < B.ms.exps.size(); ++i) {
+    const double c = poly[i];
+    if (c == 0.0) continue;
+    const auto& e = B.ms.exps[i];
+    if (e[axis] < k) continue;
+    double t = c;
+    for (int j = 0; j < k; ++j) t *= (double)(e[axis] - j);
+    for (int b = 0; b < B.D; ++b) {
+      const int p = e[b] - (b == axis ? k : 0);
+      for (int j = 0; j < p; ++j) t *= x[b];
+    }
+    s += t;
+  }
+  return s;
+}
+
+// tensor Gauss rule with d+1 points per dimension (last axis fastest)
+void gauss_tensor(int D, int npts, std::vector<std::array<double, 3>>& pts, std::vector<double>& wts) {
+  std::vector<double> x, w;
+  gauss_legendre(npts, x, w);
+  int total = 1;
+  for (int a = 0; a < D; ++a) total *= npts;
+  pts.assign(total, {0.0, 0.0, 0.0});
+  wts.assign(total, 1.0);
+  for (int q = 0; q < total; ++q) {
+    int r = q;
+    for (int a = D - 1; a >= 0; --a) {
+      pts[q][a] = x[r % npts];
+      wts[q] *= w[r % npts];
+      r /= npts;
+    }
+  }
+}
+
+}  // namespace
+
+// Layout of the regridding tables in one device buffer (offsets in doubles).
+struct RgLayout {
+  int n = 0, nd = 0, D = 3, no = 8;
+  size_t QL = 0, QB = 0, PL = 0, PB = 0, RL = 0, RB = 0, total = 0;
+  void set(int D_, int n_, int nd_) {
+    D = D_, n = n_, nd = nd_, no = 1 << D;
+    QL = 0;
+    QB = QL + (size_t)D * n * n;
+    PL = QB + (size_t)D * D * nd * nd;
+    PB = PL + (size_t)no * n * n;
+    RL = PB + (size_t)no * nd * nd;
+    RB = RL + (size_t)no * n * n;
+    total = RB + (size_t)no * nd * nd;
+  }
+};
+
+// Host tables of the context's basis; true on success.
+bool regrid_tables(const Basis& B, std::vector<double>& tab, RgLayout& L) {
+  const int D = B.D, d = B.d, n = B.n, nd = B.ndiv;
+  L.set(D, n, nd);
+  tab.assign(L.total, 0.0);
+  std::vector<std::array<double, 3>> pts;
+  std::vector<double> wts;
+  gauss_tensor(D, d + 1, pts, wts);
+  const int Q = (int)wts.size();
+  // smoothness forms: sum_k 2^(2k-1) sum_q w_q d^k phi d^k phi'
+  for (int a = 0; a < D; ++a) {
+    for (int k = 1; k <= d; ++k) {
+      const double fk = std::ldexp(1.0, 2 * k - 1);
+      std::vector<double> vl((size_t)n * Q), vb((size_t)D * nd * Q);
+      for (int q = 0; q < Q; ++q) {
+        for (int l = 0; l < n; ++l) vl[(size_t)l * Q + q] = deriv_k(B, B.leg[l], a, k, pts[q].data());
+        for (int c = 0; c < D; ++c)
+          for (int j = 0; j < nd; ++j) vb[((size_t)c * nd + j) * Q + q] = deriv_k(B, B.ldf[j][c], a, k, pts[q].data());
+      }
+      for (int l = 0; l < n; ++l)
+        for (int m = 0; m < n; ++m) {
+          double s = 0.0;
+          for (int q = 0; q < Q; ++q) s += wts[q] * vl[(size_t)l * Q + q] * vl[(size_t)m * Q + q];
+          tab[L.QL + ((size_t)a * n + l) * n + m] += fk * s;
+        }
+      for (int c = 0; c < D; ++c)
+        for (int j = 0; j < nd; ++j)
+          for (int m = 0; m < nd; ++m) {
+            double s = 0.0;
+            for (int q = 0; q < Q; ++q)
+              s += wts[q] * vb[((size_t)c * nd + j) * Q + q] * vb[((size_t)c * nd + m) * Q + q];
+            tab[L.QB + (((size_t)c * D + a) * nd + j) * nd + m] += fk * s;
+          }
+    }
+  }
+  // prolongation: child row from parent row, <phi_parent((xi+s)/2), phi_child(xi)> / M_child
+  for (int o = 0; o < L.no; ++o) {
+    double s[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) s[a] = ((o >> a) & 1) ? 1.0 : -1.0;
+    for (int q = 0; q < Q; ++q) {
+      double xp[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) xp[a] = 0.5 * (pts[q][a] + s[a]);
+      // basis values at the child point and at the mapped parent point
+      std::vector<double> lc_v(n), lp_v(n), bc_v((size_t)nd * D), bp_v((size_t)nd * D);
+      for (int l = 0; l < n; ++l) {
+        lc_v[l] = B.eval(B.leg[l], pts[q].data());
+        lp_v[l] = B.eval(B.leg[l], xp);
+      }
+      for (int j = 0; j < nd; ++j)
+        for (int c = 0; c < D; ++c) {
+          bc_v[(size_t)j * D + c] = B.eval(B.ldf[j][c], pts[q].data());
+          bp_v[(size_t)j * D + c] = B.eval(B.ldf[j][c], xp);
+        }
+      for (int lc = 0; lc < n; ++lc)
+        for (int lp = 0; lp < n; ++lp)
+          tab[L.PL + ((size_t)o * n + lc) * n + lp] += wts[q] * lc_v[lc] * lp_v[lp] / B.leg_mass[lc];
+      for (int jc = 0; jc < nd; ++jc)
+        for (int jp = 0; jp < nd; ++jp) {
+          double dot = 0.0;
+          for (int c = 0; c < D; ++c) dot += bc_v[(size_t)jc * D + c] * bp_v[(size_t)jp * D + c];
+          tab[L.PB + ((size_t)o * nd + jc) * nd + jp] += wts[q] * dot / B.ldf_mass[jc];
+        }
+    }
+  }
+  // restriction: parent row r from child o's row r' = 2^-D M_r' / M_r x prolongation(o)[r'][r]
+  const double inv = 1.0 / (double)L.no;
+  for (int o = 0; o < L.no; ++o) {
+    for (int lp = 0; lp < n; ++lp)
+      for (int lc = 0; lc < n; ++lc)
+        tab[L.RL + ((size_t)o * n + lp) * n + lc] =
+            inv * B.leg_mass[lc] / B.leg_mass[lp] * tab[L.PL + ((size_t)o * n + lc) * n + lp];
+    for (int jp = 0; jp < nd; ++jp)
+      for (int jc = 0; jc < nd; ++jc)
+        tab[L.RB + ((size_t)o * nd + jp) * nd + jc] =
+            inv * B.ldf_mass[jc] / B.ldf_mass[jp] * tab[L.PB + ((size_t)o * nd + jc) * nd + jp];
+  }
+  return true;
+}
+
+namespace {
+
+constexpr int RG_MAXN = 20;  // Legendre modes, degree <= 3
+constexpr int RG_MAXD = 50;  // LDF rows, degree <= 3
+
+struct RgDev {
+  const double* tab;
+  int n, nd, D, no;
+  size_t QL, QB, PL, PB, RL, RB;
+};
+
+// FP64 mean index of row r (mean rows: Legendre mode 0, the D degree-0 LDF
+// rows, the 2D B_z mode 0), -1 for the other rows
+__host__ __device__ __forceinline__ int rg_mean_index(const Geom& g, int r) {
+  if (g.glm || r < 5 * g.n) return r % g.n == 0 ? r / g.n : -1;
+  if (g.ldf0 >= 0 && r >= g.ldf0 && r < g.ldf0 + g.ndiv) return r - g.ldf0 < g.D ? 5 + (r - g.ldf0) : -1;
+  if (g.bz2d >= 0 && r == g.bz2d) return 7;
+  return -1;
+}
+
+// row r of cell c in FP64 (the FP64 mean where the row is a mean row)
+template <typename T>
+__device__ __forceinline__ double rg_val(const Geom& g, const T* w, const double* wmean, int r, int64_t c) {
+  if (wmean) {
+    const int m = rg_mean_index(g, r);
+    if (m >= 0) return wmean[(int64_t)m * g.stride + c];
+  }
+  return (double)w[(int64_t)r * g.stride + c];
+}
+
+// field v: Legendre rows base .. base+n-1 (ldf = false) or, in the Powell form,
+// B component v-5 of the LDF rows (ldf = true)
+__device__ __forceinline__ bool rg_field(const Geom& g, int v, int* base) {
+  if (g.glm || v < 5) {
+    *base = v * g.n;
+    return false;
+  }
+  if (g.D == 2 && v == 7) {
+    *base = g.bz2d;
+    return false;
+  }
+  *base = g.ldf0;
+  return true;
+}
+
+// max over the directions of S_a for field v from its coefficients coef[]
+__device__ double rg_smax(const Geom& g, const RgDev& L, int v, bool ldf, const double* coef) {
+  double smax = 0.0;
+  if (!ldf) {
+    for (int a = 0; a < g.D; ++a) {
+      const double* Q = L.tab + L.QL + (size_t)a * L.n * L.n;
+      double s = 0.0;
+      for (int l = 1; l < L.n; ++l) {  // mode 0 has no derivative
+        double t = 0.0;
+        for (int m = 1; m < L.n; ++m) t += Q[l * L.n + m] * coef[m];
+        s += coef[l] * t;
+      }
+      smax = fmax(smax, s);
+    }
+  } else {
+    const int cc = v - 5;
+    for (int a = 0; a < g.D; ++a) {
+      const double* Q = L.tab + L.QB + ((size_t)cc * L.D + a) * L.nd * L.nd;
+      double s = 0.0;
+      for (int j = g.D; j < L.nd; ++j) {  // the degree-0 rows have no derivative
+        double t = 0.0;
+        for (int m = g.D; m < L.nd; ++m) t += Q[j * L.nd + m] * coef[m];
+        s += coef[j] * t;
+      }
+      smax = fmax(smax, s);
+    }
+  }
+  return smax;
+}
+
+// s_max[c] = max over the monitored fields (bit v of mask) and directions of S_a
+template <typename T>
+__global__ void k_rg_smooth(Geom g, RgDev L, const T* __restrict__ w, const double* __restrict__ wmean, int mask,
+                            double* __restrict__ s_max) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  double coef[RG_MAXD];
+  double smax = 0.0;
+  for (int v = 0; v < g.V; ++v) {
+    if (!((mask >> v) & 1)) continue;
+    int base;
+    const bool ldf = rg_field(g, v, &base);
+    const int cnt = ldf ? L.nd : L.n;
+    for (int l = 0; l < cnt; ++l) coef[l] = rg_val(g, w, wmean, base + l, c);
+    smax = fmax(smax, rg_smax(g, L, v, ldf, coef));
+  }
+  s_max[c] = smax;
+}
+
+// refinement marks of the leaves
+__global__ void k_rg_marks_leaf(int64_t ncell, const int8_t* __restrict__ level, const double* __restrict__ s_max,
+                                double s_tilde, int max_level, int8_t* __restrict__ marks) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  marks[c] = (s_max[c] > 2.0 * s_tilde && level[c] < max_level) ? 1 : 0;
+}
+
+// coarsening marks of the sibling groups: the restriction of the group must
+// have S_a < S~/2 for every monitored field and direction
+template <typename T>
+__global__ void k_rg_marks_group(Geom g, RgDev L, const T* __restrict__ w, const double* __restrict__ wmean,
+                                 int mask, const int32_t* __restrict__ groups, int64_t ngroups,
+                                 const int8_t* __restrict__ level, double s_tilde, int min_level,
+                                 int8_t* __restrict__ marks) {
+  const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= ngroups) return;
+  const int32_t* mem = groups + gi * L.no;
+  if (level[mem[0]] - 1 < min_level) return;
+  for (int o = 0; o < L.no; ++o)
+    if (marks[mem[o]] == 1) return;
+  double coef[RG_MAXD];
+  for (int v = 0; v < g.V; ++v) {
+    if (!((mask >> v) & 1)) continue;
+    int base;
+    const bool ldf = rg_field(g, v, &base);
+    const int cnt = ldf ? L.nd : L.n;
+    const double* R = L.tab + (ldf ? L.RB : L.RL);
+    for (int l = 0; l < cnt; ++l) coef[l] = 0.0;
+    for (int o = 0; o < L.no; ++o)
+      for (int m = 0; m < cnt; ++m) {
+        const double x = rg_val(g, w, wmean, base + m, (int64_t)mem[o]);
+        if (x == 0.0) continue;
+        for (int l = 0; l < cnt; ++l) coef[l] += R[((size_t)o * cnt + l) * cnt + m] * x;
+      }
+    if (rg_smax(g, L, v, ldf, coef) >= 0.5 * s_tilde) return;
+  }
+  for (int o = 0; o < L.no; ++o) marks[mem[o]] = -1;
+}
+
+// new state: row r (blockIdx.y) of new cell i from its source (src[2i]: kind
+// 0 copy, 1 prolongation, 2 restriction in bits 0-3, octant in bits 4-7;
+// src[2i+1]: old cell, or old sibling group for a restriction)
+// (entries out of range are skipped and latch status bit 16: DG_E_ARG)
+template <typename T>
+__global__ void k_rg_remap(Geom go, Geom gn, RgDev L, const int32_t* __restrict__ src,
+                           const int32_t* __restrict__ groups, int64_t ngroups, const T* __restrict__ w,
+                           const double* __restrict__ wmean, T* __restrict__ wn, double* __restrict__ wmean_n,
+                           DevScalars* sc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (i >= gn.ncell) return;
+  const int code = src[2 * i], idx = src[2 * i + 1];
+  const int kind = code & 15, o = (code >> 4) & 15;
+  if (code < 0 || kind > 2 || o >= L.no || idx < 0 || (kind < 2 && idx >= go.ncell) ||
+      (kind == 2 && idx >= ngroups)) {
+    if (r == 0) atomicOr(&sc->status, 16);
+    return;
+  }
+  // the block of rows r belongs to
+  int base = (r / go.n) * go.n, cnt = L.n;
+  bool ldf = false;
+  if (go.ldf0 >= 0 && r >= go.ldf0 && r < go.ldf0 + go.ndiv) {
+    base = go.ldf0;
+    cnt = L.nd;
+    ldf = true;
+  } else if (go.bz2d >= 0 && r >= go.bz2d) {
+    base = go.bz2d;
+  }
+  const int l = r - base;
+  double v = 0.0;
+  if (kind == 0) {
+    v = rg_val(go, w, wmean, r, (int64_t)idx);
+  } else if (kind == 1) {
+    const double* P = L.tab + (ldf ? L.PB : L.PL) + ((size_t)o * cnt + l) * cnt;
+    for (int m = 0; m < cnt; ++m) v += P[m] * rg_val(go, w, wmean, base + m, (int64_t)idx);
+  } else {
+    const double* R = L.tab + (ldf ? L.RB : L.RL);
+    for (int oo = 0; oo < L.no; ++oo) {
+      const int64_t cc = groups[(int64_t)idx * L.no + oo];
+      const double* Ro = R + ((size_t)oo * cnt + l) * cnt;
+      for (int m = 0; m < cnt; ++m) v += Ro[m] * rg_val(go, w, wmean, base + m, cc);
+    }
+  }
+  wn[(int64_t)r * gn.stride + i] = (T)v;
+  const int mi = rg_mean_index(gn, r);
+  if (mi >= 0 && wmean_n) wmean_n[(int64_t)mi * gn.stride + i] = v;
+}
+
+}  // namespace
+
+namespace {
+
+// tables of the context (built and uploaded on first use)
+int ensure_tables(Ctx& c, RgDev& L) {
+  RgLayout lay;
+  std::vector<double> tab;
+  if (!c.rg_tabs) {
+    if (!regrid_tables(*c.hb, tab, lay)) return DG_E_ARG;
+    if (cudaMalloc(&c.rg_tabs, std::max<size_t>(1, tab.size()) * sizeof(double)) != cudaSuccess) return DG_E_CUDA;
+    if (cudaMemcpy(c.rg_tabs, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+      return DG_E_CUDA;
+  } else {
+    lay.set(c.hb->D, c.hb->n, c.hb->ndiv);
+  }
+  L = RgDev{c.rg_tabs, lay.n, lay.nd, lay.D, lay.no, lay.QL, lay.QB, lay.PL, lay.PB, lay.RL, lay.RB};
+  return DG_OK;
+}
+
+uint64_t leaf_key(int l, const int32_t* k, int D) {
+  const uint64_t z = D == 3 ? (uint64_t)k[2] : 0;
+  return ((uint64_t)l << 58) | ((uint64_t)k[0] << 38) | ((uint64_t)k[1] << 18) | z;
+}
+
+// sibling groups of an octree context (host and device), on first use
+int ensure_groups(Ctx& c) {
+  AmrHost& h = c.amr;
+  if (h.ngroups >= 0) return DG_OK;
+  const int D = h.D, no = 1 << D;
+  const int64_t N = (int64_t)h.hlevel.size();
+  std::unordered_map<uint64_t, int32_t> idx;
+  idx.reserve((size_t)N * 2);
+  for (int64_t i = 0; i < N; ++i) idx.emplace(leaf_key(h.hlevel[i], &h.hijk[i * D], D), (int32_t)i);
+  // parent key -> members (complete groups only), sorted by parent key
+  std::vector<std::pair<uint64_t, std::vector<int32_t>>> found;
+  std::unordered_map<uint64_t, char> seen;
+  for (int64_t i = 0; i < N; ++i) {
+    const int l = h.hlevel[i];
+    if (l == 0) continue;
+    int32_t pk[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) pk[a] = h.hijk[i * D + a] >> 1;
+    const uint64_t key = leaf_key(l - 1, pk, D);
+    if (!seen.emplace(key, 1).second) continue;
+    std::vector<int32_t> mem(no, -1);
+    bool all = true;
+    for (int o = 0; o < no; ++o) {
+      int32_t ck[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) ck[a] = 2 * pk[a] + ((o >> a) & 1);
+      auto it = idx.find(leaf_key(l, ck, D));
+      if (it == idx.end()) {
+        all = false;
+        break;
+      }
+      mem[o] = it->second;
+    }
+    if (all) found.emplace_back(key, std::move(mem));
+  }
+  std::sort(found.begin(), found.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  h.ngroups = (int64_t)found.size();
+  h.hgroups.assign((size_t)h.ngroups * no, 0);
+  for (int64_t gi = 0; gi < h.ngroups; ++gi)
+    for (int o = 0; o < no; ++o) h.hgroups[gi * no + o] = found[gi].second[o];
+  if (cudaMalloc(&h.groups, std::max<size_t>(1, h.hgroups.size()) * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&h.lev_dev, std::max<size_t>(1, (size_t)N)) != cudaSuccess)
+    return DG_E_CUDA;
+  if (!h.hgroups.empty() &&
+      cudaMemcpy(h.groups, h.hgroups.data(), h.hgroups.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+    return DG_E_CUDA;
+  if (cudaMemcpy(h.lev_dev, h.hlevel.data(), (size_t)N, cudaMemcpyHostToDevice) != cudaSuccess) return DG_E_CUDA;
+  return DG_OK;
+}
+
+bool mask_ok(const Geom& g, int mask) { return mask > 0 && (mask >> g.V) == 0; }
+
+inline cudaStream_t SR(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+}  // namespace dgmhd
+
+using namespace dgmhd;
+
+extern "C" int dg_mhd_smoothness(dg_mhd_ctx* ctx, const void* w, const double* wmean, int field_mask, double* s_max,
+                                 void* stream) {
+  if (!ctx || !w || !s_max) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  if (!mask_ok(c.g, field_mask) || c.g.d > 3) return DG_E_ARG;
+  RgDev L;
+  int e = ensure_tables(c, L);
+  if (e) return e;
+  const unsigned nb = (unsigned)((c.g.ncell + 127) / 128);
+  if (c.p.precision == DG_PREC_FP32MIX)
+    k_rg_smooth<float><<<nb, 128, 0, SR(stream)>>>(c.g, L, (const float*)w, wmean, field_mask, s_max);
+  else
+    k_rg_smooth<double><<<nb, 128, 0, SR(stream)>>>(c.g, L, (const double*)w, wmean, field_mask, s_max);
+  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
+}
+
+extern "C" int dg_mhd_amr_marks(dg_mhd_ctx* ctx, const void* w, const double* wmean, int field_mask, double s_tilde,
+                                int min_level, int max_level, int8_t* marks, double* s_max, void* stream) {
+  if (!ctx || !w || !marks || !s_max || !(s_tilde > 0.0)) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  if (!c.amr.on) return DG_E_UNSUPPORTED;
+  int e = dg_mhd_smoothness(ctx, w, wmean, field_mask, s_max, stream);
+  if (e) return e;
+  if ((e = ensure_groups(c))) return e;
+  RgDev L;
+  if ((e = ensure_tables(c, L))) return e;
+  const cudaStream_t st = SR(stream);
+  k_rg_marks_leaf<<<(unsigned)((c.g.ncell + 127) / 128), 128, 0, st>>>(c.g.ncell, c.amr.lev_dev, s_max, s_tilde,
+                                                                       max_level, marks);
+  if (c.amr.ngroups > 0) {
+    const unsigned nbg = (unsigned)((c.amr.ngroups + 127) / 128);
+    if (c.p.precision == DG_PREC_FP32MIX)
+      k_rg_marks_group<float><<<nbg, 128, 0, st>>>(c.g, L, (const float*)w, wmean, field_mask, c.amr.groups,
+                                                   c.amr.ngroups, c.amr.lev_dev, s_tilde, min_level, marks);
+    else
+      k_rg_marks_group<double><<<nbg, 128, 0, st>>>(c.g, L, (const double*)w, wmean, field_mask, c.amr.groups,
+                                                    c.amr.ngroups, c.amr.lev_dev, s_tilde, min_level, marks);
+  }
+  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
+}
+
+extern "C" int dg_mhd_remap(const dg_mhd_ctx* old_ctx, dg_mhd_ctx* new_ctx, const int32_t* src, const void* w_old,
+                            const double* wmean_old, void* w_new, double* wmean_new, void* stream) {
+  if (!old_ctx || !new_ctx || !src || !w_old || !w_new) return DG_E_ARG;
+  Ctx& co = const_cast<Ctx&>(old_ctx->c);
+  Ctx& cn = new_ctx->c;
+  const Geom &go = co.g, &gn = cn.g;
+  if (go.D != gn.D || go.d != gn.d || go.glm != gn.glm || go.nrows != gn.nrows ||
+      co.p.precision != cn.p.precision || !co.amr.on)
+    return DG_E_ARG;
+  if ((wmean_old == nullptr) != (wmean_new == nullptr)) return DG_E_ARG;
+  int e = ensure_groups(co);
+  if (e) return e;
+  RgDev L;
+  if ((e = ensure_tables(co, L))) return e;
+  if (gn.ncell == 0) return DG_OK;
+  const dim3 grid((unsigned)((gn.ncell + 127) / 128), (unsigned)gn.nrows);
+  if (co.p.precision == DG_PREC_FP32MIX)
+    k_rg_remap<float><<<grid, 128, 0, SR(stream)>>>(go, gn, L, src, co.amr.groups, co.amr.ngroups,
+                                                    (const float*)w_old, wmean_old, (float*)w_new, wmean_new, cn.sc);
+  else
+    k_rg_remap<double><<<grid, 128, 0, SR(stream)>>>(go, gn, L, src, co.amr.groups, co.amr.ngroups,
+                                                     (const double*)w_old, wmean_old, (double*)w_new, wmean_new, cn.sc);
+  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
+}
+
+namespace {
+
+struct PlanLeaf {
+  int l;
+  int32_t k[3];
+  int kind, idx, oct;  // source: 0 copy, 1 prolongation (octant oct), 2 restriction (group idx)
+};
+
+// level of the leaf of `mesh` containing the cube (l, k), -1 if the cube is split
+int covering_level(const std::unordered_map<uint64_t, PlanLeaf>& mesh, int l, const int32_t* k, int D) {
+  for (int ll = l; ll >= 0; --ll) {
+    int32_t kk[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) kk[a] = k[a] >> (l - ll);
+    if (mesh.count(leaf_key(ll, kk, D))) return ll;
+  }
+  return -1;
+}
+
+// no face neighbour of the cube (l, k) holds leaves of level >= l + 2
+bool face_ok(const std::unordered_map<uint64_t, PlanLeaf>& mesh, int l, const int32_t* k, int D) {
+  const int32_t n = 1 << l;
+  for (int a = 0; a < D; ++a)
+    for (int s = -1; s <= 1; s += 2) {
+      int32_t nk[3] = {k[0], k[1], k[2]};
+      nk[a] = (nk[a] + s + n) % n;
+      if (covering_level(mesh, l, nk, D) >= 0) continue;
+      int others[2], no = 0;
+      for (int b = 0; b < D; ++b)
+        if (b != a) others[no++] = b;
+      for (int t = 0; t < (1 << (D - 1)); ++t) {
+        int32_t ck[3] = {2 * nk[0], 2 * nk[1], 2 * nk[2]};
+        ck[a] += s < 0 ? 1 : 0;
+        for (int j = 0; j < no; ++j) ck[others[j]] += (t >> j) & 1;
+        if (covering_level(mesh, l + 1, ck, D) < 0) return false;
+      }
+    }
+  return true;
+}
+
+void insert_children(std::unordered_map<uint64_t, PlanLeaf>& mesh, int l, const int32_t* k, int idx, int D) {
+  for (int o = 0; o < (1 << D); ++o) {
+    PlanLeaf c{l + 1, {0, 0, 0}, 1, idx, o};
+    for (int a = 0; a < D; ++a) c.k[a] = 2 * k[a] + ((o >> a) & 1);
+    mesh[leaf_key(c.l, c.k, D)] = c;
+  }
+}
+
+}  // namespace
+
+// New leaf list from the marks (host): refine the leaves marked +1, then 2:1
+// balance by refining every leaf two levels coarser than a face neighbour
+// (until none is), then coarsen the sibling groups whose members are all
+// marked -1 where the parent keeps the balance (until no further group can).
+// Output in Morton order (lower corner at the finest level, then level).
+extern "C" int dg_mhd_regrid_plan(const dg_mhd_ctx* ctx, const int8_t* marks, int64_t cap, int8_t* new_level,
+                                  int32_t* new_ijk, int32_t* src, int64_t* n_new) {
+  if (!ctx || !marks || !n_new) return DG_E_ARG;
+  Ctx& c = const_cast<Ctx&>(ctx->c);
+  if (!c.amr.on) return DG_E_UNSUPPORTED;
+  int e = ensure_groups(c);
+  if (e) return e;
+  const AmrHost& h = c.amr;
+  const int D = h.D, no = 1 << D;
+  const int64_t N = (int64_t)h.hlevel.size();
+  std::unordered_map<uint64_t, PlanLeaf> mesh;
+  mesh.reserve((size_t)N * 2);
+  for (int64_t i = 0; i < N; ++i) {
+    const int l = h.hlevel[i];
+    const int32_t* k = &h.hijk[i * D];
+    if (marks[i] == 1 && l < 17) {
+      insert_children(mesh, l, k, (int)i, D);
+    } else {
+      PlanLeaf p{l, {0, 0, 0}, 0, (int)i, 0};
+      for (int a = 0; a < D; ++a) p.k[a] = k[a];
+      mesh[leaf_key(l, p.k, D)] = p;
+    }
+  }
+  // 2:1 balance by refinement of the coarser side
+  for (bool changed = true; changed;) {
+    changed = false;
+    std::vector<PlanLeaf> copies;
+    for (const auto& kv : mesh)
+      if (kv.second.kind == 0) copies.push_back(kv.second);
+    for (const PlanLeaf& p : copies) {
+      if (face_ok(mesh, p.l, p.k, D)) continue;
+      mesh.erase(leaf_key(p.l, p.k, D));
+      insert_children(mesh, p.l, p.k, p.idx, D);
+      changed = true;
+    }
+  }
+  // coarsening where the parent keeps the balance, to a fixed point
+  std::vector<char> done((size_t)std::max<int64_t>(h.ngroups, 0), 0);
+  for (bool changed = true; changed;) {
+    changed = false;
+    for (int64_t gi = 0; gi < h.ngroups; ++gi) {
+      if (done[gi]) continue;
+      const int32_t* mem = &h.hgroups[gi * no];
+      bool cand = true;
+      for (int o = 0; o < no && cand; ++o) cand = marks[mem[o]] == -1;
+      if (!cand) continue;
+      const int l = h.hlevel[mem[0]];
+      int32_t pk[3] = {0, 0, 0};
+      for (int a = 0; a < D; ++a) pk[a] = h.hijk[(int64_t)mem[0] * D + a] >> 1;
+      bool intact = true;
+      for (int o = 0; o < no && intact; ++o) {
+        auto it = mesh.find(leaf_key(l, &h.hijk[(int64_t)mem[o] * D], D));
+        intact = it != mesh.end() && it->second.kind == 0 && it->second.idx == mem[o];
+      }
+      if (!intact) continue;
+      for (int o = 0; o < no; ++o) mesh.erase(leaf_key(l, &h.hijk[(int64_t)mem[o] * D], D));
+      PlanLeaf p{l - 1, {pk[0], pk[1], pk[2]}, 2, (int)gi, 0};
+      mesh[leaf_key(l - 1, pk, D)] = p;
+      if (face_ok(mesh, l - 1, pk, D)) {
+        done[gi] = 1;
+        changed = true;
+      } else {
+        mesh.erase(leaf_key(l - 1, pk, D));
+        for (int o = 0; o < no; ++o) {
+          PlanLeaf q{l, {0, 0, 0}, 0, mem[o], 0};
+          for (int a = 0; a < D; ++a) q.k[a] = h.hijk[(int64_t)mem[o] * D + a];
+          mesh[leaf_key(l, q.k, D)] = q;
+        }
+      }
+    }
+  }
+  // Morton order
+  std::vector<PlanLeaf> out;
+  out.reserve(mesh.size());
+  int lmax = 0;
+  for (const auto& kv : mesh) {
+    out.push_back(kv.second);
+    lmax = std::max(lmax, kv.second.l);
+  }
+  auto zkey = [&](const PlanLeaf& p) {
+    uint64_t z = 0;
+    for (int bit = lmax; bit >= 0; --bit)
+      for (int a = D - 1; a >= 0; --a) z = (z << 1) | (((uint64_t)p.k[a] << (lmax - p.l)) >> bit & 1u);
+    return z;
+  };
+  std::sort(out.begin(), out.end(), [&](const PlanLeaf& a, const PlanLeaf& b) {
+    const uint64_t za = zkey(a), zb = zkey(b);
+    return za != zb ? za < zb : a.l < b.l;
+  });
+  *n_new = (int64_t)out.size();
+  if (!new_level || !new_ijk || !src) return DG_OK;  // size query
+  if (cap < (int64_t)out.size()) return DG_E_ARG;
+  for (size_t i = 0; i < out.size(); ++i) {
+    new_level[i] = (int8_t)out[i].l;
+    for (int a = 0; a < D; ++a) new_ijk[i * D + a] = out[i].k[a];
+    src[2 * i] = out[i].kind | (out[i].oct << 4);
+    src[2 * i + 1] = out[i].idx;
+  }
+  return DG_OK;
+}
