@@ -198,6 +198,9 @@ struct AmrHost {
   std::vector<int32_t> hgroups;
   int32_t* groups = nullptr;
   int8_t* lev_dev = nullptr;
+  // the last regrid plan (6 ints per new leaf) and a hash of the marks it was made from
+  uint64_t plan_hash = 0;
+  std::vector<int32_t> plan;
 };
 
 struct Ctx {

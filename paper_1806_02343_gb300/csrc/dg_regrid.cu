@@ -300,53 +300,73 @@ __global__ void k_rg_marks_group(Geom g, RgDev L, const T* __restrict__ w, const
   for (int o = 0; o < L.no; ++o) marks[mem[o]] = -1;
 }
 
-// new state: row r (blockIdx.y) of new cell i from its source (src[2i]: kind
-// 0 copy, 1 prolongation, 2 restriction in bits 0-3, octant in bits 4-7;
-// src[2i+1]: old cell, or old sibling group for a restriction)
-// (entries out of range are skipped and latch status bit 16: DG_E_ARG)
+// number of row blocks: the Legendre variables, then the LDF rows, then (2D
+// Powell) the B_z Legendre rows
+__host__ __device__ inline int rg_nblocks(const Geom& g) {
+  return (g.glm ? 9 : 5) + (g.ldf0 >= 0 ? 1 : 0) + (g.bz2d >= 0 ? 1 : 0);
+}
+
+// new state: the rows of block b (blockIdx.y) of new cell i from its source
+// (src[2i]: kind 0 copy, 1 prolongation, 2 restriction in bits 0-3, octant in
+// bits 4-7; src[2i+1]: old cell, or old sibling group for a restriction). Each
+// thread reads its sources once. Entries out of range are skipped and latch
+// status bit 16 (DG_E_ARG).
 template <typename T>
 __global__ void k_rg_remap(Geom go, Geom gn, RgDev L, const int32_t* __restrict__ src,
                            const int32_t* __restrict__ groups, int64_t ngroups, const T* __restrict__ w,
                            const double* __restrict__ wmean, T* __restrict__ wn, double* __restrict__ wmean_n,
                            DevScalars* sc) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = blockIdx.y;
+  const int b = blockIdx.y;
   if (i >= gn.ncell) return;
   const int code = src[2 * i], idx = src[2 * i + 1];
   const int kind = code & 15, o = (code >> 4) & 15;
   if (code < 0 || kind > 2 || o >= L.no || idx < 0 || (kind < 2 && idx >= go.ncell) ||
       (kind == 2 && idx >= ngroups)) {
-    if (r == 0) atomicOr(&sc->status, 16);
+    if (b == 0) atomicOr(&sc->status, 16);
     return;
   }
-  // the block of rows r belongs to
-  int base = (r / go.n) * go.n, cnt = L.n;
+  const int nleg = go.glm ? 9 : 5;
+  int base = b * go.n, cnt = L.n;
   bool ldf = false;
-  if (go.ldf0 >= 0 && r >= go.ldf0 && r < go.ldf0 + go.ndiv) {
+  if (b == nleg && go.ldf0 >= 0) {
     base = go.ldf0;
     cnt = L.nd;
     ldf = true;
-  } else if (go.bz2d >= 0 && r >= go.bz2d) {
+  } else if (b >= nleg) {
     base = go.bz2d;
   }
-  const int l = r - base;
-  double v = 0.0;
+  double in[RG_MAXD], out[RG_MAXD];
   if (kind == 0) {
-    v = rg_val(go, w, wmean, r, (int64_t)idx);
+    for (int l = 0; l < cnt; ++l) out[l] = rg_val(go, w, wmean, base + l, (int64_t)idx);
   } else if (kind == 1) {
-    const double* P = L.tab + (ldf ? L.PB : L.PL) + ((size_t)o * cnt + l) * cnt;
-    for (int m = 0; m < cnt; ++m) v += P[m] * rg_val(go, w, wmean, base + m, (int64_t)idx);
+    for (int m = 0; m < cnt; ++m) in[m] = rg_val(go, w, wmean, base + m, (int64_t)idx);
+    const double* P = L.tab + (ldf ? L.PB : L.PL) + (size_t)o * cnt * cnt;
+    for (int l = 0; l < cnt; ++l) {
+      double v = 0.0;
+      for (int m = 0; m < cnt; ++m) v += P[l * cnt + m] * in[m];
+      out[l] = v;
+    }
   } else {
+    for (int l = 0; l < cnt; ++l) out[l] = 0.0;
     const double* R = L.tab + (ldf ? L.RB : L.RL);
     for (int oo = 0; oo < L.no; ++oo) {
       const int64_t cc = groups[(int64_t)idx * L.no + oo];
-      const double* Ro = R + ((size_t)oo * cnt + l) * cnt;
-      for (int m = 0; m < cnt; ++m) v += Ro[m] * rg_val(go, w, wmean, base + m, cc);
+      for (int m = 0; m < cnt; ++m) in[m] = rg_val(go, w, wmean, base + m, cc);
+      const double* Ro = R + (size_t)oo * cnt * cnt;
+      for (int l = 0; l < cnt; ++l) {
+        double v = out[l];
+        for (int m = 0; m < cnt; ++m) v += Ro[l * cnt + m] * in[m];
+        out[l] = v;
+      }
     }
   }
-  wn[(int64_t)r * gn.stride + i] = (T)v;
-  const int mi = rg_mean_index(gn, r);
-  if (mi >= 0 && wmean_n) wmean_n[(int64_t)mi * gn.stride + i] = v;
+  for (int l = 0; l < cnt; ++l) {
+    const int r = base + l;
+    wn[(int64_t)r * gn.stride + i] = (T)out[l];
+    const int mi = rg_mean_index(gn, r);
+    if (mi >= 0 && wmean_n) wmean_n[(int64_t)mi * gn.stride + i] = out[l];
+  }
 }
 
 }  // namespace
@@ -488,7 +508,7 @@ extern "C" int dg_mhd_remap(const dg_mhd_ctx* old_ctx, dg_mhd_ctx* new_ctx, cons
   RgDev L;
   if ((e = ensure_tables(co, L))) return e;
   if (gn.ncell == 0) return DG_OK;
-  const dim3 grid((unsigned)((gn.ncell + 127) / 128), (unsigned)gn.nrows);
+  const dim3 grid((unsigned)((gn.ncell + 127) / 128), (unsigned)rg_nblocks(go));
   if (co.p.precision == DG_PREC_FP32MIX)
     k_rg_remap<float><<<grid, 128, 0, SR(stream)>>>(go, gn, L, src, co.amr.groups, co.amr.ngroups,
                                                     (const float*)w_old, wmean_old, (float*)w_new, wmean_new, cn.sc);
@@ -547,19 +567,10 @@ void insert_children(std::unordered_map<uint64_t, PlanLeaf>& mesh, int l, const 
 
 }  // namespace
 
-// New leaf list from the marks (host): refine the leaves marked +1, then 2:1
-// balance by refining every leaf two levels coarser than a face neighbour
-// (until none is), then coarsen the sibling groups whose members are all
-// marked -1 where the parent keeps the balance (until no further group can).
-// Output in Morton order (lower corner at the finest level, then level).
-extern "C" int dg_mhd_regrid_plan(const dg_mhd_ctx* ctx, const int8_t* marks, int64_t cap, int8_t* new_level,
-                                  int32_t* new_ijk, int32_t* src, int64_t* n_new) {
-  if (!ctx || !marks || !n_new) return DG_E_ARG;
-  Ctx& c = const_cast<Ctx&>(ctx->c);
-  if (!c.amr.on) return DG_E_UNSUPPORTED;
-  int e = ensure_groups(c);
-  if (e) return e;
-  const AmrHost& h = c.amr;
+namespace {
+
+// the planning rules of dg_mhd_regrid_plan; out: the new leaves in Morton order
+void plan_leaves(const AmrHost& h, const int8_t* marks, std::vector<PlanLeaf>& out) {
   const int D = h.D, no = 1 << D;
   const int64_t N = (int64_t)h.hlevel.size();
   std::unordered_map<uint64_t, PlanLeaf> mesh;
@@ -575,18 +586,36 @@ extern "C" int dg_mhd_regrid_plan(const dg_mhd_ctx* ctx, const int8_t* marks, in
       mesh[leaf_key(l, p.k, D)] = p;
     }
   }
-  // 2:1 balance by refinement of the coarser side
-  for (bool changed = true; changed;) {
-    changed = false;
-    std::vector<PlanLeaf> copies;
-    for (const auto& kv : mesh)
-      if (kv.second.kind == 0) copies.push_back(kv.second);
-    for (const PlanLeaf& p : copies) {
-      if (face_ok(mesh, p.l, p.k, D)) continue;
-      mesh.erase(leaf_key(p.l, p.k, D));
-      insert_children(mesh, p.l, p.k, p.idx, D);
-      changed = true;
-    }
+  // 2:1 balance by refinement of the coarser side. The old mesh is balanced,
+  // so only the leaves next to a refined cube can break it: a worklist of the
+  // leaves covering the face neighbours of every refined cube (same fixed
+  // point as checking every leaf until none changes).
+  std::vector<uint64_t> work;
+  auto push_neighbours = [&](int l, const int32_t* k) {
+    const int32_t n = 1 << l;
+    for (int a = 0; a < D; ++a)
+      for (int s = -1; s <= 1; s += 2) {
+        int32_t nk[3] = {k[0], k[1], k[2]};
+        nk[a] = (nk[a] + s + n) % n;
+        const int lv = covering_level(mesh, l, nk, D);
+        if (lv < 0 || lv >= l) continue;  // split or same level: no two-level jump here
+        int32_t ck[3] = {0, 0, 0};
+        for (int b = 0; b < D; ++b) ck[b] = nk[b] >> (l - lv);
+        work.push_back(leaf_key(lv, ck, D));
+      }
+  };
+  for (int64_t i = 0; i < N; ++i)
+    if (marks[i] == 1 && h.hlevel[i] < 17) push_neighbours(h.hlevel[i], &h.hijk[i * D]);
+  while (!work.empty()) {
+    const uint64_t key = work.back();
+    work.pop_back();
+    auto it = mesh.find(key);
+    if (it == mesh.end() || it->second.kind != 0) continue;
+    const PlanLeaf p = it->second;
+    if (face_ok(mesh, p.l, p.k, D)) continue;
+    mesh.erase(it);
+    insert_children(mesh, p.l, p.k, p.idx, D);
+    push_neighbours(p.l, p.k);
   }
   // coarsening where the parent keeps the balance, to a fixed point
   std::vector<char> done((size_t)std::max<int64_t>(h.ngroups, 0), 0);
@@ -624,7 +653,7 @@ extern "C" int dg_mhd_regrid_plan(const dg_mhd_ctx* ctx, const int8_t* marks, in
     }
   }
   // Morton order
-  std::vector<PlanLeaf> out;
+  out.clear();
   out.reserve(mesh.size());
   int lmax = 0;
   for (const auto& kv : mesh) {
@@ -637,18 +666,59 @@ extern "C" int dg_mhd_regrid_plan(const dg_mhd_ctx* ctx, const int8_t* marks, in
       for (int a = D - 1; a >= 0; --a) z = (z << 1) | (((uint64_t)p.k[a] << (lmax - p.l)) >> bit & 1u);
     return z;
   };
-  std::sort(out.begin(), out.end(), [&](const PlanLeaf& a, const PlanLeaf& b) {
-    const uint64_t za = zkey(a), zb = zkey(b);
-    return za != zb ? za < zb : a.l < b.l;
-  });
-  *n_new = (int64_t)out.size();
+  std::vector<std::pair<std::pair<uint64_t, int>, size_t>> order(out.size());
+  for (size_t i = 0; i < out.size(); ++i) order[i] = {{zkey(out[i]), out[i].l}, i};
+  std::sort(order.begin(), order.end());
+  std::vector<PlanLeaf> sorted(out.size());
+  for (size_t i = 0; i < out.size(); ++i) sorted[i] = out[order[i].second];
+  out.swap(sorted);
+}
+
+}  // namespace
+
+// New leaf list from the marks (host): refine the leaves marked +1, then 2:1
+// balance by refining every leaf two levels coarser than a face neighbour
+// (until none is), then coarsen the sibling groups whose members are all
+// marked -1 where the parent keeps the balance (until no further group can).
+// Output in Morton order (lower corner at the finest level, then level).
+extern "C" int dg_mhd_regrid_plan(const dg_mhd_ctx* ctx, const int8_t* marks, int64_t cap, int8_t* new_level,
+                                  int32_t* new_ijk, int32_t* src, int64_t* n_new) {
+  if (!ctx || !marks || !n_new) return DG_E_ARG;
+  Ctx& c = const_cast<Ctx&>(ctx->c);
+  if (!c.amr.on) return DG_E_UNSUPPORTED;
+  int e = ensure_groups(c);
+  if (e) return e;
+  AmrHost& h = c.amr;
+  const int D = h.D, no = 1 << D;
+  const int64_t N = (int64_t)h.hlevel.size();
+  // FNV-1a hash of the marks: a size query followed by the fill call plans once
+  uint64_t hash = 1469598103934665603ull;
+  for (int64_t i = 0; i < N; ++i) hash = (hash ^ (uint8_t)marks[i]) * 1099511628211ull;
+  if (h.plan.empty() || h.plan_hash != hash) {
+    std::vector<PlanLeaf> out;
+    plan_leaves(h, marks, out);
+    h.plan.resize(out.size() * 6);
+    for (size_t i = 0; i < out.size(); ++i) {
+      int32_t* q = &h.plan[i * 6];
+      q[0] = out[i].l;
+      q[1] = out[i].k[0];
+      q[2] = out[i].k[1];
+      q[3] = out[i].k[2];
+      q[4] = out[i].kind | (out[i].oct << 4);
+      q[5] = out[i].idx;
+    }
+    h.plan_hash = hash;
+  }
+  const size_t nn = h.plan.size() / 6;
+  *n_new = (int64_t)nn;
   if (!new_level || !new_ijk || !src) return DG_OK;  // size query
-  if (cap < (int64_t)out.size()) return DG_E_ARG;
-  for (size_t i = 0; i < out.size(); ++i) {
-    new_level[i] = (int8_t)out[i].l;
-    for (int a = 0; a < D; ++a) new_ijk[i * D + a] = out[i].k[a];
-    src[2 * i] = out[i].kind | (out[i].oct << 4);
-    src[2 * i + 1] = out[i].idx;
+  if (cap < (int64_t)nn) return DG_E_ARG;
+  for (size_t i = 0; i < nn; ++i) {
+    const int32_t* q = &h.plan[i * 6];
+    new_level[i] = (int8_t)q[0];
+    for (int a = 0; a < D; ++a) new_ijk[i * D + a] = q[1 + a];
+    src[2 * i] = q[4];
+    src[2 * i + 1] = q[5];
   }
   return DG_OK;
 }
