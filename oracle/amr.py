@@ -139,7 +139,12 @@ class AMRScheme(Scheme):
             wR = self.wf * (self.sub_w if kind == 2 else 1.0)
             uL = np.einsum("r,rpv->pv", w[cL], SL)
             uR = np.einsum("r,rpv->pv", w[cR], SR)
-            F, BnF = self.face_state(uL[None], uR[None], a, ch)
+            interp = not glm and self.P.powell_q == "interp"
+            if interp:
+                F, BnF, qdL, qdR = self.face_state(uL[None], uR[None], a, ch, qdag=True)
+                qdL, qdR = qdL[0], qdR[0]
+            else:
+                F, BnF = self.face_state(uL[None], uR[None], a, ch)
             F, BnF = F[0], BnF[0]
             mL, mR = 2.0 / self.dxc[cL], 2.0 / self.dxc[cR]
             R[cL] -= mL * np.einsum("pv,p,rpv->r", F, wL, SL)
@@ -147,8 +152,12 @@ class AMRScheme(Scheme):
             if not glm:
                 jumpL = BnF - uL[:, mhd.BX + a]
                 jumpR = -(BnF - uR[:, mhd.BX + a])
-                R[cL] -= mL * np.einsum("v,rpv,p,p->r", q[cL], SL, jumpL, wL)
-                R[cR] -= mR * np.einsum("v,rpv,p,p->r", q[cR], SR, jumpR, wR)
+                if interp:   # q^dagger per face point and side, eq. powellq-interp
+                    R[cL] -= mL * np.einsum("pv,rpv,p,p->r", qdL, SL, jumpL, wL)
+                    R[cR] -= mR * np.einsum("pv,rpv,p,p->r", qdR, SR, jumpR, wR)
+                else:
+                    R[cL] -= mL * np.einsum("v,rpv,p,p->r", q[cL], SL, jumpL, wL)
+                    R[cR] -= mR * np.einsum("v,rpv,p,p->r", q[cR], SR, jumpR, wR)
         out = R / self.mass
         if glm:
             psi_rows = [r for r, (k, v, i) in enumerate(self.rows) if k == "L" and v == mhd.PSI]

@@ -16,7 +16,9 @@ Passages followed:
   + int s.phi_l  (the paper prints dx/2; the mapping xi = 2(x-x_c)/dx gives
   d/dx = (2/dx) d/dxi, which is what is used here);
 * Sec. 3.5: Gauss-Legendre with d+1 points per dimension for volume and faces;
-* Sec. 4.1.3 eq. powell-src-face with q^dagger = q(<u>_K) (eq. powellq-average)
+* Sec. 4.1.3 eq. powell-src-face with q^dagger = q(<u>_K) (eq. powellq-average,
+  the default) or, with Params.powell_q = "interp", eq. powellq-interp against
+  the HLLD interface state
   and B^n_F from eq. bxface-average-alfven;
 * Sec. 4.1.5: GLM fluxes, upwinded psi*/B_n*, damping source -(c_h^2/c_p^2) psi,
   c_h = C'/(2d+1) dx/(D dt), c_r = c_p^2/c_h = 0.18, damping time >= 3 dt;
@@ -39,6 +41,7 @@ class Params:
     cfl_glm: float = 0.9      # C' of Sec. 4.1.5 (C < C' < 1)
     c_r: float = 0.18         # c_p^2 / c_h
     eta_powell: float = 0.2   # eq. powell_dt
+    powell_q: str = "mean"    # q^dagger: "mean" eq. powellq-average (default), "interp" eq. powellq-interp
     eps_hlld: float = 1e-8
     Mtilde: float = 5.0       # Sec. 4.2.1 / 5.1
     beta: float = 2.0
@@ -207,13 +210,20 @@ class Scheme:
         tau = max(self.P.c_r / ch, 3.0 * dt)
         return ch, 1.0 / tau
 
-    def face_state(self, uL, uR, axis, ch=None):
-        """Numerical flux F* at face points and B^n_F (Sec. 4.1.2-4.1.5)."""
+    def face_state(self, uL, uR, axis, ch=None, qdag=False):
+        """Numerical flux F* at face points and B^n_F (Sec. 4.1.2-4.1.5); with
+        qdag also q^dagger of eq. powellq-interp for the left and the right
+        trace against the HLLD interface state."""
         g = self.gamma
         rL, vL, pL, BL = mhd.primitives(uL, g)
         rR, vR, pR, BR = mhd.primitives(uR, g)
         BnL, BnR = BL[..., axis], BR[..., axis]
         BnF = mhd.bn_face(rL, rR, BnL, BnR)
+        if qdag:
+            F8, vF, BF = mhd.hlld(rL, vL, pL, BL, rR, vR, pR, BR, BnF, axis, g, self.P.eps_hlld, state=True)
+            F = np.zeros(uL.shape)
+            F[..., :8] = F8
+            return F, BnF, mhd.powell_q_interp(vL, BL, vF, BF), mhd.powell_q_interp(vR, BR, vF, BF)
         F8 = mhd.hlld(rL, vL, pL, BL, rR, vR, pR, BR, BnF, axis, g, self.P.eps_hlld)
         F = np.zeros(uL.shape)
         F[..., :8] = F8
@@ -242,7 +252,11 @@ class Scheme:
             L = self.nbr_minus[a]
             uL = self.eval_points(w[L], self.Sf[(a, 1)])
             uR = self.eval_points(w, self.Sf[(a, -1)])
-            F, BnF = self.face_state(uL, uR, a, ch)
+            interp = not glm and self.P.powell_q == "interp"
+            if interp:
+                F, BnF, qdL, qdR = self.face_state(uL, uR, a, ch, qdag=True)
+            else:
+                F, BnF = self.face_state(uL, uR, a, ch)
             contribL = np.einsum("cpv,p,rpv->cr", F, self.wf, self.Sf[(a, 1)])
             contribR = np.einsum("cpv,p,rpv->cr", F, self.wf, self.Sf[(a, -1)])
             R[L] -= contribL          # outward normal of L is +e_a
@@ -251,8 +265,12 @@ class Scheme:
                 # -oint (q.phi_l)(B_F - B_K).n dS,  eq. powell-src-face
                 jumpL = BnF - uL[..., mhd.BX + a]          # (B_F - B_L).(+e_a)
                 jumpR = -(BnF - uR[..., mhd.BX + a])       # (B_F - B_R).(-e_a)
-                qphiL = np.einsum("cv,rpv->cpr", q[L], self.Sf[(a, 1)])
-                qphiR = np.einsum("cv,rpv->cpr", q, self.Sf[(a, -1)])
+                if interp:   # q^dagger per face point and side, eq. powellq-interp
+                    qphiL = np.einsum("cpv,rpv->cpr", qdL, self.Sf[(a, 1)])
+                    qphiR = np.einsum("cpv,rpv->cpr", qdR, self.Sf[(a, -1)])
+                else:
+                    qphiL = np.einsum("cv,rpv->cpr", q[L], self.Sf[(a, 1)])
+                    qphiR = np.einsum("cv,rpv->cpr", q, self.Sf[(a, -1)])
                 R[L] -= np.einsum("cpr,cp,p->cr", qphiL, jumpL, self.wf)
                 R -= np.einsum("cpr,cp,p->cr", qphiR, jumpR, self.wf)
         out = (2.0 / self.dx) * R / self.mass
@@ -284,19 +302,31 @@ class Scheme:
                 if side == 0:   # face with the -a neighbour: this cell is R
                     uL = self.eval_points(wn, self.Sf[(a, 1)])
                     uR = self.eval_points(wc, self.Sf[(a, -1)])
-                    F, BnF = self.face_state(uL, uR, a, ch)
+                    interp = not glm and self.P.powell_q == "interp"
+                    if interp:
+                        F, BnF, _, qd = self.face_state(uL, uR, a, ch, qdag=True)
+                    else:
+                        F, BnF = self.face_state(uL, uR, a, ch)
                     R += np.einsum("cpv,p,rpv->cr", F, self.wf, self.Sf[(a, -1)])
                     if not glm:
                         jump = -(BnF - uR[..., mhd.BX + a])
-                        R -= np.einsum("cpr,cp,p->cr", np.einsum("cv,rpv->cpr", q, self.Sf[(a, -1)]), jump, self.wf)
+                        qphi = (np.einsum("cpv,rpv->cpr", qd, self.Sf[(a, -1)]) if interp
+                                else np.einsum("cv,rpv->cpr", q, self.Sf[(a, -1)]))
+                        R -= np.einsum("cpr,cp,p->cr", qphi, jump, self.wf)
                 else:           # face with the +a neighbour: this cell is L
                     uL = self.eval_points(wc, self.Sf[(a, 1)])
                     uR = self.eval_points(wn, self.Sf[(a, -1)])
-                    F, BnF = self.face_state(uL, uR, a, ch)
+                    interp = not glm and self.P.powell_q == "interp"
+                    if interp:
+                        F, BnF, qd, _ = self.face_state(uL, uR, a, ch, qdag=True)
+                    else:
+                        F, BnF = self.face_state(uL, uR, a, ch)
                     R -= np.einsum("cpv,p,rpv->cr", F, self.wf, self.Sf[(a, 1)])
                     if not glm:
                         jump = BnF - uL[..., mhd.BX + a]
-                        R -= np.einsum("cpr,cp,p->cr", np.einsum("cv,rpv->cpr", q, self.Sf[(a, 1)]), jump, self.wf)
+                        qphi = (np.einsum("cpv,rpv->cpr", qd, self.Sf[(a, 1)]) if interp
+                                else np.einsum("cv,rpv->cpr", q, self.Sf[(a, 1)]))
+                        R -= np.einsum("cpr,cp,p->cr", qphi, jump, self.wf)
         out = (2.0 / self.dx) * R / self.mass
         if glm:
             psi_rows = [r for r, (k, v, i) in enumerate(self.rows) if k == "L" and v == mhd.PSI]

@@ -95,12 +95,15 @@ def _rot(axis):
     return axis, (axis + 1) % 3, (axis + 2) % 3
 
 
-def hlld(rhoL, vL, pL, BL, rhoR, vR, pR, BR, Bn, axis, gamma, eps=1e-8):
+def hlld(rhoL, vL, pL, BL, rhoR, vR, pR, BR, Bn, axis, gamma, eps=1e-8, state=False):
     """HLLD flux (Miyoshi & Kusano 2005) across a face normal to `axis`, with
     the normal field of both states set to Bn beforehand (Sec. 4.1.3:
     primitives rho, v, p are kept, B_n := B^n_F).
 
     Returns the 8-component flux in the (x, y, z) frame; its B_axis entry is 0.
+    With state=True also (v_F, B_F): velocity and field of the interface state
+    u_F, the state of the Riemann fan that contains the interface (Sec. 4.1.3,
+    "Interface state"), in the (x, y, z) frame.
     """
     n, t1, t2 = _rot(axis)
     shape = np.broadcast(rhoL, rhoR).shape
@@ -203,6 +206,25 @@ def hlld(rhoL, vL, pL, BL, rhoR, vR, pR, BR, Bn, axis, gamma, eps=1e-8):
          np.where((SM >= 0)[..., None], FssL,
          np.where((SsR >= 0)[..., None], FssR,
          np.where((SR >= 0)[..., None], FsR, FR)))))
+    if state:
+        # region of the fan containing x/t = 0 (the selection of the flux above):
+        # rotated (v_n, v_t1, v_t2, B_t1, B_t2) of that state; B_n = Bn throughout
+        def pick(*vals):
+            conds = [SL > 0, SsL >= 0, SM >= 0, SsR >= 0, SR >= 0]
+            out = vals[5]
+            for c, v in zip(reversed(conds), reversed(vals[:5])):
+                out = np.where(c, v, out)
+            return out
+        smv = np.broadcast_to(SM, shape)
+        vn = pick(uL, smv, smv, smv, smv, uR)
+        vt = pick(vtL, vtsL, vss, vss, vtsR, vtR)
+        wt = pick(wtL, wtsL, wss, wss, wtsR, wtR)
+        By = pick(ByL, BysL, Byss, Byss, BysR, ByR)
+        Bz = pick(BzL, BzsL, Bzss, Bzss, BzsR, BzR)
+        vF = np.zeros(shape + (3,))
+        BF = np.zeros(shape + (3,))
+        vF[..., n], vF[..., t1], vF[..., t2] = vn, vt, wt
+        BF[..., n], BF[..., t1], BF[..., t2] = np.broadcast_to(Bn, shape), By, Bz
     # rotate back: rotated index k -> xyz component
     F = np.zeros(shape + (8,))
     F[..., RHO] = Fr[..., 0]
@@ -213,6 +235,8 @@ def hlld(rhoL, vL, pL, BL, rhoR, vR, pR, BR, Bn, axis, gamma, eps=1e-8):
     F[..., BX + n] = Fr[..., 5]
     F[..., BX + t1] = Fr[..., 6]
     F[..., BX + t2] = Fr[..., 7]
+    if state:
+        return F, vF, BF
     return F
 
 
@@ -223,6 +247,19 @@ def powell_q(U, gamma):
     q[..., MX:MZ + 1] = B
     q[..., EN] = np.sum(v * B, -1)
     q[..., BX:BZ + 1] = v
+    return q
+
+
+def powell_q_interp(vL, BL, vF, BF):
+    """q^dagger of eq. powellq-interp: the Powell q of a state interpolated
+    linearly in primitive variables between the trace u_L and the interface
+    state u_F, averaged over the layer: (0, (B_L+B_F)/2,
+    (2 B_L.v_L + B_L.v_F + B_F.v_L + 2 B_F.v_F)/6, (v_L+v_F)/2)."""
+    q = np.zeros(np.broadcast(vL, vF).shape[:-1] + (8,))
+    q[..., MX:MZ + 1] = 0.5 * (BL + BF)
+    q[..., EN] = (2 * np.sum(BL * vL, -1) + np.sum(BL * vF, -1) + np.sum(BF * vL, -1)
+                  + 2 * np.sum(BF * vF, -1)) / 6.0
+    q[..., BX:BZ + 1] = 0.5 * (vL + vF)
     return q
 
 
