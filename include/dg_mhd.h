@@ -109,6 +109,13 @@ typedef struct {
                          specialised kernel exists (testing)                 */
   int rk_order;       /* SSP-RK order of dg_mhd_step, 1..4 (Sec. 3.6); [3]
                          0: degree + 1 (at most 4), the paper's default      */
+  int powell_q;       /* Powell face term q^dagger (Sec. 4.1.3):       [0]
+                         0: q of the cell mean (eq. powellq-average, the
+                         paper's default); 1: eq. powellq-interp, the layer
+                         average between the trace and the HLLD interface
+                         state, per face point (generic and octree
+                         kernels; ignored with GLM and by
+                         dg_mhd_rhs_noalloc)                                 */
 } dg_mhd_params;
 
 /* Fills *p with the defaults listed above. */

@@ -39,7 +39,8 @@ class MeshDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("cfl", "cfl_glm", "c_r", "c_h_fixed", "eta_powell", "eps_hlld",
                                                "Mtilde", "beta", "tvb_eps", "eps_rho", "eps_p")] + \
-               [(k, ctypes.c_int) for k in ("precision", "limiter", "positivity", "generic_kernels", "rk_order")]
+               [(k, ctypes.c_int) for k in ("precision", "limiter", "positivity", "generic_kernels", "rk_order",
+                                            "powell_q")]
 
 
 _lib = None

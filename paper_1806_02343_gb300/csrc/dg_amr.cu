@@ -99,7 +99,7 @@ __device__ __forceinline__ SideTab<T> side_tab(const Geom& g, const Tables<T>& t
 
 template <typename T, int DEG, int GLMF>
 __global__ void k_face_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __restrict__ w, T* __restrict__ fbuf,
-                            const DevScalars* __restrict__ sc, T eps) {
+                            const DevScalars* __restrict__ sc, T eps, T* __restrict__ qbuf) {
   const Geom g = pin_geom<DEG, GLMF>(gin);
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= am.nface * g.Qf) return;
@@ -113,7 +113,7 @@ __global__ void k_face_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __res
   eval_pt(g, tl.P, tl.L, g.Qf, p, [&](int r) { return w[r * S + cL]; }, uL);
   eval_pt(g, tr.P, tr.L, g.Qf, p, [&](int r) { return w[r * S + cR]; }, uR);
   const T ch = g.glm ? (T)sc->ch : T(0);
-  const T bnF = face_flux(uL, uR, a, (T)g.gamma, g.glm != 0, ch, eps, F);
+  const T bnF = face_flux(uL, uR, a, (T)g.gamma, g.glm != 0, ch, eps, F, qbuf ? qbuf + tid * 14 : nullptr);
   T* o = fbuf + tid * 9;
   for (int k = 0; k < g.V; ++k) o[k] = F[k];
   if (!g.glm) o[8] = bnF;
@@ -135,7 +135,7 @@ template <typename T, int DEG, int GLMF, bool VEC>
 __global__ void k_cell_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __restrict__ w,
                             const T* __restrict__ fbuf, T* out, const T* w0, double ca, double cb, int combine,
                             const DevScalars* __restrict__ sc, const double* __restrict__ wmean, const double* w0mean,
-                            double* outmean) {
+                            double* outmean, const T* __restrict__ qbuf) {
   const Geom g = pin_geom<DEG, GLMF>(gin);
   // out / outmean may alias w0 / w0mean: each element is read, then written, by one lane.
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -196,12 +196,21 @@ __global__ void k_cell_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __res
     if (!g.glm) {
       T ba = T(0);
       for (int j = 0; j < g.ndiv; ++j) ba += wc[g.ldf0 + j] * t.L[(j * g.DB + a) * g.Qf + p];
-      PJ[e * QFP + p] = wp * sgn * (F[8] - ba);
+      const T pj = wp * sgn * (F[8] - ba);
+      PJ[e * QFP + p] = pj;
+      if (qbuf) {
+        // q^dagger of eq. powellq-interp at this point, own trace (side 0: left cell)
+        const T* q = qbuf + (f * g.Qf + p) * 14 + (side == 0 ? 0 : 7);
+        for (int v = 1; v < 8; ++v) FS[fsi(e, p, v)] += pj * q[v - 1];
+      }
     }
   }
   __syncwarp();
+  // Powell q(<u>_K) from the cell mean (zero when q^dagger is folded into the face terms)
   T qv[MAXV];
-  if (!g.glm) {
+  if (!g.glm && qbuf) {
+    for (int v = 0; v < MAXV; ++v) qv[v] = T(0);
+  } else if (!g.glm) {
     const T rho = wc[0];
     const T vx = wc[g.n] / rho, vy = wc[2 * g.n] / rho, vz = wc[3 * g.n] / rho;
     T b[3] = {T(0), T(0), T(0)};
@@ -611,7 +620,7 @@ AmrDev<float> amr_dev<float>(const Ctx& c) {
 template <typename T>
 void launch_amr_operator(const Ctx& c, const Tables<T>& tb, const T* w, T* fbuf, T* out, const T* w0, double ca,
                          double cb, int combine, const DevScalars* sc, const double* wmean, const double* w0mean,
-                         double* outmean, double eps, cudaStream_t st) {
+                         double* outmean, double eps, cudaStream_t st, T* qbuf) {
   const Geom& g = c.g;
   const AmrDev<T> am = amr_dev<T>(c);
   const int64_t np = am.nface * g.Qf;
@@ -620,10 +629,10 @@ void launch_amr_operator(const Ctx& c, const Tables<T>& tb, const T* w, T* fbuf,
                    am.Lsub4;
   const size_t sm = (size_t)cell_list_warp_elems(g, am.maxent, vec) * WPB * sizeof(T);
   auto run = [&](auto face_k, auto cell_k) {
-    face_k<<<(unsigned)((np + 127) / 128), 128, 0, st>>>(g, tb, am, w, fbuf, sc, (T)eps);
+    face_k<<<(unsigned)((np + 127) / 128), 128, 0, st>>>(g, tb, am, w, fbuf, sc, (T)eps, qbuf);
     cudaFuncSetAttribute(cell_k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cell_k<<<(unsigned)((g.ncell + WPB - 1) / WPB), 32 * WPB, sm, st>>>(g, tb, am, w, fbuf, out, w0, ca, cb, combine,
-                                                                       sc, wmean, w0mean, outmean);
+                                                                       sc, wmean, w0mean, outmean, qbuf);
   };
   // compile-time sizes for the 3D degree-1 and degree-2 schemes
   if (!pinned_sizes_ok(g)) run(k_face_list<T, -1, 0>, k_cell_list<T, -1, 0, false>);
@@ -653,10 +662,10 @@ void launch_amr_dt(const Ctx& c, const Tables<T>& tb, const T* w, const double* 
 
 template void launch_amr_operator<double>(const Ctx&, const Tables<double>&, const double*, double*, double*,
                                           const double*, double, double, int, const DevScalars*, const double*,
-                                          const double*, double*, double, cudaStream_t);
+                                          const double*, double*, double, cudaStream_t, double*);
 template void launch_amr_operator<float>(const Ctx&, const Tables<float>&, const float*, float*, float*,
                                          const float*, double, double, int, const DevScalars*, const double*,
-                                         const double*, double*, double, cudaStream_t);
+                                         const double*, double*, double, cudaStream_t, float*);
 template void launch_amr_dt<double>(const Ctx&, const Tables<double>&, const double*, const double*, double*,
                                     const dg_mhd_params&, DevScalars*, cudaStream_t);
 template void launch_amr_dt<float>(const Ctx&, const Tables<float>&, const float*, const double*, float*,

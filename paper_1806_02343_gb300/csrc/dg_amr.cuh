@@ -33,7 +33,7 @@ void free_amr(Ctx& c);
 template <typename T>
 void launch_amr_operator(const Ctx& c, const Tables<T>& tb, const T* w, T* fbuf, T* out, const T* w0, double ca,
                          double cb, int combine, const DevScalars* sc, const double* wmean, const double* w0mean,
-                         double* outmean, double eps, cudaStream_t st);
+                         double* outmean, double eps, cudaStream_t st, T* qbuf = nullptr);
 template <typename T>
 void launch_amr_dt(const Ctx& c, const Tables<T>& tb, const T* w, const double* wmean, T* jbuf,
                    const dg_mhd_params& p, DevScalars* sc, cudaStream_t st);

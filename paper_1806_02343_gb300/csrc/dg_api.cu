@@ -400,6 +400,7 @@ void dg_mhd_default_params(dg_mhd_params* p) {
   p->limiter = DG_LIMIT_OFF;
   p->positivity = 0;
   p->rk_order = 3;
+  p->powell_q = 0;
 }
 
 const char* dg_mhd_strerror(int s) {
@@ -427,7 +428,7 @@ void dg_mhd_destroy(dg_mhd_ctx* ctx) {
   free_tables(c.t32);
   void* ptrs[] = {c.sc, c.face_buf, c.face_buf32, c.stage_buf[0], c.stage_buf[1], c.stage_buf[2],
                   c.stage_mean[0], c.stage_mean[1], c.stage_mean[2], c.cellscratch, c.proj_tab, c.proj_w,
-                  c.troubled, c.flag_list, c.pos_list, c.mlp_w1, c.mlp_w2, c.mlp_bias, c.rg_tabs};
+                  c.troubled, c.flag_list, c.pos_list, c.mlp_w1, c.mlp_w2, c.mlp_bias, c.rg_tabs, c.qdag_buf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c.hb;
@@ -461,6 +462,7 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
   if (prm.precision != DG_PREC_FP64 && prm.precision != DG_PREC_FP32MIX) return DG_E_ARG;
   if (!(prm.cfl > 0.0) || !(prm.cfl_glm > 0.0)) return DG_E_ARG;
   if (prm.rk_order < 0 || prm.rk_order > 4) return DG_E_ARG;
+  if (prm.powell_q != 0 && prm.powell_q != 1) return DG_E_ARG;
   if (prm.rk_order == 0) prm.rk_order = degree + 1 < 4 ? degree + 1 : 4;
   // octree meshes: a global, time-independent c_h (Sec. 4.1.5)
   if (octree && divB_scheme == DG_DIVB_GLM && !(prm.c_h_fixed > 0.0)) return DG_E_ARG;
@@ -546,6 +548,9 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
     } else {
       ok = cudaMalloc(&c.face_buf, face_elems * sizeof(double)) == cudaSuccess;
     }
+    // Powell q^dagger of eq. powellq-interp: 14 values per face point
+    if (ok && prm.powell_q == 1 && !g.glm)
+      ok = cudaMalloc(&c.qdag_buf, face_elems / 9 * 14 * (fp32(c) ? sizeof(float) : sizeof(double))) == cudaSuccess;
   }
   if (!ok) {
     dg_mhd_destroy(ctx);
@@ -651,10 +656,10 @@ int operator_pass(Ctx& c, const void* w, const double* wmean, void* out, double*
     c.prof.begin(1, st);
     if (fp32(c))
       launch_amr_operator<float>(c, c.t32, (const float*)w, c.face_buf32, (float*)out, (const float*)w0, ca, cb,
-                                 combine, c.sc, wmean, w0mean, outmean, c.p.eps_hlld, st);
+                                 combine, c.sc, wmean, w0mean, outmean, c.p.eps_hlld, st, (float*)c.qdag_buf);
     else
       launch_amr_operator<double>(c, c.t64, (const double*)w, c.face_buf, (double*)out, (const double*)w0, ca, cb,
-                                  combine, c.sc, nullptr, nullptr, nullptr, c.p.eps_hlld, st);
+                                  combine, c.sc, nullptr, nullptr, nullptr, c.p.eps_hlld, st, (double*)c.qdag_buf);
     c.prof.end(1, st);
     c.prof.launches[1] += 1;
     return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
@@ -685,19 +690,19 @@ int operator_pass(Ctx& c, const void* w, const double* wmean, void* out, double*
   }
   if (fp32(c)) {
     c.prof.begin(0, st);
-    launch_face<float>(g, c.t32, (const float*)w, c.face_buf32, c.sc, c.p.eps_hlld, st);
+    launch_face<float>(g, c.t32, (const float*)w, c.face_buf32, c.sc, c.p.eps_hlld, st, (float*)c.qdag_buf);
     c.prof.end(0, st);
     c.prof.begin(1, st);
     launch_cell<float>(g, c.t32, (const float*)w, c.face_buf32, (float*)out, (const float*)w0, ca, cb, combine,
-                       c.sc, wmean, w0mean, outmean, st);
+                       c.sc, wmean, w0mean, outmean, st, (const float*)c.qdag_buf);
     c.prof.end(1, st);
   } else {
     c.prof.begin(0, st);
-    launch_face<double>(g, c.t64, (const double*)w, c.face_buf, c.sc, c.p.eps_hlld, st);
+    launch_face<double>(g, c.t64, (const double*)w, c.face_buf, c.sc, c.p.eps_hlld, st, (double*)c.qdag_buf);
     c.prof.end(0, st);
     c.prof.begin(1, st);
     launch_cell<double>(g, c.t64, (const double*)w, c.face_buf, (double*)out, (const double*)w0, ca, cb,
-                        combine, c.sc, nullptr, nullptr, nullptr, st);
+                        combine, c.sc, nullptr, nullptr, nullptr, st, (const double*)c.qdag_buf);
     c.prof.end(1, st);
   }
   return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;

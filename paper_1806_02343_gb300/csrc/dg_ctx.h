@@ -232,6 +232,7 @@ struct Ctx {
   int32_t* pos_list = nullptr;     // cells the positivity screen could not clear in the current pass
   PosScreen pscr;                  // FP32 positivity screen tables
   double* rg_tabs = nullptr;       // regridding tables (dg_regrid.cu), built on first use
+  void* qdag_buf = nullptr;        // Powell q^dagger per face point (powell_q = 1)
   int64_t lim_passes = 0;          // limiter passes with TVB since the last counter reset
   int64_t lim_plain_cells = 0;     // cells the plain TVB detection examined since the last reset
   int nsm = 152;                   // streaming multiprocessors of the device

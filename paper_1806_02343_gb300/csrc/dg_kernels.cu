@@ -102,7 +102,7 @@ __device__ __forceinline__ void eval_state(const Geom& g, const T* __restrict__ 
 // ---------------------------------------------------------------- face fluxes
 template <typename T, int DEG, int GLMF>
 __global__ void k_face(Geom gin, Tables<T> tb, const T* __restrict__ w, T* __restrict__ fbuf,
-                       const DevScalars* __restrict__ sc, T eps) {
+                       const DevScalars* __restrict__ sc, T eps, T* __restrict__ qbuf) {
   const Geom g = pin_geom<DEG, GLMF>(gin);
   const int64_t total = (int64_t)g.D * g.ncell * g.Qf;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -121,7 +121,7 @@ __global__ void k_face(Geom gin, Tables<T> tb, const T* __restrict__ w, T* __res
              [&](int r) { return w[r * S + c]; }, uR);
   T F[MAXV];
   const T ch = g.glm ? (T)sc->ch : T(0);
-  const T bnF = face_flux(uL, uR, a, (T)g.gamma, g.glm != 0, ch, eps, F);
+  const T bnF = face_flux(uL, uR, a, (T)g.gamma, g.glm != 0, ch, eps, F, qbuf ? qbuf + tid * 14 : nullptr);
   T* o = fbuf + tid * 9;
   for (int k = 0; k < g.V; ++k) o[k] = F[k];
   if (!g.glm) o[8] = bnF;
@@ -144,7 +144,8 @@ __host__ __device__ inline int cell_warp_elems(const Geom& g, bool vec) {
 template <typename T, int DEG, int GLMF, bool VEC>
 __global__ void k_cell(Geom gin, Tables<T> tb, const T* __restrict__ w, const T* __restrict__ fbuf, T* out,
                        const T* w0, double ca, double cb, int combine, const DevScalars* __restrict__ sc,
-                       const double* __restrict__ wmean, const double* w0mean, double* outmean) {
+                       const double* __restrict__ wmean, const double* w0mean, double* outmean,
+                       const T* __restrict__ qbuf) {
   const Geom g = pin_geom<DEG, GLMF>(gin);
   // out may alias w0 (in-place final stage): each element is read and then
   // written by the same thread.
@@ -205,13 +206,23 @@ __global__ void k_cell(Geom gin, Tables<T> tb, const T* __restrict__ w, const T*
       T ba = T(0);
       for (int j = 0; j < g.ndiv; ++j)
         ba += wc[g.ldf0 + j] * tb.Lf[(((size_t)f * g.ndiv + j) * g.DB + a) * g.Qf + p];
-      PJ[f * QFP + p] = wp * sgn * (F[8] - ba);
+      const T pj = wp * sgn * (F[8] - ba);
+      PJ[f * QFP + p] = pj;
+      if (qbuf) {
+        // q^dagger of eq. powellq-interp at this point, own trace: the +a face
+        // (side 1) has this cell on its left, the -a face on its right
+        const T* q = qbuf + (((int64_t)a * g.ncell + fc) * g.Qf + p) * 14 + (side ? 0 : 7);
+        for (int v = 1; v < 8; ++v) FS[fsi(f, p, v)] += pj * q[v - 1];
+      }
     }
   }
   __syncwarp();
-  // Powell q(<u>_K) = (0, B, v.B, v) from the cell mean
+  // Powell q(<u>_K) = (0, B, v.B, v) from the cell mean (zero when q^dagger
+  // is folded into the face terms)
   T qv[MAXV];
-  if (!g.glm) {
+  if (!g.glm && qbuf) {
+    for (int v = 0; v < MAXV; ++v) qv[v] = T(0);
+  } else if (!g.glm) {
     const T rho = wc[0];
     const T vx = wc[g.n] / rho, vy = wc[2 * g.n] / rho, vz = wc[3 * g.n] / rho;
     T b[3] = {T(0), T(0), T(0)};
@@ -756,10 +767,10 @@ static inline unsigned nblocks(int64_t n, int b) { return (unsigned)((n + b - 1)
 
 template <typename T>
 void launch_face(const Geom& g, const Tables<T>& tb, const T* w, T* fbuf, const DevScalars* sc, double eps,
-                 cudaStream_t st) {
+                 cudaStream_t st, T* qbuf) {
   const int64_t total = (int64_t)g.D * g.ncell * g.Qf;
   // compile-time sizes for the 3D degree-1 and degree-2 schemes
-  auto run = [&](auto k) { k<<<nblocks(total, 128), 128, 0, st>>>(g, tb, w, fbuf, sc, (T)eps); };
+  auto run = [&](auto k) { k<<<nblocks(total, 128), 128, 0, st>>>(g, tb, w, fbuf, sc, (T)eps, qbuf); };
   if (!pinned_sizes_ok(g)) run(k_face<T, -1, 0>);
   else if (g.d == 2) g.glm ? run(k_face<T, 2, 1>) : run(k_face<T, 2, 0>);
   else g.glm ? run(k_face<T, 1, 1>) : run(k_face<T, 1, 0>);
@@ -773,14 +784,14 @@ static size_t cell_smem(const Geom& g, bool vec = false) {
 template <typename T>
 void launch_cell(const Geom& g, const Tables<T>& tb, const T* w, const T* fbuf, T* out, const T* w0,
                  double ca, double cb, int combine, const DevScalars* sc, const double* wmean,
-                 const double* w0mean, double* outmean, cudaStream_t st) {
+                 const double* w0mean, double* outmean, cudaStream_t st, const T* qbuf) {
   // FP32 only: FP64 is bound by its multiply-add rate, which the padding would raise
   const bool vec = sizeof(T) == 4 && pinned_sizes_ok(g) && tb.dPv4 && tb.dLv4 && tb.Pf4 && tb.Lf4;
   const size_t sm = cell_smem<T>(g, vec);
   auto run = [&](auto k) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     k<<<nblocks(g.ncell, WARPS_PER_BLOCK), 32 * WARPS_PER_BLOCK, sm, st>>>(g, tb, w, fbuf, out, w0, ca, cb, combine,
-                                                                        sc, wmean, w0mean, outmean);
+                                                                        sc, wmean, w0mean, outmean, qbuf);
   };
   // compile-time sizes for the 3D degree-1 and degree-2 schemes
   if (!pinned_sizes_ok(g)) run(k_cell<T, -1, 0, false>);
@@ -876,10 +887,10 @@ void launch_mirror_means(const Geom& g, const double* wmean, T* w, cudaStream_t 
 
 #define INST(T)                                                                                              \
   template void launch_face<T>(const Geom&, const Tables<T>&, const T*, T*, const DevScalars*, double,      \
-                               cudaStream_t);                                                                \
+                               cudaStream_t, T*);                                                            \
   template void launch_cell<T>(const Geom&, const Tables<T>&, const T*, const T*, T*, const T*, double,     \
                                double, int, const DevScalars*, const double*, const double*, double*,      \
-                               cudaStream_t);                                                                \
+                               cudaStream_t, const T*);                                                      \
   template void launch_project<T>(const Geom&, int, const double*, const double*, const double*, const T*, \
                                   T*, double*, cudaStream_t);                                               \
   template void launch_divb_face<T>(const Geom&, const Tables<T>&, const T*, T*, cudaStream_t);            \

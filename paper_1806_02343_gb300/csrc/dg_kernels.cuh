@@ -5,13 +5,16 @@
 namespace dgmhd {
 
 // launches (all asynchronous on `st`)
+// qbuf (Powell, nullable): q^dagger of eq. powellq-interp per face point,
+// 14 values (left then right trace), written by launch_face and read by
+// launch_cell in place of q(<u>_K)
 template <typename T>
 void launch_face(const Geom& g, const Tables<T>& tb, const T* w, T* fbuf, const DevScalars* sc, double eps,
-                 cudaStream_t st);
+                 cudaStream_t st, T* qbuf = nullptr);
 template <typename T>
 void launch_cell(const Geom& g, const Tables<T>& tb, const T* w, const T* fbuf, T* out, const T* w0,
                  double ca, double cb, int combine, const DevScalars* sc, const double* wmean,
-                 const double* w0mean, double* outmean, cudaStream_t st);
+                 const double* w0mean, double* outmean, cudaStream_t st, const T* qbuf = nullptr);
 template <typename T>
 void launch_project(const Geom& g, int npts, const double* tab, const double* wq, const double* nodal,
                     const T* minv, T* w, double* wmean, cudaStream_t st);

@@ -74,8 +74,17 @@ struct Prim {
 };
 
 // HLLD flux in the rotated frame; out[0..7] = (rho, m_n, m_t1, m_t2, E, B_n, B_t1, B_t2).
+// st (nullable): velocity (u, v, w) and tangential field (by, bz) of the
+// interface state, the state of the Riemann fan that contains the face
+// (Sec. 4.1.3, "Interface state"); its normal field is bn.
 template <typename T>
-__device__ __forceinline__ void hlld(const Prim<T>& L, const Prim<T>& R, T bn, T gamma, T eps, T* out) {
+__device__ __forceinline__ void hlld(const Prim<T>& L, const Prim<T>& R, T bn, T gamma, T eps, T* out,
+                                     Prim<T>* st = nullptr) {
+  auto set_state = [&](T u, T v, T w, T by, T bz) {
+    if (st) {
+      st->u = u; st->v = v; st->w = w; st->by = by; st->bz = bz;
+    }
+  };
   const T gm1i = rcp(gamma - T(1));
   const T bn2 = bn * bn;
   const T b2L = bn2 + L.by * L.by + L.bz * L.bz;
@@ -120,6 +129,7 @@ __device__ __forceinline__ void hlld(const Prim<T>& L, const Prim<T>& R, T bn, T
   if (SL > T(0)) {
     phys(L, EL, pTL, FL, UL);
     for (int k = 0; k < 8; ++k) out[k] = FL[k];
+    set_state(L.u, L.v, L.w, L.by, L.bz);
     return;
   }
   T FR[8], UR[8];
@@ -170,14 +180,17 @@ __device__ __forceinline__ void hlld(const Prim<T>& L, const Prim<T>& R, T bn, T
   if (SsL >= T(0)) {  // left single-starred region
     const T Us[8] = {rsL, rsL * SM, rsL * vsL, rsL * wsL, EsL, bn, bysL, bzsL};
     for (int k = 0; k < 8; ++k) out[k] = FL[k] + SL * (Us[k] - UL[k]);
+    set_state(SM, vsL, wsL, bysL, bzsL);
     return;
   }
   if (SM < T(0) && SsR < T(0)) {
     if (SR >= T(0)) {  // right single-starred region
       const T Us[8] = {rsR, rsR * SM, rsR * vsR, rsR * wsR, EsR, bn, bysR, bzsR};
       for (int k = 0; k < 8; ++k) out[k] = FR[k] + SR * (Us[k] - UR[k]);
+      set_state(SM, vsR, wsR, bysR, bzsR);
     } else {
       for (int k = 0; k < 8; ++k) out[k] = FR[k];
+      set_state(R.u, R.v, R.w, R.by, R.bz);
     }
     return;
   }
@@ -188,6 +201,7 @@ __device__ __forceinline__ void hlld(const Prim<T>& L, const Prim<T>& R, T bn, T
   const T byss = (sqL * bysR + sqR * bysL + sqL * sqR * (vsR - vsL) * sgn) * inv;
   const T bzss = (sqL * bzsR + sqR * bzsL + sqL * sqR * (wsR - wsL) * sgn) * inv;
   const T vbss = SM * bn + vss * byss + wss * bzss;
+  set_state(SM, vss, wss, byss, bzss);
   if (SM >= T(0)) {
     const T Ess = EsL - sqL * (vbsL - vbss) * sgn;
     const T Us[8] = {rsL, rsL * SM, rsL * vsL, rsL * wsL, EsL, bn, bysL, bzsL};
@@ -202,10 +216,15 @@ __device__ __forceinline__ void hlld(const Prim<T>& L, const Prim<T>& R, T bn, T
 }
 
 // Face flux for a face normal to `a` from conserved traces uL, uR (xyz frame).
-// Writes F[0..V-1] in the xyz frame and returns B^n_F.
+// Writes F[0..V-1] in the xyz frame and returns B^n_F. qd (nullable, Powell):
+// q^dagger of eq. powellq-interp against the HLLD interface state u_F for the
+// left trace (qd[0..6]) and the right trace (qd[7..13]); per side the
+// components act on the momentum (B_L + B_F)/2 [0..2], the energy
+// (2 B_L.v_L + B_L.v_F + B_F.v_L + 2 B_F.v_F)/6 [3] and the induction
+// (v_L + v_F)/2 [4..6] equations, in the xyz frame.
 template <typename T>
 __device__ __forceinline__ T face_flux(const T* uL, const T* uR, int a, T gamma, bool glm, T ch, T eps,
-                                       T* F) {
+                                       T* F, T* qd = nullptr) {
   const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
   Prim<T> L, R;
   {
@@ -231,7 +250,30 @@ __device__ __forceinline__ T face_flux(const T* uL, const T* uR, int a, T gamma,
   const T bnL = uL[5 + a], bnR = uR[5 + a];
   const T bnF = bn_face(L.r, R.r, bnL, bnR);
   T Fr[8];
-  hlld(L, R, bnF, gamma, eps, Fr);
+  Prim<T> sf;
+  hlld(L, R, bnF, gamma, eps, Fr, qd ? &sf : nullptr);
+  if (qd) {
+    T vF[3], BF[3];
+    vF[a] = sf.u; vF[t1] = sf.v; vF[t2] = sf.w;
+    BF[a] = bnF; BF[t1] = sf.by; BF[t2] = sf.bz;
+    for (int side = 0; side < 2; ++side) {
+      const T* u = side ? uR : uL;
+      const T ir = rcp(u[0]);
+      const T vX[3] = {u[1] * ir, u[2] * ir, u[3] * ir};
+      const T BX[3] = {u[5], u[6], u[7]};
+      T* q = qd + 7 * side;
+      T bxvx = T(0), bxvf = T(0), bfvx = T(0), bfvf = T(0);
+      for (int k = 0; k < 3; ++k) {
+        q[k] = T(0.5) * (BX[k] + BF[k]);
+        q[4 + k] = T(0.5) * (vX[k] + vF[k]);
+        bxvx += BX[k] * vX[k];
+        bxvf += BX[k] * vF[k];
+        bfvx += BF[k] * vX[k];
+        bfvf += BF[k] * vF[k];
+      }
+      q[3] = (T(2) * bxvx + bxvf + bfvx + T(2) * bfvf) * (T(1) / T(6));
+    }
+  }
   F[0] = Fr[0];
   F[1 + a] = Fr[1]; F[1 + t1] = Fr[2]; F[1 + t2] = Fr[3];
   F[4] = Fr[4];
