@@ -60,6 +60,48 @@ def alfven_2d(x, t=0.0, gamma=5.0 / 3.0, eps=0.1, nvar=8):
     return _assemble(xp, one, vx, vy, vz, 0.1 * one, bx, by, bz, gamma, nvar)
 
 
+def isodensity_vortex_2d(x, t=0.0, alpha_deg=45.0, gamma=5.0 / 3.0, eta=1.0, xi=1.0, L=20.0, nvar=8):
+    """Isodensity MHD vortex (Sec. 5.1.2), exact solution at time t on the
+    periodic box [0, L)^2 (the paper's [-10, 10]^2 shifted by L/2): rho = 1, the
+    background p = 1 and v0 = sqrt(2) (cos a, sin a); with psi = exp((1-r^2)/2),
+    dv = eta/(2 pi) curl(0, 0, psi), dB = xi/(2 pi) curl(0, 0, psi),
+    dp = [xi^2 (1 - r^2) - eta^2] exp(1 - r^2) / (8 pi^2); advected: u(x - v0 t, 0)."""
+    xp = _xp(x)
+    a = math.radians(alpha_deg)
+    v0x, v0y = math.sqrt(2.0) * math.cos(a), math.sqrt(2.0) * math.sin(a)
+    X = xp.remainder(x[..., 0] - v0x * t, L) - 0.5 * L
+    Y = xp.remainder(x[..., 1] - v0y * t, L) - 0.5 * L
+    r2 = X * X + Y * Y
+    psi = xp.exp(0.5 * (1.0 - r2))
+    one = xp.ones_like(r2)
+    # curl(0, 0, psi) = (d_y psi, -d_x psi, 0) = psi (-Y, X, 0)
+    cv, cb = eta / (2.0 * math.pi), xi / (2.0 * math.pi)
+    p = 1.0 + (xi * xi * (1.0 - r2) - eta * eta) * xp.exp(1.0 - r2) / (8.0 * math.pi ** 2)
+    return _assemble(xp, one, v0x - cv * psi * Y, v0y + cv * psi * X, 0.0 * one, p,
+                     -cb * psi * Y, cb * psi * X, 0.0 * one, gamma, nvar)
+
+
+def alfven_3d(x, t=0.0, gamma=5.0 / 3.0, eps=0.02, nvar=8):
+    """Circularly polarised Alfven wave in 3D (Sec. 5.2), exact solution at time
+    t on the periodic unit cube: rho = 1, p = 100; in the frame e1 = (1,1,1)/sqrt(3),
+    e2 = (1,-1,0)/sqrt(2), e3 = e1 x e2, v = e1 + eps (cos phi e2 + sin phi e3),
+    B = e1 - eps (cos phi e2 + sin phi e3), phi = 2 pi / lambda (x.e1 - 2t) with
+    lambda = 1/sqrt(3) (periodic along every axis; Alfven speed 1 plus the flow
+    speed 1 along e1)."""
+    xp = _xp(x)
+    s3, s2, s6 = math.sqrt(3.0), math.sqrt(2.0), math.sqrt(6.0)
+    e1 = (1 / s3, 1 / s3, 1 / s3)
+    e2 = (1 / s2, -1 / s2, 0.0)
+    e3 = (1 / s6, 1 / s6, -2 / s6)
+    xpar = (x[..., 0] + x[..., 1] + x[..., 2]) / s3
+    phi = 2.0 * math.pi * s3 * (xpar - 2.0 * t)
+    c, sn = eps * xp.cos(phi), eps * xp.sin(phi)
+    one = xp.ones_like(phi)
+    v = [e1[k] * one + c * e2[k] + sn * e3[k] for k in range(3)]
+    Bf = [e1[k] * one - c * e2[k] - sn * e3[k] for k in range(3)]
+    return _assemble(xp, one, v[0], v[1], v[2], 100.0 * one, Bf[0], Bf[1], Bf[2], gamma, nvar)
+
+
 # ---------------------------------------------------------------------------
 # entropy (density) wave: uniform v, p, B; advected density (pin case)
 # ---------------------------------------------------------------------------

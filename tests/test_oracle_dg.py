@@ -335,3 +335,24 @@ def test_divb_diagnostics_volume_part_converges():
     # |div B|_K's face part is a jump of O(dx^3) over dx: second order
     ratio = np.mean(out[0]["face"]) / np.mean(out[1]["face"])
     assert 3.5 < ratio < 4.5, ratio
+
+
+def test_isodensity_vortex_converges_at_order_2():
+    """The closed-form isodensity vortex (Sec. 5.1.2, 30 deg) with the GLM scheme
+    at degree 1 and SSP-RK2: L1 errors fall by about 2^2 from 32^2 to 64^2
+    cells at t = 0.5 (an equilibrium that the scheme must merely advect)."""
+    import math
+    from paper_1806_02343_gb300 import workloads as W
+    errs = []
+    for n in (32, 64):
+        S = Scheme(2, 1, "glm", 5.0 / 3.0, n, L=20.0)
+        w = S.project(lambda x: W.isodensity_vortex_2d(x, alpha_deg=30.0, nvar=S.V))
+        t, T = 0.0, 0.5
+        while t < T - 1e-14:
+            dt = min(S.dt(w), T - t)
+            w, _ = S.step(w, dt)
+            t += dt
+        e, _ = S.l1_error(w, lambda x: W.isodensity_vortex_2d(x, t=t, alpha_deg=30.0, nvar=S.V))
+        errs.append(e)
+    for v in (mhd.MX, mhd.MY, mhd.EN, mhd.BX, mhd.BY):
+        assert 1.8 < math.log2(errs[0][v] / errs[1][v]) < 2.5
