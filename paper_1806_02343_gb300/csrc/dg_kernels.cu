@@ -142,7 +142,7 @@ __host__ __device__ inline int cell_warp_elems(const Geom& g, bool vec) {
 // contractions run as 16-byte vector loads of the fluxes and the tables
 // (four multiply-adds per pair of loads instead of one).
 template <typename T, int DEG, int GLMF, bool VEC>
-__global__ void k_cell(Geom gin, Tables<T> tb, const T* __restrict__ w, const T* __restrict__ fbuf, T* out,
+__global__ void __launch_bounds__(32 * WARPS_PER_BLOCK, VEC ? 8 : 1) k_cell(Geom gin, Tables<T> tb, const T* __restrict__ w, const T* __restrict__ fbuf, T* out,
                        const T* w0, double ca, double cb, int combine, const DevScalars* __restrict__ sc,
                        const double* __restrict__ wmean, const double* w0mean, double* outmean,
                        const T* __restrict__ qbuf) {
