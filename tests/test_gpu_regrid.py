@@ -148,3 +148,47 @@ def test_remap_rejects_out_of_range_sources():
     rc = Bd.lib().dg_mhd_remap(sol.h, new.h, Bd._ptr(src), Bd._ptr(w), None, Bd._ptr(wn), None, Bd._stream())
     assert rc == 0
     assert new.status(1) == -1  # DG_E_ARG
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("divb", ["glm", "powell"])
+def test_marks_plan_and_remap_match_oracle_2d(divb, prec):
+    """The same on a 2D quadtree (level 4, 256 leaves): groups of four, the
+    2D Powell form's B_z Legendre rows next to its LDF rows."""
+    from paper_1806_02343_gb300.binding import Solver, DG_PREC_FP32MIX, DG_PREC_FP64
+    leaves = [(4, k) for k in itertools.product(range(16), repeat=2)]
+    A = AMRScheme(2, 2, divb, GAM, leaves)
+    w0 = A.project(_front(A.V))
+    s_tilde, lo, hi = 0.03, 3, 6
+    refine, groups, coarsen = G.marks(A, leaves, w0, FIELDS, s_tilde, lo, hi)
+    items = G.plan(leaves, 2, refine, groups, coarsen)
+    marks_ref = np.zeros(len(leaves), dtype=np.int8)
+    marks_ref[refine] = 1
+    for g in coarsen:
+        marks_ref[groups[g][2]] = -1
+    assert (marks_ref == 1).any() and (marks_ref == -1).any()
+    kw = {"c_h_fixed": 3.0} if divb == "glm" else {}
+    sol = Solver(2, None, 2, divb, gamma=GAM, box_len=1.0, leaves=leaves,
+                 precision=DG_PREC_FP32MIX if prec == "fp32" else DG_PREC_FP64, **kw)
+    w = to_device(w0, sol)
+    wm = means_to_device(w0, sol, A) if prec == "fp32" else None
+    marks, _ = sol.amr_marks(w, wm, FIELDS, s_tilde, lo, hi)
+    assert np.array_equal(marks.cpu().numpy(), marks_ref)
+    lev, ijk, src = sol.regrid_plan(marks)
+    assert [(int(l), tuple(int(x) for x in k)) for l, k in zip(lev, ijk)] == [key for key, _ in items]
+    new, wn, wmn = sol.regrid(w, wm, marks=marks)
+    ref = G.remap(A, w0, groups, items)
+    assert rel_err(from_device(wn, new), ref) < (1e-6 if prec == "fp32" else 1e-11)
+    assert new.status(True) == 0
+
+
+def test_smoothness_on_a_uniform_mesh():
+    """dg_mhd_smoothness takes uniform meshes too (FP64, Powell, 6 x 5 x 4)."""
+    from oracle.dg import Scheme
+    from paper_1806_02343_gb300.binding import Solver
+    S = Scheme(3, 2, "powell", GAM, (6, 5, 4))
+    w0 = S.project(_front(S.V))
+    ref = G.smoothness(S, w0, FIELDS).reshape(S.C, -1).max(axis=1)
+    sol = Solver(3, (6, 5, 4), 2, "powell", gamma=GAM, box_len=S.L)
+    got = sol.smoothness(to_device(w0, sol), None, FIELDS).cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-11 * ref.max()
