@@ -131,6 +131,9 @@ __host__ __device__ inline int cell_list_warp_elems(const Geom& g, int maxent, b
 
 // VEC (3D, sizes fixed at compile time, padded tables present): the row
 // contractions run as 16-byte vector loads.
+constexpr int kEntryChunk = 6;  // face entries staged at a time (a leaf has 6 to 24)
+constexpr int kRowsPerLane = 6;  // state rows per lane (at most 180 rows)
+
 template <typename T, int DEG, int GLMF, bool VEC>
 __global__ void k_cell_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __restrict__ w,
                             const T* __restrict__ fbuf, T* out, const T* w0, double ca, double cb, int combine,
@@ -142,12 +145,13 @@ __global__ void k_cell_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __res
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t c = (int64_t)blockIdx.x * WPB + warp;
   const int QVP = VEC ? pad4(g.Qv) : g.Qv, QFP = VEC ? pad4(g.Qf) : g.Qf;
-  const int per_warp = cell_list_warp_elems(g, am.maxent, VEC);
+  const int che = am.maxent < kEntryChunk ? am.maxent : kEntryChunk;  // entries per staged chunk
+  const int per_warp = cell_list_warp_elems(g, che, VEC);
   T* wc = reinterpret_cast<T*>(smraw) + (size_t)warp * per_warp;
   T* G = wc + (VEC ? pad4(g.nrows) : g.nrows);
   T* FS = G + g.D * g.V * QVP;
-  T* PJ = FS + am.maxent * QFP * g.V;
-  // face term of (entry e, point p, variable v)
+  T* PJ = FS + che * QFP * g.V;
+  // face term of (chunk entry e, point p, variable v)
   auto fsi = [&](int e, int p, int v) { return VEC ? (e * g.V + v) * QFP + p : (e * g.Qf + p) * g.V + v; };
   if (c >= g.ncell) return;
   const int64_t S = g.stride;
@@ -168,43 +172,9 @@ __global__ void k_cell_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __res
       for (int v = 0; v < g.V; ++v) G[(a * g.V + v) * QVP + q] = wq * f[v];
     }
   }
-  const int e0 = am.cstart[c], ne = am.cstart[c + 1] - e0;
-  if (VEC) {
-    // zero padding of the point index (the padded tables are zero there too)
+  if (VEC)
     for (int i = lane; i < g.D * g.V * (QVP - g.Qv); i += 32)
       G[(i / (QVP - g.Qv)) * QVP + g.Qv + i % (QVP - g.Qv)] = T(0);
-    for (int i = lane; i < ne * (g.V + 1) * (QFP - g.Qf); i += 32) {
-      const int row = i / (QFP - g.Qf), pp = g.Qf + i % (QFP - g.Qf);
-      if (row < ne * g.V) FS[row * QFP + pp] = T(0);
-      else PJ[(row - ne * g.V) * QFP + pp] = T(0);
-    }
-  }
-  const T subw = T(1) / T(am.nsub);
-  for (int idx = lane; idx < ne * g.Qf; idx += 32) {
-    const int e = idx / g.Qf, p = idx % g.Qf;
-    const int ent = am.centry[e0 + e];
-    const int64_t f = ent >> 1;
-    const int side = ent & 1;
-    const int meta = am.fmeta[f];
-    const int a = meta & 3;
-    const SideTab<T> t = side_tab(g, tb, am, meta, side);
-    const T* F = fbuf + (f * g.Qf + p) * 9;
-    // outward normal: +e_a for the left cell, -e_a for the right cell
-    const T sgn = side == 0 ? T(1) : T(-1);
-    const T wp = tb.wf[p] * (t.coarse ? subw : T(1));
-    for (int v = 0; v < g.V; ++v) FS[fsi(e, p, v)] = sgn * wp * F[v];
-    if (!g.glm) {
-      T ba = T(0);
-      for (int j = 0; j < g.ndiv; ++j) ba += wc[g.ldf0 + j] * t.L[(j * g.DB + a) * g.Qf + p];
-      const T pj = wp * sgn * (F[8] - ba);
-      PJ[e * QFP + p] = pj;
-      if (qbuf) {
-        // q^dagger of eq. powellq-interp at this point, own trace (side 0: left cell)
-        const T* q = qbuf + (f * g.Qf + p) * 14 + (side == 0 ? 0 : 7);
-        for (int v = 1; v < 8; ++v) FS[fsi(e, p, v)] += pj * q[v - 1];
-      }
-    }
-  }
   __syncwarp();
   // Powell q(<u>_K) from the cell mean (zero when q^dagger is folded into the face terms)
   T qv[MAXV];
@@ -221,22 +191,29 @@ __global__ void k_cell_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __res
     qv[4] = vx * b[0] + vy * b[1] + vz * b[2];
     qv[5] = vx; qv[6] = vy; qv[7] = vz; qv[8] = T(0);
   }
-  const double dt = sc->dt;
-  const double kappa = g.glm ? sc->kappa : 0.0;
-  const double metric = 2.0 / am.dxc[c];
   // FP32 form: rows other than the degree-0 ones accumulate and combine in
-  // FP32 (GB300's FP64 rate is 1/64 of FP32); the degree-0 rows keep FP64
-  const T tm = (T)metric, tdt = (T)dt, tca = (T)ca, tcb = (T)cb;
-  for (int r = lane; r < g.nrows; r += 32) {
-    const int m = mix ? mindex_a(g, r) : -1;
-    const bool lowp = sizeof(T) == 4 && m < 0;
-    double acc = 0.0;
-    T acct = T(0);
-    const bool ldf = g.ldf0 >= 0 && r >= g.ldf0 && r < g.ldf0 + g.ndiv;
+  // FP32 (GB300's FP64 rate is 1/64 of FP32); the degree-0 rows keep FP64.
+  // Each lane owns rows lane + 32 i; their accumulators live across the chunks.
+  double acc[kRowsPerLane];
+  T acct[kRowsPerLane];
+  auto row_kind = [&](int r, bool& ldf, int& v, int& l) {
+    ldf = g.ldf0 >= 0 && r >= g.ldf0 && r < g.ldf0 + g.ndiv;
+    v = (g.bz2d >= 0 && r >= g.bz2d) ? 7 : r / g.n;
+    l = ldf ? r - g.ldf0 : ((g.bz2d >= 0 && r >= g.bz2d) ? r - g.bz2d : r % g.n);
+  };
+  // volume terms
+#pragma unroll
+  for (int i = 0; i < kRowsPerLane; ++i) {
+    acc[i] = 0.0;
+    acct[i] = T(0);
+    const int r = lane + 32 * i;
+    if (r >= g.nrows) continue;
+    const bool lowp = sizeof(T) == 4 && (mix ? mindex_a(g, r) : -1) < 0;
+    bool ldf;
+    int v, l;
+    row_kind(r, ldf, v, l);
+    T s = T(0);
     if (!ldf) {
-      const int v = (g.bz2d >= 0 && r >= g.bz2d) ? 7 : r / g.n;
-      const int l = (g.bz2d >= 0 && r >= g.bz2d) ? r - g.bz2d : r % g.n;
-      T s = T(0);
       if (l != 0)
         for (int a = 0; a < g.D; ++a) {
           const T* Gp = G + (a * g.V + v) * QVP;
@@ -247,67 +224,122 @@ __global__ void k_cell_list(Geom gin, Tables<T> tb, AmrDev<T> am, const T* __res
             for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
           }
         }
-      if (lowp) acct += s; else acc += (double)s;
-      for (int e = 0; e < ne; ++e) {
-        const int ent = am.centry[e0 + e];
-        const SideTab<T> t = side_tab(g, tb, am, am.fmeta[ent >> 1], ent & 1);
-        T sf = T(0);
-        if constexpr (VEC) {
-          constexpr int QF4 = pad4((DEG + 1) * (DEG + 1));
-          const T* Pp = t.P4 + (size_t)l * QFP;
-          sf = dotp<T, QF4>(FS + (e * g.V + v) * QFP, Pp);
-          if (!g.glm) sf += qv[v] * dotp<T, QF4>(PJ + e * QFP, Pp);
-        } else {
-          const T* Pp = t.P + (size_t)l * g.Qf;
-          for (int p = 0; p < g.Qf; ++p) {
-            T term = FS[fsi(e, p, v)];
-            if (!g.glm) term += PJ[e * QFP + p] * qv[v];
-            sf += term * Pp[p];
-          }
-        }
-        if (lowp) acct -= sf; else acc -= (double)sf;
-      }
     } else {
-      const int j = r - g.ldf0;
-      T s = T(0);
       for (int a = 0; a < g.D; ++a)
         for (int cc = 0; cc < g.DB; ++cc) {
           const T* Gp = G + (a * g.V + 5 + cc) * QVP;
           if constexpr (VEC) {
             s += dotp<T, pad4((DEG + 1) * (DEG + 1) * (DEG + 1))>(
-                Gp, tb.dLv4 + (((size_t)a * g.ndiv + j) * g.DB + cc) * QVP);
+                Gp, tb.dLv4 + (((size_t)a * g.ndiv + l) * g.DB + cc) * QVP);
           } else {
-            const T* Dp = tb.dLv + (((size_t)a * g.ndiv + j) * g.DB + cc) * g.Qv;
+            const T* Dp = tb.dLv + (((size_t)a * g.ndiv + l) * g.DB + cc) * g.Qv;
             for (int q = 0; q < g.Qv; ++q) s += Gp[q] * Dp[q];
           }
         }
-      if (lowp) acct += s; else acc += (double)s;
-      for (int e = 0; e < ne; ++e) {
-        const int ent = am.centry[e0 + e];
-        const SideTab<T> t = side_tab(g, tb, am, am.fmeta[ent >> 1], ent & 1);
-        T sf = T(0);
-        for (int cc = 0; cc < g.DB; ++cc) {
-          if constexpr (VEC) {
-            constexpr int QF4 = pad4((DEG + 1) * (DEG + 1));
-            const T* Lp = t.L4 + ((size_t)j * g.DB + cc) * QFP;
-            sf += dotp<T, QF4>(FS + (e * g.V + 5 + cc) * QFP, Lp) + qv[5 + cc] * dotp<T, QF4>(PJ + e * QFP, Lp);
-          } else {
-            const T* Lp = t.L + ((size_t)j * g.DB + cc) * g.Qf;
-            for (int p = 0; p < g.Qf; ++p)
-              sf += (FS[fsi(e, p, 5 + cc)] + PJ[e * QFP + p] * qv[5 + cc]) * Lp[p];
-          }
+    }
+    if (lowp) acct[i] += s; else acc[i] += (double)s;
+  }
+  // surface terms, the face entries staged kEntryChunk at a time
+  const int e0 = am.cstart[c], ne = am.cstart[c + 1] - e0;
+  const T subw = T(1) / T(am.nsub);
+  for (int k0 = 0; k0 < ne; k0 += che) {
+    const int nc = ne - k0 < che ? ne - k0 : che;
+    __syncwarp();  // the previous chunk's reads are done
+    if (VEC)
+      for (int i = lane; i < nc * (g.V + 1) * (QFP - g.Qf); i += 32) {
+        // zero padding of the point index (the padded tables are zero there too)
+        const int row = i / (QFP - g.Qf), pp = g.Qf + i % (QFP - g.Qf);
+        if (row < nc * g.V) FS[row * QFP + pp] = T(0);
+        else PJ[(row - nc * g.V) * QFP + pp] = T(0);
+      }
+    for (int idx = lane; idx < nc * g.Qf; idx += 32) {
+      const int e = idx / g.Qf, p = idx % g.Qf;
+      const int ent = am.centry[e0 + k0 + e];
+      const int64_t f = ent >> 1;
+      const int side = ent & 1;
+      const int meta = am.fmeta[f];
+      const int a = meta & 3;
+      const SideTab<T> t = side_tab(g, tb, am, meta, side);
+      const T* F = fbuf + (f * g.Qf + p) * 9;
+      // outward normal: +e_a for the left cell, -e_a for the right cell
+      const T sgn = side == 0 ? T(1) : T(-1);
+      const T wp = tb.wf[p] * (t.coarse ? subw : T(1));
+      for (int v = 0; v < g.V; ++v) FS[fsi(e, p, v)] = sgn * wp * F[v];
+      if (!g.glm) {
+        T ba = T(0);
+        for (int j = 0; j < g.ndiv; ++j) ba += wc[g.ldf0 + j] * t.L[(j * g.DB + a) * g.Qf + p];
+        const T pj = wp * sgn * (F[8] - ba);
+        PJ[e * QFP + p] = pj;
+        if (qbuf) {
+          // q^dagger of eq. powellq-interp at this point, own trace (side 0: left cell)
+          const T* q = qbuf + (f * g.Qf + p) * 14 + (side == 0 ? 0 : 7);
+          for (int v = 1; v < 8; ++v) FS[fsi(e, p, v)] += pj * q[v - 1];
         }
-        if (lowp) acct -= sf; else acc -= (double)sf;
       }
     }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < kRowsPerLane; ++i) {
+      const int r = lane + 32 * i;
+      if (r >= g.nrows) continue;
+      const bool lowp = sizeof(T) == 4 && (mix ? mindex_a(g, r) : -1) < 0;
+      bool ldf;
+      int v, l;
+      row_kind(r, ldf, v, l);
+      for (int e = 0; e < nc; ++e) {
+        const int ent = am.centry[e0 + k0 + e];
+        const SideTab<T> t = side_tab(g, tb, am, am.fmeta[ent >> 1], ent & 1);
+        T sf = T(0);
+        if (!ldf) {
+          if constexpr (VEC) {
+            constexpr int QF4 = pad4((DEG + 1) * (DEG + 1));
+            const T* Pp = t.P4 + (size_t)l * QFP;
+            sf = dotp<T, QF4>(FS + (e * g.V + v) * QFP, Pp);
+            if (!g.glm) sf += qv[v] * dotp<T, QF4>(PJ + e * QFP, Pp);
+          } else {
+            const T* Pp = t.P + (size_t)l * g.Qf;
+            for (int p = 0; p < g.Qf; ++p) {
+              T term = FS[fsi(e, p, v)];
+              if (!g.glm) term += PJ[e * QFP + p] * qv[v];
+              sf += term * Pp[p];
+            }
+          }
+        } else {
+          for (int cc = 0; cc < g.DB; ++cc) {
+            if constexpr (VEC) {
+              constexpr int QF4 = pad4((DEG + 1) * (DEG + 1));
+              const T* Lp = t.L4 + ((size_t)l * g.DB + cc) * QFP;
+              sf += dotp<T, QF4>(FS + (e * g.V + 5 + cc) * QFP, Lp) + qv[5 + cc] * dotp<T, QF4>(PJ + e * QFP, Lp);
+            } else {
+              const T* Lp = t.L + ((size_t)l * g.DB + cc) * g.Qf;
+              for (int p = 0; p < g.Qf; ++p)
+                sf += (FS[fsi(e, p, 5 + cc)] + PJ[e * QFP + p] * qv[5 + cc]) * Lp[p];
+            }
+          }
+        }
+        if (lowp) acct[i] -= sf; else acc[i] -= (double)sf;
+      }
+    }
+  }
+  // combination and write
+  const double dt = sc->dt;
+  const double kappa = g.glm ? sc->kappa : 0.0;
+  const double metric = 2.0 / am.dxc[c];
+  const T tm = (T)metric, tdt = (T)dt, tca = (T)ca, tcb = (T)cb;
+#pragma unroll
+  for (int i = 0; i < kRowsPerLane; ++i) {
+    const int r = lane + 32 * i;
+    if (r >= g.nrows) continue;
+    const int m = mix ? mindex_a(g, r) : -1;
+    const bool lowp = sizeof(T) == 4 && m < 0;
     if (lowp) {
-      T rt = tm * tb.minv[r] * acct;
+      T rt = tm * tb.minv[r] * acct[i];
       if (g.glm && r >= 8 * g.n) rt -= (T)kappa * wc[r];
       if (!combine) out[r * S + c] = rt;
       else out[r * S + c] = tca * w0[r * S + c] + tcb * (wc[r] + tdt * rt);
       continue;
     }
-    double rhs = metric * (double)tb.minv[r] * acc;
+    double rhs = metric * (double)tb.minv[r] * acc[i];
     if (g.glm && r >= 8 * g.n) rhs -= kappa * (double)wc[r];
     if (!combine) {
       out[r * S + c] = (T)rhs;
@@ -627,7 +659,7 @@ void launch_amr_operator(const Ctx& c, const Tables<T>& tb, const T* w, T* fbuf,
   // FP32 only: FP64 is bound by its multiply-add rate, which the padding would raise
   const bool vec = sizeof(T) == 4 && pinned_sizes_ok(g) && tb.dPv4 && tb.dLv4 && tb.Pf4 && tb.Lf4 && am.Psub4 &&
                    am.Lsub4;
-  const size_t sm = (size_t)cell_list_warp_elems(g, am.maxent, vec) * WPB * sizeof(T);
+  const size_t sm = (size_t)cell_list_warp_elems(g, std::min(am.maxent, kEntryChunk), vec) * WPB * sizeof(T);
   auto run = [&](auto face_k, auto cell_k) {
     face_k<<<(unsigned)((np + 127) / 128), 128, 0, st>>>(g, tb, am, w, fbuf, sc, (T)eps, qbuf);
     cudaFuncSetAttribute(cell_k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
