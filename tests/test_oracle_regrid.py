@@ -36,50 +36,55 @@ def test_affine_octant_equals_evaluation_at_mapped_points():
         assert np.allclose(got, B.peval(poly, (pts + s) / 2), atol=1e-14)
 
 
+@pytest.mark.parametrize("D", [2, 3])
 @pytest.mark.parametrize("divb", ["glm", "powell"])
-def test_prolonged_children_reproduce_the_parent_pointwise(divb):
-    """The parent polynomial (Legendre variables and the LDF B field) restricted
-    to octant o is represented exactly by child o's weights."""
-    S = _scheme(divb)
+def test_prolonged_children_reproduce_the_parent_pointwise(divb, D):
+    """The parent polynomial (Legendre variables and the LDF B field; in 2D the
+    Powell form's B_z Legendre rows too) restricted to octant o is represented
+    exactly by child o's weights."""
+    S = _scheme(divb, D=D)
     rng = np.random.default_rng(2)
     wp = _random_state(S, rng)
     ch = G.prolong(S, wp)
-    pts = rng.uniform(-1, 1, (40, 3))
+    pts = rng.uniform(-1, 1, (40, D))
     Sc = S.synth(pts)
-    for o in range(8):
-        s = np.array(G.octant_sign(o, 3), dtype=float)
+    for o in range(2 ** D):
+        s = np.array(G.octant_sign(o, D), dtype=float)
         up = np.einsum("r,rqv->qv", wp, S.synth((pts + s) / 2))
         uc = np.einsum("r,rqv->qv", ch[o], Sc)
         assert np.abs(up - uc).max() < 1e-12
 
 
+@pytest.mark.parametrize("D", [2, 3])
 @pytest.mark.parametrize("divb", ["glm", "powell"])
-def test_restriction_is_the_l2_projection_of_the_children(divb):
+def test_restriction_is_the_l2_projection_of_the_children(divb, D):
     """Arbitrary children: the residual u_children - u_parent is orthogonal to
     every parent basis row (each octant integrated with its own Gauss rule),
     and the parent mean of every variable is the average of the children's."""
-    S = _scheme(divb)
+    S = _scheme(divb, D=D)
     rng = np.random.default_rng(3)
-    wc = rng.standard_normal((8, S.N))
+    no = 2 ** D
+    wc = rng.standard_normal((no, S.N))
     wp = G.restrict(S, wc)
-    qp, qw = B.gauss_tensor(3, S.d + 2)
+    qp, qw = B.gauss_tensor(D, S.d + 2)
     resid = np.zeros(S.N)
-    for o in range(8):
-        s = np.array(G.octant_sign(o, 3), dtype=float)
+    for o in range(no):
+        s = np.array(G.octant_sign(o, D), dtype=float)
         xp = (qp + s) / 2                         # octant points in parent coordinates
         uc = np.einsum("r,rqv->qv", wc[o], S.synth(qp))
         up = np.einsum("r,rqv->qv", wp, S.synth(xp))
         Sp = S.synth(xp)
-        resid += np.einsum("qv,rqv,q->r", uc - up, Sp, qw) / 8.0
+        resid += np.einsum("qv,rqv,q->r", uc - up, Sp, qw) / no
     assert np.abs(resid).max() < 1e-12
     mp = S.means(wp[None])[0]
     mc = S.means(wc).mean(axis=0)
     assert np.abs(mp - mc).max() < 1e-13
 
 
+@pytest.mark.parametrize("D", [2, 3])
 @pytest.mark.parametrize("divb", ["glm", "powell"])
-def test_restrict_after_prolong_is_identity(divb):
-    S = _scheme(divb)
+def test_restrict_after_prolong_is_identity(divb, D):
+    S = _scheme(divb, D=D)
     w = np.random.default_rng(4).standard_normal(S.N)
     assert np.abs(G.restrict(S, G.prolong(S, w)) - w).max() < 1e-13
 
@@ -205,3 +210,18 @@ def test_marks_and_remap_keep_totals():
     tot_old = (S.means(w) * vol_old[:, None]).sum(0)
     tot_new = (S.means(w2) * vol_new[:, None]).sum(0)
     assert np.abs(tot_old - tot_new).max() < 1e-13
+
+
+def test_plan_in_2d_tiles_and_balances():
+    """2D quadtree: refining one corner leaf of a level-3 mesh and coarsening
+    the groups far from it gives a tiling, 2:1-balanced mesh."""
+    leaves = [(3, k) for k in itertools.product(range(8), repeat=2)]
+    groups = G.sibling_groups(leaves, 2)
+    assert len(groups) == 16
+    refine = np.zeros(len(leaves), bool)
+    refine[leaves.index((3, (0, 0)))] = True
+    far = [g for g, (_, pk, _) in enumerate(groups) if min(pk) >= 2]
+    items = G.plan(leaves, 2, refine, groups, far)
+    new = [(l, k) for (l, k), _ in items]
+    assert _tiles(new, 2) and balanced(new, 2)
+    assert sum(1 for l, _ in new if l == 2) == len(far) and sum(1 for l, _ in new if l == 4) == 4
