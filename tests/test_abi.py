@@ -65,6 +65,12 @@ def test_init_rejects_bad_arguments(lib):
     assert lib.dg_mhd_rhs(None, None, None, None, None, None) == -1
     assert lib.dg_mhd_step(None, None, None, None, None) == -1
     assert lib.dg_mhd_divb(None, None, None, None, None, None) == -1
+    # regridding entry points: NULL contexts and arrays are DG_E_ARG before any device work
+    assert lib.dg_mhd_smoothness(None, None, None, 1, None, None) == -1
+    assert lib.dg_mhd_amr_marks(None, None, None, 1, 0.03, 0, 8, None, None, None) == -1
+    n = ctypes.c_int64(-5)
+    assert lib.dg_mhd_regrid_plan(None, None, 0, None, None, None, ctypes.byref(n)) == -1
+    assert lib.dg_mhd_remap(None, None, None, None, None, None, None, None) == -1
 
 
 def test_octree_mesh_validation_rejects_bad_meshes(lib):
