@@ -317,6 +317,27 @@ int dg_mhd_amr_marks(dg_mhd_ctx* ctx, const void* w, const double* wmean, int fi
 int dg_mhd_regrid_plan(const dg_mhd_ctx* ctx, const int8_t* marks, int64_t cap, int8_t* new_level,
                        int32_t* new_ijk, int32_t* src, int64_t* n_new);
 
+/* The same planning without a context (HOST arrays; synchronous, no device
+ * work): the leaves (dim, n, level[n], ijk[n*dim], any order) must tile the
+ * periodic unit cube without overlap, be 2:1 balanced across faces and have
+ * levels <= 17 (DG_E_MESH otherwise; DG_E_ARG for dim not 2 or 3, n < 1 or a
+ * mark outside {-1, 0, 1}). marks[c] in the given leaf order; the output and
+ * its size query are those of dg_mhd_regrid_plan, the groups numbered as
+ * dg_mhd_sibling_groups numbers them (the numbering a context built on the
+ * same leaves uses). */
+int dg_mhd_regrid_plan_mesh(int dim, int64_t n, const int8_t* level, const int32_t* ijk, const int8_t* marks,
+                            int64_t cap, int8_t* new_level, int32_t* new_ijk, int32_t* src, int64_t* n_new);
+
+/* The groups of 2^dim sibling leaves of a mesh (HOST arrays, no context; the
+ * mesh rules of dg_mhd_regrid_plan_mesh): the children of one cube, all of
+ * them leaves, sorted by (parent level, parent i, j, k); groups[g*2^dim + o]
+ * = index of the leaf in octant o (o = sum_a bit_a << a, bit_a the lowest bit
+ * of its coordinate a). Writes *n_groups and, if groups is non-NULL and
+ * cap >= *n_groups, the groups (DG_E_ARG if cap is too small). These are the
+ * groups the restriction sources of a plan and the -1 marks refer to. */
+int dg_mhd_sibling_groups(int dim, int64_t n, const int8_t* level, const int32_t* ijk, int64_t cap,
+                          int32_t* groups, int64_t* n_groups);
+
 /* State of the new context from the old one (asynchronous on stream): per new
  * leaf a copy, an L2 prolongation (parent octant onto the child's basis; the
  * LDF rows under the vector inner product of eq. innerp) or an L2 restriction

@@ -25,7 +25,8 @@ EXPORTS = [
     "dg_mhd_profile", "dg_mhd_profile_read", "dg_mhd_launch_count", "dg_mhd_rhs_noalloc", "dg_mhd_destroy",
     "dg_mhd_strerror", "dg_mhd_mlp_features", "dg_mhd_mlp_set_weights", "dg_mhd_mlp_infer", "dg_mhd_mlp_loss_grad",
     "dg_mhd_mlp_train", "dg_mhd_counters", "dg_mhd_limiter_counts", "dg_mhd_divb", "dg_mhd_smoothness",
-    "dg_mhd_amr_marks", "dg_mhd_regrid_plan", "dg_mhd_remap",
+    "dg_mhd_amr_marks", "dg_mhd_regrid_plan", "dg_mhd_remap", "dg_mhd_regrid_plan_mesh",
+    "dg_mhd_sibling_groups",
 ]
 KIND_FACE, KIND_CELL, KIND_DT, KIND_LIMIT, KIND_PROJECT, KIND_POSITIVITY, KIND_MLP = range(7)
 
@@ -91,6 +92,8 @@ def lib():
     L.dg_mhd_amr_marks.argtypes = [vp, vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp, vp, vp]
     L.dg_mhd_regrid_plan.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp, i64p]
     L.dg_mhd_remap.argtypes = [vp, vp, vp, vp, dp, vp, dp, vp]
+    L.dg_mhd_regrid_plan_mesh.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, vp, ctypes.c_int64, vp, vp, vp, i64p]
+    L.dg_mhd_sibling_groups.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_int64, vp, i64p]
     L.dg_mhd_destroy.argtypes = [vp]
     L.dg_mhd_destroy.restype = None
     L.dg_mhd_strerror.argtypes = [ctypes.c_int]
@@ -142,6 +145,49 @@ def rhs_noalloc(dim, n, degree, divb, w, out, gamma=5.0 / 3.0, box_len=1.0, c_h=
     _check(lib().dg_mhd_rhs_noalloc(ctypes.byref(m), degree, DG_DIVB_GLM if divb == "glm" else DG_DIVB_POWELL,
                                     gamma, None, c_h, damping_rate, _ptr(w), _ptr(out), _stream()),
            "dg_mhd_rhs_noalloc")
+
+
+def _leaf_arrays(levels, ijk):
+    import numpy as np
+    lev = np.ascontiguousarray(levels, dtype=np.int8)
+    k = np.ascontiguousarray(ijk, dtype=np.int32)
+    if k.ndim != 2 or k.shape[0] != lev.shape[0]:
+        raise ValueError("ijk must be [n, dim] with one row per level")
+    return lev, k
+
+
+def sibling_groups(levels, ijk):
+    """Groups of 2^dim sibling leaves of an octree mesh (host, no GPU):
+    int32 [n_groups, 2^dim], the leaf index of each octant."""
+    import numpy as np
+    lev, k = _leaf_arrays(levels, ijk)
+    dim, n, ng = k.shape[1], lev.shape[0], ctypes.c_int64()
+    _check(lib().dg_mhd_sibling_groups(dim, n, lev.ctypes.data, k.ctypes.data, 0, None, ctypes.byref(ng)),
+           "dg_mhd_sibling_groups")
+    out = np.zeros((ng.value, 1 << dim), dtype=np.int32)
+    _check(lib().dg_mhd_sibling_groups(dim, n, lev.ctypes.data, k.ctypes.data, ng.value, out.ctypes.data,
+                                       ctypes.byref(ng)), "dg_mhd_sibling_groups")
+    return out
+
+
+def regrid_plan_mesh(levels, ijk, marks):
+    """New leaves (levels int8, ijk int32 [n, dim]) and their sources (int32
+    [n, 2]) from per-leaf marks, without a context (host, no GPU)."""
+    import numpy as np
+    lev, k = _leaf_arrays(levels, ijk)
+    mk = np.ascontiguousarray(marks, dtype=np.int8)
+    if mk.shape != lev.shape:
+        raise ValueError("one mark per leaf")
+    dim, n, nn = k.shape[1], lev.shape[0], ctypes.c_int64()
+    _check(lib().dg_mhd_regrid_plan_mesh(dim, n, lev.ctypes.data, k.ctypes.data, mk.ctypes.data, 0, None, None,
+                                         None, ctypes.byref(nn)), "dg_mhd_regrid_plan_mesh")
+    lev_n = np.zeros(nn.value, dtype=np.int8)
+    ijk_n = np.zeros((nn.value, dim), dtype=np.int32)
+    src = np.zeros((nn.value, 2), dtype=np.int32)
+    _check(lib().dg_mhd_regrid_plan_mesh(dim, n, lev.ctypes.data, k.ctypes.data, mk.ctypes.data, nn.value,
+                                         lev_n.ctypes.data, ijk_n.ctypes.data, src.ctypes.data, ctypes.byref(nn)),
+           "dg_mhd_regrid_plan_mesh")
+    return lev_n, ijk_n, src
 
 
 def mlp_loss_grad(X, y, theta, nin, pos_weight=1.0):

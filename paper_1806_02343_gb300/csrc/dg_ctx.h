@@ -7,6 +7,7 @@
 
 #include "../../include/dg_mhd.h"
 #include "dg_basis.h"
+#include "dg_plan.h"
 
 namespace dgmhd {
 
@@ -194,6 +195,7 @@ struct AmrHost {
   int D = 0;
   std::vector<int8_t> hlevel;
   std::vector<int32_t> hijk;
+  MortonIndex morton;  // the leaves in Morton order (built with the groups)
   int64_t ngroups = -1;
   std::vector<int32_t> hgroups;
   int32_t* groups = nullptr;

@@ -21,7 +21,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <unordered_map>
 #include <vector>
 
 #include "../../include/dg_mhd.h"
@@ -389,56 +388,23 @@ int ensure_tables(Ctx& c, RgDev& L) {
   return DG_OK;
 }
 
-uint64_t leaf_key(int l, const int32_t* k, int D) {
-  const uint64_t z = D == 3 ? (uint64_t)k[2] : 0;
-  return ((uint64_t)l << 58) | ((uint64_t)k[0] << 38) | ((uint64_t)k[1] << 18) | z;
-}
-
 // sibling groups of an octree context (host and device), on first use
 int ensure_groups(Ctx& c) {
   AmrHost& h = c.amr;
   if (h.ngroups >= 0) return DG_OK;
   const int D = h.D, no = 1 << D;
   const int64_t N = (int64_t)h.hlevel.size();
-  std::unordered_map<uint64_t, int32_t> idx;
-  idx.reserve((size_t)N * 2);
-  for (int64_t i = 0; i < N; ++i) idx.emplace(leaf_key(h.hlevel[i], &h.hijk[i * D], D), (int32_t)i);
-  // parent key -> members (complete groups only), sorted by parent key
-  std::vector<std::pair<uint64_t, std::vector<int32_t>>> found;
-  std::unordered_map<uint64_t, char> seen;
-  for (int64_t i = 0; i < N; ++i) {
-    const int l = h.hlevel[i];
-    if (l == 0) continue;
-    int32_t pk[3] = {0, 0, 0};
-    for (int a = 0; a < D; ++a) pk[a] = h.hijk[i * D + a] >> 1;
-    const uint64_t key = leaf_key(l - 1, pk, D);
-    if (!seen.emplace(key, 1).second) continue;
-    std::vector<int32_t> mem(no, -1);
-    bool all = true;
-    for (int o = 0; o < no; ++o) {
-      int32_t ck[3] = {0, 0, 0};
-      for (int a = 0; a < D; ++a) ck[a] = 2 * pk[a] + ((o >> a) & 1);
-      auto it = idx.find(leaf_key(l, ck, D));
-      if (it == idx.end()) {
-        all = false;
-        break;
-      }
-      mem[o] = it->second;
-    }
-    if (all) found.emplace_back(key, std::move(mem));
-  }
-  std::sort(found.begin(), found.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
-  h.ngroups = (int64_t)found.size();
-  h.hgroups.assign((size_t)h.ngroups * no, 0);
-  for (int64_t gi = 0; gi < h.ngroups; ++gi)
-    for (int o = 0; o < no; ++o) h.hgroups[gi * no + o] = found[gi].second[o];
-  if (cudaMalloc(&h.groups, std::max<size_t>(1, h.hgroups.size()) * sizeof(int32_t)) != cudaSuccess ||
-      cudaMalloc(&h.lev_dev, std::max<size_t>(1, (size_t)N)) != cudaSuccess)
+  const int e = morton_index(D, N, h.hlevel.data(), h.hijk.data(), h.morton);
+  if (e) return e;
+  sibling_groups(h.morton, h.hijk.data(), h.hgroups);
+  if (!h.groups && cudaMalloc(&h.groups, std::max<size_t>(1, h.hgroups.size()) * sizeof(int32_t)) != cudaSuccess)
     return DG_E_CUDA;
+  if (!h.lev_dev && cudaMalloc(&h.lev_dev, std::max<size_t>(1, (size_t)N)) != cudaSuccess) return DG_E_CUDA;
   if (!h.hgroups.empty() &&
       cudaMemcpy(h.groups, h.hgroups.data(), h.hgroups.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
     return DG_E_CUDA;
   if (cudaMemcpy(h.lev_dev, h.hlevel.data(), (size_t)N, cudaMemcpyHostToDevice) != cudaSuccess) return DG_E_CUDA;
+  h.ngroups = (int64_t)h.hgroups.size() / no;  // set last: a failed call is retried in full
   return DG_OK;
 }
 
@@ -518,164 +484,6 @@ extern "C" int dg_mhd_remap(const dg_mhd_ctx* old_ctx, dg_mhd_ctx* new_ctx, cons
   return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
 }
 
-namespace {
-
-struct PlanLeaf {
-  int l;
-  int32_t k[3];
-  int kind, idx, oct;  // source: 0 copy, 1 prolongation (octant oct), 2 restriction (group idx)
-};
-
-// level of the leaf of `mesh` containing the cube (l, k), -1 if the cube is split
-int covering_level(const std::unordered_map<uint64_t, PlanLeaf>& mesh, int l, const int32_t* k, int D) {
-  for (int ll = l; ll >= 0; --ll) {
-    int32_t kk[3] = {0, 0, 0};
-    for (int a = 0; a < D; ++a) kk[a] = k[a] >> (l - ll);
-    if (mesh.count(leaf_key(ll, kk, D))) return ll;
-  }
-  return -1;
-}
-
-// no face neighbour of the cube (l, k) holds leaves of level >= l + 2
-bool face_ok(const std::unordered_map<uint64_t, PlanLeaf>& mesh, int l, const int32_t* k, int D) {
-  const int32_t n = 1 << l;
-  for (int a = 0; a < D; ++a)
-    for (int s = -1; s <= 1; s += 2) {
-      int32_t nk[3] = {k[0], k[1], k[2]};
-      nk[a] = (nk[a] + s + n) % n;
-      if (covering_level(mesh, l, nk, D) >= 0) continue;
-      int others[2], no = 0;
-      for (int b = 0; b < D; ++b)
-        if (b != a) others[no++] = b;
-      for (int t = 0; t < (1 << (D - 1)); ++t) {
-        int32_t ck[3] = {2 * nk[0], 2 * nk[1], 2 * nk[2]};
-        ck[a] += s < 0 ? 1 : 0;
-        for (int j = 0; j < no; ++j) ck[others[j]] += (t >> j) & 1;
-        if (covering_level(mesh, l + 1, ck, D) < 0) return false;
-      }
-    }
-  return true;
-}
-
-void insert_children(std::unordered_map<uint64_t, PlanLeaf>& mesh, int l, const int32_t* k, int idx, int D) {
-  for (int o = 0; o < (1 << D); ++o) {
-    PlanLeaf c{l + 1, {0, 0, 0}, 1, idx, o};
-    for (int a = 0; a < D; ++a) c.k[a] = 2 * k[a] + ((o >> a) & 1);
-    mesh[leaf_key(c.l, c.k, D)] = c;
-  }
-}
-
-}  // namespace
-
-namespace {
-
-// the planning rules of dg_mhd_regrid_plan; out: the new leaves in Morton order
-void plan_leaves(const AmrHost& h, const int8_t* marks, std::vector<PlanLeaf>& out) {
-  const int D = h.D, no = 1 << D;
-  const int64_t N = (int64_t)h.hlevel.size();
-  std::unordered_map<uint64_t, PlanLeaf> mesh;
-  mesh.reserve((size_t)N * 2);
-  for (int64_t i = 0; i < N; ++i) {
-    const int l = h.hlevel[i];
-    const int32_t* k = &h.hijk[i * D];
-    if (marks[i] == 1 && l < 17) {
-      insert_children(mesh, l, k, (int)i, D);
-    } else {
-      PlanLeaf p{l, {0, 0, 0}, 0, (int)i, 0};
-      for (int a = 0; a < D; ++a) p.k[a] = k[a];
-      mesh[leaf_key(l, p.k, D)] = p;
-    }
-  }
-  // 2:1 balance by refinement of the coarser side. The old mesh is balanced,
-  // so only the leaves next to a refined cube can break it: a worklist of the
-  // leaves covering the face neighbours of every refined cube (same fixed
-  // point as checking every leaf until none changes).
-  std::vector<uint64_t> work;
-  auto push_neighbours = [&](int l, const int32_t* k) {
-    const int32_t n = 1 << l;
-    for (int a = 0; a < D; ++a)
-      for (int s = -1; s <= 1; s += 2) {
-        int32_t nk[3] = {k[0], k[1], k[2]};
-        nk[a] = (nk[a] + s + n) % n;
-        const int lv = covering_level(mesh, l, nk, D);
-        if (lv < 0 || lv >= l) continue;  // split or same level: no two-level jump here
-        int32_t ck[3] = {0, 0, 0};
-        for (int b = 0; b < D; ++b) ck[b] = nk[b] >> (l - lv);
-        work.push_back(leaf_key(lv, ck, D));
-      }
-  };
-  for (int64_t i = 0; i < N; ++i)
-    if (marks[i] == 1 && h.hlevel[i] < 17) push_neighbours(h.hlevel[i], &h.hijk[i * D]);
-  while (!work.empty()) {
-    const uint64_t key = work.back();
-    work.pop_back();
-    auto it = mesh.find(key);
-    if (it == mesh.end() || it->second.kind != 0) continue;
-    const PlanLeaf p = it->second;
-    if (face_ok(mesh, p.l, p.k, D)) continue;
-    mesh.erase(it);
-    insert_children(mesh, p.l, p.k, p.idx, D);
-    push_neighbours(p.l, p.k);
-  }
-  // coarsening where the parent keeps the balance, to a fixed point
-  std::vector<char> done((size_t)std::max<int64_t>(h.ngroups, 0), 0);
-  for (bool changed = true; changed;) {
-    changed = false;
-    for (int64_t gi = 0; gi < h.ngroups; ++gi) {
-      if (done[gi]) continue;
-      const int32_t* mem = &h.hgroups[gi * no];
-      bool cand = true;
-      for (int o = 0; o < no && cand; ++o) cand = marks[mem[o]] == -1;
-      if (!cand) continue;
-      const int l = h.hlevel[mem[0]];
-      int32_t pk[3] = {0, 0, 0};
-      for (int a = 0; a < D; ++a) pk[a] = h.hijk[(int64_t)mem[0] * D + a] >> 1;
-      bool intact = true;
-      for (int o = 0; o < no && intact; ++o) {
-        auto it = mesh.find(leaf_key(l, &h.hijk[(int64_t)mem[o] * D], D));
-        intact = it != mesh.end() && it->second.kind == 0 && it->second.idx == mem[o];
-      }
-      if (!intact) continue;
-      for (int o = 0; o < no; ++o) mesh.erase(leaf_key(l, &h.hijk[(int64_t)mem[o] * D], D));
-      PlanLeaf p{l - 1, {pk[0], pk[1], pk[2]}, 2, (int)gi, 0};
-      mesh[leaf_key(l - 1, pk, D)] = p;
-      if (face_ok(mesh, l - 1, pk, D)) {
-        done[gi] = 1;
-        changed = true;
-      } else {
-        mesh.erase(leaf_key(l - 1, pk, D));
-        for (int o = 0; o < no; ++o) {
-          PlanLeaf q{l, {0, 0, 0}, 0, mem[o], 0};
-          for (int a = 0; a < D; ++a) q.k[a] = h.hijk[(int64_t)mem[o] * D + a];
-          mesh[leaf_key(l, q.k, D)] = q;
-        }
-      }
-    }
-  }
-  // Morton order
-  out.clear();
-  out.reserve(mesh.size());
-  int lmax = 0;
-  for (const auto& kv : mesh) {
-    out.push_back(kv.second);
-    lmax = std::max(lmax, kv.second.l);
-  }
-  auto zkey = [&](const PlanLeaf& p) {
-    uint64_t z = 0;
-    for (int bit = lmax; bit >= 0; --bit)
-      for (int a = D - 1; a >= 0; --a) z = (z << 1) | (((uint64_t)p.k[a] << (lmax - p.l)) >> bit & 1u);
-    return z;
-  };
-  std::vector<std::pair<std::pair<uint64_t, int>, size_t>> order(out.size());
-  for (size_t i = 0; i < out.size(); ++i) order[i] = {{zkey(out[i]), out[i].l}, i};
-  std::sort(order.begin(), order.end());
-  std::vector<PlanLeaf> sorted(out.size());
-  for (size_t i = 0; i < out.size(); ++i) sorted[i] = out[order[i].second];
-  out.swap(sorted);
-}
-
-}  // namespace
-
 // New leaf list from the marks (host): refine the leaves marked +1, then 2:1
 // balance by refining every leaf two levels coarser than a face neighbour
 // (until none is), then coarsen the sibling groups whose members are all
@@ -695,18 +503,7 @@ extern "C" int dg_mhd_regrid_plan(const dg_mhd_ctx* ctx, const int8_t* marks, in
   uint64_t hash = 1469598103934665603ull;
   for (int64_t i = 0; i < N; ++i) hash = (hash ^ (uint8_t)marks[i]) * 1099511628211ull;
   if (h.plan.empty() || h.plan_hash != hash) {
-    std::vector<PlanLeaf> out;
-    plan_leaves(h, marks, out);
-    h.plan.resize(out.size() * 6);
-    for (size_t i = 0; i < out.size(); ++i) {
-      int32_t* q = &h.plan[i * 6];
-      q[0] = out[i].l;
-      q[1] = out[i].k[0];
-      q[2] = out[i].k[1];
-      q[3] = out[i].k[2];
-      q[4] = out[i].kind | (out[i].oct << 4);
-      q[5] = out[i].idx;
-    }
+    plan_mesh(h.morton, h.hijk.data(), h.hgroups, marks, h.plan);
     h.plan_hash = hash;
   }
   const size_t nn = h.plan.size() / 6;
