@@ -355,6 +355,15 @@ def run_ours(args, cfg, rank, world, device):
                 "steps": args.l1_steps, "quantity": "cell means, per variable: sum|a-b| / sum|b| "
                 "(variables with sum|b| < 1e-6 of the largest: / the largest)",
                 "values": [float(x) for x in l1.cpu()], "status": [s64.status(), s32.status()]}
+            if "blast" in cfg["name"]:
+                r64 = shock_radii(m64[0].cpu().numpy(), n)
+                r32 = shock_radii(m32[0].cpu().numpy(), n)
+                res["l1_fp32_learned_vs_fp64_plain"]["shock_radius"] = {
+                    "rays": ["+x", "+y", "+z", "(1,1,1)", "(-1,1,1)", "(1,-1,1)", "(-1,-1,1)"],
+                    "fp64_plain": r64, "fp32_learned": r32,
+                    "max_abs_diff": max((abs(a - b) for a, b in zip(r64, r32) if a is not None and b is not None),
+                                        default=None),
+                    "definition": "largest radius where rho reaches (max rho + 1) / 2, from the blast centre"}
         del s64, w64, s32, w32, wm32
         torch.cuda.empty_cache()
     return res
@@ -406,6 +415,35 @@ def cpu_baseline(cfg, nsample=24, steps=1, warmup=0, sample=None):
             "sample": f"SSP-RK3 steps of the same scheme and start on a {nsample}^3 periodic box"
                       f"{' (uniform stand-in for the octree)' if cfg.get('amr') else ''} "
                       f"({S.C} cells x {S.N} DoF), numpy FP64, single thread", "seconds": el}
+
+
+RAYS = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 1), (-1, 1, 1), (1, -1, 1), (-1, -1, 1)]
+
+
+def shock_radii(rho, n, center=(0.5, 0.5, 0.5), rho_bg=1.0):
+    """Shock position of a blast on a periodic n^3 unit box from the density
+    cell means rho [n^3] (x fastest): along the 3 axes and 4 diagonals from the
+    centre, the largest radius where rho reaches (max rho + rho_bg) / 2,
+    sampled every half cell and interpolated linearly between samples (None
+    where the ray never reaches it inside half the box)."""
+    import numpy as np
+    r3 = np.asarray(rho, dtype=np.float64).reshape(n, n, n)           # [k, j, i]
+    thr = 0.5 * (float(r3.max()) + rho_bg)
+    rs = np.arange(0.0, 0.5, 0.5 / n)
+    out = []
+    for ray in RAYS:
+        e = np.asarray(ray, dtype=np.float64) / math.sqrt(sum(x * x for x in ray))
+        pts = np.asarray(center)[None, :] + rs[:, None] * e[None, :]
+        idx = np.floor(pts * n).astype(np.int64) % n
+        vals = r3[idx[:, 2], idx[:, 1], idx[:, 0]]
+        above = np.nonzero(vals >= thr)[0]
+        if len(above) == 0 or above[-1] + 1 >= len(rs):
+            out.append(None)
+            continue
+        a = above[-1]
+        t = (vals[a] - thr) / (vals[a] - vals[a + 1]) if vals[a] != vals[a + 1] else 0.0
+        out.append(float(rs[a] + t * (rs[a + 1] - rs[a])))
+    return out
 
 
 def max_over_ranks(ms, world, device):

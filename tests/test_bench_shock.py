@@ -1,0 +1,43 @@
+"""The shock-position report of the blast runs (bench.shock_radii): on
+density fields with a known front, the radius along the 3 axes and 4
+diagonals is within one cell of it, centred or across the periodic wrap."""
+import math
+
+import numpy as np
+
+import bench
+
+
+def _field(n, fn, center):
+    c = (np.arange(n) + 0.5) / n
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    d = [x - center[0], y - center[1], z - center[2]]
+    d = [a - np.round(a) for a in d]                       # periodic distance
+    r = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+    return fn(r).reshape(-1)
+
+
+def test_sphere_radius_on_every_ray():
+    n = 64
+    rho = _field(n, lambda r: 1.0 + 2.0 * (r < 0.23), (0.5, 0.5, 0.5))
+    radii = bench.shock_radii(rho, n)
+    assert len(radii) == 7
+    assert all(abs(r - 0.23) < 1.0 / n for r in radii)
+
+
+def test_shell_half_maximum_off_centre_across_the_wrap():
+    """A Gaussian shell at r = 0.3 (width 0.02, peak 4 over a background of 1):
+    the outer half-maximum crossing is at 0.3 + 0.02 sqrt(ln 2)."""
+    n = 96
+    ctr = (0.15, 0.8, 0.5)
+    rho = _field(n, lambda r: 1.0 + 3.0 * np.exp(-((r - 0.3) / 0.02) ** 2), ctr)
+    want = 0.3 + 0.02 * math.sqrt(math.log(2.0))
+    radii = bench.shock_radii(rho, n, center=ctr)
+    assert all(abs(r - want) < 1.0 / n for r in radii)
+
+
+def test_no_front_inside_half_the_box():
+    n = 16
+    rho = np.ones(n ** 3)
+    rho[0] = 2.0                                           # a peak far from the centre's rays
+    assert bench.shock_radii(rho, n) == [None] * 7
