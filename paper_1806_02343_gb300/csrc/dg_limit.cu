@@ -554,7 +554,6 @@ __device__ void pos_cell(const Geom& g, const Tables<T>& tb, const LimTabs& lt, 
     }
   }
   const int npt = g.Qv + 2 * g.D * g.Qf;
-  const bool dbl = sizeof(T) == 8;
   const double pmean = pres(m);
   // per variable, sum of |coefficients| beyond the mean (x |basis| bound): with
   // |mean|, the scale of every point value, which bounds its rounding

@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(128) k_mlp_infer(Geom g, MlpTabs mt, const T* 
                                                    uint8_t* __restrict__ flag, float* __restrict__ prob,
                                                    int32_t* __restrict__ list, DevScalars* __restrict__ sc) {
   constexpr int LD1 = KP + 8, LD2 = HID + 8;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(smraw);
   __nv_bfloat16* W2s = W1s + HID * LD1;
   __nv_bfloat16* Xs = W2s + HID * LD2;

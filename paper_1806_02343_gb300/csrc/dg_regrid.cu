@@ -167,7 +167,6 @@ bool regrid_tables(const Basis& B, std::vector<double>& tab, RgLayout& L) {
 
 namespace {
 
-constexpr int RG_MAXN = 20;  // Legendre modes, degree <= 3
 constexpr int RG_MAXD = 50;  // LDF rows, degree <= 3
 
 struct RgDev {
@@ -497,7 +496,7 @@ extern "C" int dg_mhd_regrid_plan(const dg_mhd_ctx* ctx, const int8_t* marks, in
   int e = ensure_groups(c);
   if (e) return e;
   AmrHost& h = c.amr;
-  const int D = h.D, no = 1 << D;
+  const int D = h.D;
   const int64_t N = (int64_t)h.hlevel.size();
   // FNV-1a hash of the marks: a size query followed by the fill call plans once
   uint64_t hash = 1469598103934665603ull;
