@@ -24,6 +24,10 @@ import sys
 import threading
 import time
 
+# the CPU oracle legs report the threads they use: numpy's BLAS stays on one
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -402,21 +406,38 @@ def _oracle_sample(cfg, nsample):
     return S, w
 
 
-def cpu_baseline(cfg, nsample=24, steps=1, warmup=0, sample=None):
+def cpu_baseline(cfg, nsample=24, steps=1, warmup=0, sample=None, limited=True):
     """The CPU oracle as it stands: SSP-RK3 steps on a bounded sample (a
-    periodic nsample^3 box of the same scheme and initial condition)."""
+    periodic nsample^3 box of the same scheme and initial condition). With
+    `limited` (the GPU runs limit too) the oracle's TVB-characteristic and
+    positivity limiters act before every stage, as in the plain GPU path; the
+    dt of a step comes from its start, c_h (GLM) from that dt."""
     S, w = sample if sample is not None else _oracle_sample(cfg, nsample)
+    L = None
+    if limited:
+        from oracle.limiter import Limiter
+        L = Limiter(S, tvb=True, positivity=True)
+
+    def one(w):
+        if L is None:
+            return S.step(w)[0]
+        dt = S.dt(L(w, None) if S.divb == "powell" else w)
+        ch = S.glm_speeds(dt)[0] if S.divb == "glm" else None
+        return S.step(w, dt, limiter=lambda x: L(x, ch))[0]
+
     for _ in range(warmup):
-        S.step(w)
+        one(w)
     t0 = time.perf_counter()
     for _ in range(steps):
-        w, dt = S.step(w)
+        w = one(w)
     el = time.perf_counter() - t0
     dof = S.C * S.N
     return {"value": dof * 3 * steps / el, "unit": "DoF-updates/s", "cores": 1, "kind": "oracle",
             "sample": f"SSP-RK3 steps of the same scheme and start on a {nsample}^3 periodic box"
                       f"{' (uniform stand-in for the octree)' if cfg.get('amr') else ''} "
-                      f"({S.C} cells x {S.N} DoF), numpy FP64, single thread", "seconds": el}
+                      f"({S.C} cells x {S.N} DoF)"
+                      f"{', TVB-characteristic + positivity limiters before every stage' if limited else ''}, "
+                      f"numpy FP64, one thread (BLAS pinned to one)", "seconds": el, "w": w}
 
 
 RAYS = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 1), (-1, 1, 1), (1, -1, 1), (-1, -1, 1)]
@@ -569,7 +590,8 @@ def main():
         if rank != 0:
             return
         sample = _oracle_sample(cfg, args.cpu_sample)
-        cb = cpu_baseline(cfg, args.cpu_sample, steps=args.steps, warmup=args.warmup, sample=sample)
+        cb = cpu_baseline(cfg, args.cpu_sample, steps=args.steps, warmup=args.warmup, sample=sample,
+                          limited=args.limiter != "off")
         v = cb["value"]
         line = {"impl": "reference", "metric": "DG-MHD DoF-updates/s per RK stage", "value": v,
                 "unit": "DoF-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -598,7 +620,7 @@ def main():
         return
     config["l2_flush"] = (f"inputs larger than L2: the state is {res['state_bytes'] / 1e9:.2f} GB and every "
                           f"stage streams it (L2 129 MB)")
-    cb = cpu_baseline(cfg, args.cpu_sample)
+    cb = cpu_baseline(cfg, args.cpu_sample, limited=args.limiter != "off")
     line = {
         "metric": "DG-MHD DoF-updates/s per RK stage", "value": res["value"], "unit": "DoF-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps,

@@ -1,4 +1,5 @@
-"""The shock-position report of the blast runs (bench.shock_radii): on
+"""Host-side pieces of the bench: the shock-position report of the blast runs
+(bench.shock_radii) and the CPU baseline's sample. Shock radius: on
 density fields with a known front, the radius along the 3 axes and 4
 diagonals is within one cell of it, centred or across the periodic wrap."""
 import math
@@ -41,3 +42,20 @@ def test_no_front_inside_half_the_box():
     rho = np.ones(n ** 3)
     rho[0] = 2.0                                           # a peak far from the centre's rays
     assert bench.shock_radii(rho, n) == [None] * 7
+
+
+def test_cpu_baseline_sample_is_a_physical_run():
+    """The oracle's timed sample of the Mach-2 turbulence (an under-resolved
+    6^3 box) has negative pressure at face points: without limiters a step
+    turns non-finite, with the limiters the plain GPU path also runs (TVB +
+    positivity before every stage) it stays finite. The baseline times the
+    latter whenever the GPU run limits."""
+    import warnings
+    cfg = dict(bench.CONFIGS["turb256"], name="turb256")
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        plain = bench.cpu_baseline(cfg, 6, limited=False)
+        lim = bench.cpu_baseline(cfg, 6, limited=True)
+    assert not np.isfinite(plain["w"]).all()
+    assert np.isfinite(lim["w"]).all() and lim["value"] > 0 and lim["cores"] == 1
+    assert "positivity" in lim["sample"]
