@@ -13,7 +13,6 @@
 #include <cfloat>
 #include <cmath>
 #include <cstring>
-#include <unordered_map>
 #include <vector>
 
 #include "dg_amr.cuh"
@@ -467,99 +466,14 @@ int build_amr(Ctx& c, const dg_mesh_desc* mesh) {
   Geom& g = c.g;
   const int D = mesh->dim;
   const int64_t N = mesh->n_leaves;
-  if (N < 1 || N > ((int64_t)1 << 30)) return DG_E_MESH;
-  // key: level and coordinates (levels <= 20 so coordinates fit 21 bits)
-  auto key = [&](int l, int64_t i, int64_t j, int64_t k) -> uint64_t {
-    return ((uint64_t)l << 58) | ((uint64_t)i << 38) | ((uint64_t)j << 18) | (uint64_t)k;
-  };
-  std::unordered_map<uint64_t, int32_t> idx;
-  idx.reserve((size_t)N * 2);
-  int maxl = 0;
-  for (int64_t cidx = 0; cidx < N; ++cidx) {
-    const int l = mesh->level[cidx];
-    if (l < 0 || l > 17) return DG_E_MESH;
-    maxl = std::max(maxl, l);
-    int64_t k[3] = {0, 0, 0};
-    for (int a = 0; a < D; ++a) {
-      k[a] = mesh->ijk[cidx * D + a];
-      if (k[a] < 0 || k[a] >= ((int64_t)1 << l)) return DG_E_MESH;
-    }
-    if (!idx.emplace(key(l, k[0], k[1], k[2]), (int32_t)cidx).second) return DG_E_MESH;  // duplicate
-  }
-  // complete, non-overlapping cover: volumes sum to the box and no leaf has a leaf ancestor
-  unsigned long long vol = 0;
-  for (int64_t cidx = 0; cidx < N; ++cidx) {
-    const int l = mesh->level[cidx];
-    vol += 1ull << (D * (maxl - l));
-    int64_t k[3] = {0, 0, 0};
-    for (int a = 0; a < D; ++a) k[a] = mesh->ijk[cidx * D + a];
-    for (int j = 1; j <= l; ++j)
-      if (idx.count(key(l - j, k[0] >> j, k[1] >> j, k[2] >> j))) return DG_E_MESH;
-  }
-  if (vol != (1ull << (D * maxl))) return DG_E_MESH;
-  // faces
-  std::vector<int32_t> fL, fR, fmeta;
-  std::vector<std::vector<int32_t>> cell_ent(N);
-  for (int64_t cidx = 0; cidx < N; ++cidx) {
-    const int l = mesh->level[cidx];
-    const int64_t n = (int64_t)1 << l;
-    int64_t k[3] = {0, 0, 0};
-    for (int a = 0; a < D; ++a) k[a] = mesh->ijk[cidx * D + a];
-    for (int a = 0; a < D; ++a) {
-      int others[2], no = 0;
-      for (int b = 0; b < D; ++b)
-        if (b != a) others[no++] = b;
-      for (int s = -1; s <= 1; s += 2) {
-        int64_t kk[3] = {k[0], k[1], k[2]};
-        kk[a] = (kk[a] + s + n) % n;
-        auto it = idx.find(key(l, kk[0], kk[1], kk[2]));
-        if (it != idx.end()) {
-          if (s < 0) {
-            fL.push_back(it->second);
-            fR.push_back((int32_t)cidx);
-            fmeta.push_back(a);
-          }
-          continue;
-        }
-        if (l > 0) {
-          auto ip = idx.find(key(l - 1, kk[0] >> 1, kk[1] >> 1, kk[2] >> 1));
-          if (ip != idx.end()) {
-            int sub = 0;
-            for (int j = 0; j < no; ++j) sub |= (int)(k[others[j]] & 1) << j;
-            if (s < 0) {
-              fL.push_back(ip->second);
-              fR.push_back((int32_t)cidx);
-              fmeta.push_back(a | (1 << 2) | (sub << 4));
-            } else {
-              fL.push_back((int32_t)cidx);
-              fR.push_back(ip->second);
-              fmeta.push_back(a | (2 << 2) | (sub << 4));
-            }
-            continue;
-          }
-        }
-        // refined neighbour: all adjacent children must be leaves (2:1 balance)
-        for (int t = 0; t < (1 << (D - 1)); ++t) {
-          int64_t ch[3] = {2 * kk[0], 2 * kk[1], 2 * kk[2]};
-          ch[a] += s < 0 ? 1 : 0;
-          for (int j = 0; j < no; ++j) ch[others[j]] += (t >> j) & 1;
-          if (!idx.count(key(l + 1, ch[0], ch[1], ch[2]))) return DG_E_MESH;
-        }
-      }
-    }
-  }
-  const int64_t nf = (int64_t)fL.size();
-  for (int64_t f = 0; f < nf; ++f) {
-    cell_ent[fL[f]].push_back((int32_t)(f << 1));
-    cell_ent[fR[f]].push_back((int32_t)((f << 1) | 1));
-  }
-  std::vector<int32_t> cstart(N + 1, 0), centry;
+  // validation (a 2:1-balanced tiling of the cube) and the face lists, on the
+  // Morton index of the leaves (kept for regridding)
+  MortonIndex mi;
+  std::vector<int32_t> fL, fR, fmeta, cstart, centry;
   int maxent = 0;
-  for (int64_t cidx = 0; cidx < N; ++cidx) {
-    cstart[cidx + 1] = cstart[cidx] + (int32_t)cell_ent[cidx].size();
-    maxent = std::max(maxent, (int)cell_ent[cidx].size());
-    for (int32_t e : cell_ent[cidx]) centry.push_back(e);
-  }
+  const int ef = octree_faces(D, N, mesh->level, mesh->ijk, mi, fL, fR, fmeta, cstart, centry, maxent);
+  if (ef) return ef;
+  const int64_t nf = (int64_t)fL.size();
   std::vector<double> dxc(N);
   for (int64_t cidx = 0; cidx < N; ++cidx) dxc[cidx] = mesh->box_len / (double)(1ll << mesh->level[cidx]);
   // sub-face tables (coarse side), for each face f of the coarse cell and sub-face s
@@ -595,6 +509,7 @@ int build_amr(Ctx& c, const dg_mesh_desc* mesh) {
   h.D = D;
   h.hlevel.assign(mesh->level, mesh->level + N);
   h.hijk.assign(mesh->ijk, mesh->ijk + N * D);
+  h.morton = std::move(mi);
   h.nface = nf;
   h.maxent = maxent;
   h.nsub = nsub;

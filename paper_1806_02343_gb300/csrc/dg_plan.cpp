@@ -167,6 +167,86 @@ bool mesh_balanced(const MortonIndex& mi, const int32_t* ijk) {
   return true;
 }
 
+int octree_faces(int D, int64_t N, const int8_t* level, const int32_t* ijk, MortonIndex& mi,
+                 std::vector<int32_t>& fL, std::vector<int32_t>& fR, std::vector<int32_t>& fmeta,
+                 std::vector<int32_t>& cstart, std::vector<int32_t>& centry, int& maxent) {
+  if (N < 1 || N > ((int64_t)1 << 30)) return DG_E_MESH;
+  if (morton_index(D, N, level, ijk, mi) != DG_OK) return DG_E_MESH;
+  fL.clear();
+  fR.clear();
+  fmeta.clear();
+  fL.reserve((size_t)(N * D + N / 2));
+  fR.reserve((size_t)(N * D + N / 2));
+  fmeta.reserve((size_t)(N * D + N / 2));
+  for (int64_t cidx = 0; cidx < N; ++cidx) {
+    const int l = level[cidx];
+    const int32_t n = 1 << l;
+    const int32_t* k = &ijk[cidx * D];
+    const int64_t p = mi.position((int32_t)cidx);
+    for (int a = 0; a < D; ++a) {
+      int others[2], no = 0;
+      for (int b = 0; b < D; ++b)
+        if (b != a) others[no++] = b;
+      for (int s = -1; s <= 1; s += 2) {
+        int32_t nk[3] = {k[0], k[1], D == 3 ? k[2] : 0};
+        nk[a] = (nk[a] + s + n) % n;
+        // the leaf holding the corner of the same-level neighbour cube
+        const int64_t q = locate(mi.start, morton(D, mi.R, l, nk), p);
+        const int lq = mi.lev[q];
+        if (lq == l) {  // same level: listed once, by the right cell
+          if (s < 0) {
+            fL.push_back(mi.leaf(q));
+            fR.push_back((int32_t)cidx);
+            fmeta.push_back(a);
+          }
+          continue;
+        }
+        if (lq == l - 1) {  // coarser neighbour: listed by this (fine) cell
+          int sub = 0;
+          for (int j = 0; j < no; ++j) sub |= (int)(k[others[j]] & 1) << j;
+          if (s < 0) {
+            fL.push_back(mi.leaf(q));
+            fR.push_back((int32_t)cidx);
+            fmeta.push_back(a | (1 << 2) | (sub << 4));
+          } else {
+            fL.push_back((int32_t)cidx);
+            fR.push_back(mi.leaf(q));
+            fmeta.push_back(a | (2 << 2) | (sub << 4));
+          }
+          continue;
+        }
+        if (lq < l - 1) return DG_E_MESH;  // two levels coarser
+        // split neighbour: its children along the face must be leaves (2:1)
+        for (int t = 0; t < (1 << (D - 1)); ++t) {
+          int32_t ch[3] = {2 * nk[0], 2 * nk[1], 2 * nk[2]};
+          ch[a] += s < 0 ? 1 : 0;
+          for (int j = 0; j < no; ++j) ch[others[j]] += (t >> j) & 1;
+          if (mi.lev[locate(mi.start, morton(D, mi.R, l + 1, ch), q)] != l + 1) return DG_E_MESH;
+        }
+      }
+    }
+  }
+  // per-cell entries in face order (counting sort)
+  const int64_t nf = (int64_t)fL.size();
+  cstart.assign((size_t)N + 1, 0);
+  for (int64_t f = 0; f < nf; ++f) {
+    ++cstart[fL[f] + 1];
+    ++cstart[fR[f] + 1];
+  }
+  maxent = 0;
+  for (int64_t c = 0; c < N; ++c) {
+    maxent = std::max(maxent, cstart[c + 1]);
+    cstart[c + 1] += cstart[c];
+  }
+  centry.assign((size_t)cstart[N], 0);
+  std::vector<int32_t> fill(cstart.begin(), cstart.end() - 1);
+  for (int64_t f = 0; f < nf; ++f) {
+    centry[fill[fL[f]]++] = (int32_t)(f << 1);
+    centry[fill[fR[f]]++] = (int32_t)((f << 1) | 1);
+  }
+  return DG_OK;
+}
+
 void sibling_groups(const MortonIndex& mi, const int32_t* ijk, std::vector<int32_t>& groups) {
   const int D = mi.D, no = 1 << D;
   // In Morton order a complete group is a run of 2^D leaves of one level that

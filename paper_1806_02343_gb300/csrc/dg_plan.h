@@ -33,6 +33,19 @@ int morton_index(int D, int64_t N, const int8_t* level, const int32_t* ijk, Mort
 // No two face neighbours differ by more than one level (periodic box).
 bool mesh_balanced(const MortonIndex& mi, const int32_t* ijk);
 
+// Faces of an octree mesh for the operator's surface integrals (Sec. 3.5) with
+// coarse-fine faces (Sec. 4.4), and the validation of a context's mesh: the
+// leaves tile the cube (morton_index) and are 2:1 balanced, else DG_E_MESH.
+// Cells in the given order; per cell, axes in order and the lower side first:
+// a same-level face is listed by its right cell (fL = left neighbour, fR =
+// cell, meta = axis); a coarse-fine face by its fine cell (meta = axis | side
+// << 2 | sub-face << 4, side 1 when the coarse cell is on the left, 2 when on
+// the right; sub-face = the fine cell's octant bits across the face). cstart /
+// centry: per cell its face entries (2 f + (cell is fR)) in face order.
+int octree_faces(int D, int64_t N, const int8_t* level, const int32_t* ijk, MortonIndex& mi,
+                 std::vector<int32_t>& fL, std::vector<int32_t>& fR, std::vector<int32_t>& fmeta,
+                 std::vector<int32_t>& cstart, std::vector<int32_t>& centry, int& maxent);
+
 // Groups of 2^D sibling leaves (the children of one cube, all leaves), sorted by
 // (parent level, parent coordinates); groups[g * 2^D + o] = leaf index of octant o.
 void sibling_groups(const MortonIndex& mi, const int32_t* ijk, std::vector<int32_t>& groups);

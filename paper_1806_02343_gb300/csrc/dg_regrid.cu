@@ -393,8 +393,10 @@ int ensure_groups(Ctx& c) {
   if (h.ngroups >= 0) return DG_OK;
   const int D = h.D, no = 1 << D;
   const int64_t N = (int64_t)h.hlevel.size();
-  const int e = morton_index(D, N, h.hlevel.data(), h.hijk.data(), h.morton);
-  if (e) return e;
+  if (h.morton.N != N) {  // built with the face lists at init
+    const int e = morton_index(D, N, h.hlevel.data(), h.hijk.data(), h.morton);
+    if (e) return e;
+  }
   sibling_groups(h.morton, h.hijk.data(), h.hgroups);
   if (!h.groups && cudaMalloc(&h.groups, std::max<size_t>(1, h.hgroups.size()) * sizeof(int32_t)) != cudaSuccess)
     return DG_E_CUDA;
