@@ -183,15 +183,28 @@ int octree_faces(int D, int64_t N, const int8_t* level, const int32_t* ijk, Mort
     const int32_t n = 1 << l;
     const int32_t* k = &ijk[cidx * D];
     const int64_t p = mi.position((int32_t)cidx);
+    // When the cell's 2^D siblings are all leaves (a run of its level in Morton
+    // order ending the parent's range), the leaf across a face inside the
+    // parent is the sibling of octant o ^ (1 << a): no search.
+    int oct = 0;
+    for (int a = 0; a < D; ++a) oct |= (k[a] & 1) << a;
+    const int64_t first = p - oct;
+    bool group = l > 0 && first >= 0 && first + (1 << D) <= N;
+    for (int o = 0; o < (1 << D) && group; ++o) group = mi.lev[first + o] == l;
     for (int a = 0; a < D; ++a) {
       int others[2], no = 0;
       for (int b = 0; b < D; ++b)
         if (b != a) others[no++] = b;
       for (int s = -1; s <= 1; s += 2) {
-        int32_t nk[3] = {k[0], k[1], D == 3 ? k[2] : 0};
-        nk[a] = (nk[a] + s + n) % n;
-        // the leaf holding the corner of the same-level neighbour cube
-        const int64_t q = locate(mi.start, morton(D, mi.R, l, nk), p);
+        int64_t q;
+        if (group && ((oct >> a) & 1) == (s < 0 ? 1 : 0)) {
+          q = first + (oct ^ (1 << a));
+        } else {
+          // the leaf holding the corner of the same-level neighbour cube
+          int32_t nk[3] = {k[0], k[1], D == 3 ? k[2] : 0};
+          nk[a] = (nk[a] + s + n) % n;
+          q = locate(mi.start, morton(D, mi.R, l, nk), p);
+        }
         const int lq = mi.lev[q];
         if (lq == l) {  // same level: listed once, by the right cell
           if (s < 0) {
@@ -217,6 +230,8 @@ int octree_faces(int D, int64_t N, const int8_t* level, const int32_t* ijk, Mort
         }
         if (lq < l - 1) return DG_E_MESH;  // two levels coarser
         // split neighbour: its children along the face must be leaves (2:1)
+        int32_t nk[3] = {k[0], k[1], D == 3 ? k[2] : 0};
+        nk[a] = (nk[a] + s + n) % n;
         for (int t = 0; t < (1 << (D - 1)); ++t) {
           int32_t ch[3] = {2 * nk[0], 2 * nk[1], 2 * nk[2]};
           ch[a] += s < 0 ? 1 : 0;
