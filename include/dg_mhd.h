@@ -338,6 +338,20 @@ int dg_mhd_regrid_plan_mesh(int dim, int64_t n, const int8_t* level, const int32
 int dg_mhd_sibling_groups(int dim, int64_t n, const int8_t* level, const int32_t* ijk, int64_t cap,
                           int32_t* groups, int64_t* n_groups);
 
+/* The faces a context builds for an octree mesh (HOST arrays, no context; Sec.
+ * 3.5 surface integrals, coarse-fine faces as in dg_mesh_desc): the mesh rules
+ * of dg_mesh_desc (DG_E_MESH otherwise; DG_E_ARG for dim not 2 or 3). Cells in
+ * the given order, per cell its axes in order, the lower side first; a
+ * same-level face is listed once by its right (upper) cell, a coarse-fine face
+ * by its fine cell. Face f: face_left[f] / face_right[f] = the cells below /
+ * above it along the axis (periodic wrap), face_meta[f] = axis | kind << 2 |
+ * sub << 4, kind 0 same level, 1 coarse cell on the left, 2 on the right, sub
+ * = the fine cell's coordinate parities across the face (bit j for the j-th
+ * other axis in increasing order). Writes *n_faces and, if the three arrays
+ * are non-NULL and cap >= *n_faces, the faces (DG_E_ARG if cap is too small). */
+int dg_mhd_octree_faces(int dim, int64_t n, const int8_t* level, const int32_t* ijk, int64_t cap,
+                        int32_t* face_left, int32_t* face_right, int32_t* face_meta, int64_t* n_faces);
+
 /* State of the new context from the old one (asynchronous on stream): per new
  * leaf a copy, an L2 prolongation (parent octant onto the child's basis; the
  * LDF rows under the vector inner product of eq. innerp) or an L2 restriction

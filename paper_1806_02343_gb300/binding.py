@@ -26,7 +26,7 @@ EXPORTS = [
     "dg_mhd_strerror", "dg_mhd_mlp_features", "dg_mhd_mlp_set_weights", "dg_mhd_mlp_infer", "dg_mhd_mlp_loss_grad",
     "dg_mhd_mlp_train", "dg_mhd_counters", "dg_mhd_limiter_counts", "dg_mhd_divb", "dg_mhd_smoothness",
     "dg_mhd_amr_marks", "dg_mhd_regrid_plan", "dg_mhd_remap", "dg_mhd_regrid_plan_mesh",
-    "dg_mhd_sibling_groups",
+    "dg_mhd_sibling_groups", "dg_mhd_octree_faces",
 ]
 KIND_FACE, KIND_CELL, KIND_DT, KIND_LIMIT, KIND_PROJECT, KIND_POSITIVITY, KIND_MLP = range(7)
 
@@ -94,6 +94,7 @@ def lib():
     L.dg_mhd_remap.argtypes = [vp, vp, vp, vp, dp, vp, dp, vp]
     L.dg_mhd_regrid_plan_mesh.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, vp, ctypes.c_int64, vp, vp, vp, i64p]
     L.dg_mhd_sibling_groups.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_int64, vp, i64p]
+    L.dg_mhd_octree_faces.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_int64, vp, vp, vp, i64p]
     L.dg_mhd_destroy.argtypes = [vp]
     L.dg_mhd_destroy.restype = None
     L.dg_mhd_strerror.argtypes = [ctypes.c_int]
@@ -168,6 +169,20 @@ def sibling_groups(levels, ijk):
     _check(lib().dg_mhd_sibling_groups(dim, n, lev.ctypes.data, k.ctypes.data, ng.value, out.ctypes.data,
                                        ctypes.byref(ng)), "dg_mhd_sibling_groups")
     return out
+
+
+def octree_faces(levels, ijk):
+    """Faces of an octree mesh as a context builds them (host, no GPU): int32
+    arrays left cell, right cell, meta (axis | kind << 2 | sub << 4)."""
+    import numpy as np
+    lev, k = _leaf_arrays(levels, ijk)
+    dim, n, nf = k.shape[1], lev.shape[0], ctypes.c_int64()
+    _check(lib().dg_mhd_octree_faces(dim, n, lev.ctypes.data, k.ctypes.data, 0, None, None, None, ctypes.byref(nf)),
+           "dg_mhd_octree_faces")
+    out = [np.zeros(nf.value, dtype=np.int32) for _ in range(3)]
+    _check(lib().dg_mhd_octree_faces(dim, n, lev.ctypes.data, k.ctypes.data, nf.value, *(o.ctypes.data for o in out),
+                                     ctypes.byref(nf)), "dg_mhd_octree_faces")
+    return tuple(out)
 
 
 def regrid_plan_mesh(levels, ijk, marks):

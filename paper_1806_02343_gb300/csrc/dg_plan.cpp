@@ -496,3 +496,22 @@ extern "C" int dg_mhd_regrid_plan_mesh(int dim, int64_t n, const int8_t* level, 
   }
   return DG_OK;
 }
+
+extern "C" int dg_mhd_octree_faces(int dim, int64_t n, const int8_t* level, const int32_t* ijk, int64_t cap,
+                                   int32_t* face_left, int32_t* face_right, int32_t* face_meta, int64_t* n_faces) {
+  if (!n_faces || !level || !ijk) return DG_E_ARG;
+  if (dim != 2 && dim != 3) return DG_E_ARG;
+  dgmhd::MortonIndex mi;
+  std::vector<int32_t> fL, fR, fmeta, cstart, centry;
+  int maxent = 0;
+  const int e = dgmhd::octree_faces(dim, n, level, ijk, mi, fL, fR, fmeta, cstart, centry, maxent);
+  if (e) return e;
+  const int64_t nf = (int64_t)fL.size();
+  *n_faces = nf;
+  if (!face_left || !face_right || !face_meta) return DG_OK;  // size query
+  if (cap < nf) return DG_E_ARG;
+  std::copy(fL.begin(), fL.end(), face_left);
+  std::copy(fR.begin(), fR.end(), face_right);
+  std::copy(fmeta.begin(), fmeta.end(), face_meta);
+  return DG_OK;
+}

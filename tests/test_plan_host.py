@@ -191,3 +191,36 @@ def test_rejects_invalid_meshes_and_marks(B):
     mk[0] = 2
     assert code(lev, ijk, mk) == -1                                       # mark outside {-1, 0, 1}
     assert code(np.full(1, 18, np.int8), np.zeros((1, 2), np.int32), np.zeros(1, np.int8)) == -2
+
+
+@pytest.mark.parametrize("name", sorted(MESHES) + ["3d_ball_shuffled", "one_leaf"])
+def test_octree_faces_match_oracle(B, name):
+    """The face list a context builds (dg_mhd_octree_faces) equals the
+    oracle's, face by face: left cell, right cell, axis, kind, sub-face."""
+    from oracle.amr import AMRScheme
+    if name == "3d_ball_shuffled":
+        leaves = MESHES["3d_ball"]()
+        leaves = [leaves[i] for i in np.random.default_rng(5).permutation(len(leaves))]
+    elif name == "one_leaf":
+        leaves = [(0, (0, 0, 0))]
+    else:
+        leaves = MESHES[name]()
+    D = len(leaves[0][1])
+    A = AMRScheme(D, 1, "glm", 5.0 / 3.0, leaves)
+    fl, fr, meta = B.octree_faces(*_arrays(leaves))
+    ref = np.array([(cl, cr, a | (kind << 2) | (sub << 4)) for cl, cr, a, kind, sub in A.faces], dtype=np.int32)
+    assert len(ref) > 0
+    assert np.array_equal(np.stack([fl, fr, meta], 1), ref)
+    if name.startswith("3d_ball"):
+        assert ((meta >> 2) & 3 == 1).any() and ((meta >> 2) & 3 == 2).any()    # coarse-fine both ways
+
+
+def test_octree_faces_reject_invalid_meshes(B):
+    from paper_1806_02343_gb300.binding import DGError
+    uni = [(2, k) for k in itertools.product(range(4), repeat=2)]
+    unb = [(1, (1, 0)), (1, (0, 1)), (1, (1, 1))] + [(2, (1, 0)), (2, (0, 1)), (2, (1, 1))] + \
+          [(3, (0, 0)), (3, (1, 0)), (3, (0, 1)), (3, (1, 1))]
+    for bad in (uni[1:], uni + [(1, (0, 0))], uni + [uni[3]], unb):
+        with pytest.raises(DGError) as e:
+            B.octree_faces(*_arrays(bad))
+        assert e.value.code == -2
