@@ -142,6 +142,20 @@ int dg_mhd_state_layout(const dg_mhd_ctx* ctx, int64_t* n_rows, int64_t* n_mean_
 int dg_mhd_project(dg_mhd_ctx* ctx, const double* nodal, int npts, void* w, double* wmean,
                    void* stream);
 
+/* The basis as a linear map from state rows to point values (HOST, no
+ * context, no device work; Sec. 3.1 eq. u-exp, Sec. 3.2-3.3): for npts
+ * reference points xi[p*dim + a] in [-1, 1]^dim of a cell,
+ * out[(r*n_vars + v)*npts + p] = the value of conserved variable v at point p
+ * of the field whose only non-zero weight is a 1 in state row r (the rows of
+ * the state layout above: a Legendre row feeds its own variable, an LDF row
+ * B_x, B_y (, B_z)). So u_v(xi_p) = sum_r out[r][v][p] w[r][cell]. Writes
+ * *n_rows and *n_vars (9 GLM, 8 Powell) and, if out is non-NULL and cap >=
+ * n_rows*n_vars*npts doubles, out (DG_E_ARG if too small; DG_E_ARG for dim
+ * not 2 or 3, degree outside 0..3, an unknown scheme, npts outside
+ * 0..2^24 or xi NULL with npts > 0). */
+int dg_mhd_basis_values(int dim, int degree, int divB_scheme, int64_t npts, const double* xi, int64_t cap,
+                        double* out, int* n_rows, int* n_vars);
+
 /* Sets the GLM wave speed c_h and damping rate c_h^2/c_p^2 used by
  * dg_mhd_rhs (Sec. 4.1.5). dg_mhd_dt and dg_mhd_step set them on the device
  * themselves; this call is for evaluating the operator at chosen values. */

@@ -8,6 +8,7 @@ is missing, `lib()` raises.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -26,7 +27,7 @@ EXPORTS = [
     "dg_mhd_strerror", "dg_mhd_mlp_features", "dg_mhd_mlp_set_weights", "dg_mhd_mlp_infer", "dg_mhd_mlp_loss_grad",
     "dg_mhd_mlp_train", "dg_mhd_counters", "dg_mhd_limiter_counts", "dg_mhd_divb", "dg_mhd_smoothness",
     "dg_mhd_amr_marks", "dg_mhd_regrid_plan", "dg_mhd_remap", "dg_mhd_regrid_plan_mesh",
-    "dg_mhd_sibling_groups", "dg_mhd_octree_faces",
+    "dg_mhd_sibling_groups", "dg_mhd_octree_faces", "dg_mhd_basis_values",
 ]
 KIND_FACE, KIND_CELL, KIND_DT, KIND_LIMIT, KIND_PROJECT, KIND_POSITIVITY, KIND_MLP = range(7)
 
@@ -95,6 +96,9 @@ def lib():
     L.dg_mhd_regrid_plan_mesh.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, vp, ctypes.c_int64, vp, vp, vp, i64p]
     L.dg_mhd_sibling_groups.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_int64, vp, i64p]
     L.dg_mhd_octree_faces.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_int64, vp, vp, vp, i64p]
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.dg_mhd_basis_values.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp, ctypes.c_int64, vp,
+                                      ip, ip]
     L.dg_mhd_destroy.argtypes = [vp]
     L.dg_mhd_destroy.restype = None
     L.dg_mhd_strerror.argtypes = [ctypes.c_int]
@@ -169,6 +173,76 @@ def sibling_groups(levels, ijk):
     _check(lib().dg_mhd_sibling_groups(dim, n, lev.ctypes.data, k.ctypes.data, ng.value, out.ctypes.data,
                                        ctypes.byref(ng)), "dg_mhd_sibling_groups")
     return out
+
+
+def basis_values(dim, degree, divb, xi):
+    """The basis at reference points xi [P, dim] in [-1, 1]^dim (host, no GPU):
+    float64 [rows, vars, P]; u_v(xi_p) = sum_r out[r, v, p] w[r]."""
+    import numpy as np
+    x = np.ascontiguousarray(xi, dtype=np.float64).reshape(-1, dim)
+    scheme = DG_DIVB_GLM if divb == "glm" else DG_DIVB_POWELL
+    R, V = ctypes.c_int(), ctypes.c_int()
+    P = x.shape[0]
+    _check(lib().dg_mhd_basis_values(dim, degree, scheme, P, x.ctypes.data, 0, None, ctypes.byref(R),
+                                     ctypes.byref(V)), "dg_mhd_basis_values")
+    out = np.zeros((R.value, V.value, P), dtype=np.float64)
+    _check(lib().dg_mhd_basis_values(dim, degree, scheme, P, x.ctypes.data, out.size, out.ctypes.data,
+                                     ctypes.byref(R), ctypes.byref(V)), "dg_mhd_basis_values")
+    return out
+
+
+def cell_points(dim, npts, box_len=1.0, n=None, levels=None, ijk=None, device="cpu"):
+    """Physical coordinates of the npts^dim Gauss-Legendre points of every cell
+    in the order dg_mhd_project takes them (cells in mesh order; points with
+    the last axis fastest): float64 [cells, npts^dim, dim]. Uniform box: n
+    cells per axis of size box_len / n[0], numbered x-fastest; octree: levels
+    and ijk [cells, dim] in a cube of side box_len."""
+    import numpy as np
+    import torch
+    g, _ = np.polynomial.legendre.leggauss(npts)
+    g = torch.as_tensor(g, dtype=torch.float64, device=device)
+    grids = torch.meshgrid(*([g] * dim), indexing="ij")
+    qp = torch.stack([x.reshape(-1) for x in grids], -1)           # [Q, dim]
+    if levels is None:
+        nn = [int(x) for x in list(n)[:dim]]
+        r = torch.arange(int(np.prod(nn)), device=device)
+        ks = []
+        for a in range(dim):
+            ks.append(r % nn[a])
+            r = r // nn[a]
+        k = torch.stack(ks, -1).to(torch.float64)
+        size = torch.full((k.shape[0], 1), box_len / nn[0], dtype=torch.float64, device=device)
+    else:
+        lev = torch.as_tensor(np.asarray(levels, dtype=np.float64), device=device)
+        size = (box_len / torch.pow(2.0, lev))[:, None]
+        k = torch.as_tensor(np.asarray(ijk, dtype=np.float64).reshape(-1, dim), device=device)
+    centers = (k + 0.5) * size
+    return centers[:, None, :] + 0.5 * size[:, None, :] * qp[None, :, :]
+
+
+def mean_rows(dim, degree, divb, nrows):
+    """State rows of the degree-0 fields, in the order of the FP64 mean array:
+    Legendre mode 0 of each variable, then the degree-0 LDF rows, row order."""
+    n = math.comb(degree + dim, dim)
+    if divb == "glm":
+        return [v * n for v in range(9)]
+    rows = [v * n for v in range(5)] + [5 * n + j for j in range(dim)]
+    if dim == 2:
+        rows.append(nrows - n)                     # B_z mode 0 after the LDF rows
+    return rows
+
+
+def eval_points(table, w, mean=None, wmean=None):
+    """Point values [vars, P, cells] (float64) from the basis table of
+    basis_values [rows, vars, P] and state rows w [rows, cells] (any device);
+    with wmean [len(mean), cells] the FP64 means replace the float mean rows."""
+    import torch
+    W = w.to(torch.float64)
+    if wmean is not None:
+        W = W.clone()
+        W[mean] = wmean.to(torch.float64)
+    T = torch.as_tensor(table, dtype=torch.float64, device=W.device)
+    return torch.einsum("rvp,rc->vpc", T, W)
 
 
 def octree_faces(levels, ijk):
@@ -253,6 +327,7 @@ class Solver:
         if leaves is not None:
             levels = [l for l, _ in leaves]
             ijk = [k for _, k in leaves]
+        self._n, self._lev, self._ijk = (nn[:dim] if levels is None else None), None, None
         if levels is not None:
             self._lev = np.ascontiguousarray(np.asarray(levels, dtype=np.int8))
             self._ijk = np.ascontiguousarray(np.asarray(ijk, dtype=np.int32).reshape(-1))
@@ -281,6 +356,33 @@ class Solver:
                 self.h = None
         except Exception:
             pass
+
+    # ------------------------------------------------------------- point values
+    def project_ic(self, fn, w, wmean=None, npts=None):
+        """L2 projection of fn onto the basis (dg_mhd_project): fn takes the
+        cells' Gauss points x [cells, points, dim] (float64 on w's device) and
+        returns the conserved variables [cells, points, vars]; npts points per
+        axis (default degree + 3, at most 8). Holds [vars][points][stride]
+        doubles at once: for very large meshes fill dg_mhd_project's input in
+        slabs instead."""
+        import torch
+        npts = npts or min(8, self.degree + 3)
+        x = cell_points(self.dim, npts, self.box_len, self._n, self._lev, self._ijk, w.device)
+        u = fn(x)
+        nodal = torch.zeros((u.shape[-1], x.shape[1], self.stride), dtype=torch.float64, device=w.device)
+        nodal[:, :, : self.ncell] = torch.as_tensor(u, dtype=torch.float64, device=w.device).permute(2, 1, 0)
+        self.project(nodal, npts, w, wmean)
+
+    def mean_rows(self):
+        return mean_rows(self.dim, self.degree, self.divb, self.nrows)
+
+    def eval_at_points(self, w, wmean=None, xi=None):
+        """Conserved variables at reference points xi [P, dim] in [-1, 1]^dim
+        of every cell: float64 [vars, P, ncell] on w's device (the FP64 means
+        used where given), independent of the basis ordering."""
+        table = basis_values(self.dim, self.degree, self.divb, xi)
+        wm = None if wmean is None else wmean[:, : self.ncell]
+        return eval_points(table, w[:, : self.ncell], self.mean_rows(), wm)
 
     # ------------------------------------------------------------- buffers
     def alloc_state(self, device="cuda"):

@@ -257,3 +257,42 @@ void gauss_legendre(int npts, std::vector<double>& x, std::vector<double>& w) {
 }
 
 }  // namespace dgmhd
+
+// ------------------------------------------------------------------ C ABI
+
+#include "../../include/dg_mhd.h"
+
+extern "C" int dg_mhd_basis_values(int dim, int degree, int divB_scheme, int64_t npts, const double* xi,
+                                   int64_t cap, double* out, int* n_rows, int* n_vars) {
+  if (!n_rows || !n_vars || (dim != 2 && dim != 3) || degree < 0 || degree > 3 ||
+      (divB_scheme != DG_DIVB_POWELL && divB_scheme != DG_DIVB_GLM) || npts < 0 || npts > (1 << 24) ||
+      (npts > 0 && !xi))
+    return DG_E_ARG;
+  const bool glm = divB_scheme == DG_DIVB_GLM;
+  dgmhd::Basis B;
+  if (!B.build(dim, degree, !glm)) return DG_E_ARG;
+  const int n = B.n, V = glm ? 9 : 8;
+  const int R = glm ? 9 * n : 5 * n + B.ndiv + (dim == 2 ? n : 0);
+  *n_rows = R;
+  *n_vars = V;
+  if (!out) return DG_OK;  // size query
+  if (cap < (int64_t)R * V * npts) return DG_E_ARG;
+  std::fill(out, out + (int64_t)R * V * npts, 0.0);
+  auto at = [&](int r, int v, int64_t p) -> double& { return out[((int64_t)r * V + v) * npts + p]; };
+  for (int64_t p = 0; p < npts; ++p) {
+    double x[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < dim; ++a) x[a] = xi[p * dim + a];
+    std::vector<double> leg(n);
+    for (int l = 0; l < n; ++l) leg[l] = B.eval(B.leg[l], x);
+    const int nleg = glm ? 9 : 5;  // variables carried by Legendre rows in row order
+    for (int v = 0; v < nleg; ++v)
+      for (int l = 0; l < n; ++l) at(v * n + l, v, p) = leg[l];
+    if (!glm) {
+      for (int j = 0; j < B.ndiv; ++j)
+        for (int c = 0; c < dim; ++c) at(5 * n + j, 5 + c, p) = B.eval(B.ldf[j][c], x);
+      if (dim == 2)
+        for (int l = 0; l < n; ++l) at(5 * n + B.ndiv + l, 7, p) = leg[l];
+    }
+  }
+  return DG_OK;
+}

@@ -1,0 +1,97 @@
+"""The library's host basis generator (Legendre products and the LDF basis of
+Sec. 3.2-3.3 / App. A.2, built in double precision) through the context-free
+C ABI dg_mhd_basis_values, against the oracle's exact-rational basis
+(Scheme.synth): every state row's field at reference points, for 2D and 3D,
+degrees 0-3, both schemes. Also the mean-row list and point evaluation of the
+binding (eval_points) against the oracle's eval_points. CPU only."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle.dg import Scheme
+from paper_1806_02343_gb300 import workloads as W
+
+G = 5.0 / 3.0
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1806_02343_gb300 import build, binding
+    build.build()
+    return binding
+
+
+def _points(D, seed=0):
+    rng = np.random.default_rng(seed)
+    corners = np.array(list(itertools.product((-1.0, 1.0), repeat=D)))
+    return np.vstack([rng.uniform(-1, 1, (17, D)), corners, np.zeros((1, D))])
+
+
+CASES = [(D, d, divb) for D in (2, 3) for d in range(4) for divb in ("glm", "powell")]
+
+
+@pytest.mark.parametrize("D,d,divb", CASES)
+def test_basis_values_match_oracle(B, D, d, divb):
+    S = Scheme(D, d, divb, G, 2)
+    pts = _points(D, seed=d)
+    got = B.basis_values(D, d, divb, pts)                 # [rows, vars, P]
+    ref = S.synth(pts).transpose(0, 2, 1)                 # [rows, vars, P]
+    assert got.shape == ref.shape
+    assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("D,d,divb", CASES)
+def test_mean_rows_are_the_degree_zero_rows(B, D, d, divb):
+    S = Scheme(D, d, divb, G, 2)
+    assert B.mean_rows(D, d, divb, S.N) == np.flatnonzero(S.is_mean).tolist()
+
+
+@pytest.mark.parametrize("divb", ["glm", "powell"])
+def test_eval_points_matches_oracle(B, divb):
+    import torch
+    S = Scheme(3, 2, divb, G, (3, 3, 2))
+    w0 = S.project(W.SmoothFourier3D(nvar=S.V))
+    pts = _points(3, seed=7)
+    ref = S.eval_points(w0, S.synth(pts))                 # [cells, P, vars]
+    table = B.basis_values(3, 2, divb, pts)
+    got = B.eval_points(table, torch.as_tensor(w0.T.copy())).numpy()   # [vars, P, cells]
+    assert np.abs(got.transpose(2, 1, 0) - ref).max() <= 1e-13 * np.abs(ref).max()
+    # FP32 rows with the FP64 means put back: exact where only the means are non-zero
+    rows = B.mean_rows(3, 2, divb, S.N)
+    wmean_only = np.zeros_like(w0)
+    wmean_only[:, rows] = w0[:, rows]
+    w32 = torch.as_tensor(wmean_only.T.copy()).float()
+    got32 = B.eval_points(table, w32, rows, torch.as_tensor(w0[:, rows].T.copy())).numpy()
+    ref_m = S.eval_points(wmean_only, S.synth(pts))
+    assert np.abs(got32.transpose(2, 1, 0) - ref_m).max() <= 1e-15 * np.abs(ref_m).max()
+
+
+def test_basis_values_rejects_bad_arguments(B):
+    from paper_1806_02343_gb300.binding import DGError
+    for args in ((4, 2, "glm"), (3, 4, "glm"), (2, -1, "powell")):
+        with pytest.raises(DGError) as e:
+            B.basis_values(args[0], args[1], args[2], np.zeros((1, args[0])))
+        assert e.value.code == -1
+
+
+def test_cell_points_match_oracle_geometry(B):
+    """The Gauss points project_ic evaluates at: cell centre + dx/2 * tensor
+    Gauss nodes (last axis fastest), cells in mesh order, for uniform boxes
+    (cells per axis unequal, 2D and 3D) and an octree."""
+    from oracle import basis as OB
+    from oracle.amr import AMRScheme
+    for D, ncell, npts in ((3, (4, 3, 2), 3), (2, (5, 3), 4)):
+        S = Scheme(D, 1, "glm", G, ncell)
+        qp, _ = OB.gauss_tensor(D, npts)
+        ref = S.centers[:, None, :] + 0.5 * S.dx * qp[None, :, :]
+        got = B.cell_points(D, npts, S.L, n=ncell).numpy()
+        assert got.shape == ref.shape and np.abs(got - ref).max() < 1e-14
+    leaves = W.octree_leaves(3, 1, 3, lambda c, dx, l: np.linalg.norm(np.asarray(c) - 0.3) < 0.25)
+    A = AMRScheme(3, 1, "powell", G, leaves)
+    qp, _ = OB.gauss_tensor(3, 2)
+    ref = A.centers[:, None, :] + 0.5 * A.dxc[:, None, None] * qp[None, :, :]
+    lev = [l for l, _ in leaves]
+    ijk = [k for _, k in leaves]
+    got = B.cell_points(3, 2, 1.0, levels=lev, ijk=ijk).numpy()
+    assert np.abs(got - ref).max() < 1e-14
