@@ -366,6 +366,19 @@ int dg_mhd_sibling_groups(int dim, int64_t n, const int8_t* level, const int32_t
 int dg_mhd_octree_faces(int dim, int64_t n, const int8_t* level, const int32_t* ijk, int64_t cap,
                         int32_t* face_left, int32_t* face_right, int32_t* face_meta, int64_t* n_faces);
 
+/* The tables a context's regridding calls use (HOST, no context, no device
+ * work), concatenated in out (doubles) with the six sizes in sizes[6]; n =
+ * Legendre modes, nd = LDF rows (0 for GLM), no = 2^dim:
+ *   QL [dim a][n][n]       smoothness form of a Legendre field along a:
+ *                          S_a = w^T QL[a] w (Sec. 5, sum_k 2^(2k-1) int (d_a^k u)^2
+ *                          over the reference cell, by the (d+1)-point rule);
+ *   QB [dim c][dim a][nd][nd]  the same for component c of the LDF field;
+ *   PL [no][n][n], PB [no][nd][nd]  L2 prolongation: child row from parent rows;
+ *   RL [no][n][n], RB [no][nd][nd]  L2 restriction: parent row from child o's rows.
+ * DG_E_ARG for dim not 2 or 3, degree outside 0..3, an unknown scheme, or cap
+ * below the total (call with out NULL to get the sizes). */
+int dg_mhd_regrid_tables(int dim, int degree, int divB_scheme, int64_t cap, double* out, int64_t* sizes);
+
 /* State of the new context from the old one (asynchronous on stream): per new
  * leaf a copy, an L2 prolongation (parent octant onto the child's basis; the
  * LDF rows under the vector inner product of eq. innerp) or an L2 restriction

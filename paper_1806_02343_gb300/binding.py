@@ -27,7 +27,7 @@ EXPORTS = [
     "dg_mhd_strerror", "dg_mhd_mlp_features", "dg_mhd_mlp_set_weights", "dg_mhd_mlp_infer", "dg_mhd_mlp_loss_grad",
     "dg_mhd_mlp_train", "dg_mhd_counters", "dg_mhd_limiter_counts", "dg_mhd_divb", "dg_mhd_smoothness",
     "dg_mhd_amr_marks", "dg_mhd_regrid_plan", "dg_mhd_remap", "dg_mhd_regrid_plan_mesh",
-    "dg_mhd_sibling_groups", "dg_mhd_octree_faces", "dg_mhd_basis_values",
+    "dg_mhd_sibling_groups", "dg_mhd_octree_faces", "dg_mhd_basis_values", "dg_mhd_regrid_tables",
 ]
 KIND_FACE, KIND_CELL, KIND_DT, KIND_LIMIT, KIND_PROJECT, KIND_POSITIVITY, KIND_MLP = range(7)
 
@@ -97,6 +97,7 @@ def lib():
     L.dg_mhd_sibling_groups.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_int64, vp, i64p]
     L.dg_mhd_octree_faces.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_int64, vp, vp, vp, i64p]
     ip = ctypes.POINTER(ctypes.c_int)
+    L.dg_mhd_regrid_tables.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp, vp]
     L.dg_mhd_basis_values.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp, ctypes.c_int64, vp,
                                       ip, ip]
     L.dg_mhd_destroy.argtypes = [vp]
@@ -243,6 +244,28 @@ def eval_points(table, w, mean=None, wmean=None):
         W[mean] = wmean.to(torch.float64)
     T = torch.as_tensor(table, dtype=torch.float64, device=W.device)
     return torch.einsum("rvp,rc->vpc", T, W)
+
+
+def regrid_tables(dim, degree, divb):
+    """The regridding tables of a context (host, no GPU): dict of float64
+    arrays QL [dim, n, n], QB [dim, dim, nd, nd], PL / RL [2^dim, n, n],
+    PB / RB [2^dim, nd, nd] (nd = 0 for GLM)."""
+    import numpy as np
+    scheme = DG_DIVB_GLM if divb == "glm" else DG_DIVB_POWELL
+    sizes = np.zeros(6, dtype=np.int64)
+    _check(lib().dg_mhd_regrid_tables(dim, degree, scheme, 0, None, sizes.ctypes.data), "dg_mhd_regrid_tables")
+    flat = np.zeros(int(sizes.sum()), dtype=np.float64)
+    _check(lib().dg_mhd_regrid_tables(dim, degree, scheme, flat.size, flat.ctypes.data, sizes.ctypes.data),
+           "dg_mhd_regrid_tables")
+    n, no = math.comb(degree + dim, dim), 1 << dim
+    nd = int(round(math.sqrt(sizes[3] / no))) if sizes[3] else 0
+    shapes = {"QL": (dim, n, n), "QB": (dim, dim, nd, nd), "PL": (no, n, n), "PB": (no, nd, nd),
+              "RL": (no, n, n), "RB": (no, nd, nd)}
+    out, o = {}, 0
+    for key, size in zip(("QL", "QB", "PL", "PB", "RL", "RB"), sizes):
+        out[key] = flat[o:o + size].reshape(shapes[key])
+        o += size
+    return out
 
 
 def octree_faces(levels, ijk):

@@ -520,3 +520,22 @@ extern "C" int dg_mhd_regrid_plan(const dg_mhd_ctx* ctx, const int8_t* marks, in
   }
   return DG_OK;
 }
+
+// The context's regridding tables without a context (host only).
+extern "C" int dg_mhd_regrid_tables(int dim, int degree, int divB_scheme, int64_t cap, double* out,
+                                    int64_t* sizes) {
+  if (!sizes || (dim != 2 && dim != 3) || degree < 0 || degree > 3 ||
+      (divB_scheme != DG_DIVB_POWELL && divB_scheme != DG_DIVB_GLM))
+    return DG_E_ARG;
+  dgmhd::Basis B;
+  if (!B.build(dim, degree, divB_scheme == DG_DIVB_POWELL)) return DG_E_ARG;
+  std::vector<double> tab;
+  dgmhd::RgLayout L;
+  if (!dgmhd::regrid_tables(B, tab, L)) return DG_E_ARG;
+  const size_t off[7] = {L.QL, L.QB, L.PL, L.PB, L.RL, L.RB, L.total};
+  for (int i = 0; i < 6; ++i) sizes[i] = (int64_t)(off[i + 1] - off[i]);
+  if (!out) return DG_OK;  // size query
+  if (cap < (int64_t)L.total) return DG_E_ARG;
+  std::copy(tab.begin(), tab.end(), out);
+  return DG_OK;
+}

@@ -95,3 +95,48 @@ def test_cell_points_match_oracle_geometry(B):
     ijk = [k for _, k in leaves]
     got = B.cell_points(3, 2, 1.0, levels=lev, ijk=ijk).numpy()
     assert np.abs(got - ref).max() < 1e-14
+
+
+def _full(S, blockL, blockB):
+    """Block-diagonal matrix over the scheme's rows from per-basis blocks."""
+    M = np.zeros((S.N, S.N))
+    for r1, (k1, v1, i1) in enumerate(S.rows):
+        for r2, (k2, v2, i2) in enumerate(S.rows):
+            if k1 == k2 == "L" and v1 == v2:
+                M[r1, r2] = blockL[i1, i2]
+            elif k1 == k2 == "B":
+                M[r1, r2] = blockB[i1, i2]
+    return M
+
+
+@pytest.mark.parametrize("D,d,divb", [c for c in CASES if c[1] >= 1])
+def test_regrid_tables_match_oracle(B, D, d, divb):
+    """dg_mhd_regrid_tables (the host tables of the regridding kernels) against
+    the oracle: prolongation and restriction matrices of every octant, and the
+    smoothness indicator as quadratic forms on random weights (Sec. 5)."""
+    from oracle import mhd
+    from oracle import regrid as RG
+    S = Scheme(D, d, divb, G, 2)
+    T = B.regrid_tables(D, d, divb)
+    Pr, Re = RG.prolongation(S), RG.restriction(S)
+    for o in range(2 ** D):
+        assert np.abs(_full(S, T["PL"][o], T["PB"][o]) - Pr[o]).max() < 1e-12
+        assert np.abs(_full(S, T["RL"][o], T["RB"][o]) - Re[o]).max() < 1e-12
+    rng = np.random.default_rng(d + 10 * D)
+    w = rng.standard_normal((5, S.N))
+    fields = (mhd.RHO, mhd.BX, mhd.BY, mhd.BZ)
+    ref = RG.smoothness(S, w, fields)                      # [cells, fields, D]
+    for fi, v in enumerate(fields):
+        legrows = [(r, i) for r, (k, vv, i) in enumerate(S.rows) if k == "L" and vv == v]
+        for a in range(D):
+            if legrows:
+                idx = [r for r, _ in legrows]
+                modes = [i for _, i in legrows]
+                got = np.einsum("cl,lm,cm->c", w[:, idx], T["QL"][a][np.ix_(modes, modes)], w[:, idx])
+            else:                                          # a component of the LDF field
+                brow = [(r, i) for r, (k, _, i) in enumerate(S.rows) if k == "B"]
+                idx = [r for r, _ in brow]
+                js = [i for _, i in brow]
+                c = v - mhd.BX
+                got = np.einsum("cj,jm,cm->c", w[:, idx], T["QB"][c, a][np.ix_(js, js)], w[:, idx])
+            assert np.abs(got - ref[:, fi, a]).max() <= 1e-11 * max(1.0, np.abs(ref).max())
