@@ -100,3 +100,37 @@ def test_octree_mesh_validation_rejects_bad_meshes(lib):
     deep += [(2, k) for k in np.ndindex(2, 2, 2) if k != (1, 1, 1)]
     deep += [(3, tuple(2 + x for x in k)) for k in np.ndindex(2, 2, 2)]
     assert init(deep) == -2
+
+
+def test_host_entry_points_reject_null_arguments(lib):
+    """The context-free host calls (planning, faces, basis, regrid tables)
+    return DG_E_ARG for NULL outputs or inputs and for a too-small capacity,
+    and answer size queries with NULL output arrays."""
+    import ctypes
+    import numpy as np
+    lev = np.full(4, 1, dtype=np.int8)
+    ijk = np.array([[0, 0], [1, 0], [0, 1], [1, 1]], dtype=np.int32)
+    marks = np.zeros(4, dtype=np.int8)
+    n = ctypes.c_int64()
+    lp, kp, mp = lev.ctypes.data, ijk.ctypes.data, marks.ctypes.data
+    assert lib.dg_mhd_regrid_plan_mesh(2, 4, lp, kp, None, 0, None, None, None, ctypes.byref(n)) == -1
+    assert lib.dg_mhd_regrid_plan_mesh(2, 4, lp, kp, mp, 0, None, None, None, None) == -1
+    assert lib.dg_mhd_regrid_plan_mesh(2, 4, lp, kp, mp, 0, None, None, None, ctypes.byref(n)) == 0 and n.value == 4
+    out = np.zeros(3, dtype=np.int32)
+    assert lib.dg_mhd_regrid_plan_mesh(2, 4, lp, kp, mp, 3, out.ctypes.data, out.ctypes.data, out.ctypes.data,
+                                       ctypes.byref(n)) == -1                     # capacity 3 < 4
+    assert lib.dg_mhd_sibling_groups(2, 4, lp, kp, 0, None, None) == -1
+    assert lib.dg_mhd_sibling_groups(2, 4, lp, kp, 0, None, ctypes.byref(n)) == 0 and n.value == 1
+    assert lib.dg_mhd_octree_faces(2, 4, None, kp, 0, None, None, None, ctypes.byref(n)) == -1
+    assert lib.dg_mhd_octree_faces(2, 4, lp, kp, 0, None, None, None, None) == -1
+    assert lib.dg_mhd_octree_faces(2, 4, lp, kp, 0, None, None, None, ctypes.byref(n)) == 0 and n.value == 8
+    r, v = ctypes.c_int(), ctypes.c_int()
+    assert lib.dg_mhd_basis_values(3, 2, 1, 1, None, 0, None, ctypes.byref(r), ctypes.byref(v)) == -1
+    assert lib.dg_mhd_basis_values(3, 2, 1, 0, None, 0, None, None, ctypes.byref(v)) == -1
+    assert lib.dg_mhd_basis_values(3, 2, 1, 0, None, 0, None, ctypes.byref(r), ctypes.byref(v)) == 0
+    assert (r.value, v.value) == (90, 9)
+    assert lib.dg_mhd_regrid_tables(3, 2, 0, 0, None, None) == -1
+    sizes = np.zeros(6, dtype=np.int64)
+    assert lib.dg_mhd_regrid_tables(3, 2, 0, 0, None, sizes.ctypes.data) == 0 and sizes[0] == 3 * 10 * 10
+    small = np.zeros(1)
+    assert lib.dg_mhd_regrid_tables(3, 2, 0, 1, small.ctypes.data, sizes.ctypes.data) == -1
