@@ -224,3 +224,22 @@ def test_octree_faces_reject_invalid_meshes(B):
         with pytest.raises(DGError) as e:
             B.octree_faces(*_arrays(bad))
         assert e.value.code == -2
+
+
+def test_orszag_tang_octree_workload(B):
+    """The static octree of the Orszag-Tang workload: 1,387,520 leaves of
+    levels 5/6/7 (3,072 / 73,728 / 1,310,720) tiling the cube 2:1-balanced
+    (the face builder validates it), Morton-sorted, and a z-extrusion: each
+    (level, i, j) column holds all 2^level cells along z."""
+    lev, ijk = W.orszag_tang_octree()
+    assert len(lev) == 1_387_520
+    assert np.bincount(lev, minlength=8)[5:8].tolist() == [3_072, 73_728, 1_310_720]
+    fl, fr, meta = B.octree_faces(lev, ijk)                   # raises unless a balanced tiling
+    assert len(fl) > 3 * len(lev) // 2
+    assert ((meta >> 2) & 3).max() > 0                         # coarse-fine faces exist
+    cols = {}
+    for l, (i, j, k) in zip(lev.tolist(), ijk.tolist()):
+        cols.setdefault((l, i, j), set()).add(k)
+    assert all(len(ks) == 2 ** l for (l, _, _), ks in cols.items())
+    g = B.sibling_groups(lev, ijk)                             # Morton order: groups are index runs
+    assert len(g) > 0 and np.all(np.diff(g, axis=1) == 1)
