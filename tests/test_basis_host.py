@@ -140,3 +140,38 @@ def test_regrid_tables_match_oracle(B, D, d, divb):
                 c = v - mhd.BX
                 got = np.einsum("cj,jm,cm->c", w[:, idx], T["QB"][c, a][np.ix_(js, js)], w[:, idx])
             assert np.abs(got - ref[:, fi, a]).max() <= 1e-11 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("case", ["uniform", "octree"])
+def test_project_ic_input_preparation(B, case):
+    """project_ic's host side without a GPU: with dg_mhd_project replaced by a
+    capture, the point values it hands over, projected with the oracle's own
+    formula (sum_q w_q u phi / M), give the oracle's L2 projection."""
+    import types
+    import torch
+    from oracle import basis as OB
+    from oracle.amr import AMRScheme
+    obj = types.SimpleNamespace()
+    if case == "uniform":
+        S = Scheme(3, 2, "glm", G, (6, 5, 4))
+        fn, npts = W.SmoothFourier3D(nvar=9), 5
+        obj.dim, obj.degree, obj.box_len, obj._n, obj._lev, obj._ijk = 3, 2, S.L, [6, 5, 4], None, None
+        obj.ncell = obj.stride = 120
+    else:
+        leaves = W.octree_leaves(3, 2, 3, lambda c, dx, l: np.linalg.norm(np.asarray(c) - 0.5) < 0.3)
+        S = AMRScheme(3, 1, "powell", G, leaves)
+        fn, npts = W.SmoothFourier3D(nvar=8), None
+        obj.dim, obj.degree, obj.box_len, obj._n = 3, 1, 1.0, None
+        obj._lev = np.array([l for l, _ in leaves], dtype=np.int8)
+        obj._ijk = np.array([k for _, k in leaves], dtype=np.int32).reshape(-1)
+        obj.ncell, obj.stride = len(leaves), (len(leaves) + 3) // 4 * 4
+    seen = {}
+    obj.project = lambda nodal, q, w, wmean=None: seen.update(nodal=nodal, q=q)
+    B.Solver.project_ic(obj, fn, torch.zeros((S.N, obj.stride), dtype=torch.float64), npts=npts)
+    q = seen["q"]
+    assert q == (npts or min(8, obj.degree + 3))
+    qp, qw = OB.gauss_tensor(3, q)
+    u = seen["nodal"][:, :, : obj.ncell].permute(2, 1, 0).numpy()
+    mine = np.einsum("cqv,q,rqv->cr", u, qw, S.synth(qp)) / S.mass
+    assert np.abs(mine - S.project(fn, npts=q)).max() < 1e-14
+    assert torch.all(seen["nodal"][:, :, obj.ncell:] == 0)
