@@ -156,12 +156,9 @@ bool mesh_balanced(const MortonIndex& mi, const int32_t* ijk) {
       const int b0 = k[a] & 1, b1 = (k[a] >> 1) & 1;
       if (b0 != b1) continue;
       const int s = b0 ? 1 : -1;
-      {
-        int32_t nk[3] = {k[0], k[1], D == 3 ? k[2] : 0};
-        nk[a] = (nk[a] + s + n) % n;
-        const int64_t q = locate(mi.start, morton(D, mi.R, l, nk), p);
-        if (mi.lev[q] < l - 1) return false;
-      }
+      int32_t nk[3] = {k[0], k[1], D == 3 ? k[2] : 0};
+      nk[a] = (nk[a] + s + n) % n;
+      if (mi.lev[locate(mi.start, morton(D, mi.R, l, nk), p)] < l - 1) return false;
     }
   }
   return true;
