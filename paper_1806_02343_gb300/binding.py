@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libdgmhd.so")
 
 DG_OK, DG_W_FLOOR = 0, 1
+DG_E_TIMEOUT = -6
 DG_DIVB_POWELL, DG_DIVB_GLM = 0, 1
 DG_PREC_FP64, DG_PREC_FP32MIX = 0, 1
 DG_LIMIT_OFF, DG_LIMIT_TVB, DG_LIMIT_MLP = 0, 1, 2
@@ -121,6 +122,25 @@ def _check(code, what):
     if code < 0:
         raise DGError(code, what)
     return code
+
+
+def wait(stream=None, timeout_s=60.0, poll_s=1e-4, event=None):
+    """Host-side watchdog on stream completion: records an event on the stream
+    (default: the current one) and polls it until the work before it has
+    finished, raising DGError(DG_E_TIMEOUT) once timeout_s has passed instead
+    of blocking inside the driver. The device work is not cancelled; the
+    caller decides what to do with a stream that did not finish. `event`:
+    an already recorded object with a query() method (tests inject one)."""
+    import time
+    if event is None:
+        import torch
+        event = torch.cuda.Event()
+        event.record(stream if stream is not None else torch.cuda.current_stream())
+    deadline = time.monotonic() + timeout_s
+    while not event.query():
+        if time.monotonic() > deadline:
+            raise DGError(DG_E_TIMEOUT, f"stream not complete after {timeout_s:g} s")
+        time.sleep(poll_s)
 
 
 def _ptr(t):
@@ -548,5 +568,10 @@ class Solver:
                                            1 if reset else 0), "dg_mhd_limiter_counts")
         return {"passes": p.value, "flagged": f.value, "limited": l.value}
 
-    def status(self, sync=True):
+    def status(self, sync=True, timeout_s=None):
+        """The context's status word (dg_mhd_status). With timeout_s, the
+        stream is first waited for by the watchdog (`wait`), so a stream that
+        does not finish raises DG_E_TIMEOUT instead of blocking the host."""
+        if sync and timeout_s is not None:
+            wait(timeout_s=timeout_s)
         return lib().dg_mhd_status(self.h, 1 if sync else 0)
