@@ -3,8 +3,9 @@
 The paper frames troubled-cell detection as its own step, judged by
 sensitivity and specificity (Sec. 4.2: detection, then limiting). This
 indicator replaces the TVB detection with a small multilayer perceptron that
-decides which cells the TVB procedure processes; the plain TVB trigger is the
-label and the judge. Nothing here is printed in the paper; the choices are:
+decides which cells the TVB procedure processes; the plain TVB trigger gives
+the labels and is the reference it is scored against. Nothing here is printed
+in the paper; the choices are:
 
 * features of a cell (8 n(d) + 2D + 8D values): the Legendre coefficients of
   the 8 MHD conserved variables (for the LDF basis, B is first mapped exactly
