@@ -59,3 +59,24 @@ def test_cpu_baseline_sample_is_a_physical_run():
     assert not np.isfinite(plain["w"]).all()
     assert np.isfinite(lim["w"]).all() and lim["value"] > 0 and lim["cores"] == 1
     assert "positivity" in lim["sample"]
+
+
+def test_alu_flop_count_of_the_headline_stage():
+    """The ALU roofline's flops per cell and stage at degree 2, GLM, 3D (n = 10
+    modes, Q_v = 27, Q_f = 9, 9 variables): contractions counted from their
+    definitions (2 flop per multiply-add), the pointwise physics as the stated
+    estimates (60 per volume point, 500 per face point); the mode counts of
+    every (dimension, degree) agree with C(d + D, D)."""
+    fl = bench.stage_flops_per_cell(3, 2, "glm", 90)
+    V, n, qv, qf, D = 9, 10, 27, 9, 3
+    assert fl["projection"] == 2 * V * n * qv == 4_860
+    assert fl["volume_integral"] == 2 * V * n * qv * D == 14_580
+    assert fl["face_traces"] == 2 * V * n * 2 * D * qf == 9_720          # both sides of the D lower faces
+    assert fl["surface_integral"] == 2 * V * n * 2 * D * qf == 9_720
+    assert fl["volume_flux_est"] == 60 * qv and fl["hlld_est"] == 500 * D * qf
+    assert fl["total"] == 54_000
+    for D in (2, 3):
+        for d in range(4):
+            n = math.comb(d + D, D)
+            f = bench.stage_flops_per_cell(D, d, "glm", 9 * n)
+            assert f["projection"] == 2 * 9 * n * (d + 1) ** D
