@@ -230,8 +230,7 @@ def run_ours(args, cfg, rank, world, device):
     # roofline of the dominant kernel: algorithmic bytes of a stage attributed to the
     # cell-update kernel (it reads the stage input and u^n and writes the stage output)
     hbm, src = _peaks()
-    nf32 = sol.nrows - sol.nmean
-    bytes_cell = nf32 * 4 * (1 + 2.0 / 3.0 + 1) + sol.nmean * 8 * (1 + 2.0 / 3.0 + 1)
+    bytes_cell = stage_bytes_per_cell(sol.nrows, sol.nmean, fp32=True)
     dom = max(("face_flux", "cell_update"), key=lambda k: kern[k]["ms_total"])
     per_launch_ms = kern["cell_update"]["ms_per_launch"]
     achieved = bytes_cell * ncell / (per_launch_ms * 1e-3) / 1e9
@@ -485,6 +484,16 @@ def whole_job_value(dof, stages, world, ms):
     """DoF-updates/s of the whole job: world replicas of dof DoF, `stages` RK
     stages each, in the slowest rank's ms."""
     return dof * stages * world / (ms * 1e-3)
+
+
+def stage_bytes_per_cell(nrows, nmean, fp32=True):
+    """Algorithmic bytes of one SSP-RK3 stage per cell, averaged over the three
+    stages: the stage input read and the output written every stage, u^n read
+    in the two stages that combine with it (1 + 2/3 + 1 passes over the
+    state). FP32 form: float rows and the FP64 means; plain FP64: every row in
+    double."""
+    per_pass = (nrows - nmean) * 4 + nmean * 8 if fp32 else nrows * 8
+    return per_pass * (1 + 2.0 / 3.0 + 1)
 
 
 def stage_flops_per_cell(D, d, divb, nrows):

@@ -5,6 +5,7 @@ diagonals is within one cell of it, centred or across the periodic wrap."""
 import math
 
 import numpy as np
+import pytest
 
 import bench
 
@@ -80,3 +81,13 @@ def test_alu_flop_count_of_the_headline_stage():
             n = math.comb(d + D, D)
             f = bench.stage_flops_per_cell(D, d, "glm", 9 * n)
             assert f["projection"] == 2 * 9 * n * (d + 1) ** D
+
+
+def test_hbm_bytes_per_cell_of_the_stage():
+    """Algorithmic bytes per cell and stage (each coefficient read once as
+    stage input, u^n read in two of three stages, the output written once):
+    1,056 B for the 256^3 GLM FP32 form (81 float rows + 9 FP64 means), 896 B
+    for the Powell FP32 form at degree 2 (68 + 8), 1,920 B for plain FP64 GLM."""
+    assert bench.stage_bytes_per_cell(90, 9) == pytest.approx(1056.0)
+    assert bench.stage_bytes_per_cell(76, 8) == pytest.approx(896.0)
+    assert bench.stage_bytes_per_cell(90, 9, fp32=False) == pytest.approx(1920.0)
