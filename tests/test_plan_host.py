@@ -243,3 +243,20 @@ def test_orszag_tang_octree_workload(B):
     assert all(len(ks) == 2 ** l for (l, _, _), ks in cols.items())
     g = B.sibling_groups(lev, ijk)                             # Morton order: groups are index runs
     assert len(g) > 0 and np.all(np.diff(g, axis=1) == 1)
+
+
+def test_orszag_tang_coarsening_step_of_the_bench(B):
+    """The regrid step the octree bench times marks every complete sibling
+    group for coarsening (the Orszag-Tang start is smooth at this resolution):
+    the 1,387,520 leaves become 204,800 (every one of the 168,960 complete
+    groups restricts: 1,387,520 - 7 x 168,960), the counts the bench's GPU
+    regrid leg reports, and the new mesh is again a balanced tiling."""
+    lev, ijk = W.orszag_tang_octree()
+    g = B.sibling_groups(lev, ijk)
+    assert len(g) == 168_960
+    marks = np.zeros(len(lev), dtype=np.int8)
+    marks[g.reshape(-1)] = -1
+    lev_n, ijk_n, src = B.regrid_plan_mesh(lev, ijk, marks)
+    assert len(lev_n) == 204_800
+    assert int(((src[:, 0] & 15) == 2).sum()) == 168_960
+    B.octree_faces(lev_n, ijk_n)                              # raises unless a balanced tiling
