@@ -274,22 +274,30 @@ int64_t dg_mhd_launch_count(const dg_mhd_ctx* ctx);
  * device memory, code that must not trigger the device synchronisation that
  * cudaMalloc/cudaFree can cause, or an embedding that fixes the device
  * footprint at start-up. No context is needed: mesh, degree, scheme, gamma and
- * p (NULL = defaults; only eps_hlld is used) describe the problem, and c_h and
- * damping_rate set the GLM terms (ignored for Powell). The caller passes the
- * FP64 state w and the FP64 output rhs (DEVICE, layout of dg_mhd_rhs with
- * cell_stride = n_cells rounded up to a multiple of 32).
+ * p (NULL = defaults; only eps_hlld is read, DG_E_ARG unless it lies in
+ * [0, 1)) describe the problem, and c_h > 0 and damping_rate >= 0 set the GLM
+ * terms (ignored for Powell). The caller passes the FP64 state w and the FP64
+ * output rhs (DEVICE, layout of dg_mhd_rhs with cell_stride = n_cells rounded
+ * up to a multiple of 32; the library cannot check their sizes).
+ * status_dev (nullable, DEVICE int owned by the caller) receives the call's
+ * device status word in stream order: 0, or bit 1 set when rhs holds a NaN or
+ * an infinity (dg_mhd_status's DG_E_NONFINITE).
  * All scratch (basis tables, device scalars, face fluxes) lives in one static
  * device array of 4 Mi doubles (32 MiB) that every GPU loading the library
- * keeps until the process exits. The first call on a device resolves that
- * array's device address (cudaGetSymbolAddress) with the device current; make
- * that first call before any stream capture. Problems whose scratch exceeds the
- * array return DG_E_ARG (about 16 thousand cells at degree 2 in 3D). Every call
- * rewrites the shared array (tables and scalars are re-uploaded and the status
- * word cleared), so calls that overlap on the GPU -- two streams, two host
- * threads -- race and must be serialised by the caller. */
+ * keeps until the process exits; the call looks up its device address
+ * (cudaGetSymbolAddress) on the current device every time. With lazy module
+ * loading (the CUDA default) the first call on a device loads this library's
+ * module, which can allocate device memory and synchronise: make one warm-up
+ * call per device at start-up, before any stream capture. The host copies of
+ * the tables it uploads are built once per (dim, degree, scheme) and kept
+ * until exit. Problems whose scratch exceeds the array return DG_E_ARG (about
+ * 16 thousand cells at degree 2 in 3D). Every call rewrites the shared array
+ * (tables and scalars are re-uploaded and the status word cleared), so calls
+ * that overlap on the GPU -- two streams, two host threads -- race and must be
+ * serialised by the caller. */
 int dg_mhd_rhs_noalloc(const dg_mesh_desc* mesh, int degree, int divB_scheme, double gamma,
                        const dg_mhd_params* p, double c_h, double damping_rate, const double* w,
-                       double* rhs, void* stream);
+                       double* rhs, int* status_dev, void* stream);
 
 /* ---- Dynamic regridding of octree meshes (Sec. 5, adaptive mesh refinement) ----
  * A regrid step: dg_mhd_amr_marks -> copy the marks to the host ->

@@ -76,7 +76,7 @@ def lib():
     L.dg_mhd_launch_count.argtypes = [vp]
     L.dg_mhd_launch_count.restype = ctypes.c_int64
     L.dg_mhd_rhs_noalloc.argtypes = [ctypes.POINTER(MeshDesc), ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                     ctypes.POINTER(Params), ctypes.c_double, ctypes.c_double, vp, vp, vp]
+                                     ctypes.POINTER(Params), ctypes.c_double, ctypes.c_double, vp, vp, vp, vp]
     L.dg_mhd_mlp_features.argtypes = [vp, vp, dp, vp, ctypes.c_int, vp]
     L.dg_mhd_mlp_set_weights.argtypes = [vp, vp, ctypes.c_int, ctypes.c_float]
     L.dg_mhd_mlp_infer.argtypes = [vp, vp, dp, vp, vp, vp]
@@ -164,12 +164,34 @@ def mesh_desc(dim, n, box_len=1.0) -> MeshDesc:
     return m
 
 
-def rhs_noalloc(dim, n, degree, divb, w, out, gamma=5.0 / 3.0, box_len=1.0, c_h=0.0, damping_rate=0.0):
+def rhs_noalloc(dim, n, degree, divb, w, out, gamma=5.0 / 3.0, box_len=1.0, c_h=0.0, damping_rate=0.0,
+                status=None):
     """dg_mhd_rhs_noalloc: the operator with all device scratch in the library's
-    static array (for callers that must not allocate device memory)."""
+    static array (for callers that must not allocate device memory). w and out:
+    contiguous CUDA float64 tensors of shape (state rows, cells rounded up to 32);
+    status: optional CUDA int32 tensor of one element that receives the call's
+    device status word."""
+    import torch
+    dim_n = [int(x) for x in (n if isinstance(n, (tuple, list)) else (n,) * dim)]
+    ncell = 1
+    for x in dim_n[:dim]:
+        ncell *= x
+    stride = (ncell + 31) // 32 * 32
+    nv = ctypes.c_int()
+    nr = ctypes.c_int()
+    scheme = DG_DIVB_GLM if divb == "glm" else DG_DIVB_POWELL
+    _check(lib().dg_mhd_basis_values(dim, degree, scheme, 0, None, 0, None, ctypes.byref(nr), ctypes.byref(nv)),
+           "dg_mhd_basis_values")
+    for name, t in (("w", w), ("out", out)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                and tuple(t.shape) == (nr.value, stride)):
+            raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of shape ({nr.value}, {stride})")
+    if status is not None and not (isinstance(status, torch.Tensor) and status.is_cuda
+                                   and status.dtype == torch.int32 and status.numel() >= 1):
+        raise ValueError("status must be a CUDA int32 tensor with at least one element")
     m = mesh_desc(dim, n, box_len)
-    _check(lib().dg_mhd_rhs_noalloc(ctypes.byref(m), degree, DG_DIVB_GLM if divb == "glm" else DG_DIVB_POWELL,
-                                    gamma, None, c_h, damping_rate, _ptr(w), _ptr(out), _stream()),
+    _check(lib().dg_mhd_rhs_noalloc(ctypes.byref(m), degree, scheme, gamma, None, c_h, damping_rate, _ptr(w),
+                                    _ptr(out), _ptr(status) if status is not None else None, _stream()),
            "dg_mhd_rhs_noalloc")
 
 

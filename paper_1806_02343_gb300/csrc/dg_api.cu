@@ -463,6 +463,7 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
   if (!(prm.cfl > 0.0) || !(prm.cfl_glm > 0.0)) return DG_E_ARG;
   if (prm.rk_order < 0 || prm.rk_order > 4) return DG_E_ARG;
   if (prm.powell_q != 0 && prm.powell_q != 1) return DG_E_ARG;
+  if (!(prm.eps_hlld >= 0.0 && prm.eps_hlld < 1.0)) return DG_E_ARG;
   if (prm.rk_order == 0) prm.rk_order = degree + 1 < 4 ? degree + 1 : 4;
   // octree meshes: a global, time-independent c_h (Sec. 4.1.5)
   if (octree && divB_scheme == DG_DIVB_GLM && !(prm.c_h_fixed > 0.0)) return DG_E_ARG;
@@ -672,7 +673,6 @@ int operator_pass(Ctx& c, const void* w, const double* wmean, void* out, double*
     c.prof.begin(0, st);                                                                                    \
     launch_face_glm<T, DEG>(ft, fg, (const T*)w, FB, c.sc, c.p.eps_hlld, st);                               \
     c.prof.end(0, st);                                                                                      \
-    c.prof.launches[0] += 2;                                                                                \
     c.prof.begin(1, st);                                                                                    \
     launch_cell_glm<T, DEG>(ft, fg, (const T*)w, FB, (T*)out, (const T*)w0, ca, cb, combine, c.sc, wmean,   \
                             w0mean, outmean, st);                                                           \
@@ -729,8 +729,9 @@ int dt_pass(Ctx& c, const void* w, const double* wmean, double* dt_out, cudaStre
     launch_dt<double>(g, c.t64, (const double*)w, nullptr, c.face_buf, c.p, c.sc, dt_out, st);
   }
   c.prof.end(2, st);
-  // k_dt_init + k_dt + k_dt_finalize (+ k_divb_face): count the extra launches
-  c.prof.launches[2] += g.glm ? 2 : 3;
+  // k_dt_init + k_dt + k_dt_finalize (FP32 form: k_dt32 + k_dt32_refine in place
+  // of k_dt), + k_divb_face for Powell: count the launches beyond the first
+  c.prof.launches[2] += (g.glm ? 2 : 3) + (fp32(c) ? 1 : 0);
   return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
 }
 

@@ -114,6 +114,7 @@ struct DevScalars {
   float dt32, ch32, kappa32;       // FP32 copies of dt, ch, kappa (written with them)
   float pad32;
   double dt_step;                  // the step's dt; dt itself may be a fraction of it for some stages
+  unsigned long long dt64_bits;    // FP32 form: FP64 minimum of the screened cells' FP64 bounds
 };
 
 // a device scalar in the working precision T (FP32 kernels read the float copy)

@@ -407,6 +407,10 @@ __global__ void k_divb_face(Geom g, Tables<T> tb, const T* __restrict__ w, T* __
 
 // ---------------------------------------------------------------- dt
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+__device__ __forceinline__ double warp_min(double x) {
+  for (int o = 16; o > 0; o >>= 1) x = fmin(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
 
 // ---------------------------------------------------------------- div B diagnostics (App. C)
 // normal component a of B on face f of cell c at face point p (GLM: Legendre
@@ -542,58 +546,68 @@ __global__ void k_divb_diag_cell(Geom g, Tables<T> tb, const T* __restrict__ w, 
   }
 }
 
+// eq. cfl (and eq. powell_dt for Powell) of cell c in FP64 from its cell means
+// (wmean when given, else the degree-0 rows of w); *smax: the cell's mean
+// signal speed sum_a (|v_a| + c) / D. Returns DBL_MAX where the bound is not a
+// positive finite number (and sets status bit 1).
+template <typename T>
+__device__ double dt_cell64(const Geom& g, const Tables<T>& tb, const T* __restrict__ w,
+                            const double* __restrict__ wmean, const T* __restrict__ jbuf, const dg_mhd_params& p,
+                            DevScalars* __restrict__ sc, int64_t c, double* smax) {
+  const int64_t S = g.stride;
+  auto mean = [&](int m) {
+    return wmean ? wmean[m * S + c] : (double)w[(int64_t)mean_row(g, m) * S + c];
+  };
+  const double rho = mean(0);
+  const double vx = mean(1) / rho, vy = mean(2) / rho, vz = mean(3) / rho;
+  const double E = mean(4);
+  double b[3];
+  if (g.glm) {
+    b[0] = mean(5); b[1] = mean(6); b[2] = mean(7);
+  } else {
+    b[0] = b[1] = b[2] = 0.0;
+    for (int j = 0; j < g.DB; ++j)
+      for (int cc = 0; cc < g.DB; ++cc) b[cc] += mean(5 + j) * (double)tb.L0[j * g.DB + cc];
+    if (g.bz2d >= 0) b[2] = mean(7);
+  }
+  const double b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  const double pr = (g.gamma - 1.0) * (E - 0.5 * rho * (vx * vx + vy * vy + vz * vz) - 0.5 * b2);
+  const double cs = sqrt(g.gamma * pr / rho + b2 / rho);
+  const double av[3] = {fabs(vx), fabs(vy), fabs(vz)};
+  double s = 0.0;
+  for (int a = 0; a < g.D; ++a) s += (av[a] + cs) / g.dx;
+  double dtc = p.cfl / (2.0 * g.d + 1.0) / s;
+  *smax = s * g.dx / g.D;
+  if (!g.glm) {
+    // (1/V_K) oint |B^n_F - B^n_K| dS: sum this cell's 2D faces in fixed order
+    double acc = 0.0;
+    for (int a = 0; a < g.D; ++a) {
+      const int64_t cp = neighbour(g, c, a, +1);
+      for (int q = 0; q < g.Qf; ++q) {
+        acc += (double)jbuf[(((int64_t)a * g.ncell + c) * g.Qf + q) * 2 + 1];   // minus face: R side
+        acc += (double)jbuf[(((int64_t)a * g.ncell + cp) * g.Qf + q) * 2 + 0];  // plus face: L side
+      }
+    }
+    double meas = 1.0;
+    for (int a = 0; a < g.D - 1; ++a) meas *= 0.5 * g.dx;
+    double divb = acc * meas;
+    for (int a = 0; a < g.D; ++a) divb /= g.dx;
+    const double rate = divb * fabs(vx * b[0] + vy * b[1] + vz * b[2]) / E;
+    if (rate > 0.0) dtc = fmin(dtc, p.eta_powell / rate);
+  }
+  if (!(dtc > 0.0) || !isfinite(dtc)) {
+    atomicOr(&sc->status, 1);
+    dtc = DBL_MAX;
+  }
+  return dtc;
+}
+
 template <typename T>
 __global__ void k_dt(Geom g, Tables<T> tb, const T* __restrict__ w, const double* __restrict__ wmean,
                      const T* __restrict__ jbuf, dg_mhd_params p, DevScalars* __restrict__ sc) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double dtc = DBL_MAX, smax = 0.0;
-  if (c < g.ncell) {
-    const int64_t S = g.stride;
-    auto mean = [&](int m) {
-      return wmean ? wmean[m * S + c] : (double)w[(int64_t)mean_row(g, m) * S + c];
-    };
-    const double rho = mean(0);
-    const double vx = mean(1) / rho, vy = mean(2) / rho, vz = mean(3) / rho;
-    const double E = mean(4);
-    double b[3];
-    if (g.glm) {
-      b[0] = mean(5); b[1] = mean(6); b[2] = mean(7);
-    } else {
-      b[0] = b[1] = b[2] = 0.0;
-      for (int j = 0; j < g.DB; ++j)
-        for (int cc = 0; cc < g.DB; ++cc) b[cc] += mean(5 + j) * (double)tb.L0[j * g.DB + cc];
-      if (g.bz2d >= 0) b[2] = mean(7);
-    }
-    const double b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-    const double pr = (g.gamma - 1.0) * (E - 0.5 * rho * (vx * vx + vy * vy + vz * vz) - 0.5 * b2);
-    const double cs = sqrt(g.gamma * pr / rho + b2 / rho);
-    const double av[3] = {fabs(vx), fabs(vy), fabs(vz)};
-    double s = 0.0;
-    for (int a = 0; a < g.D; ++a) s += (av[a] + cs) / g.dx;
-    dtc = p.cfl / (2.0 * g.d + 1.0) / s;
-    smax = s * g.dx / g.D;
-    if (!g.glm) {
-      // (1/V_K) oint |B^n_F - B^n_K| dS: sum this cell's 2D faces in fixed order
-      double acc = 0.0;
-      for (int a = 0; a < g.D; ++a) {
-        const int64_t cp = neighbour(g, c, a, +1);
-        for (int q = 0; q < g.Qf; ++q) {
-          acc += (double)jbuf[(((int64_t)a * g.ncell + c) * g.Qf + q) * 2 + 1];   // minus face: R side
-          acc += (double)jbuf[(((int64_t)a * g.ncell + cp) * g.Qf + q) * 2 + 0];  // plus face: L side
-        }
-      }
-      double meas = 1.0;
-      for (int a = 0; a < g.D - 1; ++a) meas *= 0.5 * g.dx;
-      double divb = acc * meas;
-      for (int a = 0; a < g.D; ++a) divb /= g.dx;
-      const double rate = divb * fabs(vx * b[0] + vy * b[1] + vz * b[2]) / E;
-      if (rate > 0.0) dtc = fmin(dtc, p.eta_powell / rate);
-    }
-    if (!(dtc > 0.0) || !isfinite(dtc)) {
-      atomicOr(&sc->status, 1);
-      dtc = DBL_MAX;
-    }
-  }
+  if (c < g.ncell) dtc = dt_cell64(g, tb, w, wmean, jbuf, p, sc, c, &smax);
   // block reduction then one atomic per block
   __shared__ double red[256];
   __shared__ double reds[256];
@@ -613,79 +627,86 @@ __global__ void k_dt(Geom g, Tables<T> tb, const T* __restrict__ w, const double
   }
 }
 
-// FP32 form on uniform meshes: the same CFL and Powell bounds from the float
-// mirror of the cell means, in single precision (the step length is a bound,
-// not a conserved quantity: a relative 1e-7 in dt is harmless), with the
-// FP64 means used only where the FP32 pressure would lose its digits to the
-// cancellation E - kinetic - magnetic. Warp minimum, one atomic per warp.
+// FP32 screen of the FP32 form's timestep (uniform meshes): the same CFL and
+// Powell bounds from the float mirror of the cell means, in single precision,
+// with the FP64 means used where the FP32 pressure would lose its digits to
+// the cancellation E - kinetic - magnetic. *smax as in dt_cell64. Returns
+// FLT_MAX where the bound is not a positive finite number (status bit 1).
+__device__ float dt_cell32(const Geom& g, const Tables<float>& tb, const float* __restrict__ w,
+                           const double* __restrict__ wmean, const float* __restrict__ jbuf,
+                           const dg_mhd_params& p, DevScalars* __restrict__ sc, int64_t c, float* smax) {
+  const int64_t S = g.stride;
+  auto mean = [&](int m) { return w[(int64_t)mean_row(g, m) * S + c]; };
+  const float rho = mean(0), ir = 1.f / rho;
+  const float vx = mean(1) * ir, vy = mean(2) * ir, vz = mean(3) * ir;
+  const float E = mean(4);
+  float b[3];
+  if (g.glm) {
+    b[0] = mean(5); b[1] = mean(6); b[2] = mean(7);
+  } else {
+    b[0] = b[1] = b[2] = 0.f;
+    for (int j = 0; j < g.DB; ++j)
+      for (int cc = 0; cc < g.DB; ++cc) b[cc] += mean(5 + j) * tb.L0[j * g.DB + cc];
+    if (g.bz2d >= 0) b[2] = mean(7);
+  }
+  const float gam = (float)g.gamma;
+  const float b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  const float kin = 0.5f * rho * (vx * vx + vy * vy + vz * vz);
+  float pr = (gam - 1.f) * (E - kin - 0.5f * b2);
+  if (!(pr > 1e-3f * E)) {
+    // cancellation (or a non-positive mean pressure): FP64 from the means
+    auto md = [&](int m) { return wmean[m * S + c]; };
+    const double rd = md(0);
+    const double mx = md(1), my = md(2), mz = md(3);
+    double bd[3];
+    if (g.glm) {
+      bd[0] = md(5); bd[1] = md(6); bd[2] = md(7);
+    } else {
+      bd[0] = bd[1] = bd[2] = 0.0;
+      for (int j = 0; j < g.DB; ++j)
+        for (int cc = 0; cc < g.DB; ++cc) bd[cc] += md(5 + j) * (double)tb.L0[j * g.DB + cc];
+      if (g.bz2d >= 0) bd[2] = md(7);
+    }
+    pr = (float)((g.gamma - 1.0) * (md(4) - 0.5 * (mx * mx + my * my + mz * mz) / rd -
+                                    0.5 * (bd[0] * bd[0] + bd[1] * bd[1] + bd[2] * bd[2])));
+  }
+  const float cs = sqrtf((gam * pr + b2) * ir);
+  const float av[3] = {fabsf(vx), fabsf(vy), fabsf(vz)};
+  float sum = 0.f;
+  for (int a = 0; a < g.D; ++a) sum += av[a] + cs;
+  const float idx = (float)(1.0 / g.dx);
+  const float s = sum * idx;
+  float dtc = (float)(p.cfl / (2.0 * g.d + 1.0)) / s;
+  *smax = sum / (float)g.D;
+  if (!g.glm) {
+    // (1/V_K) oint |B^n_F - B^n_K| dS: this cell's 2D faces in fixed order
+    float acc = 0.f;
+    for (int a = 0; a < g.D; ++a) {
+      const int64_t cp = neighbour(g, c, a, +1);
+      for (int q = 0; q < g.Qf; ++q) {
+        acc += jbuf[(((int64_t)a * g.ncell + c) * g.Qf + q) * 2 + 1];
+        acc += jbuf[(((int64_t)a * g.ncell + cp) * g.Qf + q) * 2 + 0];
+      }
+    }
+    // face measure (dx/2)^(D-1) over the volume dx^D: 2^(1-D) / dx
+    const float divb = acc * (g.D == 3 ? 0.25f : 0.5f) * idx;
+    const float rate = divb * fabsf(vx * b[0] + vy * b[1] + vz * b[2]) / E;
+    if (rate > 0.f) dtc = fminf(dtc, (float)p.eta_powell / rate);
+  }
+  if (!(dtc > 0.f) || !isfinite(dtc)) {
+    atomicOr(&sc->status, 1);
+    dtc = FLT_MAX;
+  }
+  return dtc;
+}
+
+// Pass 1 of the FP32 form's timestep: the FP32 bound of every cell, its
+// minimum m32 (warp minimum, one atomic per warp) and the signal-speed maximum.
 __global__ void k_dt32(Geom g, Tables<float> tb, const float* __restrict__ w, const double* __restrict__ wmean,
                        const float* __restrict__ jbuf, dg_mhd_params p, DevScalars* __restrict__ sc) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float dtc = FLT_MAX, smax = 0.f;
-  if (c < g.ncell) {
-    const int64_t S = g.stride;
-    auto mean = [&](int m) { return w[(int64_t)mean_row(g, m) * S + c]; };
-    const float rho = mean(0), ir = 1.f / rho;
-    const float vx = mean(1) * ir, vy = mean(2) * ir, vz = mean(3) * ir;
-    const float E = mean(4);
-    float b[3];
-    if (g.glm) {
-      b[0] = mean(5); b[1] = mean(6); b[2] = mean(7);
-    } else {
-      b[0] = b[1] = b[2] = 0.f;
-      for (int j = 0; j < g.DB; ++j)
-        for (int cc = 0; cc < g.DB; ++cc) b[cc] += mean(5 + j) * tb.L0[j * g.DB + cc];
-      if (g.bz2d >= 0) b[2] = mean(7);
-    }
-    const float gam = (float)g.gamma;
-    const float b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-    const float kin = 0.5f * rho * (vx * vx + vy * vy + vz * vz);
-    float pr = (gam - 1.f) * (E - kin - 0.5f * b2);
-    if (!(pr > 1e-3f * E)) {
-      // cancellation (or a non-positive mean pressure): FP64 from the means
-      auto md = [&](int m) { return wmean[m * S + c]; };
-      const double rd = md(0);
-      const double mx = md(1), my = md(2), mz = md(3);
-      double bd[3];
-      if (g.glm) {
-        bd[0] = md(5); bd[1] = md(6); bd[2] = md(7);
-      } else {
-        bd[0] = bd[1] = bd[2] = 0.0;
-        for (int j = 0; j < g.DB; ++j)
-          for (int cc = 0; cc < g.DB; ++cc) bd[cc] += md(5 + j) * (double)tb.L0[j * g.DB + cc];
-        if (g.bz2d >= 0) bd[2] = md(7);
-      }
-      pr = (float)((g.gamma - 1.0) * (md(4) - 0.5 * (mx * mx + my * my + mz * mz) / rd -
-                                      0.5 * (bd[0] * bd[0] + bd[1] * bd[1] + bd[2] * bd[2])));
-    }
-    const float cs = sqrtf((gam * pr + b2) * ir);
-    const float av[3] = {fabsf(vx), fabsf(vy), fabsf(vz)};
-    float sum = 0.f;
-    for (int a = 0; a < g.D; ++a) sum += av[a] + cs;
-    const float idx = (float)(1.0 / g.dx);
-    const float s = sum * idx;
-    dtc = (float)(p.cfl / (2.0 * g.d + 1.0)) / s;
-    smax = sum / (float)g.D;
-    if (!g.glm) {
-      // (1/V_K) oint |B^n_F - B^n_K| dS: this cell's 2D faces in fixed order
-      float acc = 0.f;
-      for (int a = 0; a < g.D; ++a) {
-        const int64_t cp = neighbour(g, c, a, +1);
-        for (int q = 0; q < g.Qf; ++q) {
-          acc += jbuf[(((int64_t)a * g.ncell + c) * g.Qf + q) * 2 + 1];
-          acc += jbuf[(((int64_t)a * g.ncell + cp) * g.Qf + q) * 2 + 0];
-        }
-      }
-      // face measure (dx/2)^(D-1) over the volume dx^D: 2^(1-D) / dx
-      const float divb = acc * (g.D == 3 ? 0.25f : 0.5f) * idx;
-      const float rate = divb * fabsf(vx * b[0] + vy * b[1] + vz * b[2]) / E;
-      if (rate > 0.f) dtc = fminf(dtc, (float)p.eta_powell / rate);
-    }
-    if (!(dtc > 0.f) || !isfinite(dtc)) {
-      atomicOr(&sc->status, 1);
-      dtc = FLT_MAX;
-    }
-  }
+  if (c < g.ncell) dtc = dt_cell32(g, tb, w, wmean, jbuf, p, sc, c, &smax);
   // positive floats order as their bit patterns
   const unsigned mn = __reduce_min_sync(0xffffffffu, __float_as_uint(dtc));
   const unsigned mxs = __reduce_max_sync(0xffffffffu, __float_as_uint(smax));
@@ -696,13 +717,42 @@ __global__ void k_dt32(Geom g, Tables<float> tb, const float* __restrict__ w, co
   }
 }
 
+// Pass 2: the timestep is the FP64 minimum of the FP64 bounds (the same
+// arithmetic as the plain FP64 path, from the FP64 means). Only the cells
+// whose FP32 bound lies within kDtScreen (relative) of the FP32 minimum can
+// hold it: the FP32 bound's error is below 1e-4 relative (FP32 rounding of a
+// few dozen operations, the FP32 pressure used only while it keeps 1e-3 of E),
+// so the cell with the smallest FP64 bound is always among them. They are
+// recomputed in FP64 and min-reduced into dt64_bits.
+constexpr float kDtScreen = 1e-3f;
+__global__ void k_dt32_refine(Geom g, Tables<float> tb, const float* __restrict__ w,
+                              const double* __restrict__ wmean, const float* __restrict__ jbuf, dg_mhd_params p,
+                              DevScalars* __restrict__ sc) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double dtc = DBL_MAX;
+  if (c < g.ncell) {
+    const double m32 = __longlong_as_double((long long)sc->dt_bits);
+    float sm32;
+    const float d32 = dt_cell32(g, tb, w, wmean, jbuf, p, sc, c, &sm32);
+    if (m32 < DBL_MAX && (double)d32 <= m32 * (1.0 + (double)kDtScreen)) {
+      double sm64;
+      dtc = dt_cell64<float>(g, tb, w, wmean, jbuf, p, sc, c, &sm64);
+    }
+  }
+  const double m = warp_min(dtc);
+  if ((threadIdx.x & 31) == 0 && m < DBL_MAX) atomicMin(&sc->dt64_bits, dbits(m));
+}
+
 __global__ void k_dt_init(DevScalars* sc) {
   sc->dt_bits = dbits(DBL_MAX);
+  sc->dt64_bits = dbits(DBL_MAX);
   sc->smax_bits = 0ull;
 }
 
 __global__ void k_dt_finalize(Geom g, dg_mhd_params p, DevScalars* sc, const double* dt_in, double* dt_out) {
-  double dt = dt_in ? *dt_in : __longlong_as_double((long long)sc->dt_bits);
+  // the FP32 form's refined FP64 minimum where that pass ran, else the FP64 pass's minimum
+  const double dt64 = __longlong_as_double((long long)sc->dt64_bits);
+  double dt = dt_in ? *dt_in : (dt64 < DBL_MAX ? dt64 : __longlong_as_double((long long)sc->dt_bits));
   if (!(dt > 0.0) || !isfinite(dt) || dt >= DBL_MAX) {
     atomicOr(&sc->status, 1);
   }
@@ -823,6 +873,7 @@ void launch_dt(const Geom& g, const Tables<T>& tb, const T* w, const double* wme
   if constexpr (sizeof(T) == 4) {
     if (wmean) {
       k_dt32<<<nblocks(g.ncell, 256), 256, 0, st>>>(g, tb, w, wmean, jbuf, p, sc);
+      k_dt32_refine<<<nblocks(g.ncell, 256), 256, 0, st>>>(g, tb, w, wmean, jbuf, p, sc);
       k_dt_finalize<<<1, 1, 0, st>>>(g, p, sc, nullptr, dt_out);
       return;
     }

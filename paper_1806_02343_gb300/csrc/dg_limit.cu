@@ -1034,7 +1034,7 @@ int run_limiter(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t 
         k_pos<float><<<nbl, 128, 0, st>>>(g, c.t32, c.lim, (float*)w, wmean, c.p, c.sc, c.pos_list);
       else if (g.d == 2) g.glm ? pw(k_pos_list<2, 1>) : pw(k_pos_list<2, 0>);
       else g.glm ? pw(k_pos_list<1, 1>) : pw(k_pos_list<1, 0>);
-      c.prof.launches[5] += 1;
+      if (!screened) c.prof.launches[5] += 1;  // the screen and the list kernel
     } else {
       k_pos<double><<<nb, 128, 0, st>>>(g, c.t64, c.lim, (double*)w, nullptr, c.p, c.sc, nullptr);
     }

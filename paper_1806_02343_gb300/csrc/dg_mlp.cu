@@ -616,8 +616,16 @@ __global__ void __launch_bounds__(256) k_mlp_staged(Geom g, MlpTabs mt, const fl
       if (clock64() - t0 > kWaitCycles) break;
     return __syncthreads_and(ok) != 0;
   };
-  // two buffers: the next tile's copies run while this one is computed
-  if (nbuf == 2 && t == 0 && blockIdx.x < ntile) issue(blockIdx.x, 0);
+  // two buffers: the next tile's copies run while this one is computed.
+  // Every thread tracks which buffers have copies issued but not yet observed
+  // complete (the issue decisions are block-uniform): a block that gives up on
+  // a wait drains them before it exits, so no asynchronous write into its
+  // shared memory outlives it.
+  unsigned pend = 0;  // bit b: copies into buffer b issued, completion not yet observed
+  if (nbuf == 2 && blockIdx.x < ntile) {
+    if (t == 0) issue(blockIdx.x, 0);
+    pend |= 1u;
+  }
   unsigned par = 0;  // bit b: phase parity of bar[b]
   int it = 0;
   int mma_pending = -1;  // parity of an MMA commit not yet observed (timeout path), else -1
@@ -625,9 +633,12 @@ __global__ void __launch_bounds__(256) k_mlp_staged(Geom g, MlpTabs mt, const fl
     const int64_t c0 = tile * 128;
     const int b = nbuf == 2 ? (it & 1) : 0;
     const int64_t next = tile + gridDim.x;
-    if (t == 0) {
-      if (nbuf == 1) issue(tile, 0);
-      else if (next < ntile) issue(next, b ^ 1);  // released by the previous iteration's barrier
+    if (nbuf == 1) {
+      if (t == 0) issue(tile, 0);
+      pend |= 1u;
+    } else if (next < ntile) {
+      if (t == 0) issue(next, b ^ 1);  // released by the previous iteration's barrier
+      pend |= 1u << (b ^ 1);
     }
     if (t < 16) {
       const int sd = t >> 3, k = t & 7;
@@ -640,6 +651,7 @@ __global__ void __launch_bounds__(256) k_mlp_staged(Geom g, MlpTabs mt, const fl
       break;
     }
     par ^= 1u << b;
+    pend &= ~(1u << b);
     const float* st = buf + b * bufsz;
     {
       using Dm = CtDims<GLM, DEG>;
@@ -746,6 +758,14 @@ __global__ void __launch_bounds__(256) k_mlp_staged(Geom g, MlpTabs mt, const fl
     // a commit not observed in time: wait once more (bounded) before the columns are freed
     const long long t0 = clock64();
     while (!mbar_try_wait(bar + 2, (unsigned)mma_pending))
+      if (clock64() - t0 > kWaitCycles) break;
+  }
+  // timeout path: no new copies were issued after the failed wait; drain those
+  // still in flight (bounded) before the block's shared memory is released
+  for (int bb = 0; bb < 2; ++bb) {
+    if (!((pend >> bb) & 1u)) continue;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar + bb, (par >> bb) & 1u))
       if (clock64() - t0 > kWaitCycles) break;
   }
   tc::fence_before_sync();

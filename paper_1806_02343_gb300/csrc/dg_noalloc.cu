@@ -10,6 +10,9 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "../../include/dg_mhd.h"
@@ -30,45 +33,71 @@ namespace {
 constexpr size_t kScratchDoubles = size_t(4) << 20;  // 32 MiB
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-double* g_scratch_addr[kMaxDevices] = {nullptr};
-
 inline size_t round256(size_t n_doubles) { return (n_doubles + 31) / 32 * 32; }
 
-// Device address of g_scratch on the current device; resolved once per device.
-int scratch_address(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DG_E_CUDA;
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) return DG_E_CUDA;
-    g_scratch_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_addr[dev];
-  return DG_OK;
+// Host copies of the reference-element tables, one set per (dimension, degree,
+// scheme), built on first use and kept until the process exits: the
+// asynchronous uploads below read them after this function has returned, so
+// their storage must outlive every call.
+struct HostTabs {
+  std::vector<double> t[10];  // Pv dPv Pf Lv dLv Lf L0 wv wf minv
+};
+std::mutex g_tabs_mu;
+std::map<std::tuple<int, int, int>, HostTabs>& tabs_cache() {
+  static std::map<std::tuple<int, int, int>, HostTabs> m;  // never destroyed before exit
+  return m;
 }
+
+const HostTabs& host_tabs_for(const Basis& B, const Geom& g, int divB_scheme) {
+  std::lock_guard<std::mutex> lk(g_tabs_mu);
+  auto key = std::make_tuple(g.D, g.d, divB_scheme);
+  auto& m = tabs_cache();
+  auto it = m.find(key);
+  if (it == m.end()) {
+    HostTabs h;
+    host_tables(B, g, h.t);
+    it = m.emplace(key, std::move(h)).first;  // std::map nodes never move afterwards
+  }
+  return it->second;
+}
+
+// Sets status bit 1 (non-finite) if any entry of the rhs rows is NaN or infinite.
+__global__ void k_noalloc_finite(const double* __restrict__ rhs, int nrows, int64_t ncell, int64_t stride,
+                                 DevScalars* sc) {
+  bool bad = false;
+  const int64_t total = (int64_t)nrows * ncell;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / ncell, c = i - r * ncell;
+    bad |= !isfinite(rhs[r * stride + c]);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&sc->status, 1);
+}
+
+// Copies the status word of the scalars to the caller's device int.
+__global__ void k_noalloc_status(const DevScalars* sc, int* status_dev) { *status_dev = sc->status; }
 
 }  // namespace
 
 extern "C" int dg_mhd_rhs_noalloc(const dg_mesh_desc* mesh, int degree, int divB_scheme, double gamma,
                                   const dg_mhd_params* p, double c_h, double damping_rate, const double* w,
-                                  double* rhs, void* stream) {
+                                  double* rhs, int* status_dev, void* stream) {
   if (!mesh || !w || !rhs) return DG_E_ARG;
   Basis B;
   Geom g;
   int e = make_geom(mesh, degree, divB_scheme, gamma, B, g);
   if (e) return e;
-  if (g.glm && !(c_h > 0.0)) return DG_E_ARG;
+  if (g.glm && (!(c_h > 0.0) || !(damping_rate >= 0.0))) return DG_E_ARG;
   dg_mhd_params prm;
   if (p) prm = *p;
   else dg_mhd_default_params(&prm);
+  // the HLLD degeneracy tolerance is the only parameter read here
+  if (!(prm.eps_hlld >= 0.0 && prm.eps_hlld < 1.0)) return DG_E_ARG;
 
-  std::vector<double> tabs[10];  // Pv dPv Pf Lv dLv Lf L0 wv wf minv
-  host_tables(B, g, tabs);
+  const HostTabs& ht = host_tabs_for(B, g, divB_scheme);
   size_t off[10], total = 0;
   for (int i = 0; i < 10; ++i) {
     off[i] = total;
-    total += round256(tabs[i].size());
+    total += round256(ht.t[i].size());
   }
   const size_t sc_off = total;
   total += round256((sizeof(DevScalars) + sizeof(double) - 1) / sizeof(double));
@@ -77,12 +106,17 @@ extern "C" int dg_mhd_rhs_noalloc(const dg_mesh_desc* mesh, int degree, int divB
   total += round256(face_elems);
   if (total > kScratchDoubles) return DG_E_ARG;  // problem larger than the static scratch
 
-  double* base = nullptr;
-  if ((e = scratch_address(&base))) return e;
+  // The array's device address on the current device, looked up on every call
+  // (the lookup allocates nothing). On a device's first call with lazily
+  // loaded modules it may load this library's module: that can allocate and
+  // synchronise, so such callers make one warm-up call at start-up.
+  void* pv = nullptr;
+  if (cudaGetSymbolAddress(&pv, g_scratch) != cudaSuccess || pv == nullptr) return DG_E_CUDA;
+  double* base = static_cast<double*>(pv);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   for (int i = 0; i < 10; ++i)
-    if (!tabs[i].empty() &&
-        cudaMemcpyAsync(base + off[i], tabs[i].data(), tabs[i].size() * sizeof(double), cudaMemcpyHostToDevice,
+    if (!ht.t[i].empty() &&
+        cudaMemcpyAsync(base + off[i], ht.t[i].data(), ht.t[i].size() * sizeof(double), cudaMemcpyHostToDevice,
                         st) != cudaSuccess)
       return DG_E_CUDA;
   Tables<double> tb;
@@ -95,7 +129,12 @@ extern "C" int dg_mhd_rhs_noalloc(const dg_mesh_desc* mesh, int degree, int divB
   double* fbuf = base + face_off;  // fully written by the face kernel before it is read
   launch_face<double>(g, tb, w, fbuf, sc, prm.eps_hlld, st);
   launch_cell<double>(g, tb, w, fbuf, rhs, nullptr, 0.0, 1.0, 0, sc, nullptr, nullptr, nullptr, st);
+  // the call's device status word (bit 1: a non-finite value in rhs), copied
+  // out before a later call clears it
+  if (status_dev) {
+    k_noalloc_finite<<<64, 256, 0, st>>>(rhs, g.nrows, g.ncell, g.stride, sc);
+    k_noalloc_status<<<1, 1, 0, st>>>(sc, status_dev);
+  }
   if (cudaGetLastError() != cudaSuccess) return DG_E_CUDA;
-  // the host vectors above are pageable: the copies were staged before returning
   return DG_OK;
 }

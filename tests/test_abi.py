@@ -134,3 +134,20 @@ def test_host_entry_points_reject_null_arguments(lib):
     assert lib.dg_mhd_regrid_tables(3, 2, 0, 0, None, sizes.ctypes.data) == 0 and sizes[0] == 3 * 10 * 10
     small = np.zeros(1)
     assert lib.dg_mhd_regrid_tables(3, 2, 0, 1, small.ctypes.data, sizes.ctypes.data) == -1
+
+
+def test_eps_hlld_and_noalloc_arguments_checked_on_host(lib):
+    """NaN or out-of-range HLLD tolerances, and missing GLM speeds of the
+    allocation-free operator, are rejected before any device work."""
+    import ctypes
+    from paper_1806_02343_gb300 import binding
+    m = binding.mesh_desc(3, (4, 4, 4))
+    h = ctypes.c_void_p()
+    for eps in (float("nan"), -1e-8, 1.0):
+        bad = binding.default_params(eps_hlld=eps)
+        assert lib.dg_mhd_init(ctypes.byref(m), 2, 1, 5.0 / 3.0, ctypes.byref(bad), ctypes.byref(h)) == -1
+        assert lib.dg_mhd_rhs_noalloc(ctypes.byref(m), 2, 1, 5.0 / 3.0, ctypes.byref(bad), 1.0, 1.0,
+                                      ctypes.c_void_p(16), ctypes.c_void_p(16), None, None) == -1
+    for ch, kap in ((0.0, 1.0), (float("nan"), 1.0), (1.0, -1.0)):
+        assert lib.dg_mhd_rhs_noalloc(ctypes.byref(m), 2, 1, 5.0 / 3.0, None, ch, kap,
+                                      ctypes.c_void_p(16), ctypes.c_void_p(16), None, None) == -1

@@ -117,11 +117,12 @@ def test_dt_fp64(D, d, divb, ncell, fname):
 
 @pytest.mark.parametrize("D,d,divb,ncell,fname", CASES)
 def test_dt_fp32_form(D, d, divb, ncell, fname):
-    """FP32 form: the step length from the float mirror of the means. The CFL
-    bound is a few float operations per cell (relative error ~1e-6); the Powell
-    bound divides by the face jumps |B^n_F - B^n_K| of FP32 traces, whose
-    relative error is eps32 |B| / |jump| (~1e-3 on smooth data, where the
-    jumps are O(dx^(d+1)))."""
+    """FP32 form: an FP32 screen over the float mirror of the means finds the
+    cells whose bound can be the minimum; those are recomputed in FP64 from the
+    FP64 means and min-reduced in FP64, so the CFL bound is the FP64 one (the
+    oracle's to rounding). The Powell bound divides by the face jumps
+    |B^n_F - B^n_K| of FP32 traces, whose relative error is eps32 |B| / |jump|
+    (~1e-3 on smooth data, where the jumps are O(dx^(d+1)))."""
     S, w0, sol = _setup(D, d, divb, ncell, fname, precision="fp32")
     w = to_device(w0, sol)
     wm = means_to_device(w0, sol, S)
@@ -131,8 +132,32 @@ def test_dt_fp32_form(D, d, divb, ncell, fname):
     S.P.eta_powell = float("inf")
     cfl_only = S.dt(w0)
     S.P.eta_powell = eta
-    tol = 1e-5 if (divb == "glm" or cfl_only == ref) else 5e-3
+    tol = 1e-13 if (divb == "glm" or cfl_only == ref) else 5e-3
     assert abs(dt - ref) <= tol * ref
+
+
+@pytest.mark.parametrize("divb", ["glm", "powell"])
+def test_dt_fp32_form_uniform_state(divb):
+    """Every cell holds the same state, so every cell is a candidate of the FP64
+    pass; the step length is the closed form C/(2d+1) / sum_a((|v_a| + c_f)/dx)
+    of eq. cfl (Powell: no face jumps, so the eta bound is inactive)."""
+    import numpy as np
+    D, d, ncell = 3, 2, (8, 8, 8)
+    u = np.array([1.3, 0.39, -0.26, 0.13, 4.1, 0.5, -0.3, 0.2, 0.0])
+    V = 9 if divb == "glm" else 8
+    S = Scheme(D, d, divb, G, ncell)
+    w0 = S.project(lambda x: np.broadcast_to(u[:V], x.shape[:-1] + (V,)).copy())
+    from paper_1806_02343_gb300.binding import DG_PREC_FP32MIX, Solver
+    sol = Solver(D, ncell, d, divb, gamma=G, box_len=S.L, precision=DG_PREC_FP32MIX)
+    w = to_device(w0, sol)
+    wm = means_to_device(w0, sol, S)
+    dt = sol.dt(w, wm).item()
+    rho, m, E, B = u[0], u[1:4], u[4], u[5:8]
+    v = m / rho
+    p = (G - 1) * (E - 0.5 * rho * v @ v - 0.5 * B @ B)
+    c = np.sqrt((G * p + B @ B) / rho)
+    ref = S.P.cfl / (2 * d + 1) / np.sum((np.abs(v) + c) / S.dx)
+    assert abs(dt - ref) <= 1e-13 * ref
 
 
 @pytest.mark.parametrize("D,d,divb,ncell,fname", CASES[:1] + CASES[2:3] + CASES[4:5])

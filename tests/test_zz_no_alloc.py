@@ -36,18 +36,42 @@ def test_noalloc_matches_rhs_twice(D, d, divb, ncell):
     ref = torch.zeros_like(w)
     sol.rhs(w, None, ref)
     ref_np = ref[:, : sol.ncell].cpu().numpy()
+    status = torch.full((1,), -7, dtype=torch.int32, device="cuda")
     for _ in range(2):
         out = torch.full_like(w, float("nan"))
-        rhs_noalloc(D, ncell, d, divb, w, out, gamma=G, box_len=S.L, c_h=ch, damping_rate=kap)
+        rhs_noalloc(D, ncell, d, divb, w, out, gamma=G, box_len=S.L, c_h=ch, damping_rate=kap, status=status)
         torch.cuda.synchronize()
         got = out[:, : sol.ncell].cpu().numpy()
         assert _rel(got, ref_np) < 1e-12
+        assert int(status.item()) == 0
+    # a NaN planted in the input (on the host side of the call) reaches the
+    # caller through the status word; the next clean call reports 0 again
+    wbad = w.clone()
+    wbad[0, 3] = float("nan")
+    rhs_noalloc(D, ncell, d, divb, wbad, out, gamma=G, box_len=S.L, c_h=ch, damping_rate=kap, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) & 1
+    rhs_noalloc(D, ncell, d, divb, w, out, gamma=G, box_len=S.L, c_h=ch, damping_rate=kap, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert _rel(out[:, : sol.ncell].cpu().numpy(), ref_np) < 1e-12
 
 
 def test_noalloc_rejects_oversized_problem():
     import torch
     from paper_1806_02343_gb300 import binding
-    w = torch.zeros((90, 32), dtype=torch.float64, device="cuda")
+    w = torch.zeros((90, 64 ** 3), dtype=torch.float64, device="cuda")
     with pytest.raises(binding.DGError) as e:
         binding.rhs_noalloc(3, (64, 64, 64), 2, "glm", w, w, c_h=1.0, damping_rate=1.0)
     assert e.value.code == -1
+
+
+def test_noalloc_rejects_mismatched_buffers():
+    import torch
+    from paper_1806_02343_gb300 import binding
+    ok = torch.zeros((90, 224), dtype=torch.float64, device="cuda")   # 7 x 6 x 5 cells -> stride 224
+    for bad in (torch.zeros((90, 32), dtype=torch.float64, device="cuda"),
+                torch.zeros((90, 224), dtype=torch.float32, device="cuda"),
+                torch.zeros((224, 90), dtype=torch.float64, device="cuda").t()):
+        with pytest.raises(ValueError):
+            binding.rhs_noalloc(3, (7, 6, 5), 2, "glm", ok, bad, c_h=1.0, damping_rate=1.0)
