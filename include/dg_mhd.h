@@ -106,7 +106,11 @@ typedef struct {
   int limiter;        /* DG_LIMIT_*                                  [OFF]  */
   int positivity;     /* 1: positivity limiter on                    [0]    */
   int generic_kernels;/* 1: force the generic kernels even where a    [0]
-                         specialised kernel exists (testing)                 */
+                         specialised kernel exists (testing); 2: the
+                         specialised kernels with the cell update's
+                         contractions on the tensor core (3D GLM, degree
+                         2, FP32 form; slower than the default CUDA-core
+                         update on GB300, kept for comparison)               */
   int rk_order;       /* SSP-RK order of dg_mhd_step, 1..4 (Sec. 3.6); [3]
                          0: degree + 1 (at most 4), the paper's default      */
   int powell_q;       /* Powell face term q^dagger (Sec. 4.1.3):       [0]

@@ -8,12 +8,14 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/dg_mhd.h"
 #include "dg_amr.cuh"
 #include "dg_basis.h"
 #include "dg_ctx.h"
+#include "dg_cell_tc.cuh"
 #include "dg_fast.cuh"
 #include "dg_kernels.cuh"
 #include "dg_limit.cuh"
@@ -256,6 +258,22 @@ FastGeom fast_geom(const Geom& g) {
 
 inline bool fp32(const Ctx& c) { return c.p.precision == DG_PREC_FP32MIX; }
 
+// the tensor-core cell update where the context built its tables (FP32 form,
+// degree 2); false: the caller launches the CUDA-core one
+template <typename T, int DEG>
+bool launch_cell_fast(Ctx& c, const FastAll<T, DEG>& ft, const FastGeom& fg, const T* w, const T* F, T* out,
+                      const T* w0, double ca, double cb, int combine, const double* wmean, const double* w0mean,
+                      double* outmean, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value && DEG == 2) {
+    if (c.tc_tabs) {
+      launch_cell_tc(c.tc_tabs, ft, fg, w, F, out, w0, ca, cb, combine, c.sc, wmean, w0mean, outmean, c.nsm, st);
+      return true;
+    }
+  }
+  return false;
+}
+
+
 }  // namespace
 
 namespace dgmhd {
@@ -428,7 +446,8 @@ void dg_mhd_destroy(dg_mhd_ctx* ctx) {
   free_tables(c.t32);
   void* ptrs[] = {c.sc, c.face_buf, c.face_buf32, c.stage_buf[0], c.stage_buf[1], c.stage_buf[2],
                   c.stage_mean[0], c.stage_mean[1], c.stage_mean[2], c.cellscratch, c.proj_tab, c.proj_w,
-                  c.troubled, c.flag_list, c.pos_list, c.mlp_w1, c.mlp_w2, c.mlp_bias, c.rg_tabs, c.qdag_buf};
+                  c.troubled, c.flag_list, c.pos_list, c.mlp_w1, c.mlp_w2, c.mlp_bias, c.rg_tabs, c.qdag_buf,
+                  c.tc_tabs};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c.hb;
@@ -560,13 +579,26 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
   upload_limiter_tables(c);
   mlp_build_tables(c);
   // specialised GLM kernels for uniform 3D meshes
-  if (g.glm && g.D == 3 && !prm.generic_kernels && !c.amr.on) {
+  if (g.glm && g.D == 3 && prm.generic_kernels != 1 && !c.amr.on) {
     if (fp32(c)) {
       if (degree == 1) c.fast_tabs = make_fast_tabs<float, 1>(h, g, *c.hb);
       if (degree == 2) c.fast_tabs = make_fast_tabs<float, 2>(h, g, *c.hb);
       // degree 3 runs the generic kernels: its fully unrolled specialisation
       // costs minutes of compilation for a secondary workload
       if (c.fast_tabs) c.fast = 10 + degree;
+      // degree 2, on request: the cell update's contractions on the tensor
+      // core (operand tables in device memory, staged into shared memory by
+      // each block). Not the default: the contractions are too small for the
+      // tensor core's per-instruction cost on this GPU (see dg_cell_tc.cu)
+      if (c.fast == 12 && prm.generic_kernels == 2) {
+        std::vector<float> tt;
+        build_tc_tables(h.Pv, h.dPv, h.Pf, h.wv, h.wf, tt);
+        if (cudaMalloc(&c.tc_tabs, tt.size() * sizeof(float)) != cudaSuccess ||
+            cudaMemcpy(c.tc_tabs, tt.data(), tt.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+          dg_mhd_destroy(ctx);
+          return DG_E_CUDA;
+        }
+      }
     } else {
       if (degree == 1) c.fast_tabs = make_fast_tabs<double, 1>(h, g, *c.hb);
       if (degree == 2) c.fast_tabs = make_fast_tabs<double, 2>(h, g, *c.hb);
@@ -674,8 +706,10 @@ int operator_pass(Ctx& c, const void* w, const double* wmean, void* out, double*
     launch_face_glm<T, DEG>(ft, fg, (const T*)w, FB, c.sc, c.p.eps_hlld, st);                               \
     c.prof.end(0, st);                                                                                      \
     c.prof.begin(1, st);                                                                                    \
-    launch_cell_glm<T, DEG>(ft, fg, (const T*)w, FB, (T*)out, (const T*)w0, ca, cb, combine, c.sc, wmean,   \
-                            w0mean, outmean, st);                                                           \
+    if (!launch_cell_fast<T, DEG>(c, ft, fg, (const T*)w, FB, (T*)out, (const T*)w0, ca, cb, combine,      \
+                                  wmean, w0mean, outmean, st))                                              \
+      launch_cell_glm<T, DEG>(ft, fg, (const T*)w, FB, (T*)out, (const T*)w0, ca, cb, combine, c.sc, wmean, \
+                              w0mean, outmean, st);                                                         \
     c.prof.end(1, st);                                                                                      \
     break;                                                                                                  \
   }

@@ -241,6 +241,7 @@ struct Ctx {
   int nsm = 152;                   // streaming multiprocessors of the device
   int fast = 0;                    // specialised GLM path: 10*prec + degree, 0 = none
   void* fast_tabs = nullptr;       // host FastAll<T, DEG> (kernel parameters)
+  float* tc_tabs = nullptr;        // device operand tables of the tensor-core cell kernel (FP32, degree 2)
 };
 
 }  // namespace dgmhd

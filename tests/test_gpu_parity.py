@@ -53,9 +53,11 @@ def _setup(D, d, divb, ncell, fname, precision="fp64", generic=0):
 GLM3D = [(3, 1, "glm", (9, 8, 7), "fourier"), CASES[2], CASES[3]]
 
 
-@pytest.mark.parametrize("generic", [0, 1])
+@pytest.mark.parametrize("generic", [0, 1, 2])
 @pytest.mark.parametrize("D,d,divb,ncell,fname", GLM3D)
 def test_rhs_glm3d_both_kernel_paths(D, d, divb, ncell, fname, generic):
+    """generic 0: specialised kernels, 1: generic kernels, 2: specialised with
+    the cell update's contractions on the tensor core (degree 2 FP32 form)."""
     for prec, tol in (("fp64", 1e-12), ("fp32", 2e-4)):
         S, w0, sol = _setup(D, d, divb, ncell, fname, precision=prec, generic=generic)
         sol.set_glm(2.7, 1.3)
@@ -378,3 +380,41 @@ def test_alfven_3d_degree3_rk4_converges(divb):
     lo_b = 3.5 if divb == "glm" else 3.2
     for v in (mhd.BX, mhd.BY, mhd.BZ):
         assert order[v] > lo_b, order
+
+
+@pytest.mark.parametrize("combine", [False, True])
+def test_tensor_core_cell_update_matches_cuda_core(combine):
+    """The tensor-core cell update (3xTF32 contractions, FP32 accumulation in
+    tensor memory) against the CUDA-core one on the same state and face
+    fluxes: 3,663 cells (115 tiles of 32, a ragged tail of 15), degree 2 GLM,
+    FP32 form; the plain operator and a full SSP-RK3 step. The mean rows use
+    the same face sums in the same order on both paths: bitwise equal for the
+    operator. Other rows: the two FP32 contraction orders differ by rounding
+    (3xTF32 products ~5e-7 relative), far inside the FP32 form's 2e-4."""
+    import torch
+    ncell = (37, 11, 9)
+    res = []
+    for generic in (2, 0):
+        S, w0, sol = _setup(3, 2, "glm", ncell, "fourier", precision="fp32", generic=generic)
+        w = to_device(w0, sol)
+        wm = means_to_device(w0, sol, S)
+        if combine:
+            sol.step(w, wm)
+            res.append((from_device(w, sol), wm[:, : sol.ncell].cpu().numpy().T.copy(), sol.status()))
+        else:
+            sol.set_glm(2.7, 1.3)
+            out = torch_empty_like(w)
+            om = torch_empty_like(wm)
+            sol.rhs(w, wm, out, om)
+            res.append((from_device(out, sol), om[:, : sol.ncell].cpu().numpy().T.copy(), sol.status()))
+    (a, am, sa), (b, bm, sb) = res
+    assert sa == 0 and sb == 0
+    assert np.all(np.isfinite(a))
+    if combine:
+        # after three stages the face fluxes differ by rounding too: the means
+        # carry FP32-level differences of the fluxes times dt (1e-8 measured)
+        assert rel_err(a, b) < 2e-6
+        assert rel_err(am, bm) < 1e-7
+    else:
+        assert rel_err(a, b) < 2e-5
+        assert np.array_equal(am, bm)
