@@ -33,15 +33,15 @@ sys.path.insert(0, ROOT)
 
 CONFIGS = {
     "turb256": dict(workload="3D 256^3 periodic, degree 2, GLM, decaying turbulence (Mach 2)", D=3, n=256, d=2,
-                    divb="glm"),
+                    divb="glm", run_steps=20),
     "turb128": dict(workload="3D 128^3 periodic, degree 2, GLM, decaying turbulence (Mach 2)", D=3, n=128, d=2,
-                    divb="glm"),
+                    divb="glm", run_steps=20),
     "fourier64": dict(workload="3D 64^3 periodic, degree 3, GLM, seeded smooth Fourier state", D=3, n=64, d=3,
-                      divb="glm"),
+                      divb="glm", run_steps=10),
     "blast128": dict(workload="3D 128^3 periodic, degree 2, Powell/LDF, MHD blast (p=100 in r<0.1, 0.1 outside, "
-                              "rho=1, B=(10/sqrt(4 pi),0,0))", D=3, n=128, d=2, divb="powell"),
+                              "rho=1, B=(10/sqrt(4 pi),0,0))", D=3, n=128, d=2, divb="powell", run_steps=20),
     "ot_amr": dict(workload="3D Orszag-Tang extrusion on a static octree, levels 5-7 (1,387,520 leaves), "
-                            "degree 2, Powell/LDF", D=3, n=None, d=2, divb="powell", amr=True),
+                            "degree 2, Powell/LDF", D=3, n=None, d=2, divb="powell", amr=True, run_steps=50),
 }
 
 
@@ -137,13 +137,86 @@ def build_fourier(sol, cfg, device):
     return nodal, npts
 
 
+def run_probes(device):
+    """Device throughput probes through the library (dg_mhd_probe), in the same
+    job as the benchmark: packed FP32 FMA, FP64 FMA, the TF32 tensor core and a
+    1 GiB device copy (read + write bytes)."""
+    from paper_1806_02343_gb300 import binding as Bd
+    out = {}
+    for name, kind, unit, scale in (("fp32_fma", Bd.PROBE_FP32_FMA, "TFLOP/s", 1e-12),
+                                    ("fp64_fma", Bd.PROBE_FP64_FMA, "TFLOP/s", 1e-12),
+                                    ("tf32_mma", Bd.PROBE_TF32_MMA, "TFLOP/s", 1e-12),
+                                    ("copy", Bd.PROBE_COPY, "GB/s", 1e-9)):
+        try:
+            r, ms = Bd.probe(kind)
+            out[name] = {"value": r * scale, "unit": unit, "ms": ms}
+        except Exception as e:  # a probe that fails is reported, not fatal
+            out[name] = {"error": str(e)}
+    import torch
+    torch.cuda.empty_cache()
+    out["how"] = ("dg_mhd_probe: one warm-up and one CUDA-event-timed launch each; FMA kinds: 8 independent "
+                  "chains per thread, 2048 threads per SM (FP32 as fma.rn.f32x2); tf32_mma: one block per SM "
+                  "issuing M=128 N=256 K=8 kind::tf32 MMAs into two tensor-memory accumulators; copy: 1 GiB "
+                  "float4 grid-stride copy, bytes read + written")
+    return out
+
+
+def host_info():
+    """nproc and the CPU model of the host the benchmark runs on."""
+    info = {"nproc": os.cpu_count()}
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    info["cpu_model"] = model
+    return info
+
+
+def state_l1(table, wa, wma, rows_a, wb, wmb, rows_b, ncell, weights, chunk=1 << 18):
+    """Per-variable L1 difference of two DG states over the cells, with the
+    quadrature of eq. lp_norm (the npts^3 Gauss points whose basis values are
+    `table` [rows, vars, P] and whose tensor weights are `weights` [P]):
+    sum |u_a - u_b| w / sum |u_b| w per variable (variables whose reference
+    sum is below 1e-6 of the largest: divided by the largest)."""
+    import torch
+    from paper_1806_02343_gb300.binding import eval_points
+    num = None
+    den = None
+    wq = torch.as_tensor(weights, dtype=torch.float64, device=wa.device)
+    for c0 in range(0, ncell, chunk):
+        c1 = min(ncell, c0 + chunk)
+        ua = eval_points(table, wa[:, c0:c1], rows_a, None if wma is None else wma[:, c0:c1])
+        ub = eval_points(table, wb[:, c0:c1], rows_b, None if wmb is None else wmb[:, c0:c1])
+        n_ = ((ua - ub).abs() * wq[None, :, None]).sum((1, 2))
+        d_ = (ub.abs() * wq[None, :, None]).sum((1, 2))
+        num = n_ if num is None else num + n_
+        den = d_ if den is None else den + d_
+        del ua, ub
+    scale = den.max()
+    l1 = torch.where(den > 1e-6 * scale, num / den, num / scale)
+    return [float(x) for x in l1.cpu()]
+
+
 def run_ours(args, cfg, rank, world, device):
     import torch
     from paper_1806_02343_gb300 import binding as Bd
     from paper_1806_02343_gb300.binding import Solver
 
     D, n, d, divb = cfg["D"], cfg["n"], cfg["d"], cfg["divb"]
-    res = {}
+    res = {"probes": run_probes(device) if rank == 0 else None}
 
     amr_mesh = None
     if cfg.get("amr"):
@@ -251,16 +324,80 @@ def run_ours(args, cfg, rank, world, device):
     # ALU view of the whole stage (the kernels are issue-bound, not HBM-bound)
     fl = stage_flops_per_cell(D, sol.degree if hasattr(sol, "degree") else d, cfg["divb"], sol.nrows)
     sm_mhz = (res.get("clocks") or {}).get("sm_mhz") or 2070.0
-    peak_tf = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    pr32 = ((res.get("probes") or {}).get("fp32_fma") or {}).get("value")
+    formula_tf = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    peak_tf = pr32 if pr32 else formula_tf
     ach_tf = fl["total"] * ncell * stages / (ms * 1e-3) / 1e12
     res["alu"] = {"bound": "alu", "flops_per_cell_stage": fl, "achieved_tflops": ach_tf, "peak_tflops": peak_tf,
-                  "peak_source": "152 SMs x 128 FP32 FMA per clock x 2 flop x the median SM clock under load "
-                                 "(bench_alu_peak.cu measured 76.7 TFLOP/s of packed FP32 FMA at 1,973 MHz on "
-                                 "this GPU type: the formula's value at that clock within 0.2%)",
+                  "peak_source": ("measured in this job: the packed FP32 FMA probe (dg_mhd_probe kind 0)" if pr32
+                                  else "152 SMs x 128 FP32 FMA per clock x 2 flop x the median SM clock under load"),
+                  "formula_tflops": formula_tf,
                   "frac": ach_tf / peak_tf,
                   "note": "contractions counted exactly; the pointwise volume flux (~60 flop per point) and HLLD "
                           "(~500 flop per face point) estimated; the indicator's network runs on the tensor "
                           "cores and is not counted"}
+
+    # ------------------------------------------------------------ FP32 form with the plain detector
+    # The same workload with TVB-characteristic detection on every cell instead
+    # of the learned indicator: separates the indicator's gain from the
+    # FP32-vs-FP64 gain.
+    if args.limiter == "mlp" and not args.skip_plain_arm:
+        solp, wp, wmp = make(Bd.DG_PREC_FP32MIX, "tvb")
+        for _ in range(args.warmup):
+            solp.step(wp, wmp)
+        torch.cuda.synchronize()
+        solp.limiter_counts(reset=True)
+        solp.counters(reset=True)
+        solp.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            solp.step(wp, wmp)
+        e1.record(st)
+        torch.cuda.synchronize()
+        msp = e0.elapsed_time(e1)
+        kp = {}
+        for k, name in ((Bd.KIND_FACE, "face_flux"), (Bd.KIND_CELL, "cell_update"), (Bd.KIND_DT, "timestep"),
+                        (Bd.KIND_LIMIT, "tvb_limiter"), (Bd.KIND_POSITIVITY, "positivity")):
+            t, nl = solp.profile_read(k)
+            kp[name] = {"ms_total": t, "launches": nl}
+        solp.profile(False)
+        lc = solp.limiter_counts()
+        passes, flagged, limited = lc["passes"], lc["flagged"], lc["limited"]
+        pos_cells = solp.counters()["pos_cells"]
+        lim_ms = (kp["tvb_limiter"]["ms_total"] + kp["positivity"]["ms_total"]) / stages
+        res["fp32_plain_tvb"] = {
+            "value": whole_job_value(dof, stages, world, max_over_ranks(msp, world, device)),
+            "unit": "DoF-updates/s", "ms_per_step": msp / args.steps, "limiter_ms_per_stage": lim_ms,
+            "cells_examined_per_pass": flagged / max(passes, 1), "cells_limited_per_pass": limited / max(passes, 1),
+            "positivity_cells_per_pass": pos_cells / max(passes, 1), "kernels": kp, "status": solp.status()}
+        # the learned arm's own limiter figures over the timed steps
+        lim_l = (kern["tvb_limiter"]["ms_total"] + kern["positivity"]["ms_total"] + kern["indicator"]["ms_total"])
+        res["fp32_learned_limiter"] = {"limiter_ms_per_stage": lim_l / stages}
+        # detector quality on the learned arm's final state: the cells whose slopes
+        # the plain procedure changes (the judge) against those the gated one
+        # changes; a missed cell is plain-limited but not limited under the gate
+        tm_ = torch.zeros(sol.stride, dtype=torch.uint8, device=device)
+        tp_ = torch.zeros_like(tm_)
+        a1, m1 = w.clone(), wm.clone()
+        a2, m2 = w.clone(), wm.clone()
+        sol.limiter_counts(reset=True)
+        sol.limit(a1, m1, tm_)
+        solp.limit(a2, m2, tp_)
+        lcm = sol.limiter_counts()
+        fl_m, li_m = lcm["flagged"], lcm["limited"]
+        P = tp_[:ncell].bool()
+        M = tm_[:ncell].bool()
+        n_plain = int(P.sum().item())
+        missed = int((P & ~M).sum().item())
+        res["indicator_quality"] = {
+            "state": f"the learned arm's state after {args.warmup + args.steps} steps",
+            "cells": ncell, "flagged_by_network": fl_m, "limited_under_gate": li_m,
+            "limited_by_plain_detector": n_plain, "missed": missed,
+            "missed_rate": (missed / n_plain) if n_plain else None,
+            "note": "missed_rate is null when the plain detector limits no cell"}
+        del solp, wp, wmp, a1, m1, a2, m2, tm_, tp_
+        torch.cuda.empty_cache()
 
     # ------------------------------------------------------------ one regrid step (octree workloads)
     if amr_mesh is not None:
@@ -332,44 +469,60 @@ def run_ours(args, cfg, rank, world, device):
         del sol, w
         torch.cuda.empty_cache()
 
-    # ------------------------------------------------------------ accuracy of the FP32+learned form
-    # the same start advanced by both forms with the same dt sequence (taken from
-    # the plain FP64 run): L1 difference of the cell means per variable
+    # ------------------------------------------------------------ accuracy of the FP32 forms
+    # The same start advanced by the plain FP64 path and by the FP32 forms with the
+    # same dt sequence (taken from the FP64 run) over the configuration's steps:
+    # L1 difference per variable of the full state (eq. lp_norm, d+3 Gauss points
+    # per axis) and of the cell means.
     if not args.skip_fp64 and args.l1_steps > 0:
+        import numpy as np
+        from paper_1806_02343_gb300.binding import basis_values
         s64, w64, _ = make(Bd.DG_PREC_FP64, "tvb" if args.limiter != "off" else "off")
-        s32, w32, wm32 = make(Bd.DG_PREC_FP32MIX, args.limiter)
+        arms = [("fp32_learned" if args.limiter == "mlp" else "fp32", args.limiter)]
+        if args.limiter == "mlp" and not args.skip_plain_arm:
+            arms.append(("fp32_plain_tvb", "tvb"))
+        ctx32 = [(nm, *make(Bd.DG_PREC_FP32MIX, lim)) for nm, lim in arms]
+        t0 = time.perf_counter()
         for _ in range(args.l1_steps):
             dt = s64.dt(w64)
             s64.step(w64, None, dt)
-            s32.step(w32, wm32, dt)
+            for _, s32, w32, wm32 in ctx32:
+                s32.step(w32, wm32, dt)
         torch.cuda.synchronize()
-        nm = (d + 1) * (d + 2) * (d + 3) // 6  # Legendre modes per variable (3D)
-        # the degree-0 rows: Legendre variables' mode 0, then (Powell) the degree-0 LDF rows
-        rows = [v * nm for v in range(9)] if divb == "glm" else [v * nm for v in range(5)] + [5 * nm + j
-                                                                                         for j in range(3)]
-        if cfg.get("amr") or D != 3:
-            rows = None
-        if rows is not None:
-            m64 = w64[rows, :ncell]
-            m32 = wm32[:, :ncell]
-            num = (m32 - m64).abs().sum(1)
-            den = m64.abs().sum(1)
-            scale = den.max()
-            l1 = torch.where(den > 1e-6 * scale, num / den, num / scale)
-            res["l1_fp32_learned_vs_fp64_plain"] = {
-                "steps": args.l1_steps, "quantity": "cell means, per variable: sum|a-b| / sum|b| "
-                "(variables with sum|b| < 1e-6 of the largest: / the largest)",
-                "values": [float(x) for x in l1.cpu()], "status": [s64.status(), s32.status()]}
-            if "blast" in cfg["name"]:
-                r64 = shock_radii(m64[0].cpu().numpy(), n)
-                r32 = shock_radii(m32[0].cpu().numpy(), n)
-                res["l1_fp32_learned_vs_fp64_plain"]["shock_radius"] = {
-                    "rays": ["+x", "+y", "+z", "(1,1,1)", "(-1,1,1)", "(1,-1,1)", "(-1,-1,1)"],
-                    "fp64_plain": r64, "fp32_learned": r32,
-                    "max_abs_diff": max((abs(a - b) for a, b in zip(r64, r32) if a is not None and b is not None),
-                                        default=None),
-                    "definition": "largest radius where rho reaches (max rho + 1) / 2, from the blast centre"}
-        del s64, w64, s32, w32, wm32
+        l1_wall = time.perf_counter() - t0
+        nq = d + 3
+        g1, gw = np.polynomial.legendre.leggauss(nq)
+        pts = np.stack(np.meshgrid(g1, g1, g1, indexing="ij"), -1).reshape(-1, 3)
+        wq = np.einsum("i,j,k->ijk", gw, gw, gw).reshape(-1)
+        out = {"steps": args.l1_steps, "dt": "the plain FP64 run's CFL step, shared by every form",
+               "quantity": "per variable sum|a-b| / sum|b| (variables whose sum|b| < 1e-6 of the largest: / the "
+                           "largest), a = FP32 form, b = plain FP64",
+               "state": f"point values at {nq}^3 Gauss points per cell (eq. lp_norm)", "wall_s": l1_wall}
+        if not cfg.get("amr") and D == 3:
+            table = basis_values(3, d, divb, pts)
+            r64 = s64.mean_rows()
+            m64 = w64[r64, :ncell]
+            for nm, s32, w32, wm32 in ctx32:
+                full = state_l1(table, w32, wm32, s32.mean_rows(), w64, None, r64, ncell, wq)
+                m32 = wm32[:, :ncell]
+                num = (m32 - m64).abs().sum(1)
+                den = m64.abs().sum(1)
+                scale = den.max()
+                lm = torch.where(den > 1e-6 * scale, num / den, num / scale)
+                entry = {"full_state": full, "cell_means": [float(x) for x in lm.cpu()], "status": s32.status()}
+                if "blast" in cfg["name"]:
+                    ra = shock_radii(m64[0].cpu().numpy(), n)
+                    rb = shock_radii(m32[0].cpu().numpy(), n)
+                    entry["shock_radius"] = {
+                        "rays": ["+x", "+y", "+z", "(1,1,1)", "(-1,1,1)", "(1,-1,1)", "(-1,-1,1)"],
+                        "fp64_plain": ra, nm: rb,
+                        "max_abs_diff": max((abs(a - b) for a, b in zip(ra, rb) if a is not None and b is not None),
+                                            default=None),
+                        "definition": "largest radius where rho reaches (max rho + 1) / 2, from the blast centre"}
+                out[nm] = entry
+        out["fp64_status"] = s64.status()
+        res["l1_vs_fp64_plain"] = out
+        del s64, w64, ctx32
         torch.cuda.empty_cache()
     return res
 
@@ -426,6 +579,7 @@ def cpu_baseline(cfg, nsample=24, steps=1, warmup=0, sample=None, limited=True):
 
     for _ in range(warmup):
         one(w)
+    ts = time.time()
     t0 = time.perf_counter()
     for _ in range(steps):
         w = one(w)
@@ -436,7 +590,30 @@ def cpu_baseline(cfg, nsample=24, steps=1, warmup=0, sample=None, limited=True):
                       f"{' (uniform stand-in for the octree)' if cfg.get('amr') else ''} "
                       f"({S.C} cells x {S.N} DoF)"
                       f"{', TVB-characteristic + positivity limiters before every stage' if limited else ''}, "
-                      f"numpy FP64, one thread (BLAS pinned to one)", "seconds": el, "w": w}
+                      f"numpy FP64, one thread (BLAS pinned to one)", "seconds": el, "w": w,
+            "t_start": ts, "t_end": ts + el}
+
+
+def _cpu_worker(a):
+    cfg, nsample, limited = a
+    r = cpu_baseline(cfg, nsample, limited=limited)
+    return r["value"] * r["seconds"], r["t_start"], r["t_end"]
+
+
+def cpu_baseline_all_cores(cfg, nsample=24, limited=True, procs=None):
+    """The same oracle sample run by one process per host core at once (spawned
+    processes: the parent already holds a CUDA context); throughput = all
+    DoF-updates / the wall time from the first start to the last end."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        res = pool.map(_cpu_worker, [(cfg, nsample, limited)] * procs)
+    work = sum(r[0] for r in res)
+    wall = max(r[2] for r in res) - min(r[1] for r in res)
+    return {"value": work / wall, "unit": "DoF-updates/s", "cores": procs, "kind": "oracle",
+            "sample": f"{procs} concurrent copies of the one-thread sample below (one per host core)",
+            "seconds": wall}
 
 
 RAYS = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 1), (-1, 1, 1), (1, -1, 1), (-1, -1, 1)]
@@ -573,10 +750,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="turb256", choices=sorted(CONFIGS))
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--l1-steps", type=int, default=2,
+    ap.add_argument("--l1-steps", type=int, default=None,
                     help="steps of the FP32+learned vs plain FP64 accuracy comparison (0: off)")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-plain-arm", action="store_true",
+                    help="no FP32 arm with the plain TVB detector beside the learned one")
     ap.add_argument("--cpu-sample", type=int, default=24)
+    ap.add_argument("--cpu-one-core", action="store_true", help="skip the all-core run of the CPU oracle")
     ap.add_argument("--limiter", default=None, choices=["mlp", "tvb", "off"],
                     help="default: mlp (learned indicator); tvb on octree meshes")
     ap.add_argument("--threshold", type=float, default=0.1)
@@ -585,6 +765,8 @@ def main():
     cfg["name"] = args.config
     if args.limiter is None:
         args.limiter = "tvb" if cfg.get("amr") else "mlp"
+    if args.l1_steps is None:
+        args.l1_steps = cfg.get("run_steps", 20)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -607,7 +789,7 @@ def main():
                 "ms_per_step": cb["seconds"] * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
                 "cpu_baseline": {"kind": cb["kind"], "cores": cb["cores"], "sample": cb["sample"], "value": v,
-                                 "unit": "DoF-updates/s"},
+                                 "unit": "DoF-updates/s"}, "host": host_info(),
                 "e2e": {"value": v, "unit": "DoF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -630,15 +812,27 @@ def main():
     config["l2_flush"] = (f"inputs larger than L2: the state is {res['state_bytes'] / 1e9:.2f} GB and every "
                           f"stage streams it (L2 129 MB)")
     cb = cpu_baseline(cfg, args.cpu_sample, limited=args.limiter != "off")
+    cb1 = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    cball = None
+    if not args.cpu_one_core:
+        try:
+            cball = cpu_baseline_all_cores(cfg, args.cpu_sample, limited=args.limiter != "off")
+            cball["sample"] += ": " + cb["sample"]
+            cball = {k: cball[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        except Exception as e:
+            cball = None
+            cb1["all_cores_error"] = str(e)
     line = {
         "metric": "DG-MHD DoF-updates/s per RK stage", "value": res["value"], "unit": "DoF-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 cell means)",
         "data": "synthetic", "config": config, "e2e": res["e2e"], "roofline": res["roofline"],
-        "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "cpu_baseline": cball or cb1, "cpu_baseline_1core": cb1, "host": host_info(),
         "clocks": res["clocks"], "gpu_launches": res["launches"], "kernels": res["kern"],
         "fp64_plain": res.get("fp64_plain"), "status": res["status"], "finite": res["finite"],
-        "l1_fp32_learned_vs_fp64_plain": res.get("l1_fp32_learned_vs_fp64_plain"),
+        "l1_vs_fp64_plain": res.get("l1_vs_fp64_plain"),
+        "fp32_plain_tvb": res.get("fp32_plain_tvb"), "fp32_learned_limiter": res.get("fp32_learned_limiter"),
+        "indicator_quality": res.get("indicator_quality"), "probes": res.get("probes"),
         "dof": res["dof"],
         "regrid": res.get("regrid"),
         "alu": res.get("alu"),

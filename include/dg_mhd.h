@@ -87,6 +87,12 @@ typedef struct {
   int64_t n_leaves;      /* octree: number of leaves                           */
   const int8_t* level;   /* octree: n_leaves levels (NULL: uniform mesh)       */
   const int32_t* ijk;    /* octree: n_leaves*dim integer coordinates           */
+  int partial;           /* octree, 1: a partition's local mesh -- the owned
+                            leaves and their face neighbours (ghosts) of a
+                            larger octree; they need not cover the cube, a face
+                            with no leaf across it is left out (the ghosts'
+                            results are the caller's to discard), regridding
+                            calls return DG_E_UNSUPPORTED. 0: a full mesh    */
 } dg_mesh_desc;
 
 /* Parameters of Sec. 3.6, 4.1, 4.2, 4.3, 5.1 (defaults in brackets). */
@@ -170,6 +176,28 @@ int dg_mhd_set_glm(dg_mhd_ctx* ctx, double c_h, double damping_rate, void* strea
  * w is not modified. rhs has the layout of w. */
 int dg_mhd_rhs(dg_mhd_ctx* ctx, const void* w, const double* wmean, void* rhs, double* rhs_mean,
                void* stream);
+
+/* One stage of an SSP Runge-Kutta step (Sec. 3.6): out = a u0 + b (w + dt
+ * L(w)) with L the operator of dg_mhd_rhs and dt the context's current step
+ * (from dg_mhd_dt or dg_mhd_set_dt); the SSP-RK3 step of dg_mhd_step is
+ * stage(w -> s1; 0, 1), stage(s1 -> s2; 3/4 w, 1/4), stage(s2 -> w; 1/3 w,
+ * 2/3) with the limiter applied to s1 and s2. u0 may be NULL when a == 0; out
+ * may alias u0 (not w). FP32MIX: wmean, outmean and (with u0) u0mean are the
+ * FP64 means. Layouts as dg_mhd_rhs. */
+int dg_mhd_stage(dg_mhd_ctx* ctx, const void* w, const double* wmean, const void* u0, const double* u0mean,
+                 void* out, double* outmean, double a, double b, void* stream);
+
+/* Sets the step length from a DEVICE double (for instance the minimum over
+ * the ranks of a partitioned run, after an all-reduce) and, for GLM, the
+ * cleaning speed and damping rate derived from it (Sec. 4.1.5), as dg_mhd_step
+ * does with a given dt. Asynchronous on stream. */
+int dg_mhd_set_dt(dg_mhd_ctx* ctx, const double* dt_dev, void* stream);
+
+/* Cells that count in the timestep minimum of dg_mhd_dt (eq. cfl, eq.
+ * powell_dt): mask (DEVICE, n_cells bytes, copied) holds 1 for the cells a
+ * partition's rank owns, 0 for its ghost cells, whose face neighbours may be
+ * missing or stale; NULL restores all cells. */
+int dg_mhd_set_owned(dg_mhd_ctx* ctx, const uint8_t* mask, void* stream);
 
 /* Limiters of Sec. 4.2-4.3 in place on w: TVB-characteristic slope limiter
  * (with the LDF slope fix of Sec. 4.2.4 for Powell) if enabled, then the
@@ -269,6 +297,17 @@ int dg_mhd_mlp_train(const float* X, int ldx, const uint8_t* y, int64_t n, int n
  * summed event-timed device milliseconds and the number of launches since the
  * last reset. dg_mhd_launch_count returns all launches since the last reset. */
 int dg_mhd_profile(dg_mhd_ctx* ctx, int enable);
+/* Throughput probe of the current device (measurement support, no counterpart
+ * in the paper; synchronous: one warm-up and one timed launch, CUDA events on
+ * `stream`). kind 0: packed FP32 FMA (fma.rn.f32x2), 1: FP64 FMA, 2: TF32
+ * tensor-core MMA (tcgen05 kind::tf32, M = 128, N = 256, K = 8, FP32
+ * accumulators in tensor memory, one block per SM), 3: device-memory copy of
+ * `bytes` (a multiple of 16) from src to dst (caller-owned DEVICE buffers,
+ * 16-byte aligned; ignored for kinds 0-2). *rate: flop/s (kinds 0-2, 2 flop per
+ * FMA) or bytes/s read plus written (kind 3); *ms: the timed launch.
+ * DG_E_ARG for a bad kind or copy size, DG_E_TIMEOUT if the MMA probe's
+ * bounded wait ran out. */
+int dg_mhd_probe(int kind, const void* src, void* dst, int64_t bytes, double* rate, double* ms, void* stream);
 int dg_mhd_profile_read(dg_mhd_ctx* ctx, int kind, double* total_ms, int64_t* launches);
 int64_t dg_mhd_launch_count(const dg_mhd_ctx* ctx);
 
@@ -374,8 +413,11 @@ int dg_mhd_sibling_groups(int dim, int64_t n, const int8_t* level, const int32_t
  * sub << 4, kind 0 same level, 1 coarse cell on the left, 2 on the right, sub
  * = the fine cell's coordinate parities across the face (bit j for the j-th
  * other axis in increasing order). Writes *n_faces and, if the three arrays
- * are non-NULL and cap >= *n_faces, the faces (DG_E_ARG if cap is too small). */
-int dg_mhd_octree_faces(int dim, int64_t n, const int8_t* level, const int32_t* ijk, int64_t cap,
+ * are non-NULL and cap >= *n_faces, the faces (DG_E_ARG if cap is too small).
+ * partial = 1: the leaves of a partition's local mesh (owned and ghost cells,
+ * see dg_mesh_desc.partial): they need not cover the cube; a face with no leaf
+ * across it is left out. */
+int dg_mhd_octree_faces(int dim, int64_t n, const int8_t* level, const int32_t* ijk, int partial, int64_t cap,
                         int32_t* face_left, int32_t* face_right, int32_t* face_meta, int64_t* n_faces);
 
 /* The tables a context's regridding calls use (HOST, no context, no device

@@ -29,6 +29,7 @@ EXPORTS = [
     "dg_mhd_mlp_train", "dg_mhd_counters", "dg_mhd_limiter_counts", "dg_mhd_divb", "dg_mhd_smoothness",
     "dg_mhd_amr_marks", "dg_mhd_regrid_plan", "dg_mhd_remap", "dg_mhd_regrid_plan_mesh",
     "dg_mhd_sibling_groups", "dg_mhd_octree_faces", "dg_mhd_basis_values", "dg_mhd_regrid_tables",
+    "dg_mhd_probe", "dg_mhd_stage", "dg_mhd_set_dt", "dg_mhd_set_owned",
 ]
 KIND_FACE, KIND_CELL, KIND_DT, KIND_LIMIT, KIND_PROJECT, KIND_POSITIVITY, KIND_MLP = range(7)
 
@@ -36,7 +37,8 @@ KIND_FACE, KIND_CELL, KIND_DT, KIND_LIMIT, KIND_PROJECT, KIND_POSITIVITY, KIND_M
 class MeshDesc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int32 * 3), ("box_len", ctypes.c_double),
                 ("periodic", ctypes.c_int), ("n_leaves", ctypes.c_int64),
-                ("level", ctypes.POINTER(ctypes.c_int8)), ("ijk", ctypes.POINTER(ctypes.c_int32))]
+                ("level", ctypes.POINTER(ctypes.c_int8)), ("ijk", ctypes.POINTER(ctypes.c_int32)),
+                ("partial", ctypes.c_int)]
 
 
 class Params(ctypes.Structure):
@@ -66,6 +68,9 @@ def lib():
     L.dg_mhd_set_glm.argtypes = [vp, ctypes.c_double, ctypes.c_double, vp]
     L.dg_mhd_rhs.argtypes = [vp, vp, dp, vp, dp, vp]
     L.dg_mhd_limit.argtypes = [vp, vp, dp, vp, vp]
+    L.dg_mhd_stage.argtypes = [vp, vp, dp, vp, dp, vp, dp, ctypes.c_double, ctypes.c_double, vp]
+    L.dg_mhd_set_dt.argtypes = [vp, dp, vp]
+    L.dg_mhd_set_owned.argtypes = [vp, vp, vp]
     L.dg_mhd_dt.argtypes = [vp, vp, dp, dp, vp]
     L.dg_mhd_step.argtypes = [vp, vp, dp, dp, vp]
     L.dg_mhd_last_dt.argtypes = [vp]
@@ -96,11 +101,14 @@ def lib():
     L.dg_mhd_remap.argtypes = [vp, vp, vp, vp, dp, vp, dp, vp]
     L.dg_mhd_regrid_plan_mesh.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, vp, ctypes.c_int64, vp, vp, vp, i64p]
     L.dg_mhd_sibling_groups.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_int64, vp, i64p]
-    L.dg_mhd_octree_faces.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_int64, vp, vp, vp, i64p]
+    L.dg_mhd_octree_faces.argtypes = [ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_int, ctypes.c_int64, vp, vp, vp,
+                                      i64p]
     ip = ctypes.POINTER(ctypes.c_int)
     L.dg_mhd_regrid_tables.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp, vp]
     L.dg_mhd_basis_values.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp, ctypes.c_int64, vp,
                                       ip, ip]
+    L.dg_mhd_probe.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double), vp]
     L.dg_mhd_destroy.argtypes = [vp]
     L.dg_mhd_destroy.restype = None
     L.dg_mhd_strerror.argtypes = [ctypes.c_int]
@@ -193,6 +201,24 @@ def rhs_noalloc(dim, n, degree, divb, w, out, gamma=5.0 / 3.0, box_len=1.0, c_h=
     _check(lib().dg_mhd_rhs_noalloc(ctypes.byref(m), degree, scheme, gamma, None, c_h, damping_rate, _ptr(w),
                                     _ptr(out), _ptr(status) if status is not None else None, _stream()),
            "dg_mhd_rhs_noalloc")
+
+
+PROBE_FP32_FMA, PROBE_FP64_FMA, PROBE_TF32_MMA, PROBE_COPY = range(4)
+
+
+def probe(kind, nbytes=1 << 30):
+    """dg_mhd_probe: (rate, ms) of one timed launch on the current device; rate in
+    flop/s (FMA and MMA kinds) or bytes/s read plus written (copy: two device
+    buffers of nbytes are allocated here)."""
+    import torch
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    src = dst = None
+    if kind == PROBE_COPY:
+        src = torch.ones(nbytes // 4, dtype=torch.float32, device="cuda")
+        dst = torch.empty_like(src)
+    _check(lib().dg_mhd_probe(kind, _ptr(src), _ptr(dst), nbytes if kind == PROBE_COPY else 0, ctypes.byref(rate),
+                              ctypes.byref(ms), _stream()), "dg_mhd_probe")
+    return rate.value, ms.value
 
 
 def _leaf_arrays(levels, ijk):
@@ -310,17 +336,19 @@ def regrid_tables(dim, degree, divb):
     return out
 
 
-def octree_faces(levels, ijk):
+def octree_faces(levels, ijk, partial=False):
     """Faces of an octree mesh as a context builds them (host, no GPU): int32
-    arrays left cell, right cell, meta (axis | kind << 2 | sub << 4)."""
+    arrays left cell, right cell, meta (axis | kind << 2 | sub << 4). partial:
+    a partition's local mesh (faces with no leaf across them left out)."""
     import numpy as np
     lev, k = _leaf_arrays(levels, ijk)
     dim, n, nf = k.shape[1], lev.shape[0], ctypes.c_int64()
-    _check(lib().dg_mhd_octree_faces(dim, n, lev.ctypes.data, k.ctypes.data, 0, None, None, None, ctypes.byref(nf)),
-           "dg_mhd_octree_faces")
-    out = [np.zeros(nf.value, dtype=np.int32) for _ in range(3)]
-    _check(lib().dg_mhd_octree_faces(dim, n, lev.ctypes.data, k.ctypes.data, nf.value, *(o.ctypes.data for o in out),
+    pf = 1 if partial else 0
+    _check(lib().dg_mhd_octree_faces(dim, n, lev.ctypes.data, k.ctypes.data, pf, 0, None, None, None,
                                      ctypes.byref(nf)), "dg_mhd_octree_faces")
+    out = [np.zeros(nf.value, dtype=np.int32) for _ in range(3)]
+    _check(lib().dg_mhd_octree_faces(dim, n, lev.ctypes.data, k.ctypes.data, pf, nf.value,
+                                     *(o.ctypes.data for o in out), ctypes.byref(nf)), "dg_mhd_octree_faces")
     return tuple(out)
 
 
@@ -376,7 +404,7 @@ class Solver:
     the layout reported by dg_mhd_state_layout: w[row][cell_stride]."""
 
     def __init__(self, dim, n, degree, divb, gamma=5.0 / 3.0, box_len=1.0, leaves=None, levels=None, ijk=None,
-                 **params):
+                 partial=False, **params):
         """n: cells per axis of a uniform box, or None with `leaves` =
         [(level, (i, j[, k]))] for an octree mesh of a cube of side box_len."""
         import numpy as np
@@ -399,6 +427,7 @@ class Solver:
             m.n_leaves = len(self._lev)
             m.level = self._lev.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
             m.ijk = self._ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            m.partial = 1 if partial else 0
         self.params = default_params(**params)
         self.divb = divb
         h = ctypes.c_void_p()
@@ -476,6 +505,19 @@ class Solver:
             out = torch.zeros(1, dtype=torch.float64, device=w.device)
         _check(lib().dg_mhd_dt(self.h, _ptr(w), _ptr(wmean), _ptr(out), _stream()), "dg_mhd_dt")
         return out
+
+    def stage(self, w, wmean, u0, u0mean, out, outmean, a, b):
+        """out = a u0 + b (w + dt L(w)) with the context's current dt (dg_mhd_stage)."""
+        _check(lib().dg_mhd_stage(self.h, _ptr(w), _ptr(wmean), _ptr(u0), _ptr(u0mean), _ptr(out), _ptr(outmean),
+                                  a, b, _stream()), "dg_mhd_stage")
+
+    def set_dt(self, dt):
+        """dt (and the GLM speeds) from a one-element CUDA float64 tensor."""
+        _check(lib().dg_mhd_set_dt(self.h, _ptr(dt), _stream()), "dg_mhd_set_dt")
+
+    def set_owned(self, mask):
+        """Cells that count in the timestep minimum (CUDA uint8 tensor of n_cells), or None."""
+        _check(lib().dg_mhd_set_owned(self.h, _ptr(mask), _stream()), "dg_mhd_set_owned")
 
     def step(self, w, wmean=None, dt=None):
         _check(lib().dg_mhd_step(self.h, _ptr(w), _ptr(wmean), _ptr(dt), _stream()), "dg_mhd_step")

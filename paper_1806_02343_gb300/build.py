@@ -16,7 +16,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # reciprocal square root and square root (FP64 code is unaffected)
 FAST_MATH = {"dg_fast_f1.cu", "dg_fast_f2.cu", "dg_fast_d1.cu", "dg_fast_d2.cu"}
 SOURCES = ["dg_api.cu", "dg_kernels.cu", "dg_fast_f1.cu", "dg_fast_f2.cu", "dg_fast_d1.cu", "dg_fast_d2.cu",
-           "dg_cell_tc.cu", "dg_limit.cu", "dg_mlp.cu", "dg_amr.cu", "dg_noalloc.cu", "dg_regrid.cu", "dg_plan.cpp", "dg_basis.cpp"]
+           "dg_cell_tc.cu", "dg_limit.cu", "dg_mlp.cu", "dg_amr.cu", "dg_noalloc.cu", "dg_probe.cu", "dg_regrid.cu", "dg_plan.cpp", "dg_basis.cpp"]
 
 
 def _nvcc():

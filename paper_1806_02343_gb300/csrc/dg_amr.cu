@@ -387,7 +387,7 @@ __global__ void k_dt_list(Geom g, Tables<T> tb, AmrDev<T> am, const T* __restric
                           DevScalars* __restrict__ sc) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double dtc = DBL_MAX, smax = 0.0;
-  if (c < g.ncell) {
+  if (c < g.ncell && (!g.owned || g.owned[c])) {
     const int64_t S = g.stride;
     auto mean = [&](int m) { return wmean ? wmean[m * S + c] : (double)w[(int64_t)mrow_a(g, m) * S + c]; };
     const double rho = mean(0);
@@ -471,8 +471,10 @@ int build_amr(Ctx& c, const dg_mesh_desc* mesh) {
   MortonIndex mi;
   std::vector<int32_t> fL, fR, fmeta, cstart, centry;
   int maxent = 0;
-  const int ef = octree_faces(D, N, mesh->level, mesh->ijk, mi, fL, fR, fmeta, cstart, centry, maxent);
+  const int ef =
+      octree_faces(D, N, mesh->level, mesh->ijk, mi, fL, fR, fmeta, cstart, centry, maxent, mesh->partial != 0);
   if (ef) return ef;
+  c.amr.partial = mesh->partial != 0;
   const int64_t nf = (int64_t)fL.size();
   std::vector<double> dxc(N);
   for (int64_t cidx = 0; cidx < N; ++cidx) dxc[cidx] = mesh->box_len / (double)(1ll << mesh->level[cidx]);

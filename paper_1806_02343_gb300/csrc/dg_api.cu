@@ -447,7 +447,7 @@ void dg_mhd_destroy(dg_mhd_ctx* ctx) {
   void* ptrs[] = {c.sc, c.face_buf, c.face_buf32, c.stage_buf[0], c.stage_buf[1], c.stage_buf[2],
                   c.stage_mean[0], c.stage_mean[1], c.stage_mean[2], c.cellscratch, c.proj_tab, c.proj_w,
                   c.troubled, c.flag_list, c.pos_list, c.mlp_w1, c.mlp_w2, c.mlp_bias, c.rg_tabs, c.qdag_buf,
-                  c.tc_tabs};
+                  c.tc_tabs, c.owned};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c.hb;
@@ -465,6 +465,7 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
   if (!(gamma > 1.0)) return DG_E_ARG;
   const bool octree = mesh->level != nullptr;
   if (octree && !mesh->ijk) return DG_E_MESH;
+  if (mesh->partial != 0 && (mesh->partial != 1 || !octree)) return DG_E_ARG;
   if (!octree)
     for (int a = 0; a < mesh->dim; ++a)
       if (mesh->n[a] < 1) return DG_E_MESH;
@@ -784,6 +785,44 @@ int dg_mhd_rhs(dg_mhd_ctx* ctx, const void* w, const double* wmean, void* rhs, d
   Ctx& c = ctx->c;
   if (fp32(c) && (!wmean || !rhs_mean)) return DG_E_ARG;
   return operator_pass(c, w, wmean, rhs, rhs_mean, nullptr, nullptr, 0.0, 1.0, 0, S(stream));
+}
+
+int dg_mhd_stage(dg_mhd_ctx* ctx, const void* w, const double* wmean, const void* u0, const double* u0mean,
+                 void* out, double* outmean, double a, double b, void* stream) {
+  if (!ctx || !w || !out || !std::isfinite(a) || !std::isfinite(b)) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  if (!u0) {
+    if (a != 0.0) return DG_E_ARG;
+    u0 = w;  // read but weighted by zero
+    u0mean = wmean;
+  }
+  if (fp32(c) && (!wmean || !outmean || !u0mean)) return DG_E_ARG;
+  return operator_pass(c, w, wmean, out, outmean, u0, u0mean, a, b, 1, S(stream));
+}
+
+int dg_mhd_set_dt(dg_mhd_ctx* ctx, const double* dt_dev, void* stream) {
+  if (!ctx || !dt_dev) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  c.prof.launches[2] += 1;
+  launch_dt_from_value(c.g, c.p, dt_dev, c.sc, S(stream));
+  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
+}
+
+int dg_mhd_set_owned(dg_mhd_ctx* ctx, const uint8_t* mask, void* stream) {
+  if (!ctx) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  if (!mask) {
+    c.g.owned = nullptr;
+    return DG_OK;
+  }
+  if (!c.owned && cudaMalloc(&c.owned, (size_t)c.g.ncell) != cudaSuccess) {
+    c.owned = nullptr;
+    return DG_E_CUDA;
+  }
+  if (cudaMemcpyAsync(c.owned, mask, (size_t)c.g.ncell, cudaMemcpyDeviceToDevice, S(stream)) != cudaSuccess)
+    return DG_E_CUDA;
+  c.g.owned = c.owned;
+  return DG_OK;
 }
 
 int dg_mhd_limit(dg_mhd_ctx* ctx, void* w, double* wmean, uint8_t* troubled, void* stream) {

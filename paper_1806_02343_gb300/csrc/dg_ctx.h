@@ -55,6 +55,8 @@ struct Geom {
   int nx, ny, nz;         // cells per axis (nz = 1 in 2D)
   int64_t ncell, stride;  // cells and row stride
   double dx, gamma;
+  // cells that count in the timestep minimum (a partition's owned cells; NULL: all)
+  const uint8_t* owned = nullptr;
 };
 
 // Sizes fixed at compile time (3D, degree DEG >= 0, GLM or Powell): the
@@ -181,6 +183,7 @@ struct MlpTabs {
 // Octree mesh data owned by a context (device arrays; see dg_amr.cuh).
 struct AmrHost {
   bool on = false;
+  bool partial = false;  // a partition's local mesh (no regridding)
   int64_t nface = 0;
   int maxent = 0, nsub = 0;
   int32_t *fL = nullptr, *fR = nullptr, *fmeta = nullptr, *cstart = nullptr, *centry = nullptr;
@@ -242,6 +245,7 @@ struct Ctx {
   int fast = 0;                    // specialised GLM path: 10*prec + degree, 0 = none
   void* fast_tabs = nullptr;       // host FastAll<T, DEG> (kernel parameters)
   float* tc_tabs = nullptr;        // device operand tables of the tensor-core cell kernel (FP32, degree 2)
+  uint8_t* owned = nullptr;        // device copy of the owned-cell mask (dg_mhd_set_owned), or NULL
 };
 
 }  // namespace dgmhd

@@ -607,7 +607,7 @@ __global__ void k_dt(Geom g, Tables<T> tb, const T* __restrict__ w, const double
                      const T* __restrict__ jbuf, dg_mhd_params p, DevScalars* __restrict__ sc) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double dtc = DBL_MAX, smax = 0.0;
-  if (c < g.ncell) dtc = dt_cell64(g, tb, w, wmean, jbuf, p, sc, c, &smax);
+  if (c < g.ncell && (!g.owned || g.owned[c])) dtc = dt_cell64(g, tb, w, wmean, jbuf, p, sc, c, &smax);
   // block reduction then one atomic per block
   __shared__ double red[256];
   __shared__ double reds[256];
@@ -632,9 +632,19 @@ __global__ void k_dt(Geom g, Tables<T> tb, const T* __restrict__ w, const double
 // with the FP64 means used where the FP32 pressure would lose its digits to
 // the cancellation E - kinetic - magnetic. *smax as in dt_cell64. Returns
 // FLT_MAX where the bound is not a positive finite number (status bit 1).
+// Uniform FP32 constants of the screen, computed once on the host (an FP64
+// division per thread costs dozens of FP64 instructions on this GPU).
+struct Dt32Const {
+  float idx;      // 1 / dx
+  float cflfac;   // C / (2 d + 1)
+  float gam;      // gamma
+  float eta;      // eta of eq. powell_dt
+  float invD;     // 1 / D
+};
+
 __device__ float dt_cell32(const Geom& g, const Tables<float>& tb, const float* __restrict__ w,
-                           const double* __restrict__ wmean, const float* __restrict__ jbuf,
-                           const dg_mhd_params& p, DevScalars* __restrict__ sc, int64_t c, float* smax) {
+                           const double* __restrict__ wmean, const float* __restrict__ jbuf, const Dt32Const& k,
+                           DevScalars* __restrict__ sc, int64_t c, float* smax) {
   const int64_t S = g.stride;
   auto mean = [&](int m) { return w[(int64_t)mean_row(g, m) * S + c]; };
   const float rho = mean(0), ir = 1.f / rho;
@@ -649,7 +659,7 @@ __device__ float dt_cell32(const Geom& g, const Tables<float>& tb, const float* 
       for (int cc = 0; cc < g.DB; ++cc) b[cc] += mean(5 + j) * tb.L0[j * g.DB + cc];
     if (g.bz2d >= 0) b[2] = mean(7);
   }
-  const float gam = (float)g.gamma;
+  const float gam = k.gam;
   const float b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
   const float kin = 0.5f * rho * (vx * vx + vy * vy + vz * vz);
   float pr = (gam - 1.f) * (E - kin - 0.5f * b2);
@@ -674,10 +684,10 @@ __device__ float dt_cell32(const Geom& g, const Tables<float>& tb, const float* 
   const float av[3] = {fabsf(vx), fabsf(vy), fabsf(vz)};
   float sum = 0.f;
   for (int a = 0; a < g.D; ++a) sum += av[a] + cs;
-  const float idx = (float)(1.0 / g.dx);
+  const float idx = k.idx;
   const float s = sum * idx;
-  float dtc = (float)(p.cfl / (2.0 * g.d + 1.0)) / s;
-  *smax = sum / (float)g.D;
+  float dtc = k.cflfac / s;
+  *smax = sum * k.invD;
   if (!g.glm) {
     // (1/V_K) oint |B^n_F - B^n_K| dS: this cell's 2D faces in fixed order
     float acc = 0.f;
@@ -691,7 +701,7 @@ __device__ float dt_cell32(const Geom& g, const Tables<float>& tb, const float* 
     // face measure (dx/2)^(D-1) over the volume dx^D: 2^(1-D) / dx
     const float divb = acc * (g.D == 3 ? 0.25f : 0.5f) * idx;
     const float rate = divb * fabsf(vx * b[0] + vy * b[1] + vz * b[2]) / E;
-    if (rate > 0.f) dtc = fminf(dtc, (float)p.eta_powell / rate);
+    if (rate > 0.f) dtc = fminf(dtc, k.eta / rate);
   }
   if (!(dtc > 0.f) || !isfinite(dtc)) {
     atomicOr(&sc->status, 1);
@@ -700,17 +710,36 @@ __device__ float dt_cell32(const Geom& g, const Tables<float>& tb, const float* 
   return dtc;
 }
 
+// block minimum of a and maximum of b (256 threads), written by thread 0
+__device__ __forceinline__ void block_minmax256(unsigned& a, unsigned& b) {
+  __shared__ unsigned ra[8], rb[8];
+  a = __reduce_min_sync(0xffffffffu, a);
+  b = __reduce_max_sync(0xffffffffu, b);
+  const int wi = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    ra[wi] = a;
+    rb[wi] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    a = threadIdx.x < 8 ? ra[threadIdx.x] : 0xffffffffu;
+    b = threadIdx.x < 8 ? rb[threadIdx.x] : 0u;
+    a = __reduce_min_sync(0xffffffffu, a);
+    b = __reduce_max_sync(0xffffffffu, b);
+  }
+}
+
 // Pass 1 of the FP32 form's timestep: the FP32 bound of every cell, its
 // minimum m32 (warp minimum, one atomic per warp) and the signal-speed maximum.
 __global__ void k_dt32(Geom g, Tables<float> tb, const float* __restrict__ w, const double* __restrict__ wmean,
-                       const float* __restrict__ jbuf, dg_mhd_params p, DevScalars* __restrict__ sc) {
+                       const float* __restrict__ jbuf, Dt32Const k, DevScalars* __restrict__ sc) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float dtc = FLT_MAX, smax = 0.f;
-  if (c < g.ncell) dtc = dt_cell32(g, tb, w, wmean, jbuf, p, sc, c, &smax);
-  // positive floats order as their bit patterns
-  const unsigned mn = __reduce_min_sync(0xffffffffu, __float_as_uint(dtc));
-  const unsigned mxs = __reduce_max_sync(0xffffffffu, __float_as_uint(smax));
-  if ((threadIdx.x & 31) == 0) {
+  if (c < g.ncell && (!g.owned || g.owned[c])) dtc = dt_cell32(g, tb, w, wmean, jbuf, k, sc, c, &smax);
+  // positive floats order as their bit patterns: block reduction, one atomic per block
+  unsigned mn = __float_as_uint(dtc), mxs = __float_as_uint(smax);
+  block_minmax256(mn, mxs);
+  if (threadIdx.x == 0) {
     const float dm = __uint_as_float(mn);
     if (dm < FLT_MAX) atomicMin(&sc->dt_bits, dbits((double)dm));
     atomicMax(&sc->smax_bits, dbits((double)__uint_as_float(mxs)));
@@ -726,15 +755,17 @@ __global__ void k_dt32(Geom g, Tables<float> tb, const float* __restrict__ w, co
 // recomputed in FP64 and min-reduced into dt64_bits.
 constexpr float kDtScreen = 1e-3f;
 __global__ void k_dt32_refine(Geom g, Tables<float> tb, const float* __restrict__ w,
-                              const double* __restrict__ wmean, const float* __restrict__ jbuf, dg_mhd_params p,
-                              DevScalars* __restrict__ sc) {
+                              const double* __restrict__ wmean, const float* __restrict__ jbuf, Dt32Const k,
+                              dg_mhd_params p, DevScalars* __restrict__ sc) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double dtc = DBL_MAX;
-  if (c < g.ncell) {
+  if (c < g.ncell && (!g.owned || g.owned[c])) {
+    // m32 is a float value (the FP32 pass's minimum); the screen compares in FP32
     const double m32 = __longlong_as_double((long long)sc->dt_bits);
+    const float thr = m32 < DBL_MAX ? (float)m32 * (1.f + kDtScreen) : -1.f;
     float sm32;
-    const float d32 = dt_cell32(g, tb, w, wmean, jbuf, p, sc, c, &sm32);
-    if (m32 < DBL_MAX && (double)d32 <= m32 * (1.0 + (double)kDtScreen)) {
+    const float d32 = dt_cell32(g, tb, w, wmean, jbuf, k, sc, c, &sm32);
+    if (d32 <= thr) {
       double sm64;
       dtc = dt_cell64<float>(g, tb, w, wmean, jbuf, p, sc, c, &sm64);
     }
@@ -872,8 +903,14 @@ void launch_dt(const Geom& g, const Tables<T>& tb, const T* w, const double* wme
   k_dt_init<<<1, 1, 0, st>>>(sc);
   if constexpr (sizeof(T) == 4) {
     if (wmean) {
-      k_dt32<<<nblocks(g.ncell, 256), 256, 0, st>>>(g, tb, w, wmean, jbuf, p, sc);
-      k_dt32_refine<<<nblocks(g.ncell, 256), 256, 0, st>>>(g, tb, w, wmean, jbuf, p, sc);
+      Dt32Const k;
+      k.idx = (float)(1.0 / g.dx);
+      k.cflfac = (float)(p.cfl / (2.0 * g.d + 1.0));
+      k.gam = (float)g.gamma;
+      k.eta = (float)p.eta_powell;
+      k.invD = 1.f / (float)g.D;
+      k_dt32<<<nblocks(g.ncell, 256), 256, 0, st>>>(g, tb, w, wmean, jbuf, k, sc);
+      k_dt32_refine<<<nblocks(g.ncell, 256), 256, 0, st>>>(g, tb, w, wmean, jbuf, k, p, sc);
       k_dt_finalize<<<1, 1, 0, st>>>(g, p, sc, nullptr, dt_out);
       return;
     }

@@ -90,7 +90,7 @@ inline uint64_t leaf_key(int l, const int32_t* k, int D) {
 
 }  // namespace
 
-int morton_index(int D, int64_t N, const int8_t* level, const int32_t* ijk, MortonIndex& mi) {
+int morton_index(int D, int64_t N, const int8_t* level, const int32_t* ijk, MortonIndex& mi, bool partial) {
   if ((D != 2 && D != 3) || N < 1 || N > ((int64_t)1 << 30) || !level || !ijk) return DG_E_ARG;
   mi = MortonIndex{};
   mi.D = D;
@@ -132,10 +132,10 @@ int morton_index(int D, int64_t N, const int8_t* level, const int32_t* ijk, Mort
   // ends at 2^(D R)
   uint64_t next = 0;
   for (int64_t p = 0; p < N; ++p) {
-    if (mi.start[p] != next) return DG_E_MESH;
-    next += 1ull << (D * (mi.R - mi.lev[p]));
+    if (partial ? mi.start[p] < next : mi.start[p] != next) return DG_E_MESH;  // overlap (or a hole)
+    next = mi.start[p] + (1ull << (D * (mi.R - mi.lev[p])));
   }
-  if (next != 1ull << (D * mi.R)) return DG_E_MESH;
+  if (!partial && next != 1ull << (D * mi.R)) return DG_E_MESH;
   return DG_OK;
 }
 
@@ -166,9 +166,13 @@ bool mesh_balanced(const MortonIndex& mi, const int32_t* ijk) {
 
 int octree_faces(int D, int64_t N, const int8_t* level, const int32_t* ijk, MortonIndex& mi,
                  std::vector<int32_t>& fL, std::vector<int32_t>& fR, std::vector<int32_t>& fmeta,
-                 std::vector<int32_t>& cstart, std::vector<int32_t>& centry, int& maxent) {
+                 std::vector<int32_t>& cstart, std::vector<int32_t>& centry, int& maxent, bool partial) {
   if (N < 1 || N > ((int64_t)1 << 30)) return DG_E_MESH;
-  if (morton_index(D, N, level, ijk, mi) != DG_OK) return DG_E_MESH;
+  if (morton_index(D, N, level, ijk, mi, partial) != DG_OK) return DG_E_MESH;
+  // the leaf at Morton position q holds the code (always, on a full mesh)
+  auto holds = [&](int64_t q, uint64_t code) {
+    return mi.start[q] <= code && code - mi.start[q] < (1ull << (D * (mi.R - mi.lev[q])));
+  };
   fL.clear();
   fR.clear();
   fmeta.clear();
@@ -188,6 +192,12 @@ int octree_faces(int D, int64_t N, const int8_t* level, const int32_t* ijk, Mort
     const int64_t first = p - oct;
     bool group = l > 0 && first >= 0 && first + (1 << D) <= N;
     for (int o = 0; o < (1 << D) && group; ++o) group = mi.lev[first + o] == l;
+    if (partial && group) {
+      // on a partial mesh, a run of same-level leaves need not be the siblings
+      const uint64_t span = 1ull << (D * (mi.R - l));
+      for (int o = 0; o < (1 << D) && group; ++o)
+        group = mi.start[first + o] == mi.start[p] - (uint64_t)oct * span + (uint64_t)o * span;
+    }
     for (int a = 0; a < D; ++a) {
       int others[2], no = 0;
       for (int b = 0; b < D; ++b)
@@ -200,7 +210,9 @@ int octree_faces(int D, int64_t N, const int8_t* level, const int32_t* ijk, Mort
           // the leaf holding the corner of the same-level neighbour cube
           int32_t nk[3] = {k[0], k[1], D == 3 ? k[2] : 0};
           nk[a] = (nk[a] + s + n) % n;
-          q = locate(mi.start, morton(D, mi.R, l, nk), p);
+          const uint64_t code = morton(D, mi.R, l, nk);
+          q = locate(mi.start, code, p);
+          if (partial && !holds(q, code)) continue;  // no leaf there: a face of a ghost cell
         }
         const int lq = mi.lev[q];
         if (lq == l) {  // same level: listed once, by the right cell
@@ -226,6 +238,7 @@ int octree_faces(int D, int64_t N, const int8_t* level, const int32_t* ijk, Mort
           continue;
         }
         if (lq < l - 1) return DG_E_MESH;  // two levels coarser
+        if (partial) continue;             // finer neighbours list the faces they have
         // split neighbour: its children along the face must be leaves (2:1)
         int32_t nk[3] = {k[0], k[1], D == 3 ? k[2] : 0};
         nk[a] = (nk[a] + s + n) % n;
@@ -494,14 +507,16 @@ extern "C" int dg_mhd_regrid_plan_mesh(int dim, int64_t n, const int8_t* level, 
   return DG_OK;
 }
 
-extern "C" int dg_mhd_octree_faces(int dim, int64_t n, const int8_t* level, const int32_t* ijk, int64_t cap,
-                                   int32_t* face_left, int32_t* face_right, int32_t* face_meta, int64_t* n_faces) {
+extern "C" int dg_mhd_octree_faces(int dim, int64_t n, const int8_t* level, const int32_t* ijk, int partial,
+                                   int64_t cap, int32_t* face_left, int32_t* face_right, int32_t* face_meta,
+                                   int64_t* n_faces) {
   if (!n_faces || !level || !ijk) return DG_E_ARG;
   if (dim != 2 && dim != 3) return DG_E_ARG;
+  if (partial != 0 && partial != 1) return DG_E_ARG;
   dgmhd::MortonIndex mi;
   std::vector<int32_t> fL, fR, fmeta, cstart, centry;
   int maxent = 0;
-  const int e = dgmhd::octree_faces(dim, n, level, ijk, mi, fL, fR, fmeta, cstart, centry, maxent);
+  const int e = dgmhd::octree_faces(dim, n, level, ijk, mi, fL, fR, fmeta, cstart, centry, maxent, partial != 0);
   if (e) return e;
   const int64_t nf = (int64_t)fL.size();
   *n_faces = nf;

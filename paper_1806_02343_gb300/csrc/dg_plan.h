@@ -28,7 +28,9 @@ struct MortonIndex {
 
 // Levels in [0, 17], coordinates in [0, 2^level), the leaves tiling the unit
 // cube without overlap: DG_OK, else DG_E_MESH (DG_E_ARG for a bad dim / count).
-int morton_index(int D, int64_t N, const int8_t* level, const int32_t* ijk, MortonIndex& mi);
+// partial: the leaves need not cover the cube (a partition's owned and ghost
+// leaves); they still must not overlap.
+int morton_index(int D, int64_t N, const int8_t* level, const int32_t* ijk, MortonIndex& mi, bool partial = false);
 
 // No two face neighbours differ by more than one level (periodic box).
 bool mesh_balanced(const MortonIndex& mi, const int32_t* ijk);
@@ -42,9 +44,12 @@ bool mesh_balanced(const MortonIndex& mi, const int32_t* ijk);
 // << 2 | sub-face << 4, side 1 when the coarse cell is on the left, 2 when on
 // the right; sub-face = the fine cell's octant bits across the face). cstart /
 // centry: per cell its face entries (2 f + (cell is fR)) in face order.
+// partial: a partition's local mesh; a face whose neighbour region holds no
+// leaf is left out (only ghost cells, whose results are discarded, have such
+// faces), and the 2:1 checks apply to the leaves present.
 int octree_faces(int D, int64_t N, const int8_t* level, const int32_t* ijk, MortonIndex& mi,
                  std::vector<int32_t>& fL, std::vector<int32_t>& fR, std::vector<int32_t>& fmeta,
-                 std::vector<int32_t>& cstart, std::vector<int32_t>& centry, int& maxent);
+                 std::vector<int32_t>& cstart, std::vector<int32_t>& centry, int& maxent, bool partial = false);
 
 // Groups of 2^D sibling leaves (the children of one cube, all leaves), sorted by
 // (parent level, parent coordinates); groups[g * 2^D + o] = leaf index of octant o.

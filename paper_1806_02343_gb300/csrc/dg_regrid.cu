@@ -439,7 +439,7 @@ extern "C" int dg_mhd_amr_marks(dg_mhd_ctx* ctx, const void* w, const double* wm
                                 int min_level, int max_level, int8_t* marks, double* s_max, void* stream) {
   if (!ctx || !w || !marks || !s_max || !(s_tilde > 0.0)) return DG_E_ARG;
   Ctx& c = ctx->c;
-  if (!c.amr.on) return DG_E_UNSUPPORTED;
+  if (!c.amr.on || c.amr.partial) return DG_E_UNSUPPORTED;
   int e = dg_mhd_smoothness(ctx, w, wmean, field_mask, s_max, stream);
   if (e) return e;
   if ((e = ensure_groups(c))) return e;
@@ -467,7 +467,7 @@ extern "C" int dg_mhd_remap(const dg_mhd_ctx* old_ctx, dg_mhd_ctx* new_ctx, cons
   Ctx& cn = new_ctx->c;
   const Geom &go = co.g, &gn = cn.g;
   if (go.D != gn.D || go.d != gn.d || go.glm != gn.glm || go.nrows != gn.nrows ||
-      co.p.precision != cn.p.precision || !co.amr.on)
+      co.p.precision != cn.p.precision || !co.amr.on || co.amr.partial || cn.amr.partial)
     return DG_E_ARG;
   if ((wmean_old == nullptr) != (wmean_new == nullptr)) return DG_E_ARG;
   int e = ensure_groups(co);
@@ -494,7 +494,7 @@ extern "C" int dg_mhd_regrid_plan(const dg_mhd_ctx* ctx, const int8_t* marks, in
                                   int32_t* new_ijk, int32_t* src, int64_t* n_new) {
   if (!ctx || !marks || !n_new) return DG_E_ARG;
   Ctx& c = const_cast<Ctx&>(ctx->c);
-  if (!c.amr.on) return DG_E_UNSUPPORTED;
+  if (!c.amr.on || c.amr.partial) return DG_E_UNSUPPORTED;
   int e = ensure_groups(c);
   if (e) return e;
   AmrHost& h = c.amr;

@@ -121,9 +121,10 @@ def test_host_entry_points_reject_null_arguments(lib):
                                        ctypes.byref(n)) == -1                     # capacity 3 < 4
     assert lib.dg_mhd_sibling_groups(2, 4, lp, kp, 0, None, None) == -1
     assert lib.dg_mhd_sibling_groups(2, 4, lp, kp, 0, None, ctypes.byref(n)) == 0 and n.value == 1
-    assert lib.dg_mhd_octree_faces(2, 4, None, kp, 0, None, None, None, ctypes.byref(n)) == -1
-    assert lib.dg_mhd_octree_faces(2, 4, lp, kp, 0, None, None, None, None) == -1
-    assert lib.dg_mhd_octree_faces(2, 4, lp, kp, 0, None, None, None, ctypes.byref(n)) == 0 and n.value == 8
+    assert lib.dg_mhd_octree_faces(2, 4, None, kp, 0, 0, None, None, None, ctypes.byref(n)) == -1
+    assert lib.dg_mhd_octree_faces(2, 4, lp, kp, 0, 0, None, None, None, None) == -1
+    assert lib.dg_mhd_octree_faces(2, 4, lp, kp, 2, 0, None, None, None, ctypes.byref(n)) == -1
+    assert lib.dg_mhd_octree_faces(2, 4, lp, kp, 0, 0, None, None, None, ctypes.byref(n)) == 0 and n.value == 8
     r, v = ctypes.c_int(), ctypes.c_int()
     assert lib.dg_mhd_basis_values(3, 2, 1, 1, None, 0, None, ctypes.byref(r), ctypes.byref(v)) == -1
     assert lib.dg_mhd_basis_values(3, 2, 1, 0, None, 0, None, None, ctypes.byref(v)) == -1
@@ -151,3 +152,14 @@ def test_eps_hlld_and_noalloc_arguments_checked_on_host(lib):
     for ch, kap in ((0.0, 1.0), (float("nan"), 1.0), (1.0, -1.0)):
         assert lib.dg_mhd_rhs_noalloc(ctypes.byref(m), 2, 1, 5.0 / 3.0, None, ch, kap,
                                       ctypes.c_void_p(16), ctypes.c_void_p(16), None, None) == -1
+
+
+def test_probe_rejects_bad_arguments_on_host(lib):
+    import ctypes
+    r, m = ctypes.c_double(), ctypes.c_double()
+    assert lib.dg_mhd_probe(4, None, None, 0, ctypes.byref(r), ctypes.byref(m), None) == -1
+    assert lib.dg_mhd_probe(-1, None, None, 0, ctypes.byref(r), ctypes.byref(m), None) == -1
+    assert lib.dg_mhd_probe(3, None, None, 1 << 20, ctypes.byref(r), ctypes.byref(m), None) == -1
+    assert lib.dg_mhd_probe(3, ctypes.c_void_p(16), ctypes.c_void_p(32), 100, ctypes.byref(r), ctypes.byref(m),
+                            None) == -1
+    assert lib.dg_mhd_probe(0, None, None, 0, None, ctypes.byref(m), None) == -1

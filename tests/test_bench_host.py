@@ -91,3 +91,35 @@ def test_hbm_bytes_per_cell_of_the_stage():
     assert bench.stage_bytes_per_cell(90, 9) == pytest.approx(1056.0)
     assert bench.stage_bytes_per_cell(76, 8) == pytest.approx(896.0)
     assert bench.stage_bytes_per_cell(90, 9, fp32=False) == pytest.approx(1920.0)
+
+
+def test_state_l1_closed_form():
+    """L1 of eq. lp_norm between two DG states on CPU tensors: a state whose
+    density is 2 everywhere against one with density 2.5 + 0.25 xi_x (no sign
+    change of the difference): L1_rho = 0.5 / 2 exactly; m_x identical: 0."""
+    import numpy as np
+    import torch
+    from paper_1806_02343_gb300.binding import basis_values
+    d, ncell = 2, 40
+    g1, gw = np.polynomial.legendre.leggauss(d + 3)
+    pts = np.stack(np.meshgrid(g1, g1, g1, indexing="ij"), -1).reshape(-1, 3)
+    wq = np.einsum("i,j,k->ijk", gw, gw, gw).reshape(-1)
+    table = basis_values(3, d, "glm", pts)
+    rows = [10 * v for v in range(9)]
+    b = torch.zeros((90, 64), dtype=torch.float64)
+    b[0, :ncell] = 2.0
+    b[10, :ncell] = 1.0
+    a = b.clone()
+    a[0, :ncell] += 0.5
+    a[1, :ncell] = 0.25        # the first degree-1 Legendre mode (xi_x) of rho
+    l1 = bench.state_l1(table, a, None, rows, b, None, rows, ncell, wq, chunk=16)
+    assert l1[0] == pytest.approx(0.25, rel=1e-13)
+    assert l1[1] == 0.0 and all(x == 0.0 for x in l1[2:])
+
+
+def test_cpu_baseline_all_cores_runs_concurrent_copies():
+    cfg = dict(bench.CONFIGS["turb256"], name="turb256")
+    r = bench.cpu_baseline_all_cores(cfg, 4, limited=False, procs=2)
+    assert r["cores"] == 2 and r["value"] > 0 and r["kind"] == "oracle"
+    info = bench.host_info()
+    assert info["nproc"] >= 1
