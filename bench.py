@@ -402,6 +402,9 @@ def run_ours(args, cfg, rank, world, device):
     # ------------------------------------------------------------ one regrid step (octree workloads)
     if amr_mesh is not None:
         res["regrid"] = time_regrid(sol, w, wm, amr_mesh, D, d, divb, args, device)
+        if args.amr_steps > 0:
+            res["amr_evolution"] = amr_evolution(sol, w, wm, args)
+            torch.cuda.empty_cache()
 
     # ------------------------------------------------------------ end to end through the C ABI
     # host (pinned) state in, one step, state out
@@ -693,6 +696,39 @@ def stage_flops_per_cell(D, d, divb, nrows):
     return out
 
 
+def amr_evolution(sol, w, wm, args):
+    """The octree workload advanced with regridding inside the time loop (Sec. 5):
+    args.amr_steps SSP-RK3 steps, a regrid check every args.regrid_every steps
+    on rho and B. S~ is set from the state the evolution starts from: half the
+    95th percentile of the smoothness indicator, so that about 5% of the leaves
+    exceed 2 S~ (refine) while the smooth regions coarsen (the paper's S~ = 0.03
+    coarsens every group of this smooth start). Levels 4..8. Work on copies of
+    the state; the static-mesh solver is left as it was."""
+    import torch
+    from paper_1806_02343_gb300.evolve import evolve_amr
+    s = sol.smoothness(w, wm, (0, 5, 6, 7))
+    s_tilde = float(torch.quantile(s.float(), 0.95).item()) / 2.0
+    w1, wm1 = w.clone(), wm.clone() if wm is not None else None
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0.record(st)
+    sol2, w2, wm2, hist = evolve_amr(sol, w1, wm1, args.amr_steps, args.regrid_every, (0, 5, 6, 7), s_tilde, 4, 8,
+                                     sync_timing=True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    regrid_ms = sum(h.get("wall_ms", 0.0) for h in hist)
+    out = {"steps": args.amr_steps, "regrid_every": args.regrid_every, "s_tilde": s_tilde,
+           "s_tilde_rule": "half the 95th percentile of the start's smoothness indicator (rho, B)",
+           "levels": [4, 8], "history": hist, "cells_final": sol2.ncell, "wall_ms": wall * 1e3,
+           "device_ms": e0.elapsed_time(e1), "regrid_wall_ms": regrid_ms, "status": sol2.status(),
+           "finite": bool(torch.isfinite(wm2[:, : sol2.ncell] if wm2 is not None else w2[:, : sol2.ncell]).all())}
+    del sol2, w2, wm2, w1, wm1
+    return out
+
+
 def time_regrid(sol, w, wm, mesh, D, d, divb, args, device):
     """One regrid step of the octree state after the timed steps (Sec. 5):
     marks on rho and B with the paper's S~ = 0.03 (kernels, CUDA events), the
@@ -760,6 +796,9 @@ def main():
     ap.add_argument("--limiter", default=None, choices=["mlp", "tvb", "off"],
                     help="default: mlp (learned indicator); tvb on octree meshes")
     ap.add_argument("--threshold", type=float, default=0.1)
+    ap.add_argument("--amr-steps", type=int, default=None,
+                    help="octree workload: steps of the evolution with regridding (default: the configuration's)")
+    ap.add_argument("--regrid-every", type=int, default=10)
     args = ap.parse_args()
     cfg = dict(CONFIGS[args.config])
     cfg["name"] = args.config
@@ -767,6 +806,8 @@ def main():
         args.limiter = "tvb" if cfg.get("amr") else "mlp"
     if args.l1_steps is None:
         args.l1_steps = cfg.get("run_steps", 20)
+    if args.amr_steps is None:
+        args.amr_steps = cfg.get("run_steps", 50) if cfg.get("amr") else 0
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -834,7 +875,7 @@ def main():
         "fp32_plain_tvb": res.get("fp32_plain_tvb"), "fp32_learned_limiter": res.get("fp32_learned_limiter"),
         "indicator_quality": res.get("indicator_quality"), "probes": res.get("probes"),
         "dof": res["dof"],
-        "regrid": res.get("regrid"),
+        "regrid": res.get("regrid"), "amr_evolution": res.get("amr_evolution"),
         "alu": res.get("alu"),
         "kernel_path": ("octree face-list kernels (k_face_list, k_cell_list)" if cfg.get("amr") else
                         "specialised GLM 3D kernels (k_face_glm, k_cell_glm)" if cfg["divb"] == "glm" else

@@ -133,6 +133,12 @@ __device__ __forceinline__ void hlld(const Prim<T>& L, const Prim<T>& R, T bn, T
     return;
   }
   T FR[8], UR[8];
+  if (SR < T(0)) {  // the whole fan moves left of the face: the right state's flux
+    phys(R, ER, pTR, FR, UR);
+    for (int k = 0; k < 8; ++k) out[k] = FR[k];
+    set_state(R.u, R.v, R.w, R.by, R.bz);
+    return;
+  }
   phys(L, EL, pTL, FL, UL);
   phys(R, ER, pTR, FR, UR);
   const T dL = SL - L.u, dR = SR - R.u;

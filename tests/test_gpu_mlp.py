@@ -236,10 +236,50 @@ def test_staged_inference_and_gating(divb):
     expect = np.where(g[:, None], ref, w0)
     f = flags[: sol.ncell].cpu().numpy().astype(bool)
     # FP32 form against FP64 decisions: a trigger within rounding of the TVB
-    # bound may flip; every other cell matches
+    # bound may flip; every other cell matches, and every flipped cell has a
+    # decision quantity within FP32 rounding of its threshold
     same = f == (trig & g)
     assert same.mean() > 0.99
     assert rel_err(out[same], expect[same]) < 1e-5
+    assert _flip_within_rounding(S, w0, np.nonzero(~same)[0], 3.0).all()
+
+
+def _flip_within_rounding(S, w0, cells, ch, tau=1e-5):
+    """For each cell whose FP32 TVB decision differs from the FP64 oracle's:
+    True if FP32 rounding can decide it. The decision of a characteristic field
+    (Sec. 4.2.1-4.2.2) is "|c_x| > M~ dx and |minmod(c_x, beta c+, beta c-) -
+    c_x| > epsilon"; its three arguments are dot products with the left
+    eigenvectors, each known to delta = tau (sum |L_kj| |slope_j| + beta sum
+    |L_kj| (|D+_j| + |D-_j|)). The cell counts as within rounding if moving the
+    arguments by -delta, 0 or +delta changes the decision of some field."""
+    import itertools
+    from oracle.limiter import eigensystem, minmod3
+    Lim = Limiter(S, tvb=True, positivity=False)
+    P = S.P
+    m = S.means(w0)
+    sl = Lim.slopes(w0)
+    dpa, dma = Lim.mean_differences(m)
+    thr = P.Mtilde * S.dx
+
+    def decide(x, y, z):
+        return abs(x) > thr and abs(minmod3(x, y, z) - x) > P.tvb_eps
+
+    out = []
+    for c in cells:
+        near = False
+        for a in range(S.D):
+            R, L, _ = eigensystem(m[c], a, S.gamma, ch)
+            dp, dm = dpa[c, a], dma[c, a]
+            cx, cp, cm = L @ sl[c, a], L @ dp, L @ dm
+            delta = tau * (np.abs(L) @ np.abs(sl[c, a]) + P.beta * (np.abs(L) @ (np.abs(dp) + np.abs(dm))))
+            for k in range(S.V):
+                x, y, z, dl = cx[k], P.beta * cp[k], P.beta * cm[k], delta[k]
+                d0 = decide(x, y, z)
+                if any(decide(x + e1 * dl, y + e2 * dl, z + e3 * dl) != d0
+                       for e1, e2, e3 in itertools.product((-1, 0, 1), repeat=3)):
+                    near = True
+        out.append(near)
+    return np.array(out, dtype=bool)
 
 
 @pytest.mark.parametrize("divb", ["powell", "glm"])
@@ -283,5 +323,6 @@ def test_staged_gating_with_positivity(divb):
     f = flags[: sol.ncell].cpu().numpy().astype(bool)
     same = f == (trig & g)
     assert same.mean() > 0.99
+    assert _flip_within_rounding(S, w0, np.nonzero(~same)[0], 3.0).all()
     out = from_device(w, sol)
     assert rel_err(out[same], expect[same]) < 1e-5

@@ -192,3 +192,42 @@ def test_smoothness_on_a_uniform_mesh():
     sol = Solver(3, (6, 5, 4), 2, "powell", gamma=GAM, box_len=S.L)
     got = sol.smoothness(to_device(w0, sol), None, FIELDS).cpu().numpy()
     assert np.abs(got - ref).max() <= 1e-11 * ref.max()
+
+
+def test_regrid_cycles_in_the_time_loop_match_oracle():
+    """Regridding inside the time loop (paper_1806_02343_gb300/evolve.py): five
+    SSP-RK3 steps of the FP64 Powell scheme (degree 1) from the steep front on
+    a level-3 octree, regridding before steps 2 and 4 (marks on rho and B,
+    S~ = 0.03, levels 2..5), against the oracle doing the same with its own
+    marks, plan, remap and steps: the same leaves after every cycle, the state
+    to 1e-11, both refinements and coarsenings among the cycles."""
+    from paper_1806_02343_gb300.binding import Solver, DG_PREC_FP64
+    from paper_1806_02343_gb300.evolve import evolve_amr
+    leaves = _leaves(3)
+    d, s_tilde, lo, hi, steps, every = 1, 0.03, 2, 4, 5, 2
+    A = AMRScheme(3, d, "powell", GAM, leaves)
+    w0 = A.project(_front(A.V))
+    # oracle: the same loop
+    w, lv = w0.copy(), list(leaves)
+    n_ref = n_coarse = 0
+    meshes = []
+    for n in range(steps):
+        if n > 0 and n % every == 0:
+            refine, groups, coarsen = G.marks(A, lv, w, FIELDS, s_tilde, lo, hi)
+            n_ref += int(refine.sum())
+            n_coarse += len(coarsen)
+            items = G.plan(lv, 3, refine, groups, coarsen)
+            w = G.remap(A, w, groups, items)
+            lv = [key for key, _ in items]
+            A = AMRScheme(3, d, "powell", GAM, lv)
+            meshes.append(len(lv))
+        w, _ = A.step(w)
+    assert n_ref > 0 and n_coarse > 0
+    sol = Solver(3, None, d, "powell", gamma=GAM, box_len=1.0, leaves=leaves, precision=DG_PREC_FP64)
+    sol, wg, _, hist = evolve_amr(sol, to_device(w0, sol), None, steps, every, FIELDS, s_tilde, lo, hi)
+    assert [h["cells_after"] for h in hist] == meshes
+    assert sum(h["refined"] for h in hist) == n_ref and sum(h["coarsened_groups"] for h in hist) == n_coarse
+    got_leaves = [(int(l), tuple(int(x) for x in k)) for l, k in zip(sol._lev, sol._ijk.reshape(-1, 3))]
+    assert got_leaves == lv
+    assert rel_err(from_device(wg, sol), w) < 1e-11
+    assert sol.status(1) == 0
