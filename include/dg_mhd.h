@@ -193,6 +193,11 @@ int dg_mhd_stage(dg_mhd_ctx* ctx, const void* w, const double* wmean, const void
  * does with a given dt. Asynchronous on stream. */
 int dg_mhd_set_dt(dg_mhd_ctx* ctx, const double* dt_dev, void* stream);
 
+/* The context's current GLM cleaning speed c_h and damping rate (Sec. 4.1.5)
+ * into host doubles; synchronises the device. 0 until a timestep, dg_mhd_set_glm
+ * or dg_mhd_set_dt has set them (or c_h_fixed at init). */
+int dg_mhd_glm_speeds(dg_mhd_ctx* ctx, double* c_h, double* damping_rate);
+
 /* Cells that count in the timestep minimum of dg_mhd_dt (eq. cfl, eq.
  * powell_dt): mask (DEVICE, n_cells bytes, copied) holds 1 for the cells a
  * partition's rank owns, 0 for its ghost cells, whose face neighbours may be

@@ -29,7 +29,7 @@ EXPORTS = [
     "dg_mhd_mlp_train", "dg_mhd_counters", "dg_mhd_limiter_counts", "dg_mhd_divb", "dg_mhd_smoothness",
     "dg_mhd_amr_marks", "dg_mhd_regrid_plan", "dg_mhd_remap", "dg_mhd_regrid_plan_mesh",
     "dg_mhd_sibling_groups", "dg_mhd_octree_faces", "dg_mhd_basis_values", "dg_mhd_regrid_tables",
-    "dg_mhd_probe", "dg_mhd_stage", "dg_mhd_set_dt", "dg_mhd_set_owned",
+    "dg_mhd_probe", "dg_mhd_stage", "dg_mhd_set_dt", "dg_mhd_set_owned", "dg_mhd_glm_speeds",
 ]
 KIND_FACE, KIND_CELL, KIND_DT, KIND_LIMIT, KIND_PROJECT, KIND_POSITIVITY, KIND_MLP = range(7)
 
@@ -71,6 +71,7 @@ def lib():
     L.dg_mhd_stage.argtypes = [vp, vp, dp, vp, dp, vp, dp, ctypes.c_double, ctypes.c_double, vp]
     L.dg_mhd_set_dt.argtypes = [vp, dp, vp]
     L.dg_mhd_set_owned.argtypes = [vp, vp, vp]
+    L.dg_mhd_glm_speeds.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.dg_mhd_dt.argtypes = [vp, vp, dp, dp, vp]
     L.dg_mhd_step.argtypes = [vp, vp, dp, dp, vp]
     L.dg_mhd_last_dt.argtypes = [vp]
@@ -514,6 +515,12 @@ class Solver:
     def set_dt(self, dt):
         """dt (and the GLM speeds) from a one-element CUDA float64 tensor."""
         _check(lib().dg_mhd_set_dt(self.h, _ptr(dt), _stream()), "dg_mhd_set_dt")
+
+    def glm_speeds(self):
+        """(c_h, damping rate) of the context (host floats; synchronises)."""
+        ch, kap = ctypes.c_double(), ctypes.c_double()
+        _check(lib().dg_mhd_glm_speeds(self.h, ctypes.byref(ch), ctypes.byref(kap)), "dg_mhd_glm_speeds")
+        return ch.value, kap.value
 
     def set_owned(self, mask):
         """Cells that count in the timestep minimum (CUDA uint8 tensor of n_cells), or None."""

@@ -609,6 +609,7 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
   // initial GLM speeds: fixed c_h if given (damping from c_r), else set by dt
   if (g.glm && prm.c_h_fixed > 0.0) {
     launch_set_glm(c.sc, prm.c_h_fixed, prm.c_h_fixed / prm.c_r, nullptr);
+    c.glm_speeds_set = true;
   }
   if (cudaDeviceSynchronize() != cudaSuccess) {
     dg_mhd_destroy(ctx);
@@ -677,6 +678,7 @@ int dg_mhd_project(dg_mhd_ctx* ctx, const double* nodal, int npts, void* w, doub
 int dg_mhd_set_glm(dg_mhd_ctx* ctx, double c_h, double damping_rate, void* stream) {
   if (!ctx || !(c_h > 0.0) || !(damping_rate >= 0.0)) return DG_E_ARG;
   launch_set_glm(ctx->c.sc, c_h, damping_rate, S(stream));
+  ctx->c.glm_speeds_set = true;
   return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
 }
 
@@ -745,6 +747,7 @@ int operator_pass(Ctx& c, const void* w, const double* wmean, void* out, double*
 
 int dt_pass(Ctx& c, const void* w, const double* wmean, double* dt_out, cudaStream_t st) {
   const Geom& g = c.g;
+  if (g.glm) c.glm_speeds_set = true;  // the finalize kernel derives c_h and the damping from dt
   if (c.amr.on) {
     c.prof.begin(2, st);
     launch_dt_init(c.sc, st);
@@ -805,7 +808,18 @@ int dg_mhd_set_dt(dg_mhd_ctx* ctx, const double* dt_dev, void* stream) {
   Ctx& c = ctx->c;
   c.prof.launches[2] += 1;
   launch_dt_from_value(c.g, c.p, dt_dev, c.sc, S(stream));
+  c.glm_speeds_set = true;
   return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
+}
+
+int dg_mhd_glm_speeds(dg_mhd_ctx* ctx, double* c_h, double* damping_rate) {
+  if (!ctx || !c_h || !damping_rate) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  if (cudaDeviceSynchronize() != cudaSuccess) return DG_E_CUDA;
+  if (cudaMemcpy(c_h, &c.sc->ch, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(damping_rate, &c.sc->kappa, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DG_E_CUDA;
+  return DG_OK;
 }
 
 int dg_mhd_set_owned(dg_mhd_ctx* ctx, const uint8_t* mask, void* stream) {
@@ -854,9 +868,15 @@ int dg_mhd_step(dg_mhd_ctx* ctx, void* w, double* wmean, const double* dt_dev, v
     // the step's dt (and GLM c_h) first, so the limiter sees this step's c_h
     c.prof.launches[2] += 1;
     launch_dt_from_value(c.g, c.p, dt_dev, c.sc, st);
+    c.glm_speeds_set = true;
     if ((e = limit_pass(c, w, wmean, nullptr, st))) return e;
   } else {
-    // dt from the limited state; the limiter uses the c_h of the previous step
+    // dt from the limited state; the limiter uses the c_h of the previous
+    // step -- on a GLM context's first step, the c_h of the dt of the input
+    // state (the characteristic GLM pair needs c_h > 0)
+    if (c.g.glm && !c.glm_speeds_set && (c.p.limiter != DG_LIMIT_OFF || c.p.positivity) &&
+        (e = dt_pass(c, w, wmean, nullptr, st)))
+      return e;
     if ((e = limit_pass(c, w, wmean, nullptr, st))) return e;
     if ((e = dt_pass(c, w, wmean, nullptr, st))) return e;
   }

@@ -246,6 +246,7 @@ struct Ctx {
   void* fast_tabs = nullptr;       // host FastAll<T, DEG> (kernel parameters)
   float* tc_tabs = nullptr;        // device operand tables of the tensor-core cell kernel (FP32, degree 2)
   uint8_t* owned = nullptr;        // device copy of the owned-cell mask (dg_mhd_set_owned), or NULL
+  bool glm_speeds_set = false;     // GLM: c_h and the damping rate hold a value (from a dt, set_glm or set_dt)
 };
 
 }  // namespace dgmhd

@@ -116,13 +116,18 @@ struct GlobalSrc {
 };
 
 // features of one cell, written through put(k, value) for k in [0, nin)
-// part < 0: every feature; part 0 / 1: the two halves of the work (for two
-// threads per cell): part 0 writes the neighbour-density features and the
-// variables below `vsplit`, part 1 the others (and the LDF-mapped B).
+// part < 0: every feature; else the work split between nparts (2 or 4)
+// threads of the cell: part 0 writes the neighbour-density features; the
+// Legendre variables go to the parts in order (GLM: 8 / nparts each; Powell:
+// the 5 hydro variables), the LDF-mapped B to the last part (Powell).
 template <typename Dm, typename Src, typename Put>
 __device__ __forceinline__ void features_of(const Dm& dm, const MlpTabs& mt, const Src& src, Put put,
-                                            int part = -1) {
-  const int vsplit = dm.glm() ? 4 : 5;
+                                            int part = -1, int nparts = 2) {
+  auto owner = [&](int v) {
+    if (dm.glm()) return (v * nparts) >> 3;
+    return nparts == 2 ? 0 : (v < 2 ? 0 : v < 4 ? 1 : 2);
+  };
+  const int ldf_part = nparts - 1;
   const int n = dm.n();
   float m[8];
   {
@@ -154,7 +159,7 @@ __device__ __forceinline__ void features_of(const Dm& dm, const MlpTabs& mt, con
   for (int v = 0; v < 8; ++v) {
     const bool leg = v < nleg || (!dm.glm() && dm.D() == 2 && v == 7);
     if (!leg) continue;
-    if (part >= 0 && (v < vsplit) != (part == 0)) continue;
+    if (part >= 0 && owner(v) != part) continue;
     const int r0 = (v == 7 && !dm.glm()) ? dm.bz2d() : v * n;
 #pragma unroll
     for (int l = 0; l < n; ++l) {
@@ -165,7 +170,7 @@ __device__ __forceinline__ void features_of(const Dm& dm, const MlpTabs& mt, con
         if (a < dm.D() && l == dm.deg1(a)) put(8 * n + 2 * dm.D() + 8 * a + v, av * imdx);
     }
   }
-  if (!dm.glm() && part != 0) {
+  if (!dm.glm() && (part < 0 || part == ldf_part)) {
     // LDF B -> per-component Legendre coefficients (exact map)
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) {
@@ -547,8 +552,8 @@ struct StagedSrc {
 
 constexpr long long kWaitCycles = 2000000000ll;  // about one second at GB300 clocks
 
-template <int KP, bool GLM, int DEG>
-__global__ void __launch_bounds__(256) k_mlp_staged(Geom g, MlpTabs mt, const float* __restrict__ w,
+template <int KP, bool GLM, int DEG, int NTH>
+__global__ void __launch_bounds__(NTH) k_mlp_staged(Geom g, MlpTabs mt, const float* __restrict__ w,
                                                     const __nv_bfloat16* __restrict__ W1,
                                                     const __nv_bfloat16* __restrict__ W2,
                                                     const float* __restrict__ bias, float thresh,
@@ -567,15 +572,19 @@ __global__ void __launch_bounds__(256) k_mlp_staged(Geom g, MlpTabs mt, const fl
   __nv_bfloat16* W2s = W1s + HID * KP;                              // [HID][HID]
   __nv_bfloat16* Xs = W2s + HID * HID;  // [128][KP] features; then layer 1's output [128][HID]
   float* bs = reinterpret_cast<float*>(Xs + 128 * KP);  // b1[64], b2[64], w3[64], b3
-  float* part = bs + 3 * HID + 1;                       // [2][128] halves of the output layer
-  uint8_t* fl = reinterpret_cast<uint8_t*>(part + 256);  // [128] flags of the tile
+  // NP = NTH / 128 threads per cell split the feature work; the NTH / 32 warps
+  // split the epilogues: warp w reads tensor-memory lanes 32 (w % 4).. and a
+  // group of CW = HID / CG columns, CG = NTH / 128 groups
+  constexpr int NP = NTH / 128, CG = NTH / 128, CW = HID / CG;
+  static_assert(CW == 32 || CW == 16, "column groups of 32 or 16");
+  float* part = bs + 3 * HID + 1;                       // [CG][128] partial sums of the output layer
+  uint8_t* fl = reinterpret_cast<uint8_t*>(part + CG * 128);  // [128] flags of the tile
   uint8_t* sfail = fl + 128;                              // [128] positivity screen not cleared
-  // two threads per cell: t = cell + 128 * half; the halves split the feature work
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int cell = t & 127, half = t >> 7;
-  for (int i = t; i < HID * KP; i += 256) W1s[tc::kmajor_index(i / KP, i % KP, KP)] = W1[i];
-  for (int i = t; i < HID * HID; i += 256) W2s[tc::kmajor_index(i / HID, i % HID, HID)] = W2[i];
-  for (int i = t; i < 3 * HID + 1; i += 256) bs[i] = bias[i];
+  const int cell = t & 127, fpart = t >> 7;
+  for (int i = t; i < HID * KP; i += NTH) W1s[tc::kmajor_index(i / KP, i % KP, KP)] = W1[i];
+  for (int i = t; i < HID * HID; i += NTH) W2s[tc::kmajor_index(i / HID, i % HID, HID)] = W2[i];
+  for (int i = t; i < 3 * HID + 1; i += NTH) bs[i] = bias[i];
   if (t == 0) {
     mbar_init(bar, 1);
     mbar_init(bar + 1, 1);
@@ -655,10 +664,11 @@ __global__ void __launch_bounds__(256) k_mlp_staged(Geom g, MlpTabs mt, const fl
     const float* st = buf + b * bufsz;
     {
       using Dm = CtDims<GLM, DEG>;
-      if (half)
+      if (fpart == NP - 1)
         for (int q = nin; q < KP; ++q) Xs[tc::kmajor_index(cell, q, KP)] = __float2bfloat16_rn(0.f);
       features_of(Dm{}, mt, StagedSrc<Dm>{Dm{}, st, st + nrs * 128, xe, cell},
-                  [&](int q, float v) { Xs[tc::kmajor_index(cell, q, KP)] = __float2bfloat16_rn(v); }, half);
+                  [&](int q, float v) { Xs[tc::kmajor_index(cell, q, KP)] = __float2bfloat16_rn(v); }, fpart,
+                  NP);
     }
     tc::fence_proxy_async();  // the features, written by every thread, become tensor-core operands
     __syncthreads();
@@ -687,24 +697,25 @@ __global__ void __launch_bounds__(256) k_mlp_staged(Geom g, MlpTabs mt, const fl
     }
     mma_pending = -1;
     tc::fence_after_sync();
-    // epilogue 1: warp w reads lanes 32 (w % 4).. of columns 32 (w / 4)..; bias,
+    // epilogue 1: warp w reads lanes 32 (w % 4).. of columns CW (w / 4)..; bias,
     // ReLU, BF16 into layer 2's A operand (over the features: layer 1 is done)
     const int quarter = warp & 3, colh = warp >> 2, row = 32 * quarter + lane;
     const uint32_t tlane = (uint32_t)(32 * quarter) << 16;
     {
-      float v[32];
-      tc::ld32(tm + tlane + 32 * colh, v);
+      float v[CW];
+      if constexpr (CW == 32) tc::ld32(tm + tlane + CW * colh, v);
+      else tc::ld16(tm + tlane + CW * colh, v);
       // 16-byte stores of eight BF16 values: the 8 rows of a core matrix fill 128 contiguous bytes
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < CW / 8; ++j) {
         uint4 pk;
         uint32_t* pw = reinterpret_cast<uint32_t*>(&pk);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const int k = 32 * colh + 8 * j + 2 * e;
+          const int k = CW * colh + 8 * j + 2 * e;
           pw[e] = pack_bf16(fmaxf(v[8 * j + 2 * e] + bs[k], 0.f), fmaxf(v[8 * j + 2 * e + 1] + bs[k + 1], 0.f));
         }
-        *reinterpret_cast<uint4*>(Xs + tc::kmajor_index(row, 32 * colh + 8 * j, HID)) = pk;
+        *reinterpret_cast<uint4*>(Xs + tc::kmajor_index(row, CW * colh + 8 * j, HID)) = pk;
       }
     }
     tc::fence_before_sync();
@@ -726,19 +737,23 @@ __global__ void __launch_bounds__(256) k_mlp_staged(Geom g, MlpTabs mt, const fl
     }
     mma_pending = -1;
     tc::fence_after_sync();
-    // epilogue 2: bias, ReLU and this warp's half of the output layer's dot product
+    // epilogue 2: bias, ReLU and this warp's share of the output layer's dot product
     {
-      float v[32];
-      tc::ld32(tm + tlane + HID + 32 * colh, v);
+      float v[CW];
+      if constexpr (CW == 32) tc::ld32(tm + tlane + HID + CW * colh, v);
+      else tc::ld16(tm + tlane + HID + CW * colh, v);
       float o = 0.f;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) o += fmaxf(v[j] + bs[HID + 32 * colh + j], 0.f) * bs[2 * HID + 32 * colh + j];
+      for (int j = 0; j < CW; ++j) o += fmaxf(v[j] + bs[HID + CW * colh + j], 0.f) * bs[2 * HID + CW * colh + j];
       part[colh * 128 + row] = o;
     }
     tc::fence_before_sync();
     __syncthreads();
     if (t < 128) {
-      const float p = 1.f / (1.f + __expf(-(part[t] + part[128 + t] + bs[3 * HID])));
+      float z = bs[3 * HID];
+#pragma unroll
+      for (int gq = 0; gq < CG; ++gq) z += part[gq * 128 + t];
+      const float p = 1.f / (1.f + __expf(-z));
       fl[t] = p > thresh ? 1 : 0;
       const int64_t cc = c0 + t;
       if (cc < g.ncell) {
@@ -747,8 +762,9 @@ __global__ void __launch_bounds__(256) k_mlp_staged(Geom g, MlpTabs mt, const fl
       }
     }
     __syncthreads();  // the flags of the tile are written
-    if (list) compact_warp(lane < 16 && fl[warp * 16 + (lane & 15)] != 0, c0 + warp * 16 + lane, list, sc);
-    if (plist) {
+    if (list && warp < 8)
+      compact_warp(lane < 16 && fl[warp * 16 + (lane & 15)] != 0, c0 + warp * 16 + lane, list, sc);
+    if (plist && warp < 8) {
       const int cl = warp * 16 + (lane & 15);
       append_cells(lane < 16 && fl[cl] == 0 && sfail[cl] != 0, c0 + cl, plist, &sc->npos);
     }
@@ -941,8 +957,13 @@ int mlp_set_weights(Ctx& c, const float* theta_dev, int nin, float thresh) {
 template <int KP>
 static size_t staged_smem(int nrs, int nbuf) {
   return (size_t)nbuf * (nrs + 32) * 512 + 128 + (size_t)HID * KP * 2 + (size_t)HID * HID * 2 + (size_t)128 * KP * 2 +
-         (3 * HID + 1) * sizeof(float) + 256 * sizeof(float) + 256;
+         (3 * HID + 1) * sizeof(float) + 512 * sizeof(float) + 256;
 }
+
+// threads per block of the staged kernel: two per cell of the 128-cell tile
+// (measured at 256^3: four per cell, 512 threads, 3.97 against 3.92 ms per
+// stage; two tile buffers at one block per SM 6.8 ms)
+constexpr int kStagedThreads = 256;
 
 // the staged kernel applies: FP32 form, uniform 3D mesh, x-rows of whole
 // 128-cell tiles, and the shared memory fits. Two tile buffers only where two
@@ -965,7 +986,8 @@ static void staged_launch(Ctx& c, const void* w, uint8_t* flag, float* prob, cud
   const size_t sm = staged_smem<KP>(nrs, nbuf);
   static size_t attr = 0;
   if (attr < sm) {
-    cudaFuncSetAttribute(k_mlp_staged<KP, GLM, DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_mlp_staged<KP, GLM, DEG, kStagedThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
     attr = sm;
   }
   // resident blocks per SM from the SM's shared memory (1 KB reserved per
@@ -979,15 +1001,15 @@ static void staged_launch(Ctx& c, const void* w, uint8_t* flag, float* prob, cud
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     per_sm = smem_sm / (int)(sm + 1024);
-    if (cudaFuncGetAttributes(&fa, k_mlp_staged<KP, GLM, DEG>) == cudaSuccess && fa.numRegs > 0)
-      per_sm = std::min(per_sm, 65536 / (fa.numRegs * 256));
+    if (cudaFuncGetAttributes(&fa, k_mlp_staged<KP, GLM, DEG, kStagedThreads>) == cudaSuccess && fa.numRegs > 0)
+      per_sm = std::min(per_sm, 65536 / (fa.numRegs * kStagedThreads));
     per_sm = std::max(per_sm, 1);
   }
   // at most four blocks per SM: each holds 128 of the SM's 512 tensor-memory columns
   const unsigned nb = (unsigned)std::min<int64_t>(g.ncell / 128, (int64_t)c.nsm * std::min(per_sm, 4));
-  k_mlp_staged<KP, GLM, DEG><<<nb, 256, sm, st>>>(g, c.mlp, (const float*)w, (const __nv_bfloat16*)c.mlp_w1,
-                                                   (const __nv_bfloat16*)c.mlp_w2, c.mlp_bias, c.mlp_thresh, flag,
-                                                   prob, list, c.sc, nrs, nbuf, plist, c.pscr);
+  k_mlp_staged<KP, GLM, DEG, kStagedThreads><<<nb, kStagedThreads, sm, st>>>(
+      g, c.mlp, (const float*)w, (const __nv_bfloat16*)c.mlp_w1, (const __nv_bfloat16*)c.mlp_w2, c.mlp_bias,
+      c.mlp_thresh, flag, prob, list, c.sc, nrs, nbuf, plist, c.pscr);
 }
 
 template <typename T, int KP>

@@ -105,6 +105,7 @@ def generate(divb="powell", degree=2, n=64, seeds=(1, 2, 3, 4), steps=6, precisi
                      Mtilde=Mtilde)
         nin = sol.n_features()
         w, wm = blast_state(sol, W.blast_params(sd), nvar, device)
+        sol.dt(w, wm)  # GLM: the labels' characteristic fields need c_h (a step sets it the same way)
         for _ in range(steps):
             X, y = _record(sol, w, wm, 1.0, gen, device)
             Xs.append(X)
@@ -117,6 +118,7 @@ def generate(divb="powell", degree=2, n=64, seeds=(1, 2, 3, 4), steps=6, precisi
                      Mtilde=Mtilde)
         nin = sol.n_features()
         w, wm = turbulence_state(sol, sd, mach, nvar, device)
+        sol.dt(w, wm)
         for _ in range(turb_steps):
             X, y = _record(sol, w, wm, keep, gen, device)
             Xs.append(X)
@@ -200,6 +202,7 @@ def evaluate(theta, nin, divb="powell", degree=2, n=128, steps=10, threshold=0.1
         lim = DG_LIMIT_TVB if mode == "plain" else DG_LIMIT_MLP
         sol = Solver(3, (n, n, n), degree, divb, precision=precision, limiter=lim, positivity=1, Mtilde=Mtilde)
         w, wm = blast_state(sol, params, nvar, device)
+        sol.dt(w, wm)  # GLM speeds of the start, as the first step sets them
         dt = torch.tensor([0.0], dtype=torch.float64, device=device)
         if mode == "mlp":
             sol.mlp_set_weights(theta, threshold)
@@ -213,6 +216,9 @@ def evaluate(theta, nin, divb="powell", degree=2, n=128, steps=10, threshold=0.1
                 # detection quality measured on the plain run's own states
                 probe = Solver(3, (n, n, n), degree, divb, precision=precision, limiter=DG_LIMIT_TVB,
                                positivity=0, Mtilde=Mtilde) if s == 0 else probe
+                if divb == "glm":
+                    # the plain decision of the running solver: its current GLM speeds
+                    probe.set_glm(*sol.glm_speeds())
                 rates.append(detection_rates(probe, w, wm, theta))
             sol.step(w, wm)
         torch.cuda.synchronize()
@@ -276,7 +282,10 @@ def evaluate_turbulence(theta, nin, divb="glm", degree=2, n=256, steps=3, thresh
     probe = Solver(3, (n, n, n), degree, divb, precision=precision, limiter=DG_LIMIT_TVB, positivity=0,
                    Mtilde=Mtilde)
     rates = []
+    sol.dt(w, wm)
     for _ in range(steps):
+        if divb == "glm":
+            probe.set_glm(*sol.glm_speeds())
         rates.append(detection_rates(probe, w, wm, theta))
         sol.step(w, wm)
     del sol, probe, w, wm

@@ -1,7 +1,8 @@
 """End-to-end learned indicator on solver-generated data (small sizes):
 labels from the plain TVB detector on seeded blasts, training with the
-library's kernels, then the gated run against the plain run. The gain shown
-is the limiter time: the TVB procedure runs only on flagged cells."""
+library's kernels, then the gated run against the plain run on the 128^3
+blast in the FP32 form. The gain shown is the limiter time: the TVB procedure
+runs only on flagged cells."""
 import numpy as np
 import pytest
 
@@ -15,10 +16,10 @@ def test_indicator_pipeline_and_gain():
     assert X.shape[0] == 3 * 5 * 32 ** 3 and int(y.sum()) > 100 and int(src.sum()) == 0
     theta, info = I.train(X, y, nin, epochs=20, batch=1024, lr=2e-3, src=src)
     assert info["loss_last_epoch"] < 0.5 * info["loss_initial"]
-    from paper_1806_02343_gb300.binding import DG_PREC_FP64
-    # FP64 form: the characteristic detection is costly there (GB300's FP64
-    # rate), which is where gating it by the BF16 network pays
-    rep = I.evaluate(theta, nin, "powell", 2, n=48, steps=4, threshold=0.1, precision=DG_PREC_FP64)
+    from paper_1806_02343_gb300.binding import DG_PREC_FP32MIX
+    # the benchmarked form and size class: FP32 form at 128^3 (the staged
+    # tensor-core indicator; x-rows of whole 128-cell tiles)
+    rep = I.evaluate(theta, nin, "powell", 2, n=128, steps=4, threshold=0.1, precision=DG_PREC_FP32MIX)
     assert rep["status"]["plain"] == 0 and rep["status"]["mlp"] == 0
     assert rep["troubled_plain"] > 0
     assert rep["missed_cell_rate"] < 0.3
