@@ -879,7 +879,7 @@ def main():
         "alu": res.get("alu"),
         "kernel_path": ("octree face-list kernels (k_face_list, k_cell_list)" if cfg.get("amr") else
                         "specialised GLM 3D kernels (k_face_glm, k_cell_glm)" if cfg["divb"] == "glm" else
-                        "generic kernels (k_face, k_cell)"),
+                        "specialised Powell/LDF 3D kernels (k_face_pow3, k_cell_pow, k_divb_face_pow)"),
     }
     print(json.dumps(line))
 

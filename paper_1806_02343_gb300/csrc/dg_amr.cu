@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "dg_amr.cuh"
+#include "dg_fast.cuh"
 #include "dg_phys.cuh"
 
 namespace dgmhd {
@@ -539,13 +540,97 @@ int build_amr(Ctx& c, const dg_mesh_desc* mesh) {
   double dmin = DBL_MAX;
   for (double d : dxc) dmin = std::min(dmin, d);
   g.dx = dmin;
+  // specialised Powell kernels: faces grouped by type in blocks of <= 32, and
+  // the tables of each type (the std tables: the full face; coarse sides: the
+  // sub-face tables Ps above)
+  if (!g.glm && D == 3 && (g.d == 1 || g.d == 2) && c.p.generic_kernels != 1 && c.p.powell_q != 1) {
+    const int n = g.n, Qf = g.Qf, QFP = Qf + (Qf & 1);
+    std::vector<std::vector<int32_t>> by_type(27);
+    for (int64_t f = 0; f < nf; ++f) {
+      const int m = fmeta[f], a = m & 3, kind = (m >> 2) & 3, sb = m >> 4;
+      by_type[a * 9 + (kind == 0 ? 0 : kind == 1 ? 1 + sb : 5 + sb)].push_back((int32_t)f);
+    }
+    std::vector<int32_t> bface, bstart, btype;
+    bface.reserve(nf);
+    for (int ty = 0; ty < 27; ++ty) {
+      const auto& L = by_type[ty];
+      for (size_t k = 0; k < L.size(); k += 32) {
+        bstart.push_back((int32_t)(bface.size() + k));
+        btype.push_back(ty | (int32_t)(std::min<size_t>(32, L.size() - k) << 8));
+      }
+      bface.insert(bface.end(), L.begin(), L.end());
+    }
+    // Legendre values on the full face f (its tangential axes in increasing
+    // order, the last fastest), and face_val: full face (sb < 0) or sub-face sb
+    std::vector<double> Pfull((size_t)2 * D * n * Qf);
+    for (int f = 0; f < 2 * D; ++f) {
+      const int a = f >> 1;
+      int others[2], no = 0;
+      for (int b = 0; b < D; ++b)
+        if (b != a) others[no++] = b;
+      for (int p = 0; p < Qf; ++p) {
+        double xi[3] = {0, 0, 0};
+        int pp = p;
+        for (int j = no - 1; j >= 0; --j) {
+          xi[others[j]] = x1[pp % g.nq1];
+          pp /= g.nq1;
+        }
+        xi[a] = (f & 1) ? 1.0 : -1.0;
+        for (int l = 0; l < n; ++l) Pfull[((size_t)f * n + l) * Qf + p] = B.eval(B.leg[l], xi);
+      }
+    }
+    auto face_val = [&](int f, int sb, int l, int p) {
+      return sb < 0 ? Pfull[((size_t)f * n + l) * Qf + p] : Ps[((size_t)(f * nsub + sb) * n + l) * Qf + p];
+    };
+    std::vector<double> ftab((size_t)27 * 2 * n * QFP, 0.0), ctab((size_t)30 * Qf * n, 0.0);
+    for (int ty = 0; ty < 27; ++ty) {
+      const int a = ty / 9, k = ty % 9;
+      const int sbL = (k >= 1 && k <= 4) ? k - 1 : -1, sbR = k >= 5 ? k - 5 : -1;
+      for (int l = 0; l < n; ++l)
+        for (int p = 0; p < Qf; ++p) {
+          ftab[(((size_t)ty * 2 + 0) * n + l) * QFP + p] = face_val(2 * a + 1, sbL, l, p);
+          ftab[(((size_t)ty * 2 + 1) * n + l) * QFP + p] = face_val(2 * a, sbR, l, p);
+        }
+    }
+    std::vector<double> wf(Qf, 1.0);
+    for (int p = 0; p < Qf; ++p)
+      for (int k = 0, pp = p; k < D - 1; ++k, pp /= g.nq1) wf[p] *= w1[pp % g.nq1];
+    for (int t = 0; t < 30; ++t) {
+      const int f = t < 6 ? t : (t - 6) / 4, sb = t < 6 ? -1 : (t - 6) % 4;
+      for (int p = 0; p < Qf; ++p)
+        for (int l = 0; l < n; ++l)
+          ctab[((size_t)t * Qf + p) * n + l] = face_val(f, sb, l, p) * wf[p] * (sb < 0 ? 1.0 : 1.0 / nsub);
+    }
+    if ((e = upload_vec(&h.bface, bface)) || (e = upload_vec(&h.bstart, bstart)) || (e = upload_vec(&h.btype, btype)))
+      return e;
+    if (c.p.precision == DG_PREC_FP32MIX) {
+      std::vector<float> a(ftab.begin(), ftab.end()), b(ctab.begin(), ctab.end());
+      if ((e = upload_vec((float**)&h.ftab, a)) || (e = upload_vec((float**)&h.ctab, b))) return e;
+    } else {
+      if ((e = upload_vec((double**)&h.ftab, ftab)) || (e = upload_vec((double**)&h.ctab, ctab))) return e;
+    }
+    h.nblk = (int64_t)btype.size();
+    h.fast = true;
+  }
   return DG_OK;
+}
+
+OctPow<float> oct_pow32(const Ctx& c) {
+  const AmrHost& h = c.amr;
+  return OctPow<float>{h.fL, h.fR, h.fmeta, h.cstart, h.centry, h.dxc, h.bface, h.bstart, h.btype,
+                       (const float*)h.ftab, (const float*)h.ctab, c.g.ncell, c.g.stride, h.nblk};
+}
+OctPow<double> oct_pow64(const Ctx& c) {
+  const AmrHost& h = c.amr;
+  return OctPow<double>{h.fL, h.fR, h.fmeta, h.cstart, h.centry, h.dxc, h.bface, h.bstart, h.btype,
+                        (const double*)h.ftab, (const double*)h.ctab, c.g.ncell, c.g.stride, h.nblk};
 }
 
 void free_amr(Ctx& c) {
   AmrHost& h = c.amr;
   void* ptrs[] = {h.fL,     h.fR,     h.fmeta,    h.cstart,   h.centry,   h.dxc,    h.Psub64, h.Lsub64,
-                  h.Psub32, h.Lsub32, h.Psub64p, h.Lsub64p, h.Psub32p, h.Lsub32p, h.groups, h.lev_dev};
+                  h.Psub32, h.Lsub32, h.Psub64p, h.Lsub64p, h.Psub32p, h.Lsub32p, h.groups, h.lev_dev,
+                  h.bface,  h.bstart, h.btype,    h.ftab,     h.ctab};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h = AmrHost();

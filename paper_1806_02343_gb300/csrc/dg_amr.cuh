@@ -28,6 +28,11 @@ struct AmrDev {
 };
 
 int build_amr(Ctx& c, const dg_mesh_desc* mesh);
+// the specialised Powell kernels' view of the octree (AmrHost::fast)
+template <typename T>
+struct OctPow;
+OctPow<float> oct_pow32(const Ctx& c);
+OctPow<double> oct_pow64(const Ctx& c);
 void free_amr(Ctx& c);
 
 template <typename T>

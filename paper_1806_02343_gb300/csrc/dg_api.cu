@@ -194,6 +194,87 @@ void free_tables(Tables<T>& t) {
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Powell kernels' tables (dg_fast.cuh PowTabs): the Legendre coefficients of
+// the LDF functions' components by quadrature (exact: every component is a
+// polynomial of total degree <= d), checked against the functions themselves;
+// ok = 0 when the basis lacks the structure the kernels rely on (three
+// constant functions, each along one axis, and no other function with a
+// non-zero mean). The same for every context of this degree.
+template <typename T, int DEG>
+void build_pow_tabs(PowTabs<T, DEG>& pt) {
+  using Dm = FastDims<DEG>;
+  constexpr int N = Dm::N, NDIV = PowDims<DEG>::NDIV, NP = PowDims<DEG>::NP;
+  pt = PowTabs<T, DEG>();
+  Basis L;
+  if (!L.build(3, DEG, true) || L.ndiv != NDIV || L.n != N) return;
+  std::vector<double> x1, w1;
+  gauss_legendre(DEG + 1, x1, w1);
+  const int Qv = Dm::QV;
+  std::vector<double> A((size_t)NDIV * 3 * N, 0.0);  // [j][cc][l]
+  double xi[3];
+  for (int q = 0; q < Qv; ++q) {
+    vol_point(3, x1, q, xi);
+    double wq = 1.0;
+    for (int k = 0, qq = q; k < 3; ++k, qq /= DEG + 1) wq *= w1[qq % (DEG + 1)];
+    for (int l = 0; l < N; ++l) {
+      const double Pl = L.eval(L.leg[l], xi) * wq / L.leg_mass[l];
+      for (int j = 0; j < NDIV; ++j)
+        for (int cc = 0; cc < 3; ++cc) A[((size_t)j * 3 + cc) * N + l] += L.eval(L.ldf[j][cc], xi) * Pl;
+    }
+  }
+  auto a = [&](int j, int cc, int l) -> double& { return A[((size_t)j * 3 + cc) * N + l]; };
+  for (double& x : A)
+    if (std::fabs(x) < 1e-13) x = 0.0;
+  // the expansion reproduces every function at the points
+  for (int q = 0; q < Qv; ++q) {
+    vol_point(3, x1, q, xi);
+    for (int j = 0; j < NDIV; ++j)
+      for (int cc = 0; cc < 3; ++cc) {
+        double s = 0.0;
+        for (int l = 0; l < N; ++l) s += a(j, cc, l) * L.eval(L.leg[l], xi);
+        if (std::fabs(s - L.eval(L.ldf[j][cc], xi)) > 1e-11) return;
+      }
+  }
+  int seen = 0;
+  for (int j = 0; j < NDIV; ++j)
+    for (int cc = 0; cc < 3; ++cc)
+      for (int l = 0; l < N; ++l) {
+        if (j < 3 && l > 0 && a(j, cc, l) != 0.0) return;
+        if (j >= 3 && l == 0 && a(j, cc, l) != 0.0) return;
+      }
+  for (int j = 0; j < 3; ++j) {
+    int nz = 0, at = -1;
+    for (int cc = 0; cc < 3; ++cc)
+      if (a(j, cc, 0) != 0.0) ++nz, at = cc;
+    if (nz != 1 || (seen >> at) & 1) return;
+    seen |= 1 << at;
+    pt.jm[at] = j;
+  }
+  for (int cc = 0; cc < 3; ++cc)
+    for (int j = 0; j < NDIV; ++j)
+      for (int l = 0; l < N; ++l) pt.Af[cc][j][l] = (T)a(j, cc, l);
+  for (int k = 0; k < NP; ++k)
+    for (int e = 0; e < 2; ++e) {
+      const int j = 3 + 2 * k + e;
+      for (int cc = 0; cc < 3; ++cc)
+        for (int l = 0; l < N; ++l) pt.Ab[k][cc][l][e] = j < NDIV ? (T)a(j, cc, l) : T(0);
+    }
+  for (int j = 0; j < NDIV; ++j) pt.minvL[j] = (T)(1.0 / L.ldf_mass[j]);
+  for (int a2 = 0; a2 < 3; ++a2)
+    for (int sd = 0; sd < 2; ++sd)
+      for (int p = 0; p < Dm::QF; ++p) {
+        face_point(3, x1, 2 * a2 + sd, p, xi);
+        for (int j = 0; j < NDIV; ++j) pt.Ln[a2][sd][j][p] = (T)L.eval(L.ldf[j][a2], xi);
+      }
+  for (int p = 0; p < Dm::QF; ++p) {
+    double wp = 1.0;
+    for (int k = 0, pp = p; k < 2; ++k, pp /= DEG + 1) wp *= w1[pp % (DEG + 1)];
+    pt.wf[p] = (T)wp;
+  }
+  for (int cc = 0; cc < 3; ++cc) pt.kL[cc] = a(pt.jm[cc], cc, 0) / L.ldf_mass[pt.jm[cc]];
+  pt.ok = 1;
+}
+
 template <typename T, int DEG>
 void* make_fast_tabs(const HostTables& h, const Geom& g, const Basis& B) {
   using Dm = FastDims<DEG>;
@@ -225,6 +306,7 @@ void* make_fast_tabs(const HostTables& h, const Geom& g, const Basis& B) {
       for (int q = 0; q < Qv; ++q) ft->cell.dP2[a][i / 2][q][i % 2] = (T)(h.dPv[((size_t)a * n + l) * Qv + q] * h.wv[q]);
     }
   static_assert(Dm::N > 0, "");
+  build_pow_tabs<T, DEG>(ft->pow);
   if (fast_to_constant<T, DEG>(*ft)) {
     delete ft;
     return nullptr;
@@ -242,6 +324,17 @@ void free_fast_tabs(Ctx& c) {
   }
   c.fast_tabs = nullptr;
   c.fast = 0;
+}
+
+// the Powell tables of the context's specialised kernels have the expected structure
+bool fast_pow_ok(const Ctx& c) {
+  switch (c.fast) {
+    case 11: return ((const FastAll<float, 1>*)c.fast_tabs)->pow.ok != 0;
+    case 12: return ((const FastAll<float, 2>*)c.fast_tabs)->pow.ok != 0;
+    case 21: return ((const FastAll<double, 1>*)c.fast_tabs)->pow.ok != 0;
+    case 22: return ((const FastAll<double, 2>*)c.fast_tabs)->pow.ok != 0;
+  }
+  return false;
 }
 
 FastGeom fast_geom(const Geom& g) {
@@ -546,8 +639,12 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
   }
   const size_t esz = fp32(c) ? sizeof(float) : sizeof(double);
   const size_t state_bytes = (size_t)g.nrows * g.stride * esz;
-  size_t face_elems = (size_t)g.D * g.stride * g.Qf * 9;
-  if (c.amr.on) face_elems = std::max(face_elems, (size_t)c.amr.nface * g.Qf * 9);
+  // Powell / LDF specialised kernels: 10 face-buffer slots per face point
+  const bool pow_fast = !g.glm && g.D == 3 && (degree == 1 || degree == 2) && prm.generic_kernels != 1 &&
+                        prm.powell_q != 1;
+  size_t face_pts = (size_t)g.D * g.stride * g.Qf;
+  if (c.amr.on) face_pts = std::max(face_pts, (size_t)c.amr.nface * g.Qf);
+  const size_t face_elems = face_pts * (pow_fast ? 10 : 9);
   bool ok = cudaMalloc(&c.sc, sizeof(DevScalars)) == cudaSuccess &&
             cudaMemset(c.sc, 0, sizeof(DevScalars)) == cudaSuccess &&
             cudaMalloc(&c.stage_buf[0], state_bytes) == cudaSuccess &&
@@ -571,7 +668,7 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
     }
     // Powell q^dagger of eq. powellq-interp: 14 values per face point
     if (ok && prm.powell_q == 1 && !g.glm)
-      ok = cudaMalloc(&c.qdag_buf, face_elems / 9 * 14 * (fp32(c) ? sizeof(float) : sizeof(double))) == cudaSuccess;
+      ok = cudaMalloc(&c.qdag_buf, face_pts * 14 * (fp32(c) ? sizeof(float) : sizeof(double))) == cudaSuccess;
   }
   if (!ok) {
     dg_mhd_destroy(ctx);
@@ -579,6 +676,19 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
   }
   upload_limiter_tables(c);
   mlp_build_tables(c);
+  // specialised Powell / LDF kernels for uniform 3D meshes (not the q^dagger variant)
+  if (pow_fast) {
+    if (fp32(c)) {
+      if (degree == 1) c.fast_tabs = make_fast_tabs<float, 1>(h, g, *c.hb);
+      if (degree == 2) c.fast_tabs = make_fast_tabs<float, 2>(h, g, *c.hb);
+      if (c.fast_tabs) c.fast = 10 + degree;
+    } else {
+      if (degree == 1) c.fast_tabs = make_fast_tabs<double, 1>(h, g, *c.hb);
+      if (degree == 2) c.fast_tabs = make_fast_tabs<double, 2>(h, g, *c.hb);
+      if (c.fast_tabs) c.fast = 20 + degree;
+    }
+    if (c.fast && !fast_pow_ok(c)) free_fast_tabs(c);
+  }
   // specialised GLM kernels for uniform 3D meshes
   if (g.glm && g.D == 3 && prm.generic_kernels != 1 && !c.amr.on) {
     if (fp32(c)) {
@@ -688,6 +798,27 @@ namespace {
 int operator_pass(Ctx& c, const void* w, const double* wmean, void* out, double* outmean, const void* w0,
                   const double* w0mean, double ca, double cb, int combine, cudaStream_t st) {
   const Geom& g = c.g;
+  if (c.amr.on && c.amr.fast && c.fast) {
+    // specialised Powell kernels over the face list (face pass + cell pass)
+    c.prof.begin(1, st);
+    switch (c.fast) {
+      case 11: launch_list_pow<float, 1>(oct_pow32(c), g.gamma, (const float*)w, c.face_buf32, (float*)out,
+                                         (const float*)w0, ca, cb, combine, c.sc, wmean, w0mean, outmean,
+                                         c.p.eps_hlld, st); break;
+      case 12: launch_list_pow<float, 2>(oct_pow32(c), g.gamma, (const float*)w, c.face_buf32, (float*)out,
+                                         (const float*)w0, ca, cb, combine, c.sc, wmean, w0mean, outmean,
+                                         c.p.eps_hlld, st); break;
+      case 21: launch_list_pow<double, 1>(oct_pow64(c), g.gamma, (const double*)w, c.face_buf, (double*)out,
+                                          (const double*)w0, ca, cb, combine, c.sc, nullptr, nullptr, nullptr,
+                                          c.p.eps_hlld, st); break;
+      case 22: launch_list_pow<double, 2>(oct_pow64(c), g.gamma, (const double*)w, c.face_buf, (double*)out,
+                                          (const double*)w0, ca, cb, combine, c.sc, nullptr, nullptr, nullptr,
+                                          c.p.eps_hlld, st); break;
+    }
+    c.prof.end(1, st);
+    c.prof.launches[1] += 1;
+    return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
+  }
   if (c.amr.on) {
     c.prof.begin(1, st);
     if (fp32(c))
@@ -706,11 +837,15 @@ int operator_pass(Ctx& c, const void* w, const double* wmean, void* out, double*
   case code: {                                                                                              \
     const auto& ft = *(const FastAll<T, DEG>*)c.fast_tabs;                                                \
     c.prof.begin(0, st);                                                                                    \
-    launch_face_glm<T, DEG>(ft, fg, (const T*)w, FB, c.sc, c.p.eps_hlld, st);                               \
+    if (g.glm) launch_face_glm<T, DEG>(ft, fg, (const T*)w, FB, c.sc, c.p.eps_hlld, st);                    \
+    else launch_face_pow<T, DEG>(ft, fg, (const T*)w, FB, c.p.eps_hlld, st);                                \
     c.prof.end(0, st);                                                                                      \
     c.prof.begin(1, st);                                                                                    \
-    if (!launch_cell_fast<T, DEG>(c, ft, fg, (const T*)w, FB, (T*)out, (const T*)w0, ca, cb, combine,      \
-                                  wmean, w0mean, outmean, st))                                              \
+    if (!g.glm)                                                                                             \
+      launch_cell_pow<T, DEG>(ft, fg, (const T*)w, FB, (T*)out, (const T*)w0, ca, cb, combine, c.sc, wmean, \
+                              w0mean, outmean, st);                                                         \
+    else if (!launch_cell_fast<T, DEG>(c, ft, fg, (const T*)w, FB, (T*)out, (const T*)w0, ca, cb, combine, \
+                                       wmean, w0mean, outmean, st))                                         \
       launch_cell_glm<T, DEG>(ft, fg, (const T*)w, FB, (T*)out, (const T*)w0, ca, cb, combine, c.sc, wmean, \
                               w0mean, outmean, st);                                                         \
     c.prof.end(1, st);                                                                                      \
@@ -745,6 +880,19 @@ int operator_pass(Ctx& c, const void* w, const double* wmean, void* out, double*
   return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
 }
 
+// Powell face jumps of the timestep by the specialised kernel (uniform 3D,
+// degrees 1 and 2); false: the caller runs the generic one
+bool divb_face_fast(Ctx& c, const void* w, cudaStream_t st) {
+  const FastGeom fg = fast_geom(c.g);
+  switch (c.fast) {
+    case 11: launch_divb_face_pow<float, 1>(fg, (const float*)w, c.face_buf32, st); return true;
+    case 12: launch_divb_face_pow<float, 2>(fg, (const float*)w, c.face_buf32, st); return true;
+    case 21: launch_divb_face_pow<double, 1>(fg, (const double*)w, c.face_buf, st); return true;
+    case 22: launch_divb_face_pow<double, 2>(fg, (const double*)w, c.face_buf, st); return true;
+  }
+  return false;
+}
+
 int dt_pass(Ctx& c, const void* w, const double* wmean, double* dt_out, cudaStream_t st) {
   const Geom& g = c.g;
   if (g.glm) c.glm_speeds_set = true;  // the finalize kernel derives c_h and the damping from dt
@@ -760,10 +908,10 @@ int dt_pass(Ctx& c, const void* w, const double* wmean, double* dt_out, cudaStre
   }
   c.prof.begin(2, st);
   if (fp32(c)) {
-    if (!g.glm) launch_divb_face<float>(g, c.t32, (const float*)w, c.face_buf32, st);
+    if (!g.glm && !divb_face_fast(c, w, st)) launch_divb_face<float>(g, c.t32, (const float*)w, c.face_buf32, st);
     launch_dt<float>(g, c.t32, (const float*)w, wmean, c.face_buf32, c.p, c.sc, dt_out, st);
   } else {
-    if (!g.glm) launch_divb_face<double>(g, c.t64, (const double*)w, c.face_buf, st);
+    if (!g.glm && !divb_face_fast(c, w, st)) launch_divb_face<double>(g, c.t64, (const double*)w, c.face_buf, st);
     launch_dt<double>(g, c.t64, (const double*)w, nullptr, c.face_buf, c.p, c.sc, dt_out, st);
   }
   c.prof.end(2, st);

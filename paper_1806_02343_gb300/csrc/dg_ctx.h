@@ -204,6 +204,13 @@ struct AmrHost {
   std::vector<int32_t> hgroups;
   int32_t* groups = nullptr;
   int8_t* lev_dev = nullptr;
+  // specialised Powell kernels (3D, degrees 1 and 2): face blocks by type and
+  // the trace / own-side tables in the context's precision (OctPow)
+  bool fast = false;
+  int32_t *bface = nullptr, *bstart = nullptr, *btype = nullptr;
+  int64_t nblk = 0;
+  void* ftab = nullptr;
+  void* ctab = nullptr;
   // the last regrid plan (6 ints per new leaf) and a hash of the marks it was made from
   uint64_t plan_hash = 0;
   std::vector<int32_t> plan;

@@ -72,10 +72,37 @@ struct CellTabs {
   alignas(16) T minv[FastDims<DEG>::N];
 };
 
+// Powell scheme (Sec. 3.3): the magnetic field's locally divergence-free
+// (LDF) coefficients c_j and the Legendre coefficients of its components,
+// b[cc][l] = sum_j A[j][cc][l] c_j (every LDF function's components are
+// polynomials of total degree <= d, so A is exact). The kernels evaluate and
+// integrate B in that Legendre form, then map the residuals back to LDF rows
+// with the same matrix: R_j = sum_{cc,l} A[j][cc][l] R[cc][l].
+// The first three LDF functions are constant vectors (the cell means of B);
+// the others have zero mean.
+template <int DEG>
+struct PowDims {
+  static constexpr int NDIV = DEG == 1 ? 11 : 26;  // Table A1, D = 3
+  static constexpr int NP = (NDIV - 3 + 1) / 2;   // pairs of non-mean LDF rows
+};
+template <typename T, int DEG>
+struct PowTabs {
+  alignas(16) T Af[3][PowDims<DEG>::NDIV][FastDims<DEG>::N];      // forward: [cc][j][l]
+  alignas(16) T Ab[PowDims<DEG>::NP][3][FastDims<DEG>::N][2];     // back: rows 3+2k, 4+2k
+  alignas(16) T minvL[PowDims<DEG>::NDIV + 1];                    // 1 / LDF mass
+  // normal component (axis a) of LDF function j at point p of face 2a + s
+  alignas(16) T Ln[3][2][PowDims<DEG>::NDIV][FaceTabs<T, DEG>::QFP];
+  alignas(16) T wf[FaceTabs<T, DEG>::QFP];                        // face weights
+  double kL[3];   // mean of component cc: minvL[jm] A[jm][cc][0] (times 2/dx in the kernel)
+  int jm[3];      // the constant LDF row whose vector is along component cc
+  int ok;         // the basis has the structure above (else Powell runs the generic kernels)
+};
+
 template <typename T, int DEG>
 struct FastAll {
   FaceTabs<T, DEG> face[3];
   CellTabs<T, DEG> cell;
+  PowTabs<T, DEG> pow;
 };
 
 struct FastGeom {
@@ -94,6 +121,47 @@ int fast_to_constant(const FastAll<T, DEG>& tabs);
 template <typename T, int DEG>
 void launch_face_glm(const FastAll<T, DEG>& tabs, const FastGeom& g, const T* w, T* F, const DevScalars* sc,
                      double eps, cudaStream_t st);
+// Powell / LDF kernels (face buffer: 10 slots per face point, see dg_fast_impl.cuh)
+template <typename T, int DEG>
+void launch_face_pow(const FastAll<T, DEG>& tabs, const FastGeom& g, const T* w, T* F, double eps, cudaStream_t st);
+template <typename T, int DEG>
+void launch_cell_pow(const FastAll<T, DEG>& tabs, const FastGeom& g, const T* w, const T* F, T* out, const T* w0,
+                     double ca, double cb, int combine, const DevScalars* sc, const double* wmean,
+                     const double* w0mean, double* outmean, cudaStream_t st);
+// Octree meshes (Powell / LDF): the face list of the generic octree kernels
+// plus the face blocks of the specialised pass -- bface lists the faces
+// grouped by type (axis a, same level / left coarse / right coarse, sub-face),
+// block b takes bface[bstart[b] ..] with btype[b] = type | count << 8 (count
+// <= 32, type = 9 a + (0 | 1 + sub | 5 + sub)); ftab[type][side][N][QFP] the
+// trace tables of the two sides (side 0: the left cell) and
+// ctab[30][QF][N] the own-side weighted face tables of the cell pass (0..5:
+// the faces, 6 + 4 f + sub: sub-face sub of face f of a coarse cell, weights
+// w_p / 4).
+template <typename T>
+struct OctPow {
+  const int32_t* fL;
+  const int32_t* fR;
+  const int32_t* fmeta;
+  const int32_t* cstart;
+  const int32_t* centry;
+  const double* dxc;
+  const int32_t* bface;
+  const int32_t* bstart;
+  const int32_t* btype;
+  const T* ftab;
+  const T* ctab;
+  int64_t ncell, stride;
+  int64_t nblk;
+};
+template <typename T, int DEG>
+void launch_list_pow(const OctPow<T>& o, double gamma, const T* w, T* F, T* out, const T* w0, double ca, double cb,
+                     int combine, const DevScalars* sc, const double* wmean, const double* w0mean, double* outmean,
+                     double eps, cudaStream_t st);
+
+// Powell timestep's face jumps (eq. powell_dt): per face point w_p |B^n_F - B^n_L|
+// and w_p |B^n_F - B^n_R|, laid out as the generic k_divb_face writes them
+template <typename T, int DEG>
+void launch_divb_face_pow(const FastGeom& g, const T* w, T* jbuf, cudaStream_t st);
 template <typename T, int DEG>
 void launch_cell_glm(const FastAll<T, DEG>& tabs, const FastGeom& g, const T* w, const T* F, T* out, const T* w0,
                      double ca, double cb, int combine, const DevScalars* sc, const double* wmean,

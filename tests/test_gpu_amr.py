@@ -46,6 +46,33 @@ def test_amr_rhs_fp64(D, d, divb):
     assert rel_err(from_device(out, sol), ref) < 1e-12
 
 
+@pytest.mark.parametrize("generic", [0, 1])
+@pytest.mark.parametrize("d", [1, 2])
+def test_amr_powell3d_both_kernel_paths(d, generic):
+    """generic 0: the specialised Powell face-list kernels (faces in blocks of
+    one type, B in the Legendre form of its components), 1: the generic ones;
+    FP64 and the FP32 form."""
+    from gpu_helpers import mean_rows
+    leaves = _mesh(3)
+    A = AMRScheme(3, d, "powell", G, leaves)
+    assert any(f[3] == 1 for f in A.faces) and any(f[3] == 2 for f in A.faces)
+    w0 = A.project(_fn(3, A.V))
+    ref = A.rhs(w0, None, 0.0)
+    for prec, tol in (("fp64", 1e-12), ("fp32", 2e-4)):
+        sol = _solver(A, leaves, prec=prec, generic_kernels=generic)
+        w = to_device(w0, sol)
+        out = torch_nan(w)
+        if prec == "fp32":
+            wm = means_to_device(w0, sol, A)
+            om = torch_nan(wm)
+            sol.rhs(w, wm, out, om)
+            assert rel_err(om[:, : sol.ncell].cpu().numpy().T, ref[:, mean_rows(A)]) < 2e-5
+        else:
+            sol.rhs(w, None, out)
+        assert rel_err(from_device(out, sol), ref) < tol
+        assert sol.status() == 0
+
+
 def torch_nan(w):
     import torch
     return torch.full_like(w, float("nan"))

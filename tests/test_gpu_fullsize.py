@@ -3,7 +3,10 @@ degree 2, GLM, decaying-turbulence start): one application of the operator on
 the GPU, checked on seeded sampled cells against the FP64 oracle evaluated
 cell by cell from the same input coefficients. Also the 2D Alfven workload
 (32^2, Powell/LDF, 10 SSP-RK3 steps at CFL 0.3) against the oracle and the
-closed form, and the 64^3 degree-3 workload's FP32 form against its FP64 form."""
+closed form, the 64^3 degree-3 workload's FP32 form against its FP64 form, and
+the 128^3 degree-2 Powell/LDF blast's operator on sampled cells after three
+limited steps (the face jumps of B, and with them the Powell terms, are
+non-zero there)."""
 import math
 
 import numpy as np
@@ -18,11 +21,11 @@ pytestmark = pytest.mark.gpu
 G = 5.0 / 3.0
 
 
-def _gather(sol, w, wm, cells, n):
+def _gather(sol, w, wm, cells, n, mrows=None):
     """Own and face-neighbour weights of sampled cells (FP64 copies of the
-    device state; the FP64 means replace the mode-0 rows)."""
+    device state; the FP64 means replace the mean rows, by default those of
+    the GLM layout)."""
     import torch
-    from gpu_helpers import mean_rows
     ix, iy, iz = cells % n, (cells // n) % n, cells // (n * n)
     nbrs = []
     for a in range(3):
@@ -36,7 +39,9 @@ def _gather(sol, w, wm, cells, n):
     idx = torch.as_tensor(allc, device="cuda")
     x = w[:, idx].double().cpu().numpy().T.copy()
     if wm is not None:
-        x[:, list(range(0, sol.nrows, sol.nrows // 9))] = wm[:, idx].cpu().numpy().T
+        if mrows is None:
+            mrows = list(range(0, sol.nrows, sol.nrows // 9))
+        x[:, mrows] = wm[:, idx].cpu().numpy().T
     b = len(cells)
     return x[:b], np.stack([x[b * (1 + k): b * (2 + k)] for k in range(6)], 1)
 
@@ -123,3 +128,45 @@ def test_fourier_64_fp32_form_matches_fp64_form():
     # psi starts at zero and is made by the divergence error itself: its
     # difference is measured against the largest variable norm of the run
     assert math.sqrt(diff[8].item() / norm.max().item()) < 1e-5, rel
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_powell_blast_operator_at_full_size_on_sampled_cells(prec):
+    import torch
+    from gpu_helpers import mean_rows
+    from paper_1806_02343_gb300.binding import Solver, DG_PREC_FP32MIX, DG_PREC_FP64, DG_LIMIT_TVB
+    n, d = 128, 2
+    sol = Solver(3, (n, n, n), d, "powell", precision=DG_PREC_FP32MIX if prec == "fp32" else DG_PREC_FP64,
+                 limiter=DG_LIMIT_TVB, positivity=1)
+    w, wm = sol.alloc_state()
+    nodal = W.gauss_nodal(lambda x: W.blast_3d(x, nvar=8), n, d + 1, 3, sol.stride, "cuda")
+    sol.project(nodal, d + 1, w, wm)
+    del nodal
+    for _ in range(3):
+        sol.step(w, wm)
+    out, om = sol.alloc_state()
+    sol.rhs(w, wm, out, om)
+    torch.cuda.synchronize()
+    assert sol.status() == 0
+    rng = np.random.default_rng(77)
+    # random cells, cells around the blast front (centre 0.5, radius 0.1) and the box corners
+    idx = np.arange(n ** 3)
+    xc = (np.stack([idx % n, (idx // n) % n, idx // (n * n)], 1) + 0.5) / n
+    r = np.linalg.norm(xc - 0.5, axis=1)
+    front = np.flatnonzero((r > 0.08) & (r < 0.14))
+    cells = np.unique(np.concatenate([rng.choice(n ** 3, 100, replace=False), rng.choice(front, 100, replace=False),
+                                      [0, n - 1, n * n - 1, n ** 3 - 1]]))
+    S = Scheme(3, d, "powell", G, 4)
+    S.dx = 1.0 / n
+    mr = mean_rows(S)
+    wc, wnb = _gather(sol, w, wm, cells, n, mr)
+    ref = S.rhs_local(wc, wnb)
+    got = out[:, torch.as_tensor(cells, device="cuda")].double().cpu().numpy().T
+    # the sampled front cells carry face jumps of B: the Powell terms are exercised
+    assert np.max(np.abs(wnb[:, 0, 5 * S.n:] - wc[:, 5 * S.n:])) > 1e-3 * np.max(np.abs(wc[:, 5 * S.n:]))
+    if prec == "fp64":
+        assert rel_err(got, ref) < 1e-12
+    else:
+        assert rel_err(got, ref) < 2e-4
+        gm = om[:, torch.as_tensor(cells, device="cuda")].cpu().numpy().T
+        assert rel_err(gm, ref[:, mr]) < 2e-5

@@ -77,6 +77,32 @@ def test_rhs_glm3d_both_kernel_paths(D, d, divb, ncell, fname, generic):
         assert rel_err(from_device(out, sol), ref) < tol
 
 
+# Powell / LDF in 3D (degrees 1 and 2) has specialised kernels too
+POW3D = [(3, 1, "powell", (9, 8, 7), "fourier"), (3, 2, "powell", (9, 8, 7), "fourier"), CASES[4]]
+
+
+@pytest.mark.parametrize("generic", [0, 1])
+@pytest.mark.parametrize("D,d,divb,ncell,fname", POW3D)
+def test_rhs_powell3d_both_kernel_paths(D, d, divb, ncell, fname, generic):
+    """generic 0: the specialised Powell kernels (B in the Legendre form of its
+    components inside the kernels), 1: the generic kernels."""
+    for prec, tol in (("fp64", 1e-12), ("fp32", 2e-4)):
+        S, w0, sol = _setup(D, d, divb, ncell, fname, precision=prec, generic=generic)
+        w = to_device(w0, sol)
+        out = torch_empty_like(w)
+        ref = S.rhs(w0, None, 0.0)
+        if prec == "fp32":
+            wm = means_to_device(w0, sol, S)
+            om = torch_empty_like(wm)
+            sol.rhs(w, wm, out, om)
+            from gpu_helpers import mean_rows
+            assert rel_err(om[:, : sol.ncell].cpu().numpy().T, ref[:, mean_rows(S)]) < 2e-5
+        else:
+            sol.rhs(w, None, out)
+        assert rel_err(from_device(out, sol), ref) < tol
+        assert sol.status() == 0
+
+
 @pytest.mark.parametrize("D,d,divb,ncell,fname", CASES)
 def test_rhs_fp64(D, d, divb, ncell, fname):
     S, w0, sol = _setup(D, d, divb, ncell, fname)
@@ -199,7 +225,7 @@ def test_rhs_fp32_form(D, d, divb, ncell, fname):
     assert rel_err(got, ref) < 2e-4
 
 
-@pytest.mark.parametrize("D,d,divb,ncell,fname", [CASES[0], CASES[2]])
+@pytest.mark.parametrize("D,d,divb,ncell,fname", [CASES[0], CASES[2], CASES[4]])
 def test_step_fp32_form(D, d, divb, ncell, fname):
     S, w0, sol = _setup(D, d, divb, ncell, fname, precision="fp32")
     w = to_device(w0, sol)
