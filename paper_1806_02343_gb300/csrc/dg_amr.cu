@@ -592,6 +592,31 @@ int build_amr(Ctx& c, const dg_mesh_desc* mesh) {
           ftab[(((size_t)ty * 2 + 1) * n + l) * QFP + p] = face_val(2 * a, sbR, l, p);
         }
     }
+    // normal component (axis a) of every LDF function on each type's two (sub-)faces
+    const int nd = g.ndiv;
+    std::vector<double> ntab((size_t)27 * 2 * nd * QFP, 0.0);
+    for (int ty = 0; ty < 27; ++ty) {
+      const int a = ty / 9, k = ty % 9;
+      const int sbL = (k >= 1 && k <= 4) ? k - 1 : -1, sbR = k >= 5 ? k - 5 : -1;
+      for (int sd = 0; sd < 2; ++sd) {
+        const int f = sd == 0 ? 2 * a + 1 : 2 * a, sb = sd == 0 ? sbL : sbR;
+        int others[2], no = 0;
+        for (int b = 0; b < D; ++b)
+          if (b != a) others[no++] = b;
+        for (int p = 0; p < Qf; ++p) {
+          double xi[3] = {0, 0, 0};
+          int pp = p;
+          for (int j = no - 1; j >= 0; --j) {
+            const double xf = x1[pp % g.nq1];
+            pp /= g.nq1;
+            xi[others[j]] = sb < 0 ? xf : 0.5 * (xf + (((sb >> j) & 1) ? 1.0 : -1.0));
+          }
+          xi[a] = (f & 1) ? 1.0 : -1.0;
+          for (int j = 0; j < nd; ++j)
+            ntab[(((size_t)ty * 2 + sd) * nd + j) * QFP + p] = B.eval(B.ldf[j][a], xi);
+        }
+      }
+    }
     std::vector<double> wf(Qf, 1.0);
     for (int p = 0; p < Qf; ++p)
       for (int k = 0, pp = p; k < D - 1; ++k, pp /= g.nq1) wf[p] *= w1[pp % g.nq1];
@@ -604,10 +629,14 @@ int build_amr(Ctx& c, const dg_mesh_desc* mesh) {
     if ((e = upload_vec(&h.bface, bface)) || (e = upload_vec(&h.bstart, bstart)) || (e = upload_vec(&h.btype, btype)))
       return e;
     if (c.p.precision == DG_PREC_FP32MIX) {
-      std::vector<float> a(ftab.begin(), ftab.end()), b(ctab.begin(), ctab.end());
-      if ((e = upload_vec((float**)&h.ftab, a)) || (e = upload_vec((float**)&h.ctab, b))) return e;
+      std::vector<float> a(ftab.begin(), ftab.end()), b(ctab.begin(), ctab.end()), nt(ntab.begin(), ntab.end());
+      if ((e = upload_vec((float**)&h.ftab, a)) || (e = upload_vec((float**)&h.ctab, b)) ||
+          (e = upload_vec((float**)&h.ntab, nt)))
+        return e;
     } else {
-      if ((e = upload_vec((double**)&h.ftab, ftab)) || (e = upload_vec((double**)&h.ctab, ctab))) return e;
+      if ((e = upload_vec((double**)&h.ftab, ftab)) || (e = upload_vec((double**)&h.ctab, ctab)) ||
+          (e = upload_vec((double**)&h.ntab, ntab)))
+        return e;
     }
     h.nblk = (int64_t)btype.size();
     h.fast = true;
@@ -618,19 +647,21 @@ int build_amr(Ctx& c, const dg_mesh_desc* mesh) {
 OctPow<float> oct_pow32(const Ctx& c) {
   const AmrHost& h = c.amr;
   return OctPow<float>{h.fL, h.fR, h.fmeta, h.cstart, h.centry, h.dxc, h.bface, h.bstart, h.btype,
-                       (const float*)h.ftab, (const float*)h.ctab, c.g.ncell, c.g.stride, h.nblk};
+                       (const float*)h.ftab, (const float*)h.ctab, (const float*)h.ntab, c.g.ncell, c.g.stride,
+                       h.nblk};
 }
 OctPow<double> oct_pow64(const Ctx& c) {
   const AmrHost& h = c.amr;
   return OctPow<double>{h.fL, h.fR, h.fmeta, h.cstart, h.centry, h.dxc, h.bface, h.bstart, h.btype,
-                        (const double*)h.ftab, (const double*)h.ctab, c.g.ncell, c.g.stride, h.nblk};
+                        (const double*)h.ftab, (const double*)h.ctab, (const double*)h.ntab, c.g.ncell,
+                        c.g.stride, h.nblk};
 }
 
 void free_amr(Ctx& c) {
   AmrHost& h = c.amr;
   void* ptrs[] = {h.fL,     h.fR,     h.fmeta,    h.cstart,   h.centry,   h.dxc,    h.Psub64, h.Lsub64,
                   h.Psub32, h.Lsub32, h.Psub64p, h.Lsub64p, h.Psub32p, h.Lsub32p, h.groups, h.lev_dev,
-                  h.bface,  h.bstart, h.btype,    h.ftab,     h.ctab};
+                  h.bface,  h.bstart, h.btype,    h.ftab,     h.ctab,     h.ntab};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h = AmrHost();
@@ -682,12 +713,28 @@ void launch_amr_operator(const Ctx& c, const Tables<T>& tb, const T* w, T* fbuf,
   }
 }
 
+// the Powell face jumps by the specialised kernel where the context has it
+bool divb_list_fast(const Ctx& c, const float* w, float* jbuf, cudaStream_t st) {
+  if (!c.amr.fast) return false;
+  if (c.fast == 11) launch_divb_list_pow<float, 1>(oct_pow32(c), w, jbuf, st);
+  else if (c.fast == 12) launch_divb_list_pow<float, 2>(oct_pow32(c), w, jbuf, st);
+  else return false;
+  return true;
+}
+bool divb_list_fast(const Ctx& c, const double* w, double* jbuf, cudaStream_t st) {
+  if (!c.amr.fast) return false;
+  if (c.fast == 21) launch_divb_list_pow<double, 1>(oct_pow64(c), w, jbuf, st);
+  else if (c.fast == 22) launch_divb_list_pow<double, 2>(oct_pow64(c), w, jbuf, st);
+  else return false;
+  return true;
+}
+
 template <typename T>
 void launch_amr_dt(const Ctx& c, const Tables<T>& tb, const T* w, const double* wmean, T* jbuf,
                    const dg_mhd_params& p, DevScalars* sc, cudaStream_t st) {
   const Geom& g = c.g;
   const AmrDev<T> am = amr_dev<T>(c);
-  if (!g.glm) {
+  if (!g.glm && !divb_list_fast(c, w, jbuf, st)) {
     const int64_t np = am.nface * g.Qf;
     k_divb_list<T><<<(unsigned)((np + 127) / 128), 128, 0, st>>>(g, tb, am, w, jbuf);
   }

@@ -211,6 +211,7 @@ struct AmrHost {
   int64_t nblk = 0;
   void* ftab = nullptr;
   void* ctab = nullptr;
+  void* ntab = nullptr;
   // the last regrid plan (6 ints per new leaf) and a hash of the marks it was made from
   uint64_t plan_hash = 0;
   std::vector<int32_t> plan;

@@ -150,9 +150,12 @@ struct OctPow {
   const int32_t* btype;
   const T* ftab;
   const T* ctab;
+  const T* ntab;  // [type][side][NDIV][QFP]: normal component of each LDF function on the side's (sub-)face
   int64_t ncell, stride;
   int64_t nblk;
 };
+template <typename T, int DEG>
+void launch_divb_list_pow(const OctPow<T>& o, const T* w, T* jbuf, cudaStream_t st);
 template <typename T, int DEG>
 void launch_list_pow(const OctPow<T>& o, double gamma, const T* w, T* F, T* out, const T* w0, double ca, double cb,
                      int combine, const DevScalars* sc, const double* wmean, const double* w0mean, double* outmean,

@@ -1178,6 +1178,61 @@ __global__ void __launch_bounds__(NT) k_divb_face_pow(const FastGeom g, const T*
   });
 }
 
+
+// Face jumps of the normal field on an octree (the Powell timestep, eq.
+// powell_dt), per face block of one type: the density traces through the
+// type's trace tables, the normal field through the LDF functions' normal
+// components on the type's (sub-)faces (ntab); layout of the generic k_divb_list.
+template <typename T, int DEG>
+__global__ void __launch_bounds__(NT) k_divb_list_pow(const OctPow<T> o, const T* __restrict__ w,
+                                                      T* __restrict__ jbuf) {
+  constexpr int N = FastDims<DEG>::N, QF = FastDims<DEG>::QF, NDIV = PowDims<DEG>::NDIV, NRD = N + NDIV;
+  constexpr int QFP = FaceTabs<T, DEG>::QFP;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* TT = reinterpret_cast<T*>(smraw);  // [2][N][QFP] density trace tables
+  T* TN = TT + 2 * N * QFP;             // [2][NDIV][QFP] normal LDF components
+  T* XL = TN + 2 * NDIV * QFP;          // [NRD][TC]
+  T* XR = XL + NRD * TC;                // [NRD][TC]
+  const PowTabs<T, DEG>& pt = pow_tabs<T, DEG>();
+  const int t = threadIdx.x;
+  const int f = t & (TC - 1);
+  const int v = t >> 5;
+  const int bt = o.btype[blockIdx.x];
+  const int type = bt & 255, cnt = bt >> 8;
+  const bool live = f < cnt;
+  const int64_t fid = live ? o.bface[o.bstart[blockIdx.x] + f] : 0;
+  const int64_t cL = live ? o.fL[fid] : 0, cR = live ? o.fR[fid] : 0;
+  const int64_t S = o.stride;
+  for (int i = t; i < 2 * N * QFP; i += NT) TT[i] = o.ftab[(size_t)type * 2 * N * QFP + i];
+  for (int i = t; i < 2 * NDIV * QFP; i += NT) TN[i] = o.ntab[(size_t)type * 2 * NDIV * QFP + i];
+  for (int r = v; r < NRD; r += 9) {
+    const int64_t row = r < N ? r : 5 * N + (r - N);
+    XL[r * TC + f] = live ? w[row * S + cL] : (r == 0 ? T(1) : T(0));
+    XR[r * TC + f] = live ? w[row * S + cR] : (r == 0 ? T(1) : T(0));
+  }
+  __syncthreads();
+  for (int p = v; p < QF; p += 9) {
+    T rL = T(0), rR = T(0), bL = T(0), bR = T(0);
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      rL = fma_rn(XL[l * TC + f], TT[l * QFP + p], rL);
+      rR = fma_rn(XR[l * TC + f], TT[(N + l) * QFP + p], rR);
+    }
+#pragma unroll
+    for (int j = 0; j < NDIV; ++j) {
+      bL = fma_rn(XL[(N + j) * TC + f], TN[j * QFP + p], bL);
+      bR = fma_rn(XR[(N + j) * TC + f], TN[(NDIV + j) * QFP + p], bR);
+    }
+    const T bF = bn_face(rL, rR, bL, bR);
+    const T wp = pt.wf[p];
+    if (live) {
+      T* q = jbuf + (fid * QF + p) * 2;
+      q[0] = wp * (bF > bL ? bF - bL : bL - bF);
+      q[1] = wp * (bF > bR ? bF - bR : bR - bF);
+    }
+  }
+}
+
 template <typename T>
 void set_smem_attr(const void* fn, size_t bytes) {
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -1301,6 +1356,13 @@ void launch_list_pow(const OctPow<T>& o, double gamma, const T* w, T* F, T* out,
 }
 
 template <typename T, int DEG>
+void launch_divb_list_pow(const OctPow<T>& o, const T* w, T* jbuf, cudaStream_t st) {
+  constexpr int N = FastDims<DEG>::N, NDIV = PowDims<DEG>::NDIV, QFP = FaceTabs<T, DEG>::QFP;
+  const size_t sm = (size_t)(2 * N * QFP + 2 * NDIV * QFP + 2 * (N + NDIV) * TC) * sizeof(T);
+  if (o.nblk > 0) k_divb_list_pow<T, DEG><<<(unsigned)o.nblk, NT, sm, st>>>(o, w, jbuf);
+}
+
+template <typename T, int DEG>
 int fast_to_constant(const FastAll<T, DEG>& tabs) {
   if constexpr (FastConst<T, DEG>::on) return FastConst<T, DEG>::upload(tabs) == cudaSuccess ? 0 : -3;
   return 0;
@@ -1321,7 +1383,8 @@ int fast_to_constant(const FastAll<T, DEG>& tabs) {
   template void launch_divb_face_pow<T, DEG>(const FastGeom&, const T*, T*, cudaStream_t);                    \
   template void launch_list_pow<T, DEG>(const OctPow<T>&, double, const T*, T*, T*, const T*, double, double, \
                                         int, const DevScalars*, const double*, const double*, double*, double, \
-                                        cudaStream_t);
+                                        cudaStream_t);                                                        \
+  template void launch_divb_list_pow<T, DEG>(const OctPow<T>&, const T*, T*, cudaStream_t);
 INSTF(DG_FAST_T, DG_FAST_DEG)
 
 }  // namespace dgmhd

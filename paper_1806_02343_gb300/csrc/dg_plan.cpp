@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <numeric>
+#include <thread>
 #include <utility>
 
 #include "../../include/dg_mhd.h"
@@ -173,13 +174,10 @@ int octree_faces(int D, int64_t N, const int8_t* level, const int32_t* ijk, Mort
   auto holds = [&](int64_t q, uint64_t code) {
     return mi.start[q] <= code && code - mi.start[q] < (1ull << (D * (mi.R - mi.lev[q])));
   };
-  fL.clear();
-  fR.clear();
-  fmeta.clear();
-  fL.reserve((size_t)(N * D + N / 2));
-  fR.reserve((size_t)(N * D + N / 2));
-  fmeta.reserve((size_t)(N * D + N / 2));
-  for (int64_t cidx = 0; cidx < N; ++cidx) {
+  // the faces a leaf lists: same-level faces on its -a sides, coarse-fine
+  // faces on the sides with a coarser neighbour (checking the 2:1 rule)
+  auto faces_of_leaf = [&](int64_t cidx, std::vector<int32_t>& fL_, std::vector<int32_t>& fR_,
+                           std::vector<int32_t>& fm_) -> int {
     const int l = level[cidx];
     const int32_t n = 1 << l;
     const int32_t* k = &ijk[cidx * D];
@@ -217,9 +215,9 @@ int octree_faces(int D, int64_t N, const int8_t* level, const int32_t* ijk, Mort
         const int lq = mi.lev[q];
         if (lq == l) {  // same level: listed once, by the right cell
           if (s < 0) {
-            fL.push_back(mi.leaf(q));
-            fR.push_back((int32_t)cidx);
-            fmeta.push_back(a);
+            fL_.push_back(mi.leaf(q));
+            fR_.push_back((int32_t)cidx);
+            fm_.push_back(a);
           }
           continue;
         }
@@ -227,13 +225,13 @@ int octree_faces(int D, int64_t N, const int8_t* level, const int32_t* ijk, Mort
           int sub = 0;
           for (int j = 0; j < no; ++j) sub |= (int)(k[others[j]] & 1) << j;
           if (s < 0) {
-            fL.push_back(mi.leaf(q));
-            fR.push_back((int32_t)cidx);
-            fmeta.push_back(a | (1 << 2) | (sub << 4));
+            fL_.push_back(mi.leaf(q));
+            fR_.push_back((int32_t)cidx);
+            fm_.push_back(a | (1 << 2) | (sub << 4));
           } else {
-            fL.push_back((int32_t)cidx);
-            fR.push_back(mi.leaf(q));
-            fmeta.push_back(a | (2 << 2) | (sub << 4));
+            fL_.push_back((int32_t)cidx);
+            fR_.push_back(mi.leaf(q));
+            fm_.push_back(a | (2 << 2) | (sub << 4));
           }
           continue;
         }
@@ -250,6 +248,48 @@ int octree_faces(int D, int64_t N, const int8_t* level, const int32_t* ijk, Mort
         }
       }
     }
+      return DG_OK;
+  };
+  // The leaves are split into contiguous chunks searched by parallel host
+  // threads; each chunk lists its faces in leaf order and the chunks are
+  // concatenated in order, so the lists do not depend on the thread count.
+  struct Part {
+    std::vector<int32_t> L, R, M;
+    int err = DG_OK;
+  };
+  const int64_t kChunk = 1 << 16;
+  const int nth = (int)std::max<int64_t>(
+      1, std::min<int64_t>({(int64_t)std::max(1u, std::thread::hardware_concurrency()), 16, (N + kChunk - 1) / kChunk}));
+  std::vector<Part> parts((size_t)nth);
+  auto work = [&](int t) {
+    Part& P = parts[(size_t)t];
+    const int64_t c0 = N * t / nth, c1 = N * (t + 1) / nth;
+    P.L.reserve((size_t)((c1 - c0) * D + (c1 - c0) / 2));
+    P.R.reserve(P.L.capacity());
+    P.M.reserve(P.L.capacity());
+    for (int64_t cidx = c0; cidx < c1 && P.err == DG_OK; ++cidx) P.err = faces_of_leaf(cidx, P.L, P.R, P.M);
+  };
+  {
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nth; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto& th : pool) th.join();
+  }
+  size_t total = 0;
+  for (const Part& P : parts) {
+    if (P.err != DG_OK) return P.err;
+    total += P.L.size();
+  }
+  fL.clear();
+  fR.clear();
+  fmeta.clear();
+  fL.reserve(total);
+  fR.reserve(total);
+  fmeta.reserve(total);
+  for (const Part& P : parts) {
+    fL.insert(fL.end(), P.L.begin(), P.L.end());
+    fR.insert(fR.end(), P.R.begin(), P.R.end());
+    fmeta.insert(fmeta.end(), P.M.begin(), P.M.end());
   }
   // per-cell entries in face order (counting sort)
   const int64_t nf = (int64_t)fL.size();
