@@ -421,7 +421,8 @@ __global__ void k_dt_list(Geom g, Tables<T> tb, AmrDev<T> am, const T* __restric
         double area = 1.0;
         for (int a = 0; a < g.D - 1; ++a) area *= 0.5 * dxf;
         double js = 0.0;
-        for (int q = 0; q < g.Qf; ++q) js += (double)jbuf[(f * g.Qf + q) * 2 + (ent & 1)];
+        const int nq = g.jq ? g.jq : g.Qf;
+        for (int q = 0; q < nq; ++q) js += (double)jbuf[(f * nq + q) * 2 + (ent & 1)];
         acc += area * js;
       }
       double divb = acc;
@@ -732,9 +733,11 @@ bool divb_list_fast(const Ctx& c, const double* w, double* jbuf, cudaStream_t st
 template <typename T>
 void launch_amr_dt(const Ctx& c, const Tables<T>& tb, const T* w, const double* wmean, T* jbuf,
                    const dg_mhd_params& p, DevScalars* sc, cudaStream_t st) {
-  const Geom& g = c.g;
+  Geom g = c.g;
   const AmrDev<T> am = amr_dev<T>(c);
-  if (!g.glm && !divb_list_fast(c, w, jbuf, st)) {
+  if (!g.glm && divb_list_fast(c, w, jbuf, st)) {
+    g.jq = 1;  // two sums per face
+  } else if (!g.glm) {
     const int64_t np = am.nface * g.Qf;
     k_divb_list<T><<<(unsigned)((np + 127) / 128), 128, 0, st>>>(g, tb, am, w, jbuf);
   }

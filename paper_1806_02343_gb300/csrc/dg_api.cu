@@ -907,12 +907,15 @@ int dt_pass(Ctx& c, const void* w, const double* wmean, double* dt_out, cudaStre
     return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
   }
   c.prof.begin(2, st);
+  // the specialised Powell jump kernel stores two sums per face (gj.jq = 1)
+  Geom gj = g;
+  if (!g.glm && divb_face_fast(c, w, st)) gj.jq = 1;
   if (fp32(c)) {
-    if (!g.glm && !divb_face_fast(c, w, st)) launch_divb_face<float>(g, c.t32, (const float*)w, c.face_buf32, st);
-    launch_dt<float>(g, c.t32, (const float*)w, wmean, c.face_buf32, c.p, c.sc, dt_out, st);
+    if (!g.glm && !gj.jq) launch_divb_face<float>(g, c.t32, (const float*)w, c.face_buf32, st);
+    launch_dt<float>(gj, c.t32, (const float*)w, wmean, c.face_buf32, c.p, c.sc, dt_out, st);
   } else {
-    if (!g.glm && !divb_face_fast(c, w, st)) launch_divb_face<double>(g, c.t64, (const double*)w, c.face_buf, st);
-    launch_dt<double>(g, c.t64, (const double*)w, nullptr, c.face_buf, c.p, c.sc, dt_out, st);
+    if (!g.glm && !gj.jq) launch_divb_face<double>(g, c.t64, (const double*)w, c.face_buf, st);
+    launch_dt<double>(gj, c.t64, (const double*)w, nullptr, c.face_buf, c.p, c.sc, dt_out, st);
   }
   c.prof.end(2, st);
   // k_dt_init + k_dt + k_dt_finalize (FP32 form: k_dt32 + k_dt32_refine in place

@@ -57,6 +57,9 @@ struct Geom {
   double dx, gamma;
   // cells that count in the timestep minimum (a partition's owned cells; NULL: all)
   const uint8_t* owned = nullptr;
+  // points per face in the Powell jump buffer of the timestep: Qf (0), or 1
+  // where the specialised kernels store each face's two sums
+  int jq = 0;
 };
 
 // Sizes fixed at compile time (3D, degree DEG >= 0, GLM or Powell): the

@@ -1122,10 +1122,11 @@ __global__ void __launch_bounds__(NTP, 3) k_cell_list_pow(const OctPow<T> o, T g
 }
 
 // Face jumps of the normal field for the Powell timestep (eq. powell_dt):
-// per face point of the faces normal to each axis (right cell = this
-// block's cell), B^n_F from the two traces (eq. bxface-average) and the
-// weighted distances to each side's own normal trace. Staged like the face
-// pass: the density and LDF rows of the left and own cells.
+// per face normal to each axis (right cell = this block's cell), B^n_F from
+// the two traces (eq. bxface-average) at every point and the weighted
+// distances to each side's own normal trace, summed over the face's points:
+// jbuf[(axis * ncell + cell) * 2 + side] (side 0: the left cell). Staged like
+// the face pass: the density and LDF rows of the left and own cells.
 template <typename T, int DEG>
 __global__ void __launch_bounds__(NT) k_divb_face_pow(const FastGeom g, const T* __restrict__ w,
                                                       T* __restrict__ jbuf) {
@@ -1133,6 +1134,7 @@ __global__ void __launch_bounds__(NT) k_divb_face_pow(const FastGeom g, const T*
   extern __shared__ __align__(16) unsigned char smraw[];
   T* XL = reinterpret_cast<T*>(smraw);  // [NRD][TC] left cells
   T* XR = XL + NRD * TC;                // [NRD][TC] own cells
+  T* JS = XR + NRD * TC;                // [2][QF][TC] weighted jumps per point
   const PowTabs<T, DEG>& pt = pow_tabs<T, DEG>();
   const int t = threadIdx.x;
   const int f = t & (TC - 1);
@@ -1169,12 +1171,19 @@ __global__ void __launch_bounds__(NT) k_divb_face_pow(const FastGeom g, const T*
       }
       const T bF = bn_face(rL, rR, bL, bR);
       const T wp = pt.wf[p];
-      if (live) {
-        T* o = jbuf + (((int64_t)A * g.ncell + c) * QF + p) * 2;
-        o[0] = wp * (bF > bL ? bF - bL : bL - bF);
-        o[1] = wp * (bF > bR ? bF - bR : bR - bF);
-      }
+      JS[(0 * QF + p) * TC + f] = wp * (bF > bL ? bF - bL : bL - bF);
+      JS[(1 * QF + p) * TC + f] = wp * (bF > bR ? bF - bR : bR - bF);
     });
+    __syncthreads();
+    // the face's two sums over its points, in point order
+    if (t < 2 * TC) {
+      const int sd = t / TC, ff = t % TC;
+      const int64_t cc = (int64_t)blockIdx.x * TC + ff;
+      T sum = T(0);
+#pragma unroll
+      for (int p = 0; p < QF; ++p) sum += JS[(sd * QF + p) * TC + ff];
+      if (cc < g.ncell) jbuf[((int64_t)A * g.ncell + cc) * 2 + sd] = sum;
+    }
   });
 }
 
@@ -1182,7 +1191,8 @@ __global__ void __launch_bounds__(NT) k_divb_face_pow(const FastGeom g, const T*
 // Face jumps of the normal field on an octree (the Powell timestep, eq.
 // powell_dt), per face block of one type: the density traces through the
 // type's trace tables, the normal field through the LDF functions' normal
-// components on the type's (sub-)faces (ntab); layout of the generic k_divb_list.
+// components on the type's (sub-)faces (ntab); each face's two sums over its
+// points at jbuf[face * 2 + side].
 template <typename T, int DEG>
 __global__ void __launch_bounds__(NT) k_divb_list_pow(const OctPow<T> o, const T* __restrict__ w,
                                                       T* __restrict__ jbuf) {
@@ -1193,6 +1203,7 @@ __global__ void __launch_bounds__(NT) k_divb_list_pow(const OctPow<T> o, const T
   T* TN = TT + 2 * N * QFP;             // [2][NDIV][QFP] normal LDF components
   T* XL = TN + 2 * NDIV * QFP;          // [NRD][TC]
   T* XR = XL + NRD * TC;                // [NRD][TC]
+  T* JS = XR + NRD * TC;                // [2][QF][TC] weighted jumps per point
   const PowTabs<T, DEG>& pt = pow_tabs<T, DEG>();
   const int t = threadIdx.x;
   const int f = t & (TC - 1);
@@ -1225,11 +1236,16 @@ __global__ void __launch_bounds__(NT) k_divb_list_pow(const OctPow<T> o, const T
     }
     const T bF = bn_face(rL, rR, bL, bR);
     const T wp = pt.wf[p];
-    if (live) {
-      T* q = jbuf + (fid * QF + p) * 2;
-      q[0] = wp * (bF > bL ? bF - bL : bL - bF);
-      q[1] = wp * (bF > bR ? bF - bR : bR - bF);
-    }
+    JS[(0 * QF + p) * TC + f] = wp * (bF > bL ? bF - bL : bL - bF);
+    JS[(1 * QF + p) * TC + f] = wp * (bF > bR ? bF - bR : bR - bF);
+  }
+  __syncthreads();
+  if (t < 2 * TC) {
+    const int sd = t / TC, ff = t % TC;
+    T sum = T(0);
+#pragma unroll
+    for (int p = 0; p < QF; ++p) sum += JS[(sd * QF + p) * TC + ff];
+    if (ff < cnt) jbuf[(int64_t)o.bface[o.bstart[blockIdx.x] + ff] * 2 + sd] = sum;
   }
 }
 
@@ -1330,7 +1346,7 @@ void launch_cell_pow(const FastAll<T, DEG>&, const FastGeom& g, const T* w, cons
 template <typename T, int DEG>
 void launch_divb_face_pow(const FastGeom& g, const T* w, T* jbuf, cudaStream_t st) {
   const unsigned nb = (unsigned)((g.ncell + TC - 1) / TC);
-  const size_t sm = (size_t)2 * (FastDims<DEG>::N + PowDims<DEG>::NDIV) * TC * sizeof(T);
+  const size_t sm = (size_t)(2 * (FastDims<DEG>::N + PowDims<DEG>::NDIV) + 2 * FastDims<DEG>::QF) * TC * sizeof(T);
   k_divb_face_pow<T, DEG><<<nb, NT, sm, st>>>(g, w, jbuf);
 }
 
@@ -1358,7 +1374,8 @@ void launch_list_pow(const OctPow<T>& o, double gamma, const T* w, T* F, T* out,
 template <typename T, int DEG>
 void launch_divb_list_pow(const OctPow<T>& o, const T* w, T* jbuf, cudaStream_t st) {
   constexpr int N = FastDims<DEG>::N, NDIV = PowDims<DEG>::NDIV, QFP = FaceTabs<T, DEG>::QFP;
-  const size_t sm = (size_t)(2 * N * QFP + 2 * NDIV * QFP + 2 * (N + NDIV) * TC) * sizeof(T);
+  const size_t sm = (size_t)(2 * N * QFP + 2 * NDIV * QFP + 2 * (N + NDIV) * TC + 2 * FastDims<DEG>::QF * TC) *
+                    sizeof(T);
   if (o.nblk > 0) k_divb_list_pow<T, DEG><<<(unsigned)o.nblk, NT, sm, st>>>(o, w, jbuf);
 }
 

@@ -581,11 +581,12 @@ __device__ double dt_cell64(const Geom& g, const Tables<T>& tb, const T* __restr
   if (!g.glm) {
     // (1/V_K) oint |B^n_F - B^n_K| dS: sum this cell's 2D faces in fixed order
     double acc = 0.0;
+    const int nq = g.jq ? g.jq : g.Qf;
     for (int a = 0; a < g.D; ++a) {
       const int64_t cp = neighbour(g, c, a, +1);
-      for (int q = 0; q < g.Qf; ++q) {
-        acc += (double)jbuf[(((int64_t)a * g.ncell + c) * g.Qf + q) * 2 + 1];   // minus face: R side
-        acc += (double)jbuf[(((int64_t)a * g.ncell + cp) * g.Qf + q) * 2 + 0];  // plus face: L side
+      for (int q = 0; q < nq; ++q) {
+        acc += (double)jbuf[(((int64_t)a * g.ncell + c) * nq + q) * 2 + 1];   // minus face: R side
+        acc += (double)jbuf[(((int64_t)a * g.ncell + cp) * nq + q) * 2 + 0];  // plus face: L side
       }
     }
     double meas = 1.0;
@@ -691,11 +692,12 @@ __device__ float dt_cell32(const Geom& g, const Tables<float>& tb, const float* 
   if (!g.glm) {
     // (1/V_K) oint |B^n_F - B^n_K| dS: this cell's 2D faces in fixed order
     float acc = 0.f;
+    const int nq = g.jq ? g.jq : g.Qf;
     for (int a = 0; a < g.D; ++a) {
       const int64_t cp = neighbour(g, c, a, +1);
-      for (int q = 0; q < g.Qf; ++q) {
-        acc += jbuf[(((int64_t)a * g.ncell + c) * g.Qf + q) * 2 + 1];
-        acc += jbuf[(((int64_t)a * g.ncell + cp) * g.Qf + q) * 2 + 0];
+      for (int q = 0; q < nq; ++q) {
+        acc += jbuf[(((int64_t)a * g.ncell + c) * nq + q) * 2 + 1];
+        acc += jbuf[(((int64_t)a * g.ncell + cp) * nq + q) * 2 + 0];
       }
     }
     // face measure (dx/2)^(D-1) over the volume dx^D: 2^(1-D) / dx
