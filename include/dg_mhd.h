@@ -269,7 +269,9 @@ int dg_mhd_limiter_counts(dg_mhd_ctx* ctx, int64_t* passes, int64_t* flagged, in
  * of the 8 MHD variables (LDF B mapped exactly to per-component Legendre
  * coefficients), variable v divided by |mean_v| + max_nb |mean_nb,v - mean_v|
  * + 1e-12, then rho_nb/rho - 1 for neighbours -x, +x, -y, +y (, -z, +z), then
- * for each direction the 8 degree-1 coefficients divided by M~ dx.
+ * for each direction the 8 degree-1 coefficients divided by M~ dx. Octree
+ * meshes: the neighbour mean on a side is the average of the leaves across it
+ * (as in the octree TVB procedure) and dx the leaf's own size.
  * theta (DEVICE, FP32, flat): W1[64][nin], b1[64], W2[64][64], b2[64],
  * w3[64], b3. */
 /* X[cell*ldx + k] (DEVICE float, ldx >= nin; padding written as 0). */

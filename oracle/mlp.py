@@ -13,7 +13,9 @@ in the paper; the choices are:
   s_v = |mean_v| + max over the 2D face neighbours |mean_nb,v - mean_v| + 1e-12,
   then the neighbour density ratios rho_nb/rho - 1 in the order
   -x, +x, -y, +y, -z, +z, then for each direction a and variable v the
-  degree-1 coefficient along a divided by M~ dx (the TVB slope scale);
+  degree-1 coefficient along a divided by M~ dx (the TVB slope scale); on an
+  octree the neighbour mean of a side is the average of the leaves across it
+  and dx the leaf's own size;
 * network: in -> 64 -> 64 -> 1, ReLU hidden layers, sigmoid output;
 * loss: mean binary cross-entropy; optimiser: Adam.
 Weights are one flat vector: W1[64][in], b1[64], W2[64][64], b2[64], w3[64], b3.
@@ -84,19 +86,38 @@ def coefficients(S, w):
     return a
 
 
+def side_means(S, m):
+    """Neighbour means per cell, axis and side (0: -axis, 1: +axis). Uniform
+    mesh: the face neighbour; octree: the average of the leaves across the
+    side (one of the same level or coarser, or the finer ones), the neighbour
+    mean the octree TVB procedure uses (limiter.mean_differences)."""
+    if not hasattr(S, "faces"):
+        return np.stack([np.stack([m[S.nbr_minus[ax]], m[S.nbr_plus[ax]]], 1) for ax in range(S.D)], 1)
+    acc = np.zeros((S.C, S.D, 2, m.shape[1]))
+    cnt = np.zeros((S.C, S.D, 2))
+    for cL, cR, ax, kind, sub in S.faces:
+        acc[cR, ax, 0] += m[cL]     # cR sees cL on its -axis side
+        cnt[cR, ax, 0] += 1
+        acc[cL, ax, 1] += m[cR]
+        cnt[cL, ax, 1] += 1
+    return acc / cnt[..., None]
+
+
 def features(S, w):
     a = coefficients(S, w)
     m = S.means(w)[:, :8]
+    nb = side_means(S, m)
     dmax = np.zeros_like(m)
     ratios = []
     for ax in range(S.D):
-        for nbr in (S.nbr_minus[ax], S.nbr_plus[ax]):
-            dmax = np.maximum(dmax, np.abs(m[nbr] - m))
-            ratios.append(m[nbr, 0] / m[:, 0] - 1.0)
+        for side in (0, 1):
+            dmax = np.maximum(dmax, np.abs(nb[:, ax, side] - m))
+            ratios.append(nb[:, ax, side, 0] / m[:, 0] - 1.0)
     s = np.abs(m) + dmax + 1e-12
     X = (a / s[:, :, None]).reshape(S.C, -1)
     deg1 = [S.modes.index(tuple(1 if i == ax else 0 for i in range(S.D))) for ax in range(S.D)]
-    sl = np.concatenate([a[:, :, deg1[ax]] for ax in range(S.D)], -1) / (S.P.Mtilde * S.dx)
+    dx = S.dxc[:, None] if hasattr(S, "faces") else S.dx
+    sl = np.concatenate([a[:, :, deg1[ax]] for ax in range(S.D)], -1) / (S.P.Mtilde * dx)
     return np.concatenate([X, np.stack(ratios, -1), sl], -1)
 
 

@@ -927,8 +927,7 @@ int dt_pass(Ctx& c, const void* w, const double* wmean, double* dt_out, cudaStre
 int limit_pass(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t st) {
   if (c.p.limiter == DG_LIMIT_OFF && !c.p.positivity) return DG_OK;
   // octree meshes: TVB with neighbour means across coarse-fine faces; the
-  // learned detector's features assume uniform neighbours
-  if (c.amr.on && c.p.limiter == DG_LIMIT_MLP) return DG_E_UNSUPPORTED;
+  // learned detector reads the same side averages as its neighbour means
   return run_limiter(c, w, wmean, troubled, st);
 }
 

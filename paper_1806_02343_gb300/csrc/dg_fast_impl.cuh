@@ -1121,6 +1121,32 @@ __global__ void __launch_bounds__(NTP, 3) k_cell_list_pow(const OctPow<T> o, T g
                     ca32, cb32, cmode, sc, wmean, w0mean, outmean);
 }
 
+// Stages the density and LDF rows (N + NDIV) of cell cb into XB (with BOTH)
+// and of cell ca into XA, thread (v, f) rows v + 9 i; every load is issued
+// before the first shared-memory store. Absent faces stage rho = 1, zeros.
+template <typename T, int DEG, bool BOTH>
+__device__ __forceinline__ void stage_rd(const T* __restrict__ w, int64_t S, int64_t cb, int64_t ca, bool live,
+                                         int v, int f, T* XB, T* XA) {
+  constexpr int N = FastDims<DEG>::N, NRD = N + PowDims<DEG>::NDIV, PER = (NRD + 8) / 9;
+  T a[PER], b[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int r = v + 9 * i;
+    const int64_t row = r < N ? r : 5 * N + (r - N);
+    const bool ok = live && r < NRD;
+    if (BOTH) b[i] = ok ? w[row * S + cb] : (r == 0 ? T(1) : T(0));
+    a[i] = ok ? w[row * S + ca] : (r == 0 ? T(1) : T(0));
+  }
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int r = v + 9 * i;
+    if (r < NRD) {
+      if (BOTH) XB[r * TC + f] = b[i];
+      XA[r * TC + f] = a[i];
+    }
+  }
+}
+
 // Face jumps of the normal field for the Powell timestep (eq. powell_dt):
 // per face normal to each axis (right cell = this block's cell), B^n_F from
 // the two traces (eq. bxface-average) at every point and the weighted
@@ -1148,11 +1174,7 @@ __global__ void __launch_bounds__(NT) k_divb_face_pow(const FastGeom g, const T*
     const FaceTabs<T, DEG>& tb = FastConst<T, DEG>::get().face[A];
     const int64_t cl = live ? nbr(g, kc, A, -1) : 0;
     if (A > 0) __syncthreads();  // the previous axis is done with XL
-    for (int r = v; r < NRD; r += 9) {
-      const int64_t row = r < N ? r : 5 * N + (r - N);
-      if (A == 0) XR[r * TC + f] = live ? w[row * S + c] : (r == 0 ? T(1) : T(0));
-      XL[r * TC + f] = live ? w[row * S + cl] : (r == 0 ? T(1) : T(0));
-    }
+    stage_rd<T, DEG, A == 0>(w, S, c, cl, live, v, f, XR, XL);
     __syncthreads();
     // face point P on warp P mod 9: compile-time table offsets (constant operands)
     static_for<QF>([&](auto PI) {
@@ -1216,11 +1238,7 @@ __global__ void __launch_bounds__(NT) k_divb_list_pow(const OctPow<T> o, const T
   const int64_t S = o.stride;
   for (int i = t; i < 2 * N * QFP; i += NT) TT[i] = o.ftab[(size_t)type * 2 * N * QFP + i];
   for (int i = t; i < 2 * NDIV * QFP; i += NT) TN[i] = o.ntab[(size_t)type * 2 * NDIV * QFP + i];
-  for (int r = v; r < NRD; r += 9) {
-    const int64_t row = r < N ? r : 5 * N + (r - N);
-    XL[r * TC + f] = live ? w[row * S + cL] : (r == 0 ? T(1) : T(0));
-    XR[r * TC + f] = live ? w[row * S + cR] : (r == 0 ? T(1) : T(0));
-  }
+  stage_rd<T, DEG, true>(w, S, cR, cL, live, v, f, XR, XL);
   __syncthreads();
   for (int p = v; p < QF; p += 9) {
     T rL = T(0), rR = T(0), bL = T(0), bR = T(0);

@@ -113,6 +113,51 @@ struct GlobalSrc {
     const int64_t cn = nbc(g, c, a, s ? 1 : -1);
     for (int k = 0; k < 8; ++k) raw[k] = (float)w[(int64_t)mrow(g, k) * g.stride + cn];
   }
+  __device__ float imdx(const MlpTabs& mt) const { return mt.inv_mdx; }
+};
+
+// Octree meshes (the face lists of dg_amr.cuh): the neighbour mean on side
+// (a, s) is the average of the leaves across that side (one of the same level
+// or coarser, or the 2^(D-1) finer ones), as the octree TVB procedure reads
+// it; the slope scale is the leaf's own M~ dx_K. A side without a leaf (the
+// edge of a partition's local mesh) reads the cell's own means.
+struct AmrFeat {
+  const int32_t* cstart;
+  const int32_t* centry;
+  const int32_t* fmeta;
+  const int32_t* fL;
+  const int32_t* fR;
+  const double* dxc;
+  double dxmin;  // the mesh's smallest cell (the one inv_mdx was made with)
+  int on;
+};
+
+template <typename T>
+struct AmrSrc {
+  const Geom& g;
+  const T* w;
+  int64_t c;
+  const AmrFeat& af;
+  __device__ float row(int r) const { return (float)w[(int64_t)r * g.stride + c]; }
+  __device__ void nbraw(int a, int s, float* raw) const {
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int cnt = 0;
+    for (int e = af.cstart[c]; e < af.cstart[c + 1]; ++e) {
+      const int ent = af.centry[e];
+      const int f = ent >> 1, side = ent & 1;  // side 0: this cell is the face's left cell (its +a side)
+      if ((af.fmeta[f] & 3) != a || side != (s ? 0 : 1)) continue;
+      const int64_t cn = side == 0 ? af.fR[f] : af.fL[f];
+      for (int k = 0; k < 8; ++k) acc[k] += (float)w[(int64_t)mrow(g, k) * g.stride + cn];
+      ++cnt;
+    }
+    if (cnt == 0) {
+      for (int k = 0; k < 8; ++k) raw[k] = (float)w[(int64_t)mrow(g, k) * g.stride + c];
+      return;
+    }
+    const float inv = 1.f / (float)cnt;  // 1 or 2^(D-1): exact
+    for (int k = 0; k < 8; ++k) raw[k] = acc[k] * inv;
+  }
+  __device__ float imdx(const MlpTabs& mt) const { return mt.inv_mdx * (float)(af.dxmin / af.dxc[c]); }
 };
 
 // features of one cell, written through put(k, value) for k in [0, nin)
@@ -153,7 +198,7 @@ __device__ __forceinline__ void features_of(const Dm& dm, const MlpTabs& mt, con
   float inv[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) inv[k] = 1.f / (fabsf(m[k]) + dmax[k] + 1e-12f);
-  const float imdx = mt.inv_mdx;
+  const float imdx = src.imdx(mt);
   const int nleg = dm.glm() ? 8 : 5;
 #pragma unroll
   for (int v = 0; v < 8; ++v) {
@@ -190,19 +235,20 @@ __device__ __forceinline__ void features_of(const Dm& dm, const MlpTabs& mt, con
 
 template <typename T, typename Put>
 __device__ __forceinline__ void cell_features(const Geom& g, const MlpTabs& mt, const T* w, const double* /*wmean*/,
-                                              int64_t c, Put put) {
-  features_of(RtDims{g, mt}, mt, GlobalSrc<T>{g, w, c}, put);
+                                              int64_t c, const AmrFeat& af, Put put) {
+  if (af.on) features_of(RtDims{g, mt}, mt, AmrSrc<T>{g, w, c, af}, put);
+  else features_of(RtDims{g, mt}, mt, GlobalSrc<T>{g, w, c}, put);
 }
 
 template <typename T>
 __global__ void k_features(Geom g, MlpTabs mt, const T* __restrict__ w, const double* __restrict__ wmean,
-                           float* __restrict__ X, int ldx) {
+                           float* __restrict__ X, int ldx, AmrFeat af) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
   const int nin = 8 * g.n + 10 * g.D;
   float* xr = X + c * ldx;
   for (int k = nin; k < ldx; ++k) xr[k] = 0.f;
-  cell_features(g, mt, w, wmean, c, [&](int k, float v) { xr[k] = v; });
+  cell_features(g, mt, w, wmean, c, af, [&](int k, float v) { xr[k] = v; });
 }
 
 // ---------------------------------------------------------------- inference (BF16 mma.sync)
@@ -338,7 +384,8 @@ __global__ void __launch_bounds__(128) k_mlp_infer(Geom g, MlpTabs mt, const T* 
                                                    const __nv_bfloat16* __restrict__ W2,
                                                    const float* __restrict__ bias, float thresh,
                                                    uint8_t* __restrict__ flag, float* __restrict__ prob,
-                                                   int32_t* __restrict__ list, DevScalars* __restrict__ sc) {
+                                                   int32_t* __restrict__ list, DevScalars* __restrict__ sc,
+                                                   AmrFeat af) {
   constexpr int LD1 = KP + 8, LD2 = HID + 8;
   extern __shared__ __align__(128) unsigned char smraw[];
   __nv_bfloat16* W1s = reinterpret_cast<__nv_bfloat16*>(smraw);
@@ -359,7 +406,7 @@ __global__ void __launch_bounds__(128) k_mlp_infer(Geom g, MlpTabs mt, const T* 
     {
       __nv_bfloat16* xr = Xs + (warp * 32 + lane) * LD1;
       for (int k = live ? nin : 0; k < KP; ++k) xr[k] = __float2bfloat16_rn(0.f);
-      if (live) cell_features(g, mt, w, wmean, c, [&](int k, float v) { xr[k] = __float2bfloat16_rn(v); });
+      if (live) cell_features(g, mt, w, wmean, c, af, [&](int k, float v) { xr[k] = __float2bfloat16_rn(v); });
     }
     __syncwarp();
     infer_warp<KP>(Xs + warp * 32 * LD1, W1s, W2s, bs, fl + warp * 32, base + warp * 32, g.ncell, thresh, flag,
@@ -536,6 +583,7 @@ struct StagedSrc {
   const float* xe;
   int t;
   __device__ float row(int r) const { return st[r * 128 + t]; }
+  __device__ float imdx(const MlpTabs& mt) const { return mt.inv_mdx; }
   __device__ void nbraw(int a, int s, float* raw) const {
     if (a == 0) {
       const int tt = t + (s ? 1 : -1);
@@ -878,6 +926,10 @@ int mlp_train_dev(const float* X, int ldx, const uint8_t* y, int64_t n, int nin,
   return e;
 }
 
+static AmrFeat amr_feat(const Ctx& c) {
+  return AmrFeat{c.amr.cstart, c.amr.centry, c.amr.fmeta, c.amr.fL, c.amr.fR, c.amr.dxc, c.g.dx, c.amr.on ? 1 : 0};
+}
+
 int mlp_build_tables(Ctx& c) {
   const Basis& B = *c.hb;
   const Geom& g = c.g;
@@ -922,9 +974,9 @@ int mlp_features_launch(Ctx& c, const void* w, const double* wmean, float* X, in
   const Geom& g = c.g;
   const unsigned nb = (unsigned)((g.ncell + 127) / 128);
   if (c.p.precision == DG_PREC_FP32MIX)
-    k_features<float><<<nb, 128, 0, st>>>(g, c.mlp, (const float*)w, nullptr, X, ldx);
+    k_features<float><<<nb, 128, 0, st>>>(g, c.mlp, (const float*)w, nullptr, X, ldx, amr_feat(c));
   else
-    k_features<double><<<nb, 128, 0, st>>>(g, c.mlp, (const double*)w, nullptr, X, ldx);
+    k_features<double><<<nb, 128, 0, st>>>(g, c.mlp, (const double*)w, nullptr, X, ldx, amr_feat(c));
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -1043,7 +1095,7 @@ static void infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* fl
   const unsigned nb = (unsigned)std::min<int64_t>(tiles, (int64_t)c.nsm * 4);
   k_mlp_infer<T, KP><<<nb, 128, sm, st>>>(g, c.mlp, (const T*)w, wmean, (const __nv_bfloat16*)c.mlp_w1,
                                            (const __nv_bfloat16*)c.mlp_w2, c.mlp_bias, c.mlp_thresh, flag, prob,
-                                           list, c.sc);
+                                           list, c.sc, amr_feat(c));
 }
 
 int mlp_infer_launch(Ctx& c, const void* w, const double* wmean, uint8_t* flag, float* prob, cudaStream_t st,

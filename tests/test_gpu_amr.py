@@ -149,3 +149,56 @@ def test_amr_tvb_and_positivity_fp64(D, divb):
     assert trig.sum() > 5
     assert np.array_equal(flags[: sol.ncell].cpu().numpy().astype(bool), trig)
     assert rel_err(from_device(w, sol), ref) < 1e-12
+
+
+@pytest.mark.parametrize("divb,prec", [("powell", "fp64"), ("powell", "fp32"), ("glm", "fp64")])
+def test_amr_indicator_features(divb, prec):
+    """The learned indicator's features on an octree (neighbour means: the
+    average of the leaves across each side; slope scale: the leaf's own size)
+    against the oracle's."""
+    import torch
+    from oracle import mlp as M
+    leaves = _mesh(3)
+    A = AMRScheme(3, 2, divb, G, leaves)
+    w0 = A.project(_shock(A.V))
+    sol = _solver(A, leaves, prec=prec, c_h_fixed=3.0)   # (GLM on an octree takes a fixed c_h)
+    w = to_device(w0, sol)
+    wm = means_to_device(w0, sol, A) if prec == "fp32" else None
+    X = torch.full((sol.ncell, 112), float("nan"), dtype=torch.float32, device="cuda")
+    sol.mlp_features(w, wm, X, 112)
+    ref = M.features(A, w0)
+    got = X.cpu().numpy()
+    assert np.max(np.abs(got[:, :110] - ref)) < 2e-5 * max(1.0, np.abs(ref).max())
+    assert np.all(got[:, 110:] == 0.0)
+
+
+@pytest.mark.parametrize("divb", ["powell", "glm"])
+def test_amr_gated_tvb(divb):
+    """Learned indicator on an octree: part of the leaves flagged; flagged
+    leaves get the octree TVB result, the others stay unchanged."""
+    import torch
+    from oracle import mlp as M
+    from oracle.limiter import Limiter
+    leaves = _mesh(3)
+    A = AMRScheme(3, 2, divb, G, leaves)
+    A.P.Mtilde = 0.5
+    A.P.c_h_fixed = 3.0
+    w0 = A.project(_shock(A.V))
+    ref, trig = Limiter(A, tvb=True, positivity=False).tvb_limit(w0, 3.0)
+    th = M.init_params(110, seed=7)
+    z, _ = M.forward(th, M.features(A, w0))
+    th[-1] -= float(np.median(z))
+    sol = _solver(A, leaves, limiter=2, Mtilde=0.5, c_h_fixed=3.0)
+    if divb == "glm":
+        sol.set_glm(3.0, 1.0)
+    sol.mlp_set_weights(torch.as_tensor(th, dtype=torch.float32, device="cuda"), 0.5)
+    w = to_device(w0, sol)
+    gate = torch.zeros(sol.stride, dtype=torch.uint8, device="cuda")
+    sol.mlp_infer(w, None, gate, None)
+    g = gate[: sol.ncell].cpu().numpy().astype(bool)
+    assert 0.05 < g.mean() < 0.95
+    assert (trig & g).sum() > 2 and (trig & ~g).sum() > 2
+    flags = torch.zeros(sol.stride, dtype=torch.uint8, device="cuda")
+    sol.limit(w, None, flags)
+    assert rel_err(from_device(w, sol), np.where(g[:, None], ref, w0)) < 1e-12
+    assert np.array_equal(flags[: sol.ncell].cpu().numpy().astype(bool), trig & g)

@@ -211,6 +211,55 @@ def test_mlp_features_ldf_map_is_exact():
     assert X.shape == (S.C, 86 + 24)
 
 
+def test_mlp_features_octree_of_one_level_equal_uniform():
+    """An octree whose leaves all have one level is the uniform mesh: the
+    octree features (side averages of one leaf each, the leaf size) must equal
+    the uniform ones cell by cell."""
+    from oracle.amr import AMRScheme
+    n = 4
+    S = Scheme(3, 2, "powell", G, (n, n, n))
+    leaves = [(2, (i, j, k)) for k in range(n) for j in range(n) for i in range(n)]
+    A = AMRScheme(3, 2, "powell", G, leaves)
+    fn = lambda x: np.stack(np.broadcast_arrays(
+        1.0 + 0.3 * np.sin(2 * np.pi * x[..., 0]), 0.2 * x[..., 1], 0 * x[..., 0] + 0.1, 0 * x[..., 0],
+        3.0 + np.cos(2 * np.pi * x[..., 2]), 0.5 + 0 * x[..., 0], 0.2 * np.sin(2 * np.pi * x[..., 1]),
+        0 * x[..., 0] - 0.1), -1)
+    wS, wA = S.project(fn), A.project(fn)
+    # the same cell order (x fastest): the uniform cell index of each leaf
+    idx = [(k * n + j) * n + i for (_, (i, j, k)) in leaves]
+    assert np.max(np.abs(wA - wS[idx])) < 1e-13
+    XS, XA = M.features(S, wS)[idx], M.features(A, wA)
+    assert np.max(np.abs(XA - XS)) < 1e-12 * max(1.0, np.abs(XS).max())
+
+
+def test_mlp_features_octree_side_average():
+    """A coarse leaf beside four finer ones reads their average density (the
+    ratio feature), a fine leaf beside a coarse one reads the coarse density,
+    and the slope features scale with the leaf's own size."""
+    from oracle.amr import AMRScheme
+    leaves = [(1, (i, j, k)) for k in range(2) for j in range(2) for i in range(2)]
+    at = leaves.index((1, (1, 0, 0)))
+    kids = [(2, (2 + a, b, e)) for e in (0, 1) for b in (0, 1) for a in (0, 1)]
+    leaves = leaves[:at] + kids + leaves[at + 1:]
+    A = AMRScheme(3, 1, "powell", G, leaves)
+    rng = np.random.default_rng(5)
+    w = np.zeros((A.C, A.N))
+    w[:, 0] = 1.0 + rng.uniform(0, 1, A.C)          # density means
+    w[:, 4 * A.n] = 10.0                            # energy mean
+    w[:, 1] = 0.01 * rng.normal(size=A.C)           # a density slope along x
+    X = M.features(A, w)
+    nin = 8 * A.n
+    coarse = leaves.index((1, (0, 0, 0)))          # its +x side: the four kids at i = 2
+    kid_rho = [w[leaves.index(kd), 0] for kd in kids if kd[1][0] == 2]
+    assert len(kid_rho) == 4
+    assert abs(X[coarse, nin + 1] - (np.mean(kid_rho) / w[coarse, 0] - 1.0)) < 1e-13
+    fine = leaves.index((2, (2, 0, 0)))             # its -x side: the coarse leaf (0, 0, 0)
+    assert abs(X[fine, nin + 0] - (w[coarse, 0] / w[fine, 0] - 1.0)) < 1e-13
+    deg1x = A.modes.index((1, 0, 0))
+    for c in (coarse, fine):
+        assert abs(X[c, nin + 6] - w[c, deg1x] / (A.P.Mtilde * A.dxc[c])) < 1e-12
+
+
 def test_mlp_training_reduces_loss():
     rng = np.random.default_rng(4)
     X = rng.normal(size=(512, 20))
