@@ -310,14 +310,20 @@ def run_ours(args, cfg, rank, world, device):
     # DRAM bytes (read + write) per launch of k_cell_glm<float, 2> per cell, from the ncu
     # capture of one launch on the 128^3 GLM degree-2 turbulence workload (3.843 GB for
     # 2,097,152 cells); traffic grows with the cells, so it is scaled by the cell count
-    traffic = None
-    if cfg["divb"] == "glm" and d == 2 and not cfg.get("amr"):
-        traffic = 1832.4 * ncell
+    # (k_cell_pow: 4.510 GB for the 2,097,152 cells of the 128^3 Powell blast; k_cell_list_pow:
+    # 3.114 GB for the 1,387,520 leaves of the Orszag-Tang octree)
+    traffic, tsrc = None, None
+    if d == 2 and cfg["divb"] == "glm" and not cfg.get("amr"):
+        traffic, tsrc = 1832.4 * ncell, "k_cell_glm launch at 128^3"
+    elif d == 2 and cfg["divb"] == "powell" and not cfg.get("amr"):
+        traffic, tsrc = 2150.6 * ncell, "k_cell_pow launch on the 128^3 Powell blast"
+    elif d == 2 and cfg["divb"] == "powell" and cfg.get("amr"):
+        traffic, tsrc = 2244.6 * ncell, "k_cell_list_pow launch on the Orszag-Tang octree (1,387,520 leaves)"
     res["roofline"] = {"bound": "hbm", "kernel": "k_cell (stage algorithmic bytes)", "dominant_kernel": dom,
                        "achieved": achieved, "peak": hbm, "peak_source": src, "unit": "GB/s",
                        "frac": achieved / hbm, "traffic": traffic,
-                       "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_cell_glm "
-                                         "launch at 128^3, scaled per cell" if traffic else None,
+                       "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one " + tsrc +
+                                          ", scaled per cell") if traffic else None,
                        "bytes_per_cell_stage": bytes_cell,
                        "stage_frac": bytes_cell * ncell * stages / (ms * 1e-3) / 1e9 / hbm}
 
@@ -877,7 +883,9 @@ def main():
         "dof": res["dof"],
         "regrid": res.get("regrid"), "amr_evolution": res.get("amr_evolution"),
         "alu": res.get("alu"),
-        "kernel_path": ("octree face-list kernels (k_face_list, k_cell_list)" if cfg.get("amr") else
+        "kernel_path": ("specialised Powell/LDF octree kernels (k_face_list_pow, k_cell_list_pow, k_divb_list_pow)"
+                        if cfg.get("amr") and cfg["divb"] == "powell" else
+                        "octree face-list kernels (k_face_list, k_cell_list)" if cfg.get("amr") else
                         "specialised GLM 3D kernels (k_face_glm, k_cell_glm)" if cfg["divb"] == "glm" else
                         "specialised Powell/LDF 3D kernels (k_face_pow3, k_cell_pow, k_divb_face_pow)"),
     }

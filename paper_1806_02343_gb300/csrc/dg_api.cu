@@ -799,24 +799,26 @@ int operator_pass(Ctx& c, const void* w, const double* wmean, void* out, double*
                   const double* w0mean, double ca, double cb, int combine, cudaStream_t st) {
   const Geom& g = c.g;
   if (c.amr.on && c.amr.fast && c.fast) {
-    // specialised Powell kernels over the face list (face pass + cell pass)
-    c.prof.begin(1, st);
+    // specialised Powell kernels over the face list: face pass, then cell pass
+#define LISTCASE(code, T, DEG, OP, FB, WM, W0M, OM)                                                         \
+  case code: {                                                                                              \
+    const auto o = OP(c);                                                                                   \
+    c.prof.begin(0, st);                                                                                    \
+    launch_face_list_pow<T, DEG>(o, g.gamma, (const T*)w, FB, c.p.eps_hlld, st);                           \
+    c.prof.end(0, st);                                                                                      \
+    c.prof.begin(1, st);                                                                                    \
+    launch_cell_list_pow<T, DEG>(o, g.gamma, (const T*)w, FB, (T*)out, (const T*)w0, ca, cb, combine, c.sc, \
+                                 WM, W0M, OM, st);                                                          \
+    c.prof.end(1, st);                                                                                      \
+    break;                                                                                                  \
+  }
     switch (c.fast) {
-      case 11: launch_list_pow<float, 1>(oct_pow32(c), g.gamma, (const float*)w, c.face_buf32, (float*)out,
-                                         (const float*)w0, ca, cb, combine, c.sc, wmean, w0mean, outmean,
-                                         c.p.eps_hlld, st); break;
-      case 12: launch_list_pow<float, 2>(oct_pow32(c), g.gamma, (const float*)w, c.face_buf32, (float*)out,
-                                         (const float*)w0, ca, cb, combine, c.sc, wmean, w0mean, outmean,
-                                         c.p.eps_hlld, st); break;
-      case 21: launch_list_pow<double, 1>(oct_pow64(c), g.gamma, (const double*)w, c.face_buf, (double*)out,
-                                          (const double*)w0, ca, cb, combine, c.sc, nullptr, nullptr, nullptr,
-                                          c.p.eps_hlld, st); break;
-      case 22: launch_list_pow<double, 2>(oct_pow64(c), g.gamma, (const double*)w, c.face_buf, (double*)out,
-                                          (const double*)w0, ca, cb, combine, c.sc, nullptr, nullptr, nullptr,
-                                          c.p.eps_hlld, st); break;
+      LISTCASE(11, float, 1, oct_pow32, c.face_buf32, wmean, w0mean, outmean)
+      LISTCASE(12, float, 2, oct_pow32, c.face_buf32, wmean, w0mean, outmean)
+      LISTCASE(21, double, 1, oct_pow64, c.face_buf, nullptr, nullptr, nullptr)
+      LISTCASE(22, double, 2, oct_pow64, c.face_buf, nullptr, nullptr, nullptr)
     }
-    c.prof.end(1, st);
-    c.prof.launches[1] += 1;
+#undef LISTCASE
     return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
   }
   if (c.amr.on) {

@@ -157,9 +157,11 @@ struct OctPow {
 template <typename T, int DEG>
 void launch_divb_list_pow(const OctPow<T>& o, const T* w, T* jbuf, cudaStream_t st);
 template <typename T, int DEG>
-void launch_list_pow(const OctPow<T>& o, double gamma, const T* w, T* F, T* out, const T* w0, double ca, double cb,
-                     int combine, const DevScalars* sc, const double* wmean, const double* w0mean, double* outmean,
-                     double eps, cudaStream_t st);
+void launch_face_list_pow(const OctPow<T>& o, double gamma, const T* w, T* F, double eps, cudaStream_t st);
+template <typename T, int DEG>
+void launch_cell_list_pow(const OctPow<T>& o, double gamma, const T* w, const T* F, T* out, const T* w0, double ca,
+                          double cb, int combine, const DevScalars* sc, const double* wmean, const double* w0mean,
+                          double* outmean, cudaStream_t st);
 
 // Powell timestep's face jumps (eq. powell_dt): per face point w_p |B^n_F - B^n_L|
 // and w_p |B^n_F - B^n_R|, laid out as the generic k_divb_face writes them

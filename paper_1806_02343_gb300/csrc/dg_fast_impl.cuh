@@ -1369,20 +1369,30 @@ void launch_divb_face_pow(const FastGeom& g, const T* w, T* jbuf, cudaStream_t s
 }
 
 template <typename T, int DEG>
-void launch_list_pow(const OctPow<T>& o, double gamma, const T* w, T* F, T* out, const T* w0, double ca, double cb,
-                     int combine, const DevScalars* sc, const double* wmean, const double* w0mean, double* outmean,
-                     double eps, cudaStream_t st) {
-  constexpr int N = FastDims<DEG>::N, QF = FastDims<DEG>::QF, QC = FastDims<DEG>::QC;
+void launch_face_list_pow(const OctPow<T>& o, double gamma, const T* w, T* F, double eps, cudaStream_t st) {
+  constexpr int N = FastDims<DEG>::N, QF = FastDims<DEG>::QF;
   constexpr int NDIV = PowDims<DEG>::NDIV, NRP = 5 * N + NDIV, QFP = FaceTabs<T, DEG>::QFP;
   const size_t smf = (size_t)(2 * N * QFP + 2 * NRP * TC + 2 * QF * 8 * TC) * sizeof(T);
-  const size_t smc = (size_t)(QC * NSL * TC + NDIV * TC + 8 * TC + 30 * QF * N) * sizeof(T);
   static bool attr = false;
   if (!attr) {
     set_smem_attr<T>((const void*)k_face_list_pow<T, DEG>, smf);
-    set_smem_attr<T>((const void*)k_cell_list_pow<T, DEG>, smc);
     attr = true;
   }
   if (o.nblk > 0) k_face_list_pow<T, DEG><<<(unsigned)o.nblk, NT, smf, st>>>(o, (T)gamma, (T)eps, w, F);
+}
+
+template <typename T, int DEG>
+void launch_cell_list_pow(const OctPow<T>& o, double gamma, const T* w, const T* F, T* out, const T* w0, double ca,
+                          double cb, int combine, const DevScalars* sc, const double* wmean, const double* w0mean,
+                          double* outmean, cudaStream_t st) {
+  constexpr int N = FastDims<DEG>::N, QF = FastDims<DEG>::QF, QC = FastDims<DEG>::QC;
+  constexpr int NDIV = PowDims<DEG>::NDIV;
+  const size_t smc = (size_t)(QC * NSL * TC + NDIV * TC + 8 * TC + 30 * QF * N) * sizeof(T);
+  static bool attr = false;
+  if (!attr) {
+    set_smem_attr<T>((const void*)k_cell_list_pow<T, DEG>, smc);
+    attr = true;
+  }
   const int cmode = combine ? (ca != 0.0 ? 2 : 1) : 0;
   const unsigned nb = (unsigned)((o.ncell + TC - 1) / TC);
   k_cell_list_pow<T, DEG><<<nb, NTP, smc, st>>>(o, (T)gamma, w, F, out, w0, ca, cb, (float)ca, (float)cb, cmode, sc,
@@ -1416,9 +1426,10 @@ int fast_to_constant(const FastAll<T, DEG>& tabs) {
                                         const T*, double, double, int, const DevScalars*, const double*,    \
                                         const double*, double*, cudaStream_t);                              \
   template void launch_divb_face_pow<T, DEG>(const FastGeom&, const T*, T*, cudaStream_t);                    \
-  template void launch_list_pow<T, DEG>(const OctPow<T>&, double, const T*, T*, T*, const T*, double, double, \
-                                        int, const DevScalars*, const double*, const double*, double*, double, \
-                                        cudaStream_t);                                                        \
+  template void launch_face_list_pow<T, DEG>(const OctPow<T>&, double, const T*, T*, double, cudaStream_t);   \
+  template void launch_cell_list_pow<T, DEG>(const OctPow<T>&, double, const T*, const T*, T*, const T*, double, \
+                                             double, int, const DevScalars*, const double*, const double*,      \
+                                             double*, cudaStream_t);                                           \
   template void launch_divb_list_pow<T, DEG>(const OctPow<T>&, const T*, T*, cudaStream_t);
 INSTF(DG_FAST_T, DG_FAST_DEG)
 
