@@ -1151,51 +1151,79 @@ __device__ __forceinline__ void stage_rd(const T* __restrict__ w, int64_t S, int
 // per face normal to each axis (right cell = this block's cell), B^n_F from
 // the two traces (eq. bxface-average) at every point and the weighted
 // distances to each side's own normal trace, summed over the face's points:
-// jbuf[(axis * ncell + cell) * 2 + side] (side 0: the left cell). Staged like
-// the face pass: the density and LDF rows of the left and own cells.
+// jbuf[(axis * ncell + cell) * 2 + side] (side 0: the left cell). Block of 32
+// cells x 4 warps: warp 0 / 1 the density traces of the left / own cells,
+// warp 2 / 3 their normal-field traces (from the LDF rows), every point of
+// the face per thread (compile-time table offsets; four code paths per axis).
+constexpr int NTD = 4 * TC;
+
+template <typename T, int DEG, int A>
+__device__ __forceinline__ void divb_traces(const T* __restrict__ w, int64_t S, int64_t cx, bool live, int role,
+                                            int f, T* TD) {
+  constexpr int N = FastDims<DEG>::N, QF = FastDims<DEG>::QF, NDIV = PowDims<DEG>::NDIV;
+  const FaceTabs<T, DEG>& tb = FastConst<T, DEG>::get().face[A];
+  const PowTabs<T, DEG>& pt = pow_tabs<T, DEG>();
+  T acc[QF];
+#pragma unroll
+  for (int p = 0; p < QF; ++p) acc[p] = T(0);
+  if (role < 2) {
+    // density: rows 0..N-1; left cell on its +A face (PL), own cell on its -A face (PR)
+    T x[N];
+    const T* pw = w + cx;
+#pragma unroll
+    for (int l = 0; l < N; ++l, pw += S) x[l] = live ? *pw : (l == 0 ? T(1) : T(0));
+#pragma unroll
+    for (int l = 0; l < N; ++l)
+#pragma unroll
+      for (int p = 0; p < QF; ++p) acc[p] = fma_rn(x[l], role == 0 ? tb.PL[l][p] : tb.PR[l][p], acc[p]);
+  } else {
+    // normal field from the LDF rows
+    const T* pw = w + (int64_t)(5 * N) * S + cx;
+#pragma unroll
+    for (int j = 0; j < NDIV; ++j, pw += S) {
+      const T x = live ? *pw : T(0);
+#pragma unroll
+      for (int p = 0; p < QF; ++p) acc[p] = fma_rn(x, role == 2 ? pt.Ln[A][1][j][p] : pt.Ln[A][0][j][p], acc[p]);
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < QF; ++p) TD[(role * QF + p) * TC + f] = acc[p];
+}
+
 template <typename T, int DEG>
-__global__ void __launch_bounds__(NT) k_divb_face_pow(const FastGeom g, const T* __restrict__ w,
-                                                      T* __restrict__ jbuf) {
-  constexpr int N = FastDims<DEG>::N, QF = FastDims<DEG>::QF, NDIV = PowDims<DEG>::NDIV, NRD = N + NDIV;
+__global__ void __launch_bounds__(NTD) k_divb_face_pow(const FastGeom g, const T* __restrict__ w,
+                                                       T* __restrict__ jbuf) {
+  constexpr int QF = FastDims<DEG>::QF;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* XL = reinterpret_cast<T*>(smraw);  // [NRD][TC] left cells
-  T* XR = XL + NRD * TC;                // [NRD][TC] own cells
-  T* JS = XR + NRD * TC;                // [2][QF][TC] weighted jumps per point
+  T* TD = reinterpret_cast<T*>(smraw);  // [4][QF][TC] traces: rho L, rho R, B_n L, B_n R
+  T* JS = TD + 4 * QF * TC;             // [2][QF][TC] weighted jumps per point
   const PowTabs<T, DEG>& pt = pow_tabs<T, DEG>();
   const int t = threadIdx.x;
   const int f = t & (TC - 1);
-  const int v = t >> 5;
+  const int role = t >> 5;  // warp-uniform
   const int64_t c = (int64_t)blockIdx.x * TC + f;
   const bool live = c < g.ncell;
   const int64_t S = g.stride;
   const Coord kc = coord_of(g, live ? c : 0);
   static_for<3>([&](auto AX) {
     constexpr int A = decltype(AX)::value;
-    const FaceTabs<T, DEG>& tb = FastConst<T, DEG>::get().face[A];
     const int64_t cl = live ? nbr(g, kc, A, -1) : 0;
-    if (A > 0) __syncthreads();  // the previous axis is done with XL
-    stage_rd<T, DEG, A == 0>(w, S, c, cl, live, v, f, XR, XL);
+    const int64_t cx = (role & 1) ? c : cl;
+    if (A > 0) __syncthreads();  // the previous axis is done with TD and JS
+    if (role == 0) divb_traces<T, DEG, A>(w, S, cx, live, 0, f, TD);
+    else if (role == 1) divb_traces<T, DEG, A>(w, S, cx, live, 1, f, TD);
+    else if (role == 2) divb_traces<T, DEG, A>(w, S, cx, live, 2, f, TD);
+    else divb_traces<T, DEG, A>(w, S, cx, live, 3, f, TD);
     __syncthreads();
-    // face point P on warp P mod 9: compile-time table offsets (constant operands)
-    static_for<QF>([&](auto PI) {
-      constexpr int p = decltype(PI)::value;
-      if (p % 9 != v) return;
-      T rL = T(0), rR = T(0), bL = T(0), bR = T(0);
-#pragma unroll
-      for (int l = 0; l < N; ++l) {
-        rL = fma_rn(XL[l * TC + f], tb.PL[l][p], rL);
-        rR = fma_rn(XR[l * TC + f], tb.PR[l][p], rR);
-      }
-#pragma unroll
-      for (int j = 0; j < NDIV; ++j) {
-        bL = fma_rn(XL[(N + j) * TC + f], pt.Ln[A][1][j][p], bL);
-        bR = fma_rn(XR[(N + j) * TC + f], pt.Ln[A][0][j][p], bR);
-      }
+    for (int i = t; i < QF * TC; i += NTD) {
+      const int p = i / TC, ff = i % TC;
+      const T rL = TD[(0 * QF + p) * TC + ff], rR = TD[(1 * QF + p) * TC + ff];
+      const T bL = TD[(2 * QF + p) * TC + ff], bR = TD[(3 * QF + p) * TC + ff];
       const T bF = bn_face(rL, rR, bL, bR);
       const T wp = pt.wf[p];
-      JS[(0 * QF + p) * TC + f] = wp * (bF > bL ? bF - bL : bL - bF);
-      JS[(1 * QF + p) * TC + f] = wp * (bF > bR ? bF - bR : bR - bF);
-    });
+      JS[(0 * QF + p) * TC + ff] = wp * (bF > bL ? bF - bL : bL - bF);
+      JS[(1 * QF + p) * TC + ff] = wp * (bF > bR ? bF - bR : bR - bF);
+    }
     __syncthreads();
     // the face's two sums over its points, in point order
     if (t < 2 * TC) {
@@ -1208,7 +1236,6 @@ __global__ void __launch_bounds__(NT) k_divb_face_pow(const FastGeom g, const T*
     }
   });
 }
-
 
 // Face jumps of the normal field on an octree (the Powell timestep, eq.
 // powell_dt), per face block of one type: the density traces through the
@@ -1364,8 +1391,8 @@ void launch_cell_pow(const FastAll<T, DEG>&, const FastGeom& g, const T* w, cons
 template <typename T, int DEG>
 void launch_divb_face_pow(const FastGeom& g, const T* w, T* jbuf, cudaStream_t st) {
   const unsigned nb = (unsigned)((g.ncell + TC - 1) / TC);
-  const size_t sm = (size_t)(2 * (FastDims<DEG>::N + PowDims<DEG>::NDIV) + 2 * FastDims<DEG>::QF) * TC * sizeof(T);
-  k_divb_face_pow<T, DEG><<<nb, NT, sm, st>>>(g, w, jbuf);
+  const size_t sm = (size_t)6 * FastDims<DEG>::QF * TC * sizeof(T);
+  k_divb_face_pow<T, DEG><<<nb, NTD, sm, st>>>(g, w, jbuf);
 }
 
 template <typename T, int DEG>
