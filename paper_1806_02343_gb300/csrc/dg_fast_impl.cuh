@@ -128,11 +128,42 @@ __device__ __forceinline__ int64_t nbr(const FastGeom& g, Coord k, int a, int di
   return ((int64_t)k.iz * g.ny + k.iy) * g.nx + k.ix;
 }
 
+// Asynchronous per-thread copies (cp.async, 4 bytes each) of the rows r = v + 9 i
+// (r < NR) of the -axis neighbours of the block's cells into X[r][TC]; waited
+// for by cp_async_wait_all and a barrier. Absent cells copy cell 0 (their
+// results are not stored).
+template <typename T, int NR>
+__device__ __forceinline__ void stage_left_async(const FastGeom& g, const T* __restrict__ w, int64_t c, bool live,
+                                                 int axis, int v, int f, T* X) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  const int64_t cl = live ? nbr(g, coord_of(g, c), axis, -1) : 0;
+  const int64_t S = g.stride;
+  constexpr int PER = (NR + 8) / 9;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int r = v + 9 * i;
+    if (r < NR) {
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(X + r * TC + f);
+      if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(w + (int64_t)r * S + cl) : "memory");
+      else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(w + (int64_t)r * S + cl) : "memory");
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // ------------------------------------------------------------------ faces
 // The faces normal to axis A whose right cells are the block's 32 cells:
 // stage the left cells' (and, with own, this block's) coefficients, traces,
-// HLLD. WR keeps this block's coefficients between calls.
-template <typename T, int DEG, int A, bool OWN>
+// HLLD. WR keeps this block's coefficients between calls. PRE: the left
+// cells' rows are already being copied into WL (asynchronous copies issued
+// by the previous axis); NEXT >= 0: once this axis's traces are done, issue
+// those copies for axis NEXT, so they run while this axis's HLLD does
+// (measured: 11.0 -> 10.5 ms per stage at 256^3).
+template <typename T, int DEG, int A, bool OWN, bool PRE = false, int NEXT = -1>
 __device__ __forceinline__ void face_axis(const FaceTabs<T, DEG>& tbp, const FastGeom& g, const T* __restrict__ w,
                                           T* __restrict__ F, const DevScalars* __restrict__ sc, T eps, T* WL, T* WR,
                                           T* TR) {
@@ -148,7 +179,9 @@ __device__ __forceinline__ void face_axis(const FaceTabs<T, DEG>& tbp, const Fas
   const int64_t cl = live ? nbr(g, coord_of(g, c), A, -1) : 0;
   // stage both cells' coefficients (coalesced along cells); all loads of a
   // thread are issued before the first shared-memory store
-  {
+  if (PRE) {
+    cp_async_wait_all();
+  } else {
     constexpr int PER = (NR + 8) / 9;
     T a[PER], b[PER];
     const int64_t S9 = 9 * S;
@@ -195,6 +228,7 @@ __device__ __forceinline__ void face_axis(const FaceTabs<T, DEG>& tbp, const Fas
     }
   }
   __syncthreads();
+  if constexpr (NEXT >= 0) stage_left_async<T, NR>(g, w, c, live, NEXT, v, f, WL);
   // HLLD per face point
   const T ch = pick_prec<T>(sc->ch, sc->ch32);
   const T gamma = pick_prec<T>(g.gamma, g.gamma32);
@@ -237,11 +271,11 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 3) k_fa
   T* WL = reinterpret_cast<T*>(smraw);
   T* WR = WL + NR * TC;
   T* TR = WR + NR * TC;
-  face_axis<T, DEG, 0, true>(tb0, g, w, F, sc, eps, WL, WR, TR);
+  face_axis<T, DEG, 0, true, false, 1>(tb0, g, w, F, sc, eps, WL, WR, TR);
   __syncthreads();
-  face_axis<T, DEG, 1, false>(tb1, g, w, F, sc, eps, WL, WR, TR);
+  face_axis<T, DEG, 1, false, true, 2>(tb1, g, w, F, sc, eps, WL, WR, TR);
   __syncthreads();
-  face_axis<T, DEG, 2, false>(tb2, g, w, F, sc, eps, WL, WR, TR);
+  face_axis<T, DEG, 2, false, true, -1>(tb2, g, w, F, sc, eps, WL, WR, TR);
 }
 
 // ------------------------------------------------------------------ cells
@@ -542,7 +576,7 @@ __device__ __forceinline__ void face_trace(const T (&wl)[FastDims<DEG>::N], cons
 // WL / WR: raw state rows of the left / own cells; BR: the own cells' B in
 // Legendre form (computed with OWN, kept for the next axes); TR: traces
 // [side][point][variable][cell].
-template <typename T, int DEG, int A, bool OWN>
+template <typename T, int DEG, int A, bool OWN, bool PRE = false, int NEXT = -1>
 __device__ __forceinline__ void face_axis_pow(const FastGeom& g, const T* __restrict__ w, T* __restrict__ F, T eps,
                                               T* WL, T* WR, T* BR, T* TR) {
   constexpr int N = FastDims<DEG>::N, QF = FastDims<DEG>::QF, NDIV = PowDims<DEG>::NDIV, NRP = 5 * N + NDIV;
@@ -554,7 +588,9 @@ __device__ __forceinline__ void face_axis_pow(const FastGeom& g, const T* __rest
   const bool live = c < g.ncell;
   const int64_t S = g.stride;
   const int64_t cl = live ? nbr(g, coord_of(g, c), A, -1) : 0;
-  {
+  if (PRE) {
+    cp_async_wait_all();  // the left cells' rows, copied while the previous axis ran HLLD
+  } else {
     constexpr int PER = (NRP + 8) / 9;
     T a[PER], b[PER];
     const int64_t S9 = 9 * S;
@@ -601,6 +637,7 @@ __device__ __forceinline__ void face_axis_pow(const FastGeom& g, const T* __rest
     face_trace<T, DEG>(wl, tb.PR, TR + (QF * 8 + v) * TC + f);
   }
   __syncthreads();
+  if constexpr (NEXT >= 0) stage_left_async<T, NRP>(g, w, c, live, NEXT, v, f, WL);
   // HLLD per face point (Sec. 4.1.2), B^n_F of eq. bxface-average
   const T gamma = pick_prec<T>(g.gamma, g.gamma32);
   for (int p = v; p < QF; p += 9) {
@@ -632,11 +669,11 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && DEG <= 2) ? 4 : 2) k_fa
   T* WR = WL + NRP * TC;                // [NRP][TC]
   T* BR = WR + NRP * TC;                // [3 N][TC]
   T* TR = BR + 3 * N * TC;              // [2][QF][8][TC]
-  face_axis_pow<T, DEG, 0, true>(g, w, F, eps, WL, WR, BR, TR);
+  face_axis_pow<T, DEG, 0, true, false, 1>(g, w, F, eps, WL, WR, BR, TR);
   __syncthreads();
-  face_axis_pow<T, DEG, 1, false>(g, w, F, eps, WL, WR, BR, TR);
+  face_axis_pow<T, DEG, 1, false, true, 2>(g, w, F, eps, WL, WR, BR, TR);
   __syncthreads();
-  face_axis_pow<T, DEG, 2, false>(g, w, F, eps, WL, WR, BR, TR);
+  face_axis_pow<T, DEG, 2, false, true, -1>(g, w, F, eps, WL, WR, BR, TR);
 }
 
 // Sum of a cell's six face sums of one mean row. FP32: an unevaluated float
