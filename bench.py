@@ -308,13 +308,13 @@ def run_ours(args, cfg, rank, world, device):
     per_launch_ms = kern["cell_update"]["ms_per_launch"]
     achieved = bytes_cell * ncell / (per_launch_ms * 1e-3) / 1e9
     # DRAM bytes (read + write) per launch of k_cell_glm<float, 2> per cell, from the ncu
-    # capture of one launch on the 128^3 GLM degree-2 turbulence workload (3.843 GB for
+    # capture of one launch on the 128^3 GLM degree-2 turbulence workload (3.841 GB for
     # 2,097,152 cells); traffic grows with the cells, so it is scaled by the cell count
     # (k_cell_pow: 4.510 GB for the 2,097,152 cells of the 128^3 Powell blast; k_cell_list_pow:
     # 3.114 GB for the 1,387,520 leaves of the Orszag-Tang octree)
     traffic, tsrc = None, None
     if d == 2 and cfg["divb"] == "glm" and not cfg.get("amr"):
-        traffic, tsrc = 1832.4 * ncell, "k_cell_glm launch at 128^3"
+        traffic, tsrc = 1831.5 * ncell, "k_cell_glm launch at 128^3"
     elif d == 2 and cfg["divb"] == "powell" and not cfg.get("amr"):
         traffic, tsrc = 2150.6 * ncell, "k_cell_pow launch on the 128^3 Powell blast"
     elif d == 2 and cfg["divb"] == "powell" and cfg.get("amr"):
