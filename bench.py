@@ -37,7 +37,7 @@ CONFIGS = {
     "turb128": dict(workload="3D 128^3 periodic, degree 2, GLM, decaying turbulence (Mach 2)", D=3, n=128, d=2,
                     divb="glm", run_steps=20),
     "fourier64": dict(workload="3D 64^3 periodic, degree 3, GLM, seeded smooth Fourier state", D=3, n=64, d=3,
-                      divb="glm", run_steps=10),
+                      divb="glm", run_steps=10, limiter="off"),
     "blast128": dict(workload="3D 128^3 periodic, degree 2, Powell/LDF, MHD blast (p=100 in r<0.1, 0.1 outside, "
                               "rho=1, B=(10/sqrt(4 pi),0,0))", D=3, n=128, d=2, divb="powell", run_steps=20),
     "ot_amr": dict(workload="3D Orszag-Tang extrusion on a static octree, levels 5-7 (1,387,520 leaves), "
@@ -811,7 +811,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=24)
     ap.add_argument("--cpu-one-core", action="store_true", help="skip the all-core run of the CPU oracle")
     ap.add_argument("--limiter", default=None, choices=["mlp", "tvb", "off"],
-                    help="default: mlp (learned indicator); tvb on octree meshes")
+                    help="default: mlp (learned indicator); tvb on octree meshes; off for the smooth 64^3 "
+                         "degree-3 workload (its configuration runs no limiter)")
     ap.add_argument("--threshold", type=float, default=0.1)
     ap.add_argument("--amr-steps", type=int, default=None,
                     help="octree workload: steps of the evolution with regridding (default: the configuration's)")
@@ -820,7 +821,7 @@ def main():
     cfg = dict(CONFIGS[args.config])
     cfg["name"] = args.config
     if args.limiter is None:
-        args.limiter = "tvb" if cfg.get("amr") else "mlp"
+        args.limiter = cfg.get("limiter") or ("tvb" if cfg.get("amr") else "mlp")
     if args.l1_steps is None:
         args.l1_steps = cfg.get("run_steps", 20)
     if args.amr_steps is None:

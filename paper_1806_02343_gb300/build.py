@@ -14,8 +14,8 @@ LIB = os.path.join(OUT, "libdgmhd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # FP32 kernels of the specialised path use the hardware's approximate division,
 # reciprocal square root and square root (FP64 code is unaffected)
-FAST_MATH = {"dg_fast_f1.cu", "dg_fast_f2.cu", "dg_fast_d1.cu", "dg_fast_d2.cu"}
-SOURCES = ["dg_api.cu", "dg_kernels.cu", "dg_fast_f1.cu", "dg_fast_f2.cu", "dg_fast_d1.cu", "dg_fast_d2.cu",
+FAST_MATH = {"dg_fast_f1.cu", "dg_fast_f2.cu", "dg_fast_f3.cu", "dg_fast_d1.cu", "dg_fast_d2.cu"}
+SOURCES = ["dg_api.cu", "dg_kernels.cu", "dg_fast_f1.cu", "dg_fast_f2.cu", "dg_fast_f3.cu", "dg_fast_d1.cu", "dg_fast_d2.cu",
            "dg_cell_tc.cu", "dg_limit.cu", "dg_mlp.cu", "dg_amr.cu", "dg_noalloc.cu", "dg_probe.cu", "dg_regrid.cu", "dg_plan.cpp", "dg_basis.cpp"]
 
 

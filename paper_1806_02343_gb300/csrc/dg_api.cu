@@ -306,7 +306,7 @@ void* make_fast_tabs(const HostTables& h, const Geom& g, const Basis& B) {
       for (int q = 0; q < Qv; ++q) ft->cell.dP2[a][i / 2][q][i % 2] = (T)(h.dPv[((size_t)a * n + l) * Qv + q] * h.wv[q]);
     }
   static_assert(Dm::N > 0, "");
-  build_pow_tabs<T, DEG>(ft->pow);
+  if constexpr (DEG <= 2) build_pow_tabs<T, DEG>(ft->pow);
   if (fast_to_constant<T, DEG>(*ft)) {
     delete ft;
     return nullptr;
@@ -319,6 +319,7 @@ void free_fast_tabs(Ctx& c) {
   switch (c.fast) {
     case 11: delete (FastAll<float, 1>*)c.fast_tabs; break;
     case 12: delete (FastAll<float, 2>*)c.fast_tabs; break;
+    case 13: delete (FastAll<float, 3>*)c.fast_tabs; break;
     case 21: delete (FastAll<double, 1>*)c.fast_tabs; break;
     case 22: delete (FastAll<double, 2>*)c.fast_tabs; break;
   }
@@ -331,6 +332,7 @@ bool fast_pow_ok(const Ctx& c) {
   switch (c.fast) {
     case 11: return ((const FastAll<float, 1>*)c.fast_tabs)->pow.ok != 0;
     case 12: return ((const FastAll<float, 2>*)c.fast_tabs)->pow.ok != 0;
+    case 13: return false;
     case 21: return ((const FastAll<double, 1>*)c.fast_tabs)->pow.ok != 0;
     case 22: return ((const FastAll<double, 2>*)c.fast_tabs)->pow.ok != 0;
   }
@@ -350,6 +352,20 @@ FastGeom fast_geom(const Geom& g) {
 }
 
 inline bool fp32(const Ctx& c) { return c.p.precision == DG_PREC_FP32MIX; }
+
+// the Powell kernels exist for degrees 1 and 2 (a degree-3 context never
+// selects them: its tables are not built)
+template <typename T, int DEG>
+void face_pow_fast(const FastAll<T, DEG>& ft, const FastGeom& fg, const T* w, T* F, double eps, cudaStream_t st) {
+  if constexpr (DEG <= 2) launch_face_pow<T, DEG>(ft, fg, w, F, eps, st);
+}
+template <typename T, int DEG>
+void cell_pow_fast(const FastAll<T, DEG>& ft, const FastGeom& fg, const T* w, const T* F, T* out, const T* w0,
+                   double ca, double cb, int combine, const DevScalars* sc, const double* wmean, const double* w0mean,
+                   double* outmean, cudaStream_t st) {
+  if constexpr (DEG <= 2)
+    launch_cell_pow<T, DEG>(ft, fg, w, F, out, w0, ca, cb, combine, sc, wmean, w0mean, outmean, st);
+}
 
 // the tensor-core cell update where the context built its tables (FP32 form,
 // degree 2); false: the caller launches the CUDA-core one
@@ -694,8 +710,8 @@ int dg_mhd_init(const dg_mesh_desc* mesh, int degree, int divB_scheme, double ga
     if (fp32(c)) {
       if (degree == 1) c.fast_tabs = make_fast_tabs<float, 1>(h, g, *c.hb);
       if (degree == 2) c.fast_tabs = make_fast_tabs<float, 2>(h, g, *c.hb);
-      // degree 3 runs the generic kernels: its fully unrolled specialisation
-      // costs minutes of compilation for a secondary workload
+      // degree 3: FP32 only (the FP64 tables exceed the constant bank)
+      if (degree == 3) c.fast_tabs = make_fast_tabs<float, 3>(h, g, *c.hb);
       if (c.fast_tabs) c.fast = 10 + degree;
       // degree 2, on request: the cell update's contractions on the tensor
       // core (operand tables in device memory, staged into shared memory by
@@ -840,12 +856,12 @@ int operator_pass(Ctx& c, const void* w, const double* wmean, void* out, double*
     const auto& ft = *(const FastAll<T, DEG>*)c.fast_tabs;                                                \
     c.prof.begin(0, st);                                                                                    \
     if (g.glm) launch_face_glm<T, DEG>(ft, fg, (const T*)w, FB, c.sc, c.p.eps_hlld, st);                    \
-    else launch_face_pow<T, DEG>(ft, fg, (const T*)w, FB, c.p.eps_hlld, st);                                \
+    else face_pow_fast<T, DEG>(ft, fg, (const T*)w, FB, c.p.eps_hlld, st);                                  \
     c.prof.end(0, st);                                                                                      \
     c.prof.begin(1, st);                                                                                    \
     if (!g.glm)                                                                                             \
-      launch_cell_pow<T, DEG>(ft, fg, (const T*)w, FB, (T*)out, (const T*)w0, ca, cb, combine, c.sc, wmean, \
-                              w0mean, outmean, st);                                                         \
+      cell_pow_fast<T, DEG>(ft, fg, (const T*)w, FB, (T*)out, (const T*)w0, ca, cb, combine, c.sc, wmean,   \
+                            w0mean, outmean, st);                                                           \
     else if (!launch_cell_fast<T, DEG>(c, ft, fg, (const T*)w, FB, (T*)out, (const T*)w0, ca, cb, combine, \
                                        wmean, w0mean, outmean, st))                                         \
       launch_cell_glm<T, DEG>(ft, fg, (const T*)w, FB, (T*)out, (const T*)w0, ca, cb, combine, c.sc, wmean, \
@@ -856,6 +872,7 @@ int operator_pass(Ctx& c, const void* w, const double* wmean, void* out, double*
     switch (c.fast) {
       FASTCASE(11, float, 1, c.face_buf32)
       FASTCASE(12, float, 2, c.face_buf32)
+      FASTCASE(13, float, 3, c.face_buf32)
       FASTCASE(21, double, 1, c.face_buf)
       FASTCASE(22, double, 2, c.face_buf)
     }

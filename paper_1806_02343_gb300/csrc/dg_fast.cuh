@@ -1,6 +1,8 @@
 // Specialised GLM kernels for uniform 3D meshes: compile-time sizes and the
 // basis tables they take as kernel parameters.
 #pragma once
+#include <type_traits>
+
 #include "dg_ctx.h"
 
 namespace dgmhd {
@@ -82,8 +84,8 @@ struct CellTabs {
 // the others have zero mean.
 template <int DEG>
 struct PowDims {
-  static constexpr int NDIV = DEG == 1 ? 11 : 26;  // Table A1, D = 3
-  static constexpr int NP = (NDIV - 3 + 1) / 2;   // pairs of non-mean LDF rows
+  static constexpr int NDIV = DEG == 1 ? 11 : DEG == 2 ? 26 : 50;  // Table A1, D = 3
+  static constexpr int NP = (NDIV - 3 + 1) / 2;                   // pairs of non-mean LDF rows
 };
 template <typename T, int DEG>
 struct PowTabs {
@@ -98,11 +100,16 @@ struct PowTabs {
   int ok;         // the basis has the structure above (else Powell runs the generic kernels)
 };
 
+// (degree 3 runs the Powell scheme on the generic kernels: its tables would
+// not fit in the constant bank next to the GLM ones)
+struct NoPowTabs {
+  int ok;  // 0 (value-initialised with the tables)
+};
 template <typename T, int DEG>
 struct FastAll {
   FaceTabs<T, DEG> face[3];
   CellTabs<T, DEG> cell;
-  PowTabs<T, DEG> pow;
+  std::conditional_t<(DEG <= 2), PowTabs<T, DEG>, NoPowTabs> pow;
 };
 
 struct FastGeom {

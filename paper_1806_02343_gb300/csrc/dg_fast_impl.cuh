@@ -1489,7 +1489,9 @@ int fast_to_constant(const FastAll<T, DEG>& tabs) {
   template void launch_cell_glm<T, DEG>(const FastAll<T, DEG>&, const FastGeom&, const T*, const T*, T*,    \
                                         const T*, double, double, int, const DevScalars*, const double*,    \
                                         const double*, double*, cudaStream_t);          \
-  template int fast_to_constant<T, DEG>(const FastAll<T, DEG>&);                                              \
+  template int fast_to_constant<T, DEG>(const FastAll<T, DEG>&);
+// the Powell kernels for degrees 1 and 2
+#define INSTP(T, DEG)                                                                                         \
   template void launch_face_pow<T, DEG>(const FastAll<T, DEG>&, const FastGeom&, const T*, T*, double,        \
                                         cudaStream_t);                                                        \
   template void launch_cell_pow<T, DEG>(const FastAll<T, DEG>&, const FastGeom&, const T*, const T*, T*,    \
@@ -1502,5 +1504,8 @@ int fast_to_constant(const FastAll<T, DEG>& tabs) {
                                              double*, cudaStream_t);                                           \
   template void launch_divb_list_pow<T, DEG>(const OctPow<T>&, const T*, T*, cudaStream_t);
 INSTF(DG_FAST_T, DG_FAST_DEG)
+#if DG_FAST_DEG <= 2
+INSTP(DG_FAST_T, DG_FAST_DEG)
+#endif
 
 }  // namespace dgmhd

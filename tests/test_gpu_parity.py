@@ -49,7 +49,8 @@ def _setup(D, d, divb, ncell, fname, precision="fp64", generic=0):
     return S, w0, sol
 
 
-# GLM in 3D has specialised kernels; the generic ones stay covered too
+# GLM in 3D has specialised kernels (degrees 1-2, and degree 3 in the FP32
+# form); the generic ones stay covered too
 GLM3D = [(3, 1, "glm", (9, 8, 7), "fourier"), CASES[2], CASES[3]]
 
 
@@ -225,7 +226,7 @@ def test_rhs_fp32_form(D, d, divb, ncell, fname):
     assert rel_err(got, ref) < 2e-4
 
 
-@pytest.mark.parametrize("D,d,divb,ncell,fname", [CASES[0], CASES[2], CASES[4]])
+@pytest.mark.parametrize("D,d,divb,ncell,fname", [CASES[0], CASES[2], CASES[3], CASES[4]])
 def test_step_fp32_form(D, d, divb, ncell, fname):
     S, w0, sol = _setup(D, d, divb, ncell, fname, precision="fp32")
     w = to_device(w0, sol)
