@@ -238,6 +238,13 @@ int dg_mhd_status(dg_mhd_ctx* ctx, int sync);
  * since the last reset. Synchronises the device; reset = 1 clears them. */
 int dg_mhd_counters(dg_mhd_ctx* ctx, int64_t* pos_cells, double* inj_mass, double* inj_energy, int reset);
 
+/* Workload of the positivity limiter in the FP32 form (measurement support,
+ * no counterpart in the paper): cells whose FP32 screen could not clear them
+ * and that therefore went through the full procedure, summed over limiter
+ * passes since the last reset (FP64 contexts run the procedure on every cell
+ * and count 0). Synchronises the device; reset = 1 clears the count. */
+int dg_mhd_positivity_listed(dg_mhd_ctx* ctx, int64_t* listed, int reset);
+
 /* Divergence diagnostics of App. C on a uniform mesh (DG_E_UNSUPPORTED on
  * octrees), from the state w (and wmean in the FP32 form):
  * res (DEVICE, 4 doubles): [0] ||div B||_1 = (1/V) sum_K V_K |div B|_K

@@ -26,7 +26,7 @@ EXPORTS = [
     "dg_mhd_rhs", "dg_mhd_limit", "dg_mhd_dt", "dg_mhd_step", "dg_mhd_last_dt", "dg_mhd_status",
     "dg_mhd_profile", "dg_mhd_profile_read", "dg_mhd_launch_count", "dg_mhd_rhs_noalloc", "dg_mhd_destroy",
     "dg_mhd_strerror", "dg_mhd_mlp_features", "dg_mhd_mlp_set_weights", "dg_mhd_mlp_infer", "dg_mhd_mlp_loss_grad",
-    "dg_mhd_mlp_train", "dg_mhd_counters", "dg_mhd_limiter_counts", "dg_mhd_divb", "dg_mhd_smoothness",
+    "dg_mhd_mlp_train", "dg_mhd_counters", "dg_mhd_positivity_listed", "dg_mhd_limiter_counts", "dg_mhd_divb", "dg_mhd_smoothness",
     "dg_mhd_amr_marks", "dg_mhd_regrid_plan", "dg_mhd_remap", "dg_mhd_regrid_plan_mesh",
     "dg_mhd_sibling_groups", "dg_mhd_octree_faces", "dg_mhd_basis_values", "dg_mhd_regrid_tables",
     "dg_mhd_probe", "dg_mhd_stage", "dg_mhd_set_dt", "dg_mhd_set_owned", "dg_mhd_glm_speeds",
@@ -91,6 +91,7 @@ def lib():
     L.dg_mhd_mlp_train.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64, ctypes.c_int, vp, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_uint64,
                                    ctypes.POINTER(ctypes.c_double), vp]
+    L.dg_mhd_positivity_listed.argtypes = [vp, i64p, ctypes.c_int]
     L.dg_mhd_counters.argtypes = [vp, i64p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                   ctypes.c_int]
     L.dg_mhd_limiter_counts.argtypes = [vp, i64p, i64p, i64p, ctypes.c_int]
@@ -564,6 +565,13 @@ class Solver:
         _check(lib().dg_mhd_counters(self.h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(e), 1 if reset else 0),
                "dg_mhd_counters")
         return {"pos_cells": n.value, "inj_mass": m.value, "inj_energy": e.value}
+
+    def positivity_listed(self, reset=False):
+        """Cells the FP32 positivity screen sent to the full procedure, summed
+        over limiter passes since the last reset (dg_mhd_positivity_listed)."""
+        n = ctypes.c_int64()
+        _check(lib().dg_mhd_positivity_listed(self.h, ctypes.byref(n), 1 if reset else 0), "dg_mhd_positivity_listed")
+        return n.value
 
     # ------------------------------------------------------------ regridding
     def smoothness(self, w, wmean=None, fields=(0, 5, 6, 7)):

@@ -1176,6 +1176,17 @@ int dg_mhd_counters(dg_mhd_ctx* ctx, int64_t* pos_cells, double* inj_mass, doubl
   return DG_OK;
 }
 
+int dg_mhd_positivity_listed(dg_mhd_ctx* ctx, int64_t* listed, int reset) {
+  if (!ctx || !listed) return DG_E_ARG;
+  Ctx& c = ctx->c;
+  if (cudaDeviceSynchronize() != cudaSuccess) return DG_E_CUDA;
+  unsigned long long v = 0;
+  if (cudaMemcpy(&v, &c.sc->cnt_poslisted, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return DG_E_CUDA;
+  *listed = (int64_t)v;
+  if (reset && cudaMemset(&c.sc->cnt_poslisted, 0, sizeof(v)) != cudaSuccess) return DG_E_CUDA;
+  return DG_OK;
+}
+
 int dg_mhd_divb(dg_mhd_ctx* ctx, const void* w, const double* wmean, double* res, double* per_cell,
                 void* stream) {
   if (!ctx || !w || !res) return DG_E_ARG;

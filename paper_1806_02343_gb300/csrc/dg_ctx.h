@@ -120,6 +120,7 @@ struct DevScalars {
   float pad32;
   double dt_step;                  // the step's dt; dt itself may be a fraction of it for some stages
   unsigned long long dt64_bits;    // FP32 form: FP64 minimum of the screened cells' FP64 bounds
+  unsigned long long cnt_poslisted;  // cells listed for the full positivity procedure, summed over passes
 };
 
 // a device scalar in the working precision T (FP32 kernels read the float copy)

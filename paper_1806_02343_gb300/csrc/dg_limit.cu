@@ -504,6 +504,23 @@ __device__ __forceinline__ bool pos_point_open(const T* uu, const double* m, con
   return pq < eps_p + screen_t * gm1 * (sc[4] + kin_s + mag_s);
 }
 
+// The same test from float copies of the cell's mean magnitudes (|m_v| in
+// FP32, converted once per cell): bitwise the same decision, since rounding
+// to nearest commutes with the absolute value.
+__device__ __forceinline__ bool pos_point_open_f(const float* uu, const float* mabs, const float* dev, float tt,
+                                                 float gm1, float eps_p, float screen_t) {
+  float sc[8];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) sc[v] = mabs[v] + tt * dev[v];
+  const float kin = 0.5f * (uu[1] * uu[1] + uu[2] * uu[2] + uu[3] * uu[3]) / uu[0];
+  const float mag = 0.5f * (uu[5] * uu[5] + uu[6] * uu[6] + uu[7] * uu[7]);
+  const float pq = gm1 * (uu[4] - kin - mag);
+  if (uu[0] < 1e-2f * sc[0]) return true;
+  const float kin_s = 0.5f * (sc[1] * sc[1] + sc[2] * sc[2] + sc[3] * sc[3]) / uu[0];
+  const float mag_s = 0.5f * (sc[5] * sc[5] + sc[6] * sc[6] + sc[7] * sc[7]);
+  return pq < eps_p + screen_t * gm1 * (sc[4] + kin_s + mag_s);
+}
+
 // Positivity procedure of one cell (Sec. 4.3).
 template <typename T>
 __device__ void pos_cell(const Geom& g, const Tables<T>& tb, const LimTabs& lt, T* w, double* wmean,
@@ -712,6 +729,7 @@ template <typename T>
 __global__ void k_pos(Geom g, Tables<T> tb, LimTabs lt, T* w, double* wmean, dg_mhd_params p, DevScalars* sc,
                       const int32_t* __restrict__ list) {
   const int64_t total = list ? (int64_t)sc->npos : g.ncell;
+  if (list && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&sc->cnt_poslisted, (unsigned long long)total);
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += step)
     pos_cell(g, tb, lt, w, wmean, p, sc, list ? (int64_t)list[i] : i);
@@ -749,6 +767,7 @@ __global__ void __launch_bounds__(128) k_pos_list(Geom gin, Tables<float> tb, Li
     return v;
   };
   const int64_t total = (int64_t)sc->npos;
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&sc->cnt_poslisted, (unsigned long long)total);
   for (int64_t i0 = ((int64_t)blockIdx.x * 4 + warp) * 32; i0 < total; i0 += (int64_t)gridDim.x * 4 * 32) {
     const bool valid = i0 + lane < total;
     const int64_t c = valid ? (int64_t)list[i0 + lane] : 0;
@@ -837,12 +856,24 @@ __global__ void __launch_bounds__(128) k_pos_list(Geom gin, Tables<float> tb, Li
       float dvo[8];
 #pragma unroll
       for (int v = 0; v < 8; ++v) dvo[v] = __shfl_sync(0xffffffffu, devt[v], o);
+      // float copies of the cell's constants, converted once per cell (an FP64
+      // -> FP32 conversion occupies GB300's FP64 pipe; inside the point loops
+      // they made this kernel FP64-bound)
+      float mof[8], maf[8];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        mof[v] = (float)mo[v];
+        maf[v] = fabsf(mof[v]);
+      }
+      const float mr0f = (float)mro[0];
+      const float rho_thr = (float)p.eps_rho + screen_t * (maf[0] + dvo[0]);
+      const float eps_pf = (float)p.eps_p;
       // tau_rho over the volume and face points
       double tau = 1.0;
       for (int pt = lane; pt < npt; pt += 32) {
         float acc = 0.f;
         for (int l = 1; l < g.n; ++l) acc += R[l][o] * tb.Pp[l * npt + pt];
-        if ((float)mro[0] + acc < (float)p.eps_rho + screen_t * (fabsf((float)mo[0]) + dvo[0])) {
+        if (mr0f + acc < rho_thr) {
           double rd = mro[0];
           for (int l = 1; l < g.n; ++l) rd += (double)R[l][o] * (double)tb.Pp[l * npt + pt];
           if (rd < p.eps_rho) tau = fmin(tau, (mo[0] - p.eps_rho) / (mo[0] - rd));
@@ -852,6 +883,7 @@ __global__ void __launch_bounds__(128) k_pos_list(Geom gin, Tables<float> tb, Li
       // tau_p from the density-limited state m + tau (u - m)
       double taup = 1.0;
       const int nleg = g.glm ? 8 : 5;
+      const float tt = (float)tau;
       for (int pt = lane; pt < npt; pt += 32) {
         float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -865,11 +897,10 @@ __global__ void __launch_bounds__(128) k_pos_list(Geom gin, Tables<float> tb, Li
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc) acc[5 + cc] += wj * tb.Lp[(j * g.DB + cc) * npt + pt];
           }
-        const float tt = (float)tau;
         float uu[8];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) uu[v] = (float)mo[v] + tt * acc[v];
-        if (pos_point_open(uu, mo, dvo, tt, gm1t, (float)p.eps_p, screen_t)) {
+        for (int v = 0; v < 8; ++v) uu[v] = mof[v] + tt * acc[v];
+        if (pos_point_open_f(uu, maf, dvo, tt, gm1t, eps_pf, screen_t)) {
           // FP64 recovery of this point's pressure
           double u[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
           const int nps = g.glm ? 9 : 5;
