@@ -541,6 +541,26 @@ int build_amr(Ctx& c, const dg_mesh_desc* mesh) {
   double dmin = DBL_MAX;
   for (double d : dxc) dmin = std::min(dmin, d);
   g.dx = dmin;
+  // the leaves across each side of every leaf, for the limiter's neighbour means
+  {
+    std::vector<int32_t> snb((size_t)N * 24, -1);
+    std::vector<uint8_t> sinf((size_t)N * 6, 0);
+    for (int64_t cc = 0; cc < N; ++cc)
+      for (int e2 = cstart[cc]; e2 < cstart[cc + 1]; ++e2) {
+        const int ent = centry[e2];
+        const int64_t f = ent >> 1;
+        const int side = ent & 1, m = fmeta[f], a = m & 3, kind = (m >> 2) & 3;
+        const int sidx = 2 * a + (side == 0 ? 1 : 0);
+        const int cnt = sinf[(size_t)cc * 6 + sidx] & 15;
+        if (cnt >= 4) return DG_E_MESH;  // more than 2^(D-1) leaves across one side: not 2:1 balanced
+        snb[(size_t)cc * 24 + sidx * 4 + cnt] = side == 0 ? fR[f] : fL[f];
+        const bool self_coarse = (side == 0 && kind == 1) || (side == 1 && kind == 2);
+        const int rel = kind == 0 ? 0 : (self_coarse ? 1 : 2);
+        sinf[(size_t)cc * 6 + sidx] = (uint8_t)((cnt + 1) | (rel << 4));
+      }
+    int e3;
+    if ((e3 = upload_vec(&h.side_nb, snb)) || (e3 = upload_vec(&h.side_info, sinf))) return e3;
+  }
   // specialised Powell kernels: faces grouped by type in blocks of <= 32, and
   // the tables of each type (the std tables: the full face; coarse sides: the
   // sub-face tables Ps above)
@@ -662,7 +682,7 @@ void free_amr(Ctx& c) {
   AmrHost& h = c.amr;
   void* ptrs[] = {h.fL,     h.fR,     h.fmeta,    h.cstart,   h.centry,   h.dxc,    h.Psub64, h.Lsub64,
                   h.Psub32, h.Lsub32, h.Psub64p, h.Lsub64p, h.Psub32p, h.Lsub32p, h.groups, h.lev_dev,
-                  h.bface,  h.bstart, h.btype,    h.ftab,     h.ctab,     h.ntab};
+                  h.bface,  h.bstart, h.btype,    h.ftab,     h.ctab,     h.ntab,     h.side_nb, h.side_info};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h = AmrHost();

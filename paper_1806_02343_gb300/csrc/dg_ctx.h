@@ -216,6 +216,12 @@ struct AmrHost {
   void* ftab = nullptr;
   void* ctab = nullptr;
   void* ntab = nullptr;
+  // per leaf and side (2 axis + 1 for +axis): the leaves across it, in face-entry
+  // order, side_nb[leaf * 24 + side * 4 + k] (-1 past the count), and
+  // side_info[leaf * 6 + side] = count | relation << 4 (0 same level, 1 the
+  // leaf is the coarser side, 2 the neighbour is coarser)
+  int32_t* side_nb = nullptr;
+  uint8_t* side_info = nullptr;
   // the last regrid plan (6 ints per new leaf) and a hash of the marks it was made from
   uint64_t plan_hash = 0;
   std::vector<int32_t> plan;

@@ -234,6 +234,8 @@ struct AmrNb {
   const int32_t* centry;
   const double* dxc;
   int on;
+  const int32_t* side_nb;    // AmrHost::side_nb: the leaves across each side, in face-entry order
+  const uint8_t* side_info;  // count | relation << 4 per leaf and side
 };
 
 // The TVB procedure on cell c; returns whether any slope changed. All of it
@@ -278,28 +280,30 @@ __device__ bool tvb_cell(const Geom& g, const LimTabs& lt, T* w, const double* w
       cell_mean<R>(g, lt, (const T*)w, wmean, nb(g, c, a, +1), mp);
       cell_mean<R>(g, lt, (const T*)w, wmean, nb(g, c, a, -1), mm);
     } else {
-      // octree: average of the leaves across each side; 2 same level, 3 coarser, 1.5 finer
+      // octree: average of the leaves across each side (listed per side at
+      // set-up, in face-entry order); 2 same level, 3 coarser, 1.5 finer
       int np_ = 0, nm_ = 0;
       for (int k = 0; k < 9; ++k) mp[k] = mm[k] = R(0);
-      for (int e = an.cstart[c]; e < an.cstart[c + 1]; ++e) {
-        const int ent = an.centry[e];
-        const int f = ent >> 1, side = ent & 1;
-        const int meta = an.fmeta[f];
-        if ((meta & 3) != a) continue;
-        const int kind = (meta >> 2) & 3;
-        const int64_t nbc = side == 0 ? an.fR[f] : an.fL[f];
-        R mn[9];
-        cell_mean<R>(g, lt, (const T*)w, wmean, nbc, mn);
-        const bool self_coarse = (side == 0 && kind == 1) || (side == 1 && kind == 2);
-        const R fac = kind == 0 ? R(2) : (self_coarse ? R(1.5) : R(3));
-        if (side == 0) {
-          for (int k = 0; k < 9; ++k) mp[k] += mn[k];
-          ++np_;
-          fp = fac;
-        } else {
-          for (int k = 0; k < 9; ++k) mm[k] += mn[k];
-          ++nm_;
-          fm = fac;
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const int sidx = 2 * a + sd;  // sd 1: the +a side
+        const int inf = an.side_info[c * 6 + sidx];
+        const int cnt = inf & 15, rel = inf >> 4;
+        const R fac = rel == 0 ? R(2) : (rel == 1 ? R(1.5) : R(3));
+        R* acc = sd ? mp : mm;
+        for (int k2 = 0; k2 < cnt; ++k2) {
+          R mn[9];
+          cell_mean<R>(g, lt, (const T*)w, wmean, (int64_t)an.side_nb[c * 24 + sidx * 4 + k2], mn);
+          for (int k = 0; k < 9; ++k) acc[k] += mn[k];
+        }
+        if (cnt > 0) {
+          if (sd) {
+            np_ = cnt;
+            fp = fac;
+          } else {
+            nm_ = cnt;
+            fm = fac;
+          }
         }
       }
       // 1 or 2^(D-1) leaves: exact reciprocals
@@ -1035,7 +1039,8 @@ int run_limiter(Ctx& c, void* w, double* wmean, uint8_t* troubled, cudaStream_t 
     c.prof.begin(3, st);
     // FP32 form: the float mode-0 rows mirror the FP64 means exactly; reading
     // them avoids FP64 conversions (the limiter never changes the means)
-    const AmrNb an{c.amr.fL, c.amr.fR, c.amr.fmeta, c.amr.cstart, c.amr.centry, c.amr.dxc, c.amr.on ? 1 : 0};
+    const AmrNb an{c.amr.fL,  c.amr.fR, c.amr.fmeta, c.amr.cstart, c.amr.centry, c.amr.dxc, c.amr.on ? 1 : 0,
+                   c.amr.side_nb, c.amr.side_info};
     if (c.p.precision == DG_PREC_FP32MIX)
       screened ? k_tvb<float, true><<<nbt, 128, 0, st>>>(g, c.lim, (float*)w, nullptr, troubled, list, c.p, c.sc,
                                                           an, c.pos_list, c.pscr)
