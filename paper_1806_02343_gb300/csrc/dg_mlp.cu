@@ -116,17 +116,14 @@ struct GlobalSrc {
   __device__ float imdx(const MlpTabs& mt) const { return mt.inv_mdx; }
 };
 
-// Octree meshes (the face lists of dg_amr.cuh): the neighbour mean on side
+// Octree meshes (the per-side leaf lists of the context): the neighbour mean on side
 // (a, s) is the average of the leaves across that side (one of the same level
 // or coarser, or the 2^(D-1) finer ones), as the octree TVB procedure reads
 // it; the slope scale is the leaf's own M~ dx_K. A side without a leaf (the
 // edge of a partition's local mesh) reads the cell's own means.
 struct AmrFeat {
-  const int32_t* cstart;
-  const int32_t* centry;
-  const int32_t* fmeta;
-  const int32_t* fL;
-  const int32_t* fR;
+  const int32_t* side_nb;    // the leaves across each side, in face-entry order (AmrHost::side_nb)
+  const uint8_t* side_info;  // count | relation << 4 per leaf and side
   const double* dxc;
   double dxmin;  // the mesh's smallest cell (the one inv_mdx was made with)
   int on;
@@ -141,14 +138,11 @@ struct AmrSrc {
   __device__ float row(int r) const { return (float)w[(int64_t)r * g.stride + c]; }
   __device__ void nbraw(int a, int s, float* raw) const {
     float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int cnt = 0;
-    for (int e = af.cstart[c]; e < af.cstart[c + 1]; ++e) {
-      const int ent = af.centry[e];
-      const int f = ent >> 1, side = ent & 1;  // side 0: this cell is the face's left cell (its +a side)
-      if ((af.fmeta[f] & 3) != a || side != (s ? 0 : 1)) continue;
-      const int64_t cn = side == 0 ? af.fR[f] : af.fL[f];
+    const int sidx = 2 * a + (s ? 1 : 0);
+    const int cnt = af.side_info[c * 6 + sidx] & 15;
+    for (int k2 = 0; k2 < cnt; ++k2) {
+      const int64_t cn = af.side_nb[c * 24 + sidx * 4 + k2];
       for (int k = 0; k < 8; ++k) acc[k] += (float)w[(int64_t)mrow(g, k) * g.stride + cn];
-      ++cnt;
     }
     if (cnt == 0) {
       for (int k = 0; k < 8; ++k) raw[k] = (float)w[(int64_t)mrow(g, k) * g.stride + c];
@@ -927,7 +921,7 @@ int mlp_train_dev(const float* X, int ldx, const uint8_t* y, int64_t n, int nin,
 }
 
 static AmrFeat amr_feat(const Ctx& c) {
-  return AmrFeat{c.amr.cstart, c.amr.centry, c.amr.fmeta, c.amr.fL, c.amr.fR, c.amr.dxc, c.g.dx, c.amr.on ? 1 : 0};
+  return AmrFeat{c.amr.side_nb, c.amr.side_info, c.amr.dxc, c.g.dx, c.amr.on ? 1 : 0};
 }
 
 int mlp_build_tables(Ctx& c) {
