@@ -166,6 +166,18 @@ int dg_mhd_project(dg_mhd_ctx* ctx, const double* nodal, int npts, void* w, doub
 int dg_mhd_basis_values(int dim, int degree, int divB_scheme, int64_t npts, const double* xi, int64_t cap,
                         double* out, int* n_rows, int* n_vars);
 
+/* The map the specialised Powell kernels use between the 3D LDF basis of B
+ * (Sec. 3.3) and the Legendre coefficients of its components (HOST, no
+ * context, no device work): A[(j*3 + c)*n_modes + l] = <phi_j,c, P_l> / <P_l, P_l>
+ * for LDF function j of degree <= degree and component c, so the component
+ * c of sum_j w_j phi_j has Legendre coefficients sum_j w_j A[j][c][l] (exact:
+ * every component is a polynomial of total degree <= degree). Computed by
+ * quadrature with degree + 1 Gauss points per axis; entries below 1e-13 are
+ * zero. Writes *n_div, *n_modes and, if A is non-NULL and cap >=
+ * n_div*3*n_modes doubles, A (DG_E_ARG if too small or for a degree outside
+ * 0..3; DG_E_UNSUPPORTED if the expansion misses a function at the points). */
+int dg_mhd_ldf_legendre(int degree, int64_t cap, double* A, int* n_div, int* n_modes);
+
 /* Sets the GLM wave speed c_h and damping rate c_h^2/c_p^2 used by
  * dg_mhd_rhs (Sec. 4.1.5). dg_mhd_dt and dg_mhd_step set them on the device
  * themselves; this call is for evaluating the operator at chosen values. */

@@ -26,7 +26,7 @@ EXPORTS = [
     "dg_mhd_rhs", "dg_mhd_limit", "dg_mhd_dt", "dg_mhd_step", "dg_mhd_last_dt", "dg_mhd_status",
     "dg_mhd_profile", "dg_mhd_profile_read", "dg_mhd_launch_count", "dg_mhd_rhs_noalloc", "dg_mhd_destroy",
     "dg_mhd_strerror", "dg_mhd_mlp_features", "dg_mhd_mlp_set_weights", "dg_mhd_mlp_infer", "dg_mhd_mlp_loss_grad",
-    "dg_mhd_mlp_train", "dg_mhd_counters", "dg_mhd_positivity_listed", "dg_mhd_limiter_counts", "dg_mhd_divb", "dg_mhd_smoothness",
+    "dg_mhd_mlp_train", "dg_mhd_counters", "dg_mhd_positivity_listed", "dg_mhd_ldf_legendre", "dg_mhd_limiter_counts", "dg_mhd_divb", "dg_mhd_smoothness",
     "dg_mhd_amr_marks", "dg_mhd_regrid_plan", "dg_mhd_remap", "dg_mhd_regrid_plan_mesh",
     "dg_mhd_sibling_groups", "dg_mhd_octree_faces", "dg_mhd_basis_values", "dg_mhd_regrid_tables",
     "dg_mhd_probe", "dg_mhd_stage", "dg_mhd_set_dt", "dg_mhd_set_owned", "dg_mhd_glm_speeds",
@@ -92,6 +92,8 @@ def lib():
                                    ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_uint64,
                                    ctypes.POINTER(ctypes.c_double), vp]
     L.dg_mhd_positivity_listed.argtypes = [vp, i64p, ctypes.c_int]
+    L.dg_mhd_ldf_legendre.argtypes = [ctypes.c_int, ctypes.c_int64, vp, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]
     L.dg_mhd_counters.argtypes = [vp, i64p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                   ctypes.c_int]
     L.dg_mhd_limiter_counts.argtypes = [vp, i64p, i64p, i64p, ctypes.c_int]
@@ -259,6 +261,19 @@ def basis_values(dim, degree, divb, xi):
     out = np.zeros((R.value, V.value, P), dtype=np.float64)
     _check(lib().dg_mhd_basis_values(dim, degree, scheme, P, x.ctypes.data, out.size, out.ctypes.data,
                                      ctypes.byref(R), ctypes.byref(V)), "dg_mhd_basis_values")
+    return out
+
+
+def ldf_legendre(degree):
+    """The 3D LDF -> componentwise Legendre map of the specialised Powell
+    kernels (host, no GPU): float64 [n_div, 3, n_modes] with
+    B_c = sum_j w_j sum_l A[j, c, l] P_l."""
+    import numpy as np
+    nd, nm = ctypes.c_int(), ctypes.c_int()
+    _check(lib().dg_mhd_ldf_legendre(degree, 0, None, ctypes.byref(nd), ctypes.byref(nm)), "dg_mhd_ldf_legendre")
+    out = np.zeros((nd.value, 3, nm.value), dtype=np.float64)
+    _check(lib().dg_mhd_ldf_legendre(degree, out.size, out.ctypes.data, ctypes.byref(nd), ctypes.byref(nm)),
+           "dg_mhd_ldf_legendre")
     return out
 
 

@@ -200,41 +200,60 @@ inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 // ok = 0 when the basis lacks the structure the kernels rely on (three
 // constant functions, each along one axis, and no other function with a
 // non-zero mean). The same for every context of this degree.
+// A[(j * 3 + c) * n + l]: the Legendre coefficients of component c of the 3D
+// LDF function j of degree <= deg, by quadrature with deg + 1 Gauss points
+// per axis (exact: the products are polynomials of degree <= 2 deg per
+// axis), entries below 1e-13 set to zero, and the expansion checked against
+// the functions at the points (false if it misses by more than 1e-11).
+bool ldf_legendre_3d(int deg, std::vector<double>& A, int& ndiv, int& n) {
+  Basis L;
+  if (!L.build(3, deg, true)) return false;
+  ndiv = L.ndiv;
+  n = L.n;
+  std::vector<double> x1, w1;
+  gauss_legendre(deg + 1, x1, w1);
+  int Qv = 1;
+  for (int k = 0; k < 3; ++k) Qv *= deg + 1;
+  A.assign((size_t)ndiv * 3 * n, 0.0);
+  double xi[3];
+  for (int q = 0; q < Qv; ++q) {
+    vol_point(3, x1, q, xi);
+    double wq = 1.0;
+    for (int k = 0, qq = q; k < 3; ++k, qq /= deg + 1) wq *= w1[qq % (deg + 1)];
+    for (int l = 0; l < n; ++l) {
+      const double Pl = L.eval(L.leg[l], xi) * wq / L.leg_mass[l];
+      for (int j = 0; j < ndiv; ++j)
+        for (int cc = 0; cc < 3; ++cc) A[((size_t)j * 3 + cc) * n + l] += L.eval(L.ldf[j][cc], xi) * Pl;
+    }
+  }
+  for (double& x : A)
+    if (std::fabs(x) < 1e-13) x = 0.0;
+  for (int q = 0; q < Qv; ++q) {
+    vol_point(3, x1, q, xi);
+    for (int j = 0; j < ndiv; ++j)
+      for (int cc = 0; cc < 3; ++cc) {
+        double s = 0.0;
+        for (int l = 0; l < n; ++l) s += A[((size_t)j * 3 + cc) * n + l] * L.eval(L.leg[l], xi);
+        if (std::fabs(s - L.eval(L.ldf[j][cc], xi)) > 1e-11) return false;
+      }
+  }
+  return true;
+}
+
 template <typename T, int DEG>
 void build_pow_tabs(PowTabs<T, DEG>& pt) {
   using Dm = FastDims<DEG>;
   constexpr int N = Dm::N, NDIV = PowDims<DEG>::NDIV, NP = PowDims<DEG>::NP;
   pt = PowTabs<T, DEG>();
+  std::vector<double> A;
+  int nd = 0, nm = 0;
+  if (!ldf_legendre_3d(DEG, A, nd, nm) || nd != NDIV || nm != N) return;
   Basis L;
-  if (!L.build(3, DEG, true) || L.ndiv != NDIV || L.n != N) return;
+  L.build(3, DEG, true);
   std::vector<double> x1, w1;
   gauss_legendre(DEG + 1, x1, w1);
-  const int Qv = Dm::QV;
-  std::vector<double> A((size_t)NDIV * 3 * N, 0.0);  // [j][cc][l]
   double xi[3];
-  for (int q = 0; q < Qv; ++q) {
-    vol_point(3, x1, q, xi);
-    double wq = 1.0;
-    for (int k = 0, qq = q; k < 3; ++k, qq /= DEG + 1) wq *= w1[qq % (DEG + 1)];
-    for (int l = 0; l < N; ++l) {
-      const double Pl = L.eval(L.leg[l], xi) * wq / L.leg_mass[l];
-      for (int j = 0; j < NDIV; ++j)
-        for (int cc = 0; cc < 3; ++cc) A[((size_t)j * 3 + cc) * N + l] += L.eval(L.ldf[j][cc], xi) * Pl;
-    }
-  }
   auto a = [&](int j, int cc, int l) -> double& { return A[((size_t)j * 3 + cc) * N + l]; };
-  for (double& x : A)
-    if (std::fabs(x) < 1e-13) x = 0.0;
-  // the expansion reproduces every function at the points
-  for (int q = 0; q < Qv; ++q) {
-    vol_point(3, x1, q, xi);
-    for (int j = 0; j < NDIV; ++j)
-      for (int cc = 0; cc < 3; ++cc) {
-        double s = 0.0;
-        for (int l = 0; l < N; ++l) s += a(j, cc, l) * L.eval(L.leg[l], xi);
-        if (std::fabs(s - L.eval(L.ldf[j][cc], xi)) > 1e-11) return;
-      }
-  }
   int seen = 0;
   for (int j = 0; j < NDIV; ++j)
     for (int cc = 0; cc < 3; ++cc)
@@ -1172,6 +1191,20 @@ int dg_mhd_counters(dg_mhd_ctx* ctx, int64_t* pos_cells, double* inj_mass, doubl
     h.pos_cells = 0;
     h.inj_mass = h.inj_energy = 0.0;
     if (cudaMemcpy(c.sc, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) return DG_E_CUDA;
+  }
+  return DG_OK;
+}
+
+int dg_mhd_ldf_legendre(int degree, int64_t cap, double* A, int* n_div, int* n_modes) {
+  if (degree < 0 || degree > MAXD) return DG_E_ARG;
+  std::vector<double> M;
+  int nd = 0, nm = 0;
+  if (!ldf_legendre_3d(degree, M, nd, nm)) return DG_E_UNSUPPORTED;
+  if (n_div) *n_div = nd;
+  if (n_modes) *n_modes = nm;
+  if (A) {
+    if (cap < (int64_t)M.size()) return DG_E_ARG;
+    std::copy(M.begin(), M.end(), A);
   }
   return DG_OK;
 }

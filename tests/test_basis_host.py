@@ -175,3 +175,25 @@ def test_project_ic_input_preparation(B, case):
     mine = np.einsum("cqv,q,rqv->cr", u, qw, S.synth(qp)) / S.mass
     assert np.abs(mine - S.project(fn, npts=q)).max() < 1e-14
     assert torch.all(seen["nodal"][:, :, obj.ncell:] == 0)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_ldf_legendre_map_matches_oracle(d):
+    """The map with which the specialised Powell kernels carry B in the Legendre
+    form of its components (LDF coefficients mapped on load, residuals mapped
+    back on store) equals the oracle's exact rational projection of every LDF
+    function onto the Legendre modes, and has the structure the kernels rely
+    on: three constant functions, each along one axis, and no other function
+    with a non-zero mean."""
+    from oracle import mlp as M
+    from oracle.dg import Scheme
+    from paper_1806_02343_gb300 import binding
+    S = Scheme(3, d, "powell", 5.0 / 3.0, (2, 2, 2))
+    ref = M.ldf_to_legendre(S)
+    A = binding.ldf_legendre(d)
+    assert A.shape == ref.shape
+    assert np.max(np.abs(A - ref)) < 1e-13
+    assert np.all(A[:3, :, 1:] == 0.0)
+    axes = [np.flatnonzero(A[j, :, 0]) for j in range(3)]
+    assert all(len(x) == 1 for x in axes) and sorted(int(x[0]) for x in axes) == [0, 1, 2]
+    assert np.all(A[3:, :, 0] == 0.0)
