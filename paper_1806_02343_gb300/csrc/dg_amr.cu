@@ -382,59 +382,181 @@ __global__ void k_divb_list(Geom g, Tables<T> tb, AmrDev<T> am, const T* __restr
 
 __device__ __forceinline__ unsigned long long dbits_a(double x) { return (unsigned long long)__double_as_longlong(x); }
 
+// FP64 bound of leaf c (eq. cfl, eq. powell_dt from the face jumps of its
+// entries); *smax = the leaf's signal speed sum over the axes / D. Sets status
+// bit 1 and returns DBL_MAX where the bound is not a positive finite number.
+template <typename T>
+__device__ double dt_leaf64(const Geom& g, const Tables<T>& tb, const AmrDev<T>& am, const T* __restrict__ w,
+                            const double* __restrict__ wmean, const T* __restrict__ jbuf, const dg_mhd_params& p,
+                            DevScalars* __restrict__ sc, int64_t c, double* smax) {
+  const int64_t S = g.stride;
+  auto mean = [&](int m) { return wmean ? wmean[m * S + c] : (double)w[(int64_t)mrow_a(g, m) * S + c]; };
+  const double rho = mean(0);
+  const double vx = mean(1) / rho, vy = mean(2) / rho, vz = mean(3) / rho;
+  const double E = mean(4);
+  double b[3];
+  if (g.glm) {
+    b[0] = mean(5); b[1] = mean(6); b[2] = mean(7);
+  } else {
+    b[0] = b[1] = b[2] = 0.0;
+    for (int j = 0; j < g.DB; ++j)
+      for (int cc = 0; cc < g.DB; ++cc) b[cc] += mean(5 + j) * (double)tb.L0[j * g.DB + cc];
+    if (g.bz2d >= 0) b[2] = mean(7);
+  }
+  const double dx = am.dxc[c];
+  const double b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  const double pr = (g.gamma - 1.0) * (E - 0.5 * rho * (vx * vx + vy * vy + vz * vz) - 0.5 * b2);
+  const double cs = sqrt(g.gamma * pr / rho + b2 / rho);
+  const double av[3] = {fabs(vx), fabs(vy), fabs(vz)};
+  double s = 0.0;
+  for (int a = 0; a < g.D; ++a) s += (av[a] + cs) / dx;
+  double dtc = p.cfl / (2.0 * g.d + 1.0) / s;
+  *smax = s * dx / g.D;
+  if (!g.glm) {
+    double acc = 0.0;
+    for (int e = am.cstart[c]; e < am.cstart[c + 1]; ++e) {
+      const int ent = am.centry[e];
+      const int64_t f = ent >> 1;
+      const double dxf = fmin(am.dxc[am.fL[f]], am.dxc[am.fR[f]]);
+      double area = 1.0;
+      for (int a = 0; a < g.D - 1; ++a) area *= 0.5 * dxf;
+      double js = 0.0;
+      const int nq = g.jq ? g.jq : g.Qf;
+      for (int q = 0; q < nq; ++q) js += (double)jbuf[(f * nq + q) * 2 + (ent & 1)];
+      acc += area * js;
+    }
+    double divb = acc;
+    for (int a = 0; a < g.D; ++a) divb /= dx;
+    const double rate = divb * fabs(vx * b[0] + vy * b[1] + vz * b[2]) / E;
+    if (rate > 0.0) dtc = fmin(dtc, p.eta_powell / rate);
+  }
+  if (!(dtc > 0.0) || !isfinite(dtc)) {
+    atomicOr(&sc->status, 1);
+    dtc = DBL_MAX;
+  }
+  return dtc;
+}
+
+// The same bound in FP32 from the float mirror of the means (the screen of
+// the FP32 form, as on uniform meshes): FP64 from the means where the FP32
+// pressure would keep less than 1e-3 of E; FLT_MAX where not a positive
+// finite number (status bit 1).
+__device__ float dt_leaf32(const Geom& g, const Tables<float>& tb, const AmrDev<float>& am,
+                           const float* __restrict__ w, const double* __restrict__ wmean,
+                           const float* __restrict__ jbuf, const dg_mhd_params& p, DevScalars* __restrict__ sc,
+                           int64_t c, float* smax) {
+  const int64_t S = g.stride;
+  auto mean = [&](int m) { return w[(int64_t)mrow_a(g, m) * S + c]; };
+  const float gam = (float)g.gamma;
+  const float rho = mean(0), ir = 1.f / rho;
+  const float vx = mean(1) * ir, vy = mean(2) * ir, vz = mean(3) * ir;
+  const float E = mean(4);
+  float b[3];
+  if (g.glm) {
+    b[0] = mean(5); b[1] = mean(6); b[2] = mean(7);
+  } else {
+    b[0] = b[1] = b[2] = 0.f;
+    for (int j = 0; j < g.DB; ++j)
+      for (int cc = 0; cc < g.DB; ++cc) b[cc] += mean(5 + j) * tb.L0[j * g.DB + cc];
+    if (g.bz2d >= 0) b[2] = mean(7);
+  }
+  const float b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  float pr = (gam - 1.f) * (E - 0.5f * rho * (vx * vx + vy * vy + vz * vz) - 0.5f * b2);
+  if (!(pr > 1e-3f * E)) {
+    double smd;
+    const double d64 = dt_leaf64<float>(g, tb, am, w, wmean, jbuf, p, sc, c, &smd);
+    *smax = (float)smd;
+    return d64 < DBL_MAX ? (float)d64 : FLT_MAX;
+  }
+  const float dx = (float)am.dxc[c];
+  const float cs = sqrtf((gam * pr + b2) * ir);
+  const float av[3] = {fabsf(vx), fabsf(vy), fabsf(vz)};
+  float sum = 0.f;
+  for (int a = 0; a < g.D; ++a) sum += av[a] + cs;
+  float dtc = (float)(p.cfl / (2.0 * g.d + 1.0)) * dx / sum;
+  *smax = sum / (float)g.D;
+  if (!g.glm) {
+    float acc = 0.f;
+    const int nq = g.jq ? g.jq : g.Qf;
+    for (int e = am.cstart[c]; e < am.cstart[c + 1]; ++e) {
+      const int ent = am.centry[e];
+      const int64_t f = ent >> 1;
+      const float dxf = (float)fmin(am.dxc[am.fL[f]], am.dxc[am.fR[f]]);
+      float area = 1.f;
+      for (int a = 0; a < g.D - 1; ++a) area *= 0.5f * dxf;
+      float js = 0.f;
+      for (int q = 0; q < nq; ++q) js += jbuf[(f * nq + q) * 2 + (ent & 1)];
+      acc += area * js;
+    }
+    float divb = acc;
+    for (int a = 0; a < g.D; ++a) divb /= dx;
+    const float rate = divb * fabsf(vx * b[0] + vy * b[1] + vz * b[2]) / E;
+    if (rate > 0.f) dtc = fminf(dtc, (float)p.eta_powell / rate);
+  }
+  if (!(dtc > 0.f) || !isfinite(dtc)) {
+    atomicOr(&sc->status, 1);
+    dtc = FLT_MAX;
+  }
+  return dtc;
+}
+
+// Pass 1 of the FP32 form's octree timestep: every leaf's FP32 bound, the
+// minimum into dt_bits and the signal-speed maximum (block reduction).
+__global__ void k_dt_list32(Geom g, Tables<float> tb, AmrDev<float> am, const float* __restrict__ w,
+                            const double* __restrict__ wmean, const float* __restrict__ jbuf, dg_mhd_params p,
+                            DevScalars* __restrict__ sc) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float dtc = FLT_MAX, smax = 0.f;
+  if (c < g.ncell && (!g.owned || g.owned[c])) dtc = dt_leaf32(g, tb, am, w, wmean, jbuf, p, sc, c, &smax);
+  __shared__ float red[256];
+  __shared__ float reds[256];
+  red[threadIdx.x] = dtc;
+  reds[threadIdx.x] = smax;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      red[threadIdx.x] = fminf(red[threadIdx.x], red[threadIdx.x + o]);
+      reds[threadIdx.x] = fmaxf(reds[threadIdx.x], reds[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (red[0] < FLT_MAX) atomicMin(&sc->dt_bits, dbits_a((double)red[0]));
+    atomicMax(&sc->smax_bits, dbits_a((double)reds[0]));
+  }
+}
+
+// Pass 2: the FP64 bounds of the leaves whose FP32 bound lies within 1e-3
+// (relative) of the FP32 minimum -- the FP32 bound is within 1e-4 of the FP64
+// one, so the leaf holding the FP64 minimum is among them -- min-reduced in
+// FP64 into dt64_bits, which the finalize step takes.
+constexpr float kDtScreenA = 1e-3f;
+__global__ void k_dt_list32_refine(Geom g, Tables<float> tb, AmrDev<float> am, const float* __restrict__ w,
+                                   const double* __restrict__ wmean, const float* __restrict__ jbuf,
+                                   dg_mhd_params p, DevScalars* __restrict__ sc) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double dtc = DBL_MAX;
+  if (c < g.ncell && (!g.owned || g.owned[c])) {
+    const double m32 = __longlong_as_double((long long)sc->dt_bits);
+    const float thr = m32 < DBL_MAX ? (float)m32 * (1.f + kDtScreenA) : -1.f;
+    float sm32;
+    const float d32 = dt_leaf32(g, tb, am, w, wmean, jbuf, p, sc, c, &sm32);
+    if (d32 <= thr) {
+      double sm64;
+      dtc = dt_leaf64<float>(g, tb, am, w, wmean, jbuf, p, sc, c, &sm64);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) dtc = fmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
+  if ((threadIdx.x & 31) == 0 && dtc < DBL_MAX) atomicMin(&sc->dt64_bits, dbits_a(dtc));
+}
+
 template <typename T>
 __global__ void k_dt_list(Geom g, Tables<T> tb, AmrDev<T> am, const T* __restrict__ w,
                           const double* __restrict__ wmean, const T* __restrict__ jbuf, dg_mhd_params p,
                           DevScalars* __restrict__ sc) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double dtc = DBL_MAX, smax = 0.0;
-  if (c < g.ncell && (!g.owned || g.owned[c])) {
-    const int64_t S = g.stride;
-    auto mean = [&](int m) { return wmean ? wmean[m * S + c] : (double)w[(int64_t)mrow_a(g, m) * S + c]; };
-    const double rho = mean(0);
-    const double vx = mean(1) / rho, vy = mean(2) / rho, vz = mean(3) / rho;
-    const double E = mean(4);
-    double b[3];
-    if (g.glm) {
-      b[0] = mean(5); b[1] = mean(6); b[2] = mean(7);
-    } else {
-      b[0] = b[1] = b[2] = 0.0;
-      for (int j = 0; j < g.DB; ++j)
-        for (int cc = 0; cc < g.DB; ++cc) b[cc] += mean(5 + j) * (double)tb.L0[j * g.DB + cc];
-      if (g.bz2d >= 0) b[2] = mean(7);
-    }
-    const double dx = am.dxc[c];
-    const double b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-    const double pr = (g.gamma - 1.0) * (E - 0.5 * rho * (vx * vx + vy * vy + vz * vz) - 0.5 * b2);
-    const double cs = sqrt(g.gamma * pr / rho + b2 / rho);
-    const double av[3] = {fabs(vx), fabs(vy), fabs(vz)};
-    double s = 0.0;
-    for (int a = 0; a < g.D; ++a) s += (av[a] + cs) / dx;
-    dtc = p.cfl / (2.0 * g.d + 1.0) / s;
-    smax = s * dx / g.D;
-    if (!g.glm) {
-      double acc = 0.0;
-      for (int e = am.cstart[c]; e < am.cstart[c + 1]; ++e) {
-        const int ent = am.centry[e];
-        const int64_t f = ent >> 1;
-        const double dxf = fmin(am.dxc[am.fL[f]], am.dxc[am.fR[f]]);
-        double area = 1.0;
-        for (int a = 0; a < g.D - 1; ++a) area *= 0.5 * dxf;
-        double js = 0.0;
-        const int nq = g.jq ? g.jq : g.Qf;
-        for (int q = 0; q < nq; ++q) js += (double)jbuf[(f * nq + q) * 2 + (ent & 1)];
-        acc += area * js;
-      }
-      double divb = acc;
-      for (int a = 0; a < g.D; ++a) divb /= dx;
-      const double rate = divb * fabs(vx * b[0] + vy * b[1] + vz * b[2]) / E;
-      if (rate > 0.0) dtc = fmin(dtc, p.eta_powell / rate);
-    }
-    if (!(dtc > 0.0) || !isfinite(dtc)) {
-      atomicOr(&sc->status, 1);
-      dtc = DBL_MAX;
-    }
-  }
+  if (c < g.ncell && (!g.owned || g.owned[c])) dtc = dt_leaf64<T>(g, tb, am, w, wmean, jbuf, p, sc, c, &smax);
   __shared__ double red[256];
   __shared__ double reds[256];
   red[threadIdx.x] = dtc;
@@ -760,6 +882,14 @@ void launch_amr_dt(const Ctx& c, const Tables<T>& tb, const T* w, const double* 
   } else if (!g.glm) {
     const int64_t np = am.nface * g.Qf;
     k_divb_list<T><<<(unsigned)((np + 127) / 128), 128, 0, st>>>(g, tb, am, w, jbuf);
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (wmean) {
+      // FP32 form: FP32 screen of every leaf, FP64 bounds of the candidates
+      k_dt_list32<<<(unsigned)((g.ncell + 255) / 256), 256, 0, st>>>(g, tb, am, w, wmean, jbuf, p, sc);
+      k_dt_list32_refine<<<(unsigned)((g.ncell + 255) / 256), 256, 0, st>>>(g, tb, am, w, wmean, jbuf, p, sc);
+      return;
+    }
   }
   k_dt_list<T><<<(unsigned)((g.ncell + 255) / 256), 256, 0, st>>>(g, tb, am, w, wmean, jbuf, p, sc);
 }

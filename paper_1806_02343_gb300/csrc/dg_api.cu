@@ -941,7 +941,8 @@ int dt_pass(Ctx& c, const void* w, const double* wmean, double* dt_out, cudaStre
     else launch_amr_dt<double>(c, c.t64, (const double*)w, nullptr, c.face_buf, c.p, c.sc, st);
     launch_dt_finalize(g, c.p, c.sc, dt_out, st);
     c.prof.end(2, st);
-    c.prof.launches[2] += g.glm ? 2 : 3;
+    // k_dt_init, the jump kernel (Powell), k_dt_list (FP32 form: k_dt_list32 + its refine), k_dt_finalize
+    c.prof.launches[2] += (g.glm ? 2 : 3) + (fp32(c) ? 1 : 0);
     return cudaGetLastError() == cudaSuccess ? DG_OK : DG_E_CUDA;
   }
   c.prof.begin(2, st);

@@ -96,6 +96,30 @@ def test_amr_dt_and_steps_fp64(D, divb):
     assert sol.status() == 0
 
 
+@pytest.mark.parametrize("divb", ["powell", "glm"])
+def test_amr_dt_fp32_form(divb):
+    """FP32 form on an octree: an FP32 screen of every leaf, then FP64 bounds of
+    the leaves within 1e-3 of the FP32 minimum, min-reduced in FP64 -- the CFL
+    bound equals the oracle's to rounding; the Powell bound reads the face
+    jumps of FP32 traces (5e-3, as on uniform meshes)."""
+    leaves = _mesh(3)
+    A = AMRScheme(3, 2, divb, G, leaves)
+    A.P.c_h_fixed = 4.0
+    w0 = A.project(_fn(3, A.V))
+    sol = _solver(A, leaves, prec="fp32", c_h_fixed=4.0)
+    w = to_device(w0, sol)
+    wm = means_to_device(w0, sol, A)
+    dt = sol.dt(w, wm).item()
+    ref = A.dt(w0)
+    eta = A.P.eta_powell
+    A.P.eta_powell = float("inf")
+    cfl_only = A.dt(w0)
+    A.P.eta_powell = eta
+    tol = 1e-13 if (divb == "glm" or cfl_only == ref) else 5e-3
+    assert abs(dt - ref) <= tol * ref
+    assert sol.status() == 0
+
+
 @pytest.mark.parametrize("D,divb", [(3, "powell"), (3, "glm")])
 def test_amr_fp32_form_steps(D, divb):
     import torch
