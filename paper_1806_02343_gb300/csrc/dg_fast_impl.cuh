@@ -308,10 +308,10 @@ __global__ void __launch_bounds__(NT, 3) k_cell_glm(const CellTabs<T, DEG> tbp, 
   const T ch = pick_prec<T>(sc->ch, sc->ch32);
 
   T wl[N];
-#pragma unroll
   {
     // pointer steps of one row (S elements) instead of a 64-bit index per load
     const T* pw = w + (int64_t)(v * N) * S + c;
+#pragma unroll
     for (int l = 0; l < N; ++l, pw += S) wl[l] = live ? *pw : (v == 0 && l == 0 ? T(1) : T(0));
   }
   // (FP32 form: wl[0] is the float mirror of the FP64 mean, an exact copy)
